@@ -1,0 +1,251 @@
+"""Plain FP64 CPU oracle for the lubrication correction of arXiv:1308.6482.
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA library (``paper_1308_6482_gb300``) and neither
+imports the other.  The arithmetic lives in ``lub_oracle.c`` (plain C, double
+precision, paper order); this module only marshals numpy arrays.
+
+Particles are given as a dict of 1-D arrays with the keys
+``x y z qw qx qy qz r_par r_perp vx vy vz wx wy wz`` (any float dtype; they
+are converted exactly to float64).  The domain is a dict with ``L`` (3),
+``periodic`` (3 bools), ``walls`` (list of ``(z, dir)`` with ``dir=+1`` for a
+wall whose fluid side is +z).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lub_oracle.c")
+_SO = os.path.join(_HERE, "liborc.so")
+
+ST_OVERLAP = 1
+ST_NOCONV = 2
+ST_DEGENERATE = 4
+
+# cut-offs of Eq. results:cutoffs and mu = rho nu = 1/6 (tau = 1)
+DEFAULT_PARAMS = dict(mu=1.0 / 6.0, delta_n=2.0 / 3.0, delta_t=0.5, delta_r=0.25,
+                      h_c=0.0, eps_c=0.0, list_cutoff=1.0)
+
+_FIELDS = ("x", "y", "z", "qw", "qx", "qy", "qz", "r_par", "r_perp",
+           "vx", "vy", "vz", "wx", "wy", "wz")
+
+
+def build(force=False):
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Particles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(f, ctypes.POINTER(ctypes.c_double)) for f in _FIELDS]
+
+
+class _Domain(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("periodic", ctypes.c_int32 * 3),
+                ("n_walls", ctypes.c_int32), ("wall_z", ctypes.c_double * 2),
+                ("wall_dir", ctypes.c_int32 * 2)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff")]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.POINTER
+        dp, ip = P(ctypes.c_double), P(ctypes.c_int32)
+        lib.orc_candidates.restype = ctypes.c_int64
+        lib.orc_candidates.argtypes = [P(_Particles), P(_Domain), ctypes.c_double, ip, ip, ctypes.c_int64]
+        lib.orc_closest.restype = None
+        lib.orc_closest.argtypes = [P(_Particles), P(_Domain), ctypes.c_int64, ip, ip, dp, dp, dp, dp, ip]
+        lib.orc_pair_force.restype = None
+        lib.orc_pair_force.argtypes = [P(_Particles), P(_Domain), P(_Params), ctypes.c_int64, ip, ip,
+                                       dp, dp, dp, dp, dp, dp, dp, dp, ip]
+        lib.orc_apply.restype = None
+        lib.orc_apply.argtypes = [ctypes.c_int64, ctypes.c_int64, ip, ip, dp, dp, dp, dp]
+        lib.orc_surface_geometry.restype = None
+        lib.orc_surface_geometry.argtypes = [P(_Particles), ctypes.c_int64, dp, dp, dp]
+        lib.orc_g.restype = ctypes.c_double
+        lib.orc_g.argtypes = [P(_Particles), P(_Domain), ctypes.c_int32, ctypes.c_int32, dp]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+class Particles:
+    """FP64 copies of the particle arrays, kept alive for the C calls."""
+
+    def __init__(self, parts):
+        n = len(parts["x"])
+        self.arrays = {}
+        for f in _FIELDS:
+            a = parts.get(f)
+            if a is None:
+                a = np.zeros(n)
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+            assert a.shape == (n,), (f, a.shape)
+            self.arrays[f] = a
+        self.n = n
+        self.c = _Particles(n, *[_dp(self.arrays[f]) for f in _FIELDS])
+
+
+def _domain(dom):
+    walls = dom.get("walls", [])
+    assert len(walls) <= 2
+    d = _Domain()
+    for k in range(3):
+        d.L[k] = float(dom["L"][k])
+        d.periodic[k] = int(bool(dom["periodic"][k]))
+    d.n_walls = len(walls)
+    for w, (z, s) in enumerate(walls):
+        d.wall_z[w] = float(z)
+        d.wall_dir[w] = int(s)
+    return d
+
+
+def _params(prm):
+    p = dict(DEFAULT_PARAMS)
+    if prm:
+        p.update({k: v for k, v in prm.items() if k in DEFAULT_PARAMS})
+    return _Params(*[float(p[k]) for k in
+                     ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff")])
+
+
+def _as_particles(parts):
+    return parts if isinstance(parts, Particles) else Particles(parts)
+
+
+def candidates(parts, dom, list_cutoff=1.0):
+    """Candidate pairs by the paper's pre-filters (Sec. III A); (pi, pj) int32.
+
+    Particle pairs in (i, j) order with i < j, then wall pairs (j = -1 - w)
+    in (i, w) order."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    cnt = lib.orc_candidates(ctypes.byref(P.c), ctypes.byref(D), float(list_cutoff), None, None, 0)
+    pi = np.zeros(max(cnt, 1), np.int32)
+    pj = np.zeros(max(cnt, 1), np.int32)
+    lib.orc_candidates(ctypes.byref(P.c), ctypes.byref(D), float(list_cutoff), _ip(pi), _ip(pj), cnt)
+    return pi[:cnt], pj[:cnt]
+
+
+def closest(parts, dom, pi, pj):
+    """Points of closest approach: dict(n, h, yi, yj, status)."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    m = len(pi)
+    n = np.zeros((m, 3))
+    h = np.zeros(m)
+    yi = np.zeros((m, 3))
+    yj = np.zeros((m, 3))
+    st = np.zeros(m, np.int32)
+    if m:
+        lib.orc_closest(ctypes.byref(P.c), ctypes.byref(D), m, _ip(pi), _ip(pj), _dp(n), _dp(h),
+                        _dp(yi), _dp(yj), _ip(st))
+    return dict(n=n, h=h, yi=yi, yj=yj, status=st)
+
+
+def pair_force(parts, dom, prm, pi, pj, cp, want_k=False, want_geom=False):
+    """Per-pair F_i, T_i (lab, T about y*_i) and lever arms; optionally K~ and geometry.
+
+    Returns dict(FT [m,6], lever [m,6], Kt [m,6,6], geom [m,32], status)."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    p = _params(prm)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    m = len(pi)
+    FT = np.zeros((m, 6))
+    lever = np.zeros((m, 6))
+    Kt = np.zeros((m, 36)) if want_k else None
+    geom = np.zeros((m, 32)) if want_geom else None
+    st = np.array(cp["status"], np.int32, copy=True)
+    if m:
+        lib.orc_pair_force(ctypes.byref(P.c), ctypes.byref(D), ctypes.byref(p), m, _ip(pi), _ip(pj),
+                           _dp(np.ascontiguousarray(cp["n"], np.float64)),
+                           _dp(np.ascontiguousarray(cp["h"], np.float64)),
+                           _dp(np.ascontiguousarray(cp["yi"], np.float64)),
+                           _dp(np.ascontiguousarray(cp["yj"], np.float64)),
+                           _dp(FT), _dp(lever), _dp(Kt) if want_k else None,
+                           _dp(geom) if want_geom else None, _ip(st))
+    out = dict(FT=FT, lever=lever, status=st)
+    if want_k:
+        out["Kt"] = Kt.reshape(m, 6, 6)
+    if want_geom:
+        out["geom"] = geom
+    return out
+
+
+def apply(nparticles, pi, pj, FT, lever):
+    """Per-particle force and torque [n,3] each (Newton's third law for j)."""
+    lib = _load()
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    FT = np.ascontiguousarray(FT, np.float64)
+    lever = np.ascontiguousarray(lever, np.float64)
+    f = np.zeros((nparticles, 3))
+    t = np.zeros((nparticles, 3))
+    lib.orc_apply(nparticles, len(pi), _ip(pi), _ip(pj), _dp(FT), _dp(lever), _dp(f), _dp(t))
+    return f, t
+
+
+def surface_geometry(parts, k, y, nrm):
+    """(x1[3], S1, S2, Gamma0, Gamma2, p) of particle k at surface point y."""
+    lib = _load()
+    P = _as_particles(parts)
+    out = np.zeros(8)
+    y = np.ascontiguousarray(y, np.float64)
+    nrm = np.ascontiguousarray(nrm, np.float64)
+    lib.orc_surface_geometry(ctypes.byref(P.c), int(k), _dp(y), _dp(nrm), _dp(out))
+    return out[:3], out[3], out[4], out[5], out[6], out[7]
+
+
+def g_value(parts, dom, i, j, n):
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    n = np.ascontiguousarray(n, np.float64)
+    return lib.orc_g(ctypes.byref(P.c), ctypes.byref(D), int(i), int(j), _dp(n))
+
+
+def step(parts, dom, prm=None):
+    """The whole path on the CPU: candidates, closest points, pair forces, sums."""
+    p = dict(DEFAULT_PARAMS)
+    if prm:
+        p.update(prm)
+    P = _as_particles(parts)
+    pi, pj = candidates(P, dom, p["list_cutoff"])
+    cp = closest(P, dom, pi, pj)
+    pf = pair_force(P, dom, p, pi, pj, cp)
+    f, t = apply(P.n, pi, pj, pf["FT"], pf["lever"])
+    return dict(pi=pi, pj=pj, force=f, torque=t, **cp, FT=pf["FT"], lever=pf["lever"],
+                pair_status=pf["status"])
