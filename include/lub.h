@@ -1,0 +1,214 @@
+/*
+ * liblub -- lubrication corrections for near-contact spheroids, spheres and
+ * plane walls, after Janoschek, Harting & Toschi, "Accurate lubrication
+ * corrections for spherical and non-spherical particles in discretized fluid
+ * simulations" (arXiv:1308.6482), on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The correction of one step is four calls, enqueued in order on one CUDA
+ * stream:
+ *
+ *   lub_pairs_build     candidate pairs (Sec. III A pre-filters)
+ *   lub_closest_points  closest points, normal and signed gap (Sec. III A)
+ *   lub_resistance      curvatures, K~ and the pair force/torque
+ *                       (Sec. III B, Eqs. lub:resistance-correction,
+ *                       lub:model and the Appendix)
+ *   lub_apply           per-particle force and torque (Sec. III B)
+ *
+ * Conventions shared by every call
+ *   - Every array argument is DEVICE memory owned by the caller, unless the
+ *     argument's comment says "host".  The library never frees, resizes or
+ *     keeps caller memory beyond the call.
+ *   - Calls only enqueue work on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) and return without synchronising,
+ *     except where a host-side output is requested (stated per call).
+ *   - Particle arrays are structure-of-arrays with n entries each.  The
+ *     quaternion is scalar-first; the particle's body z axis is its axis of
+ *     rotational symmetry (semi-axis r_par); body x and y carry r_perp
+ *     (Eq. lub:spheroid).  The rotation used is that of q/|q|.
+ *   - Per-pair arrays are structure-of-arrays with `capacity` entries per
+ *     component: component c of pair k is at [c * capacity + k].
+ *   - Pair k processes pair_i[k] and pair_j[k]; pair_j[k] = -1 - w denotes
+ *     plane wall w.  Calls that take d_count process min(*d_count, capacity)
+ *     pairs, reading *d_count on the device (no host round trip).
+ *   - Return value: LUB_OK (0) or a negative LUB_ERR_* code; lub_last_error()
+ *     returns a message for the context's last failure.  No call aborts,
+ *     exits or traps the GPU.  Problems of one pair (overlap, no convergence,
+ *     bad index or shape) go to that pair's status byte, not the return code.
+ *   - Units are lattice units; mu = rho nu (1/6 at tau = 1, Sec. II).
+ *   - Thread safety: one context per host thread, or external locking.
+ */
+#ifndef LUB_H
+#define LUB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define LUB_OK            0
+#define LUB_ERR_ARG      (-1) /* invalid argument (null pointer, size, domain) */
+#define LUB_ERR_CAPACITY (-2) /* more candidate pairs than capacity */
+#define LUB_ERR_CUDA     (-3) /* a CUDA runtime call failed */
+#define LUB_ERR_TIMEOUT  (-4) /* a bounded device wait ran out */
+#define LUB_ERR_NOMEM    (-5) /* the context could not allocate its scratch */
+
+/* lub_params.precision */
+#define LUB_FP64  0 /* every step in double precision */
+#define LUB_MIXED 1 /* FP32 Newton, curvature, K~ and sums; FP64 gap always,
+                       FP64 Newton refinement when h/a < fp64_switch */
+
+/* lub_params.warm_start */
+#define LUB_WARM_NONE     0 /* Newton starts from the line of centres (Sec. III A) */
+#define LUB_WARM_PREVIOUS 1 /* Newton starts from the normal passed in n (in/out) */
+
+/* per-pair status bits */
+#define LUB_ST_OVERLAP    1  /* h <= 0 */
+#define LUB_ST_NOCONV     2  /* Newton did not converge within max_newton */
+#define LUB_ST_DEGENERATE 4  /* bad index, non-positive or non-finite shape, coincident centres */
+#define LUB_ST_FP64       8  /* mixed mode: refined by FP64 Newton (h/a < fp64_switch) */
+
+typedef struct lub_ctx lub_ctx;
+
+typedef struct {
+    const double *x, *y, *z;          /* centre r_i                        [n] */
+    const float *qw, *qx, *qy, *qz;   /* orientation quaternion            [n] */
+    const float *r_par, *r_perp;      /* semi-axes R_par, R_perp (> 0)     [n] */
+    const float *vx, *vy, *vz;        /* translational velocity v_i        [n] */
+    const float *wx, *wy, *wz;        /* angular velocity omega_i          [n] */
+    int32_t n;                        /* number of particles (>= 0)            */
+    float max_semi_axis;              /* upper bound of max(r_par, r_perp) over
+                                         all particles; used by lub_pairs_build
+                                         to size its cell grid.  0 = the call
+                                         computes it (one stream synchronise) */
+} lub_particles;
+
+typedef struct {
+    double L[3];          /* box edge lengths; positions need not be wrapped     */
+    int32_t periodic[3];  /* 1 = periodic along that axis (minimum image)        */
+    int32_t n_walls;      /* 0, 1 or 2 plane walls normal to z                    */
+    double wall_z[2];     /* wall w is the plane z = wall_z[w]                    */
+    int32_t wall_dir[2];  /* +1: fluid on the z > wall_z side, -1: z < wall_z     */
+} lub_domain;
+
+typedef struct {
+    double mu;            /* dynamic viscosity (1/6 at tau = 1)                      */
+    double delta_n;       /* cut-off of K33 (Eq. results:cutoffs: 2/3)                */
+    double delta_t;       /* cut-off of the other translational elements (1/2)       */
+    double delta_r;       /* cut-off of K44, K45, K54, K55 (1/4)                      */
+    double h_c;           /* contact cut-off of Eq. lub:model (0 = none: h <= 0 pairs
+                             contribute nothing and are flagged OVERLAP)               */
+    double eps_c;         /* stiffness of the Hookean repulsion, Eq. lub:frep         */
+    double list_cutoff;   /* Delta_L: pairs with a possible gap below this are listed */
+    int32_t precision;    /* LUB_FP64 or LUB_MIXED                                     */
+    double fp64_switch;   /* mixed mode: h/a below which Newton is refined in FP64;
+                             a = smallest semi-axis of the pair                        */
+    int32_t max_newton;   /* Newton iteration cap per precision stage (1..64)          */
+    double newton_tol;    /* step-size tolerance (radians) of the FP32 stage; the FP64
+                             stage converges to rounding                                */
+    int32_t warm_start;   /* LUB_WARM_NONE or LUB_WARM_PREVIOUS                        */
+} lub_params;
+
+/* Fill *p with the paper's values: mu = 1/6, Delta_n = 2/3, Delta_t = 1/2,
+ * Delta_r = 1/4 (Eq. results:cutoffs), h_c = eps_c = 0, list_cutoff = 1,
+ * LUB_MIXED, fp64_switch = 1e-3, max_newton = 32, newton_tol = 2e-5,
+ * LUB_WARM_NONE. */
+void lub_default_params(lub_params *p);
+
+/* Create a context (library-owned scratch, grown on demand by the calls that
+ * need it: lub_pairs_build and deterministic lub_apply).  *ctx receives the
+ * handle.  Errors: LUB_ERR_ARG (ctx NULL), LUB_ERR_NOMEM. */
+int lub_ctx_create(lub_ctx **ctx);
+
+/* Free the context and its device scratch (synchronises the device first). */
+int lub_ctx_destroy(lub_ctx *ctx);
+
+/* Message for the context's last error ("" if none); valid until the next
+ * call on the same context.  ctx may be NULL (returns a generic message). */
+const char *lub_last_error(const lub_ctx *ctx);
+
+/*
+ * Candidate pairs (Sec. III A).  A pair (i, j), i < j, is listed unless
+ *   r_ij > Rmax_i + Rmax_j + Delta_L, or
+ *   r_ij - sigma_i(r^_ij) > Rmax_j + Delta_L, or r_ij - sigma_j(r^_ij) > Rmax_i + Delta_L,
+ * where r_ij is the minimum-image centre distance, Rmax = max(r_par, r_perp)
+ * and sigma_k(e) the half-width of particle k along e (the plane test of
+ * Sec. III A, with R_c = Rmax + Delta_L for particles of different size).
+ * Particle w-wall pair (i, -1-w) is listed when the exact gap
+ * wall_dir (z_i - wall_z) - sigma_i(e_z) < Delta_L.  The decisions are those
+ * of double precision arithmetic.
+ *
+ * Order: particle pairs by (i, j) ascending, then wall pairs by (i, w).
+ * Writes pair_i[k], pair_j[k] for k < min(count, capacity) and *d_count =
+ * count (device int32).  If count > capacity the listed content is
+ * unspecified and the call returns LUB_ERR_CAPACITY when h_count_or_null is
+ * given (host int32, receives count; the call then synchronises `stream`).
+ * Without h_count_or_null the call does not synchronise (unless
+ * max_semi_axis is 0) and overflow is visible only through *d_count.
+ * Periodic axes need L >= 2 (2 Rmax + Delta_L) (else LUB_ERR_ARG).
+ * Uses context scratch (cell grid, counts), grown with cudaMalloc as needed.
+ */
+int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
+                    const lub_params *prm, int32_t *pair_i, int32_t *pair_j, int32_t capacity,
+                    int32_t *d_count, int32_t *h_count_or_null, void *stream);
+
+/*
+ * Closest points and signed gap (Sec. III A, with the overlap extension).
+ * For each pair, n* maximises g(n) = n.d - sigma_i(n) - sigma_j(n) over unit
+ * n (d = minimum-image r_j - r_i), solved by Newton iteration on the sphere
+ * from n = d/|d| (the paper's line-of-centres start) or, with
+ * LUB_WARM_PREVIOUS, from the n passed in.  Outputs:
+ *   n     [3][capacity] double: unit outward normal of i at y*_i (points i -> j)
+ *   gap   [capacity] double: h = g(n*) (< 0 for overlap); y*_j - y*_i = h n
+ *   status[capacity] uint8: LUB_ST_* bits
+ *   iters [capacity] uint8: Newton iterations taken (FP32 + FP64 stages), or NULL
+ * Walls and two spheres use their closed forms (0 iterations).
+ * y*_i = r_i + M_i n / sigma_i(n), y*_j = r_j - M_j n / sigma_j(n), with
+ * M = Q diag(r_perp^2, r_perp^2, r_par^2) Q^T.
+ */
+int lub_closest_points(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
+                       const lub_params *prm, const int32_t *pair_i, const int32_t *pair_j,
+                       const int32_t *d_count, int32_t capacity, double *n, double *gap,
+                       uint8_t *status, uint8_t *iters, void *stream);
+
+/*
+ * Pair force and torque (Sec. III B, Eqs. lub:resistance,
+ * lub:resistance-correction, lub:frep, lub:model; Appendix).  From n and gap
+ * of lub_closest_points: principal directions and radii of curvature and the
+ * cubic coefficients at y*_i and y*_j, the combined-gap eigenproblem, the 16
+ * elements of K, K~ with the three cut-offs, the clipped gap and Hookean
+ * repulsion, the surface velocities V = v + omega x (y* - r), and
+ * (F_i, T_i) = mu K~ (V_j - V_i, Omega_j - Omega_i) turned into the lab frame.
+ * Outputs (type float for LUB_MIXED, double for LUB_FP64):
+ *   FT    [6][capacity]: F_i (lab) and T_i (lab, about y*_i)
+ *   lever [6][capacity]: y*_i - r_i and y*_j - r_j (zero for a wall)
+ * Pairs whose status has NOCONV or DEGENERATE, and pairs with h <= 0 when
+ * h_c = 0 (OVERLAP is then set in status), get zeros.  status is read and
+ * updated in place.
+ */
+int lub_resistance(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
+                   const lub_params *prm, const int32_t *pair_i, const int32_t *pair_j,
+                   const int32_t *d_count, int32_t capacity, const double *n, const double *gap,
+                   uint8_t *status, void *FT, void *lever, void *stream);
+
+/*
+ * Per-particle force and torque (Sec. III B):
+ *   f_i += F_i,  t_i += T_i + (y*_i - r_i) x F_i,
+ *   f_j -= F_i,  t_j += -T_i + (y*_j - r_j) x (-F_i)   (Eq. lub:resistance),
+ * wall sides dropped.  force, torque: [3][n] of the precision's type
+ * (float for LUB_MIXED, double for LUB_FP64).  accumulate = 0 zeroes them
+ * first.  deterministic = 1 sums each particle's contributions in a fixed
+ * order (pair index, then side), giving bitwise-reproducible results, using
+ * context scratch; deterministic = 0 uses atomic adds.
+ */
+int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count,
+              int32_t capacity, const void *FT, const void *lever, int32_t n, void *force,
+              void *torque, int32_t precision, int32_t accumulate, int32_t deterministic,
+              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LUB_H */

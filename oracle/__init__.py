@@ -176,7 +176,10 @@ def closest(parts, dom, pi, pj):
 def pair_force(parts, dom, prm, pi, pj, cp, want_k=False, want_geom=False):
     """Per-pair F_i, T_i (lab, T about y*_i) and lever arms; optionally K~ and geometry.
 
-    Returns dict(FT [m,6], lever [m,6], Kt [m,6,6], geom [m,32], status)."""
+    Returns dict(FT [m,6], lever [m,6], Kt [m,6,6], geom [m,40], status).
+
+    geom: S1 S2 S1' S2' G0 G2 G0' G2' phi lam1 lam2 chi kappa0..3 x1[3] x2[3] x3[3]
+    H33 h_eff u[6] (local relative surface velocity)."""
     lib = _load()
     P = _as_particles(parts)
     D = _domain(dom)
@@ -187,7 +190,7 @@ def pair_force(parts, dom, prm, pi, pj, cp, want_k=False, want_geom=False):
     FT = np.zeros((m, 6))
     lever = np.zeros((m, 6))
     Kt = np.zeros((m, 36)) if want_k else None
-    geom = np.zeros((m, 32)) if want_geom else None
+    geom = np.zeros((m, 40)) if want_geom else None
     st = np.array(cp["status"], np.int32, copy=True)
     if m:
         lib.orc_pair_force(ctypes.byref(P.c), ctypes.byref(D), ctypes.byref(p), m, _ip(pi), _ip(pj),

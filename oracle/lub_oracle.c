@@ -712,7 +712,7 @@ static void ktilde(const pairgeom_t *G, const orc_params *p, double he, double K
  * Returns the status bits it adds (OVERLAP when h_c = 0 and h <= 0). */
 static int pair_force_one(const orc_particles *P, const orc_domain *Dm, const orc_params *prm, int32_t i,
                           int32_t j, const double n[3], double h, const double yi[3], const double yj[3],
-                          double FT[6], double lever[6], double Ktout[36], double geom[32])
+                          double FT[6], double lever[6], double Ktout[36], double geom[40])
 {
     for (int k = 0; k < 6; ++k) FT[k] = 0.0;
     shape_t si, sj;
@@ -731,7 +731,7 @@ static int pair_force_one(const orc_particles *P, const orc_domain *Dm, const or
         lever[3 + k] = (j >= 0) ? yj[k] - rj[k] : 0.0;
     }
     if (Ktout) memset(Ktout, 0, 36 * sizeof(double));
-    if (geom) memset(geom, 0, 32 * sizeof(double));
+    if (geom) memset(geom, 0, 40 * sizeof(double));
     int st = 0;
     double he = h;
     if (prm->h_c > 0.0) {
@@ -804,6 +804,7 @@ static int pair_force_one(const orc_particles *P, const orc_domain *Dm, const or
         }
         geom[25] = G.Hcoef33;
         geom[26] = he;
+        for (int k = 0; k < 6; ++k) geom[27 + k] = u[k];
     }
     return st;
 }
@@ -812,13 +813,13 @@ void orc_pair_force(const orc_particles *P, const orc_domain *D, const orc_param
                     const int32_t *pi, const int32_t *pj, const double *n, const double *h,
                     const double *yi, const double *yj, double *FT /*[np][6]*/,
                     double *lever /*[np][6]*/, double *Kt /*[np][36] or NULL*/,
-                    double *geom /*[np][32] or NULL*/, int32_t *status /* |= */)
+                    double *geom /*[np][40] or NULL*/, int32_t *status /* |= */)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < np; ++k) {
         int st = pair_force_one(P, D, prm, pi[k], pj[k], n + 3 * k, h[k], yi + 3 * k, yj + 3 * k,
                                 FT + 6 * k, lever + 6 * k, Kt ? Kt + 36 * k : NULL,
-                                geom ? geom + 32 * k : NULL);
+                                geom ? geom + 40 * k : NULL);
         if (status) status[k] |= st;
     }
 }

@@ -1,0 +1,331 @@
+"""ctypes binding of liblub (include/lub.h).  Argument marshalling only."""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liblub.so")
+
+LUB_OK = 0
+LUB_ERR_ARG = -1
+LUB_ERR_CAPACITY = -2
+LUB_ERR_CUDA = -3
+LUB_ERR_TIMEOUT = -4
+LUB_ERR_NOMEM = -5
+LUB_FP64 = 0
+LUB_MIXED = 1
+LUB_WARM_NONE = 0
+LUB_WARM_PREVIOUS = 1
+LUB_ST_OVERLAP = 1
+LUB_ST_NOCONV = 2
+LUB_ST_DEGENERATE = 4
+LUB_ST_FP64 = 8
+
+_P_FIELDS = ("x", "y", "z", "qw", "qx", "qy", "qz", "r_par", "r_perp", "vx", "vy", "vz", "wx", "wy", "wz")
+
+
+class LubError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("liblub error %d: %s" % (code, msg))
+        self.code = code
+
+
+class lub_particles(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in _P_FIELDS] + [("n", ctypes.c_int32),
+                                                             ("max_semi_axis", ctypes.c_float)]
+
+
+class lub_domain(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("periodic", ctypes.c_int32 * 3), ("n_walls", ctypes.c_int32),
+                ("wall_z", ctypes.c_double * 2), ("wall_dir", ctypes.c_int32 * 2)]
+
+
+class lub_params(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("delta_n", ctypes.c_double), ("delta_t", ctypes.c_double),
+                ("delta_r", ctypes.c_double), ("h_c", ctypes.c_double), ("eps_c", ctypes.c_double),
+                ("list_cutoff", ctypes.c_double), ("precision", ctypes.c_int32), ("fp64_switch", ctypes.c_double),
+                ("max_newton", ctypes.c_int32), ("newton_tol", ctypes.c_double), ("warm_start", ctypes.c_int32)]
+
+
+# every exported symbol of include/lub.h
+EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
+           "lub_closest_points", "lub_resistance", "lub_apply")
+
+_lib = None
+
+
+def library_path():
+    return _SO
+
+
+def load_library():
+    """Load liblub.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise RuntimeError("liblub.so not found at %s: build it with paper_1308_6482_gb300.build.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback" % _SO)
+    lib = ctypes.CDLL(_SO)
+    P = ctypes.POINTER
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.lub_default_params.restype = None
+    lib.lub_default_params.argtypes = [P(lub_params)]
+    lib.lub_ctx_create.restype = ctypes.c_int
+    lib.lub_ctx_create.argtypes = [P(vp)]
+    lib.lub_ctx_destroy.restype = ctypes.c_int
+    lib.lub_ctx_destroy.argtypes = [vp]
+    lib.lub_last_error.restype = ctypes.c_char_p
+    lib.lub_last_error.argtypes = [vp]
+    lib.lub_pairs_build.restype = ctypes.c_int
+    lib.lub_pairs_build.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp,
+                                    P(i32), vp]
+    lib.lub_closest_points.restype = ctypes.c_int
+    lib.lub_closest_points.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp,
+                                       vp, vp, vp, vp]
+    lib.lub_resistance.restype = ctypes.c_int
+    lib.lub_resistance.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp,
+                                   vp, vp, vp, vp]
+    lib.lub_apply.restype = ctypes.c_int
+    lib.lub_apply.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, i32, i32, i32, vp]
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    """Device (or host) pointer of a tensor / numpy array / int / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, rc):
+    if rc != LUB_OK:
+        msg = load_library().lub_last_error(ctx).decode()
+        raise LubError(rc, msg)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+def lub_default_params():
+    p = lub_params()
+    load_library().lub_default_params(ctypes.byref(p))
+    return p
+
+
+def lub_ctx_create():
+    h = ctypes.c_void_p()
+    rc = load_library().lub_ctx_create(ctypes.byref(h))
+    if rc != LUB_OK:
+        raise LubError(rc, "lub_ctx_create failed")
+    return h.value
+
+
+def lub_ctx_destroy(ctx):
+    return load_library().lub_ctx_destroy(ctx)
+
+
+def lub_last_error(ctx):
+    return load_library().lub_last_error(ctx).decode()
+
+
+def lub_pairs_build(ctx, particles, domain, params, pair_i, pair_j, capacity, d_count, h_count=None,
+                    stream=None, check=True):
+    hc = ctypes.c_int32(0)
+    rc = load_library().lub_pairs_build(ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params),
+                                        _ptr(pair_i), _ptr(pair_j), int(capacity), _ptr(d_count),
+                                        ctypes.byref(hc) if h_count else None, _stream(stream))
+    if check and rc not in (LUB_OK, LUB_ERR_CAPACITY):
+        _check(ctx, rc)
+    return rc, (hc.value if h_count else None)
+
+
+def lub_closest_points(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status,
+                       iters=None, stream=None):
+    return _check(ctx, load_library().lub_closest_points(
+        ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
+        _ptr(d_count), int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _stream(stream)))
+
+
+def lub_resistance(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, FT, lever,
+                   stream=None):
+    return _check(ctx, load_library().lub_resistance(
+        ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
+        _ptr(d_count), int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(FT), _ptr(lever), _stream(stream)))
+
+
+def lub_apply(ctx, pair_i, pair_j, d_count, capacity, FT, lever, n, force, torque, precision, accumulate=0,
+              deterministic=0, stream=None):
+    return _check(ctx, load_library().lub_apply(
+        ctx, _ptr(pair_i), _ptr(pair_j), _ptr(d_count), int(capacity), _ptr(FT), _ptr(lever), int(n), _ptr(force),
+        _ptr(torque), int(precision), int(accumulate), int(deterministic), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# conveniences: device particles, domain, params, a context, one step
+# ---------------------------------------------------------------------------
+def default_params(**kw):
+    p = lub_default_params()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": LUB_FP64, "mixed": LUB_MIXED}[v]
+        setattr(p, k, v)
+    return p
+
+
+def make_domain(dom):
+    d = lub_domain()
+    for k in range(3):
+        d.L[k] = float(dom["L"][k])
+        d.periodic[k] = int(bool(dom["periodic"][k]))
+    walls = dom.get("walls", [])
+    d.n_walls = len(walls)
+    for w, (z, s) in enumerate(walls):
+        d.wall_z[w] = float(z)
+        d.wall_dir[w] = int(s)
+    return d
+
+
+class DeviceParticles:
+    """Particle arrays on the GPU (float64 centres, float32 the rest)."""
+
+    def __init__(self, parts, device="cuda", max_semi_axis=None):
+        import torch
+        n = len(parts["x"])
+        self.n = n
+        self.t = {}
+        for f in _P_FIELDS:
+            a = parts.get(f)
+            if a is None:
+                a = np.zeros(n)
+            dt = torch.float64 if f in ("x", "y", "z") else torch.float32
+            self.t[f] = torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(device)
+        if max_semi_axis is None:
+            max_semi_axis = float(max(np.max(parts["r_par"]), np.max(parts["r_perp"]))) if n else 1.0
+        self.c = lub_particles(*[self.t[f].data_ptr() for f in _P_FIELDS], n, float(max_semi_axis))
+
+    def refresh(self):
+        self.c = lub_particles(*[self.t[f].data_ptr() for f in _P_FIELDS], self.n, self.c.max_semi_axis)
+
+
+class Context:
+    def __init__(self):
+        self.h = lub_ctx_create()
+
+    def close(self):
+        if self.h:
+            lub_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """Buffers and the four calls of one correction step for one suspension."""
+
+    def __init__(self, parts, dom, params=None, capacity=None, device="cuda", ctx=None):
+        import torch
+        self.torch = torch
+        self.P = parts if isinstance(parts, DeviceParticles) else DeviceParticles(parts, device)
+        self.D = make_domain(dom)
+        self.prm = params if params is not None else default_params()
+        self.ctx = ctx or Context()
+        self.n = self.P.n
+        if capacity is None:
+            capacity = max(1024, 16 * self.n)
+        self._alloc(capacity, device)
+
+    def _alloc(self, cap, device):
+        torch = self.torch
+        self.cap = int(cap)
+        fdt = torch.float32 if self.prm.precision == LUB_MIXED else torch.float64
+        self.pair_i = torch.empty(self.cap, dtype=torch.int32, device=device)
+        self.pair_j = torch.empty(self.cap, dtype=torch.int32, device=device)
+        self.d_count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.nrm = torch.zeros(3 * self.cap, dtype=torch.float64, device=device)
+        self.gap = torch.empty(self.cap, dtype=torch.float64, device=device)
+        self.status = torch.empty(self.cap, dtype=torch.uint8, device=device)
+        self.iters = torch.empty(self.cap, dtype=torch.uint8, device=device)
+        self.FT = torch.empty(6 * self.cap, dtype=fdt, device=device)
+        self.lever = torch.empty(6 * self.cap, dtype=fdt, device=device)
+        self.force = torch.empty(3 * max(self.n, 1), dtype=fdt, device=device)
+        self.torque = torch.empty(3 * max(self.n, 1), dtype=fdt, device=device)
+
+    def build_pairs(self, sync_count=True, grow=True, stream=None):
+        h = self.ctx.h
+        rc, cnt = lub_pairs_build(h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.cap, self.d_count,
+                                  h_count=sync_count, stream=stream)
+        if rc == LUB_ERR_CAPACITY and grow:
+            self._alloc(int(cnt * 1.25) + 1024, self.pair_i.device)
+            rc, cnt = lub_pairs_build(h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.cap,
+                                      self.d_count, h_count=True, stream=stream)
+        if rc != LUB_OK:
+            _check(h, rc)
+        return cnt
+
+    def set_pairs(self, pi, pj):
+        torch = self.torch
+        m = len(pi)
+        if m > self.cap:
+            self._alloc(m, self.pair_i.device)
+        self.pair_i[:m] = torch.as_tensor(np.asarray(pi, np.int32), device=self.pair_i.device)
+        self.pair_j[:m] = torch.as_tensor(np.asarray(pj, np.int32), device=self.pair_i.device)
+        self.d_count.fill_(m)
+        return m
+
+    def closest(self, stream=None):
+        lub_closest_points(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap,
+                           self.nrm, self.gap, self.status, self.iters, stream=stream)
+
+    def resistance(self, stream=None):
+        lub_resistance(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap,
+                       self.nrm, self.gap, self.status, self.FT, self.lever, stream=stream)
+
+    def apply(self, deterministic=0, accumulate=0, stream=None):
+        lub_apply(self.ctx.h, self.pair_i, self.pair_j, self.d_count, self.cap, self.FT, self.lever, self.n,
+                  self.force, self.torque, self.prm.precision, accumulate, deterministic, stream=stream)
+
+    def step(self, build=True, deterministic=0, sync_count=False, stream=None):
+        if build:
+            self.build_pairs(sync_count=sync_count, grow=sync_count, stream=stream)
+        self.closest(stream)
+        self.resistance(stream)
+        self.apply(deterministic=deterministic, stream=stream)
+
+    # host views (synchronising)
+    def count(self):
+        return int(self.d_count.item())
+
+    def results(self):
+        m = min(self.count(), self.cap)
+        c = self.cap
+        g = lambda t: t.cpu().numpy()
+        nrm = g(self.nrm).reshape(3, c)[:, :m].T
+        FT = g(self.FT).reshape(6, c)[:, :m].T
+        lever = g(self.lever).reshape(6, c)[:, :m].T
+        n = self.n
+        return dict(pi=g(self.pair_i)[:m], pj=g(self.pair_j)[:m], n=nrm, h=g(self.gap)[:m],
+                    status=g(self.status)[:m], iters=g(self.iters)[:m], FT=FT, lever=lever,
+                    force=g(self.force)[:3 * n].reshape(3, n).T, torque=g(self.torque)[:3 * n].reshape(3, n).T)

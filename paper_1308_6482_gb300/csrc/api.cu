@@ -1,0 +1,253 @@
+// C ABI of liblub: argument checks, context and scratch management, dispatch
+// to the kernel launchers.  See include/lub.h for the contract of each call.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lub_internal.cuh"
+
+int lub_set_error(lub_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int lub_check_cuda(lub_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return LUB_OK;
+    return lub_set_error(ctx, LUB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int lub_ensure_scratch(lub_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->scratch_bytes) return LUB_OK;
+    size_t want = bytes + bytes / 4 + 4096;
+    if (ctx->scratch) {
+        cudaError_t e = cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        if (e != cudaSuccess) return lub_check_cuda(ctx, e, "cudaFree scratch");
+    }
+    cudaError_t e = cudaMalloc(&ctx->scratch, want);
+    if (e != cudaSuccess) {
+        ctx->scratch = nullptr;
+        (void)cudaGetLastError();
+        return lub_set_error(ctx, LUB_ERR_NOMEM, "cudaMalloc of %zu bytes of scratch failed: %s", want,
+                             cudaGetErrorString(e));
+    }
+    ctx->scratch_bytes = want;
+    return LUB_OK;
+}
+
+namespace {
+
+int check_particles(lub_ctx *ctx, const lub_particles *p, bool need_vel)
+{
+    if (!p) return lub_set_error(ctx, LUB_ERR_ARG, "particles is NULL");
+    if (p->n < 0) return lub_set_error(ctx, LUB_ERR_ARG, "particles.n = %d < 0", p->n);
+    if (p->n == 0) return LUB_OK;
+    if (!p->x || !p->y || !p->z || !p->qw || !p->qx || !p->qy || !p->qz || !p->r_par || !p->r_perp)
+        return lub_set_error(ctx, LUB_ERR_ARG, "a particle pose or shape array is NULL");
+    if (need_vel && (!p->vx || !p->vy || !p->vz || !p->wx || !p->wy || !p->wz))
+        return lub_set_error(ctx, LUB_ERR_ARG, "a particle velocity array is NULL");
+    return LUB_OK;
+}
+
+int check_domain(lub_ctx *ctx, const lub_domain *d)
+{
+    if (!d) return lub_set_error(ctx, LUB_ERR_ARG, "domain is NULL");
+    if (d->n_walls < 0 || d->n_walls > 2) return lub_set_error(ctx, LUB_ERR_ARG, "n_walls must be 0, 1 or 2");
+    for (int a = 0; a < 3; ++a)
+        if (!(d->L[a] > 0.0) || !isfinite(d->L[a])) return lub_set_error(ctx, LUB_ERR_ARG, "L[%d] must be > 0", a);
+    for (int w = 0; w < d->n_walls; ++w) {
+        if (d->wall_dir[w] != 1 && d->wall_dir[w] != -1)
+            return lub_set_error(ctx, LUB_ERR_ARG, "wall_dir[%d] must be +1 or -1", w);
+        if (!isfinite(d->wall_z[w])) return lub_set_error(ctx, LUB_ERR_ARG, "wall_z[%d] is not finite", w);
+    }
+    if (d->n_walls > 0 && d->periodic[2])
+        return lub_set_error(ctx, LUB_ERR_ARG, "walls are normal to z: z cannot be periodic");
+    return LUB_OK;
+}
+
+int check_params(lub_ctx *ctx, const lub_params *p)
+{
+    if (!p) return lub_set_error(ctx, LUB_ERR_ARG, "params is NULL");
+    if (p->precision != LUB_FP64 && p->precision != LUB_MIXED)
+        return lub_set_error(ctx, LUB_ERR_ARG, "precision must be LUB_FP64 or LUB_MIXED");
+    if (!(p->mu >= 0.0) || !(p->delta_n > 0.0) || !(p->delta_t > 0.0) || !(p->delta_r > 0.0))
+        return lub_set_error(ctx, LUB_ERR_ARG, "mu must be >= 0 and the cut-offs > 0");
+    if (!(p->h_c >= 0.0) || !(p->eps_c >= 0.0)) return lub_set_error(ctx, LUB_ERR_ARG, "h_c, eps_c must be >= 0");
+    if (!(p->list_cutoff >= 0.0) || !isfinite(p->list_cutoff))
+        return lub_set_error(ctx, LUB_ERR_ARG, "list_cutoff must be finite and >= 0");
+    if (p->max_newton < 1 || p->max_newton > 64) return lub_set_error(ctx, LUB_ERR_ARG, "max_newton must be 1..64");
+    if (!(p->newton_tol > 0.0)) return lub_set_error(ctx, LUB_ERR_ARG, "newton_tol must be > 0");
+    if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS)
+        return lub_set_error(ctx, LUB_ERR_ARG, "warm_start must be LUB_WARM_NONE or LUB_WARM_PREVIOUS");
+    return LUB_OK;
+}
+
+int check_pairs(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap)
+{
+    if (cap < 0) return lub_set_error(ctx, LUB_ERR_ARG, "capacity < 0");
+    if (cap > 0 && (!pi || !pj || !d_count)) return lub_set_error(ctx, LUB_ERR_ARG, "pair arrays or d_count NULL");
+    return LUB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lub_default_params(lub_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->mu = 1.0 / 6.0;
+    p->delta_n = 2.0 / 3.0;
+    p->delta_t = 0.5;
+    p->delta_r = 0.25;
+    p->h_c = 0.0;
+    p->eps_c = 0.0;
+    p->list_cutoff = 1.0;
+    p->precision = LUB_MIXED;
+    p->fp64_switch = 1e-3;
+    p->max_newton = 32;
+    p->newton_tol = 2e-5;
+    p->warm_start = LUB_WARM_NONE;
+}
+
+int lub_ctx_create(lub_ctx **out)
+{
+    if (!out) return LUB_ERR_ARG;
+    *out = nullptr;
+    lub_ctx *ctx = new (std::nothrow) lub_ctx();
+    if (!ctx) return LUB_ERR_NOMEM;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flags, 256);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return LUB_ERR_CUDA;
+    }
+    *out = ctx;
+    return LUB_OK;
+}
+
+int lub_ctx_destroy(lub_ctx *ctx)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    cudaDeviceSynchronize();
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    delete ctx;
+    return LUB_OK;
+}
+
+const char *lub_last_error(const lub_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                    int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count, int32_t *h_count_or_null,
+                    void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)))
+        return rc;
+    if (!d_count) return lub_set_error(ctx, LUB_ERR_ARG, "d_count is NULL");
+    if (capacity < 0 || (capacity > 0 && (!pair_i || !pair_j)))
+        return lub_set_error(ctx, LUB_ERR_ARG, "bad pair arrays or capacity");
+    cudaStream_t st = (cudaStream_t)stream;
+    PView P = make_pview(p);
+    DView D = make_dview(dom);
+    float rmax = p->max_semi_axis;
+    if (!(rmax > 0.0f)) {
+        if ((rc = launch_max_semi_axis(ctx, P, &rmax, st))) return rc;
+        if (!(rmax > 0.0f) && p->n > 0)
+            return lub_set_error(ctx, LUB_ERR_ARG, "semi-axes must be positive and finite");
+        if (!(rmax > 0.0f)) rmax = 1.0f;
+    }
+    const double range = 2.0 * rmax + prm->list_cutoff;
+    for (int a = 0; a < 3; ++a)
+        if (D.periodic[a] && !(D.L[a] > 2.0 * range * (1.0 + 1e-6) + 1e-3))
+            return lub_set_error(ctx, LUB_ERR_ARG,
+                                 "periodic L[%d] = %g must exceed 2 (2 Rmax + Delta_L) = %g", a, D.L[a], 2 * range);
+    if ((rc = launch_pairs_build(ctx, P, D, *prm, rmax, pair_i, pair_j, capacity, d_count, st))) return rc;
+    if (h_count_or_null) {
+        int32_t flags = 0;
+        rc = lub_check_cuda(ctx, cudaMemcpyAsync(h_count_or_null, d_count, 4, cudaMemcpyDeviceToHost, st), "copy count");
+        if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(&flags, ctx->d_flags, 4, cudaMemcpyDeviceToHost, st), "copy flags");
+        if (!rc) rc = lub_check_cuda(ctx, cudaStreamSynchronize(st), "sync");
+        if (rc) return rc;
+        if (flags & 1)
+            return lub_set_error(ctx, LUB_ERR_ARG, "a semi-axis exceeds max_semi_axis = %g (or is not finite)", rmax);
+        if (*h_count_or_null > capacity)
+            return lub_set_error(ctx, LUB_ERR_CAPACITY, "%d candidate pairs exceed capacity %d", *h_count_or_null,
+                                 capacity);
+    }
+    return LUB_OK;
+}
+
+int lub_closest_points(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                       const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+                       double *n, double *gap, uint8_t *status, uint8_t *iters, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)) ||
+        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
+        return rc;
+    if (capacity > 0 && (!n || !gap || !status)) return lub_set_error(ctx, LUB_ERR_ARG, "n, gap or status is NULL");
+    return launch_closest(ctx, make_pview(p), make_dview(dom), *prm, pair_i, pair_j, d_count, capacity, n, gap,
+                          status, iters, (cudaStream_t)stream);
+}
+
+int lub_resistance(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                   const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+                   const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, true)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)) ||
+        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
+        return rc;
+    if (capacity > 0 && (!n || !gap || !status || !FT || !lever))
+        return lub_set_error(ctx, LUB_ERR_ARG, "n, gap, status, FT or lever is NULL");
+    return launch_resistance(ctx, make_pview(p), make_dview(dom), *prm, pair_i, pair_j, d_count, capacity, n, gap,
+                             status, FT, lever, (cudaStream_t)stream);
+}
+
+int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+              const void *FT, const void *lever, int32_t n, void *force, void *torque, int32_t precision,
+              int32_t accumulate, int32_t deterministic, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity))) return rc;
+    if (precision != LUB_FP64 && precision != LUB_MIXED)
+        return lub_set_error(ctx, LUB_ERR_ARG, "precision must be LUB_FP64 or LUB_MIXED");
+    if (n < 0) return lub_set_error(ctx, LUB_ERR_ARG, "n < 0");
+    if (n > 0 && (!force || !torque)) return lub_set_error(ctx, LUB_ERR_ARG, "force or torque is NULL");
+    if (capacity > 0 && (!FT || !lever)) return lub_set_error(ctx, LUB_ERR_ARG, "FT or lever is NULL");
+    return launch_apply(ctx, pair_i, pair_j, d_count, capacity, FT, lever, n, force, torque, precision, accumulate,
+                        deterministic, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// Internal declarations of liblub: context, device helpers and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lub.h"
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct lub_ctx {
+    std::string err;
+    int device = -1;
+    int num_sms = 0;
+    // growable device scratch
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t *d_flags = nullptr;  // [0]: overflow / error flags of the last call
+};
+
+int lub_set_error(lub_ctx *ctx, int code, const char *fmt, ...);
+int lub_check_cuda(lub_ctx *ctx, cudaError_t e, const char *what);
+int lub_ensure_scratch(lub_ctx *ctx, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// plain-old-data views passed to kernels by value
+// ---------------------------------------------------------------------------
+struct PView {
+    const double *x, *y, *z;
+    const float *qw, *qx, *qy, *qz;
+    const float *rpar, *rperp;
+    const float *vx, *vy, *vz, *wx, *wy, *wz;
+    int32_t n;
+};
+
+struct DView {
+    double L[3];
+    int32_t periodic[3];
+    int32_t n_walls;
+    double wall_z[2];
+    int32_t wall_dir[2];
+};
+
+struct RParams {
+    double mu, delta_n, delta_t, delta_r, h_c, eps_c;
+};
+
+inline PView make_pview(const lub_particles *p)
+{
+    PView v;
+    v.x = p->x; v.y = p->y; v.z = p->z;
+    v.qw = p->qw; v.qx = p->qx; v.qy = p->qy; v.qz = p->qz;
+    v.rpar = p->r_par; v.rperp = p->r_perp;
+    v.vx = p->vx; v.vy = p->vy; v.vz = p->vz;
+    v.wx = p->wx; v.wy = p->wy; v.wz = p->wz;
+    v.n = p->n;
+    return v;
+}
+
+inline DView make_dview(const lub_domain *d)
+{
+    DView v;
+    for (int k = 0; k < 3; ++k) {
+        v.L[k] = d->L[k];
+        v.periodic[k] = d->periodic[k];
+    }
+    v.n_walls = d->n_walls;
+    for (int k = 0; k < 2; ++k) {
+        v.wall_z[k] = d->wall_z[k];
+        v.wall_dir[k] = d->wall_dir[k];
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// small vector type, templated on the working precision
+// ---------------------------------------------------------------------------
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+
+template <typename T>
+__device__ __forceinline__ V3<T> mk(T x, T y, T z)
+{
+    V3<T> r;
+    r.x = x; r.y = y; r.z = z;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ T dot(const V3<T> &a, const V3<T> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ V3<T> cross(const V3<T> &a, const V3<T> &b)
+{
+    return mk<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ V3<T> add(const V3<T> &a, const V3<T> &b) { return mk<T>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <typename T>
+__device__ __forceinline__ V3<T> sub(const V3<T> &a, const V3<T> &b) { return mk<T>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <typename T>
+__device__ __forceinline__ V3<T> scl(T s, const V3<T> &a) { return mk<T>(s * a.x, s * a.y, s * a.z); }
+template <typename T>
+__device__ __forceinline__ V3<T> axpy(T s, const V3<T> &a, const V3<T> &b)  // s a + b
+{
+    return mk<T>(s * a.x + b.x, s * a.y + b.y, s * a.z + b.z);
+}
+
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+__device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sqrt_t(double v) { return sqrt(v); }
+
+template <typename T>
+__device__ __forceinline__ V3<T> normalized(const V3<T> &a)
+{
+    T l2 = dot(a, a);
+    return scl(T(1) / sqrt_t(l2), a);
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ V3<T> cvt(const V3<S> &a)
+{
+    return mk<T>((T)a.x, (T)a.y, (T)a.z);
+}
+
+// ---------------------------------------------------------------------------
+// particle shape
+// ---------------------------------------------------------------------------
+// Axis of rotational symmetry (body z) in the lab frame: third column of the
+// rotation matrix of q/|q|, q scalar first.
+template <typename T>
+__device__ __forceinline__ V3<T> quat_axis(float qw, float qx, float qy, float qz)
+{
+    T w = qw, x = qx, y = qy, z = qz;
+    T s = T(2) / (w * w + x * x + y * y + z * z);
+    return mk<T>(s * (x * z + w * y), s * (y * z - w * x), T(1) - s * (x * x + y * y));
+}
+
+// The shape of a spheroid in the form M = a2 I + e o o^T with a2 = r_perp^2,
+// e = r_par^2 - r_perp^2, o the symmetry axis.  Then for unit n
+// sigma(n)^2 = n^T M n = a2 + e (o.n)^2 and M n = a2 n + e (o.n) o.
+template <typename T>
+struct Shape {
+    V3<T> o;
+    T a2, e;
+    T rpar, rperp;
+};
+
+template <typename T>
+__device__ __forceinline__ Shape<T> load_shape(const PView &P, int k)
+{
+    Shape<T> s;
+    s.o = quat_axis<T>(__ldg(P.qw + k), __ldg(P.qx + k), __ldg(P.qy + k), __ldg(P.qz + k));
+    s.rpar = (T)__ldg(P.rpar + k);
+    s.rperp = (T)__ldg(P.rperp + k);
+    s.a2 = s.rperp * s.rperp;
+    s.e = s.rpar * s.rpar - s.a2;
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T support(const Shape<T> &s, const V3<T> &n)
+{
+    T c = dot(s.o, n);
+    return sqrt_t(s.a2 * dot(n, n) + s.e * c * c);
+}
+
+// M n / sigma(n): offset from the centre of the surface point whose outward
+// normal is n.
+template <typename T>
+__device__ __forceinline__ V3<T> support_offset(const Shape<T> &s, const V3<T> &n)
+{
+    T c = dot(s.o, n);
+    T sg = sqrt_t(s.a2 * dot(n, n) + s.e * c * c);
+    T inv = T(1) / sg;
+    return axpy(s.e * c * inv, s.o, scl(s.a2 * inv, n));
+}
+
+__device__ __forceinline__ V3<double> load_pos(const PView &P, int k)
+{
+    return mk<double>(__ldg(P.x + k), __ldg(P.y + k), __ldg(P.z + k));
+}
+
+// minimum image of r_j - r_i (same convention as the definition: subtract
+// L * floor(d / L + 1/2) along periodic axes)
+__device__ __forceinline__ V3<double> min_image(const DView &D, V3<double> d)
+{
+    if (D.periodic[0]) d.x -= D.L[0] * floor(d.x / D.L[0] + 0.5);
+    if (D.periodic[1]) d.y -= D.L[1] * floor(d.y / D.L[1] + 0.5);
+    if (D.periodic[2]) d.z -= D.L[2] * floor(d.z / D.L[2] + 0.5);
+    return d;
+}
+
+__device__ __forceinline__ bool shape_ok(float rpar, float rperp)
+{
+    return rpar > 0.f && rperp > 0.f && isfinite(rpar) && isfinite(rperp);
+}
+
+__device__ __forceinline__ int pair_count(const int32_t *d_count, int32_t capacity)
+{
+    int c = *d_count;
+    if (c > capacity) c = capacity;
+    if (c < 0) c = 0;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm,
+                   const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n,
+                   double *gap, uint8_t *status, uint8_t *iters, cudaStream_t st);
+int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm,
+                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
+                      const double *n, const double *gap, uint8_t *status, void *FT, void *lever,
+                      cudaStream_t st);
+int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
+                 const void *FT, const void *lever, int32_t n, void *force, void *torque, int precision,
+                 int accumulate, int deterministic, cudaStream_t st);
+int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, float rmax,
+                       int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count, cudaStream_t st);
+int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_t st);
+
+// device-wide exclusive scan of n int32 values (in place), total -> *d_total
+int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, void *tmp, size_t tmp_bytes,
+                   cudaStream_t st);
+size_t scan_tmp_bytes(int64_t n);
+
+inline int grid_for(int64_t work, int block, int num_sms, int per_sm = 16)
+{
+    int64_t g = (work + block - 1) / block;
+    int64_t cap = (int64_t)num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}

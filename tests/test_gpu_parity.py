@@ -1,0 +1,191 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are seeded synthetic pairs and suspensions from ``gen``; expected
+values always come from ``oracle``.  Tolerances are documented in
+``tests/parity.py``.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from parity import compare, oracle_ref, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_1308_6482_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind", ["aspect", "mixed", "spheres"])
+def test_pair_stream_parity(prec, kind):
+    # 2,500 pairs: many tiles of 128 threads plus a ragged tail
+    parts, dom, pi, pj = gen.pair_stream(2500, seed=41, kind=kind, gap_range=(1e-4, 1.0))
+    g = run_gpu(parts, dom, prec, pi, pj)
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, g, ref, prec, pi, pj)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_min_axis_scaled_gaps(prec):
+    # gaps log-uniform in [1e-4, 1] times the smaller semi-axis (h/a spans the FP64 switch)
+    parts, dom, pi, pj = gen.pair_stream(3000, seed=43, kind="aspect", gap_range=(1e-4, 1.0), gap_scale="min_axis")
+    g = run_gpu(parts, dom, prec, pi, pj)
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, g, ref, prec, pi, pj)
+    if prec == "mixed":
+        a = np.minimum(np.minimum(parts["r_par"][pi], parts["r_perp"][pi]),
+                       np.minimum(parts["r_par"][pj], parts["r_perp"][pj]))
+        near = ref["cp"]["h"] < 1e-3 * a
+        assert np.all(g["status"][near] & 8), "pairs below the switch are refined in FP64"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_suspension_with_wall_full_step(prec):
+    parts, dom = gen.config_prolate_wall(seed=1)
+    g = run_gpu(parts, dom, prec)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    assert np.any(pj < 0)
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, g, ref, prec, pi, pj)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mixed_suspension_full_step(prec):
+    parts, dom = gen.config_mixed_suspension(N=3000, phi=0.3, seed=7)
+    g = run_gpu(parts, dom, prec)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, g, ref, prec, pi, pj)
+
+
+def test_full_size_suspension_parity():
+    """The 32,768-particle, Phi = 0.3 mixed suspension the benchmark times, in
+    the benchmark's launch configuration: the whole pair list and every pair
+    and particle result against the oracle."""
+    parts, dom = gen.config_mixed_suspension()
+    g = run_gpu(parts, dom, "mixed")
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, g, ref, "mixed", pi, pj)
+
+
+def test_contact_branch_parity():
+    # h_c = 0.01, eps_c = 100 (Sec. IV C): gaps on both sides of h_c and small overlaps
+    parts, dom, pi, pj = gen.pair_stream(1500, seed=45, kind="aspect", gap_range=(1e-4, 0.05))
+    rng = np.random.default_rng(3)
+    cp0 = oracle.closest(parts, dom, pi, pj)
+    push = rng.uniform(0, 0.03, len(pi))  # some become overlapping
+    for kk, ax in zip(("x", "y", "z"), range(3)):
+        parts[kk] = parts[kk].copy()
+        parts[kk][pj] -= push * cp0["n"][:, ax]
+    for prec in ("fp64", "mixed"):
+        g = run_gpu(parts, dom, prec, pi, pj, h_c=0.01, eps_c=100.0)
+        ref = oracle_ref(parts, dom, pi, pj, h_c=0.01, eps_c=100.0)
+        assert np.any(ref["cp"]["h"] < 0)
+        compare(parts, dom, g, ref, prec, pi, pj)
+
+
+def test_overlap_without_contact_model():
+    parts, dom, pi, pj = gen.pair_stream(500, seed=46, kind="mixed", gap_range=(1e-3, 0.05))
+    cp0 = oracle.closest(parts, dom, pi, pj)
+    for kk, ax in zip(("x", "y", "z"), range(3)):
+        parts[kk] = parts[kk].copy()
+        parts[kk][pj] -= 2 * cp0["h"] * cp0["n"][:, ax]
+    g = run_gpu(parts, dom, "mixed", pi, pj)
+    ref = oracle_ref(parts, dom, pi, pj)
+    assert np.all(g["status"] & 1)
+    assert np.all(g["FT"] == 0)
+    compare(parts, dom, g, ref, "mixed", pi, pj)
+
+
+def test_deterministic_apply_is_reproducible():
+    parts, dom = gen.config_mixed_suspension(N=3000, phi=0.3, seed=8)
+    a = run_gpu(parts, dom, "mixed", deterministic=1)
+    b = run_gpu(parts, dom, "mixed", deterministic=1)
+    c = run_gpu(parts, dom, "mixed", deterministic=0)
+    np.testing.assert_array_equal(a["force"], b["force"])
+    np.testing.assert_array_equal(a["torque"], b["torque"])
+    np.testing.assert_allclose(a["force"], c["force"], rtol=0, atol=1e-5 * np.abs(a["force"]).max())
+    pi, pj = a["pi"], a["pj"]
+    ref = oracle_ref(parts, dom, pi, pj)
+    compare(parts, dom, a, ref, "mixed", pi, pj)
+
+
+def test_empty_inputs():
+    import torch
+
+    import paper_1308_6482_gb300 as lub
+    parts, dom = gen.config_mixed_suspension(N=50, phi=0.01, seed=9)
+    pl = lub.Pipeline(parts, dom, lub.default_params(list_cutoff=0.0), capacity=64)
+    cnt = pl.build_pairs()
+    pl.closest()
+    pl.resistance()
+    pl.apply()
+    torch.cuda.synchronize()
+    r = pl.results()
+    assert cnt == len(r["pi"])
+    assert np.all(np.isfinite(r["force"]))
+    # zero pairs given explicitly
+    pl.set_pairs(np.zeros(0, np.int32), np.zeros(0, np.int32))
+    pl.closest()
+    pl.resistance()
+    pl.apply()
+    torch.cuda.synchronize()
+    assert np.all(pl.results()["force"] == 0)
+
+
+def test_capacity_overflow_reports_required_count():
+    import torch
+
+    import paper_1308_6482_gb300 as lub
+    parts, dom = gen.config_mixed_suspension(N=2000, phi=0.3, seed=10)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    pl = lub.Pipeline(parts, dom, lub.default_params(), capacity=16)
+    rc, cnt = lub.lub_pairs_build(pl.ctx.h, pl.P.c, pl.D, pl.prm, pl.pair_i, pl.pair_j, pl.cap, pl.d_count,
+                                  h_count=True)
+    assert rc == lub.LUB_ERR_CAPACITY and cnt == len(pi)
+    assert pl.count() == len(pi)
+    # the downstream calls clamp to capacity and stay in bounds
+    pl.closest()
+    pl.resistance()
+    pl.apply()
+    torch.cuda.synchronize()
+    # growing and rebuilding gives the full list
+    cnt2 = pl.build_pairs()
+    assert cnt2 == len(pi)
+    np.testing.assert_array_equal(pl.results()["pi"], pi)
+
+
+def test_degenerate_pairs_are_flagged_not_faulted():
+    import torch
+    parts, dom, pi, pj = gen.pair_stream(8, seed=47, kind="aspect", gap_range=(1e-3, 0.1))
+    n = len(parts["x"])
+    parts["r_perp"] = parts["r_perp"].copy()
+    parts["r_perp"][1] = 0.0                       # zero semi-axis
+    parts["x"] = parts["x"].copy()
+    parts["x"][5] = parts["x"][4]
+    parts["y"] = parts["y"].copy()
+    parts["y"][5] = parts["y"][4]
+    parts["z"] = parts["z"].copy()
+    parts["z"][5] = parts["z"][4]                  # coincident centres
+    bad_i = np.array([0, 4, n + 5, 2, -3, 6], np.int32)
+    bad_j = np.array([1, 5, 3, -7, 2, 6], np.int32)  # bad index, bad wall index, i == j
+    g = run_gpu(parts, dom, "mixed", bad_i, bad_j)
+    torch.cuda.synchronize()
+    assert np.all(g["status"] & 4)
+    assert np.all(g["FT"] == 0)
+    assert np.all(np.isfinite(g["force"]))
