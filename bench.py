@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the lubrication correction (pairs per second).
+
+One step = one pass of the whole path over one suspension: lub_pairs_build
+(cell list + Sec. III A pre-filters), lub_closest_points, lub_resistance and
+lub_apply, enqueued on one stream.  The step is captured once into a CUDA
+graph (built from the same C-ABI calls) and replayed; the L2 cache is flushed
+between timed steps by writing a 256 MB buffer outside the step's events.
+
+Workload (N=1): the 32,768-particle mixed suspension (half spheres r = 4.5,
+half oblates with semi-axes 6, 6, 3) at volume fraction 0.3 in a periodic
+cube, list cut-off 1, mixed precision.  Under torchrun each rank runs its own
+independent suspension (different seed): weak scaling with no collective in
+the data path.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (the reference arm).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "lubrication pair-corrections/s at 1e-5 rel. err; learned vs plain GPU form"
+WORKLOAD = ("mixed suspension: N=32768 (50% spheres r=4.5, 50% oblates 6,6,3), phi=0.3, periodic cube "
+            "L=357.7, 90% of particles attached to an earlier one at a gap log-uniform in [1e-4,1], "
+            "pairs with possible gap < 1 (Delta_L=1)")
+
+# algorithmic work per unit ("Roofline"), used for the dominant call
+FP32_NEWTON_FLOP = 170.0      # one FP32 Newton iteration on the sphere
+FP64_GAP_FLOP = 70.0          # FP64 gap: 2 axes from quaternions, 2 support functions, n.d
+FP64_NEWTON_FLOP = 170.0      # one FP64 Newton iteration (refinement below the switch)
+RES_FP32_FLOP = 900.0         # K2 per pair: 2 surface frames, eigenproblem, cubic rotation, K~, u, forces
+PAIRS_BYTES_PER_PARTICLE = 48.0   # pose + shape read once
+PAIRS_BYTES_PER_PAIR = 8.0        # (i, j) written
+APPLY_BYTES_PER_PAIR = 56.0       # F, T, levers (float) + indices
+APPLY_BYTES_PER_PARTICLE = 24.0   # force + torque written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=32768)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        out.update(d)
+        out["src"] = "measured"
+    # non-tensor pipes, measured on this machine's GB300 with an FMA-chain probe
+    out.setdefault("fp32_tflops", 74.6)
+    out.setdefault("fp64_tflops", 1.20)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n, seed):
+    import gen
+    return gen.config_mixed_suspension(N=n, phi=0.3, seed=seed)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1308_6482_gb300 as lub
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    parts, dom = make_workload(args.n, 2 + 1000 * rank)
+    prm = lub.default_params(precision=args.precision)
+    pl = lub.Pipeline(parts, dom, prm, device=dev)
+    npairs = pl.build_pairs()              # sizes capacity and the context scratch
+    pl._alloc(int(npairs * 1.1) + 1024, dev)
+    npairs = pl.build_pairs()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # eager step once: per-call launch accounting and results for the work counts
+    with torch.cuda.stream(stream):
+        pl.step(stream=stream)
+    stream.synchronize()
+    res = pl.results()
+    mean_it = float(np.mean(res["iters"]))
+    fp64_frac = float(np.mean((res["status"] & lub.LUB_ST_FP64) != 0))
+
+    # capture the step into a CUDA graph
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            pl.step(stream=stream)
+        stream.synchronize()
+
+    calls = ("pairs_build", "closest", "resistance", "apply")
+
+    def step_timed(evs):
+        # per-call events (used for the roofline) around the four calls
+        evs[0].record(stream)
+        pl.build_pairs(sync_count=False, grow=False, stream=stream)
+        evs[1].record(stream)
+        pl.closest(stream=stream)
+        evs[2].record(stream)
+        pl.resistance(stream=stream)
+        evs[3].record(stream)
+        pl.apply(stream=stream)
+        evs[4].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            if graph is not None:
+                graph.replay()
+            else:
+                pl.step(stream=stream)
+    stream.synchronize()
+
+    # timed region: K steps of the graph, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                pl.step(stream=stream)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+
+    # per-call device times (eager calls, same stream, L2 flushed), for the roofline
+    K2 = min(args.steps, 100)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K2)]
+    with torch.cuda.stream(stream):
+        for k in range(K2):
+            flush.zero_()
+            step_timed(evs[k])
+    stream.synchronize()
+    call_ms = {c: float(np.mean([evs[k][q].elapsed_time(evs[k][q + 1]) for k in range(K2)]))
+               for q, c in enumerate(calls)}
+
+    # e2e through the public API: host inputs (pinned) -> device, step, force/torque -> host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in parts.items()}
+        hforce = torch.empty(pl.force.numel(), dtype=pl.force.dtype).pin_memory()
+        htorque = torch.empty(pl.torque.numel(), dtype=pl.torque.dtype).pin_memory()
+        bi = sum(t.numel() * t.element_size() for t in host.values())
+        bo = hforce.numel() * hforce.element_size() * 2
+        Ke = min(args.steps, 100)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                for k, t in host.items():
+                    pl.P.t[k].copy_(t, non_blocking=True)
+                pl.step(stream=stream)
+                hforce.copy_(pl.force, non_blocking=True)
+                htorque.copy_(pl.torque, non_blocking=True)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(Ke):
+                for k, t in host.items():
+                    pl.P.t[k].copy_(t, non_blocking=True)
+                pl.step(stream=stream)
+                hforce.copy_(pl.force, non_blocking=True)
+                htorque.copy_(pl.torque, non_blocking=True)
+            e1.record(stream)
+        stream.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / Ke
+        e2e = {"value": npairs / (e2e_ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms}
+
+    # max over ranks
+    ms_per_step = total_ms / args.steps
+    pairs_all = npairs
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_per_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+        c = torch.tensor([float(npairs)], device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        pairs_all = float(c.item())
+    value = pairs_all / (ms_per_step * 1e-3)
+
+    pk = peaks()
+    dom_call = max(call_ms, key=call_ms.get)
+    roof = roofline(dom_call, call_ms[dom_call], npairs, args.n, mean_it, fp64_frac, args.precision, pk)
+    kernels_per_step = kernels_in_step(args.precision)
+    out = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "pairs_per_step": int(npairs),
+                   "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
+                   "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",
+                   "newton_iters_mean": mean_it, "fp64_refined_fraction": fp64_frac,
+                   "call_ms": call_ms, "wall_s_timed": wall},
+        "roofline": roof, "clocks": clocks, "gpu_launches": kernels_per_step * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(parts, dom)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def kernels_in_step(precision):
+    # lub_pairs_build: cells count, 3 scan, cells fill, count sweep, 2 x 3 scan, write sweep, total = 14
+    # lub_closest_points 1, lub_resistance 1, lub_apply (atomic) 1
+    return 17
+
+
+def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
+    t = ms * 1e-3
+    if call == "closest":
+        if precision == "mixed":
+            f32 = npairs * mean_it * FP32_NEWTON_FLOP
+            f64 = npairs * FP64_GAP_FLOP + npairs * fp64_frac * 2 * FP64_NEWTON_FLOP
+        else:
+            f32 = 0.0
+            f64 = npairs * (mean_it * FP64_NEWTON_FLOP + FP64_GAP_FLOP)
+        # FP64-equivalent work: the time the two pipes need at peak, in FP64 units
+        eq = f64 + f32 * pk["fp64_tflops"] / pk["fp32_tflops"]
+        ach = eq / t / 1e12
+        peak = pk["fp64_tflops"]
+        return {"kernel": "k_closest", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
+                "peak_src": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+    if call == "resistance":
+        ach = npairs * RES_FP32_FLOP / t / 1e12
+        peak = pk["fp32_tflops"]
+        return {"kernel": "k_resistance", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_src": "FP32 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+    if call == "pairs_build":
+        b = n * PAIRS_BYTES_PER_PARTICLE + npairs * PAIRS_BYTES_PER_PAIR
+    else:
+        b = npairs * APPLY_BYTES_PER_PAIR + n * APPLY_BYTES_PER_PARTICLE
+    ach = b / t / 1e9
+    return {"kernel": call, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+
+
+def cpu_baseline(parts, dom, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: one full step of the
+    same workload (pre-filter over all pairs, closest points, forces, sums)."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count()
+    t0 = time.perf_counter()
+    P = oracle.Particles(parts)
+    pi, pj = oracle.candidates(P, dom, 1.0)
+    t1 = time.perf_counter()
+    cp = oracle.closest(P, dom, pi, pj)
+    pf = oracle.pair_force(P, dom, None, pi, pj, cp)
+    f, t = oracle.apply(P.n, pi, pj, pf["FT"], pf["lever"])
+    t2 = time.perf_counter()
+    return {"value": len(pi) / (t2 - t0), "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": "one full step of the same %d-particle suspension (%d pairs): O(N^2) pre-filter %.2f s "
+                      "(1 thread), closest points + forces + sums %.2f s (%d OpenMP threads)"
+                      % (P.n, len(pi), t1 - t0, t2 - t1, cores)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, same workload and metric."""
+    import numpy as np
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    parts, dom = make_workload(args.n, 2)
+    P = oracle.Particles(parts)
+    pi, pj = oracle.candidates(P, dom, 1.0)
+    # each step: closest points + forces + sums on a contiguous sample of the pair list,
+    # sized so the whole run stays within about a minute
+    t0 = time.perf_counter()
+    m0 = min(len(pi), 4096)
+    cp = oracle.closest(P, dom, pi[:m0], pj[:m0])
+    pf = oracle.pair_force(P, dom, None, pi[:m0], pj[:m0], cp)
+    per_pair = (time.perf_counter() - t0) / m0
+    m = int(max(256, min(len(pi), 60.0 / max(1, args.steps + args.warmup) / per_pair)))
+    for _ in range(args.warmup):
+        cp = oracle.closest(P, dom, pi[:m], pj[:m])
+        pf = oracle.pair_force(P, dom, None, pi[:m], pj[:m], cp)
+        oracle.apply(P.n, pi[:m], pj[:m], pf["FT"], pf["lever"])
+    ts = time.perf_counter()
+    for _ in range(args.steps):
+        cp = oracle.closest(P, dom, pi[:m], pj[:m])
+        pf = oracle.pair_force(P, dom, None, pi[:m], pj[:m], cp)
+        oracle.apply(P.n, pi[:m], pj[:m], pf["FT"], pf["lever"])
+    el = time.perf_counter() - ts
+    value = m * args.steps / el
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)", "pairs_per_step": m},
+           "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d of the %d pairs per step (closest points, forces, sums)" % (m, len(pi))},
+           "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
