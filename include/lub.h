@@ -53,6 +53,7 @@ extern "C" {
 #define LUB_ERR_CUDA     (-3) /* a CUDA runtime call failed */
 #define LUB_ERR_TIMEOUT  (-4) /* a bounded device wait ran out */
 #define LUB_ERR_NOMEM    (-5) /* the context could not allocate its scratch */
+#define LUB_ERR_LIMIT    (-6) /* input larger than a fixed limit of lub_pairs_build_static */
 
 /* lub_params.precision */
 #define LUB_FP64  0 /* every step in double precision */
@@ -206,6 +207,39 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
               int32_t capacity, const void *FT, const void *lever, int32_t n, void *force,
               void *torque, int32_t precision, int32_t accumulate, int32_t deterministic,
               void *stream);
+
+/*
+ * The pair build of lub_pairs_build, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is an interface for host codes
+ * that capture their whole time step into a CUDA graph (cudaMalloc cannot be
+ * captured) or that own a fixed device-memory budget and forbid allocation
+ * after start-up (cudaMalloc synchronises the device and can fail mid-run).
+ * Such callers cannot create a lub_ctx, so this call takes none.
+ *
+ * It computes exactly what lub_pairs_build computes (same arguments, same
+ * output order and *d_count), on a scratch array of LUB_STATIC_SCRATCH_BYTES
+ * bytes that is a static device array of the library: every GPU that loads
+ * the library holds it until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The caller still provides pair_i,
+ * pair_j and d_count.
+ *   - Limits: p->n <= LUB_STATIC_MAX_PARTICLES (else LUB_ERR_LIMIT, nothing
+ *     enqueued); the cell grid is coarsened to at most LUB_STATIC_MAX_CELLS
+ *     cells; p->max_semi_axis must be given (> 0, else LUB_ERR_ARG).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents (the
+ *     call clears what must start at zero).  Calls whose work overlaps on the
+ *     GPU, e.g. on two streams at once, race on it: serialise them.
+ *   - Errors are return codes only (no context, no message).  Overflow of
+ *     capacity is visible through *d_count only.
+ */
+#define LUB_STATIC_MAX_PARTICLES 65536
+#define LUB_STATIC_MAX_CELLS     262144
+#define LUB_STATIC_SCRATCH_BYTES 4718592
+int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                           int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count,
+                           void *stream);
 
 #ifdef __cplusplus
 }

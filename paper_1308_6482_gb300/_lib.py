@@ -13,6 +13,8 @@ LUB_ERR_CAPACITY = -2
 LUB_ERR_CUDA = -3
 LUB_ERR_TIMEOUT = -4
 LUB_ERR_NOMEM = -5
+LUB_ERR_LIMIT = -6
+LUB_STATIC_MAX_PARTICLES = 65536
 LUB_FP64 = 0
 LUB_MIXED = 1
 LUB_WARM_NONE = 0
@@ -50,7 +52,7 @@ class lub_params(ctypes.Structure):
 
 # every exported symbol of include/lub.h
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
-           "lub_closest_points", "lub_resistance", "lub_apply")
+           "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static")
 
 _lib = None
 
@@ -89,6 +91,8 @@ def load_library():
                                    vp, vp, vp, vp]
     lib.lub_apply.restype = ctypes.c_int
     lib.lub_apply.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, i32, i32, i32, vp]
+    lib.lub_pairs_build_static.restype = ctypes.c_int
+    lib.lub_pairs_build_static.argtypes = [P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp]
     _lib = lib
     return lib
 
@@ -156,6 +160,13 @@ def lub_pairs_build(ctx, particles, domain, params, pair_i, pair_j, capacity, d_
     if check and rc not in (LUB_OK, LUB_ERR_CAPACITY):
         _check(ctx, rc)
     return rc, (hc.value if h_count else None)
+
+
+def lub_pairs_build_static(particles, domain, params, pair_i, pair_j, capacity, d_count, stream=None):
+    """Pair build on the library's static scratch (no allocation); returns the code."""
+    return load_library().lub_pairs_build_static(ctypes.byref(particles), ctypes.byref(domain),
+                                                 ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
+                                                 _ptr(d_count), _stream(stream))
 
 
 def lub_closest_points(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status,

@@ -238,3 +238,9 @@ inline int grid_for(int64_t work, int block, int num_sms, int per_sm = 16)
     if (g < 1) g = 1;
     return (int)g;
 }
+
+// pair build on caller-provided scratch (no allocation)
+size_t pairs_scratch_bytes(int64_t n, int64_t max_cells);
+int pairs_build_on_scratch(int num_sms, void *scratch, size_t scratch_bytes, int64_t max_cells, const PView &P,
+                           const DView &D, const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap,
+                           int32_t *d_count, cudaStream_t st);

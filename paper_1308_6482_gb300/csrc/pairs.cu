@@ -346,3 +346,97 @@ int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_p
     k_total<<<1, 1, 0, st>>>(totals, d_count);
     return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
 }
+
+// ---------------------------------------------------------------------------
+// The same build on scratch the caller provides (used by the entry point that
+// allocates nothing); max_cells bounds the cell grid to fit that scratch.
+// ---------------------------------------------------------------------------
+size_t pairs_scratch_bytes(int64_t n, int64_t max_cells)
+{
+    const size_t b_cell = align256((max_cells + 1) * 4), b_n = align256((n + 1) * 4), b_rec = align256(n * 16);
+    const size_t b_tot = 256, b_tmp = align256(scan_tmp_bytes(max_cells + 1 > n + 1 ? max_cells + 1 : n + 1));
+    return b_cell + 5 * b_n + 2 * b_rec + b_tot + b_tmp + 256;  // + 256: flags
+}
+
+int pairs_build_on_scratch(int num_sms, void *scratch, size_t scratch_bytes, int64_t max_cells, const PView &P,
+                           const DView &D, const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap,
+                           int32_t *d_count, cudaStream_t st)
+{
+    const double range = 2.0 * (double)rmax + prm.list_cutoff;
+    Grid G;
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)floor(D.L[a] / range);
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        G.nc[a] = nc;
+        G.csd[a] = D.L[a] / nc;
+        G.cs[a] = (float)G.csd[a];
+    }
+    int64_t cell_limit = 8 * (int64_t)P.n + 4096;
+    if (cell_limit > max_cells) cell_limit = max_cells;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int64_t ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+        if (ncell <= cell_limit) break;
+        const double f = cbrt((double)ncell / (double)cell_limit) * (1.0 + 1e-9) + (pass ? 0.01 * pass : 0.0);
+        for (int a = 0; a < 3; ++a) {
+            int nc = (int)floor(G.nc[a] / f);
+            G.nc[a] = nc < 1 ? 1 : nc;
+            G.csd[a] = D.L[a] / G.nc[a];
+            G.cs[a] = (float)G.csd[a];
+        }
+    }
+    G.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+    if (G.ncell > max_cells) return LUB_ERR_ARG;
+    G.cutoff = (float)prm.list_cutoff;
+    G.margin = (float)(1e-5 * (range + 1.0));
+    const int64_t N = P.n;
+    const size_t b_cell = align256((G.ncell + 1) * 4), b_n = align256((N + 1) * 4), b_rec = align256(N * 16);
+    const size_t b_tot = 256, b_tmp = align256(scan_tmp_bytes(G.ncell + 1 > N + 1 ? G.ncell + 1 : N + 1));
+    if (b_cell + 5 * b_n + 2 * b_rec + b_tot + b_tmp + 256 > scratch_bytes) return LUB_ERR_ARG;
+    char *s = (char *)scratch;
+    int32_t *flags = (int32_t *)s;
+    s += 256;
+    int32_t *cell_cnt = (int32_t *)s;
+    s += b_cell;
+    int32_t *cell_of = (int32_t *)s;
+    s += b_n;
+    int32_t *slot = (int32_t *)s;
+    s += b_n;
+    int32_t *sorted = (int32_t *)s;
+    s += b_n;
+    int32_t *cnt_pp = (int32_t *)s;
+    s += b_n;
+    int32_t *cnt_w = (int32_t *)s;
+    s += b_n;
+    float4 *rec0 = (float4 *)s;
+    s += b_rec;
+    float4 *rec1 = (float4 *)s;
+    s += b_rec;
+    int32_t *totals = (int32_t *)s;
+    s += b_tot;
+    void *tmp = s;
+    // the scratch keeps the previous call's contents: clear what must start at zero
+    if (cudaMemsetAsync(cell_cnt, 0, b_cell, st) != cudaSuccess) return LUB_ERR_CUDA;
+    if (cudaMemsetAsync(flags, 0, 256, st) != cudaSuccess) return LUB_ERR_CUDA;
+    const int block = 256;
+    const int gn = grid_for(N > 0 ? N : 1, block, num_sms, 8);
+    if (N > 0) k_cells_count<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, rmax, flags);
+    int rc = scan_exclusive(nullptr, cell_cnt, G.ncell + 1, totals + 2, tmp, b_tmp, st);
+    if (rc) return rc;
+    if (N > 0) {
+        k_cells_fill<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, sorted, rec0, rec1);
+        const int gs = grid_for(N, 128, num_sms, 16);
+        k_pairs_sweep<false><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
+                                                 totals, cap, pi, pj, prm.list_cutoff);
+        rc = scan_exclusive(nullptr, cnt_pp, N, totals + 0, tmp, b_tmp, st);
+        if (rc) return rc;
+        rc = scan_exclusive(nullptr, cnt_w, N, totals + 1, tmp, b_tmp, st);
+        if (rc) return rc;
+        k_pairs_sweep<true><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
+                                                totals, cap, pi, pj, prm.list_cutoff);
+    } else {
+        if (cudaMemsetAsync(totals, 0, 8, st) != cudaSuccess) return LUB_ERR_CUDA;
+    }
+    k_total<<<1, 1, 0, st>>>(totals, d_count);
+    return cudaGetLastError() == cudaSuccess ? LUB_OK : LUB_ERR_CUDA;
+}
