@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--fp64-switch", type=float, default=1e-3,
+                    help="h/a below which pairs get the FP64 Newton refinement (0: none)")
     return ap.parse_args()
 
 
@@ -150,7 +152,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     parts, dom = make_workload(args.n, 2 + 1000 * rank)
-    prm = lub.default_params(precision=args.precision)
+    prm = lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch)
     pl = lub.Pipeline(parts, dom, prm, device=dev)
     npairs = pl.build_pairs()              # sizes capacity and the context scratch
     pl._alloc(int(npairs * 1.1) + 1024, dev)
@@ -289,7 +291,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "pairs_per_step": int(npairs),
+        "config": {"workload": WORKLOAD, "precision": args.precision, "fp64_switch": args.fp64_switch,
+                   "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",
                    "newton_iters_mean": mean_it, "fp64_refined_fraction": fp64_frac,

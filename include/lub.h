@@ -236,7 +236,7 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
  */
 #define LUB_STATIC_MAX_PARTICLES 65536
 #define LUB_STATIC_MAX_CELLS     262144
-#define LUB_STATIC_SCRATCH_BYTES 4718592
+#define LUB_STATIC_SCRATCH_BYTES 5767168
 int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const lub_params *prm,
                            int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count,
                            void *stream);

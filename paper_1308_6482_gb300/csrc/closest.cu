@@ -12,9 +12,20 @@
 //   grad_t sigma = e c u / sigma,
 //   Hess_t sigma = (a2 / sigma) (I + (e / sigma^2) u u^T),
 // so that the chart Hessian of g is -(Hess_t sigma_i + Hess_t sigma_j) - g I.
-// One thread per pair.  In LUB_MIXED the iterations run in FP32, the gap is
-// always evaluated in FP64 (h is stationary in n, so the FP32 normal costs
-// only O(dn^2)), and pairs with h/a below fp64_switch get FP64 Newton steps.
+//
+// LUB_MIXED, one thread per pair:
+//   * Newton iterations in FP32 from the line of centres (or the normal
+//     passed in, for a warm start);
+//   * the gap of every pair in float-float arithmetic (about 48 bits, on the
+//     FP32 pipe): h is stationary in n, so the FP32 normal costs only
+//     O(dn^2), while the subtraction n.d - sigma_i - sigma_j cancels far
+//     beyond FP32 for small gaps;
+//   * pairs with h/a below fp64_switch (and pairs whose FP32 Newton did not
+//     converge) are appended to a compacted work list (one atomic per warp)
+//     and refined by FP64 Newton in a second kernel, so only full warps of
+//     such pairs use the slow FP64 pipe.
+// LUB_FP64: the whole solve and gap in double.
+#include "ff.cuh"
 #include "lub_internal.cuh"
 
 namespace {
@@ -36,9 +47,10 @@ __device__ __forceinline__ V3<T> perp_unit(const V3<T> &n)
 // applied.  Steps are clamped to 0.5 rad; a step that lowers g by more than
 // the rounding noise is halved (at most 12 times per solve).
 template <typename T>
-__device__ NewtonOut newton_sphere(const Shape<T> &si, const Shape<T> &sj, const V3<T> &d, V3<T> &n,
-                                   int maxit, T tol, T noise)
+__device__ NewtonOut newton_sphere(const Shape<T> &si, const Shape<T> &sj, const V3<T> &d, V3<T> &n, int maxit,
+                                   T tol, T noise)
 {
+    n = normalized(n);  // g below assumes |n| = 1: a start off by 1e-7 would corrupt the first g
     V3<T> t1 = perp_unit(n);
     V3<T> n_acc = n, t1_acc = t1, t2_acc = cross(n, t1);
     T g_acc = -T(1e30), s1_acc = 0, s2_acc = 0;
@@ -77,11 +89,11 @@ __device__ NewtonOut newton_sphere(const Shape<T> &si, const Shape<T> &sj, const
         T det = P11 * P22 - P12 * P12;
         T s1, s2;
         if (P11 > T(0) && det > T(0)) {
-            T idet = T(1) / det;
+            T idet = rcp_t(det);
             s1 = (P22 * g1 - P12 * g2) * idet;
             s2 = (P11 * g2 - P12 * g1) * idet;
         } else {
-            T sc = T(1) / (fabs(P11) + fabs(P22) + fabs(P12) + Ai + Aj);
+            T sc = rcp_t(fabs(P11) + fabs(P22) + fabs(P12) + Ai + Aj);
             s1 = g1 * sc;
             s2 = g2 * sc;
         }
@@ -103,94 +115,243 @@ __device__ NewtonOut newton_sphere(const Shape<T> &si, const Shape<T> &sj, const
     return out;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_closest(PView P, DView D, const int32_t *__restrict__ pi,
-                                                 const int32_t *__restrict__ pj,
-                                                 const int32_t *__restrict__ d_count, int32_t cap,
-                                                 double *__restrict__ nout, double *__restrict__ gap,
-                                                 uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
-                                                 int maxit, float tol32, float fp64_switch, int warm)
+// symmetry axis of q/|q| in float-float (quaternion components exact)
+__device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o[3])
+{
+    const ff q2 = ff_add(ff_add(two_prod(w, w), two_prod(x, x)), ff_add(two_prod(y, y), two_prod(z, z)));
+    // s = 2 / |q|^2: float reciprocal plus one correction with the exact residual
+    const float r0 = __fdiv_rn(2.0f, q2.hi);
+    const ff res = ff_sub(ff_make(2.0f), ff_mulf(q2, r0));
+    const ff s = fast_two_sum(r0, __fmul_rn(res.hi, __fmul_rn(r0, 0.5f)));
+    o[0] = ff_mul(s, ff_add(two_prod(x, z), two_prod(w, y)));
+    o[1] = ff_mul(s, ff_sub(two_prod(y, z), two_prod(w, x)));
+    o[2] = ff_sub(ff_make(1.0f), ff_mul(s, ff_add(two_prod(x, x), two_prod(y, y))));
+}
+
+// sigma(n) = sqrt(R_perp^2 |n|^2 + (R_par^2 - R_perp^2) (o.n)^2) in float-float,
+// for an exactly represented (not necessarily unit) float n with |n|^2 = nn
+__device__ __forceinline__ ff ff_support(const PView &P, int k, const float n[3], ff nn)
+{
+    ff o[3];
+    ff_axis(__ldg(P.qw + k), __ldg(P.qx + k), __ldg(P.qy + k), __ldg(P.qz + k), o);
+    const float a = __ldg(P.rperp + k), c = __ldg(P.rpar + k);
+    const ff on = ff_add(ff_add(ff_mulf(o[0], n[0]), ff_mulf(o[1], n[1])), ff_mulf(o[2], n[2]));
+    const ff a2 = two_prod(a, a);
+    const ff e = ff_sub(two_prod(c, c), a2);
+    return ff_sqrt(ff_add(ff_mul(a2, nn), ff_mul(e, ff_mul(on, on))));
+}
+
+// g at the unit vector n/|n|, in float-float: g is homogeneous of degree one,
+// so g(n/|n|) = g(n) / |n| = g(n) (1 - (|n|^2 - 1)/2 + ...), |n|^2 - 1 ~ 1e-7
+__device__ __forceinline__ double ff_gap(const PView &P, int i, int j, const ff d[3], const float n[3])
+{
+    const ff nn = ff_add(ff_add(two_prod(n[0], n[0]), two_prod(n[1], n[1])), two_prod(n[2], n[2]));
+    const ff nd = ff_add(ff_add(ff_mulf(d[0], n[0]), ff_mulf(d[1], n[1])), ff_mulf(d[2], n[2]));
+    const ff G = ff_sub(ff_sub(nd, ff_support(P, i, n, nn)), ff_support(P, j, n, nn));
+    const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);
+    const ff h = ff_sub(G, ff_make(__fmul_rn(G.hi, __fmul_rn(0.5f, eps))));
+    return ff_to_double(h);
+}
+
+__device__ __forceinline__ bool pair_bad(const PView &P, const DView &D, int i, int j)
+{
+    bool bad = (i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i);
+    if (!bad) bad = !shape_ok(__ldg(P.rpar + i), __ldg(P.rperp + i));
+    if (!bad && j >= 0) bad = !shape_ok(__ldg(P.rpar + j), __ldg(P.rperp + j));
+    return bad;
+}
+
+__device__ __forceinline__ double wall_gap(const PView &P, const DView &D, int i, int w, V3<double> &n)
+{
+    // plane wall w: n = -dir e_z, h = dir (z_i - wall_z) - sigma_i(e_z)
+    const double dir = (double)D.wall_dir[w];
+    const Shape<double> si = load_shape<double>(P, i);
+    n = mk<double>(0.0, 0.0, -dir);
+    return dir * (__ldg(P.z + i) - D.wall_z[w]) - support(si, mk<double>(0.0, 0.0, 1.0));
+}
+
+// LUB_MIXED: FP32 Newton + float-float gap; near-contact / unconverged pairs
+// go to the work list (entry k: refine from the FP32 normal; -1-k: full FP64
+// solve from the line of centres)
+__global__ void __launch_bounds__(128) k_closest_mixed(PView P, DView D, const int32_t *__restrict__ pi,
+                                                       const int32_t *__restrict__ pj,
+                                                       const int32_t *__restrict__ d_count, int32_t cap,
+                                                       double *__restrict__ nout, double *__restrict__ gap,
+                                                       uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                       int maxit, float tol32, float fp64_switch, int warm,
+                                                       int32_t *__restrict__ wl_count, int32_t *__restrict__ wl)
 {
     const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop bound: the whole warp takes part in the work-list ballot
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int k = base + threadIdx.x;
+        int entry = 0x7fffffff;  // none
+        if (k < count) {
+            const int i = __ldg(pi + k), j = __ldg(pj + k);
+            int st = 0, nit = 0;
+            V3<double> n64 = mk<double>(0, 0, 0);
+            double h = 0.0;
+            if (pair_bad(P, D, i, j)) {
+                st = LUB_ST_DEGENERATE;
+            } else if (j < 0) {
+                h = wall_gap(P, D, i, -1 - j, n64);
+            } else {
+                const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+                const ff dff[3] = {ff_from_double(d.x), ff_from_double(d.y), ff_from_double(d.z)};
+                const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
+                const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
+                const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
+                const ff dd = ff_add(ff_add(ff_mul(dff[0], dff[0]), ff_mul(dff[1], dff[1])), ff_mul(dff[2], dff[2]));
+                if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
+                    st = LUB_ST_DEGENERATE;
+                } else if (rpi == rqi && rpj == rqj) {
+                    // two spheres: n = d/|d|, h = |d| - R_i - R_j
+                    const ff dl = ff_sqrt(dd);
+                    const float inv = 1.0f / dl.hi;
+                    n64 = mk<double>(df.x * inv, df.y * inv, df.z * inv);
+                    h = ff_to_double(ff_sub(ff_sub(dl, ff_make(rpi)), ff_make(rpj)));
+                } else {
+                    const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
+                    const float dl = sqrtf(dd.hi);
+                    V3<float> n = scl(1.0f / dl, df);
+                    if (warm) {
+                        const V3<float> w0 = mk<float>((float)nout[k], (float)nout[C + k], (float)nout[2 * C + k]);
+                        const float wl2 = dot(w0, w0);
+                        if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2)) n = scl(rsqrtf(wl2), w0);
+                    }
+                    const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
+                    const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
+                    nit = o.iters;
+                    const float nv[3] = {n.x, n.y, n.z};
+                    h = ff_gap(P, i, j, dff, nv);
+                    // unit normal for the output (|n|^2 - 1 ~ 1e-7)
+                    const float nn = dot(n, n);
+                    const float f = 1.5f - 0.5f * nn;
+                    n64 = mk<double>(n.x * f, n.y * f, n.z * f);
+                    const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
+                    if (!o.converged || !isfinite(h))
+                        entry = -1 - k;
+                    else if (h < (double)fp64_switch * (double)amin)
+                        entry = k;
+                    // consistency check of Sec. III A: the normals point to the other centre
+                    if (entry == 0x7fffffff && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
+                }
+            }
+            if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
+            nout[k] = n64.x;
+            nout[C + k] = n64.y;
+            nout[2 * C + k] = n64.z;
+            gap[k] = h;
+            status[k] = (uint8_t)st;
+            if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+        }
+        // compacted append to the FP64 work list
+        const bool need = entry != 0x7fffffff;
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (m) {
+            int wbase = 0;
+            const int leader = __ffs(m) - 1;
+            if (lane == leader) wbase = atomicAdd(wl_count, __popc(m));
+            wbase = __shfl_sync(0xffffffffu, wbase, leader);
+            if (need) wl[wbase + __popc(m & ((1u << lane) - 1u))] = entry;
+        }
+    }
+}
+
+// FP64 refinement of the work list
+__global__ void __launch_bounds__(32) k_closest_refine(PView P, DView D, const int32_t *__restrict__ pi,
+                                                        const int32_t *__restrict__ pj, int32_t cap,
+                                                        double *__restrict__ nout, double *__restrict__ gap,
+                                                        uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                        int maxit, const int32_t *__restrict__ wl_count,
+                                                        const int32_t *__restrict__ wl)
+{
+    const int count = min(*wl_count, cap);
+    const size_t C = (size_t)cap;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        const int v = wl[q];
+        const bool full = v < 0;
+        const int k = full ? -1 - v : v;
+        const int i = pi[k], j = pj[k];
+        const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+        const double dl = sqrt(dot(d, d));
+        const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
+        V3<double> nn = full ? scl(1.0 / dl, d) : mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
+        const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
+        // from the FP32 normal one Newton step reaches rounding level (quadratic
+        // convergence from |dn| ~ 1e-7); a full solve iterates to 1e-11 rad
+        const NewtonOut o = full ? newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale)
+                                 : newton_sphere<double>(si, sj, d, nn, 1, 1e-5, 1e-14 * scale);
+        const V3<double> n64 = normalized(nn);
+        const double h = dot(n64, d) - support(si, n64) - support(sj, n64);
+        int st = LUB_ST_FP64;
+        if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+        if (h <= 0.0) st |= LUB_ST_OVERLAP;
+        nout[k] = n64.x;
+        nout[C + k] = n64.y;
+        nout[2 * C + k] = n64.z;
+        gap[k] = h;
+        status[k] = (uint8_t)st;
+        if (iters) {
+            const int nit = (full ? 0 : iters[k]) + o.iters;
+            iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+        }
+    }
+}
+
+// LUB_FP64: everything in double
+__global__ void __launch_bounds__(128) k_closest_fp64(PView P, DView D, const int32_t *__restrict__ pi,
+                                                      const int32_t *__restrict__ pj,
+                                                      const int32_t *__restrict__ d_count, int32_t cap,
+                                                      double *__restrict__ nout, double *__restrict__ gap,
+                                                      uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                      int maxit, int warm)
+{
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
         const int i = __ldg(pi + k), j = __ldg(pj + k);
-        int st = 0;
-        int nit = 0;
+        int st = 0, nit = 0;
         V3<double> n64 = mk<double>(0, 0, 0);
         double h = 0.0;
-        bool bad = (i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i);
-        if (!bad) bad = !shape_ok(__ldg(P.rpar + i), __ldg(P.rperp + i));
-        if (!bad && j >= 0) bad = !shape_ok(__ldg(P.rpar + j), __ldg(P.rperp + j));
-        if (bad) {
+        if (pair_bad(P, D, i, j)) {
             st = LUB_ST_DEGENERATE;
         } else if (j < 0) {
-            // plane wall w: n = -dir e_z, h = dir (z_i - wall_z) - sigma_i(e_z)
-            const int w = -1 - j;
-            const double dir = (double)D.wall_dir[w];
-            Shape<double> si = load_shape<double>(P, i);
-            n64 = mk<double>(0.0, 0.0, -dir);
-            h = dir * (__ldg(P.z + i) - D.wall_z[w]) - support(si, mk<double>(0.0, 0.0, 1.0));
+            h = wall_gap(P, D, i, -1 - j, n64);
         } else {
-            V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
-            double dl = sqrt(dot(d, d));
+            const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+            const double dl = sqrt(dot(d, d));
             if (!(dl > 0.0) || !isfinite(dl)) {
                 st = LUB_ST_DEGENERATE;
             } else {
                 const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
                 const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
                 if (rpi == rqi && rpj == rqj) {
-                    // two spheres: n = d/|d|, h = |d| - R_i - R_j
                     n64 = scl(1.0 / dl, d);
                     h = dl - (double)rpi - (double)rpj;
                 } else {
-                    Shape<double> si64 = load_shape<double>(P, i), sj64 = load_shape<double>(P, j);
-                    V3<double> start = scl(1.0 / dl, d);
+                    const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
+                    V3<double> nn = scl(1.0 / dl, d);
                     if (warm) {
-                        V3<double> w0 = mk<double>(nout[k], nout[cap + k], nout[2 * (size_t)cap + k]);
-                        double wl = dot(w0, w0);
-                        if (wl > 0.25 && wl < 4.0 && isfinite(wl)) start = scl(rsqrt(wl), w0);
+                        const V3<double> w0 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
+                        const double wl2 = dot(w0, w0);
+                        if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2)) nn = scl(rsqrt(wl2), w0);
                     }
                     const double scale = dl + (double)fmaxf(rpi, rqi) + (double)fmaxf(rpj, rqj);
-                    bool conv;
-                    if (MIXED) {
-                        Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
-                        V3<float> n = cvt<float>(start);
-                        V3<float> df = cvt<float>(d);
-                        NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32,
-                                                           (float)(4e-7 * scale));
-                        nit = o.iters;
-                        conv = o.converged;
-                        n64 = normalized(cvt<double>(n));
-                        h = dot(n64, d) - support(si64, n64) - support(sj64, n64);
-                        const double amin = (double)fminf(fminf(rpi, rqi), fminf(rpj, rqj));
-                        if (!conv || h < (double)fp64_switch * amin) {
-                            // FP64 Newton: refinement near contact, or full solve as fallback
-                            V3<double> nn = conv ? n64 : start;
-                            NewtonOut o2 = newton_sphere<double>(si64, sj64, d, nn, conv ? 4 : maxit, 1e-11,
-                                                                 1e-14 * scale);
-                            nit += o2.iters;
-                            conv = o2.converged;
-                            n64 = normalized(nn);
-                            h = dot(n64, d) - support(si64, n64) - support(sj64, n64);
-                            st |= LUB_ST_FP64;
-                        }
-                    } else {
-                        V3<double> nn = start;
-                        NewtonOut o = newton_sphere<double>(si64, sj64, d, nn, maxit, 1e-11, 1e-14 * scale);
-                        nit = o.iters;
-                        conv = o.converged;
-                        n64 = normalized(nn);
-                        h = dot(n64, d) - support(si64, n64) - support(sj64, n64);
-                    }
-                    // consistency check of Sec. III A: the normals point to the other centre
-                    if (!conv || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+                    const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
+                    nit = o.iters;
+                    n64 = normalized(nn);
+                    h = dot(n64, d) - support(si, n64) - support(sj, n64);
+                    if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
                 }
             }
         }
         if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
         nout[k] = n64.x;
-        nout[cap + k] = n64.y;
-        nout[2 * (size_t)cap + k] = n64.z;
+        nout[C + k] = n64.y;
+        nout[2 * C + k] = n64.z;
         gap[k] = h;
         status[k] = (uint8_t)st;
         if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
@@ -200,19 +361,29 @@ __global__ void __launch_bounds__(128) k_closest(PView P, DView D, const int32_t
 }  // namespace
 
 int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, const int32_t *pi,
-                   const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
-                   uint8_t *status, uint8_t *iters, cudaStream_t st)
+                   const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap, uint8_t *status,
+                   uint8_t *iters, cudaStream_t st)
 {
     if (cap == 0) return LUB_OK;
     const int block = 128;
     const int grid = grid_for(cap, block, ctx->num_sms, 8);
     const int warm = prm.warm_start == LUB_WARM_PREVIOUS;
-    if (prm.precision == LUB_MIXED)
-        k_closest<true><<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton,
-                                                (float)prm.newton_tol, (float)prm.fp64_switch, warm);
-    else
-        k_closest<false><<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters,
-                                                 prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch,
-                                                 warm);
+    if (prm.precision == LUB_MIXED) {
+        // work list: count + up to cap entries in the context scratch
+        int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);
+        if (rc) return rc;
+        int32_t *wl_count = (int32_t *)ctx->scratch;
+        int32_t *wl = (int32_t *)((char *)ctx->scratch + 256);
+        rc = lub_check_cuda(ctx, cudaMemsetAsync(wl_count, 0, 4, st), "memset work list");
+        if (rc) return rc;
+        k_closest_mixed<<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton,
+                                                (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl);
+        // one warp per block so the (short) work list spreads over every SM
+        k_closest_refine<<<grid_for(cap, 32, ctx->num_sms, 16), 32, 0, st>>>(
+            P, D, pi, pj, cap, n, gap, status, iters, prm.max_newton, wl_count, wl);
+    } else {
+        k_closest_fp64<<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton,
+                                               warm);
+    }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
 }

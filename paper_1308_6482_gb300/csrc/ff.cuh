@@ -1,0 +1,113 @@
+// Float-float ("double-single") arithmetic on the FP32 pipe.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  The building blocks are the error-free
+// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2), Fast2Sum (Dekker 1971)
+// and TwoProduct with a fused multiply-add (the product's rounding error is
+// fma(a, b, -a*b)); addition, multiplication and the square root with one
+// Newton correction follow Dekker, "A floating-point technique for extending
+// the available precision", Numer. Math. 18 (1971).  GB300 runs FP32 about 60
+// times faster than FP64, so a float-float operation of 10-20 FP32
+// instructions costs less than one FP64 operation.  The _rn intrinsics keep
+// the compiler from contracting or reordering the error terms.
+#pragma once
+
+#include <cuda_runtime.h>
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_make(float a)
+{
+    ff r;
+    r.hi = a;
+    r.lo = 0.0f;
+    return r;
+}
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    ff r;
+    r.hi = s;
+    r.lo = e;
+    return r;
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    ff r;
+    r.hi = s;
+    r.lo = e;
+    return r;
+}
+
+// p + e = a * b exactly (error of the product from a fused multiply-add)
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    ff r;
+    r.hi = p;
+    r.lo = e;
+    return r;
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ ff ff_neg(ff x)
+{
+    ff r;
+    r.hi = -x.hi;
+    r.lo = -x.lo;
+    return r;
+}
+
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const ff p = two_prod(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ ff ff_mulf(ff x, float y)
+{
+    const ff p = two_prod(x.hi, y);
+    const float e = __fmaf_rn(x.lo, y, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+
+// square root of a positive value: s = sqrt(hi), one Newton correction
+// (x - s^2) / (2 s) with x - s^2 formed exactly
+__device__ __forceinline__ ff ff_sqrt(ff x)
+{
+    const float s = __fsqrt_rn(x.hi);
+    const ff p = two_prod(s, s);
+    const float r = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo), __fdiv_rn(0.5f, s));
+    return fast_two_sum(s, r);
+}
+
+__device__ __forceinline__ ff ff_from_double(double d)
+{
+    const float hi = __double2float_rn(d);
+    ff r;
+    r.hi = hi;
+    r.lo = __double2float_rn(d - (double)hi);
+    return r;
+}
+
+__device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }

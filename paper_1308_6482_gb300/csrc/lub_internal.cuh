@@ -38,6 +38,7 @@ struct PView {
 
 struct DView {
     double L[3];
+    double invL[3];
     int32_t periodic[3];
     int32_t n_walls;
     double wall_z[2];
@@ -65,6 +66,7 @@ inline DView make_dview(const lub_domain *d)
     DView v;
     for (int k = 0; k < 3; ++k) {
         v.L[k] = d->L[k];
+        v.invL[k] = 1.0 / d->L[k];
         v.periodic[k] = d->periodic[k];
     }
     v.n_walls = d->n_walls;
@@ -109,16 +111,41 @@ __device__ __forceinline__ V3<T> axpy(T s, const V3<T> &a, const V3<T> &b)  // s
     return mk<T>(s * a.x + b.x, s * a.y + b.y, s * a.z + b.z);
 }
 
+// Double-precision reciprocal and reciprocal square root by Newton-Raphson
+// from an FP32 seed (x_{k+1} = x_k (2 - a x_k) and y_{k+1} = y_k (3 - a y_k^2)/2;
+// two steps take the seed's ~2^-22 relative error below double rounding).
+// GB300's FP64 pipe is about 60 times slower than FP32, and these use a
+// handful of FP64 multiply-adds where a full-precision division or square
+// root takes several times more.  Inputs are positive, normal and within the
+// float range here (squared lengths, shape factors, determinants).
+__device__ __forceinline__ double rcp64(double a)
+{
+    double x = (double)__frcp_rn((float)a);
+    x = x * fma(-a, x, 2.0);
+    x = x * fma(-a, x, 2.0);
+    return x;
+}
+
+__device__ __forceinline__ double rsqrt64(double a)
+{
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
-__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt64(v); }
 __device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
-__device__ __forceinline__ double sqrt_t(double v) { return sqrt(v); }
+__device__ __forceinline__ double sqrt_t(double v) { return v > 0.0 ? v * rsqrt64(v) : 0.0; }
+__device__ __forceinline__ float rcp_t(float v) { return 1.0f / v; }
+__device__ __forceinline__ double rcp_t(double v) { return rcp64(v); }
 
 template <typename T>
 __device__ __forceinline__ V3<T> normalized(const V3<T> &a)
 {
-    T l2 = dot(a, a);
-    return scl(T(1) / sqrt_t(l2), a);
+    return scl(rsqrt_t(dot(a, a)), a);
 }
 
 template <typename T, typename S>
@@ -136,7 +163,7 @@ template <typename T>
 __device__ __forceinline__ V3<T> quat_axis(float qw, float qx, float qy, float qz)
 {
     T w = qw, x = qx, y = qy, z = qz;
-    T s = T(2) / (w * w + x * x + y * y + z * z);
+    T s = T(2) * rcp_t(w * w + x * x + y * y + z * z);
     return mk<T>(s * (x * z + w * y), s * (y * z - w * x), T(1) - s * (x * x + y * y));
 }
 
@@ -175,8 +202,7 @@ template <typename T>
 __device__ __forceinline__ V3<T> support_offset(const Shape<T> &s, const V3<T> &n)
 {
     T c = dot(s.o, n);
-    T sg = sqrt_t(s.a2 * dot(n, n) + s.e * c * c);
-    T inv = T(1) / sg;
+    T inv = rsqrt_t(s.a2 * dot(n, n) + s.e * c * c);
     return axpy(s.e * c * inv, s.o, scl(s.a2 * inv, n));
 }
 
@@ -185,13 +211,14 @@ __device__ __forceinline__ V3<double> load_pos(const PView &P, int k)
     return mk<double>(__ldg(P.x + k), __ldg(P.y + k), __ldg(P.z + k));
 }
 
-// minimum image of r_j - r_i (same convention as the definition: subtract
-// L * floor(d / L + 1/2) along periodic axes)
+// minimum image of r_j - r_i: subtract L * floor(d / L + 1/2) along periodic
+// axes (d / L as d * (1/L): the two differ only within an ulp of d = +-L/2,
+// far outside any interaction range)
 __device__ __forceinline__ V3<double> min_image(const DView &D, V3<double> d)
 {
-    if (D.periodic[0]) d.x -= D.L[0] * floor(d.x / D.L[0] + 0.5);
-    if (D.periodic[1]) d.y -= D.L[1] * floor(d.y / D.L[1] + 0.5);
-    if (D.periodic[2]) d.z -= D.L[2] * floor(d.z / D.L[2] + 0.5);
+    if (D.periodic[0]) d.x -= D.L[0] * floor(d.x * D.invL[0] + 0.5);
+    if (D.periodic[1]) d.y -= D.L[1] * floor(d.y * D.invL[1] + 0.5);
+    if (D.periodic[2]) d.z -= D.L[2] * floor(d.z * D.invL[2] + 0.5);
     return d;
 }
 

@@ -1,18 +1,23 @@
 // K0: candidate pairs by a cell list with the pre-filters of Sec. III A.
 //
-//   1. cell of every particle (cell edge >= 2 Rmax + Delta_L), counting sort
-//      by cell (atomic slot + scan of the cell counts); particles are copied
-//      into cell order as two float4 records: position relative to the cell
-//      centre and Rmax, symmetry axis and e = R_par^2 - R_perp^2;
-//   2. count pass: one thread per particle (in cell order, so neighbouring
-//      threads read the same cells) sweeps the 27 neighbour cells and counts
-//      partners j > i passing the tests; plane-wall candidates are counted
-//      separately; both counts are scanned;
-//   3. write pass: the same sweep writes the partners of i at its offset and
-//      sorts them, giving the canonical (i, j) order without a global sort.
-// The tests run in FP32 on cell-relative coordinates with a safety margin;
-// a test that falls inside the margin is decided again in FP64 from the
-// original double positions, so every decision is the double-precision one.
+//   1. cell of every particle (cell edge >= 2 Rmax + Delta_L) and its slot
+//      in the cell (atomic), scan of the cell counts, copy of every particle
+//      into cell order as two float4 records: position relative to its cell
+//      centre with Rmax, and symmetry axis with e = R_par^2 - R_perp^2;
+//   2. count sweep: one thread per (particle, row of three neighbour cells),
+//      nine rows per particle, particles in cell order so neighbouring
+//      threads read the same cells; each unordered pair is visited once, by
+//      the particle earlier in cell order, and counted (atomically) for the
+//      smaller of its two indices; the row-0 thread tests the plane walls;
+//      one scan over [particle-pair counts | wall-pair counts] gives every
+//      offset (wall pairs land after all particle pairs);
+//   3. write sweep: the same sweep writes each pair at its particle's offset
+//      plus an atomic cursor;
+//   4. each particle's partners are sorted in place, giving the canonical
+//      (i, j) order.
+// The tests run in FP32 on cell-relative coordinates with a safety margin; a
+// test inside the margin is decided again in FP64 from the original double
+// positions, so every decision is the double-precision one.
 #include <string.h>
 
 #include "lub_internal.cuh"
@@ -23,19 +28,22 @@ struct Grid {
     int nc[3];
     float cs[3];
     double csd[3];
+    double inv_cs[3];
+    double invL[3];
     int64_t ncell;
     float cutoff;  // Delta_L
     float margin;  // absolute FP32 error allowance of the tests
+    float rmax;    // bound of every particle's Rmax
 };
 
-__device__ __forceinline__ double wrap_axis(double x, double L, int periodic)
+__device__ __forceinline__ double wrap_axis(double x, double L, double invL, int periodic)
 {
-    return periodic ? x - L * floor(x / L) : x;
+    return periodic ? x - L * floor(x * invL) : x;
 }
 
-__device__ __forceinline__ int cell_axis(double xw, double cs, int nc)
+__device__ __forceinline__ int cell_axis(double xw, double inv_cs, int nc)
 {
-    double f = floor(xw / cs);
+    double f = floor(xw * inv_cs);
     if (!(f >= 0.0)) f = 0.0;  // also catches NaN
     if (f > (double)(nc - 1)) f = (double)(nc - 1);
     return (int)f;
@@ -45,12 +53,9 @@ __global__ void k_cells_count(PView P, DView D, Grid G, int32_t *__restrict__ ce
                               int32_t *__restrict__ slot, float rmax_bound, int32_t *__restrict__ flags)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const double xw = wrap_axis(P.x[i], D.L[0], D.periodic[0]);
-        const double yw = wrap_axis(P.y[i], D.L[1], D.periodic[1]);
-        const double zw = wrap_axis(P.z[i], D.L[2], D.periodic[2]);
-        const int cx = cell_axis(xw, G.csd[0], G.nc[0]);
-        const int cy = cell_axis(yw, G.csd[1], G.nc[1]);
-        const int cz = cell_axis(zw, G.csd[2], G.nc[2]);
+        const int cx = cell_axis(wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]), G.inv_cs[0], G.nc[0]);
+        const int cy = cell_axis(wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]), G.inv_cs[1], G.nc[1]);
+        const int cz = cell_axis(wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]), G.inv_cs[2], G.nc[2]);
         const int c = (cz * G.nc[1] + cy) * G.nc[0] + cx;
         cell_of[i] = c;
         slot[i] = atomicAdd(cell_cnt + c, 1);
@@ -61,18 +66,20 @@ __global__ void k_cells_count(PView P, DView D, Grid G, int32_t *__restrict__ ce
 
 __global__ void k_cells_fill(PView P, DView D, Grid G, const int32_t *__restrict__ cell_start,
                              const int32_t *__restrict__ cell_of, const int32_t *__restrict__ slot,
-                             int32_t *__restrict__ sorted, float4 *__restrict__ rec0, float4 *__restrict__ rec1)
+                             int32_t *__restrict__ sorted, float4 *__restrict__ rec0, float4 *__restrict__ rec1,
+                             int32_t *__restrict__ cellc)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int c = cell_of[i];
         const int s = cell_start[c] + slot[i];
         const int cx = c % G.nc[0], cy = (c / G.nc[0]) % G.nc[1], cz = c / (G.nc[0] * G.nc[1]);
-        const double xw = wrap_axis(P.x[i], D.L[0], D.periodic[0]);
-        const double yw = wrap_axis(P.y[i], D.L[1], D.periodic[1]);
-        const double zw = wrap_axis(P.z[i], D.L[2], D.periodic[2]);
+        const double xw = wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]);
+        const double yw = wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]);
+        const double zw = wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]);
         const float rpar = P.rpar[i], rperp = P.rperp[i];
         const V3<float> o = quat_axis<float>(P.qw[i], P.qx[i], P.qy[i], P.qz[i]);
         sorted[s] = i;
+        cellc[s] = cx | (cy << 10) | (cz << 20);  // nc <= 1024 per axis
         rec0[s] = make_float4((float)(xw - (cx + 0.5) * G.csd[0]), (float)(yw - (cy + 0.5) * G.csd[1]),
                               (float)(zw - (cz + 0.5) * G.csd[2]), fmaxf(rpar, rperp));
         rec1[s] = make_float4(o.x, o.y, o.z, rpar * rpar - rperp * rperp);
@@ -80,7 +87,7 @@ __global__ void k_cells_fill(PView P, DView D, Grid G, const int32_t *__restrict
 }
 
 // exact (double) form of the three tests, as in the definition
-__device__ bool pair_test_fp64(const PView &P, const DView &D, int i, int j, double cutoff)
+__device__ __forceinline__ bool pair_test_fp64(const PView &P, const DView &D, int i, int j, double cutoff)
 {
     const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
     const double r = sqrt(dot(d, d));
@@ -97,9 +104,10 @@ __device__ bool pair_test_fp64(const PView &P, const DView &D, int i, int j, dou
 
 // decision of one candidate from the cell-order records (FP32 with margin,
 // FP64 when undecided)
-__device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const Grid &G, int i, int j,
+__device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const Grid &G, int s, int t,
                                           const float4 a0, const float4 a1, const float4 b0, const float4 b1,
-                                          float ox, float oy, float oz, double cutoff_d)
+                                          float ox, float oy, float oz, double cutoff_d,
+                                          const int32_t *__restrict__ sorted)
 {
     const float dx = b0.x - a0.x + ox, dy = b0.y - a0.y + oy, dz = b0.z - a0.z + oz;
     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -128,104 +136,136 @@ __device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const 
         sure = false;
     }
     if (sure) return true;
-    return pair_test_fp64(P, D, i, j, cutoff_d);
+    return pair_test_fp64(P, D, sorted[s], sorted[t], cutoff_d);
 }
 
-template <bool WRITE>
-__global__ void __launch_bounds__(128) k_pairs_sweep(PView P, DView D, Grid G, const int32_t *__restrict__ cell_start,
-                                                     const int32_t *__restrict__ sorted,
-                                                     const float4 *__restrict__ rec0,
-                                                     const float4 *__restrict__ rec1, const int32_t *__restrict__ cell_of,
-                                                     int32_t *__restrict__ cnt_pp, int32_t *__restrict__ cnt_w,
-                                                     const int32_t *__restrict__ totals, int32_t cap,
-                                                     int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
-                                                     double cutoff_d)
+// Sweep of one row of three neighbour cells (dy, dz fixed, dx = -1, 0, 1)
+// around the cell of the particle in slot s (cell order).  Each unordered
+// pair is visited once, by the particle with the smaller slot (t > s; the
+// neighbour relation of cells is symmetric).  emit(t) is called for every
+// partner passing the tests.
+template <typename Emit>
+__device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const Grid &G,
+                                          const int32_t *__restrict__ cell_start, const int32_t *__restrict__ sorted,
+                                          const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int s,
+                                          const float4 a0, const float4 a1, int cx, int cy, int cz, int row,
+                                          double cutoff_d, Emit emit)
 {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n; s += gridDim.x * blockDim.x) {
-        const int i = sorted[s];
-        const float4 a0 = rec0[s], a1 = rec1[s];
-        const int c = cell_of[i];
-        const int cx = c % G.nc[0], cy = (c / G.nc[0]) % G.nc[1], cz = c / (G.nc[0] * G.nc[1]);
-        int base = 0;
-        bool do_write = false;
-        if (WRITE) {
-            // totals[0] = particle pairs, totals[1] = wall pairs
-            do_write = (int64_t)totals[0] + totals[1] <= (int64_t)cap;
-            base = cnt_pp[i];
+    const int dy = row % 3 - 1, dz = row / 3 - 1;
+    int yc = cy + dy, zc = cz + dz;
+    if (yc < 0 || yc >= G.nc[1]) {
+        if (!D.periodic[1]) return;
+        yc += yc < 0 ? G.nc[1] : -G.nc[1];
+    }
+    if (zc < 0 || zc >= G.nc[2]) {
+        if (!D.periodic[2]) return;
+        zc += zc < 0 ? G.nc[2] : -G.nc[2];
+    }
+    const float oy = dy * G.cs[1], oz = dz * G.cs[2];
+    const int rowbase = (zc * G.nc[1] + yc) * G.nc[0];
+    // skip neighbour cells no partner of particle s can reach: distance from
+    // the particle to the cell's box against Rmax_s + Rmax + Delta_L
+    const float reach = a0.w + G.rmax + G.cutoff + G.margin;
+    const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2], hx = 0.5f * G.cs[0];
+    const float ey = dy == 0 ? 0.f : fmaxf(fabsf(oy - a0.y) - hy, 0.f);
+    const float ez = dz == 0 ? 0.f : fmaxf(fabsf(oz - a0.z) - hz, 0.f);
+    const float r2yz = ey * ey + ez * ez;
+    if (r2yz > reach * reach) return;
+    // on a periodic axis with fewer than three cells the same cell recurs with
+    // different image offsets; the domain check (L > 2 range) leaves at most
+    // one image within range, so each partner passes at most once
+    for (int dx = -1; dx <= 1; ++dx) {
+        int xc = cx + dx;
+        if (xc < 0 || xc >= G.nc[0]) {
+            if (!D.periodic[0]) continue;
+            xc += xc < 0 ? G.nc[0] : -G.nc[0];
         }
-        int found = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            int zc = cz + dz;
-            if (zc < 0 || zc >= G.nc[2]) {
-                if (!D.periodic[2]) continue;
-                zc = (zc + G.nc[2]) % G.nc[2];
-            }
-            for (int dy = -1; dy <= 1; ++dy) {
-                int yc = cy + dy;
-                if (yc < 0 || yc >= G.nc[1]) {
-                    if (!D.periodic[1]) continue;
-                    yc = (yc + G.nc[1]) % G.nc[1];
-                }
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int xc = cx + dx;
-                    if (xc < 0 || xc >= G.nc[0]) {
-                        if (!D.periodic[0]) continue;
-                        xc = (xc + G.nc[0]) % G.nc[0];
-                    }
-                    // skip repeated cells along non-periodic axes only; on periodic
-                    // axes with fewer than three cells each image is distinct
-                    const int c2 = (zc * G.nc[1] + yc) * G.nc[0] + xc;
-                    const float ox = dx * G.cs[0], oy = dy * G.cs[1], oz = dz * G.cs[2];
-                    const int e = cell_start[c2 + 1];
-                    for (int t = cell_start[c2]; t < e; ++t) {
-                        const int j = sorted[t];
-                        if (j <= i) continue;
-                        if (pair_test(P, D, G, i, j, a0, a1, rec0[t], rec1[t], ox, oy, oz, cutoff_d)) {
-                            if (WRITE && do_write) pair_j[base + found] = j;
-                            ++found;
-                        }
-                    }
-                }
-            }
-        }
-        if (!WRITE) {
-            cnt_pp[i] = found;
-        } else if (do_write) {
-            // canonical order: sort the partners of i ascending
-            int32_t *pjb = pair_j + base;
-            for (int a = 1; a < found; ++a) {
-                const int v = pjb[a];
-                int b = a - 1;
-                while (b >= 0 && pjb[b] > v) {
-                    pjb[b + 1] = pjb[b];
-                    --b;
-                }
-                pjb[b + 1] = v;
-            }
-            for (int a = 0; a < found; ++a) pair_i[base + a] = i;
-        }
-        // plane walls (exact double gap)
-        int wf = 0;
-        int wbase = WRITE ? totals[0] + cnt_w[i] : 0;
-        for (int w = 0; w < D.n_walls; ++w) {
-            const Shape<double> si = load_shape<double>(P, i);
-            const double hw = (double)D.wall_dir[w] * (P.z[i] - D.wall_z[w]) - support(si, mk<double>(0.0, 0.0, 1.0));
-            if (hw < cutoff_d) {
-                if (WRITE && do_write) {
-                    pair_i[wbase + wf] = i;
-                    pair_j[wbase + wf] = -1 - w;
-                }
-                ++wf;
-            }
-        }
-        if (!WRITE) cnt_w[i] = wf;
+        const int c2 = rowbase + xc;
+        const float ox = dx * G.cs[0];
+        const float ex = dx == 0 ? 0.f : fmaxf(fabsf(ox - a0.x) - hx, 0.f);
+        if (ex * ex + r2yz > reach * reach) continue;
+        const int e = cell_start[c2 + 1];
+        for (int t = max(cell_start[c2], s + 1); t < e; ++t)
+            if (pair_test(P, D, G, s, t, a0, a1, rec0[t], rec1[t], ox, oy, oz, cutoff_d, sorted)) emit(t);
     }
 }
 
-__global__ void k_total(const int32_t *__restrict__ totals, int32_t *__restrict__ d_count)
+// One thread per (particle slot s in cell order, row); the row-0 thread also
+// tests the walls.  cnt: [0, N) particle-pair counts per particle (of the
+// smaller index of each pair), [N, 2N) wall-pair counts; cur: [0, N) write
+// cursors (zeroed).
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, DView D, Grid G, const int32_t *__restrict__ cell_start,
+                                                     const int32_t *__restrict__ sorted,
+                                                     const float4 *__restrict__ rec0,
+                                                     const float4 *__restrict__ rec1,
+                                                     const int32_t *__restrict__ cellc, int32_t *__restrict__ cnt,
+                                                     int32_t *__restrict__ cur, const int32_t *__restrict__ total,
+                                                     int32_t cap, int32_t *__restrict__ pair_i,
+                                                     int32_t *__restrict__ pair_j, double cutoff_d,
+                                                     int32_t *__restrict__ d_count)
 {
-    const int64_t t = (int64_t)totals[0] + totals[1];
-    *d_count = t > 0x7fffffff ? 0x7fffffff : (int32_t)t;
+    const int N = P.n;
+    if (WRITE) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *d_count = *total;
+        if (*total > cap) return;
+    }
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < 9 * N; f += gridDim.x * blockDim.x) {
+        const int s = f / 9, row = f - 9 * s;
+        const int i = sorted[s];
+        const float4 a0 = rec0[s], a1 = rec1[s];
+        const int cc = cellc[s];
+        const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
+        sweep_row(P, D, G, cell_start, sorted, rec0, rec1, s, a0, a1, cx, cy, cz, row, cutoff_d, [&](int t) {
+            const int j = sorted[t];
+            const int lo = min(i, j), hi = max(i, j);
+            if (!WRITE) {
+                atomicAdd(cnt + lo, 1);
+            } else {
+                const int pos = cnt[lo] + atomicAdd(cur + lo, 1);
+                pair_i[pos] = lo;
+                pair_j[pos] = hi;
+            }
+        });
+        if (row == 0) {
+            // plane walls (exact double gap)
+            int wf = 0;
+            const int wbase = WRITE ? cnt[N + i] : 0;
+            for (int ww = 0; ww < D.n_walls; ++ww) {
+                const Shape<double> si = load_shape<double>(P, i);
+                const double hw =
+                    (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0));
+                if (hw < cutoff_d) {
+                    if (WRITE) {
+                        pair_i[wbase + wf] = i;
+                        pair_j[wbase + wf] = -1 - ww;
+                    }
+                    ++wf;
+                }
+            }
+            if (!WRITE) cnt[N + i] = wf;
+        }
+    }
+}
+
+// canonical order: sort the partners of each particle in place
+__global__ void __launch_bounds__(256) k_pairs_sort(int32_t n, const int32_t *__restrict__ cnt,
+                                                    const int32_t *__restrict__ total, int32_t cap,
+                                                    int32_t *__restrict__ pair_j)
+{
+    if (*total > cap) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = cnt[i], e = cnt[i + 1];
+        for (int a = b + 1; a < e; ++a) {
+            const int v = pair_j[a];
+            int q = a - 1;
+            while (q >= b && pair_j[q] > v) {
+                pair_j[q + 1] = pair_j[q];
+                --q;
+            }
+            pair_j[q + 1] = v;
+        }
+    }
 }
 
 __global__ void k_max_semi(PView P, unsigned int *__restrict__ out)
@@ -240,6 +280,118 @@ __global__ void k_max_semi(PView P, unsigned int *__restrict__ out)
 }
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int64_t max_cells)
+{
+    // cells at least (1 + 1e-9) times the interaction range, so a particle
+    // assigned to a cell by rounding at its border still finds every partner
+    // in the 27 neighbour cells
+    const double range = (2.0 * (double)rmax + prm.list_cutoff) * (1.0 + 1e-9);
+    Grid G;
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)floor(D.L[a] / range);
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        G.nc[a] = nc;
+    }
+    // keep the grid at most a few cells per particle (huge, sparse boxes) and
+    // within max_cells
+    int64_t limit = 8 * n + 4096;
+    if (limit > max_cells) limit = max_cells;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int64_t ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+        if (ncell <= limit) break;
+        const double f = cbrt((double)ncell / (double)limit) * (1.0 + 0.02 * pass);
+        for (int a = 0; a < 3; ++a) {
+            int nc = (int)floor(G.nc[a] / f);
+            G.nc[a] = nc < 1 ? 1 : nc;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        G.csd[a] = D.L[a] / G.nc[a];
+        G.cs[a] = (float)G.csd[a];
+        G.inv_cs[a] = G.nc[a] / D.L[a];
+        G.invL[a] = 1.0 / D.L[a];
+    }
+    G.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+    G.cutoff = (float)prm.list_cutoff;
+    // FP32 error of cell-relative coordinates and of the test values, with headroom
+    G.margin = (float)(1e-5 * (range + 1.0));
+    G.rmax = rmax;
+    return G;
+}
+
+struct Layout {
+    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *cnt, *totals;
+    float4 *rec0, *rec1;
+    void *tmp;
+    size_t tmp_bytes, total;
+};
+
+Layout layout(void *base, int64_t N, int64_t ncell)
+{
+    const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((3 * N + 1) * 4);
+    const size_t b_rec = align256(N * 16),
+                 b_tmp = align256(scan_tmp_bytes(ncell + 1 > 2 * N + 1 ? ncell + 1 : 2 * N + 1));
+    Layout L;
+    char *s = (char *)base;
+    L.flags = (int32_t *)s;
+    s += 256;
+    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells
+    s += 256;
+    L.cell_cnt = (int32_t *)s;
+    s += b_cell;
+    L.cell_of = (int32_t *)s;
+    s += b_n;
+    L.slot = (int32_t *)s;
+    s += b_n;
+    L.sorted = (int32_t *)s;
+    s += b_n;
+    L.cellc = (int32_t *)s;
+    s += b_n;
+    L.cnt = (int32_t *)s;
+    s += b_n2;
+    L.rec0 = (float4 *)s;
+    s += b_rec;
+    L.rec1 = (float4 *)s;
+    s += b_rec;
+    L.tmp = s;
+    L.tmp_bytes = b_tmp;
+    s += b_tmp;
+    L.total = (size_t)(s - (char *)base);
+    return L;
+}
+
+// the build on a workspace; flags live in the workspace
+int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PView &P, const DView &D,
+               const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count,
+               cudaStream_t st)
+{
+    const int64_t N = P.n;
+    Layout L = layout(scratch, N, G.ncell);
+    // the scratch keeps earlier contents: clear what must start at zero
+    int rc = lub_check_cuda(ctx, cudaMemsetAsync(L.flags, 0, 512, st), "memset flags");
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cell_cnt, 0, (G.ncell + 1) * 4, st), "memset cells");
+    if (rc) return rc;
+    if (N == 0) return lub_check_cuda(ctx, cudaMemsetAsync(d_count, 0, 4, st), "memset count");
+    const int block = 256;
+    const int gn = grid_for(N, block, num_sms, 8);
+    k_cells_count<<<gn, block, 0, st>>>(P, D, G, L.cell_cnt, L.cell_of, L.slot, rmax, L.flags);
+    if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st))) return rc;
+    k_cells_fill<<<gn, block, 0, st>>>(P, D, G, L.cell_cnt, L.cell_of, L.slot, L.sorted, L.rec0, L.rec1, L.cellc);
+    // counts and write cursors start at zero
+    if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (3 * N + 1) * 4, st), "memset counts"))) return rc;
+    int32_t *cur = L.cnt + 2 * N + 1;
+    const int gs = grid_for(9 * N, 256, num_sms, 32);
+    k_pairs_sweep<false><<<gs, 256, 0, st>>>(P, D, G, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc, L.cnt, cur,
+                                             L.totals, cap, pi, pj, prm.list_cutoff, d_count);
+    // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
+    if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st))) return rc;
+    k_pairs_sweep<true><<<gs, 256, 0, st>>>(P, D, G, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc, L.cnt, cur,
+                                            L.totals, cap, pi, pj, prm.list_cutoff, d_count);
+    k_pairs_sort<<<grid_for(N, 256, num_sms, 8), 256, 0, st>>>((int32_t)N, L.cnt, L.totals, cap, pj);
+    return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
+}
 
 }  // namespace
 
@@ -265,86 +417,15 @@ int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_
 int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, float rmax, int32_t *pi,
                        int32_t *pj, int32_t cap, int32_t *d_count, cudaStream_t st)
 {
-    const double range = 2.0 * (double)rmax + prm.list_cutoff;
-    Grid G;
-    for (int a = 0; a < 3; ++a) {
-        int nc = (int)floor(D.L[a] / range);
-        if (nc < 1) nc = 1;
-        if (nc > 1024) nc = 1024;
-        G.nc[a] = nc;
-        G.csd[a] = D.L[a] / nc;
-        G.cs[a] = (float)G.csd[a];
-    }
-    // keep the grid at most a few cells per particle (huge, sparse boxes)
-    const int64_t cell_limit = 8 * (int64_t)P.n + 4096;
-    int64_t ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
-    if (ncell > cell_limit) {
-        const double f = cbrt((double)ncell / (double)cell_limit);
-        for (int a = 0; a < 3; ++a) {
-            int nc = (int)floor(G.nc[a] / f);
-            G.nc[a] = nc < 1 ? 1 : nc;
-            G.csd[a] = D.L[a] / G.nc[a];
-            G.cs[a] = (float)G.csd[a];
-        }
-    }
-    G.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
-    G.cutoff = (float)prm.list_cutoff;
-    // FP32 error of cell-relative coordinates and of the test values, with headroom
-    G.margin = (float)(1e-5 * (range + 1.0));
-    const int64_t N = P.n;
-    // scratch layout
-    const size_t b_cell = align256((G.ncell + 1) * 4), b_n = align256((N + 1) * 4), b_rec = align256(N * 16);
-    const size_t b_tot = 256, b_tmp = align256(scan_tmp_bytes(G.ncell + 1 > N + 1 ? G.ncell + 1 : N + 1));
-    const size_t total = b_cell + 5 * b_n + 2 * b_rec + b_tot + b_tmp;
-    int rc = lub_ensure_scratch(ctx, total);
+    const Grid G = make_grid(D, prm, rmax, P.n, (int64_t)1 << 40);
+    const size_t need = layout(nullptr, P.n, G.ncell).total;
+    int rc = lub_ensure_scratch(ctx, need);
     if (rc) return rc;
-    char *s = (char *)ctx->scratch;
-    int32_t *cell_cnt = (int32_t *)s;
-    s += b_cell;
-    int32_t *cell_of = (int32_t *)s;
-    s += b_n;
-    int32_t *slot = (int32_t *)s;
-    s += b_n;
-    int32_t *sorted = (int32_t *)s;
-    s += b_n;
-    int32_t *cnt_pp = (int32_t *)s;
-    s += b_n;
-    int32_t *cnt_w = (int32_t *)s;
-    s += b_n;
-    float4 *rec0 = (float4 *)s;
-    s += b_rec;
-    float4 *rec1 = (float4 *)s;
-    s += b_rec;
-    int32_t *totals = (int32_t *)s;  // [0] pp, [1] wall, [2] cells
-    s += b_tot;
-    void *tmp = s;
-
-    rc = lub_check_cuda(ctx, cudaMemsetAsync(cell_cnt, 0, b_cell, st), "memset cells");
+    rc = build_core(ctx, ctx->num_sms, ctx->scratch, G, P, D, prm, rmax, pi, pj, cap, d_count, st);
     if (rc) return rc;
-    rc = lub_check_cuda(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), st), "memset flags");
-    if (rc) return rc;
-    const int block = 256;
-    const int gn = grid_for(N > 0 ? N : 1, block, ctx->num_sms, 8);
-    if (N > 0) k_cells_count<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, rmax, ctx->d_flags);
-    rc = scan_exclusive(ctx, cell_cnt, G.ncell + 1, totals + 2, tmp, b_tmp, st);
-    if (rc) return rc;
-    if (N > 0) {
-        k_cells_fill<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, sorted, rec0, rec1);
-        const int gs = grid_for(N, 128, ctx->num_sms, 16);
-        k_pairs_sweep<false><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
-                                                 totals, cap, pi, pj, prm.list_cutoff);
-        rc = scan_exclusive(ctx, cnt_pp, N, totals + 0, tmp, b_tmp, st);
-        if (rc) return rc;
-        rc = scan_exclusive(ctx, cnt_w, N, totals + 1, tmp, b_tmp, st);
-        if (rc) return rc;
-        k_pairs_sweep<true><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
-                                                totals, cap, pi, pj, prm.list_cutoff);
-    } else {
-        rc = lub_check_cuda(ctx, cudaMemsetAsync(totals, 0, 8, st), "memset totals");
-        if (rc) return rc;
-    }
-    k_total<<<1, 1, 0, st>>>(totals, d_count);
-    return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
+    // flags of this call for the host-count path
+    return lub_check_cuda(ctx, cudaMemcpyAsync(ctx->d_flags, ctx->scratch, 4, cudaMemcpyDeviceToDevice, st),
+                          "copy flags");
 }
 
 // ---------------------------------------------------------------------------
@@ -353,90 +434,15 @@ int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_p
 // ---------------------------------------------------------------------------
 size_t pairs_scratch_bytes(int64_t n, int64_t max_cells)
 {
-    const size_t b_cell = align256((max_cells + 1) * 4), b_n = align256((n + 1) * 4), b_rec = align256(n * 16);
-    const size_t b_tot = 256, b_tmp = align256(scan_tmp_bytes(max_cells + 1 > n + 1 ? max_cells + 1 : n + 1));
-    return b_cell + 5 * b_n + 2 * b_rec + b_tot + b_tmp + 256;  // + 256: flags
+    return layout(nullptr, n, max_cells).total;
 }
 
 int pairs_build_on_scratch(int num_sms, void *scratch, size_t scratch_bytes, int64_t max_cells, const PView &P,
                            const DView &D, const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap,
                            int32_t *d_count, cudaStream_t st)
 {
-    const double range = 2.0 * (double)rmax + prm.list_cutoff;
-    Grid G;
-    for (int a = 0; a < 3; ++a) {
-        int nc = (int)floor(D.L[a] / range);
-        if (nc < 1) nc = 1;
-        if (nc > 1024) nc = 1024;
-        G.nc[a] = nc;
-        G.csd[a] = D.L[a] / nc;
-        G.cs[a] = (float)G.csd[a];
-    }
-    int64_t cell_limit = 8 * (int64_t)P.n + 4096;
-    if (cell_limit > max_cells) cell_limit = max_cells;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int64_t ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
-        if (ncell <= cell_limit) break;
-        const double f = cbrt((double)ncell / (double)cell_limit) * (1.0 + 1e-9) + (pass ? 0.01 * pass : 0.0);
-        for (int a = 0; a < 3; ++a) {
-            int nc = (int)floor(G.nc[a] / f);
-            G.nc[a] = nc < 1 ? 1 : nc;
-            G.csd[a] = D.L[a] / G.nc[a];
-            G.cs[a] = (float)G.csd[a];
-        }
-    }
-    G.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+    const Grid G = make_grid(D, prm, rmax, P.n, max_cells);
     if (G.ncell > max_cells) return LUB_ERR_ARG;
-    G.cutoff = (float)prm.list_cutoff;
-    G.margin = (float)(1e-5 * (range + 1.0));
-    const int64_t N = P.n;
-    const size_t b_cell = align256((G.ncell + 1) * 4), b_n = align256((N + 1) * 4), b_rec = align256(N * 16);
-    const size_t b_tot = 256, b_tmp = align256(scan_tmp_bytes(G.ncell + 1 > N + 1 ? G.ncell + 1 : N + 1));
-    if (b_cell + 5 * b_n + 2 * b_rec + b_tot + b_tmp + 256 > scratch_bytes) return LUB_ERR_ARG;
-    char *s = (char *)scratch;
-    int32_t *flags = (int32_t *)s;
-    s += 256;
-    int32_t *cell_cnt = (int32_t *)s;
-    s += b_cell;
-    int32_t *cell_of = (int32_t *)s;
-    s += b_n;
-    int32_t *slot = (int32_t *)s;
-    s += b_n;
-    int32_t *sorted = (int32_t *)s;
-    s += b_n;
-    int32_t *cnt_pp = (int32_t *)s;
-    s += b_n;
-    int32_t *cnt_w = (int32_t *)s;
-    s += b_n;
-    float4 *rec0 = (float4 *)s;
-    s += b_rec;
-    float4 *rec1 = (float4 *)s;
-    s += b_rec;
-    int32_t *totals = (int32_t *)s;
-    s += b_tot;
-    void *tmp = s;
-    // the scratch keeps the previous call's contents: clear what must start at zero
-    if (cudaMemsetAsync(cell_cnt, 0, b_cell, st) != cudaSuccess) return LUB_ERR_CUDA;
-    if (cudaMemsetAsync(flags, 0, 256, st) != cudaSuccess) return LUB_ERR_CUDA;
-    const int block = 256;
-    const int gn = grid_for(N > 0 ? N : 1, block, num_sms, 8);
-    if (N > 0) k_cells_count<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, rmax, flags);
-    int rc = scan_exclusive(nullptr, cell_cnt, G.ncell + 1, totals + 2, tmp, b_tmp, st);
-    if (rc) return rc;
-    if (N > 0) {
-        k_cells_fill<<<gn, block, 0, st>>>(P, D, G, cell_cnt, cell_of, slot, sorted, rec0, rec1);
-        const int gs = grid_for(N, 128, num_sms, 16);
-        k_pairs_sweep<false><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
-                                                 totals, cap, pi, pj, prm.list_cutoff);
-        rc = scan_exclusive(nullptr, cnt_pp, N, totals + 0, tmp, b_tmp, st);
-        if (rc) return rc;
-        rc = scan_exclusive(nullptr, cnt_w, N, totals + 1, tmp, b_tmp, st);
-        if (rc) return rc;
-        k_pairs_sweep<true><<<gs, 128, 0, st>>>(P, D, G, cell_cnt, sorted, rec0, rec1, cell_of, cnt_pp, cnt_w,
-                                                totals, cap, pi, pj, prm.list_cutoff);
-    } else {
-        if (cudaMemsetAsync(totals, 0, 8, st) != cudaSuccess) return LUB_ERR_CUDA;
-    }
-    k_total<<<1, 1, 0, st>>>(totals, d_count);
-    return cudaGetLastError() == cudaSuccess ? LUB_OK : LUB_ERR_CUDA;
+    if (layout(nullptr, P.n, G.ncell).total > scratch_bytes) return LUB_ERR_ARG;
+    return build_core(nullptr, num_sms, scratch, G, P, D, prm, rmax, pi, pj, cap, d_count, st);
 }

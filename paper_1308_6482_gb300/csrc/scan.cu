@@ -1,7 +1,9 @@
-// Device-wide exclusive prefix sum of int32 values, in place (three passes:
-// tile sums, scan of tile sums, tile scan plus offset).  Used for the cell
-// grid and the per-particle pair counts of the pair builder and for the
-// incidence lists of the deterministic force sum.
+// Device-wide exclusive prefix sum of int32 values, in place, in two
+// launches: (1) per-tile sums; (2) each tile adds the sums of the tiles
+// before it (read directly: there are few tiles) and scans itself; the last
+// tile writes the total.  Used for the cell grid and the per-particle pair
+// counts of the pair builder and for the incidence lists of the
+// deterministic force sum.
 #include "lub_internal.cuh"
 
 namespace {
@@ -39,49 +41,35 @@ __device__ __forceinline__ int block_exclusive(int v, int &total)
     return warp_off + x - v;
 }
 
+__device__ __forceinline__ int block_sum(int v)
+{
+    int tot;
+    block_exclusive(v, tot);
+    return tot;
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_sums(const int32_t *__restrict__ a, int64_t n,
                                                             int32_t *__restrict__ sums)
 {
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     int s = 0;
 #pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q)
-        if (base + q < n) s += a[base + q];
-    int tot;
-    block_exclusive(s, tot);
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        const int64_t idx = base + (int64_t)q * SCAN_THREADS + threadIdx.x;  // coalesced
+        if (idx < n) s += a[idx];
+    }
+    const int tot = block_sum(s);
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// single block: exclusive scan of the tile sums, total -> *d_total
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int32_t *__restrict__ sums, int64_t nb,
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(int32_t *__restrict__ a, int64_t n,
+                                                            const int32_t *__restrict__ sums,
                                                             int32_t *__restrict__ d_total)
 {
-    int carry = 0;
-    for (int64_t base = 0; base < nb; base += SCAN_TILE) {
-        int v[SCAN_ITEMS];
-        int s = 0;
-#pragma unroll
-        for (int q = 0; q < SCAN_ITEMS; ++q) {
-            int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + q;
-            v[q] = idx < nb ? sums[idx] : 0;
-            s += v[q];
-        }
-        int tot;
-        int off = block_exclusive(s, tot) + carry;
-#pragma unroll
-        for (int q = 0; q < SCAN_ITEMS; ++q) {
-            int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + q;
-            if (idx < nb) sums[idx] = off;
-            off += v[q];
-        }
-        carry += tot;
-    }
-    if (threadIdx.x == 0 && d_total) *d_total = carry;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(int32_t *__restrict__ a, int64_t n,
-                                                            const int32_t *__restrict__ sums)
-{
+    // prefix of this tile: sum of the tile sums before it
+    int pre = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_THREADS) pre += sums[t];
+    pre = block_sum(pre);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
     int s = 0;
@@ -91,12 +79,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(int32_t *__restrict_
         s += v[q];
     }
     int tot;
-    int off = block_exclusive(s, tot) + sums[blockIdx.x];
+    int off = block_exclusive(s, tot) + pre;
 #pragma unroll
     for (int q = 0; q < SCAN_ITEMS; ++q) {
         if (base + q < n) a[base + q] = off;
         off += v[q];
     }
+    if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_total = pre + tot;
 }
 
 }  // namespace
@@ -116,7 +105,6 @@ int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, voi
     if (nb < 1) nb = 1;
     int32_t *sums = (int32_t *)tmp;
     k_tile_sums<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, sums);
-    k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nb, d_total);
-    k_tile_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, sums);
+    k_tile_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, sums, d_total);
     return lub_check_cuda(ctx, cudaGetLastError(), "scan launch");
 }
