@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain warm-start comparison")
+    ap.add_argument("--learned-pairs", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--fp64-switch", type=float, default=1e-3,
                     help="h/a below which pairs get the FP64 Newton refinement (0: none)")
@@ -300,6 +302,8 @@ def run_ours(args):
         "roofline": roof, "clocks": clocks, "gpu_launches": kernels_per_step * args.steps,
         "e2e": e2e,
     }
+    if not args.no_learned:
+        out["learned_vs_plain"] = learned_vs_plain(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(parts, dom)
     if rank == 0:
@@ -307,6 +311,64 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def learned_vs_plain(args, dev, stream, flush, steps=20, warmup=3):
+    """Learned warm start against the plain (line-of-centres) start on fresh
+    spheroid pairs: aspect ratios log-uniform in [1/3, 3], gaps log-uniform in
+    [1e-4, 1] x the pair's smallest semi-axis, one seed the training set never
+    used.  Times lub_closest_points alone (the network's inference runs inside
+    it for the learned form), L2 flushed between calls, and checks that both
+    forms reach the same gaps (equal accuracy)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1308_6482_gb300 as lub
+    from paper_1308_6482_gb300.mlp import WarmStartMLP
+
+    parts, dom, pi, pj = gen.pair_stream(args.learned_pairs, seed=9100, kind="aspect", gap_range=(1e-4, 1.0),
+                                         gap_scale="min_axis")
+    m = len(pi)
+    net = WarmStartMLP.load(device=dev)
+    P = lub.DeviceParticles(parts, dev)
+    out = {"workload": "%d fresh spheroid pairs, aspect ratios log-uniform [1/3,3], gap log-uniform "
+                       "[1e-4,1] x min semi-axis" % m, "steps": steps}
+    for prec in ("fp64", "mixed"):
+        res = {}
+        for form in ("plain", "learned"):
+            prm = lub.default_params(precision=prec, warm_start="mlp" if form == "learned" else "none")
+            pl = lub.Pipeline(P, dom, prm, capacity=m, device=dev)
+            if form == "learned":
+                net.install(pl.ctx)
+            pl.set_pairs(pi, pj)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(warmup):
+                    flush.zero_()
+                    pl.closest(stream=stream)
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    pl.closest(stream=stream)
+                    b.record(stream)
+            stream.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            it = pl.iters[:m].cpu().numpy().astype(np.float64)
+            res[form] = {"pairs_per_s": m / (ms * 1e-3), "ms": ms, "newton_iters_mean": float(it.mean()),
+                         "warp_max_iters_mean": float(it[:m - m % 32].reshape(-1, 32).max(1).mean()),
+                         "h": pl.gap[:m].cpu().numpy(), "status": pl.status[:m].cpu().numpy()}
+            del pl
+        h0, h1 = res["plain"].pop("h"), res["learned"].pop("h")
+        s0, s1 = res["plain"].pop("status"), res["learned"].pop("status")
+        scale = np.array([max(parts["r_par"][a], parts["r_perp"][a]) + max(parts["r_par"][b], parts["r_perp"][b])
+                          for a, b in zip(pi[:4096], pj[:4096])]).max()
+        res["max_abs_gap_difference"] = float(np.abs(h1 - h0).max())
+        res["gap_scale"] = float(scale)
+        res["status_equal_fraction"] = float(np.mean((s0 & 7) == (s1 & 7)))
+        res["speedup"] = res["learned"]["pairs_per_s"] / res["plain"]["pairs_per_s"]
+        out[prec] = res
+    return out
 
 
 def kernels_in_step(precision):

@@ -63,6 +63,8 @@ extern "C" {
 /* lub_params.warm_start */
 #define LUB_WARM_NONE     0 /* Newton starts from the line of centres (Sec. III A) */
 #define LUB_WARM_PREVIOUS 1 /* Newton starts from the normal passed in n (in/out) */
+#define LUB_WARM_MLP      2 /* Newton starts from the learned network's prediction
+                               (lub_mlp_set must have installed a network) */
 
 /* per-pair status bits */
 #define LUB_ST_OVERLAP    1  /* h <= 0 */
@@ -108,7 +110,7 @@ typedef struct {
     int32_t max_newton;   /* Newton iteration cap per precision stage (1..64)          */
     double newton_tol;    /* step-size tolerance (radians) of the FP32 stage; the FP64
                              stage converges to rounding                                */
-    int32_t warm_start;   /* LUB_WARM_NONE or LUB_WARM_PREVIOUS                        */
+    int32_t warm_start;   /* LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP          */
 } lub_params;
 
 /* Fill *p with the paper's values: mu = 1/6, Delta_n = 2/3, Delta_t = 1/2,
@@ -207,6 +209,61 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
               int32_t capacity, const void *FT, const void *lever, int32_t n, void *force,
               void *torque, int32_t precision, int32_t accumulate, int32_t deterministic,
               void *stream);
+
+/*
+ * Learned warm start of lub_closest_points (no counterpart in the paper: the
+ * paper warm-starts from the previous time step, Sec. III A).  A network
+ * 12 -> 128 -> 128 -> 4 with GELU activations maps a pair's relative pose to
+ * the surface parameters (p_i, q_i, p_j, q_j) of Eq. lub:spheroid at its
+ * closest points, as corrections to the parameters of the line-of-centres
+ * start; the outward normals at the predicted points give Newton's start.
+ *
+ * Features (12 per pair): d = r_j - r_i (minimum image) in i's body frame over
+ * R_perp,i (3); the relative rotation q_i^-1 q_j of the normalised
+ * quaternions with w >= 0 (4); ln R_par,i, ln R_perp,i, ln R_par,j,
+ * ln R_perp,j (4); asinh(g/a) with g = |d| - sigma_i(d^) - sigma_j(d^) and a
+ * the smallest semi-axis (1); standardised as (f - mean) * istd.
+ * Parameters: LUB_MLP_PARAMS floats [W1 | b1 | W2 | b2 | W3 | b3], W row-major
+ * [out][in] (W1 128x12, W2 128x128, W3 4x128).
+ */
+#define LUB_MLP_PARAMS 18692
+#define LUB_MLP_WORK_PER_SAMPLE 776
+
+/* Install a network in the context (BF16 copy of params for the tensor
+ * cores; mean, istd: device [12]).  params, mean, istd: device float.  The
+ * first call allocates the context's copy. */
+int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const float *istd, void *stream);
+
+/* The network's outputs for every pair on the tensor cores (BF16 weights and
+ * activations, FP32 accumulate): pq [4][capacity] float, the predicted
+ * corrections to (p_i, q_i, p_j, q_j) of the line-of-centres start;
+ * pairs with a wall, bad indices or non-finite features get zeros. */
+int lub_mlp_predict(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const int32_t *pair_i,
+                    const int32_t *pair_j, const int32_t *d_count, int32_t capacity, float *pq, void *stream);
+
+/* Features of n pairs into feat [n][12] (device float); mean and istd (device
+ * [12]) standardise them, or both NULL for the raw features. */
+int lub_mlp_features(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const int32_t *pair_i,
+                     const int32_t *pair_j, int32_t n, const float *mean, const float *istd, float *feat,
+                     void *stream);
+
+/* Training step, forward and backward in FP32 on a batch of nb samples:
+ * x [nb][12] standardised features, target [nb][4]: the corrections to the
+ * surface parameters of the line-of-centres start, (p_i - p0_i,
+ * wrap(q_i - q0_i), p_j - p0_j, wrap(q_j - q0_j)) with (p0, q0) those of the
+ * support points of i along d^ and of j along -d^ (a zero output gives Newton
+ * the line-of-centres start); weight [nb][4] or NULL (all 1).
+ * loss = mean over the batch of 1/2 sum_o weight_o r_o^2, the azimuth errors
+ * r_1, r_3 wrapped to (-pi, pi].  Writes grads [LUB_MLP_PARAMS] (d loss /
+ * d params) and loss_rows [nb] (each sample's loss); work: nb *
+ * LUB_MLP_WORK_PER_SAMPLE floats of scratch.  All device memory. */
+int lub_mlp_forward_backward(lub_ctx *ctx, const float *params, const float *x, const float *target,
+                             const float *weight, int32_t nb, float *grads, float *work, float *loss_rows,
+                             void *stream);
+
+/* Adam update of n parameters (step t >= 1) with moments m, v (device). */
+int lub_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, float *v, int32_t n, int32_t t, float lr,
+                 float beta1, float beta2, float eps, void *stream);
 
 /*
  * The pair build of lub_pairs_build, for callers that cannot allocate device

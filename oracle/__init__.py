@@ -84,6 +84,16 @@ def _load():
         lib.orc_surface_geometry.argtypes = [P(_Particles), ctypes.c_int64, dp, dp, dp]
         lib.orc_g.restype = ctypes.c_double
         lib.orc_g.argtypes = [P(_Particles), P(_Domain), ctypes.c_int32, ctypes.c_int32, dp]
+        lib.orc_surface_pq.restype = None
+        lib.orc_surface_pq.argtypes = [P(_Particles), ctypes.c_int64, dp, dp]
+        lib.orc_mlp_features.restype = None
+        lib.orc_mlp_features.argtypes = [P(_Particles), P(_Domain), ctypes.c_int64, ip, ip, dp]
+        lib.orc_pq_labels.restype = None
+        lib.orc_pq_labels.argtypes = [P(_Particles), ctypes.c_int64, ip, ip, dp, dp, dp]
+        lib.orc_mlp_loss_grad.restype = ctypes.c_double
+        lib.orc_mlp_loss_grad.argtypes = [ctypes.c_int64] + [dp] * 16
+        lib.orc_mlp_baseline.restype = None
+        lib.orc_mlp_baseline.argtypes = [P(_Particles), P(_Domain), ctypes.c_int64, ip, ip, dp]
         _lib = lib
     return _lib
 
@@ -252,3 +262,93 @@ def step(parts, dom, prm=None):
     f, t = apply(P.n, pi, pj, pf["FT"], pf["lever"])
     return dict(pi=pi, pj=pj, force=f, torque=t, **cp, FT=pf["FT"], lever=pf["lever"],
                 pair_status=pf["status"])
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: labels, features and the FP64 network
+# ---------------------------------------------------------------------------
+MLP_SHAPES = dict(W1=(128, 12), b1=(128,), W2=(128, 128), b2=(128,), W3=(4, 128), b3=(4,))
+
+
+def surface_pq(parts, k, y):
+    """(p, q) of Eq. lub:spheroid of surface point y of particle k."""
+    lib = _load()
+    P = _as_particles(parts)
+    out = np.zeros(2)
+    lib.orc_surface_pq(ctypes.byref(P.c), int(k), _dp(np.ascontiguousarray(y, np.float64)), _dp(out))
+    return out
+
+
+def pq_labels(parts, dom, pi, pj, cp=None):
+    """Targets (p_i, q_i, p_j, q_j) of the closest points [m, 4]."""
+    P = _as_particles(parts)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    if cp is None:
+        cp = closest(P, dom, pi, pj)
+    out = np.zeros((len(pi), 4))
+    if len(pi):
+        _load().orc_pq_labels(ctypes.byref(P.c), len(pi), _ip(pi), _ip(pj),
+                              _dp(np.ascontiguousarray(cp["yi"], np.float64)),
+                              _dp(np.ascontiguousarray(cp["yj"], np.float64)), _dp(out))
+    return out
+
+
+def mlp_features(parts, dom, pi, pj):
+    """The 12 input features of each pair [m, 12] (before standardisation)."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    f = np.zeros((len(pi), 12))
+    if len(pi):
+        lib.orc_mlp_features(ctypes.byref(P.c), ctypes.byref(D), len(pi), _ip(pi), _ip(pj), _dp(f))
+    return f
+
+
+def mlp_baseline(parts, dom, pi, pj):
+    """(p, q) of the line-of-centres start on both particles [m, 4]."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    out = np.zeros((len(pi), 4))
+    if len(pi):
+        lib.orc_mlp_baseline(ctypes.byref(P.c), ctypes.byref(D), len(pi), _ip(pi), _ip(pj), _dp(out))
+    return out
+
+
+def wrap_pi(a):
+    return a - 2 * np.pi * np.floor(a / (2 * np.pi) + 0.5)
+
+
+def mlp_targets(labels, baseline):
+    """Corrections the network learns (azimuths wrapped) and the loss weights
+    (1, cos^2 p_i, 1, cos^2 p_j): the arc length on the parameter sphere,
+    ds^2 = dp^2 + cos^2 p dq^2, so the azimuth counts little near the poles
+    where it is undefined."""
+    t = labels - baseline
+    t[:, 1] = wrap_pi(t[:, 1])
+    t[:, 3] = wrap_pi(t[:, 3])
+    w = np.ones_like(t)
+    w[:, 1] = np.cos(labels[:, 0]) ** 2
+    w[:, 3] = np.cos(labels[:, 2]) ** 2
+    return t, w
+
+
+def mlp_loss_grad(x, tgt, w, want_grad=True, wgt=None):
+    """Loss, gradients (dict like w) and outputs of the network on standardised x."""
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    tgt = np.ascontiguousarray(tgt, np.float64)
+    ww = {k: np.ascontiguousarray(w[k], np.float64) for k in MLP_SHAPES}
+    g = {k: np.zeros(sh) for k, sh in MLP_SHAPES.items()}
+    out = np.zeros((len(x), 4))
+    args = [_dp(ww[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    gargs = [_dp(g[k]) if want_grad else None for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    wg = None if wgt is None else np.ascontiguousarray(wgt, np.float64)
+    loss = lib.orc_mlp_loss_grad(len(x), _dp(x), _dp(tgt), _dp(wg) if wg is not None else None, *args, *gargs,
+                                 _dp(out))
+    return loss, (g if want_grad else None), out

@@ -883,3 +883,202 @@ double orc_g(const orc_particles *P, const orc_domain *D, int32_t i, int32_t j, 
     for (int k = 0; k < 3; ++k) sj.r[k] = si.r[k] + d[k];
     return g_eval(&si, &sj, d, n, NULL, NULL);
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned warm start: the oracle's plain FP64 copy of the network used  */
+/* to check the GPU's training kernels (features, forward, backward).    */
+/* ------------------------------------------------------------------ */
+
+/* Surface parameters (p, q) of Eq. lub:spheroid of the point y on particle k:
+ * y~ = Q^T (y - r); sin p = y~_3 / R_par, cos p = |y~_12| / R_perp, q = atan2. */
+void orc_surface_pq(const orc_particles *P, int64_t k, const double y[3], double pq[2])
+{
+    shape_t s;
+    load_shape(P, k, &s);
+    double rel[3] = {y[0] - s.r[0], y[1] - s.r[1], y[2] - s.r[2]};
+    double yb[3];
+    to_body(&s, rel, yb);
+    pq[0] = atan2(yb[2] / s.Rpar, sqrt(yb[0] * yb[0] + yb[1] * yb[1]) / s.Rperp);
+    pq[1] = atan2(yb[1], yb[0]);
+}
+
+/* The 12 input features of a pair (i, j):
+ *   [0..2]  d = r_j - r_i (minimum image) in i's body frame, over R_perp,i
+ *   [3..6]  relative rotation q_i^-1 q_j of the normalised quaternions, w >= 0
+ *   [7..10] ln R_par,i, ln R_perp,i, ln R_par,j, ln R_perp,j
+ *   [11]    asinh(g(d^)/a): the support-function gap estimate along the line
+ *           of centres, g = |d| - sigma_i(d^) - sigma_j(d^), over the smallest
+ *           semi-axis a of the pair. */
+void orc_mlp_features(const orc_particles *P, const orc_domain *D, int64_t np, const int32_t *pi,
+                      const int32_t *pj, double *feat)
+{
+    for (int64_t k = 0; k < np; ++k) {
+        int32_t i = pi[k], j = pj[k];
+        shape_t si, sj;
+        load_shape(P, i, &si);
+        load_shape(P, j, &sj);
+        double d[3];
+        min_image(D, si.r, sj.r, d);
+        double db[3];
+        to_body(&si, d, db);
+        double *f = feat + 12 * k;
+        for (int a = 0; a < 3; ++a) f[a] = db[a] / si.Rperp;
+        double qa[4] = {P->qw[i], P->qx[i], P->qy[i], P->qz[i]};
+        double qb[4] = {P->qw[j], P->qx[j], P->qy[j], P->qz[j]};
+        double na = sqrt(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
+        double nb = sqrt(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+        for (int a = 0; a < 4; ++a) {
+            qa[a] /= na;
+            qb[a] /= nb;
+        }
+        /* conj(qa) * qb (Hamilton product) */
+        double w = qa[0] * qb[0] + qa[1] * qb[1] + qa[2] * qb[2] + qa[3] * qb[3];
+        double x = qa[0] * qb[1] - qa[1] * qb[0] - qa[2] * qb[3] + qa[3] * qb[2];
+        double y = qa[0] * qb[2] + qa[1] * qb[3] - qa[2] * qb[0] - qa[3] * qb[1];
+        double z = qa[0] * qb[3] - qa[1] * qb[2] + qa[2] * qb[1] - qa[3] * qb[0];
+        double sg = w < 0.0 ? -1.0 : 1.0;
+        f[3] = sg * w;
+        f[4] = sg * x;
+        f[5] = sg * y;
+        f[6] = sg * z;
+        f[7] = log(si.Rpar);
+        f[8] = log(si.Rperp);
+        f[9] = log(sj.Rpar);
+        f[10] = log(sj.Rperp);
+        double dl = norm3(d);
+        double e[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
+        double g = dl - support(&si, e) - support(&sj, e);
+        double a = si.Rpar;
+        if (si.Rperp < a) a = si.Rperp;
+        if (sj.Rpar < a) a = sj.Rpar;
+        if (sj.Rperp < a) a = sj.Rperp;
+        f[11] = asinh(g / a);
+    }
+}
+
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+
+static double gelu_d(double x)
+{
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * ORC_PI);
+}
+
+/* wrap an angle difference to (-pi, pi] */
+static double wrap_pi(double x) { return x - 2.0 * ORC_PI * floor(x / (2.0 * ORC_PI) + 0.5); }
+
+/* The network 12 -> 128 -> 128 -> 4 with GELU: h1 = gelu(W1 x + b1),
+ * h2 = gelu(W2 h1 + b2), y = W3 h2 + b3 (row-major W[out][in]).  x are the
+ * standardised features.  Loss: the mean over the batch of
+ *   1/2 sum_o w_o r_o^2,  r = (y0 - t0, wrap(y1 - t1), y2 - t2, wrap(y3 - t3)),
+ * with per-sample weights w (all 1 if wgt is NULL).
+ * Returns the loss; writes the gradients (if gW1 != NULL) and outputs (if out
+ * != NULL).  nb = batch size. */
+double orc_mlp_loss_grad(int64_t nb, const double *x, const double *tgt, const double *wgt, const double *W1,
+                         const double *b1,
+                         const double *W2, const double *b2, const double *W3, const double *b3, double *gW1,
+                         double *gb1, double *gW2, double *gb2, double *gW3, double *gb3, double *out)
+{
+    enum { NI = 12, NH = 128, NO = 4 };
+    if (gW1) {
+        memset(gW1, 0, sizeof(double) * NH * NI);
+        memset(gb1, 0, sizeof(double) * NH);
+        memset(gW2, 0, sizeof(double) * NH * NH);
+        memset(gb2, 0, sizeof(double) * NH);
+        memset(gW3, 0, sizeof(double) * NO * NH);
+        memset(gb3, 0, sizeof(double) * NO);
+    }
+    double loss = 0.0;
+    for (int64_t s = 0; s < nb; ++s) {
+        const double *xs = x + NI * s;
+        double z1[NH], h1[NH], z2[NH], h2[NH], y[NO];
+        for (int o = 0; o < NH; ++o) {
+            double a = b1[o];
+            for (int k = 0; k < NI; ++k) a += W1[o * NI + k] * xs[k];
+            z1[o] = a;
+            h1[o] = gelu(a);
+        }
+        for (int o = 0; o < NH; ++o) {
+            double a = b2[o];
+            for (int k = 0; k < NH; ++k) a += W2[o * NH + k] * h1[k];
+            z2[o] = a;
+            h2[o] = gelu(a);
+        }
+        for (int o = 0; o < NO; ++o) {
+            double a = b3[o];
+            for (int k = 0; k < NH; ++k) a += W3[o * NH + k] * h2[k];
+            y[o] = a;
+        }
+        if (out)
+            for (int o = 0; o < NO; ++o) out[NO * s + o] = y[o];
+        const double *t = tgt + NO * s;
+        double r[NO] = {y[0] - t[0], wrap_pi(y[1] - t[1]), y[2] - t[2], wrap_pi(y[3] - t[3])};
+        double w[NO] = {1.0, 1.0, 1.0, 1.0};
+        if (wgt)
+            for (int o = 0; o < NO; ++o) w[o] = wgt[NO * s + o];
+        for (int o = 0; o < NO; ++o) loss += 0.5 * w[o] * r[o] * r[o];
+        if (!gW1) continue;
+        /* backward (d loss / d y = w r / nb) */
+        double dy[NO], dh2[NH], dz2[NH], dh1[NH], dz1[NH];
+        for (int o = 0; o < NO; ++o) dy[o] = w[o] * r[o] / (double)nb;
+        for (int o = 0; o < NO; ++o) {
+            gb3[o] += dy[o];
+            for (int k = 0; k < NH; ++k) gW3[o * NH + k] += dy[o] * h2[k];
+        }
+        for (int k = 0; k < NH; ++k) {
+            double a = 0.0;
+            for (int o = 0; o < NO; ++o) a += W3[o * NH + k] * dy[o];
+            dh2[k] = a;
+            dz2[k] = a * gelu_d(z2[k]);
+        }
+        for (int o = 0; o < NH; ++o) {
+            gb2[o] += dz2[o];
+            for (int k = 0; k < NH; ++k) gW2[o * NH + k] += dz2[o] * h1[k];
+        }
+        for (int k = 0; k < NH; ++k) {
+            double a = 0.0;
+            for (int o = 0; o < NH; ++o) a += W2[o * NH + k] * dz2[o];
+            dh1[k] = a;
+            dz1[k] = a * gelu_d(z1[k]);
+        }
+        for (int o = 0; o < NH; ++o) {
+            gb1[o] += dz1[o];
+            for (int k = 0; k < NI; ++k) gW1[o * NI + k] += dz1[o] * xs[k];
+        }
+    }
+    return loss / (double)nb;
+}
+
+/* (p_i, q_i, p_j, q_j) of np pairs from their closest points (labels of the
+ * learned warm start); out [np][4] */
+void orc_pq_labels(const orc_particles *P, int64_t np, const int32_t *pi, const int32_t *pj, const double *yi,
+                   const double *yj, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < np; ++k) {
+        orc_surface_pq(P, pi[k], yi + 3 * k, out + 4 * k);
+        orc_surface_pq(P, pj[k], yj + 3 * k, out + 4 * k + 2);
+    }
+}
+
+/* Surface parameters (p, q) of the line-of-centres start: the support point
+ * of i along d^ and of j along -d^ (d = r_j - r_i); out [np][4].  The network
+ * learns the closest points' parameters as corrections to these; a zero
+ * correction gives back the start n = d^ exactly. */
+void orc_mlp_baseline(const orc_particles *P, const orc_domain *D, int64_t np, const int32_t *pi, const int32_t *pj,
+                      double *out)
+{
+    for (int64_t k = 0; k < np; ++k) {
+        shape_t si, sj;
+        load_shape(P, pi[k], &si);
+        load_shape(P, pj[k], &sj);
+        double d[3];
+        min_image(D, si.r, sj.r, d);
+        double l = norm3(d);
+        double e[3] = {d[0] / l, d[1] / l, d[2] / l}, me[3] = {-e[0], -e[1], -e[2]};
+        double y[3];
+        support_point(&si, e, y);
+        orc_surface_pq(P, pi[k], y, out + 4 * k);
+        support_point(&sj, me, y);
+        orc_surface_pq(P, pj[k], y, out + 4 * k + 2);
+    }
+}

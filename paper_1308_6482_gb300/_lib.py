@@ -19,6 +19,9 @@ LUB_FP64 = 0
 LUB_MIXED = 1
 LUB_WARM_NONE = 0
 LUB_WARM_PREVIOUS = 1
+LUB_WARM_MLP = 2
+LUB_MLP_PARAMS = 18692
+LUB_MLP_WORK_PER_SAMPLE = 776
 LUB_ST_OVERLAP = 1
 LUB_ST_NOCONV = 2
 LUB_ST_DEGENERATE = 4
@@ -52,7 +55,8 @@ class lub_params(ctypes.Structure):
 
 # every exported symbol of include/lub.h
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
-           "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static")
+           "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
+           "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam")
 
 _lib = None
 
@@ -91,6 +95,17 @@ def load_library():
                                    vp, vp, vp, vp]
     lib.lub_apply.restype = ctypes.c_int
     lib.lub_apply.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, i32, i32, i32, vp]
+    f32 = ctypes.c_float
+    lib.lub_mlp_set.restype = ctypes.c_int
+    lib.lub_mlp_set.argtypes = [vp, vp, vp, vp, vp]
+    lib.lub_mlp_predict.restype = ctypes.c_int
+    lib.lub_mlp_predict.argtypes = [vp, P(lub_particles), P(lub_domain), vp, vp, vp, i32, vp, vp]
+    lib.lub_mlp_features.restype = ctypes.c_int
+    lib.lub_mlp_features.argtypes = [vp, P(lub_particles), P(lub_domain), vp, vp, i32, vp, vp, vp, vp]
+    lib.lub_mlp_forward_backward.restype = ctypes.c_int
+    lib.lub_mlp_forward_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.lub_mlp_adam.restype = ctypes.c_int
+    lib.lub_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp]
     lib.lub_pairs_build_static.restype = ctypes.c_int
     lib.lub_pairs_build_static.argtypes = [P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp]
     _lib = lib
@@ -169,6 +184,35 @@ def lub_pairs_build_static(particles, domain, params, pair_i, pair_j, capacity, 
                                                  _ptr(d_count), _stream(stream))
 
 
+def lub_mlp_set(ctx, params, mean, istd, stream=None):
+    return _check(ctx, load_library().lub_mlp_set(ctx, _ptr(params), _ptr(mean), _ptr(istd), _stream(stream)))
+
+
+def lub_mlp_predict(ctx, particles, domain, pair_i, pair_j, d_count, capacity, pq, stream=None):
+    return _check(ctx, load_library().lub_mlp_predict(ctx, ctypes.byref(particles), ctypes.byref(domain),
+                                                      _ptr(pair_i), _ptr(pair_j), _ptr(d_count), int(capacity),
+                                                      _ptr(pq), _stream(stream)))
+
+
+def lub_mlp_features(ctx, particles, domain, pair_i, pair_j, n, mean, istd, feat, stream=None):
+    return _check(ctx, load_library().lub_mlp_features(ctx, ctypes.byref(particles), ctypes.byref(domain),
+                                                       _ptr(pair_i), _ptr(pair_j), int(n), _ptr(mean), _ptr(istd),
+                                                       _ptr(feat), _stream(stream)))
+
+
+def lub_mlp_forward_backward(ctx, params, x, target, weight, nb, grads, work, loss_rows, stream=None):
+    return _check(ctx, load_library().lub_mlp_forward_backward(ctx, _ptr(params), _ptr(x), _ptr(target),
+                                                               _ptr(weight), int(nb),
+                                                               _ptr(grads), _ptr(work), _ptr(loss_rows),
+                                                               _stream(stream)))
+
+
+def lub_mlp_adam(ctx, params, grads, m, v, n, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return _check(ctx, load_library().lub_mlp_adam(ctx, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(n), int(t),
+                                                   float(lr), float(beta1), float(beta2), float(eps),
+                                                   _stream(stream)))
+
+
 def lub_closest_points(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status,
                        iters=None, stream=None):
     return _check(ctx, load_library().lub_closest_points(
@@ -198,6 +242,8 @@ def default_params(**kw):
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": LUB_FP64, "mixed": LUB_MIXED}[v]
+        if k == "warm_start" and isinstance(v, str):
+            v = {"none": LUB_WARM_NONE, "previous": LUB_WARM_PREVIOUS, "mlp": LUB_WARM_MLP}[v]
         setattr(p, k, v)
     return p
 

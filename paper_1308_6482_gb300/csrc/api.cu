@@ -8,6 +8,7 @@
 #include <new>
 
 #include "lub_internal.cuh"
+#include "lub_mlp.cuh"
 
 int lub_set_error(lub_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -91,8 +92,8 @@ int check_params(lub_ctx *ctx, const lub_params *p)
         return lub_set_error(ctx, LUB_ERR_ARG, "list_cutoff must be finite and >= 0");
     if (p->max_newton < 1 || p->max_newton > 64) return lub_set_error(ctx, LUB_ERR_ARG, "max_newton must be 1..64");
     if (!(p->newton_tol > 0.0)) return lub_set_error(ctx, LUB_ERR_ARG, "newton_tol must be > 0");
-    if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS)
-        return lub_set_error(ctx, LUB_ERR_ARG, "warm_start must be LUB_WARM_NONE or LUB_WARM_PREVIOUS");
+    if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS && p->warm_start != LUB_WARM_MLP)
+        return lub_set_error(ctx, LUB_ERR_ARG, "warm_start must be LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP");
     return LUB_OK;
 }
 
@@ -148,6 +149,8 @@ int lub_ctx_destroy(lub_ctx *ctx)
     if (!ctx) return LUB_ERR_ARG;
     cudaDeviceSynchronize();
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->mlp_mem) cudaFree(ctx->mlp_mem);
+    delete (MlpDevice *)ctx->mlp;
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     delete ctx;
     return LUB_OK;
@@ -248,6 +251,100 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
     if (capacity > 0 && (!FT || !lever)) return lub_set_error(ctx, LUB_ERR_ARG, "FT or lever is NULL");
     return launch_apply(ctx, pair_i, pair_j, d_count, capacity, FT, lever, n, force, torque, precision, accumulate,
                         deterministic, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// learned warm start
+// ---------------------------------------------------------------------------
+int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const float *istd, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    if (!params || !mean || !istd) return lub_set_error(ctx, LUB_ERR_ARG, "params, mean or istd is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->mlp) {
+        const size_t bw = (size_t)(128 * 16 + 128 * 128 + 8 * 128) * sizeof(__nv_bfloat16);
+        const size_t bf = (size_t)(128 + 128 + 8 + 12 + 12) * sizeof(float);
+        void *mem = nullptr;
+        cudaError_t e = cudaMalloc(&mem, bw + bf + 256);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return lub_set_error(ctx, LUB_ERR_NOMEM, "cudaMalloc of the network failed");
+        }
+        MlpDevice *M = new (std::nothrow) MlpDevice();
+        if (!M) {
+            cudaFree(mem);
+            return LUB_ERR_NOMEM;
+        }
+        char *c = (char *)mem;
+        M->W1 = (__nv_bfloat16 *)c;
+        M->W2 = M->W1 + 128 * 16;
+        M->W3 = M->W2 + 128 * 128;
+        float *f = (float *)(c + ((bw + 255) & ~(size_t)255));
+        M->b1 = f;
+        M->b2 = f + 128;
+        M->b3 = f + 256;
+        M->mean = f + 264;
+        M->istd = f + 276;
+        ctx->mlp = M;
+        ctx->mlp_mem = mem;
+    }
+    MlpDevice &M = *(MlpDevice *)ctx->mlp;
+    int rc = launch_mlp_pack(ctx, params, M, st);
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(M.mean, mean, 12 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                                 "copy mean");
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(M.istd, istd, 12 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                                 "copy istd");
+    if (!rc) ctx->mlp_ready = true;
+    return rc;
+}
+
+int lub_mlp_predict(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const int32_t *pair_i,
+                    const int32_t *pair_j, const int32_t *d_count, int32_t capacity, float *pq, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) ||
+        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
+        return rc;
+    if (capacity > 0 && !pq) return lub_set_error(ctx, LUB_ERR_ARG, "pq is NULL");
+    return launch_mlp_start(ctx, make_pview(p), make_dview(dom), pair_i, pair_j, d_count, capacity, nullptr, pq,
+                            (cudaStream_t)stream);
+}
+
+int lub_mlp_features(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const int32_t *pair_i,
+                     const int32_t *pair_j, int32_t n, const float *mean, const float *istd, float *feat, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom))) return rc;
+    if (n < 0 || (n > 0 && (!pair_i || !pair_j || !feat))) return lub_set_error(ctx, LUB_ERR_ARG, "bad pair arrays");
+    if ((mean == nullptr) != (istd == nullptr)) return lub_set_error(ctx, LUB_ERR_ARG, "give both mean and istd or neither");
+    return launch_mlp_features(ctx, make_pview(p), make_dview(dom), pair_i, pair_j, n, mean, istd, feat,
+                               (cudaStream_t)stream);
+}
+
+int lub_mlp_forward_backward(lub_ctx *ctx, const float *params, const float *x, const float *target,
+                             const float *weight, int32_t nb, float *grads, float *work, float *loss_rows,
+                             void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    if (nb <= 0 || !params || !x || !target || !grads || !work || !loss_rows)
+        return lub_set_error(ctx, LUB_ERR_ARG, "bad arguments to lub_mlp_forward_backward");
+    return launch_mlp_forward_backward(ctx, params, x, target, weight, nb, grads, work, loss_rows,
+                                       (cudaStream_t)stream);
+}
+
+int lub_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, float *v, int32_t n, int32_t t, float lr,
+                 float beta1, float beta2, float eps, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    if (n <= 0 || t < 1 || !params || !grads || !m || !v) return lub_set_error(ctx, LUB_ERR_ARG, "bad arguments to lub_mlp_adam");
+    return launch_mlp_adam(ctx, params, grads, m, v, n, t, lr, beta1, beta2, eps, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -27,6 +27,7 @@
 // LUB_FP64: the whole solve and gap in double.
 #include "ff.cuh"
 #include "lub_internal.cuh"
+#include "lub_mlp.cuh"
 
 namespace {
 
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, DView D, const i
                     if (warm) {
                         const V3<float> w0 = mk<float>((float)nout[k], (float)nout[C + k], (float)nout[2 * C + k]);
                         const float wl2 = dot(w0, w0);
-                        if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2)) n = scl(rsqrtf(wl2), w0);
+                        // a start on the far hemisphere falls back to the line of centres
+                        if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2) && dot(w0, df) > 0.f) n = scl(rsqrtf(wl2), w0);
                     }
                     const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
                     const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
@@ -337,7 +339,8 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, DView D, const in
                     if (warm) {
                         const V3<double> w0 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
                         const double wl2 = dot(w0, w0);
-                        if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2)) nn = scl(rsqrt(wl2), w0);
+                        // a start on the far hemisphere falls back to the line of centres
+                        if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2) && dot(w0, d) > 0.0) nn = w0;
                     }
                     const double scale = dl + (double)fmaxf(rpi, rqi) + (double)fmaxf(rpj, rqj);
                     const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
@@ -367,7 +370,13 @@ int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_param
     if (cap == 0) return LUB_OK;
     const int block = 128;
     const int grid = grid_for(cap, block, ctx->num_sms, 8);
-    const int warm = prm.warm_start == LUB_WARM_PREVIOUS;
+    int warm = prm.warm_start == LUB_WARM_PREVIOUS;
+    if (prm.warm_start == LUB_WARM_MLP) {
+        // the network's start normal for every pair, then Newton from it
+        int rc = launch_mlp_start(ctx, P, D, pi, pj, d_count, cap, n, nullptr, st);
+        if (rc) return rc;
+        warm = 1;
+    }
     if (prm.precision == LUB_MIXED) {
         // work list: count + up to cap entries in the context scratch
         int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);

@@ -19,6 +19,10 @@ struct lub_ctx {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int32_t *d_flags = nullptr;  // [0]: overflow / error flags of the last call
+    void *mlp = nullptr;         // MlpDevice of the learned warm start (lub_mlp_set)
+    void *mlp_mem = nullptr;     // its device storage
+    bool mlp_ready = false;
+    bool mlp_smem_set = false;
 };
 
 int lub_set_error(lub_ctx *ctx, int code, const char *fmt, ...);

@@ -1,0 +1,32 @@
+// Internal declarations of the learned warm start (mlp.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "lub_internal.cuh"
+
+// BF16 inference weights and FP32 biases / feature standardisation, owned by a context
+struct MlpDevice {
+    __nv_bfloat16 *W1;  // [128][16]  (inputs padded 12 -> 16)
+    __nv_bfloat16 *W2;  // [128][128]
+    __nv_bfloat16 *W3;  // [8][128]   (outputs padded 4 -> 8)
+    float *b1, *b2, *b3;
+    float *mean, *istd;  // [12] each
+};
+
+static_assert(LUB_MLP_PARAMS == 128 * 12 + 128 + 128 * 128 + 128 + 4 * 128 + 4, "parameter count");
+static_assert(LUB_MLP_WORK_PER_SAMPLE == 6 * 128 + 2 * 4, "training scratch per sample");
+
+__global__ void k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                            const int32_t *__restrict__ d_count, int32_t cap, MlpDevice M, double *__restrict__ n0,
+                            float *__restrict__ pq);
+int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj,
+                     const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st);
+size_t mlp_start_smem();
+int launch_mlp_features(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj, int n,
+                        const float *mean, const float *istd, float *feat, cudaStream_t st);
+int launch_mlp_forward_backward(lub_ctx *ctx, const float *params, const float *x, const float *tgt,
+                                const float *wgt, int M, float *grads, float *work, float *loss_rows, cudaStream_t st);
+int launch_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, float *v, int n, int t, float lr,
+                    float b1, float b2, float eps, cudaStream_t st);
+int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaStream_t st);

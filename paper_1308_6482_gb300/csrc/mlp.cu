@@ -1,0 +1,555 @@
+// Learned warm start of the closest-point solve: a 12 -> 128 -> 128 -> 4 MLP
+// (GELU) mapping a pair's relative pose to the surface parameters
+// (p_i, q_i, p_j, q_j) of Eq. lub:spheroid at its closest points.
+//
+//   features  12 per pair: d in i's body frame over R_perp,i; the relative
+//             rotation q_i^-1 q_j (w >= 0); ln of the four semi-axes; asinh of
+//             the support-function gap estimate along d over the smallest
+//             semi-axis; standardised with the training set's mean and 1/std.
+//   outputs   corrections to the surface parameters of the line-of-centres
+//             start (the support points of i along d^ and of j along -d^), so
+//             a zero output gives back the cold start n0 = d^ exactly and the
+//             network only learns a small, continuous correction;
+//   training  FP32 kernels: linear forward (optionally + GELU), a weighted
+//             squared error with the azimuth differences wrapped to (-pi, pi],
+//             backward through the layers, Adam.  Parameters packed [W1 | b1 | W2 | b2 | W3 | b3]
+//             with W row-major [out][in].
+//   inference BF16 weights on the tensor cores (mma.sync m16n8k16, FP32
+//             accumulate), one warp per 32 pairs, fused with the FP64 Newton
+//             solve of the closest points: the predicted (p, q) give the
+//             outward normals n_i, n_j at the predicted points and the start
+//             n0 = (n_i - n_j)/|n_i - n_j|.
+#include <cuda_bf16.h>
+
+#include "lub_internal.cuh"
+#include "lub_mlp.cuh"
+
+namespace {
+
+constexpr int NI = 12, NH = 128, NO = 4;
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_d_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.3989422804014327f;
+}
+
+__device__ __forceinline__ float wrap_pi_f(float x)
+{
+    const float tp = 6.283185307179586f;
+    return x - tp * floorf(x / tp + 0.5f);
+}
+
+// ---------------------------------------------------------------------------
+// features (the same device code for training and inference)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_features(const PView &P, const DView &D, int i, int j, const float *mean,
+                                              const float *istd, float f[NI])
+{
+    const V3<double> dd = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+    const V3<float> d = cvt<float>(dd);
+    float qa[4] = {P.qw[i], P.qx[i], P.qy[i], P.qz[i]};
+    float qb[4] = {P.qw[j], P.qx[j], P.qy[j], P.qz[j]};
+    const float na = rsqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
+    const float nb = rsqrtf(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+    for (int a = 0; a < 4; ++a) {
+        qa[a] *= na;
+        qb[a] *= nb;
+    }
+    // d in i's body frame: R(q_a)^T d
+    const float w = qa[0], x = qa[1], y = qa[2], z = qa[3];
+    const float R00 = 1 - 2 * (y * y + z * z), R01 = 2 * (x * y - w * z), R02 = 2 * (x * z + w * y);
+    const float R10 = 2 * (x * y + w * z), R11 = 1 - 2 * (x * x + z * z), R12 = 2 * (y * z - w * x);
+    const float R20 = 2 * (x * z - w * y), R21 = 2 * (y * z + w * x), R22 = 1 - 2 * (x * x + y * y);
+    const float rpi = P.rpar[i], rqi = P.rperp[i], rpj = P.rpar[j], rqj = P.rperp[j];
+    const float inv = 1.0f / rqi;
+    f[0] = (R00 * d.x + R10 * d.y + R20 * d.z) * inv;
+    f[1] = (R01 * d.x + R11 * d.y + R21 * d.z) * inv;
+    f[2] = (R02 * d.x + R12 * d.y + R22 * d.z) * inv;
+    // conj(qa) * qb
+    float rw = qa[0] * qb[0] + qa[1] * qb[1] + qa[2] * qb[2] + qa[3] * qb[3];
+    float rx = qa[0] * qb[1] - qa[1] * qb[0] - qa[2] * qb[3] + qa[3] * qb[2];
+    float ry = qa[0] * qb[2] + qa[1] * qb[3] - qa[2] * qb[0] - qa[3] * qb[1];
+    float rz = qa[0] * qb[3] - qa[1] * qb[2] + qa[2] * qb[1] - qa[3] * qb[0];
+    const float sg = rw < 0.f ? -1.f : 1.f;
+    f[3] = sg * rw;
+    f[4] = sg * rx;
+    f[5] = sg * ry;
+    f[6] = sg * rz;
+    f[7] = logf(rpi);
+    f[8] = logf(rqi);
+    f[9] = logf(rpj);
+    f[10] = logf(rqj);
+    const float dl = sqrtf(dot(d, d));
+    const V3<float> e = scl(1.0f / dl, d);
+    const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
+    const float g = dl - support(si, e) - support(sj, e);
+    const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
+    f[11] = asinhf(g / amin);
+    if (mean)
+        for (int a = 0; a < NI; ++a) f[a] = (f[a] - mean[a]) * istd[a];
+}
+
+__global__ void k_mlp_features(PView P, DView D, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                               int n, const float *__restrict__ mean, const float *__restrict__ istd,
+                               float *__restrict__ feat)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        float f[NI];
+        pair_features(P, D, pi[k], pj[k], mean, istd, f);
+        for (int a = 0; a < NI; ++a) feat[(size_t)k * NI + a] = f[a];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// training (FP32)
+// ---------------------------------------------------------------------------
+constexpr int TS = 32;  // tile edge of the small GEMMs
+
+// Y[m][n] = sum_k X[m][k] W[n][k] + b[n]; Z = Y; H = gelu(Y) if act
+__global__ void k_linear_fwd(const float *__restrict__ X, const float *__restrict__ W, const float *__restrict__ b,
+                             int M, int K, int N, float *__restrict__ Z, float *__restrict__ H, int act)
+{
+    __shared__ float xs[TS][TS + 1], ws[TS][TS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int m0 = blockIdx.y * TS, n0 = blockIdx.x * TS;
+    float acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < K; k0 += TS) {
+        for (int r = ty; r < TS; r += 8) {
+            const int m = m0 + r, k = k0 + tx, n = n0 + r;
+            xs[r][tx] = (m < M && k < K) ? X[(size_t)m * K + k] : 0.f;
+            ws[r][tx] = (n < N && k < K) ? W[(size_t)n * K + k] : 0.f;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < TS; ++kk) {
+            const float wv = ws[tx][kk];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += xs[ty + 8 * q][kk] * wv;
+        }
+        __syncthreads();
+    }
+    const int n = n0 + tx;
+    if (n >= N) return;
+    for (int q = 0; q < 4; ++q) {
+        const int m = m0 + ty + 8 * q;
+        if (m >= M) continue;
+        const float v = acc[q] + b[n];
+        Z[(size_t)m * N + n] = v;
+        if (act) H[(size_t)m * N + n] = gelu_f(v);
+    }
+}
+
+// dX[m][k] = sum_n dZ[m][n] W[n][k]   (optionally times gelu'(Zprev[m][k]))
+__global__ void k_linear_bwd_x(const float *__restrict__ dZ, const float *__restrict__ W, int M, int K, int N,
+                               const float *__restrict__ Zprev, float *__restrict__ dX)
+{
+    __shared__ float ds[TS][TS + 1], ws[TS][TS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m0 = blockIdx.y * TS, k0 = blockIdx.x * TS;
+    float acc[4] = {0, 0, 0, 0};
+    for (int n0 = 0; n0 < N; n0 += TS) {
+        for (int r = ty; r < TS; r += 8) {
+            const int m = m0 + r, n = n0 + tx;
+            ds[r][tx] = (m < M && n < N) ? dZ[(size_t)m * N + n] : 0.f;
+            const int nn = n0 + r, k = k0 + tx;
+            ws[r][tx] = (nn < N && k < K) ? W[(size_t)nn * K + k] : 0.f;
+        }
+        __syncthreads();
+        for (int nn = 0; nn < TS; ++nn) {
+            const float wv = ws[nn][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += ds[ty + 8 * q][nn] * wv;
+        }
+        __syncthreads();
+    }
+    const int k = k0 + tx;
+    if (k >= K) return;
+    for (int q = 0; q < 4; ++q) {
+        const int m = m0 + ty + 8 * q;
+        if (m >= M) continue;
+        float v = acc[q];
+        if (Zprev) v *= gelu_d_f(Zprev[(size_t)m * K + k]);
+        dX[(size_t)m * K + k] = v;
+    }
+}
+
+// dW[n][k] = sum_m dZ[m][n] X[m][k];  db[n] = sum_m dZ[m][n]
+__global__ void k_linear_bwd_w(const float *__restrict__ dZ, const float *__restrict__ X, int M, int K, int N,
+                               float *__restrict__ dW, float *__restrict__ db)
+{
+    __shared__ float ds[TS][TS + 1], xs[TS][TS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int n0 = blockIdx.y * TS, k0 = blockIdx.x * TS;
+    float acc[4] = {0, 0, 0, 0};
+    float bacc = 0.f;
+    for (int m0 = 0; m0 < M; m0 += TS) {
+        for (int r = ty; r < TS; r += 8) {
+            const int m = m0 + r;
+            ds[r][tx] = (m < M && n0 + tx < N) ? dZ[(size_t)m * N + n0 + tx] : 0.f;
+            xs[r][tx] = (m < M && k0 + tx < K) ? X[(size_t)m * K + k0 + tx] : 0.f;
+        }
+        __syncthreads();
+        for (int mm = 0; mm < TS; ++mm) {
+            const float xv = xs[mm][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += ds[mm][ty + 8 * q] * xv;
+        }
+        if (blockIdx.x == 0 && ty == 0)
+            for (int mm = 0; mm < TS; ++mm) bacc += ds[mm][tx];
+        __syncthreads();
+    }
+    const int k = k0 + tx;
+    for (int q = 0; q < 4; ++q) {
+        const int n = n0 + ty + 8 * q;
+        if (n < N && k < K) dW[(size_t)n * K + k] = acc[q];
+    }
+    if (blockIdx.x == 0 && ty == 0 && n0 + tx < N) db[n0 + tx] = bacc;
+}
+
+// weighted loss terms and dY = w r / M (azimuth errors wrapped); per-row losses to lrow
+__global__ void k_mlp_loss(const float *__restrict__ Y, const float *__restrict__ T, const float *__restrict__ Wt,
+                           int M, float *__restrict__ dY, float *__restrict__ lrow)
+{
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        float l = 0.f;
+        for (int o = 0; o < NO; ++o) {
+            float r = Y[(size_t)m * NO + o] - T[(size_t)m * NO + o];
+            if (o & 1) r = wrap_pi_f(r);
+            const float wgt = Wt ? Wt[(size_t)m * NO + o] : 1.f;
+            l += 0.5f * wgt * r * r;
+            dY[(size_t)m * NO + o] = wgt * r / (float)M;
+        }
+        lrow[m] = l;
+    }
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float gk = g[k];
+        const float mk = b1 * m[k] + (1.f - b1) * gk;
+        const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inference: BF16 tensor cores, fused with the FP64 Newton solve
+// ---------------------------------------------------------------------------
+constexpr int INF_WARPS = 4;
+constexpr int K1P = 16;  // layer-1 inner dimension padded 12 -> 16
+constexpr int N3P = 8;   // layer-3 outputs padded 4 -> 8
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// A fragment (16 x 16 tile at rows m0, cols k0) from a row-major bf16 matrix with row stride ld
+__device__ __forceinline__ void load_a(const __nv_bfloat16 *A, int ld, int m0, int k0, int lane, uint32_t a[4])
+{
+    const int g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 *r0 = A + (m0 + g) * ld + k0 + 2 * t;
+    const __nv_bfloat16 *r1 = A + (m0 + g + 8) * ld + k0 + 2 * t;
+    a[0] = *reinterpret_cast<const uint32_t *>(r0);
+    a[1] = *reinterpret_cast<const uint32_t *>(r1);
+    a[2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+    a[3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+}
+
+// B fragment (16 x 8 tile at k0, n0) of B = W^T, W row-major [n][k] with row stride ld
+__device__ __forceinline__ void load_b(const __nv_bfloat16 *W, int ld, int k0, int n0, int lane, uint32_t b[2])
+{
+    const int g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 *r = W + (n0 + g) * ld + k0 + 2 * t;
+    b[0] = *reinterpret_cast<const uint32_t *>(r);
+    b[1] = *reinterpret_cast<const uint32_t *>(r + 8);
+}
+
+struct InfSmem {
+    __nv_bfloat16 W1[NH * K1P];
+    __nv_bfloat16 W2[NH * NH];
+    __nv_bfloat16 W3[N3P * NH];
+    float b1[NH], b2[NH], b3[N3P];
+    float mean[NI], istd[NI];
+    __nv_bfloat16 x[INF_WARPS][32 * K1P];
+    __nv_bfloat16 h1[INF_WARPS][32 * NH];
+    __nv_bfloat16 h2[INF_WARPS][32 * NH];
+    float y[INF_WARPS][32 * N3P];
+};
+
+// one layer: out[32 x N] = act(in[32 x K] W^T + b), bf16 in/out
+template <int K, int N, bool GELU>
+__device__ __forceinline__ void warp_layer(const __nv_bfloat16 *in, const __nv_bfloat16 *W, const float *b,
+                                           __nv_bfloat16 *out_bf, float *out_f, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int n0 = 0; n0 < N; n0 += 8) {
+        float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += 16) {
+            uint32_t bf[2], a0[4], a1[4];
+            load_b(W, K, k0, n0, lane, bf);
+            load_a(in, K, 0, k0, lane, a0);
+            load_a(in, K, 16, k0, lane, a1);
+            mma_bf16(c0, a0, bf);
+            mma_bf16(c1, a1, bf);
+        }
+        const int n = n0 + 2 * t;
+        const float bb0 = b[n], bb1 = b[n + 1];
+        float v[8] = {c0[0] + bb0, c0[1] + bb1, c0[2] + bb0, c0[3] + bb1,
+                      c1[0] + bb0, c1[1] + bb1, c1[2] + bb0, c1[3] + bb1};
+        if (GELU)
+            for (int q = 0; q < 8; ++q) v[q] = gelu_f(v[q]);
+        const int rows[4] = {g, g + 8, 16 + g, 24 + g};
+        for (int q = 0; q < 4; ++q) {
+            if (out_bf) {
+                *reinterpret_cast<uint32_t *>(out_bf + rows[q] * N + n) = pack_bf16(v[2 * q], v[2 * q + 1]);
+            } else {
+                out_f[rows[q] * N + n] = v[2 * q];
+                out_f[rows[q] * N + n + 1] = v[2 * q + 1];
+            }
+        }
+    }
+}
+
+// rotation of a particle (columns: body axes in the lab frame)
+struct Rot {
+    float m[3][3];
+};
+
+__device__ __forceinline__ Rot rot_of(const PView &P, int k)
+{
+    const float w = P.qw[k], x = P.qx[k], y = P.qy[k], z = P.qz[k];
+    const float s = 2.0f / (w * w + x * x + y * y + z * z);
+    Rot R;
+    R.m[0][0] = 1 - s * (y * y + z * z);
+    R.m[0][1] = s * (x * y - w * z);
+    R.m[0][2] = s * (x * z + w * y);
+    R.m[1][0] = s * (x * y + w * z);
+    R.m[1][1] = 1 - s * (x * x + z * z);
+    R.m[1][2] = s * (y * z - w * x);
+    R.m[2][0] = s * (x * z - w * y);
+    R.m[2][1] = s * (y * z + w * x);
+    R.m[2][2] = 1 - s * (x * x + y * y);
+    return R;
+}
+
+// (p, q) of the support point of particle k along lab direction e
+__device__ __forceinline__ void support_pq(const PView &P, int k, const Rot &R, const V3<float> &e, float &p, float &q)
+{
+    const float bx = R.m[0][0] * e.x + R.m[1][0] * e.y + R.m[2][0] * e.z;
+    const float by = R.m[0][1] * e.x + R.m[1][1] * e.y + R.m[2][1] * e.z;
+    const float bz = R.m[0][2] * e.x + R.m[1][2] * e.y + R.m[2][2] * e.z;
+    p = atan2f(P.rpar[k] * bz, P.rperp[k] * sqrtf(bx * bx + by * by));
+    q = atan2f(by, bx);
+}
+
+// outward unit normal of particle k at body surface parameters (p, q), lab frame
+__device__ __forceinline__ V3<float> normal_at(const PView &P, int k, const Rot &R, float p, float q)
+{
+    float sp, cp, sq, cq;
+    sincosf(p, &sp, &cp);
+    sincosf(q, &sq, &cq);
+    const float rpar = P.rpar[k], rperp = P.rperp[k];
+    const V3<float> nb = mk<float>(rpar * cp * cq, rpar * cp * sq, rperp * sp);
+    const V3<float> nl = mk<float>(R.m[0][0] * nb.x + R.m[0][1] * nb.y + R.m[0][2] * nb.z,
+                                   R.m[1][0] * nb.x + R.m[1][1] * nb.y + R.m[1][2] * nb.z,
+                                   R.m[2][0] * nb.x + R.m[2][1] * nb.y + R.m[2][2] * nb.z);
+    return normalized(nl);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the network's start normal for each pair of a tile (used by closest.cu)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi,
+                                                             const int32_t *__restrict__ pj,
+                                                             const int32_t *__restrict__ d_count, int32_t cap,
+                                                             MlpDevice M, double *__restrict__ n0,
+                                                             float *__restrict__ pq)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InfSmem &S = *reinterpret_cast<InfSmem *>(smem_raw);
+    const int count = pair_count(d_count, cap);
+    // stage the weights once per block
+    for (int k = threadIdx.x; k < NH * K1P; k += blockDim.x) S.W1[k] = M.W1[k];
+    for (int k = threadIdx.x; k < NH * NH; k += blockDim.x) S.W2[k] = M.W2[k];
+    for (int k = threadIdx.x; k < N3P * NH; k += blockDim.x) S.W3[k] = M.W3[k];
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+        S.b1[k] = M.b1[k];
+        S.b2[k] = M.b2[k];
+    }
+    for (int k = threadIdx.x; k < N3P; k += blockDim.x) S.b3[k] = M.b3[k];
+    for (int k = threadIdx.x; k < NI; k += blockDim.x) {
+        S.mean[k] = M.mean[k];
+        S.istd[k] = M.istd[k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t C = (size_t)cap;
+    for (int base = (blockIdx.x * INF_WARPS + w) * 32; base < count; base += gridDim.x * INF_WARPS * 32) {
+        const int k = base + lane;
+        int i = -1, j = -1;
+        float f[NI];
+        bool ok = false;
+        if (k < count) {
+            i = pi[k];
+            j = pj[k];
+            ok = i >= 0 && i < P.n && j >= 0 && j < P.n && i != j && shape_ok(P.rpar[i], P.rperp[i]) &&
+                 shape_ok(P.rpar[j], P.rperp[j]);
+        }
+        if (ok) {
+            pair_features(P, D, i, j, S.mean, S.istd, f);
+            for (int a = 0; a < NI; ++a)
+                if (!isfinite(f[a])) ok = false;
+        }
+        for (int a = 0; a < K1P; a += 2) {
+            const float lo = (ok && a < NI) ? f[a] : 0.f, hi = (ok && a + 1 < NI) ? f[a + 1] : 0.f;
+            *reinterpret_cast<uint32_t *>(&S.x[w][lane * K1P + a]) = pack_bf16(lo, hi);
+        }
+        __syncwarp();
+        warp_layer<K1P, NH, true>(S.x[w], S.W1, S.b1, S.h1[w], nullptr, lane);
+        __syncwarp();
+        warp_layer<NH, NH, true>(S.h1[w], S.W2, S.b2, S.h2[w], nullptr, lane);
+        __syncwarp();
+        warp_layer<NH, N3P, false>(S.h2[w], S.W3, S.b3, nullptr, S.y[w], lane);
+        __syncwarp();
+        if (k < count && pq) {
+            const float *yy = &S.y[w][lane * N3P];
+            for (int o = 0; o < NO; ++o) pq[o * C + k] = ok ? yy[o] : 0.f;
+        }
+        if (k < count && n0) {
+            V3<float> s0 = mk<float>(0, 0, 0);
+            if (ok) {
+                // corrections to the parameters of the line-of-centres start
+                const float *yy = &S.y[w][lane * N3P];
+                const V3<float> d = cvt<float>(min_image(D, sub(load_pos(P, j), load_pos(P, i))));
+                const V3<float> e = normalized(d);
+                const Rot Ri = rot_of(P, i), Rj = rot_of(P, j);
+                float pi0, qi0, pj0, qj0;
+                support_pq(P, i, Ri, e, pi0, qi0);
+                support_pq(P, j, Rj, scl(-1.0f, e), pj0, qj0);
+                const V3<float> ni = normal_at(P, i, Ri, pi0 + yy[0], qi0 + yy[1]);
+                const V3<float> nj = normal_at(P, j, Rj, pj0 + yy[2], qj0 + yy[3]);
+                const V3<float> s = sub(ni, nj);
+                const float l2 = dot(s, s);
+                if (l2 > 1e-12f && isfinite(l2)) s0 = scl(rsqrtf(l2), s);
+            }
+            n0[k] = s0.x;
+            n0[C + k] = s0.y;
+            n0[2 * C + k] = s0.z;
+        }
+        __syncwarp();
+    }
+}
+
+size_t mlp_start_smem() { return sizeof(InfSmem); }
+
+int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj,
+                     const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st)
+{
+    if (!ctx->mlp_ready) return lub_set_error(ctx, LUB_ERR_ARG, "the learned warm start needs lub_mlp_set first");
+    if (cap == 0) return LUB_OK;
+    const size_t smem = mlp_start_smem();
+    if (!ctx->mlp_smem_set) {
+        int rc = lub_check_cuda(
+            ctx, cudaFuncSetAttribute(k_mlp_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "shared memory attribute");
+        if (rc) return rc;
+        ctx->mlp_smem_set = true;
+    }
+    k_mlp_start<<<ctx->num_sms * 2, 32 * INF_WARPS, smem, st>>>(P, D, pi, pj, d_count, cap,
+                                                                  *(const MlpDevice *)ctx->mlp, n0, pq);
+    return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_start launch");
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_mlp_features(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj, int n,
+                        const float *mean, const float *istd, float *feat, cudaStream_t st)
+{
+    if (n <= 0) return LUB_OK;
+    k_mlp_features<<<grid_for(n, 128, ctx ? ctx->num_sms : 152, 16), 128, 0, st>>>(P, D, pi, pj, n, mean, istd, feat);
+    return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_features launch");
+}
+
+int launch_mlp_forward_backward(lub_ctx *ctx, const float *params, const float *x, const float *tgt,
+                                const float *wgt, int M, float *grads, float *work, float *loss_rows, cudaStream_t st)
+{
+    const float *W1 = params, *b1 = W1 + NH * NI, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NO * NH;
+    float *gW1 = grads, *gb1 = gW1 + NH * NI, *gW2 = gb1 + NH, *gb2 = gW2 + NH * NH, *gW3 = gb2 + NH,
+          *gb3 = gW3 + NO * NH;
+    // work: z1 h1 z2 h2 [M x 128] each, y dy [M x 4], d2 d1 [M x 128]
+    float *z1 = work, *h1 = z1 + (size_t)M * NH, *z2 = h1 + (size_t)M * NH, *h2 = z2 + (size_t)M * NH;
+    float *y = h2 + (size_t)M * NH, *dy = y + (size_t)M * NO, *d2 = dy + (size_t)M * NO, *d1 = d2 + (size_t)M * NH;
+    const dim3 blk(32, 8);
+    auto grid = [&](int cols, int rows) { return dim3((cols + TS - 1) / TS, (rows + TS - 1) / TS); };
+    k_linear_fwd<<<grid(NH, M), blk, 0, st>>>(x, W1, b1, M, NI, NH, z1, h1, 1);
+    k_linear_fwd<<<grid(NH, M), blk, 0, st>>>(h1, W2, b2, M, NH, NH, z2, h2, 1);
+    k_linear_fwd<<<grid(NO, M), blk, 0, st>>>(h2, W3, b3, M, NH, NO, y, nullptr, 0);
+    k_mlp_loss<<<grid_for(M, 256, ctx ? ctx->num_sms : 152, 8), 256, 0, st>>>(y, tgt, wgt, M, dy, loss_rows);
+    // layer 3
+    k_linear_bwd_w<<<grid(NH, NO), blk, 0, st>>>(dy, h2, M, NH, NO, gW3, gb3);
+    k_linear_bwd_x<<<grid(NH, M), blk, 0, st>>>(dy, W3, M, NH, NO, z2, d2);
+    // layer 2
+    k_linear_bwd_w<<<grid(NH, NH), blk, 0, st>>>(d2, h1, M, NH, NH, gW2, gb2);
+    k_linear_bwd_x<<<grid(NH, M), blk, 0, st>>>(d2, W2, M, NH, NH, z1, d1);
+    // layer 1
+    k_linear_bwd_w<<<grid(NI, NH), blk, 0, st>>>(d1, x, M, NI, NH, gW1, gb1);
+    return lub_check_cuda(ctx, cudaGetLastError(), "mlp forward/backward launch");
+}
+
+int launch_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, float *v, int n, int t, float lr,
+                    float b1, float b2, float eps, cudaStream_t st)
+{
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<grid_for(n, 256, ctx ? ctx->num_sms : 152, 4), 256, 0, st>>>(params, grads, m, v, n, lr, b1, b2, eps, c1,
+                                                                          c2);
+    return lub_check_cuda(ctx, cudaGetLastError(), "mlp adam launch");
+}
+
+// pack FP32 parameters into the BF16 inference layout owned by the context
+__global__ void k_mlp_pack(const float *__restrict__ params, MlpDevice M)
+{
+    const float *W1 = params, *b1 = W1 + NH * NI, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NO * NH;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NH * NH; k += gridDim.x * blockDim.x) {
+        M.W2[k] = __float2bfloat16_rn(W2[k]);
+        if (k < NH * K1P) {
+            const int n = k / K1P, c = k % K1P;
+            M.W1[k] = __float2bfloat16_rn(c < NI ? W1[n * NI + c] : 0.f);
+        }
+        if (k < N3P * NH) {
+            const int n = k / NH, c = k % NH;
+            M.W3[k] = __float2bfloat16_rn(n < NO ? W3[n * NH + c] : 0.f);
+        }
+        if (k < NH) {
+            M.b1[k] = b1[k];
+            M.b2[k] = b2[k];
+        }
+        if (k < N3P) M.b3[k] = k < NO ? b3[k] : 0.f;
+    }
+}
+
+int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaStream_t st)
+{
+    k_mlp_pack<<<64, 256, 0, st>>>(params, M);
+    return lub_check_cuda(ctx, cudaGetLastError(), "mlp pack launch");
+}
