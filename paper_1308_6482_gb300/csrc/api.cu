@@ -263,7 +263,7 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
     if (!params || !mean || !istd) return lub_set_error(ctx, LUB_ERR_ARG, "params, mean or istd is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if (!ctx->mlp) {
-        const size_t bw = (size_t)(128 * 16 + 128 * 128 + 8 * 128) * sizeof(__nv_bfloat16);
+        const size_t bw = (size_t)(8 * 32 + 64 * 32) * sizeof(uint4) + (size_t)(8 * 32) * sizeof(uint2);
         const size_t bf = (size_t)(128 + 128 + 8 + 12 + 12) * sizeof(float);
         void *mem = nullptr;
         cudaError_t e = cudaMalloc(&mem, bw + bf + 256);
@@ -277,9 +277,9 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
             return LUB_ERR_NOMEM;
         }
         char *c = (char *)mem;
-        M->W1 = (__nv_bfloat16 *)c;
-        M->W2 = M->W1 + 128 * 16;
-        M->W3 = M->W2 + 128 * 128;
+        M->F1 = (uint4 *)c;
+        M->F2 = M->F1 + 8 * 32;
+        M->F3 = (uint2 *)(M->F2 + 64 * 32);
         float *f = (float *)(c + ((bw + 255) & ~(size_t)255));
         M->b1 = f;
         M->b2 = f + 128;

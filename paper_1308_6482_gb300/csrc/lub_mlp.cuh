@@ -5,13 +5,18 @@
 
 #include "lub_internal.cuh"
 
-// BF16 inference weights and FP32 biases / feature standardisation, owned by a context
+// BF16 inference weights, stored in the B-fragment order of mma.m16n8k16 (one
+// 16-byte load per lane gives the fragments of two adjacent 8-column n-tiles),
+// and FP32 biases / feature standardisation; owned by a context.
+//   F1 [8 n-tile pairs][32 lanes]             layer 1, inputs padded 12 -> 16
+//   F2 [8 n-tile pairs][8 k-tiles][32 lanes]  layer 2
+//   F3 [8 k-tiles][32 lanes]                  layer 3, outputs padded 4 -> 8
 struct MlpDevice {
-    __nv_bfloat16 *W1;  // [128][16]  (inputs padded 12 -> 16)
-    __nv_bfloat16 *W2;  // [128][128]
-    __nv_bfloat16 *W3;  // [8][128]   (outputs padded 4 -> 8)
-    float *b1, *b2, *b3;
-    float *mean, *istd;  // [12] each
+    uint4 *F1;
+    uint4 *F2;
+    uint2 *F3;
+    float *b1, *b2, *b3;  // [128], [128], [8]
+    float *mean, *istd;   // [12] each
 };
 
 static_assert(LUB_MLP_PARAMS == 128 * 12 + 128 + 128 * 128 + 128 + 4 * 128 + 4, "parameter count");

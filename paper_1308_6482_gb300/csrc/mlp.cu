@@ -14,10 +14,10 @@
 //             squared error with the azimuth differences wrapped to (-pi, pi],
 //             backward through the layers, Adam.  Parameters packed [W1 | b1 | W2 | b2 | W3 | b3]
 //             with W row-major [out][in].
-//   inference BF16 weights on the tensor cores (mma.sync m16n8k16, FP32
-//             accumulate), one warp per 32 pairs, fused with the FP64 Newton
-//             solve of the closest points: the predicted (p, q) give the
-//             outward normals n_i, n_j at the predicted points and the start
+//   inference BF16 weights and activations on the tensor cores (mma.sync
+//             m16n8k16, FP32 accumulate), one warp per 32 pairs with the
+//             activations in registers; the predicted (p, q) give the outward
+//             normals n_i, n_j at the predicted points and Newton's start
 //             n0 = (n_i - n_j)/|n_i - n_j|.
 #include <cuda_bf16.h>
 
@@ -238,19 +238,27 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 }
 
 // ---------------------------------------------------------------------------
-// inference: BF16 tensor cores, fused with the FP64 Newton solve
+// inference: BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate)
 // ---------------------------------------------------------------------------
-constexpr int INF_WARPS = 4;
-constexpr int K1P = 16;  // layer-1 inner dimension padded 12 -> 16
-constexpr int N3P = 8;   // layer-3 outputs padded 4 -> 8
+// One warp runs 32 pairs (two 16-row m-tiles) through the three layers with
+// the activations in registers: the accumulator fragment of two adjacent
+// 8-column n-tiles is, element for element, the A fragment of one 16-deep
+// k-tile of the next layer, so layer 1's output becomes layer 2's A operand
+// without leaving the registers, and layer 2 is produced 16 columns at a time
+// and folded straight into layer 3.  Only the features (in) and the four
+// outputs (out) pass through shared memory.  The weights sit in shared memory
+// in fragment order (conflict-free 16-byte loads).
+constexpr int INF_WARPS = 8;
+constexpr int XS = 24;  // row stride (bf16) of the staged features: conflict-free A-fragment loads
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
 {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -259,73 +267,123 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// A fragment (16 x 16 tile at rows m0, cols k0) from a row-major bf16 matrix with row stride ld
-__device__ __forceinline__ void load_a(const __nv_bfloat16 *A, int ld, int m0, int k0, int lane, uint32_t a[4])
+// GELU of two accumulators, returned as the packed BF16 pair the next layer
+// reads: the tanh form of Hendrycks & Gimpel (2016), evaluated in BF16x2
+// arithmetic with the hardware tanh.  The inputs are rounded to BF16 first;
+// the result is within a few BF16 ulps of the exact (erf) form the network is
+// trained with.
+__device__ __forceinline__ uint32_t gelu2(float a, float b)
 {
-    const int g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16 *r0 = A + (m0 + g) * ld + k0 + 2 * t;
-    const __nv_bfloat16 *r1 = A + (m0 + g + 8) * ld + k0 + 2 * t;
-    a[0] = *reinterpret_cast<const uint32_t *>(r0);
-    a[1] = *reinterpret_cast<const uint32_t *>(r1);
-    a[2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-    a[3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-}
-
-// B fragment (16 x 8 tile at k0, n0) of B = W^T, W row-major [n][k] with row stride ld
-__device__ __forceinline__ void load_b(const __nv_bfloat16 *W, int ld, int k0, int n0, int lane, uint32_t b[2])
-{
-    const int g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16 *r = W + (n0 + g) * ld + k0 + 2 * t;
-    b[0] = *reinterpret_cast<const uint32_t *>(r);
-    b[1] = *reinterpret_cast<const uint32_t *>(r + 8);
+    const uint32_t x = pack_bf16(a, b);
+    const uint32_t c0 = 0x3F4C3F4Cu;  // sqrt(2/pi) = 0.7979 -> 0.7969 in BF16
+    const uint32_t c1 = 0x3D123D12u;  // 0.044715 sqrt(2/pi) = 0.03568 -> 0.03564
+    const uint32_t hf = 0x3F003F00u;  // 0.5
+    uint32_t x2, v, u, t, h, r;
+    asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(x2) : "r"(x));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(v) : "r"(x2), "r"(c1), "r"(c0));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(x), "r"(v));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(u));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(x), "r"(hf));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(t), "r"(h));
+    return r;
 }
 
 struct InfSmem {
-    __nv_bfloat16 W1[NH * K1P];
-    __nv_bfloat16 W2[NH * NH];
-    __nv_bfloat16 W3[N3P * NH];
-    float b1[NH], b2[NH], b3[N3P];
+    uint4 F1[8 * 32];
+    uint4 F2[64 * 32];
+    uint2 F3[8 * 32];
+    float b1[NH], b2[NH], b3[8];
     float mean[NI], istd[NI];
-    __nv_bfloat16 x[INF_WARPS][32 * K1P];
-    __nv_bfloat16 h1[INF_WARPS][32 * NH];
-    __nv_bfloat16 h2[INF_WARPS][32 * NH];
-    float y[INF_WARPS][32 * N3P];
+    __nv_bfloat16 x[INF_WARPS][32 * XS];
+    float4 y[INF_WARPS][32];
 };
 
-// one layer: out[32 x N] = act(in[32 x K] W^T + b), bf16 in/out
-template <int K, int N, bool GELU>
-__device__ __forceinline__ void warp_layer(const __nv_bfloat16 *in, const __nv_bfloat16 *W, const float *b,
-                                           __nv_bfloat16 *out_bf, float *out_f, int lane)
+// the 4 network outputs of the calling lane's pair (features f, standardised,
+// zero for an invalid pair); warp-collective
+__device__ __forceinline__ float4 warp_mlp(const InfSmem &S, __nv_bfloat16 *xs, float4 *ys, const float f[NI],
+                                           int lane)
 {
     const int g = lane >> 2, t = lane & 3;
-#pragma unroll 1
-    for (int n0 = 0; n0 < N; n0 += 8) {
-        float c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+    // stage the features: row = lane, 12 values + 4 zeros of padding
+    uint32_t *xr = reinterpret_cast<uint32_t *>(xs + lane * XS);
 #pragma unroll
-        for (int k0 = 0; k0 < K; k0 += 16) {
-            uint32_t bf[2], a0[4], a1[4];
-            load_b(W, K, k0, n0, lane, bf);
-            load_a(in, K, 0, k0, lane, a0);
-            load_a(in, K, 16, k0, lane, a1);
-            mma_bf16(c0, a0, bf);
-            mma_bf16(c1, a1, bf);
-        }
-        const int n = n0 + 2 * t;
-        const float bb0 = b[n], bb1 = b[n + 1];
-        float v[8] = {c0[0] + bb0, c0[1] + bb1, c0[2] + bb0, c0[3] + bb1,
-                      c1[0] + bb0, c1[1] + bb1, c1[2] + bb0, c1[3] + bb1};
-        if (GELU)
-            for (int q = 0; q < 8; ++q) v[q] = gelu_f(v[q]);
-        const int rows[4] = {g, g + 8, 16 + g, 24 + g};
-        for (int q = 0; q < 4; ++q) {
-            if (out_bf) {
-                *reinterpret_cast<uint32_t *>(out_bf + rows[q] * N + n) = pack_bf16(v[2 * q], v[2 * q + 1]);
-            } else {
-                out_f[rows[q] * N + n] = v[2 * q];
-                out_f[rows[q] * N + n + 1] = v[2 * q + 1];
-            }
+    for (int a = 0; a < 6; ++a) xr[a] = pack_bf16(f[2 * a], f[2 * a + 1]);
+    xr[6] = 0u;
+    xr[7] = 0u;
+    __syncwarp();
+    uint32_t A1[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const uint32_t *r0 = reinterpret_cast<const uint32_t *>(xs + (16 * mt + g) * XS) + t;
+        const uint32_t *r1 = reinterpret_cast<const uint32_t *>(xs + (16 * mt + g + 8) * XS) + t;
+        A1[mt][0] = r0[0];
+        A1[mt][1] = r1[0];
+        A1[mt][2] = r0[4];
+        A1[mt][3] = r1[4];
+    }
+    // layer 1 -> A fragments of layer 2
+    uint32_t A2[2][8][4];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const uint4 bb = S.F1[p * 32 + lane];
+        const float2 bl = *reinterpret_cast<const float2 *>(&S.b1[16 * p + 2 * t]);
+        const float2 bh = *reinterpret_cast<const float2 *>(&S.b1[16 * p + 8 + 2 * t]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float c0[4] = {bl.x, bl.y, bl.x, bl.y}, c1[4] = {bh.x, bh.y, bh.x, bh.y};
+            mma_bf16(c0, A1[mt][0], A1[mt][1], A1[mt][2], A1[mt][3], bb.x, bb.y);
+            mma_bf16(c1, A1[mt][0], A1[mt][1], A1[mt][2], A1[mt][3], bb.z, bb.w);
+            A2[mt][p][0] = gelu2(c0[0], c0[1]);
+            A2[mt][p][1] = gelu2(c0[2], c0[3]);
+            A2[mt][p][2] = gelu2(c1[0], c1[1]);
+            A2[mt][p][3] = gelu2(c1[2], c1[3]);
         }
     }
+    // layer 2, 16 columns at a time, each folded into layer 3 as one k-tile
+    const float2 b3 = *reinterpret_cast<const float2 *>(&S.b3[2 * t]);
+    float y[2][4] = {{b3.x, b3.y, b3.x, b3.y}, {b3.x, b3.y, b3.x, b3.y}};
+#pragma unroll 1
+    for (int p = 0; p < 8; ++p) {
+        const float2 bl = *reinterpret_cast<const float2 *>(&S.b2[16 * p + 2 * t]);
+        const float2 bh = *reinterpret_cast<const float2 *>(&S.b2[16 * p + 8 + 2 * t]);
+        float c[2][2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            c[mt][0][0] = c[mt][0][2] = bl.x;
+            c[mt][0][1] = c[mt][0][3] = bl.y;
+            c[mt][1][0] = c[mt][1][2] = bh.x;
+            c[mt][1][1] = c[mt][1][3] = bh.y;
+        }
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            const uint4 bb = S.F2[(p * 8 + kt) * 32 + lane];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_bf16(c[mt][0], A2[mt][kt][0], A2[mt][kt][1], A2[mt][kt][2], A2[mt][kt][3], bb.x, bb.y);
+                mma_bf16(c[mt][1], A2[mt][kt][0], A2[mt][kt][1], A2[mt][kt][2], A2[mt][kt][3], bb.z, bb.w);
+            }
+        }
+        const uint2 b = S.F3[p * 32 + lane];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+            mma_bf16(y[mt], gelu2(c[mt][0][0], c[mt][0][1]), gelu2(c[mt][0][2], c[mt][0][3]),
+                     gelu2(c[mt][1][0], c[mt][1][1]), gelu2(c[mt][1][2], c[mt][1][3]), b.x, b.y);
+    }
+    // outputs: columns 0..3 live in lanes t = 0, 1 of each row group
+    float *yf = reinterpret_cast<float *>(ys);
+    if (t < 2) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            yf[(16 * mt + g) * 4 + 2 * t] = y[mt][0];
+            yf[(16 * mt + g) * 4 + 2 * t + 1] = y[mt][1];
+            yf[(16 * mt + g + 8) * 4 + 2 * t] = y[mt][2];
+            yf[(16 * mt + g + 8) * 4 + 2 * t + 1] = y[mt][3];
+        }
+    }
+    __syncwarp();
+    const float4 out = ys[lane];
+    __syncwarp();
+    return out;
 }
 
 // rotation of a particle (columns: body axes in the lab frame)
@@ -350,23 +408,30 @@ __device__ __forceinline__ Rot rot_of(const PView &P, int k)
     return R;
 }
 
-// (p, q) of the support point of particle k along lab direction e
-__device__ __forceinline__ void support_pq(const PView &P, int k, const Rot &R, const V3<float> &e, float &p, float &q)
+// Outward unit normal (lab frame) of particle k at the surface point whose
+// parameters are those of the support point along lab direction e, shifted by
+// (dp, dq).  With the support point's body direction b = R^T e, its parameters
+// are p0 = atan2(R_par b_z, R_perp |b_xy|), q0 = atan2(b_y, b_x) (q0 = 0 on
+// the axis); cos and sin of p0 + dp and q0 + dq follow by the angle-addition
+// rules, so only the small shifts go through sin/cos.
+__device__ __forceinline__ V3<float> shifted_normal(const PView &P, int k, const Rot &R, const V3<float> &e, float dp,
+                                                    float dq)
 {
     const float bx = R.m[0][0] * e.x + R.m[1][0] * e.y + R.m[2][0] * e.z;
     const float by = R.m[0][1] * e.x + R.m[1][1] * e.y + R.m[2][1] * e.z;
     const float bz = R.m[0][2] * e.x + R.m[1][2] * e.y + R.m[2][2] * e.z;
-    p = atan2f(P.rpar[k] * bz, P.rperp[k] * sqrtf(bx * bx + by * by));
-    q = atan2f(by, bx);
-}
-
-// outward unit normal of particle k at body surface parameters (p, q), lab frame
-__device__ __forceinline__ V3<float> normal_at(const PView &P, int k, const Rot &R, float p, float q)
-{
-    float sp, cp, sq, cq;
-    sincosf(p, &sp, &cp);
-    sincosf(q, &sq, &cq);
     const float rpar = P.rpar[k], rperp = P.rperp[k];
+    const float rho = sqrtf(bx * bx + by * by);
+    const float cp0u = rperp * rho, sp0u = rpar * bz;
+    const float ih = rsqrtf(cp0u * cp0u + sp0u * sp0u);
+    const float cp0 = cp0u * ih, sp0 = sp0u * ih;
+    const float cq0 = rho > 0.f ? bx / rho : 1.f, sq0 = rho > 0.f ? by / rho : 0.f;
+    float sdp, cdp, sdq, cdq;
+    __sincosf(dp, &sdp, &cdp);
+    __sincosf(dq, &sdq, &cdq);
+    const float cp = cp0 * cdp - sp0 * sdp, sp = sp0 * cdp + cp0 * sdp;
+    const float cq = cq0 * cdq - sq0 * sdq, sq = sq0 * cdq + cq0 * sdq;
+    // normal direction of x^2/a^2 + y^2/a^2 + z^2/c^2 = 1 at (p, q), up to a positive factor
     const V3<float> nb = mk<float>(rpar * cp * cq, rpar * cp * sq, rperp * sp);
     const V3<float> nl = mk<float>(R.m[0][0] * nb.x + R.m[0][1] * nb.y + R.m[0][2] * nb.z,
                                    R.m[1][0] * nb.x + R.m[1][1] * nb.y + R.m[1][2] * nb.z,
@@ -379,24 +444,26 @@ __device__ __forceinline__ V3<float> normal_at(const PView &P, int k, const Rot 
 // ---------------------------------------------------------------------------
 // the network's start normal for each pair of a tile (used by closest.cu)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi,
-                                                             const int32_t *__restrict__ pj,
-                                                             const int32_t *__restrict__ d_count, int32_t cap,
-                                                             MlpDevice M, double *__restrict__ n0,
-                                                             float *__restrict__ pq)
+__global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi,
+                                                                const int32_t *__restrict__ pj,
+                                                                const int32_t *__restrict__ d_count, int32_t cap,
+                                                                MlpDevice M, double *__restrict__ n0,
+                                                                float *__restrict__ pq)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     InfSmem &S = *reinterpret_cast<InfSmem *>(smem_raw);
     const int count = pair_count(d_count, cap);
     // stage the weights once per block
-    for (int k = threadIdx.x; k < NH * K1P; k += blockDim.x) S.W1[k] = M.W1[k];
-    for (int k = threadIdx.x; k < NH * NH; k += blockDim.x) S.W2[k] = M.W2[k];
-    for (int k = threadIdx.x; k < N3P * NH; k += blockDim.x) S.W3[k] = M.W3[k];
+    for (int k = threadIdx.x; k < 8 * 32; k += blockDim.x) {
+        S.F1[k] = M.F1[k];
+        S.F3[k] = M.F3[k];
+    }
+    for (int k = threadIdx.x; k < 64 * 32; k += blockDim.x) S.F2[k] = M.F2[k];
     for (int k = threadIdx.x; k < NH; k += blockDim.x) {
         S.b1[k] = M.b1[k];
         S.b2[k] = M.b2[k];
     }
-    for (int k = threadIdx.x; k < N3P; k += blockDim.x) S.b3[k] = M.b3[k];
+    for (int k = threadIdx.x; k < 8; k += blockDim.x) S.b3[k] = M.b3[k];
     for (int k = threadIdx.x; k < NI; k += blockDim.x) {
         S.mean[k] = M.mean[k];
         S.istd[k] = M.istd[k];
@@ -420,34 +487,23 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_start(PView P, DView D, 
             for (int a = 0; a < NI; ++a)
                 if (!isfinite(f[a])) ok = false;
         }
-        for (int a = 0; a < K1P; a += 2) {
-            const float lo = (ok && a < NI) ? f[a] : 0.f, hi = (ok && a + 1 < NI) ? f[a + 1] : 0.f;
-            *reinterpret_cast<uint32_t *>(&S.x[w][lane * K1P + a]) = pack_bf16(lo, hi);
-        }
-        __syncwarp();
-        warp_layer<K1P, NH, true>(S.x[w], S.W1, S.b1, S.h1[w], nullptr, lane);
-        __syncwarp();
-        warp_layer<NH, NH, true>(S.h1[w], S.W2, S.b2, S.h2[w], nullptr, lane);
-        __syncwarp();
-        warp_layer<NH, N3P, false>(S.h2[w], S.W3, S.b3, nullptr, S.y[w], lane);
-        __syncwarp();
+        if (!ok)
+            for (int a = 0; a < NI; ++a) f[a] = 0.f;
+        const float4 y = warp_mlp(S, S.x[w], S.y[w], f, lane);
         if (k < count && pq) {
-            const float *yy = &S.y[w][lane * N3P];
-            for (int o = 0; o < NO; ++o) pq[o * C + k] = ok ? yy[o] : 0.f;
+            pq[k] = ok ? y.x : 0.f;
+            pq[C + k] = ok ? y.y : 0.f;
+            pq[2 * C + k] = ok ? y.z : 0.f;
+            pq[3 * C + k] = ok ? y.w : 0.f;
         }
         if (k < count && n0) {
             V3<float> s0 = mk<float>(0, 0, 0);
             if (ok) {
                 // corrections to the parameters of the line-of-centres start
-                const float *yy = &S.y[w][lane * N3P];
                 const V3<float> d = cvt<float>(min_image(D, sub(load_pos(P, j), load_pos(P, i))));
                 const V3<float> e = normalized(d);
-                const Rot Ri = rot_of(P, i), Rj = rot_of(P, j);
-                float pi0, qi0, pj0, qj0;
-                support_pq(P, i, Ri, e, pi0, qi0);
-                support_pq(P, j, Rj, scl(-1.0f, e), pj0, qj0);
-                const V3<float> ni = normal_at(P, i, Ri, pi0 + yy[0], qi0 + yy[1]);
-                const V3<float> nj = normal_at(P, j, Rj, pj0 + yy[2], qj0 + yy[3]);
+                const V3<float> ni = shifted_normal(P, i, rot_of(P, i), e, y.x, y.y);
+                const V3<float> nj = shifted_normal(P, j, rot_of(P, j), scl(-1.0f, e), y.z, y.w);
                 const V3<float> s = sub(ni, nj);
                 const float l2 = dot(s, s);
                 if (l2 > 1e-12f && isfinite(l2)) s0 = scl(rsqrtf(l2), s);
@@ -456,7 +512,6 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_start(PView P, DView D, 
             n0[C + k] = s0.y;
             n0[2 * C + k] = s0.z;
         }
-        __syncwarp();
     }
 }
 
@@ -527,29 +582,40 @@ int launch_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, f
 }
 
 // pack FP32 parameters into the BF16 inference layout owned by the context
+// B-fragment element of mma.m16n8k16 for B = W^T (W row-major [n][k], nv x kv
+// valid, zero padding): lane (g, t) holds W[8 nt + g][16 kt + 2 t + 8 h + {0, 1}]
+__device__ __forceinline__ uint32_t frag_b(const float *W, int nv, int kv, int nt, int kt, int lane, int h)
+{
+    const int n = 8 * nt + (lane >> 2), k = 16 * kt + 2 * (lane & 3) + 8 * h;
+    const float lo = (n < nv && k < kv) ? W[n * kv + k] : 0.f;
+    const float hi = (n < nv && k + 1 < kv) ? W[n * kv + k + 1] : 0.f;
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
 __global__ void k_mlp_pack(const float *__restrict__ params, MlpDevice M)
 {
     const float *W1 = params, *b1 = W1 + NH * NI, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NO * NH;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NH * NH; k += gridDim.x * blockDim.x) {
-        M.W2[k] = __float2bfloat16_rn(W2[k]);
-        if (k < NH * K1P) {
-            const int n = k / K1P, c = k % K1P;
-            M.W1[k] = __float2bfloat16_rn(c < NI ? W1[n * NI + c] : 0.f);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 32; e += gridDim.x * blockDim.x) {
+        const int lane = e & 31, kt = (e >> 5) & 7, p = e >> 8;
+        M.F2[e] = make_uint4(frag_b(W2, NH, NH, 2 * p, kt, lane, 0), frag_b(W2, NH, NH, 2 * p, kt, lane, 1),
+                             frag_b(W2, NH, NH, 2 * p + 1, kt, lane, 0), frag_b(W2, NH, NH, 2 * p + 1, kt, lane, 1));
+        if (e < 8 * 32) {
+            const int q = e >> 5;
+            M.F1[e] = make_uint4(frag_b(W1, NH, NI, 2 * q, 0, lane, 0), frag_b(W1, NH, NI, 2 * q, 0, lane, 1),
+                                 frag_b(W1, NH, NI, 2 * q + 1, 0, lane, 0), frag_b(W1, NH, NI, 2 * q + 1, 0, lane, 1));
+            M.F3[e] = make_uint2(frag_b(W3, NO, NH, 0, q, lane, 0), frag_b(W3, NO, NH, 0, q, lane, 1));
         }
-        if (k < N3P * NH) {
-            const int n = k / NH, c = k % NH;
-            M.W3[k] = __float2bfloat16_rn(n < NO ? W3[n * NH + c] : 0.f);
+        if (e < NH) {
+            M.b1[e] = b1[e];
+            M.b2[e] = b2[e];
         }
-        if (k < NH) {
-            M.b1[k] = b1[k];
-            M.b2[k] = b2[k];
-        }
-        if (k < N3P) M.b3[k] = k < NO ? b3[k] : 0.f;
+        if (e < 8) M.b3[e] = e < NO ? b3[e] : 0.f;
     }
 }
 
 int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaStream_t st)
 {
-    k_mlp_pack<<<64, 256, 0, st>>>(params, M);
+    k_mlp_pack<<<8, 256, 0, st>>>(params, M);
     return lub_check_cuda(ctx, cudaGetLastError(), "mlp pack launch");
 }
