@@ -85,6 +85,15 @@ typedef struct {
                                          all particles; used by lub_pairs_build
                                          to size its cell grid.  0 = the call
                                          computes it (one stream synchronise) */
+    const int32_t *batch_offsets;     /* ensemble mode (no counterpart in the
+                                         paper, which treats one suspension):
+                                         HOST array [n_batches + 1]; suspension b
+                                         owns particles [batch_offsets[b],
+                                         batch_offsets[b + 1]), offsets
+                                         non-decreasing from 0 to n.  NULL: one
+                                         suspension (n_batches ignored)          */
+    int32_t n_batches;                /* number of suspensions (>= 1) when
+                                         batch_offsets is set                    */
 } lub_particles;
 
 typedef struct {
@@ -112,6 +121,20 @@ typedef struct {
                              stage converges to rounding                                */
     int32_t warm_start;   /* LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP          */
 } lub_params;
+
+/* Ensemble mode.  With particles.batch_offsets set, the particle arrays hold
+ * n_batches independent suspensions back to back and every call taking a
+ * lub_domain reads dom[0 .. n_batches-1] (host memory), the box and walls of
+ * each suspension.  Pairs never cross suspensions; pair lists carry global
+ * particle indices, and a wall pair (i, -1 - w) names wall w of i's
+ * suspension.  Each stage runs as one launch over all suspensions, so an
+ * ensemble step costs the same number of launches as one suspension.  The
+ * library keeps device copies of the per-suspension tables in the context and
+ * uploads them (one stream synchronise) only when they change; a call whose
+ * tables differ from the previous call's fails with LUB_ERR_ARG while the
+ * stream is being captured into a CUDA graph.  A captured graph replays with
+ * the context's current tables and scratch: make one eager call of the
+ * largest ensemble before capturing. */
 
 /* Fill *p with the paper's values: mu = 1/6, Delta_n = 2/3, Delta_t = 1/2,
  * Delta_r = 1/4 (Eq. results:cutoffs), h_c = eps_c = 0, list_cutoff = 1,
@@ -297,6 +320,38 @@ int lub_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, floa
 int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const lub_params *prm,
                            int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count,
                            void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch-shape autotuner (no counterpart in the paper).  The tunable kernels
+ * are persistent grid-stride loops; their shape is (threads per block, blocks
+ * per SM), the grid being min(work / block, blocks_per_sm x SMs).
+ * ------------------------------------------------------------------------- */
+#define LUB_TUNE_CLOSEST_MIXED 0   /* lub_closest_points, LUB_MIXED, FP32 stage */
+#define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, FP64 work list */
+#define LUB_TUNE_CLOSEST_FP64 2    /* lub_closest_points, LUB_FP64 */
+#define LUB_TUNE_RESISTANCE 3      /* lub_resistance */
+#define LUB_TUNE_APPLY 4           /* lub_apply, atomic form */
+#define LUB_TUNE_SWEEP 5           /* lub_pairs_build, the two cell sweeps */
+#define LUB_TUNE_COUNT 6
+
+/* Time every candidate shape of the kernels a step with these arguments runs
+ * (the four calls, in prm's precision, atomic lub_apply) and keep the fastest
+ * in the context; later calls launch with them.  Runs the calls `reps` times
+ * per candidate (>= 1), synchronises the stream, and overwrites the pair and
+ * output arrays like a step does.  Not capturable: tune before capturing a
+ * graph.  The shapes change no result except the order of atomic additions. */
+int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                 int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count, double *n, double *gap,
+                 uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int32_t reps,
+                 void *stream);
+
+/* The shape kernel `kernel` (LUB_TUNE_*) launches with; 0 = the built-in
+ * default.  lub_set_launch_shape with block = blocks_per_sm = 0 restores it;
+ * otherwise block must be one of the kernel's candidates (a multiple of 32 up
+ * to its limit: 128 for the closest-point and resistance kernels, 32 for the
+ * FP64 work list, 256 for lub_apply and the sweeps) and 1 <= blocks_per_sm <= 64. */
+int lub_get_launch_shape(const lub_ctx *ctx, int32_t kernel, int32_t *block, int32_t *blocks_per_sm);
+int lub_set_launch_shape(lub_ctx *ctx, int32_t kernel, int32_t block, int32_t blocks_per_sm);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,9 @@ if ``liblub.so`` has not been built, importing the binding succeeds but the
 first call raises.
 
 ``Pipeline`` allocates the per-pair and per-particle buffers with torch and
-runs the four calls of one correction step on the current CUDA stream.
+runs the four calls of one correction step on the current CUDA stream.  With
+particles made by ``make_ensemble`` (many independent suspensions back to
+back) the same four calls process every suspension in one launch per stage.
 """
 from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT, LUB_FP64,
                    LUB_MIXED, LUB_OK, LUB_ST_DEGENERATE, LUB_ST_FP64, LUB_ST_NOCONV, LUB_ST_OVERLAP,
@@ -16,6 +18,8 @@ from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, L
                    default_params, library_path, load_library, lub_apply, lub_closest_points,
                    lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_last_error, lub_mlp_adam,
                    lub_mlp_features, lub_mlp_forward_backward, lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static,
-                   lub_resistance, make_domain)
+                   lub_resistance, make_domain, make_ensemble, lub_autotune, lub_get_launch_shape, lub_set_launch_shape,
+                   LUB_TUNE_CLOSEST_MIXED, LUB_TUNE_CLOSEST_REFINE, LUB_TUNE_CLOSEST_FP64, LUB_TUNE_RESISTANCE,
+                   LUB_TUNE_APPLY, LUB_TUNE_SWEEP, LUB_TUNE_COUNT, TUNE_NAMES)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

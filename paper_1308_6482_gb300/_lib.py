@@ -26,6 +26,14 @@ LUB_ST_OVERLAP = 1
 LUB_ST_NOCONV = 2
 LUB_ST_DEGENERATE = 4
 LUB_ST_FP64 = 8
+LUB_TUNE_CLOSEST_MIXED = 0
+LUB_TUNE_CLOSEST_REFINE = 1
+LUB_TUNE_CLOSEST_FP64 = 2
+LUB_TUNE_RESISTANCE = 3
+LUB_TUNE_APPLY = 4
+LUB_TUNE_SWEEP = 5
+LUB_TUNE_COUNT = 6
+TUNE_NAMES = ("closest_mixed", "closest_refine", "closest_fp64", "resistance", "apply", "sweep")
 
 _P_FIELDS = ("x", "y", "z", "qw", "qx", "qy", "qz", "r_par", "r_perp", "vx", "vy", "vz", "wx", "wy", "wz")
 
@@ -38,7 +46,9 @@ class LubError(RuntimeError):
 
 class lub_particles(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in _P_FIELDS] + [("n", ctypes.c_int32),
-                                                             ("max_semi_axis", ctypes.c_float)]
+                                                             ("max_semi_axis", ctypes.c_float),
+                                                             ("batch_offsets", ctypes.c_void_p),
+                                                             ("n_batches", ctypes.c_int32)]
 
 
 class lub_domain(ctypes.Structure):
@@ -56,7 +66,8 @@ class lub_params(ctypes.Structure):
 # every exported symbol of include/lub.h
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
-           "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam")
+           "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
+           "lub_get_launch_shape", "lub_set_launch_shape")
 
 _lib = None
 
@@ -106,6 +117,13 @@ def load_library():
     lib.lub_mlp_forward_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
     lib.lub_mlp_adam.restype = ctypes.c_int
     lib.lub_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp]
+    lib.lub_autotune.restype = ctypes.c_int
+    lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
+                                 vp, vp, vp, vp, i32, vp]
+    lib.lub_get_launch_shape.restype = ctypes.c_int
+    lib.lub_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32)]
+    lib.lub_set_launch_shape.restype = ctypes.c_int
+    lib.lub_set_launch_shape.argtypes = [vp, i32, i32, i32]
     lib.lub_pairs_build_static.restype = ctypes.c_int
     lib.lub_pairs_build_static.argtypes = [P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp]
     _lib = lib
@@ -123,6 +141,11 @@ def _ptr(t):
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     raise TypeError(type(t))
+
+
+def _dom(domain):
+    """A lub_domain by reference, or an ensemble's array of them (decays to a pointer)."""
+    return domain if isinstance(domain, ctypes.Array) else ctypes.byref(domain)
 
 
 def _stream(stream):
@@ -169,7 +192,7 @@ def lub_last_error(ctx):
 def lub_pairs_build(ctx, particles, domain, params, pair_i, pair_j, capacity, d_count, h_count=None,
                     stream=None, check=True):
     hc = ctypes.c_int32(0)
-    rc = load_library().lub_pairs_build(ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params),
+    rc = load_library().lub_pairs_build(ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params),
                                         _ptr(pair_i), _ptr(pair_j), int(capacity), _ptr(d_count),
                                         ctypes.byref(hc) if h_count else None, _stream(stream))
     if check and rc not in (LUB_OK, LUB_ERR_CAPACITY):
@@ -179,7 +202,7 @@ def lub_pairs_build(ctx, particles, domain, params, pair_i, pair_j, capacity, d_
 
 def lub_pairs_build_static(particles, domain, params, pair_i, pair_j, capacity, d_count, stream=None):
     """Pair build on the library's static scratch (no allocation); returns the code."""
-    return load_library().lub_pairs_build_static(ctypes.byref(particles), ctypes.byref(domain),
+    return load_library().lub_pairs_build_static(ctypes.byref(particles), _dom(domain),
                                                  ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
                                                  _ptr(d_count), _stream(stream))
 
@@ -189,13 +212,13 @@ def lub_mlp_set(ctx, params, mean, istd, stream=None):
 
 
 def lub_mlp_predict(ctx, particles, domain, pair_i, pair_j, d_count, capacity, pq, stream=None):
-    return _check(ctx, load_library().lub_mlp_predict(ctx, ctypes.byref(particles), ctypes.byref(domain),
+    return _check(ctx, load_library().lub_mlp_predict(ctx, ctypes.byref(particles), _dom(domain),
                                                       _ptr(pair_i), _ptr(pair_j), _ptr(d_count), int(capacity),
                                                       _ptr(pq), _stream(stream)))
 
 
 def lub_mlp_features(ctx, particles, domain, pair_i, pair_j, n, mean, istd, feat, stream=None):
-    return _check(ctx, load_library().lub_mlp_features(ctx, ctypes.byref(particles), ctypes.byref(domain),
+    return _check(ctx, load_library().lub_mlp_features(ctx, ctypes.byref(particles), _dom(domain),
                                                        _ptr(pair_i), _ptr(pair_j), int(n), _ptr(mean), _ptr(istd),
                                                        _ptr(feat), _stream(stream)))
 
@@ -216,14 +239,14 @@ def lub_mlp_adam(ctx, params, grads, m, v, n, t, lr, beta1=0.9, beta2=0.999, eps
 def lub_closest_points(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status,
                        iters=None, stream=None):
     return _check(ctx, load_library().lub_closest_points(
-        ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
         _ptr(d_count), int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _stream(stream)))
 
 
 def lub_resistance(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, FT, lever,
                    stream=None):
     return _check(ctx, load_library().lub_resistance(
-        ctx, ctypes.byref(particles), ctypes.byref(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
         _ptr(d_count), int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(FT), _ptr(lever), _stream(stream)))
 
 
@@ -232,6 +255,24 @@ def lub_apply(ctx, pair_i, pair_j, d_count, capacity, FT, lever, n, force, torqu
     return _check(ctx, load_library().lub_apply(
         ctx, _ptr(pair_i), _ptr(pair_j), _ptr(d_count), int(capacity), _ptr(FT), _ptr(lever), int(n), _ptr(force),
         _ptr(torque), int(precision), int(accumulate), int(deterministic), _stream(stream)))
+
+
+def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_count, n, gap, status, iters, FT,
+                 lever, force, torque, reps=3, stream=None):
+    return _check(ctx, load_library().lub_autotune(
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
+        _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
+        _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_get_launch_shape(ctx, kernel):
+    b, p = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(ctx, load_library().lub_get_launch_shape(ctx, int(kernel), ctypes.byref(b), ctypes.byref(p)))
+    return b.value, p.value
+
+
+def lub_set_launch_shape(ctx, kernel, block, blocks_per_sm):
+    return _check(ctx, load_library().lub_set_launch_shape(ctx, int(kernel), int(block), int(blocks_per_sm)))
 
 
 # ---------------------------------------------------------------------------
@@ -249,6 +290,12 @@ def default_params(**kw):
 
 
 def make_domain(dom):
+    """lub_domain of a domain dict; for a list of dicts (an ensemble), an array of them."""
+    if isinstance(dom, (list, tuple)):
+        arr = (lub_domain * len(dom))()
+        for b, one in enumerate(dom):
+            arr[b] = make_domain(one)
+        return arr
     d = lub_domain()
     for k in range(3):
         d.L[k] = float(dom["L"][k])
@@ -261,13 +308,29 @@ def make_domain(dom):
     return d
 
 
+def make_ensemble(suspensions):
+    """Concatenate independent suspensions [(parts, dom), ...] for ensemble mode.
+
+    Returns (parts, doms, offsets): the particle arrays back to back, the list
+    of domain dicts, and the host offsets [n_batches + 1] (suspension b owns
+    particles offsets[b] .. offsets[b+1]-1)."""
+    offsets = np.zeros(len(suspensions) + 1, np.int32)
+    for b, (p, _) in enumerate(suspensions):
+        offsets[b + 1] = offsets[b] + len(p["x"])
+    keys = [k for k in _P_FIELDS if all(k in p for p, _ in suspensions)]
+    parts = {k: np.concatenate([np.asarray(p[k]) for p, _ in suspensions]) for k in keys}
+    return parts, [d for _, d in suspensions], offsets
+
+
 class DeviceParticles:
     """Particle arrays on the GPU (float64 centres, float32 the rest)."""
 
-    def __init__(self, parts, device="cuda", max_semi_axis=None):
+    def __init__(self, parts, device="cuda", max_semi_axis=None, batch_offsets=None):
         import torch
         n = len(parts["x"])
         self.n = n
+        # ensemble mode: host offsets [n_batches + 1], kept alive with the struct
+        self.offsets = None if batch_offsets is None else np.ascontiguousarray(batch_offsets, np.int32)
         self.t = {}
         for f in _P_FIELDS:
             a = parts.get(f)
@@ -277,10 +340,13 @@ class DeviceParticles:
             self.t[f] = torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(device)
         if max_semi_axis is None:
             max_semi_axis = float(max(np.max(parts["r_par"]), np.max(parts["r_perp"]))) if n else 1.0
-        self.c = lub_particles(*[self.t[f].data_ptr() for f in _P_FIELDS], n, float(max_semi_axis))
+        self.max_semi_axis = float(max_semi_axis)
+        self.refresh()
 
     def refresh(self):
-        self.c = lub_particles(*[self.t[f].data_ptr() for f in _P_FIELDS], self.n, self.c.max_semi_axis)
+        off = self.offsets
+        self.c = lub_particles(*[self.t[f].data_ptr() for f in _P_FIELDS], self.n, self.max_semi_axis,
+                               None if off is None else off.ctypes.data, 0 if off is None else len(off) - 1)
 
 
 class Context:
@@ -363,6 +429,13 @@ class Pipeline:
     def apply(self, deterministic=0, accumulate=0, stream=None):
         lub_apply(self.ctx.h, self.pair_i, self.pair_j, self.d_count, self.cap, self.FT, self.lever, self.n,
                   self.force, self.torque, self.prm.precision, accumulate, deterministic, stream=stream)
+
+    def autotune(self, reps=3, stream=None):
+        """Pick the launch shapes of this step's kernels (lub_autotune); returns them by name."""
+        lub_autotune(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.cap, self.d_count,
+                     self.nrm, self.gap, self.status, self.iters, self.FT, self.lever, self.force, self.torque, reps,
+                     stream)
+        return {TUNE_NAMES[k]: lub_get_launch_shape(self.ctx.h, k) for k in range(LUB_TUNE_COUNT)}
 
     def step(self, build=True, deterministic=0, sync_count=False, stream=None):
         if build:

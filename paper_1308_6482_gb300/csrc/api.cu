@@ -50,6 +50,42 @@ int lub_ensure_scratch(lub_ctx *ctx, size_t bytes)
     return LUB_OK;
 }
 
+int lub_upload_table(lub_ctx *ctx, int slot, const void *host, size_t bytes, cudaStream_t st, const void **dev)
+{
+    lub_ctx::Table &T = ctx->table[slot];
+    if (T.dev && T.host.size() == bytes && memcmp(T.host.data(), host, bytes) == 0) {
+        *dev = T.dev;
+        return LUB_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    int rc = lub_check_cuda(ctx, cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+    if (rc) return rc;
+    if (cs != cudaStreamCaptureStatusNone)
+        return lub_set_error(ctx, LUB_ERR_ARG,
+                             "the ensemble tables changed while the stream is captured: make one eager call with "
+                             "this ensemble first");
+    if (bytes > T.cap) {
+        // a graph captured earlier may still read the old buffer: keep it until the context goes
+        if (T.dev) ctx->retired.push_back(T.dev);
+        T.dev = nullptr;
+        T.cap = 0;
+        T.host.clear();
+        cudaError_t e = cudaMalloc(&T.dev, bytes);
+        if (e != cudaSuccess) {
+            T.dev = nullptr;
+            (void)cudaGetLastError();
+            return lub_set_error(ctx, LUB_ERR_NOMEM, "cudaMalloc of an ensemble table failed");
+        }
+        T.cap = bytes;
+    }
+    rc = lub_check_cuda(ctx, cudaMemcpyAsync(T.dev, host, bytes, cudaMemcpyHostToDevice, st), "table upload");
+    if (!rc) rc = lub_check_cuda(ctx, cudaStreamSynchronize(st), "table upload sync");
+    if (rc) return rc;
+    T.host.assign((const char *)host, (const char *)host + bytes);
+    *dev = T.dev;
+    return LUB_OK;
+}
+
 namespace {
 
 int check_particles(lub_ctx *ctx, const lub_particles *p, bool need_vel)
@@ -77,6 +113,52 @@ int check_domain(lub_ctx *ctx, const lub_domain *d)
     }
     if (d->n_walls > 0 && d->periodic[2])
         return lub_set_error(ctx, LUB_ERR_ARG, "walls are normal to z: z cannot be periodic");
+    return LUB_OK;
+}
+
+// The suspension(s) of a call: D for one suspension; in ensemble mode the
+// per-suspension table E (uploaded when it changes) and, if asked, the host
+// copy of each suspension's domain.
+int prepare_domains(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, cudaStream_t st, DView *D, Ens *E,
+                    std::vector<DView> *hdom = nullptr)
+{
+    E->dom = nullptr;
+    E->nb = 0;
+    memset(D, 0, sizeof(*D));
+    if (!p->batch_offsets) {
+        int rc = check_domain(ctx, dom);
+        if (rc) return rc;
+        *D = make_dview(dom);
+        return LUB_OK;
+    }
+    const int nb = p->n_batches;
+    if (nb < 1) return lub_set_error(ctx, LUB_ERR_ARG, "n_batches = %d must be >= 1 with batch_offsets", nb);
+    if (!dom) return lub_set_error(ctx, LUB_ERR_ARG, "domain is NULL");
+    const int32_t *off = p->batch_offsets;
+    if (off[0] != 0 || off[nb] != p->n)
+        return lub_set_error(ctx, LUB_ERR_ARG, "batch_offsets must run from 0 to n = %d", p->n);
+    std::vector<EnsDom> tab((size_t)nb);
+    for (int b = 0; b < nb; ++b) {
+        if (off[b + 1] < off[b]) return lub_set_error(ctx, LUB_ERR_ARG, "batch_offsets decrease at %d", b);
+        int rc = check_domain(ctx, dom + b);
+        if (rc) {
+            const std::string m = ctx->err;
+            return lub_set_error(ctx, rc, "suspension %d: %s", b, m.c_str());
+        }
+        memset(&tab[b], 0, sizeof(EnsDom));
+        tab[b].D = make_dview(dom + b);
+        tab[b].p0 = off[b];
+        tab[b].p1 = off[b + 1];
+    }
+    const void *dev = nullptr;
+    int rc = lub_upload_table(ctx, 0, tab.data(), tab.size() * sizeof(EnsDom), st, &dev);
+    if (rc) return rc;
+    E->dom = (const EnsDom *)dev;
+    E->nb = nb;
+    if (hdom) {
+        hdom->resize((size_t)nb);
+        for (int b = 0; b < nb; ++b) (*hdom)[b] = tab[b].D;
+    }
     return LUB_OK;
 }
 
@@ -152,6 +234,9 @@ int lub_ctx_destroy(lub_ctx *ctx)
     if (ctx->mlp_mem) cudaFree(ctx->mlp_mem);
     delete (MlpDevice *)ctx->mlp;
     if (ctx->d_flags) cudaFree(ctx->d_flags);
+    for (auto &T : ctx->table)
+        if (T.dev) cudaFree(T.dev);
+    for (void *r : ctx->retired) cudaFree(r);
     delete ctx;
     return LUB_OK;
 }
@@ -169,14 +254,16 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
     if (!ctx) return LUB_ERR_ARG;
     ctx->err.clear();
     int rc;
-    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)))
-        return rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_params(ctx, prm))) return rc;
     if (!d_count) return lub_set_error(ctx, LUB_ERR_ARG, "d_count is NULL");
     if (capacity < 0 || (capacity > 0 && (!pair_i || !pair_j)))
         return lub_set_error(ctx, LUB_ERR_ARG, "bad pair arrays or capacity");
     cudaStream_t st = (cudaStream_t)stream;
     PView P = make_pview(p);
-    DView D = make_dview(dom);
+    DView D;
+    Ens E;
+    std::vector<DView> hdom;
+    if ((rc = prepare_domains(ctx, p, dom, st, &D, &E, &hdom))) return rc;
     float rmax = p->max_semi_axis;
     if (!(rmax > 0.0f)) {
         if ((rc = launch_max_semi_axis(ctx, P, &rmax, st))) return rc;
@@ -185,11 +272,21 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
         if (!(rmax > 0.0f)) rmax = 1.0f;
     }
     const double range = 2.0 * rmax + prm->list_cutoff;
-    for (int a = 0; a < 3; ++a)
-        if (D.periodic[a] && !(D.L[a] > 2.0 * range * (1.0 + 1e-6) + 1e-3))
-            return lub_set_error(ctx, LUB_ERR_ARG,
-                                 "periodic L[%d] = %g must exceed 2 (2 Rmax + Delta_L) = %g", a, D.L[a], 2 * range);
-    if ((rc = launch_pairs_build(ctx, P, D, *prm, rmax, pair_i, pair_j, capacity, d_count, st))) return rc;
+    const int nd = E.nb ? E.nb : 1;
+    for (int b = 0; b < nd; ++b) {
+        const DView &Db = E.nb ? hdom[b] : D;
+        for (int a = 0; a < 3; ++a)
+            if (Db.periodic[a] && !(Db.L[a] > 2.0 * range * (1.0 + 1e-6) + 1e-3))
+                return lub_set_error(ctx, LUB_ERR_ARG,
+                                     "suspension %d: periodic L[%d] = %g must exceed 2 (2 Rmax + Delta_L) = %g", b, a,
+                                     Db.L[a], 2 * range);
+    }
+    if (E.nb)
+        rc = launch_pairs_build_ens(ctx, P, E, hdom.data(), p->batch_offsets, *prm, rmax, pair_i, pair_j, capacity,
+                                    d_count, st);
+    else
+        rc = launch_pairs_build(ctx, P, D, *prm, rmax, pair_i, pair_j, capacity, d_count, st);
+    if (rc) return rc;
     if (h_count_or_null) {
         int32_t flags = 0;
         rc = lub_check_cuda(ctx, cudaMemcpyAsync(h_count_or_null, d_count, 4, cudaMemcpyDeviceToHost, st), "copy count");
@@ -212,12 +309,15 @@ int lub_closest_points(lub_ctx *ctx, const lub_particles *p, const lub_domain *d
     if (!ctx) return LUB_ERR_ARG;
     ctx->err.clear();
     int rc;
-    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)) ||
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_params(ctx, prm)) ||
         (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
         return rc;
     if (capacity > 0 && (!n || !gap || !status)) return lub_set_error(ctx, LUB_ERR_ARG, "n, gap or status is NULL");
-    return launch_closest(ctx, make_pview(p), make_dview(dom), *prm, pair_i, pair_j, d_count, capacity, n, gap,
-                          status, iters, (cudaStream_t)stream);
+    DView D;
+    Ens E;
+    if ((rc = prepare_domains(ctx, p, dom, (cudaStream_t)stream, &D, &E))) return rc;
+    return launch_closest(ctx, make_pview(p), D, E, *prm, pair_i, pair_j, d_count, capacity, n, gap, status, iters,
+                          (cudaStream_t)stream);
 }
 
 int lub_resistance(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
@@ -227,13 +327,16 @@ int lub_resistance(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, 
     if (!ctx) return LUB_ERR_ARG;
     ctx->err.clear();
     int rc;
-    if ((rc = check_particles(ctx, p, true)) || (rc = check_domain(ctx, dom)) || (rc = check_params(ctx, prm)) ||
+    if ((rc = check_particles(ctx, p, true)) || (rc = check_params(ctx, prm)) ||
         (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
         return rc;
     if (capacity > 0 && (!n || !gap || !status || !FT || !lever))
         return lub_set_error(ctx, LUB_ERR_ARG, "n, gap, status, FT or lever is NULL");
-    return launch_resistance(ctx, make_pview(p), make_dview(dom), *prm, pair_i, pair_j, d_count, capacity, n, gap,
-                             status, FT, lever, (cudaStream_t)stream);
+    DView D;
+    Ens E;
+    if ((rc = prepare_domains(ctx, p, dom, (cudaStream_t)stream, &D, &E))) return rc;
+    return launch_resistance(ctx, make_pview(p), D, E, *prm, pair_i, pair_j, d_count, capacity, n, gap, status, FT,
+                             lever, (cudaStream_t)stream);
 }
 
 int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
@@ -305,11 +408,12 @@ int lub_mlp_predict(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
     if (!ctx) return LUB_ERR_ARG;
     ctx->err.clear();
     int rc;
-    if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom)) ||
-        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
-        return rc;
+    if ((rc = check_particles(ctx, p, false)) || (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity))) return rc;
     if (capacity > 0 && !pq) return lub_set_error(ctx, LUB_ERR_ARG, "pq is NULL");
-    return launch_mlp_start(ctx, make_pview(p), make_dview(dom), pair_i, pair_j, d_count, capacity, nullptr, pq,
+    DView D;
+    Ens E;
+    if ((rc = prepare_domains(ctx, p, dom, (cudaStream_t)stream, &D, &E))) return rc;
+    return launch_mlp_start(ctx, make_pview(p), D, E, pair_i, pair_j, d_count, capacity, nullptr, pq,
                             (cudaStream_t)stream);
 }
 
@@ -320,6 +424,7 @@ int lub_mlp_features(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom
     ctx->err.clear();
     int rc;
     if ((rc = check_particles(ctx, p, false)) || (rc = check_domain(ctx, dom))) return rc;
+    if (p->batch_offsets) return lub_set_error(ctx, LUB_ERR_ARG, "lub_mlp_features takes one suspension");
     if (n < 0 || (n > 0 && (!pair_i || !pair_j || !feat))) return lub_set_error(ctx, LUB_ERR_ARG, "bad pair arrays");
     if ((mean == nullptr) != (istd == nullptr)) return lub_set_error(ctx, LUB_ERR_ARG, "give both mean and istd or neither");
     return launch_mlp_features(ctx, make_pview(p), make_dview(dom), pair_i, pair_j, n, mean, istd, feat,

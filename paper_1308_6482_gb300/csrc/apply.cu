@@ -165,8 +165,8 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
             if (rc) return rc;
         }
         if (cap == 0) return LUB_OK;
-        const int block = 256;
-        const int grid = grid_for(cap, block, ctx->num_sms, 8);
+        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_APPLY, cap);
+        const int grid = sh.grid, block = sh.block;
         if (precision == LUB_MIXED)
             k_apply_atomic<float><<<grid, block, 0, st>>>(pi, pj, d_count, cap, (const float *)FT,
                                                           (const float *)lever, n, (float *)force, (float *)torque);

@@ -174,7 +174,8 @@ __device__ __forceinline__ double wall_gap(const PView &P, const DView &D, int i
 // LUB_MIXED: FP32 Newton + float-float gap; near-contact / unconverged pairs
 // go to the work list (entry k: refine from the FP32 normal; -1-k: full FP64
 // solve from the line of centres)
-__global__ void __launch_bounds__(128) k_closest_mixed(PView P, DView D, const int32_t *__restrict__ pi,
+template <bool ENS>
+__global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
                                                        const int32_t *__restrict__ pj,
                                                        const int32_t *__restrict__ d_count, int32_t cap,
                                                        double *__restrict__ nout, double *__restrict__ gap,
@@ -194,7 +195,9 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, DView D, const i
             int st = 0, nit = 0;
             V3<double> n64 = mk<double>(0, 0, 0);
             double h = 0.0;
-            if (pair_bad(P, D, i, j)) {
+            bool alien;
+            const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+            if (alien || pair_bad(P, D, i, j)) {
                 st = LUB_ST_DEGENERATE;
             } else if (j < 0) {
                 h = wall_gap(P, D, i, -1 - j, n64);
@@ -263,7 +266,8 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, DView D, const i
 }
 
 // FP64 refinement of the work list
-__global__ void __launch_bounds__(32) k_closest_refine(PView P, DView D, const int32_t *__restrict__ pi,
+template <bool ENS>
+__global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
                                                         const int32_t *__restrict__ pj, int32_t cap,
                                                         double *__restrict__ nout, double *__restrict__ gap,
                                                         uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
@@ -277,6 +281,8 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, DView D, const i
         const bool full = v < 0;
         const int k = full ? -1 - v : v;
         const int i = pi[k], j = pj[k];
+        bool alien;
+        const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
         const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
         const double dl = sqrt(dot(d, d));
         const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
@@ -304,7 +310,8 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, DView D, const i
 }
 
 // LUB_FP64: everything in double
-__global__ void __launch_bounds__(128) k_closest_fp64(PView P, DView D, const int32_t *__restrict__ pi,
+template <bool ENS>
+__global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
                                                       const int32_t *__restrict__ pj,
                                                       const int32_t *__restrict__ d_count, int32_t cap,
                                                       double *__restrict__ nout, double *__restrict__ gap,
@@ -318,7 +325,9 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, DView D, const in
         int st = 0, nit = 0;
         V3<double> n64 = mk<double>(0, 0, 0);
         double h = 0.0;
-        if (pair_bad(P, D, i, j)) {
+        bool alien;
+        const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+        if (alien || pair_bad(P, D, i, j)) {
             st = LUB_ST_DEGENERATE;
         } else if (j < 0) {
             h = wall_gap(P, D, i, -1 - j, n64);
@@ -361,23 +370,20 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, DView D, const in
     }
 }
 
-}  // namespace
-
-int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, const int32_t *pi,
-                   const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap, uint8_t *status,
-                   uint8_t *iters, cudaStream_t st)
+template <bool ENS>
+int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                     const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
+                     uint8_t *status, uint8_t *iters, cudaStream_t st)
 {
-    if (cap == 0) return LUB_OK;
-    const int block = 128;
-    const int grid = grid_for(cap, block, ctx->num_sms, 8);
     int warm = prm.warm_start == LUB_WARM_PREVIOUS;
     if (prm.warm_start == LUB_WARM_MLP) {
         // the network's start normal for every pair, then Newton from it
-        int rc = launch_mlp_start(ctx, P, D, pi, pj, d_count, cap, n, nullptr, st);
+        int rc = launch_mlp_start(ctx, P, D, E, pi, pj, d_count, cap, n, nullptr, st);
         if (rc) return rc;
         warm = 1;
     }
     if (prm.precision == LUB_MIXED) {
+        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
         // work list: count + up to cap entries in the context scratch
         int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);
         if (rc) return rc;
@@ -385,14 +391,28 @@ int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_param
         int32_t *wl = (int32_t *)((char *)ctx->scratch + 256);
         rc = lub_check_cuda(ctx, cudaMemsetAsync(wl_count, 0, 4, st), "memset work list");
         if (rc) return rc;
-        k_closest_mixed<<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton,
-                                                (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl);
+        k_closest_mixed<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
+                                                          prm.max_newton, (float)prm.newton_tol,
+                                                          (float)prm.fp64_switch, warm, wl_count, wl);
         // one warp per block so the (short) work list spreads over every SM
-        k_closest_refine<<<grid_for(cap, 32, ctx->num_sms, 16), 32, 0, st>>>(
-            P, D, pi, pj, cap, n, gap, status, iters, prm.max_newton, wl_count, wl);
+        const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
+        k_closest_refine<ENS><<<sr.grid, sr.block, 0, st>>>(P, D, E, pi, pj, cap, n, gap, status, iters,
+                                                            prm.max_newton, wl_count, wl);
     } else {
-        k_closest_fp64<<<grid, block, 0, st>>>(P, D, pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton,
-                                               warm);
+        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
+        k_closest_fp64<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
+                                                         prm.max_newton, warm);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
+}
+
+}  // namespace
+
+int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                   const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
+                   uint8_t *status, uint8_t *iters, cudaStream_t st)
+{
+    if (cap == 0) return LUB_OK;
+    return E.nb ? launch_closest_t<true>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, st)
+                : launch_closest_t<false>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, st);
 }

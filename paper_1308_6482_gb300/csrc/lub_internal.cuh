@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lub.h"
 
@@ -22,8 +23,23 @@ struct lub_ctx {
     void *mlp = nullptr;         // MlpDevice of the learned warm start (lub_mlp_set)
     void *mlp_mem = nullptr;     // its device storage
     bool mlp_ready = false;
-    bool mlp_smem_set = false;
+    int mlp_smem_set = 0;        // bit k: shared-memory attribute set for instantiation k
+    // device copies of the ensemble tables (slot 0: domains, slot 1: cell grids),
+    // with the host bytes they were uploaded from; buffers only grow, retired
+    // ones are freed with the context
+    struct Table {
+        std::vector<char> host;
+        void *dev = nullptr;
+        size_t cap = 0;
+    } table[2];
+    std::vector<void *> retired;
+    // launch shapes chosen by lub_autotune (0 = built-in default)
+    int tune_block[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int tune_per_sm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+// device copy of a host table, re-uploaded only when its bytes change
+int lub_upload_table(lub_ctx *ctx, int slot, const void *host, size_t bytes, cudaStream_t st, const void **dev);
 
 int lub_set_error(lub_ctx *ctx, int code, const char *fmt, ...);
 int lub_check_cuda(lub_ctx *ctx, cudaError_t e, const char *what);
@@ -48,6 +64,47 @@ struct DView {
     double wall_z[2];
     int32_t wall_dir[2];
 };
+
+// ensemble mode: per-suspension domain and particle range [p0, p1)
+struct EnsDom {
+    DView D;
+    int32_t p0, p1;
+};
+
+struct Ens {
+    const EnsDom *dom;  // device [nb]
+    int32_t nb;         // 0: one suspension
+};
+
+// suspension of particle k (k clamped into the table's range)
+__device__ __forceinline__ int batch_of(const Ens &E, int k)
+{
+    int lo = 0, hi = E.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&E.dom[mid].p0) <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// domain of the pair (i, j): D itself for one suspension, i's suspension's in
+// ensemble mode; a particle partner j outside that suspension makes the pair
+// invalid (*alien = true)
+// (a reference: D should be a __grid_constant__ kernel parameter, read in place)
+template <bool ENS>
+__device__ __forceinline__ const DView &pair_domain(const DView &D, const Ens &E, int i, int j, bool *alien)
+{
+    if (!ENS) {
+        *alien = false;
+        return D;
+    }
+    const EnsDom &B = E.dom[batch_of(E, i)];
+    *alien = j >= 0 && (j < __ldg(&B.p0) || j >= __ldg(&B.p1));
+    return B.D;
+}
 
 struct RParams {
     double mu, delta_n, delta_t, delta_r, h_c, eps_c;
@@ -242,10 +299,10 @@ __device__ __forceinline__ int pair_count(const int32_t *d_count, int32_t capaci
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
-int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm,
+int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                    const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n,
                    double *gap, uint8_t *status, uint8_t *iters, cudaStream_t st);
-int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm,
+int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                       const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                       const double *n, const double *gap, uint8_t *status, void *FT, void *lever,
                       cudaStream_t st);
@@ -254,6 +311,10 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
                  int accumulate, int deterministic, cudaStream_t st);
 int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, float rmax,
                        int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count, cudaStream_t st);
+// ensemble form: host domains and offsets of the nb suspensions, E their device table
+int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DView *hdom, const int32_t *hoff,
+                           const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count,
+                           cudaStream_t st);
 int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_t st);
 
 // device-wide exclusive scan of n int32 values (in place), total -> *d_total
@@ -268,6 +329,34 @@ inline int grid_for(int64_t work, int block, int num_sms, int per_sm = 16)
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+// launch shape of a tunable kernel (LUB_TUNE_*) for `work` items
+struct Shape2 {
+    int grid, block;
+};
+struct TuneDefault {
+    int block, per_sm, max_block;
+};
+constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
+    {128, 8, 128},   // LUB_TUNE_CLOSEST_MIXED
+    {32, 16, 32},    // LUB_TUNE_CLOSEST_REFINE
+    {128, 8, 128},   // LUB_TUNE_CLOSEST_FP64
+    {128, 8, 128},   // LUB_TUNE_RESISTANCE
+    {256, 8, 256},   // LUB_TUNE_APPLY
+    {256, 32, 256},  // LUB_TUNE_SWEEP
+};
+inline Shape2 tuned_shape(const lub_ctx *ctx, int id, int64_t work)
+{
+    int block = kTuneDefaults[id].block, per_sm = kTuneDefaults[id].per_sm;
+    if (ctx && ctx->tune_block[id] > 0) {
+        block = ctx->tune_block[id];
+        per_sm = ctx->tune_per_sm[id];
+    }
+    Shape2 s;
+    s.block = block;
+    s.grid = grid_for(work, block, ctx ? ctx->num_sms : 152, per_sm);
+    return s;
 }
 
 // pair build on caller-provided scratch (no allocation)

@@ -22,10 +22,7 @@ struct MlpDevice {
 static_assert(LUB_MLP_PARAMS == 128 * 12 + 128 + 128 * 128 + 128 + 4 * 128 + 4, "parameter count");
 static_assert(LUB_MLP_WORK_PER_SAMPLE == 6 * 128 + 2 * 4, "training scratch per sample");
 
-__global__ void k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-                            const int32_t *__restrict__ d_count, int32_t cap, MlpDevice M, double *__restrict__ n0,
-                            float *__restrict__ pq);
-int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj,
+int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi, const int32_t *pj,
                      const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st);
 size_t mlp_start_smem();
 int launch_mlp_features(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj, int n,

@@ -444,7 +444,8 @@ __device__ __forceinline__ V3<float> shifted_normal(const PView &P, int k, const
 // ---------------------------------------------------------------------------
 // the network's start normal for each pair of a tile (used by closest.cu)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, DView D, const int32_t *__restrict__ pi,
+template <bool ENS>
+__global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
                                                                 const int32_t *__restrict__ pj,
                                                                 const int32_t *__restrict__ d_count, int32_t cap,
                                                                 MlpDevice M, double *__restrict__ n0,
@@ -476,14 +477,17 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, DView 
         int i = -1, j = -1;
         float f[NI];
         bool ok = false;
+        const DView *Dp = &D0;
         if (k < count) {
             i = pi[k];
             j = pj[k];
-            ok = i >= 0 && i < P.n && j >= 0 && j < P.n && i != j && shape_ok(P.rpar[i], P.rperp[i]) &&
+            bool alien;
+            Dp = &pair_domain<ENS>(D0, E, i, j, &alien);
+            ok = !alien && i >= 0 && i < P.n && j >= 0 && j < P.n && i != j && shape_ok(P.rpar[i], P.rperp[i]) &&
                  shape_ok(P.rpar[j], P.rperp[j]);
         }
         if (ok) {
-            pair_features(P, D, i, j, S.mean, S.istd, f);
+            pair_features(P, *Dp, i, j, S.mean, S.istd, f);
             for (int a = 0; a < NI; ++a)
                 if (!isfinite(f[a])) ok = false;
         }
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, DView 
             V3<float> s0 = mk<float>(0, 0, 0);
             if (ok) {
                 // corrections to the parameters of the line-of-centres start
-                const V3<float> d = cvt<float>(min_image(D, sub(load_pos(P, j), load_pos(P, i))));
+                const V3<float> d = cvt<float>(min_image(*Dp, sub(load_pos(P, j), load_pos(P, i))));
                 const V3<float> e = normalized(d);
                 const V3<float> ni = shifted_normal(P, i, rot_of(P, i), e, y.x, y.y);
                 const V3<float> nj = shifted_normal(P, j, rot_of(P, j), scl(-1.0f, e), y.z, y.w);
@@ -517,22 +521,30 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, DView 
 
 size_t mlp_start_smem() { return sizeof(InfSmem); }
 
-int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const int32_t *pi, const int32_t *pj,
+template <bool ENS>
+int launch_mlp_start_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi,
+                       const int32_t *pj, const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st)
+{
+    const size_t smem = mlp_start_smem();
+    if (!(ctx->mlp_smem_set & (1 << ENS))) {
+        int rc = lub_check_cuda(
+            ctx, cudaFuncSetAttribute(k_mlp_start<ENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "shared memory attribute");
+        if (rc) return rc;
+        ctx->mlp_smem_set |= 1 << ENS;
+    }
+    k_mlp_start<ENS><<<ctx->num_sms * 2, 32 * INF_WARPS, smem, st>>>(P, D, E, pi, pj, d_count, cap,
+                                                                     *(const MlpDevice *)ctx->mlp, n0, pq);
+    return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_start launch");
+}
+
+int launch_mlp_start(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi, const int32_t *pj,
                      const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st)
 {
     if (!ctx->mlp_ready) return lub_set_error(ctx, LUB_ERR_ARG, "the learned warm start needs lub_mlp_set first");
     if (cap == 0) return LUB_OK;
-    const size_t smem = mlp_start_smem();
-    if (!ctx->mlp_smem_set) {
-        int rc = lub_check_cuda(
-            ctx, cudaFuncSetAttribute(k_mlp_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-            "shared memory attribute");
-        if (rc) return rc;
-        ctx->mlp_smem_set = true;
-    }
-    k_mlp_start<<<ctx->num_sms * 2, 32 * INF_WARPS, smem, st>>>(P, D, pi, pj, d_count, cap,
-                                                                  *(const MlpDevice *)ctx->mlp, n0, pq);
-    return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_start launch");
+    return E.nb ? launch_mlp_start_t<true>(ctx, P, D, E, pi, pj, d_count, cap, n0, pq, st)
+                : launch_mlp_start_t<false>(ctx, P, D, E, pi, pj, d_count, cap, n0, pq, st);
 }
 
 // ---------------------------------------------------------------------------

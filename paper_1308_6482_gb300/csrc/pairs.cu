@@ -18,6 +18,11 @@
 // The tests run in FP32 on cell-relative coordinates with a safety margin; a
 // test inside the margin is decided again in FP64 from the original double
 // positions, so every decision is the double-precision one.
+//
+// Ensemble mode: every suspension has its own cell grid (from its own box);
+// the grids are laid out back to back in one global cell index space
+// (cell_base of each suspension), so the same counting sort, sweeps and scan
+// run once over all suspensions, and no pair crosses two of them.
 #include <string.h>
 
 #include "lub_internal.cuh"
@@ -36,6 +41,33 @@ struct Grid {
     float rmax;    // bound of every particle's Rmax
 };
 
+// one suspension's grid in ensemble mode
+struct EnsGrid {
+    Grid G;
+    int32_t cell_base;
+    int32_t pad;
+};
+
+// grid, domain and first global cell of suspension b (references: G0 and D0
+// are __grid_constant__ kernel parameters, read in place)
+template <bool ENS>
+__device__ __forceinline__ const Grid &grid_ref(const Grid &G0, const EnsGrid *EG, int b)
+{
+    if (!ENS) return G0;
+    return EG[b].G;
+}
+template <bool ENS>
+__device__ __forceinline__ const DView &dom_ref(const DView &D0, const Ens &E, int b)
+{
+    if (!ENS) return D0;
+    return E.dom[b].D;
+}
+template <bool ENS>
+__device__ __forceinline__ int cell_base(const EnsGrid *EG, int b)
+{
+    return ENS ? __ldg(&EG[b].cell_base) : 0;
+}
+
 __device__ __forceinline__ double wrap_axis(double x, double L, double invL, int periodic)
 {
     return periodic ? x - L * floor(x * invL) : x;
@@ -49,14 +81,20 @@ __device__ __forceinline__ int cell_axis(double xw, double inv_cs, int nc)
     return (int)f;
 }
 
-__global__ void k_cells_count(PView P, DView D, Grid G, int32_t *__restrict__ cell_cnt, int32_t *__restrict__ cell_of,
+template <bool ENS>
+__global__ void k_cells_count(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
+                              int32_t *__restrict__ cell_cnt, int32_t *__restrict__ cell_of,
                               int32_t *__restrict__ slot, float rmax_bound, int32_t *__restrict__ flags)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const int b = ENS ? batch_of(E, i) : 0;
+        const Grid &G = grid_ref<ENS>(G0, EG, b);
+        const DView &D = dom_ref<ENS>(D0, E, b);
+        const int base = cell_base<ENS>(EG, b);
         const int cx = cell_axis(wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]), G.inv_cs[0], G.nc[0]);
         const int cy = cell_axis(wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]), G.inv_cs[1], G.nc[1]);
         const int cz = cell_axis(wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]), G.inv_cs[2], G.nc[2]);
-        const int c = (cz * G.nc[1] + cy) * G.nc[0] + cx;
+        const int c = base + (cz * G.nc[1] + cy) * G.nc[0] + cx;
         cell_of[i] = c;
         slot[i] = atomicAdd(cell_cnt + c, 1);
         const float rm = fmaxf(P.rpar[i], P.rperp[i]);
@@ -64,14 +102,21 @@ __global__ void k_cells_count(PView P, DView D, Grid G, int32_t *__restrict__ ce
     }
 }
 
-__global__ void k_cells_fill(PView P, DView D, Grid G, const int32_t *__restrict__ cell_start,
-                             const int32_t *__restrict__ cell_of, const int32_t *__restrict__ slot,
-                             int32_t *__restrict__ sorted, float4 *__restrict__ rec0, float4 *__restrict__ rec1,
-                             int32_t *__restrict__ cellc)
+template <bool ENS>
+__global__ void k_cells_fill(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
+                             const int32_t *__restrict__ cell_start, const int32_t *__restrict__ cell_of,
+                             const int32_t *__restrict__ slot, int32_t *__restrict__ sorted,
+                             float4 *__restrict__ rec0, float4 *__restrict__ rec1, int32_t *__restrict__ cellc,
+                             int32_t *__restrict__ sbat)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const int c = cell_of[i];
-        const int s = cell_start[c] + slot[i];
+        const int b = ENS ? batch_of(E, i) : 0;
+        const Grid &G = grid_ref<ENS>(G0, EG, b);
+        const DView &D = dom_ref<ENS>(D0, E, b);
+        const int base = cell_base<ENS>(EG, b);
+        const int cg = cell_of[i];
+        const int s = cell_start[cg] + slot[i];
+        const int c = cg - base;
         const int cx = c % G.nc[0], cy = (c / G.nc[0]) % G.nc[1], cz = c / (G.nc[0] * G.nc[1]);
         const double xw = wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]);
         const double yw = wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]);
@@ -79,6 +124,7 @@ __global__ void k_cells_fill(PView P, DView D, Grid G, const int32_t *__restrict
         const float rpar = P.rpar[i], rperp = P.rperp[i];
         const V3<float> o = quat_axis<float>(P.qw[i], P.qx[i], P.qy[i], P.qz[i]);
         sorted[s] = i;
+        if (ENS) sbat[s] = b;
         cellc[s] = cx | (cy << 10) | (cz << 20);  // nc <= 1024 per axis
         rec0[s] = make_float4((float)(xw - (cx + 0.5) * G.csd[0]), (float)(yw - (cy + 0.5) * G.csd[1]),
                               (float)(zw - (cz + 0.5) * G.csd[2]), fmaxf(rpar, rperp));
@@ -149,7 +195,7 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
                                           const int32_t *__restrict__ cell_start, const int32_t *__restrict__ sorted,
                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int s,
                                           const float4 a0, const float4 a1, int cx, int cy, int cz, int row,
-                                          double cutoff_d, Emit emit)
+                                          int cbase, double cutoff_d, Emit emit)
 {
     const int dy = row % 3 - 1, dz = row / 3 - 1;
     int yc = cy + dy, zc = cz + dz;
@@ -162,7 +208,7 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
         zc += zc < 0 ? G.nc[2] : -G.nc[2];
     }
     const float oy = dy * G.cs[1], oz = dz * G.cs[2];
-    const int rowbase = (zc * G.nc[1] + yc) * G.nc[0];
+    const int rowbase = cbase + (zc * G.nc[1] + yc) * G.nc[0];
     // skip neighbour cells no partner of particle s can reach: distance from
     // the particle to the cell's box against Rmax_s + Rmax + Delta_L
     const float reach = a0.w + G.rmax + G.cutoff + G.margin;
@@ -194,12 +240,14 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
 // tests the walls.  cnt: [0, N) particle-pair counts per particle (of the
 // smaller index of each pair), [N, 2N) wall-pair counts; cur: [0, N) write
 // cursors (zeroed).
-template <bool WRITE>
-__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, DView D, Grid G, const int32_t *__restrict__ cell_start,
+template <bool WRITE, bool ENS>
+__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
+                                                     const int32_t *__restrict__ cell_start,
                                                      const int32_t *__restrict__ sorted,
                                                      const float4 *__restrict__ rec0,
                                                      const float4 *__restrict__ rec1,
-                                                     const int32_t *__restrict__ cellc, int32_t *__restrict__ cnt,
+                                                     const int32_t *__restrict__ cellc,
+                                                     const int32_t *__restrict__ sbat, int32_t *__restrict__ cnt,
                                                      int32_t *__restrict__ cur, const int32_t *__restrict__ total,
                                                      int32_t cap, int32_t *__restrict__ pair_i,
                                                      int32_t *__restrict__ pair_j, double cutoff_d,
@@ -213,10 +261,14 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, DView D, Grid G, c
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < 9 * N; f += gridDim.x * blockDim.x) {
         const int s = f / 9, row = f - 9 * s;
         const int i = sorted[s];
+        const int b = ENS ? sbat[s] : 0;
+        const Grid &G = grid_ref<ENS>(G0, EG, b);
+        const DView &D = dom_ref<ENS>(D0, E, b);
+        const int base = cell_base<ENS>(EG, b);
         const float4 a0 = rec0[s], a1 = rec1[s];
         const int cc = cellc[s];
         const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
-        sweep_row(P, D, G, cell_start, sorted, rec0, rec1, s, a0, a1, cx, cy, cz, row, cutoff_d, [&](int t) {
+        sweep_row(P, D, G, cell_start, sorted, rec0, rec1, s, a0, a1, cx, cy, cz, row, base, cutoff_d, [&](int t) {
             const int j = sorted[t];
             const int lo = min(i, j), hi = max(i, j);
             if (!WRITE) {
@@ -322,13 +374,13 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
 }
 
 struct Layout {
-    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *cnt, *totals;
+    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals;
     float4 *rec0, *rec1;
     void *tmp;
     size_t tmp_bytes, total;
 };
 
-Layout layout(void *base, int64_t N, int64_t ncell)
+Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
 {
     const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((3 * N + 1) * 4);
     const size_t b_rec = align256(N * 16),
@@ -349,6 +401,8 @@ Layout layout(void *base, int64_t N, int64_t ncell)
     s += b_n;
     L.cellc = (int32_t *)s;
     s += b_n;
+    L.sbat = (int32_t *)s;  // suspension of each slot (ensemble mode only)
+    if (ens) s += b_n;
     L.cnt = (int32_t *)s;
     s += b_n2;
     L.rec0 = (float4 *)s;
@@ -362,13 +416,15 @@ Layout layout(void *base, int64_t N, int64_t ncell)
     return L;
 }
 
-// the build on a workspace; flags live in the workspace
-int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PView &P, const DView &D,
-               const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count,
-               cudaStream_t st)
+// the build on a workspace; flags live in the workspace.  G.ncell is the
+// total number of cells (all suspensions in ensemble mode).
+template <bool ENS>
+int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PView &P, const DView &D, const Ens &E,
+               const EnsGrid *EG, const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap,
+               int32_t *d_count, cudaStream_t st)
 {
     const int64_t N = P.n;
-    Layout L = layout(scratch, N, G.ncell);
+    Layout L = layout(scratch, N, G.ncell, ENS);
     // the scratch keeps earlier contents: clear what must start at zero
     int rc = lub_check_cuda(ctx, cudaMemsetAsync(L.flags, 0, 512, st), "memset flags");
     if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cell_cnt, 0, (G.ncell + 1) * 4, st), "memset cells");
@@ -376,19 +432,23 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     if (N == 0) return lub_check_cuda(ctx, cudaMemsetAsync(d_count, 0, 4, st), "memset count");
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 8);
-    k_cells_count<<<gn, block, 0, st>>>(P, D, G, L.cell_cnt, L.cell_of, L.slot, rmax, L.flags);
+    k_cells_count<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, rmax, L.flags);
     if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st))) return rc;
-    k_cells_fill<<<gn, block, 0, st>>>(P, D, G, L.cell_cnt, L.cell_of, L.slot, L.sorted, L.rec0, L.rec1, L.cellc);
+    k_cells_fill<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted, L.rec0, L.rec1,
+                                            L.cellc, L.sbat);
     // counts and write cursors start at zero
     if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (3 * N + 1) * 4, st), "memset counts"))) return rc;
     int32_t *cur = L.cnt + 2 * N + 1;
-    const int gs = grid_for(9 * N, 256, num_sms, 32);
-    k_pairs_sweep<false><<<gs, 256, 0, st>>>(P, D, G, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc, L.cnt, cur,
-                                             L.totals, cap, pi, pj, prm.list_cutoff, d_count);
+    Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, 9 * N);
+    if (!ctx) sw.grid = grid_for(9 * N, sw.block, num_sms, kTuneDefaults[LUB_TUNE_SWEEP].per_sm);
+    const int gs = sw.grid, bs = sw.block;
+    k_pairs_sweep<false, ENS><<<gs, bs, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
+                                                  L.sbat, L.cnt, cur, L.totals, cap, pi, pj, prm.list_cutoff,
+                                                  d_count);
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st))) return rc;
-    k_pairs_sweep<true><<<gs, 256, 0, st>>>(P, D, G, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc, L.cnt, cur,
-                                            L.totals, cap, pi, pj, prm.list_cutoff, d_count);
+    k_pairs_sweep<true, ENS><<<gs, bs, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
+                                                 L.sbat, L.cnt, cur, L.totals, cap, pi, pj, prm.list_cutoff, d_count);
     k_pairs_sort<<<grid_for(N, 256, num_sms, 8), 256, 0, st>>>((int32_t)N, L.cnt, L.totals, cap, pj);
     return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
 }
@@ -421,7 +481,8 @@ int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_p
     const size_t need = layout(nullptr, P.n, G.ncell).total;
     int rc = lub_ensure_scratch(ctx, need);
     if (rc) return rc;
-    rc = build_core(ctx, ctx->num_sms, ctx->scratch, G, P, D, prm, rmax, pi, pj, cap, d_count, st);
+    const Ens E = {nullptr, 0};
+    rc = build_core<false>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, nullptr, prm, rmax, pi, pj, cap, d_count, st);
     if (rc) return rc;
     // flags of this call for the host-count path
     return lub_check_cuda(ctx, cudaMemcpyAsync(ctx->d_flags, ctx->scratch, 4, cudaMemcpyDeviceToDevice, st),
@@ -444,5 +505,40 @@ int pairs_build_on_scratch(int num_sms, void *scratch, size_t scratch_bytes, int
     const Grid G = make_grid(D, prm, rmax, P.n, max_cells);
     if (G.ncell > max_cells) return LUB_ERR_ARG;
     if (layout(nullptr, P.n, G.ncell).total > scratch_bytes) return LUB_ERR_ARG;
-    return build_core(nullptr, num_sms, scratch, G, P, D, prm, rmax, pi, pj, cap, d_count, st);
+    const Ens E = {nullptr, 0};
+    return build_core<false>(nullptr, num_sms, scratch, G, P, D, E, nullptr, prm, rmax, pi, pj, cap, d_count, st);
+}
+
+// ---------------------------------------------------------------------------
+// ensemble form: one grid per suspension, back to back in the cell index space
+// ---------------------------------------------------------------------------
+int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DView *hdom, const int32_t *hoff,
+                           const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count,
+                           cudaStream_t st)
+{
+    std::vector<EnsGrid> tab((size_t)E.nb);
+    int64_t total = 0;
+    for (int b = 0; b < E.nb; ++b) {
+        memset(&tab[b], 0, sizeof(EnsGrid));
+        tab[b].G = make_grid(hdom[b], prm, rmax, (int64_t)hoff[b + 1] - hoff[b], (int64_t)1 << 40);
+        tab[b].cell_base = (int32_t)total;
+        total += tab[b].G.ncell;
+        if (total > ((int64_t)1 << 30))
+            return lub_set_error(ctx, LUB_ERR_ARG, "the ensemble's cell grids exceed 2^30 cells");
+    }
+    const void *dev = nullptr;
+    int rc = lub_upload_table(ctx, 1, tab.data(), tab.size() * sizeof(EnsGrid), st, &dev);
+    if (rc) return rc;
+    Grid G;
+    memset(&G, 0, sizeof(G));
+    G.ncell = total;
+    DView D;
+    memset(&D, 0, sizeof(D));
+    const size_t need = layout(nullptr, P.n, total, true).total;
+    if ((rc = lub_ensure_scratch(ctx, need))) return rc;
+    rc = build_core<true>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, (const EnsGrid *)dev, prm, rmax, pi, pj, cap,
+                          d_count, st);
+    if (rc) return rc;
+    return lub_check_cuda(ctx, cudaMemcpyAsync(ctx->d_flags, ctx->scratch, 4, cudaMemcpyDeviceToDevice, st),
+                          "copy flags");
 }

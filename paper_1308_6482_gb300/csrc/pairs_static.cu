@@ -70,6 +70,7 @@ extern "C" int lub_pairs_build_static(const lub_particles *p, const lub_domain *
     if (!p || !d || !prm || !d_count) return LUB_ERR_ARG;
     if (capacity < 0 || (capacity > 0 && (!pair_i || !pair_j))) return LUB_ERR_ARG;
     if (p->n < 0) return LUB_ERR_ARG;
+    if (p->batch_offsets) return LUB_ERR_ARG;  // one suspension only
     if ((int64_t)p->n > kMaxParticles) return LUB_ERR_LIMIT;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->qw || !p->qx || !p->qy || !p->qz || !p->r_par || !p->r_perp))
         return LUB_ERR_ARG;

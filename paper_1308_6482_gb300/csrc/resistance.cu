@@ -74,8 +74,8 @@ __device__ __forceinline__ void m_rot(T c, T s, T a0, T a1, T a2, T a3, T m[4])
     m[3] = a0 * s2 * s + a1 * c * s2 + a2 * c2 * s + a3 * c2 * c;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_resistance(PView P, DView D, RParams R, const int32_t *__restrict__ pi,
+template <typename T, bool ENS>
+__global__ void __launch_bounds__(128) k_resistance(PView P, const __grid_constant__ DView D0, Ens E, RParams R, const int32_t *__restrict__ pi,
                                                     const int32_t *__restrict__ pj,
                                                     const int32_t *__restrict__ d_count, int32_t cap,
                                                     const double *__restrict__ nin, const double *__restrict__ gap,
@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(128) k_resistance(PView P, DView D, RParams R,
 #pragma unroll
         for (int a = 0; a < 12; ++a) out[a] = T(0);
         // indices are checked here too: status may not come from lub_closest_points
-        if (i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
+        bool alien;
+        const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+        if (alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
         bool skip = (st & (LUB_ST_NOCONV | LUB_ST_DEGENERATE)) != 0;
         if (!skip && R.h_c <= 0.0 && h <= 0.0) {
             st |= LUB_ST_OVERLAP;
@@ -238,19 +240,28 @@ __global__ void __launch_bounds__(128) k_resistance(PView P, DView D, RParams R,
 
 }  // namespace
 
-int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const lub_params &prm, const int32_t *pi,
-                      const int32_t *pj, const int32_t *d_count, int32_t cap, const double *n, const double *gap,
-                      uint8_t *status, void *FT, void *lever, cudaStream_t st)
+int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, const double *n,
+                      const double *gap, uint8_t *status, void *FT, void *lever, cudaStream_t st)
 {
     if (cap == 0) return LUB_OK;
     RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c};
-    const int block = 128;
-    const int grid = grid_for(cap, block, ctx->num_sms, 8);
-    if (prm.precision == LUB_MIXED)
-        k_resistance<float><<<grid, block, 0, st>>>(P, D, R, pi, pj, d_count, cap, n, gap, status, (float *)FT,
-                                                    (float *)lever);
-    else
-        k_resistance<double><<<grid, block, 0, st>>>(P, D, R, pi, pj, d_count, cap, n, gap, status, (double *)FT,
-                                                     (double *)lever);
+    const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
+    const bool ens = E.nb > 0;
+    if (prm.precision == LUB_MIXED) {
+        if (ens)
+            k_resistance<float, true><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+                                                                    (float *)FT, (float *)lever);
+        else
+            k_resistance<float, false><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+                                                                     (float *)FT, (float *)lever);
+    } else {
+        if (ens)
+            k_resistance<double, true><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap,
+                                                                     status, (double *)FT, (double *)lever);
+        else
+            k_resistance<double, false><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap,
+                                                                      status, (double *)FT, (double *)lever);
+    }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance launch");
 }
