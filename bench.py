@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain warm-start comparison")
     ap.add_argument("--learned-pairs", type=int, default=1 << 20)
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble workload")
+    ap.add_argument("--ens-n", type=int, default=256, help="suspensions in the ensemble workload")
+    ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--fp64-switch", type=float, default=1e-3,
                     help="h/a below which pairs get the FP64 Newton refinement (0: none)")
@@ -304,6 +307,8 @@ def run_ours(args):
     }
     if not args.no_learned:
         out["learned_vs_plain"] = learned_vs_plain(args, dev, stream, flush)
+    if not args.no_ensemble and ws == 1:
+        out["ensemble"] = ensemble_bench(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(parts, dom)
     if rank == 0:
@@ -371,10 +376,122 @@ def learned_vs_plain(args, dev, stream, flush, steps=20, warmup=3):
     return out
 
 
+def rigid_motion(P, g, sig_r=0.01, sig_t=0.005):
+    """Move every particle by a seeded random rigid motion: dr ~ N(0, sig_r^2)
+    per axis, a rotation by a vector ~ N(0, sig_t^2) per axis (torch ops on the
+    device; input preparation between steps, not part of the step)."""
+    import torch
+    n = P.n
+    dev = P.t["x"].device
+    for k in ("x", "y", "z"):
+        P.t[k] += sig_r * torch.randn(n, generator=g, device=dev, dtype=torch.float64)
+    th = sig_t * torch.randn((3, n), generator=g, device=dev, dtype=torch.float32)
+    a = th.norm(dim=0)
+    s = torch.where(a > 0, torch.sin(0.5 * a) / torch.where(a > 0, a, torch.ones_like(a)), 0.5 * torch.ones_like(a))
+    dw, dx, dy, dz = torch.cos(0.5 * a), s * th[0], s * th[1], s * th[2]
+    w, x, y, z = (P.t[k].clone() for k in ("qw", "qx", "qy", "qz"))
+    nw = dw * w - dx * x - dy * y - dz * z
+    nx = dw * x + dx * w + dy * z - dz * y
+    ny = dw * y - dx * z + dy * w + dz * x
+    nz = dw * z + dx * y - dy * x + dz * w
+    inv = torch.rsqrt(nw * nw + nx * nx + ny * ny + nz * nz)
+    for k, v in (("qw", nw), ("qx", nx), ("qy", ny), ("qz", nz)):
+        P.t[k].copy_(v * inv)
+
+
+def ensemble_bench(args, dev, stream, flush):
+    """Batched ensemble: args.ens_n independent periodic suspensions of mixed
+    spheroids (aspect ratio log-uniform [1/3, 3], phi uniform [0.1, 0.35],
+    pair counts log-uniform [1e3, 2e5]) stepped together: one CUDA graph per
+    step (the four calls, one launch per stage for all suspensions), launch
+    shapes from the autotuner, every particle moved by a small seeded rigid
+    motion between steps.  Against it: the same suspensions stepped one by one
+    with their own calls (a few steps)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1308_6482_gb300 as lub
+
+    t0 = time.perf_counter()
+    sus, meta = gen.ensemble(n_susp=args.ens_n, seed=4)
+    t_gen = time.perf_counter() - t0
+    parts, doms, off = lub.make_ensemble(sus)
+    rmax = float(max(parts["r_par"].max(), parts["r_perp"].max())) + 0.05
+    P = lub.DeviceParticles(parts, dev, max_semi_axis=rmax, batch_offsets=off)
+    prm = lub.default_params(precision="mixed")
+    pl = lub.Pipeline(P, doms, prm, capacity=1024, device=dev)
+    npairs = pl.build_pairs()
+    pl._alloc(int(npairs * 1.3) + 4096, dev)
+    pl.build_pairs()
+    with torch.cuda.stream(stream):
+        t1 = time.perf_counter()
+        shapes = pl.autotune(reps=2, stream=stream)
+        t_tune = time.perf_counter() - t1
+        pl.step(stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        pl.step(stream=stream)
+    stream.synchronize()
+    g = torch.Generator(device=dev)
+    g.manual_seed(12345)
+    K = args.ens_steps
+    counts = torch.zeros(K, dtype=torch.int32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            rigid_motion(P, g)
+            graph.replay()
+        for k in range(K):
+            rigid_motion(P, g)
+            flush.zero_()
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+            counts[k].copy_(pl.d_count[0])
+    stream.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    cnt = counts.cpu().numpy().astype(np.float64)
+    over = int((cnt > pl.cap).sum())
+    # the same suspensions one by one: their own calls, eager (a few steps)
+    sep = [lub.Pipeline(lub.DeviceParticles(p, dev), d, prm, device=dev) for p, d in sus]
+    for q in sep:
+        q.build_pairs()
+    Ks = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for q in sep:
+            q.step(stream=stream)
+        flush.zero_()
+        e0.record(stream)
+        for _ in range(Ks):
+            for q in sep:
+                q.step(stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    sep_ms = e0.elapsed_time(e1) / Ks
+    sep_pairs = float(sum(q.count() for q in sep))
+    return {
+        "workload": "%d periodic suspensions, phi uniform [0.1,0.35], aspect ratio log-uniform [1/3,3], pair "
+                    "counts log-uniform [1e3,2e5]; %d particles, %d steps of seeded rigid motions "
+                    "(dr ~ N(0,0.01^2), dtheta ~ N(0,0.005^2))" % (args.ens_n, P.n, K),
+        "pairs_per_step_mean": float(cnt.mean()), "ms_per_step": float(ms.mean()),
+        "pairs_per_s": float(cnt.sum() / (ms.sum() * 1e-3)), "capacity_overflows": over,
+        "launch": "one CUDA graph per step, one persistent launch per stage for all suspensions",
+        "autotuned_shapes": {k: list(v) for k, v in shapes.items()}, "autotune_s": t_tune,
+        "generation_s": t_gen,
+        "separate_calls": {"ms_per_step": sep_ms, "pairs_per_s": sep_pairs / (sep_ms * 1e-3),
+                           "launches_per_step": "13 per suspension, eager"},
+        "speedup_vs_separate": float((cnt.sum() / (ms.sum() * 1e-3)) / (sep_pairs / (sep_ms * 1e-3))),
+    }
+
+
 def kernels_in_step(precision):
-    # lub_pairs_build: cells count, 3 scan, cells fill, count sweep, 2 x 3 scan, write sweep, total = 14
-    # lub_closest_points 1, lub_resistance 1, lub_apply (atomic) 1
-    return 17
+    # lub_pairs_build: cells count, scan (2 kernels), cells fill, count sweep, scan (2), write sweep, sort = 8;
+    # lub_closest_points: the FP32 stage and the FP64 work list (mixed) or one FP64 kernel;
+    # lub_resistance 1; lub_apply (atomic) 1.  Memsets are not counted.
+    return 8 + (2 if precision == "mixed" else 1) + 1 + 1
 
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):

@@ -229,5 +229,71 @@ def pair_stream(P, seed=3, kind="mixed", gap_range=(1e-4, 1.0), gap_scale="absol
     return parts, dom, a.astype(np.int32), b.astype(np.int32)
 
 
+def aspect_shapes(N, rng):
+    """Spheroids with aspect ratio log-uniform in [1/3, 3], equivalent radius 4.5."""
+    lam = np.exp(rng.uniform(np.log(1 / 3), np.log(3.0), N))
+    return np.stack([4.5 * lam ** (2.0 / 3.0), 4.5 * lam ** (-1.0 / 3.0)], 1).astype(np.float32)
+
+
+def tile_periodic(parts, dom, k, rng):
+    """k x k x k copies of a periodic suspension side by side: again a periodic
+    suspension (of k^3 times the size), whose pairs across copy boundaries are
+    the periodic-image pairs of the original.  Velocities are drawn afresh."""
+    if k == 1:
+        return parts, dom
+    L = np.asarray(dom["L"], np.float64)
+    n = len(parts["x"])
+    sh = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), -1).reshape(-1, 3)
+    out = {}
+    for a, key in enumerate(("x", "y", "z")):
+        out[key] = (np.asarray(parts[key])[None, :] + (sh[:, a] * L[a])[:, None]).reshape(-1)
+    for key in ("qw", "qx", "qy", "qz", "r_par", "r_perp"):
+        out[key] = np.tile(np.asarray(parts[key]), k ** 3)
+    velocities(out, rng)
+    d = dict(dom)
+    d["L"] = tuple(float(v) * k for v in L)
+    return out, d
+
+
+# pairs per particle of attached suspensions (attach_prob 0.9, list cut-off 1)
+# at volume fraction phi, fitted on spheroids of aspect ratio 1/3..3
+def _pairs_per_particle(phi):
+    return 1.29 + 4.9 * (phi - 0.1)
+
+
+def ensemble_member(args):
+    """One suspension of the ensemble workload: (seed, phi, target pairs) ->
+    (parts, dom), an attached RSA base of 128..1024 spheroids tiled k^3 times."""
+    seed, phi, target = args
+    rng = np.random.default_rng(seed)
+    n_all = target / _pairs_per_particle(phi)
+    k = max(1, int(np.ceil((n_all / 1024.0) ** (1.0 / 3.0))))
+    n0 = int(max(128, round(n_all / k ** 3)))
+    sh = aspect_shapes(n0, rng)
+    vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
+    L = (vol / phi) ** (1.0 / 3.0)
+    parts, dom = suspension(sh, (L, L, L), attach_prob=0.9, seed=seed, max_attempts=400000)
+    return tile_periodic(parts, dom, k, rng)
+
+
+def ensemble(n_susp=256, seed=4, phi_range=(0.1, 0.35), pairs_range=(1e3, 2e5), processes=None):
+    """Independent periodic suspensions of mixed spheroids (aspect ratio
+    log-uniform in [1/3, 3]) at volume fractions uniform in phi_range, sized
+    for pair counts log-uniform in pairs_range.  Returns ([(parts, dom)], meta).
+    Built in a spawn process pool (safe after CUDA has started)."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(phi_range[0], phi_range[1], n_susp)
+    target = np.exp(rng.uniform(np.log(pairs_range[0]), np.log(pairs_range[1]), n_susp))
+    jobs = [(int(seed) * 100003 + b, float(phi[b]), float(target[b])) for b in range(n_susp)]
+    procs = processes if processes is not None else min(16, os.cpu_count() or 1)
+    if procs > 1:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            sus = pool.map(ensemble_member, jobs, chunksize=1)
+    else:
+        sus = [ensemble_member(j) for j in jobs]
+    return sus, dict(phi=phi, target_pairs=target)
+
+
 def subset(parts, idx):
     return {k: np.asarray(v)[idx].copy() for k, v in parts.items()}

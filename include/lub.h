@@ -349,7 +349,7 @@ int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, co
  * default.  lub_set_launch_shape with block = blocks_per_sm = 0 restores it;
  * otherwise block must be one of the kernel's candidates (a multiple of 32 up
  * to its limit: 128 for the closest-point and resistance kernels, 32 for the
- * FP64 work list, 256 for lub_apply and the sweeps) and 1 <= blocks_per_sm <= 64. */
+ * FP64 work list, 256 for lub_apply and the sweeps) and 1 <= blocks_per_sm <= 256. */
 int lub_get_launch_shape(const lub_ctx *ctx, int32_t kernel, int32_t *block, int32_t *blocks_per_sm);
 int lub_set_launch_shape(lub_ctx *ctx, int32_t kernel, int32_t block, int32_t blocks_per_sm);
 

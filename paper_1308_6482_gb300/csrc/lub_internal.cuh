@@ -338,12 +338,15 @@ struct Shape2 {
 struct TuneDefault {
     int block, per_sm, max_block;
 };
+// defaults: grids large enough that the hardware block scheduler, not the
+// grid-stride loop, balances the uneven per-pair work (Newton iteration
+// counts, FP64 refinement) on large inputs
 constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
-    {128, 8, 128},   // LUB_TUNE_CLOSEST_MIXED
-    {32, 16, 32},    // LUB_TUNE_CLOSEST_REFINE
-    {128, 8, 128},   // LUB_TUNE_CLOSEST_FP64
-    {128, 8, 128},   // LUB_TUNE_RESISTANCE
-    {256, 8, 256},   // LUB_TUNE_APPLY
+    {128, 64, 128},  // LUB_TUNE_CLOSEST_MIXED
+    {32, 64, 32},    // LUB_TUNE_CLOSEST_REFINE
+    {128, 64, 128},  // LUB_TUNE_CLOSEST_FP64
+    {128, 64, 128},  // LUB_TUNE_RESISTANCE
+    {256, 32, 256},  // LUB_TUNE_APPLY
     {256, 32, 256},  // LUB_TUNE_SWEEP
 };
 inline Shape2 tuned_shape(const lub_ctx *ctx, int id, int64_t work)

@@ -12,7 +12,7 @@
 
 namespace {
 
-const int kBlocksPerSm[] = {1, 2, 4, 8, 16, 32, 64};
+const int kBlocksPerSm[] = {2, 4, 8, 16, 32, 64, 128, 256};
 
 bool valid_block(int id, int block)
 {
@@ -49,7 +49,7 @@ int lub_set_launch_shape(lub_ctx *ctx, int32_t kernel, int32_t block, int32_t bl
         ctx->tune_per_sm[kernel] = 0;
         return LUB_OK;
     }
-    if (!valid_block(kernel, block) || blocks_per_sm < 1 || blocks_per_sm > 64)
+    if (!valid_block(kernel, block) || blocks_per_sm < 1 || blocks_per_sm > 256)
         return lub_set_error(ctx, LUB_ERR_ARG, "shape (%d, %d) not allowed for kernel %d", block, blocks_per_sm,
                              kernel);
     ctx->tune_block[kernel] = block;
@@ -106,7 +106,7 @@ int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, co
         int bb = 0, bp = 0;
         for (int block : blocks_of(id)) {
             for (int per_sm : kBlocksPerSm) {
-                if (block * per_sm > 2048 * 4) continue;  // far beyond residency: same as a smaller grid
+                if (block * per_sm > 32768) continue;  // 16 waves of resident threads: as good as any larger grid
                 ctx->tune_block[id] = block;
                 ctx->tune_per_sm[id] = per_sm;
                 if ((rc = run(id))) break;  // warm-up
