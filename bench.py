@@ -488,10 +488,10 @@ def ensemble_bench(args, dev, stream, flush):
 
 
 def kernels_in_step(precision):
-    # lub_pairs_build: cells count, scan (2 kernels), cells fill, count sweep, scan (2), write sweep, sort = 8;
+    # lub_pairs_build: cells count, scan, cells fill, sweep, scan, compaction = 6;
     # lub_closest_points: the FP32 stage and the FP64 work list (mixed) or one FP64 kernel;
     # lub_resistance 1; lub_apply (atomic) 1.  Memsets are not counted.
-    return 8 + (2 if precision == "mixed" else 1) + 1 + 1
+    return 6 + (2 if precision == "mixed" else 1) + 1 + 1
 
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):

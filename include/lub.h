@@ -167,9 +167,14 @@ const char *lub_last_error(const lub_ctx *ctx);
  *
  * Order: particle pairs by (i, j) ascending, then wall pairs by (i, w).
  * Writes pair_i[k], pair_j[k] for k < min(count, capacity) and *d_count =
- * count (device int32).  If count > capacity the listed content is
- * unspecified and the call returns LUB_ERR_CAPACITY when h_count_or_null is
- * given (host int32, receives count; the call then synchronises `stream`).
+ * count (device int32).  The arrays also serve as the overflow store of the
+ * build (pairs beyond 16 per particle, kept at their tail while it runs), so
+ * the call needs capacity >= count + overflow entries, which is count for
+ * any ordinary suspension; when that does not hold, *d_count receives the
+ * sum (> capacity), the listed content is unspecified and the call returns
+ * LUB_ERR_CAPACITY when h_count_or_null is given (host int32, receives that
+ * required capacity; the call then synchronises `stream`).  A bounded wait
+ * inside the build that times out gives LUB_ERR_TIMEOUT on that path.
  * Without h_count_or_null the call does not synchronise (unless
  * max_semi_axis is 0) and overflow is visible only through *d_count.
  * Periodic axes need L >= 2 (2 Rmax + Delta_L) (else LUB_ERR_ARG).
@@ -316,7 +321,7 @@ int lub_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, floa
  */
 #define LUB_STATIC_MAX_PARTICLES 65536
 #define LUB_STATIC_MAX_CELLS     262144
-#define LUB_STATIC_SCRATCH_BYTES 5767168
+#define LUB_STATIC_SCRATCH_BYTES 9437184
 int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const lub_params *prm,
                            int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count,
                            void *stream);

@@ -293,6 +293,8 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
         if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(&flags, ctx->d_flags, 4, cudaMemcpyDeviceToHost, st), "copy flags");
         if (!rc) rc = lub_check_cuda(ctx, cudaStreamSynchronize(st), "sync");
         if (rc) return rc;
+        if (flags & 4)
+            return lub_set_error(ctx, LUB_ERR_TIMEOUT, "a bounded wait of the scan timed out");
         if (flags & 1)
             return lub_set_error(ctx, LUB_ERR_ARG, "a semi-axis exceeds max_semi_axis = %g (or is not finite)", rmax);
         if (*h_count_or_null > capacity)

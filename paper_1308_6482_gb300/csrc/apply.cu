@@ -192,7 +192,7 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
     const int block = 256;
     const int gp = grid_for(cap > 0 ? cap : 1, block, ctx->num_sms, 8);
     k_inc_count<<<gp, block, 0, st>>>(pi, pj, d_count, cap, n, cnt);
-    rc = scan_exclusive(ctx, cnt, n, tot, tmp, b_tmp, st);
+    rc = scan_exclusive(ctx, cnt, n, tot, tmp, b_tmp, st, nullptr);
     if (rc) return rc;
     k_inc_fill<<<gp, block, 0, st>>>(pi, pj, d_count, cap, n, cnt, fill, inc);
     const int gn = grid_for(n, block, ctx->num_sms, 8);

@@ -318,8 +318,9 @@ int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DVi
 int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_t st);
 
 // device-wide exclusive scan of n int32 values (in place), total -> *d_total
+// (one launch; a bounded wait that times out sets bit 2 (value 4) of *err)
 int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, void *tmp, size_t tmp_bytes,
-                   cudaStream_t st);
+                   cudaStream_t st, int32_t *err = nullptr);
 size_t scan_tmp_bytes(int64_t n);
 
 inline int grid_for(int64_t work, int block, int num_sms, int per_sm = 16)

@@ -4,17 +4,19 @@
 //      in the cell (atomic), scan of the cell counts, copy of every particle
 //      into cell order as two float4 records: position relative to its cell
 //      centre with Rmax, and symmetry axis with e = R_par^2 - R_perp^2;
-//   2. count sweep: one thread per (particle, row of three neighbour cells),
-//      nine rows per particle, particles in cell order so neighbouring
-//      threads read the same cells; each unordered pair is visited once, by
-//      the particle earlier in cell order, and counted (atomically) for the
-//      smaller of its two indices; the row-0 thread tests the plane walls;
-//      one scan over [particle-pair counts | wall-pair counts] gives every
+//   2. sweep: one thread per (particle, row of three neighbour cells), nine
+//      rows per particle, particles in cell order so neighbouring threads
+//      read the same cells; each unordered pair is visited once, by the
+//      particle earlier in cell order, and stored for the smaller of its two
+//      indices in that particle's row of KSLOT slots (atomic slot index); the
+//      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
+//      caller's pair arrays; the row-0 thread tests the plane walls;
+//   3. one scan over [particle-pair counts | wall-pair counts] gives every
 //      offset (wall pairs land after all particle pairs);
-//   3. write sweep: the same sweep writes each pair at its particle's offset
-//      plus an atomic cursor;
-//   4. each particle's partners are sorted in place, giving the canonical
-//      (i, j) order.
+//   4. compaction: each particle sorts its partners (canonical (i, j) order)
+//      and writes them, and its wall pairs, at its offsets.
+// The pair arrays must hold the pairs plus the overflow entries; the count
+// reports their sum when it does not fit (a capacity error, as for the pairs).
 // The tests run in FP32 on cell-relative coordinates with a safety margin; a
 // test inside the margin is decided again in FP64 from the original double
 // positions, so every decision is the double-precision one.
@@ -40,6 +42,9 @@ struct Grid {
     float margin;  // absolute FP32 error allowance of the tests
     float rmax;    // bound of every particle's Rmax
 };
+
+// partner slots per particle in the sweep; more go to the overflow list
+constexpr int KSLOT = 16;
 
 // one suspension's grid in ensemble mode
 struct EnsGrid {
@@ -236,28 +241,26 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
     }
 }
 
-// One thread per (particle slot s in cell order, row); the row-0 thread also
-// tests the walls.  cnt: [0, N) particle-pair counts per particle (of the
-// smaller index of each pair), [N, 2N) wall-pair counts; cur: [0, N) write
-// cursors (zeroed).
-template <bool WRITE, bool ENS>
-__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
+// One thread per (slot s in cell order, row); the row-0 thread also tests the
+// walls.  cnt: [0, N) pair counts per particle (of the smaller index of each
+// pair), [N, 2N) wall-pair counts; slots [N][KSLOT]; wall bits per particle;
+// overflow entry o at pair_i/pair_j[cap - 1 - o].
+template <bool ENS>
+__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
+                                                     const __grid_constant__ Grid G0, Ens E,
+                                                     const EnsGrid *__restrict__ EG,
                                                      const int32_t *__restrict__ cell_start,
                                                      const int32_t *__restrict__ sorted,
                                                      const float4 *__restrict__ rec0,
                                                      const float4 *__restrict__ rec1,
                                                      const int32_t *__restrict__ cellc,
                                                      const int32_t *__restrict__ sbat, int32_t *__restrict__ cnt,
-                                                     int32_t *__restrict__ cur, const int32_t *__restrict__ total,
-                                                     int32_t cap, int32_t *__restrict__ pair_i,
-                                                     int32_t *__restrict__ pair_j, double cutoff_d,
-                                                     int32_t *__restrict__ d_count)
+                                                     int32_t *__restrict__ slots, uint8_t *__restrict__ wbits,
+                                                     int32_t *__restrict__ ovf_n, int32_t cap,
+                                                     int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
+                                                     double cutoff_d)
 {
     const int N = P.n;
-    if (WRITE) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *d_count = *total;
-        if (*total > cap) return;
-    }
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < 9 * N; f += gridDim.x * blockDim.x) {
         const int s = f / 9, row = f - 9 * s;
         const int i = sorted[s];
@@ -271,52 +274,108 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_const
         sweep_row(P, D, G, cell_start, sorted, rec0, rec1, s, a0, a1, cx, cy, cz, row, base, cutoff_d, [&](int t) {
             const int j = sorted[t];
             const int lo = min(i, j), hi = max(i, j);
-            if (!WRITE) {
-                atomicAdd(cnt + lo, 1);
+            const int q = atomicAdd(cnt + lo, 1);
+            if (q < KSLOT) {
+                slots[(size_t)lo * KSLOT + q] = hi;
             } else {
-                const int pos = cnt[lo] + atomicAdd(cur + lo, 1);
-                pair_i[pos] = lo;
-                pair_j[pos] = hi;
+                const int o = atomicAdd(ovf_n, 1);
+                if (o < cap) {
+                    pair_i[cap - 1 - o] = lo;
+                    pair_j[cap - 1 - o] = hi;
+                }
             }
         });
         if (row == 0) {
             // plane walls (exact double gap)
-            int wf = 0;
-            const int wbase = WRITE ? cnt[N + i] : 0;
+            int wf = 0, bits = 0;
             for (int ww = 0; ww < D.n_walls; ++ww) {
                 const Shape<double> si = load_shape<double>(P, i);
                 const double hw =
                     (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0));
                 if (hw < cutoff_d) {
-                    if (WRITE) {
-                        pair_i[wbase + wf] = i;
-                        pair_j[wbase + wf] = -1 - ww;
-                    }
+                    bits |= 1 << ww;
                     ++wf;
                 }
             }
-            if (!WRITE) cnt[N + i] = wf;
+            cnt[N + i] = wf;
+            wbits[i] = (uint8_t)bits;
         }
     }
 }
 
-// canonical order: sort the partners of each particle in place
-__global__ void __launch_bounds__(256) k_pairs_sort(int32_t n, const int32_t *__restrict__ cnt,
-                                                    const int32_t *__restrict__ total, int32_t cap,
-                                                    int32_t *__restrict__ pair_j)
+// Canonical order: each particle's partners, sorted, then its wall pairs, at
+// the offsets of the scan (off = the scanned counts, off[2N] = the total).
+// The count is the total, or total + overflow entries when they do not fit.
+__global__ void __launch_bounds__(256) k_pairs_compact(int32_t n, const int32_t *__restrict__ off,
+                                                       const int32_t *__restrict__ slots,
+                                                       const uint8_t *__restrict__ wbits,
+                                                       const int32_t *__restrict__ ovf_n, int32_t cap,
+                                                       int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
+                                                       int32_t *__restrict__ d_count)
 {
-    if (*total > cap) return;
+    const int total = off[2 * n];
+    const int novf = *ovf_n;
+    const int64_t need = (int64_t)total + novf;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *d_count = need > cap ? (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX) : total;
+    if (need > cap) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int b = cnt[i], e = cnt[i + 1];
-        for (int a = b + 1; a < e; ++a) {
-            const int v = pair_j[a];
-            int q = a - 1;
-            while (q >= b && pair_j[q] > v) {
-                pair_j[q + 1] = pair_j[q];
-                --q;
+        const int b = off[i], m = off[i + 1] - b;
+        if (m <= KSLOT) {
+            // sort in registers: compare-exchange passes (m is small, mostly 0..4)
+            int v[KSLOT];
+#pragma unroll
+            for (int q = 0; q < KSLOT; ++q) v[q] = q < m ? slots[(size_t)i * KSLOT + q] : INT32_MAX;
+            if (m > 1) {
+#pragma unroll
+                for (int q = 1; q < KSLOT; ++q) {
+                    if (q >= m) break;
+#pragma unroll
+                    for (int r = q; r > 0; --r) {
+                        const int x = v[r - 1], y = v[r];
+                        v[r - 1] = min(x, y);
+                        v[r] = max(x, y);
+                    }
+                }
             }
-            pair_j[q + 1] = v;
+#pragma unroll
+            for (int q = 0; q < KSLOT; ++q)
+                if (q < m) {
+                    pair_i[b + q] = i;
+                    pair_j[b + q] = v[q];
+                }
+        } else {
+            // the slots, then this particle's overflow entries, then sort in place
+            for (int q = 0; q < KSLOT; ++q) {
+                pair_i[b + q] = i;
+                pair_j[b + q] = slots[(size_t)i * KSLOT + q];
+            }
+            int c = KSLOT;
+            for (int o = 0; o < novf && c < m; ++o)
+                if (pair_i[cap - 1 - o] == i) {
+                    pair_j[b + c] = pair_j[cap - 1 - o];
+                    pair_i[b + c] = i;
+                    ++c;
+                }
+            for (int a = b + 1; a < b + m; ++a) {
+                const int x = pair_j[a];
+                int q = a - 1;
+                while (q >= b && pair_j[q] > x) {
+                    pair_j[q + 1] = pair_j[q];
+                    --q;
+                }
+                pair_j[q + 1] = x;
+            }
         }
+        const int wb = off[n + i];
+        const int bits = wbits[i];
+        int c = 0;
+        for (int w = 0; w < 2; ++w)
+            if (bits & (1 << w)) {
+                pair_i[wb + c] = i;
+                pair_j[wb + c] = -1 - w;
+                ++c;
+            }
     }
 }
 
@@ -374,7 +433,8 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
 }
 
 struct Layout {
-    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals;
+    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
+    uint8_t *wbits;
     float4 *rec0, *rec1;
     void *tmp;
     size_t tmp_bytes, total;
@@ -382,14 +442,15 @@ struct Layout {
 
 Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
 {
-    const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((3 * N + 1) * 4);
+    const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((2 * N + 1) * 4);
+    const size_t b_slots = align256((size_t)N * KSLOT * 4), b_bits = align256((size_t)N + 1);
     const size_t b_rec = align256(N * 16),
                  b_tmp = align256(scan_tmp_bytes(ncell + 1 > 2 * N + 1 ? ncell + 1 : 2 * N + 1));
     Layout L;
     char *s = (char *)base;
     L.flags = (int32_t *)s;
     s += 256;
-    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells
+    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries
     s += 256;
     L.cell_cnt = (int32_t *)s;
     s += b_cell;
@@ -405,6 +466,10 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     if (ens) s += b_n;
     L.cnt = (int32_t *)s;
     s += b_n2;
+    L.slots = (int32_t *)s;
+    s += b_slots;
+    L.wbits = (uint8_t *)s;
+    s += b_bits;
     L.rec0 = (float4 *)s;
     s += b_rec;
     L.rec1 = (float4 *)s;
@@ -433,23 +498,20 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 8);
     k_cells_count<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, rmax, L.flags);
-    if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st))) return rc;
+    if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st, L.flags))) return rc;
     k_cells_fill<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted, L.rec0, L.rec1,
                                             L.cellc, L.sbat);
-    // counts and write cursors start at zero
-    if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (3 * N + 1) * 4, st), "memset counts"))) return rc;
-    int32_t *cur = L.cnt + 2 * N + 1;
+    // counts start at zero (the overflow counter too: totals[2], cleared with the flags)
+    if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (2 * N + 1) * 4, st), "memset counts"))) return rc;
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, 9 * N);
     if (!ctx) sw.grid = grid_for(9 * N, sw.block, num_sms, kTuneDefaults[LUB_TUNE_SWEEP].per_sm);
-    const int gs = sw.grid, bs = sw.block;
-    k_pairs_sweep<false, ENS><<<gs, bs, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
-                                                  L.sbat, L.cnt, cur, L.totals, cap, pi, pj, prm.list_cutoff,
-                                                  d_count);
+    k_pairs_sweep<ENS><<<sw.grid, sw.block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
+                                                     L.sbat, L.cnt, L.slots, L.wbits, L.totals + 2, cap, pi, pj,
+                                                     prm.list_cutoff);
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
-    if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st))) return rc;
-    k_pairs_sweep<true, ENS><<<gs, bs, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
-                                                 L.sbat, L.cnt, cur, L.totals, cap, pi, pj, prm.list_cutoff, d_count);
-    k_pairs_sort<<<grid_for(N, 256, num_sms, 8), 256, 0, st>>>((int32_t)N, L.cnt, L.totals, cap, pj);
+    if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags))) return rc;
+    k_pairs_compact<<<grid_for(N, 256, num_sms, 16), 256, 0, st>>>((int32_t)N, L.cnt, L.slots, L.wbits,
+                                                                   L.totals + 2, cap, pi, pj, d_count);
     return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
 }
 

@@ -1,9 +1,14 @@
-// Device-wide exclusive prefix sum of int32 values, in place, in two
-// launches: (1) per-tile sums; (2) each tile adds the sums of the tiles
-// before it (read directly: there are few tiles) and scans itself; the last
-// tile writes the total.  Used for the cell grid and the per-particle pair
-// counts of the pair builder and for the incidence lists of the
-// deterministic force sum.
+// Device-wide exclusive prefix sum of int32 values, in place, in one launch:
+// a single pass with decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016).  Each block takes
+// the next tile by an atomic ticket (so it only ever waits on tiles whose
+// blocks are already running), scans it, publishes the tile total, looks back
+// over the published totals of earlier tiles until one publishes its
+// inclusive prefix, and publishes its own.  Every wait is bounded: on timeout
+// the block sets bit 2 of *err and carries on with what it has (the host
+// reports LUB_ERR_TIMEOUT where it reads the flags).  Used for the cell grid
+// and the per-particle pair counts of the pair builder and for the incidence
+// lists of the deterministic force sum.
 #include "lub_internal.cuh"
 
 namespace {
@@ -11,6 +16,9 @@ namespace {
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned long long ST_AGG = 1ull << 32;     // tile total published
+constexpr unsigned long long ST_PREFIX = 2ull << 32;  // inclusive prefix published
+constexpr long kSpinLimit = 1l << 22;                 // ~0.3 s of 64 ns naps
 
 // exclusive block scan of one value per thread; returns the block total
 __device__ __forceinline__ int block_exclusive(int v, int &total)
@@ -37,40 +45,26 @@ __device__ __forceinline__ int block_exclusive(int v, int &total)
     __syncthreads();
     const int warp_off = wid ? warp_tot[wid - 1] : 0;
     total = warp_tot[SCAN_THREADS / 32 - 1];
-    __syncthreads();
     return warp_off + x - v;
 }
 
-__device__ __forceinline__ int block_sum(int v)
+__device__ __forceinline__ unsigned long long load_state(const unsigned long long *p)
 {
-    int tot;
-    block_exclusive(v, tot);
-    return tot;
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_sums(const int32_t *__restrict__ a, int64_t n,
-                                                            int32_t *__restrict__ sums)
+// state: [0] ticket counter, [1 ..] one word per tile (zeroed before the launch)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restrict__ a, int64_t n,
+                                                                unsigned long long *__restrict__ state,
+                                                                int32_t *__restrict__ d_total,
+                                                                int32_t *__restrict__ err)
 {
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    int s = 0;
-#pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        const int64_t idx = base + (int64_t)q * SCAN_THREADS + threadIdx.x;  // coalesced
-        if (idx < n) s += a[idx];
-    }
-    const int tot = block_sum(s);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(int32_t *__restrict__ a, int64_t n,
-                                                            const int32_t *__restrict__ sums,
-                                                            int32_t *__restrict__ d_total)
-{
-    // prefix of this tile: sum of the tile sums before it
-    int pre = 0;
-    for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_THREADS) pre += sums[t];
-    pre = block_sum(pre);
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    __shared__ int tile_s, prefix_s;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(state, 1ull);
+    __syncthreads();
+    const int tile = tile_s;
+    unsigned long long *tstate = state + 1;
+    const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
     int s = 0;
 #pragma unroll
@@ -79,32 +73,63 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(int32_t *__restrict_
         s += v[q];
     }
     int tot;
-    int off = block_exclusive(s, tot) + pre;
+    const int off = block_exclusive(s, tot);
+    if (threadIdx.x == 0) {
+        int excl = 0;
+        if (tile == 0) {
+            __threadfence();
+            atomicExch(tstate, ST_PREFIX | (unsigned)tot);
+        } else {
+            __threadfence();
+            atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
+            long spins = 0;
+            for (int p = tile - 1; p >= 0;) {
+                const unsigned long long w = load_state(tstate + p);
+                const unsigned long long flag = w & ~0xffffffffull;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        if (err) atomicOr(err, 4);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                excl += (int)(unsigned)(w & 0xffffffffull);
+                if (flag == ST_PREFIX) break;
+                --p;
+            }
+            __threadfence();
+            atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
+        }
+        prefix_s = excl;
+        if (d_total && (int64_t)(tile + 1) * SCAN_TILE >= n) *d_total = excl + tot;
+    }
+    __syncthreads();
+    int run = prefix_s + off;
 #pragma unroll
     for (int q = 0; q < SCAN_ITEMS; ++q) {
-        if (base + q < n) a[base + q] = off;
-        off += v[q];
+        if (base + q < n) a[base + q] = run;
+        run += v[q];
     }
-    if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_total = pre + tot;
+}
+
+int64_t tiles_of(int64_t n)
+{
+    const int64_t t = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return t < 1 ? 1 : t;
 }
 
 }  // namespace
 
-size_t scan_tmp_bytes(int64_t n)
-{
-    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb < 1) nb = 1;
-    return (size_t)nb * sizeof(int32_t);
-}
+size_t scan_tmp_bytes(int64_t n) { return (size_t)(tiles_of(n) + 1) * sizeof(unsigned long long); }
 
 int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, void *tmp, size_t tmp_bytes,
-                   cudaStream_t st)
+                   cudaStream_t st, int32_t *err)
 {
     if (tmp_bytes < scan_tmp_bytes(n)) return lub_set_error(ctx, LUB_ERR_ARG, "scan: temp too small");
-    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb < 1) nb = 1;
-    int32_t *sums = (int32_t *)tmp;
-    k_tile_sums<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, sums);
-    k_tile_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, sums, d_total);
+    const int64_t nt = tiles_of(n);
+    int rc = lub_check_cuda(ctx, cudaMemsetAsync(tmp, 0, scan_tmp_bytes(n), st), "scan state");
+    if (rc) return rc;
+    k_scan_lookback<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(data, n, (unsigned long long *)tmp, d_total, err);
     return lub_check_cuda(ctx, cudaGetLastError(), "scan launch");
 }

@@ -170,6 +170,47 @@ def test_capacity_overflow_reports_required_count():
     np.testing.assert_array_equal(pl.results()["pi"], pi)
 
 
+def crowded_particle(n_around=30):
+    """Particle 0 (the lowest index, so every pair counts for it) with
+    n_around small spheres at gap 0.5 around it: more partners than the
+    builder's per-particle slots, so the overflow path runs."""
+    rng = np.random.default_rng(5)
+    k = np.arange(n_around) + 0.5
+    th = np.arccos(1 - 2 * k / n_around)
+    ph = np.pi * (1 + 5 ** 0.5) * k
+    u = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    c = np.array([50.0, 50.0, 50.0])
+    pos = np.vstack([c, c + (3.0 + 0.5 + 1.0) * u])
+    n = len(pos)
+    r = np.r_[3.0, np.full(n_around, 1.0)].astype(np.float32)
+    q = gen.random_quaternions(n, rng)
+    parts = dict(x=pos[:, 0].copy(), y=pos[:, 1].copy(), z=pos[:, 2].copy(), qw=q[:, 0].copy(), qx=q[:, 1].copy(),
+                 qy=q[:, 2].copy(), qz=q[:, 3].copy(), r_par=r, r_perp=r.copy())
+    gen.velocities(parts, rng)
+    return parts, dict(L=(100.0, 100.0, 100.0), periodic=(True, True, True), walls=[])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_more_partners_than_slots(prec):
+    import paper_1308_6482_gb300 as lub
+    parts, dom = crowded_particle()
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert np.sum(pi == 0) > 16
+    g = run_gpu(parts, dom, prec)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
+    # the overflow entries need room in the arrays while the build runs: the
+    # required capacity reported is the pairs plus those entries
+    pl = lub.Pipeline(parts, dom, lub.default_params(), capacity=len(pi))
+    rc, need = lub.lub_pairs_build(pl.ctx.h, pl.P.c, pl.D, pl.prm, pl.pair_i, pl.pair_j, pl.cap, pl.d_count,
+                                   h_count=True)
+    assert rc == lub.LUB_ERR_CAPACITY and need == len(pi) + (np.sum(pi == 0) - 16)
+    pl2 = lub.Pipeline(parts, dom, lub.default_params(), capacity=need)
+    assert pl2.build_pairs() == len(pi)
+    np.testing.assert_array_equal(pl2.results()["pj"], pj)
+
+
 def test_degenerate_pairs_are_flagged_not_faulted():
     import torch
     parts, dom, pi, pj = gen.pair_stream(8, seed=47, kind="aspect", gap_range=(1e-3, 0.1))
