@@ -139,6 +139,32 @@ def dist_setup():
     return ws, rank, local
 
 
+def aggregate(ms_per_step, units, ws, device):
+    """Whole-job figures of independent replicas: the slowest rank's time per
+    step (max over ranks) and the units all ranks processed (sum).  Identity
+    for one rank; any torch.distributed backend (NCCL on the GPUs, gloo in the
+    CPU tests)."""
+    if ws <= 1:
+        return float(ms_per_step), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_per_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
+def rank_seed(rank):
+    """Each rank steps its own suspension: the workload seed of rank r."""
+    return 2 + 1000 * rank
+
+
+def ensemble_shard(n_susp, ws, rank):
+    """Suspensions of the ensemble run by `rank` of `ws`: s with s mod ws == rank."""
+    return list(range(rank, n_susp, ws))
+
+
 def make_workload(n, seed):
     import gen
     return gen.config_mixed_suspension(N=n, phi=0.3, seed=seed)
@@ -156,7 +182,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    parts, dom = make_workload(args.n, 2 + 1000 * rank)
+    parts, dom = make_workload(args.n, rank_seed(rank))
     prm = lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch)
     pl = lub.Pipeline(parts, dom, prm, device=dev)
     npairs = pl.build_pairs()              # sizes capacity and the context scratch
@@ -276,16 +302,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms}
 
     # max over ranks
-    ms_per_step = total_ms / args.steps
-    pairs_all = npairs
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_per_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-        c = torch.tensor([float(npairs)], device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        pairs_all = float(c.item())
+    ms_per_step, pairs_all = aggregate(total_ms / args.steps, npairs, ws, dev)
     value = pairs_all / (ms_per_step * 1e-3)
 
     pk = peaks()
@@ -307,8 +324,8 @@ def run_ours(args):
     }
     if not args.no_learned:
         out["learned_vs_plain"] = learned_vs_plain(args, dev, stream, flush)
-    if not args.no_ensemble and ws == 1:
-        out["ensemble"] = ensemble_bench(args, dev, stream, flush)
+    if not args.no_ensemble:
+        out["ensemble"] = ensemble_bench(args, dev, stream, flush, ws, rank)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(parts, dom)
     if rank == 0:
@@ -399,14 +416,15 @@ def rigid_motion(P, g, sig_r=0.01, sig_t=0.005):
         P.t[k].copy_(v * inv)
 
 
-def ensemble_bench(args, dev, stream, flush):
+def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     """Batched ensemble: args.ens_n independent periodic suspensions of mixed
     spheroids (aspect ratio log-uniform [1/3, 3], phi uniform [0.1, 0.35],
     pair counts log-uniform [1e3, 2e5]) stepped together: one CUDA graph per
     step (the four calls, one launch per stage for all suspensions), launch
     shapes from the autotuner, every particle moved by a small seeded rigid
     motion between steps.  Against it: the same suspensions stepped one by one
-    with their own calls (a few steps)."""
+    with their own calls (a few steps).  Under torchrun the suspensions shard
+    over the ranks (suspension s on rank s mod N, no exchange)."""
     import numpy as np
     import torch
 
@@ -415,6 +433,7 @@ def ensemble_bench(args, dev, stream, flush):
 
     t0 = time.perf_counter()
     sus, meta = gen.ensemble(n_susp=args.ens_n, seed=4)
+    sus = [sus[b] for b in ensemble_shard(len(sus), ws, rank)]
     t_gen = time.perf_counter() - t0
     parts, doms, off = lub.make_ensemble(sus)
     rmax = float(max(parts["r_par"].max(), parts["r_perp"].max())) + 0.05
@@ -472,18 +491,20 @@ def ensemble_bench(args, dev, stream, flush):
     stream.synchronize()
     sep_ms = e0.elapsed_time(e1) / Ks
     sep_pairs = float(sum(q.count() for q in sep))
+    step_ms, all_pairs = aggregate(float(ms.mean()), float(cnt.mean()), ws, dev)
+    sep_ms, sep_pairs = aggregate(sep_ms, sep_pairs, ws, dev)
     return {
         "workload": "%d periodic suspensions, phi uniform [0.1,0.35], aspect ratio log-uniform [1/3,3], pair "
                     "counts log-uniform [1e3,2e5]; %d particles, %d steps of seeded rigid motions "
                     "(dr ~ N(0,0.01^2), dtheta ~ N(0,0.005^2))" % (args.ens_n, P.n, K),
-        "pairs_per_step_mean": float(cnt.mean()), "ms_per_step": float(ms.mean()),
-        "pairs_per_s": float(cnt.sum() / (ms.sum() * 1e-3)), "capacity_overflows": over,
+        "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
+        "pairs_per_s": all_pairs / (step_ms * 1e-3), "capacity_overflows": over, "ranks": ws,
         "launch": "one CUDA graph per step, one persistent launch per stage for all suspensions",
         "autotuned_shapes": {k: list(v) for k, v in shapes.items()}, "autotune_s": t_tune,
         "generation_s": t_gen,
         "separate_calls": {"ms_per_step": sep_ms, "pairs_per_s": sep_pairs / (sep_ms * 1e-3),
                            "launches_per_step": "13 per suspension, eager"},
-        "speedup_vs_separate": float((cnt.sum() / (ms.sum() * 1e-3)) / (sep_pairs / (sep_ms * 1e-3))),
+        "speedup_vs_separate": float((all_pairs / step_ms) / (sep_pairs / sep_ms)),
     }
 
 
