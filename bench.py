@@ -423,13 +423,16 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     step (the four calls, one launch per stage for all suspensions), launch
     shapes from the autotuner, every particle moved by a small seeded rigid
     motion between steps.  Against it: the same suspensions stepped one by one
-    with their own calls (a few steps).  Under torchrun the suspensions shard
+    with their own calls (a few steps), and the same ensemble with the two warm
+    starts of the closest-point solve (temporal: the previous step's normals
+    carried over; learned: the network).  Under torchrun the suspensions shard
     over the ranks (suspension s on rank s mod N, no exchange)."""
     import numpy as np
     import torch
 
     import gen
     import paper_1308_6482_gb300 as lub
+    from paper_1308_6482_gb300.mlp import WarmStartMLP
 
     t0 = time.perf_counter()
     sus, meta = gen.ensemble(n_susp=args.ens_n, seed=4)
@@ -437,43 +440,74 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     t_gen = time.perf_counter() - t0
     parts, doms, off = lub.make_ensemble(sus)
     rmax = float(max(parts["r_par"].max(), parts["r_perp"].max())) + 0.05
-    P = lub.DeviceParticles(parts, dev, max_semi_axis=rmax, batch_offsets=off)
-    prm = lub.default_params(precision="mixed")
-    pl = lub.Pipeline(P, doms, prm, capacity=1024, device=dev)
-    npairs = pl.build_pairs()
-    pl._alloc(int(npairs * 1.3) + 4096, dev)
-    pl.build_pairs()
-    with torch.cuda.stream(stream):
-        t1 = time.perf_counter()
-        shapes = pl.autotune(reps=2, stream=stream)
-        t_tune = time.perf_counter() - t1
-        pl.step(stream=stream)
-    stream.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        pl.step(stream=stream)
-    stream.synchronize()
-    g = torch.Generator(device=dev)
-    g.manual_seed(12345)
-    K = args.ens_steps
-    counts = torch.zeros(K, dtype=torch.int32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            rigid_motion(P, g)
-            graph.replay()
-        for k in range(K):
-            rigid_motion(P, g)
-            flush.zero_()
-            ev[k][0].record(stream)
-            graph.replay()
-            ev[k][1].record(stream)
-            counts[k].copy_(pl.d_count[0])
-    stream.synchronize()
-    ms = np.array([a.elapsed_time(b) for a, b in ev])
-    cnt = counts.cpu().numpy().astype(np.float64)
-    over = int((cnt > pl.cap).sum())
+    net = WarmStartMLP.load(device=dev)
+
+    def run(warm, steps, tune=False, shapes=None, precision="mixed"):
+        """`steps` graph-replayed steps from the initial poses, the same seeded
+        motions for every form; returns (ms [steps], pairs [steps], Newton
+        iterations per pair, capacity overflows, the context's shapes)."""
+        P = lub.DeviceParticles(parts, dev, max_semi_axis=rmax, batch_offsets=off)
+        prm = lub.default_params(precision=precision, warm_start=warm)
+        pl = lub.Pipeline(P, doms, prm, capacity=1024, device=dev)
+        if warm == lub.LUB_WARM_MLP:
+            net.install(pl.ctx)
+        if shapes:
+            for q, (blk, per) in enumerate(shapes):
+                lub.lub_set_launch_shape(pl.ctx.h, q, blk, per)
+        npairs = pl.build_pairs()
+        pl._alloc(int(npairs * 1.3) + 4096, dev)
+        pl.build_pairs()
+        with torch.cuda.stream(stream):
+            if tune:
+                pl.autotune(reps=2, stream=stream)
+            pl.step(stream=stream)
+            pl.step(stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            pl.step(stream=stream)
+        stream.synchronize()
+        g = torch.Generator(device=dev)
+        g.manual_seed(12345)
+        counts = torch.zeros(steps, dtype=torch.int32, device=dev)
+        its = torch.zeros(steps, dtype=torch.float64, device=dev)
+        idx = torch.arange(pl.cap, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                rigid_motion(P, g)
+                graph.replay()
+            for k in range(steps):
+                rigid_motion(P, g)
+                flush.zero_()
+                ev[k][0].record(stream)
+                graph.replay()
+                ev[k][1].record(stream)
+                counts[k].copy_(pl.d_count[0])
+                m = torch.clamp(pl.d_count[0], max=pl.cap)
+                its[k] = (pl.iters.double() * (idx < m)).sum() / m
+        stream.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        cnt = counts.cpu().numpy().astype(np.float64)
+        sh = [lub.lub_get_launch_shape(pl.ctx.h, q) for q in range(lub.LUB_TUNE_COUNT)]
+        return ms, cnt, float(its.mean().item()), int((cnt > pl.cap).sum()), sh
+
+    t1 = time.perf_counter()
+    ms, cnt, it_plain, over, shapes = run(lub.LUB_WARM_NONE, args.ens_steps, tune=True)
+    t_run = time.perf_counter() - t1
+    warm_forms = {}
+    for prec in ("mixed", "fp64"):
+        for name, warm in (("plain", lub.LUB_WARM_NONE), ("temporal", lub.LUB_WARM_PREVIOUS),
+                           ("learned", lub.LUB_WARM_MLP)):
+            if prec == "mixed" and name == "plain":
+                continue
+            steps_w = max(10, args.ens_steps // (4 if prec == "mixed" else 10))
+            msw, cntw, itw, _, _ = run(warm, steps_w, shapes=shapes, precision=prec)
+            wms, wpairs = aggregate(float(msw.mean()), float(cntw.mean()), ws, dev)
+            warm_forms["%s_%s" % (name, prec)] = {"ms_per_step": wms, "pairs_per_s": wpairs / (wms * 1e-3),
+                                                  "newton_iters_per_pair": itw, "steps": len(msw)}
     # the same suspensions one by one: their own calls, eager (a few steps)
+    prm = lub.default_params(precision="mixed")
     sep = [lub.Pipeline(lub.DeviceParticles(p, dev), d, prm, device=dev) for p, d in sus]
     for q in sep:
         q.build_pairs()
@@ -493,17 +527,20 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     sep_pairs = float(sum(q.count() for q in sep))
     step_ms, all_pairs = aggregate(float(ms.mean()), float(cnt.mean()), ws, dev)
     sep_ms, sep_pairs = aggregate(sep_ms, sep_pairs, ws, dev)
+    n_all = aggregate(0.0, float(len(parts["x"])), ws, dev)[1]
     return {
         "workload": "%d periodic suspensions, phi uniform [0.1,0.35], aspect ratio log-uniform [1/3,3], pair "
                     "counts log-uniform [1e3,2e5]; %d particles, %d steps of seeded rigid motions "
-                    "(dr ~ N(0,0.01^2), dtheta ~ N(0,0.005^2))" % (args.ens_n, P.n, K),
-        "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
-        "pairs_per_s": all_pairs / (step_ms * 1e-3), "capacity_overflows": over, "ranks": ws,
+                    "(dr ~ N(0,0.01^2), dtheta ~ N(0,0.005^2))" % (args.ens_n, int(n_all), args.ens_steps),
+        "precision": "mixed", "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
+        "pairs_per_s": all_pairs / (step_ms * 1e-3), "newton_iters_per_pair": it_plain,
+        "capacity_overflows": over, "ranks": ws,
         "launch": "one CUDA graph per step, one persistent launch per stage for all suspensions",
-        "autotuned_shapes": {k: list(v) for k, v in shapes.items()}, "autotune_s": t_tune,
-        "generation_s": t_gen,
+        "autotuned_shapes": {lub.TUNE_NAMES[q]: list(v) for q, v in enumerate(shapes)},
+        "autotune_and_run_s": t_run, "generation_s": t_gen,
+        "warm_starts": warm_forms,
         "separate_calls": {"ms_per_step": sep_ms, "pairs_per_s": sep_pairs / (sep_ms * 1e-3),
-                           "launches_per_step": "13 per suspension, eager"},
+                           "launches_per_step": "10 per suspension, eager"},
         "speedup_vs_separate": float((all_pairs / step_ms) / (sep_pairs / sep_ms)),
     }
 

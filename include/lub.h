@@ -326,6 +326,24 @@ int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const 
                            int32_t *pair_i, int32_t *pair_j, int32_t capacity, int32_t *d_count,
                            void *stream);
 
+/*
+ * Temporal warm start (Sec. III A: the paper starts each time step's
+ * closest-point search from the previous step's solution).  For every pair
+ * of the current list, copies into n [3][capacity] the normal that the
+ * previous list (prev_i, prev_j, prev_n [3][prev_capacity], *prev_count
+ * pairs, device) holds for the same pair (i, j) or wall pair (i, w), and
+ * zero where the pair is new; lub_closest_points with warm_start =
+ * LUB_WARM_PREVIOUS then starts Newton there (a zero or far-side start falls
+ * back to the line of centres).  Both lists must be in the canonical order of
+ * lub_pairs_build and index particles below n_particles; the current list
+ * must not alias the previous one.  Works unchanged on ensemble lists (global
+ * indices).  Asynchronous; context scratch of 8 bytes per particle (the
+ * range of each particle's pairs in the previous list).
+ */
+int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, const int32_t *prev_j,
+                      const double *prev_n, const int32_t *prev_count, int32_t prev_capacity, const int32_t *pair_i,
+                      const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Launch-shape autotuner (no counterpart in the paper).  The tunable kernels
  * are persistent grid-stride loops; their shape is (threads per block, blocks

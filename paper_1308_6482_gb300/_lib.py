@@ -67,7 +67,7 @@ class lub_params(ctypes.Structure):
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
-           "lub_get_launch_shape", "lub_set_launch_shape")
+           "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals")
 
 _lib = None
 
@@ -120,6 +120,8 @@ def load_library():
     lib.lub_autotune.restype = ctypes.c_int
     lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
                                  vp, vp, vp, vp, i32, vp]
+    lib.lub_carry_normals.restype = ctypes.c_int
+    lib.lub_carry_normals.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     lib.lub_get_launch_shape.restype = ctypes.c_int
     lib.lub_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32)]
     lib.lub_set_launch_shape.restype = ctypes.c_int
@@ -263,6 +265,14 @@ def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_cou
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
         _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
         _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_carry_normals(ctx, n_particles, prev_i, prev_j, prev_n, prev_count, prev_capacity, pair_i, pair_j, d_count,
+                      capacity, n, stream=None):
+    return _check(ctx, load_library().lub_carry_normals(
+        ctx, int(n_particles), _ptr(prev_i), _ptr(prev_j), _ptr(prev_n), _ptr(prev_count), int(prev_capacity),
+        _ptr(pair_i),
+        _ptr(pair_j), _ptr(d_count), int(capacity), _ptr(n), _stream(stream)))
 
 
 def lub_get_launch_shape(ctx, kernel):
@@ -430,6 +440,27 @@ class Pipeline:
         lub_apply(self.ctx.h, self.pair_i, self.pair_j, self.d_count, self.cap, self.FT, self.lever, self.n,
                   self.force, self.torque, self.prm.precision, accumulate, deterministic, stream=stream)
 
+    def keep_previous(self, stream=None):
+        """Copy this step's pair list and normals aside for the temporal warm start."""
+        torch = self.torch
+        cur = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(cur):
+            if getattr(self, "prev_cap", None) != self.cap:
+                self.prev_i = torch.empty_like(self.pair_i)
+                self.prev_j = torch.empty_like(self.pair_j)
+                self.prev_n = torch.empty_like(self.nrm)
+                self.prev_count = torch.zeros_like(self.d_count)
+                self.prev_cap = self.cap
+            self.prev_i.copy_(self.pair_i)
+            self.prev_j.copy_(self.pair_j)
+            self.prev_n.copy_(self.nrm)
+            self.prev_count.copy_(self.d_count)
+
+    def carry(self, stream=None):
+        """Start normals from the previous step's list (lub_carry_normals)."""
+        lub_carry_normals(self.ctx.h, self.n, self.prev_i, self.prev_j, self.prev_n, self.prev_count, self.prev_cap,
+                          self.pair_i, self.pair_j, self.d_count, self.cap, self.nrm, stream)
+
     def autotune(self, reps=3, stream=None):
         """Pick the launch shapes of this step's kernels (lub_autotune); returns them by name."""
         lub_autotune(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.cap, self.d_count,
@@ -438,11 +469,19 @@ class Pipeline:
         return {TUNE_NAMES[k]: lub_get_launch_shape(self.ctx.h, k) for k in range(LUB_TUNE_COUNT)}
 
     def step(self, build=True, deterministic=0, sync_count=False, stream=None):
+        """One correction step.  With warm_start = LUB_WARM_PREVIOUS the
+        normals are carried over from the step before (keep_previous is
+        called at the end of every step)."""
+        temporal = self.prm.warm_start == LUB_WARM_PREVIOUS
         if build:
             self.build_pairs(sync_count=sync_count, grow=sync_count, stream=stream)
+        if temporal and getattr(self, "prev_cap", None) == self.cap:
+            self.carry(stream)
         self.closest(stream)
         self.resistance(stream)
         self.apply(deterministic=deterministic, stream=stream)
+        if temporal:
+            self.keep_previous(stream)
 
     # host views (synchronising)
     def count(self):

@@ -358,6 +358,22 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
                         deterministic, (cudaStream_t)stream);
 }
 
+int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, const int32_t *prev_j,
+                      const double *prev_n, const int32_t *prev_count, int32_t prev_capacity, const int32_t *pair_i,
+                      const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if (n_particles < 0) return lub_set_error(ctx, LUB_ERR_ARG, "n_particles < 0");
+    if ((rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity))) return rc;
+    if (prev_capacity < 0 || !prev_count || (prev_capacity > 0 && (!prev_i || !prev_j || !prev_n)))
+        return lub_set_error(ctx, LUB_ERR_ARG, "bad previous pair list");
+    if (capacity > 0 && !n) return lub_set_error(ctx, LUB_ERR_ARG, "n is NULL");
+    return launch_carry_normals(ctx, n_particles, prev_i, prev_j, prev_n, prev_count, prev_capacity, pair_i, pair_j,
+                                d_count, capacity, n, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------
 // learned warm start
 // ---------------------------------------------------------------------------

@@ -406,7 +406,115 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
 }
 
+// Temporal warm start: the previous list's normal of the same pair.  Both
+// lists are canonical (particle pairs by (i, j), then wall pairs by (i, w)).
+// First pass: the range of every particle's pairs in the previous list's
+// particle segment (rng[i] = (begin, end), zero = none); second pass: each
+// pair searches its particle's range (a few entries), wall pairs the wall
+// segment by binary search.
+
+// index of the previous list's first wall pair (pj < 0 from there on)
+__device__ __forceinline__ int wall_segment(const int32_t *__restrict__ qj, int mq)
+{
+    int lo = 0, hi = mq;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(qj + mid) >= 0)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_carry_ranges(const int32_t *__restrict__ qi, const int32_t *__restrict__ qj,
+                                                      const int32_t *__restrict__ q_count, int32_t qcap, int32_t n,
+                                                      int2 *__restrict__ rng)
+{
+    __shared__ int seg_s;
+    const int mq = pair_count(q_count, qcap);
+    if (threadIdx.x == 0) seg_s = wall_segment(qj, mq);
+    __syncthreads();
+    const int seg = seg_s;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < seg; k += gridDim.x * blockDim.x) {
+        const int i = qi[k];
+        if (i < 0 || i >= n) continue;
+        if (k == 0 || qi[k - 1] != i) rng[i].x = k;
+        if (k == seg - 1 || qi[k + 1] != i) rng[i].y = k + 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_carry_normals(const int32_t *__restrict__ qi, const int32_t *__restrict__ qj,
+                                                       const double *__restrict__ qn,
+                                                       const int32_t *__restrict__ q_count, int32_t qcap,
+                                                       const int2 *__restrict__ rng, int32_t n_particles,
+                                                       const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                       const int32_t *__restrict__ d_count, int32_t cap,
+                                                       double *__restrict__ n)
+{
+    __shared__ int seg_s;
+    const int mq = pair_count(q_count, qcap);
+    if (threadIdx.x == 0) seg_s = wall_segment(qj, mq);
+    __syncthreads();
+    const int seg = seg_s;
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap, QC = (size_t)qcap;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int i = pi[k], j = pj[k];
+        int hit = -1;
+        if (i >= 0 && i < n_particles) {
+            if (j >= 0) {
+                const int2 r = rng[i];
+                for (int q = r.x; q < r.y; ++q)
+                    if (__ldg(qj + q) == j) {
+                        hit = q;
+                        break;
+                    }
+            } else {
+                // wall pairs by (i, w): key i * 4 + w
+                const int64_t key = (int64_t)i * 4 + (-1 - j);
+                int lo = seg, hi = mq;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int64_t km = (int64_t)__ldg(qi + mid) * 4 + (-1 - __ldg(qj + mid));
+                    if (km < key)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (lo < mq && __ldg(qi + lo) == i && __ldg(qj + lo) == j) hit = lo;
+            }
+        }
+        double x = 0.0, y = 0.0, z = 0.0;
+        if (hit >= 0) {
+            x = qn[hit];
+            y = qn[QC + hit];
+            z = qn[2 * QC + hit];
+        }
+        n[k] = x;
+        n[C + k] = y;
+        n[2 * C + k] = z;
+    }
+}
+
 }  // namespace
+
+int launch_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *qi, const int32_t *qj, const double *qn,
+                         const int32_t *q_count, int32_t qcap, const int32_t *pi, const int32_t *pj,
+                         const int32_t *d_count, int32_t cap, double *n, cudaStream_t st)
+{
+    if (cap == 0) return LUB_OK;
+    const size_t bytes = (size_t)(n_particles > 0 ? n_particles : 1) * sizeof(int2);
+    int rc = lub_ensure_scratch(ctx, bytes);
+    if (rc) return rc;
+    int2 *rng = (int2 *)ctx->scratch;
+    if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(rng, 0, bytes, st), "memset ranges"))) return rc;
+    if (qcap > 0)
+        k_carry_ranges<<<grid_for(qcap, 256, ctx->num_sms, 16), 256, 0, st>>>(qi, qj, q_count, qcap, n_particles, rng);
+    k_carry_normals<<<grid_for(cap, 256, ctx->num_sms, 16), 256, 0, st>>>(qi, qj, qn, q_count, qcap, rng, n_particles,
+                                                                          pi, pj, d_count, cap, n);
+    return lub_check_cuda(ctx, cudaGetLastError(), "carry launch");
+}
 
 int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                    const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,

@@ -399,6 +399,7 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
     // in the 27 neighbour cells
     const double range = (2.0 * (double)rmax + prm.list_cutoff) * (1.0 + 1e-9);
     Grid G;
+    memset(&G, 0, sizeof(G));  // padding too: grid tables are compared bytewise
     for (int a = 0; a < 3; ++a) {
         int nc = (int)floor(D.L[a] / range);
         if (nc < 1) nc = 1;
