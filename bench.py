@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--form", default="calls", choices=["fused", "calls"],
+                    help="fused: pair build + lub_correct; calls: pair build + the three per-pair calls")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain warm-start comparison")
@@ -191,9 +193,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    fused = args.form == "fused"
     # eager step once: per-call launch accounting and results for the work counts
     with torch.cuda.stream(stream):
-        pl.step(stream=stream)
+        pl.step(fused=fused, stream=stream)
     stream.synchronize()
     res = pl.results()
     mean_it = float(np.mean(res["iters"]))
@@ -204,16 +207,20 @@ def run_ours(args):
     if not args.no_graph:
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            pl.step(stream=stream)
+            pl.step(fused=fused, stream=stream)
         stream.synchronize()
 
-    calls = ("pairs_build", "closest", "resistance", "apply")
+    calls = ("pairs_build", "correct") if fused else ("pairs_build", "closest", "resistance", "apply")
 
     def step_timed(evs):
-        # per-call events (used for the roofline) around the four calls
+        # per-call events (used for the roofline) around the calls
         evs[0].record(stream)
         pl.build_pairs(sync_count=False, grow=False, stream=stream)
         evs[1].record(stream)
+        if fused:
+            pl.correct(stream=stream)
+            evs[2].record(stream)
+            return
         pl.closest(stream=stream)
         evs[2].record(stream)
         pl.resistance(stream=stream)
@@ -227,7 +234,7 @@ def run_ours(args):
             if graph is not None:
                 graph.replay()
             else:
-                pl.step(stream=stream)
+                pl.step(fused=fused, stream=stream)
     stream.synchronize()
 
     # timed region: K steps of the graph, L2 flushed between steps
@@ -248,7 +255,7 @@ def run_ours(args):
             if graph is not None:
                 graph.replay()
             else:
-                pl.step(stream=stream)
+                pl.step(fused=fused, stream=stream)
             ends[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -258,9 +265,32 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
 
+    # the other form of the step (three calls instead of the fused pass, or the
+    # reverse), graph-replayed with the same flush, for reference
+    other_ms = None
+    if graph is not None:
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2, stream=stream):
+            pl.step(fused=not fused, stream=stream)
+        stream.synchronize()
+        Ko = min(args.steps, 50)
+        eo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ko)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                flush.zero_()
+                g2.replay()
+            for a, b in eo:
+                flush.zero_()
+                a.record(stream)
+                g2.replay()
+                b.record(stream)
+        stream.synchronize()
+        other_ms = float(np.mean([a.elapsed_time(b) for a, b in eo]))
+        del g2
+
     # per-call device times (eager calls, same stream, L2 flushed), for the roofline
     K2 = min(args.steps, 100)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K2)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(K2)]
     with torch.cuda.stream(stream):
         for k in range(K2):
             flush.zero_()
@@ -282,7 +312,7 @@ def run_ours(args):
             for _ in range(3):
                 for k, t in host.items():
                     pl.P.t[k].copy_(t, non_blocking=True)
-                pl.step(stream=stream)
+                pl.step(fused=fused, stream=stream)
                 hforce.copy_(pl.force, non_blocking=True)
                 htorque.copy_(pl.torque, non_blocking=True)
         stream.synchronize()
@@ -292,7 +322,7 @@ def run_ours(args):
             for _ in range(Ke):
                 for k, t in host.items():
                     pl.P.t[k].copy_(t, non_blocking=True)
-                pl.step(stream=stream)
+                pl.step(fused=fused, stream=stream)
                 hforce.copy_(pl.force, non_blocking=True)
                 htorque.copy_(pl.torque, non_blocking=True)
             e1.record(stream)
@@ -308,12 +338,14 @@ def run_ours(args):
     pk = peaks()
     dom_call = max(call_ms, key=call_ms.get)
     roof = roofline(dom_call, call_ms[dom_call], npairs, args.n, mean_it, fp64_frac, args.precision, pk)
-    kernels_per_step = kernels_in_step(args.precision)
+    kernels_per_step = kernels_in_step(args.precision, fused)
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "fp64_switch": args.fp64_switch,
+                   "form": "pair build + fused pass (lub_correct)" if fused else "pair build + three calls",
+                   "other_form_ms_per_step": other_ms,
                    "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",
@@ -460,12 +492,12 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
         with torch.cuda.stream(stream):
             if tune:
                 pl.autotune(reps=2, stream=stream)
-            pl.step(stream=stream)
-            pl.step(stream=stream)
+            pl.step(fused=True, stream=stream)
+            pl.step(fused=True, stream=stream)
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            pl.step(stream=stream)
+            pl.step(fused=True, stream=stream)
         stream.synchronize()
         g = torch.Generator(device=dev)
         g.manual_seed(12345)
@@ -515,12 +547,12 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for q in sep:
-            q.step(stream=stream)
+            q.step(fused=True, stream=stream)
         flush.zero_()
         e0.record(stream)
         for _ in range(Ks):
             for q in sep:
-                q.step(stream=stream)
+                q.step(fused=True, stream=stream)
         e1.record(stream)
     stream.synchronize()
     sep_ms = e0.elapsed_time(e1) / Ks
@@ -535,25 +567,42 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
         "precision": "mixed", "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
         "pairs_per_s": all_pairs / (step_ms * 1e-3), "newton_iters_per_pair": it_plain,
         "capacity_overflows": over, "ranks": ws,
-        "launch": "one CUDA graph per step, one persistent launch per stage for all suspensions",
+        "launch": "one CUDA graph per step (pair build + fused pass), one persistent launch per stage for all "
+                  "suspensions",
         "autotuned_shapes": {lub.TUNE_NAMES[q]: list(v) for q, v in enumerate(shapes)},
         "autotune_and_run_s": t_run, "generation_s": t_gen,
         "warm_starts": warm_forms,
         "separate_calls": {"ms_per_step": sep_ms, "pairs_per_s": sep_pairs / (sep_ms * 1e-3),
-                           "launches_per_step": "10 per suspension, eager"},
+                           "launches_per_step": "8 per suspension, eager"},
         "speedup_vs_separate": float((all_pairs / step_ms) / (sep_pairs / sep_ms)),
     }
 
 
-def kernels_in_step(precision):
+def kernels_in_step(precision, fused):
     # lub_pairs_build: cells count, scan, cells fill, sweep, scan, compaction = 6;
-    # lub_closest_points: the FP32 stage and the FP64 work list (mixed) or one FP64 kernel;
-    # lub_resistance 1; lub_apply (atomic) 1.  Memsets are not counted.
-    return 6 + (2 if precision == "mixed" else 1) + 1 + 1
+    # fused pass (lub_correct): FP32 stage + FP64 work list (mixed) or one FP64 kernel;
+    # separate calls: the same closest-point kernels, lub_resistance 1, lub_apply (atomic) 1.
+    # Memsets are not counted.
+    closest = 2 if precision == "mixed" else 1
+    return 6 + closest + (0 if fused else 2)
 
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
     t = ms * 1e-3
+    if call == "correct":
+        # fused pass: Newton (FP32 and the FP64 refinement, or FP64), resistance in the mode's precision
+        if precision == "mixed":
+            f32 = npairs * (mean_it * FP32_NEWTON_FLOP + RES_FP32_FLOP)
+            f64 = npairs * FP64_GAP_FLOP + npairs * fp64_frac * 2 * FP64_NEWTON_FLOP
+        else:
+            f32 = 0.0
+            f64 = npairs * (mean_it * FP64_NEWTON_FLOP + FP64_GAP_FLOP + RES_FP32_FLOP)
+        eq = f64 + f32 * pk["fp64_tflops"] / pk["fp32_tflops"]
+        ach = eq / t / 1e12
+        peak = pk["fp64_tflops"]
+        return {"kernel": "k_fused (closest + resistance + scatter)", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
+                "peak_src": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
     if call == "closest":
         if precision == "mixed":
             f32 = npairs * mean_it * FP32_NEWTON_FLOP

@@ -327,6 +327,25 @@ int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const 
                            void *stream);
 
 /*
+ * Fused pass: lub_closest_points, lub_resistance and lub_apply (atomic form)
+ * for every pair in one pass over the pairs, each pair's closest points, gap
+ * and resistance staying in registers (Sec. III A, III B, Eq. lub:resistance).
+ * The same arguments and results as the three calls, up to rounding (the
+ * same arithmetic, which the compiler may contract into multiply-adds
+ * differently inside the one kernel; the particle sums also add in another
+ * order), with fewer launches and no per-pair round trip through memory.  n [3][cap]
+ * is required: it holds the start normals of a warm start (LUB_WARM_PREVIOUS,
+ * LUB_WARM_MLP) and receives the normals.  gap, status, iters, FT and lever
+ * are written where given and skipped where NULL.  force and torque [3][n]
+ * (float in LUB_MIXED, double in LUB_FP64) are zeroed first unless
+ * accumulate is set.  Ensemble mode as for the separate calls.
+ */
+int lub_correct(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n,
+                double *gap, uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque,
+                int32_t accumulate, void *stream);
+
+/*
  * Temporal warm start (Sec. III A: the paper starts each time step's
  * closest-point search from the previous step's solution).  For every pair
  * of the current list, copies into n [3][capacity] the normal that the

@@ -67,7 +67,7 @@ class lub_params(ctypes.Structure):
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
-           "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals")
+           "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct")
 
 _lib = None
 
@@ -120,6 +120,9 @@ def load_library():
     lib.lub_autotune.restype = ctypes.c_int
     lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
                                  vp, vp, vp, vp, i32, vp]
+    lib.lub_correct.restype = ctypes.c_int
+    lib.lub_correct.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp, vp, vp,
+                                vp, vp, vp, vp, i32, vp]
     lib.lub_carry_normals.restype = ctypes.c_int
     lib.lub_carry_normals.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     lib.lub_get_launch_shape.restype = ctypes.c_int
@@ -265,6 +268,14 @@ def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_cou
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
         _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
         _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_correct(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, iters, FT, lever,
+                force, torque, accumulate=0, stream=None):
+    return _check(ctx, load_library().lub_correct(
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), _ptr(d_count),
+        int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
+        _ptr(torque), int(accumulate), _stream(stream)))
 
 
 def lub_carry_normals(ctx, n_particles, prev_i, prev_j, prev_n, prev_count, prev_capacity, pair_i, pair_j, d_count,
@@ -468,18 +479,31 @@ class Pipeline:
                      stream)
         return {TUNE_NAMES[k]: lub_get_launch_shape(self.ctx.h, k) for k in range(LUB_TUNE_COUNT)}
 
-    def step(self, build=True, deterministic=0, sync_count=False, stream=None):
-        """One correction step.  With warm_start = LUB_WARM_PREVIOUS the
-        normals are carried over from the step before (keep_previous is
-        called at the end of every step)."""
+    def correct(self, per_pair=True, stream=None):
+        """Closest points, resistance and scatter in the fused pass (lub_correct);
+        per_pair=False skips the per-pair outputs other than the normals."""
+        o = (lambda t: t) if per_pair else (lambda t: None)
+        lub_correct(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap, self.nrm,
+                    o(self.gap), o(self.status), o(self.iters), o(self.FT), o(self.lever), self.force, self.torque, 0,
+                    stream)
+
+    def step(self, build=True, deterministic=0, sync_count=False, fused=False, per_pair=True, stream=None):
+        """One correction step: the pair build, then the three per-pair calls
+        (or, with fused=True, the fused pass; deterministic needs the
+        separate calls).  With warm_start = LUB_WARM_PREVIOUS the normals are
+        carried over from the step before (keep_previous is called at the end
+        of every step)."""
         temporal = self.prm.warm_start == LUB_WARM_PREVIOUS
         if build:
             self.build_pairs(sync_count=sync_count, grow=sync_count, stream=stream)
         if temporal and getattr(self, "prev_cap", None) == self.cap:
             self.carry(stream)
-        self.closest(stream)
-        self.resistance(stream)
-        self.apply(deterministic=deterministic, stream=stream)
+        if fused and not deterministic:
+            self.correct(per_pair=per_pair, stream=stream)
+        else:
+            self.closest(stream)
+            self.resistance(stream)
+            self.apply(deterministic=deterministic, stream=stream)
         if temporal:
             self.keep_previous(stream)
 

@@ -9,7 +9,7 @@
 //   deterministic  incidence lists (counting sort by particle, entries
 //                  sorted by pair index and side), one thread per particle
 //                  summing in that fixed order: bitwise reproducible.
-#include "lub_internal.cuh"
+#include "pair_force.cuh"
 
 namespace {
 
@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(256) k_apply_atomic(const int32_t *__restrict_
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     const size_t N = (size_t)n;
-    const int lane = threadIdx.x & 31;
     // the loop bound is warp-uniform so the whole warp takes part in the shuffles
     for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
         const int k = base + threadIdx.x;
@@ -49,38 +48,7 @@ __global__ void __launch_bounds__(256) k_apply_atomic(const int32_t *__restrict_
             pair_contrib<T>(FT, lever, C, k, 0, ci);
             if (j >= 0 && j < n) pair_contrib<T>(FT, lever, C, k, 1, cj);
         }
-        // segmented reduction of the i side over lanes with equal i
-        const unsigned peers = __match_any_sync(0xffffffffu, i);
-        const int leader = __ffs(peers) - 1;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            T v = ci[a];
-            // sum over the peer set: rotate through its members
-            T s = T(0);
-            unsigned m = peers;
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                s += __shfl_sync(peers, v, src);
-            }
-            ci[a] = s;
-        }
-        if (i >= 0 && lane == leader) {
-            atomicAdd(force + i, ci[0]);
-            atomicAdd(force + N + i, ci[1]);
-            atomicAdd(force + 2 * N + i, ci[2]);
-            atomicAdd(torque + i, ci[3]);
-            atomicAdd(torque + N + i, ci[4]);
-            atomicAdd(torque + 2 * N + i, ci[5]);
-        }
-        if (i >= 0 && j >= 0 && j < n) {
-            atomicAdd(force + j, cj[0]);
-            atomicAdd(force + N + j, cj[1]);
-            atomicAdd(force + 2 * N + j, cj[2]);
-            atomicAdd(torque + j, cj[3]);
-            atomicAdd(torque + N + j, cj[4]);
-            atomicAdd(torque + 2 * N + j, cj[5]);
-        }
+        scatter_warp<T>(i, (j >= 0 && j < n) ? j : -1, N, ci, cj, force, torque);
     }
 }
 

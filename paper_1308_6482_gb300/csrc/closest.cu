@@ -26,8 +26,8 @@
 //     such pairs use the slow FP64 pipe.
 // LUB_FP64: the whole solve and gap in double.
 #include "ff.cuh"
-#include "lub_internal.cuh"
 #include "lub_mlp.cuh"
+#include "pair_force.cuh"
 
 namespace {
 
@@ -171,12 +171,208 @@ __device__ __forceinline__ double wall_gap(const PView &P, const DView &D, int i
     return dir * (__ldg(P.z + i) - D.wall_z[w]) - support(si, mk<double>(0.0, 0.0, 1.0));
 }
 
-// LUB_MIXED: FP32 Newton + float-float gap; near-contact / unconverged pairs
-// go to the work list (entry k: refine from the FP32 normal; -1-k: full FP64
-// solve from the line of centres)
+// ---------------------------------------------------------------------------
+// per-pair solves, shared by the separate kernels and the fused pass
+// ---------------------------------------------------------------------------
+constexpr int kNoEntry = 0x7fffffff;
+
+// LUB_MIXED, FP32 stage of pair k = (i, j): FP32 Newton + float-float gap.
+// Returns the FP64 work-list entry: k (refine from the FP32 normal), -1-k
+// (full FP64 solve from the line of centres) or kNoEntry.
 template <bool ENS>
-__global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
-                                                       const int32_t *__restrict__ pj,
+__device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E, int i, int j, int k,
+                                                 const double *__restrict__ nin, size_t C, int warm, int maxit,
+                                                 float tol32, float fp64_switch, V3<double> &n64, double &h, int &st,
+                                                 int &nit)
+{
+    int entry = kNoEntry;
+    st = 0;
+    nit = 0;
+    n64 = mk<double>(0, 0, 0);
+    h = 0.0;
+    bool alien;
+    const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+    if (alien || pair_bad(P, D, i, j)) {
+        st = LUB_ST_DEGENERATE;
+    } else if (j < 0) {
+        h = wall_gap(P, D, i, -1 - j, n64);
+    } else {
+        const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+        const ff dff[3] = {ff_from_double(d.x), ff_from_double(d.y), ff_from_double(d.z)};
+        const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
+        const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
+        const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
+        const ff dd = ff_add(ff_add(ff_mul(dff[0], dff[0]), ff_mul(dff[1], dff[1])), ff_mul(dff[2], dff[2]));
+        if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
+            st = LUB_ST_DEGENERATE;
+        } else if (rpi == rqi && rpj == rqj) {
+            // two spheres: n = d/|d|, h = |d| - R_i - R_j
+            const ff dl = ff_sqrt(dd);
+            const float inv = 1.0f / dl.hi;
+            n64 = mk<double>(df.x * inv, df.y * inv, df.z * inv);
+            h = ff_to_double(ff_sub(ff_sub(dl, ff_make(rpi)), ff_make(rpj)));
+        } else {
+            const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
+            const float dl = sqrtf(dd.hi);
+            V3<float> n = scl(1.0f / dl, df);
+            if (warm) {
+                const V3<float> w0 = mk<float>((float)nin[k], (float)nin[C + k], (float)nin[2 * C + k]);
+                const float wl2 = dot(w0, w0);
+                // a start on the far hemisphere falls back to the line of centres
+                if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2) && dot(w0, df) > 0.f) n = scl(rsqrtf(wl2), w0);
+            }
+            const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
+            const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
+            nit = o.iters;
+            const float nv[3] = {n.x, n.y, n.z};
+            h = ff_gap(P, i, j, dff, nv);
+            // unit normal for the output (|n|^2 - 1 ~ 1e-7)
+            const float nn = dot(n, n);
+            const float f = 1.5f - 0.5f * nn;
+            n64 = mk<double>(n.x * f, n.y * f, n.z * f);
+            const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
+            if (!o.converged || !isfinite(h))
+                entry = -1 - k;
+            else if (h < (double)fp64_switch * (double)amin)
+                entry = k;
+            // consistency check of Sec. III A: the normals point to the other centre
+            if (entry == kNoEntry && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
+        }
+    }
+    if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
+    return entry;
+}
+
+// LUB_MIXED, FP64 refinement of a work-list pair: one Newton step from the
+// FP32 normal nstart (quadratic convergence from |dn| ~ 1e-7 reaches rounding)
+// or, if full, a complete solve from the line of centres (to 1e-11 rad)
+template <bool ENS>
+__device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, bool full,
+                                           V3<double> nn, int maxit, V3<double> &n64, double &h, int &st, int &nit)
+{
+    bool alien;
+    const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+    const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+    const double dl = sqrt(dot(d, d));
+    const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
+    if (full) nn = scl(1.0 / dl, d);
+    const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
+    const NewtonOut o = full ? newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale)
+                             : newton_sphere<double>(si, sj, d, nn, 1, 1e-5, 1e-14 * scale);
+    n64 = normalized(nn);
+    h = dot(n64, d) - support(si, n64) - support(sj, n64);
+    st = LUB_ST_FP64;
+    if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+    if (h <= 0.0) st |= LUB_ST_OVERLAP;
+    nit = o.iters;
+}
+
+// LUB_FP64: the whole solve and gap of pair k in double
+template <bool ENS>
+__device__ __forceinline__ void closest_fp64_one(const PView &P, const DView &D0, const Ens &E, int i, int j, int k,
+                                                 const double *__restrict__ nin, size_t C, int warm, int maxit,
+                                                 V3<double> &n64, double &h, int &st, int &nit)
+{
+    st = 0;
+    nit = 0;
+    n64 = mk<double>(0, 0, 0);
+    h = 0.0;
+    bool alien;
+    const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+    if (alien || pair_bad(P, D, i, j)) {
+        st = LUB_ST_DEGENERATE;
+    } else if (j < 0) {
+        h = wall_gap(P, D, i, -1 - j, n64);
+    } else {
+        const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
+        const double dl = sqrt(dot(d, d));
+        if (!(dl > 0.0) || !isfinite(dl)) {
+            st = LUB_ST_DEGENERATE;
+        } else {
+            const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
+            const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
+            if (rpi == rqi && rpj == rqj) {
+                n64 = scl(1.0 / dl, d);
+                h = dl - (double)rpi - (double)rpj;
+            } else {
+                const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
+                V3<double> nn = scl(1.0 / dl, d);
+                if (warm) {
+                    const V3<double> w0 = mk<double>(nin[k], nin[C + k], nin[2 * C + k]);
+                    const double wl2 = dot(w0, w0);
+                    // a start on the far hemisphere falls back to the line of centres
+                    if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2) && dot(w0, d) > 0.0) nn = w0;
+                }
+                const double scale = dl + (double)fmaxf(rpi, rqi) + (double)fmaxf(rpj, rqj);
+                const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
+                nit = o.iters;
+                n64 = normalized(nn);
+                h = dot(n64, d) - support(si, n64) - support(sj, n64);
+                if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+            }
+        }
+    }
+    if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
+}
+
+__device__ __forceinline__ void store_pair(double *__restrict__ nout, double *__restrict__ gap,
+                                           uint8_t *__restrict__ status, uint8_t *__restrict__ iters, size_t C, int k,
+                                           const V3<double> &n64, double h, int st, int nit)
+{
+    nout[k] = n64.x;
+    nout[C + k] = n64.y;
+    nout[2 * C + k] = n64.z;
+    if (gap) gap[k] = h;
+    if (status) status[k] = (uint8_t)st;
+    if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+}
+
+// Compacted append to the FP64 work list (warp-collective).  One-step
+// polishes (entry k) fill the list from the front, full solves (entry -1-k,
+// several iterations each) from the back, so each kind runs in warps of its
+// own instead of every warp waiting for one full solve.  wl_count[0]: front
+// entries, wl_count[1]: back entries; the list holds cap entries.
+__device__ __forceinline__ void worklist_append(int entry, int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
+                                                int cap)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const bool polish = entry != kNoEntry && entry >= 0, full = entry != kNoEntry && entry < 0;
+    const unsigned mp = __ballot_sync(0xffffffffu, polish), mf = __ballot_sync(0xffffffffu, full);
+    if (mp) {
+        int wbase = 0;
+        const int leader = __ffs(mp) - 1;
+        if (lane == leader) wbase = atomicAdd(wl_count, __popc(mp));
+        wbase = __shfl_sync(0xffffffffu, wbase, leader);
+        if (polish) wl[wbase + __popc(mp & below)] = entry;
+    }
+    if (mf) {
+        int wbase = 0;
+        const int leader = __ffs(mf) - 1;
+        if (lane == leader) wbase = atomicAdd(wl_count + 1, __popc(mf));
+        wbase = __shfl_sync(0xffffffffu, wbase, leader);
+        if (full) wl[cap - 1 - (wbase + __popc(mf & below))] = entry;
+    }
+}
+
+// work-list entry q of [front entries | back entries], q < wl_total(...)
+__device__ __forceinline__ int wl_total(const int32_t *__restrict__ wl_count, int cap)
+{
+    return min(wl_count[0] + wl_count[1], cap);
+}
+__device__ __forceinline__ int wl_entry(const int32_t *__restrict__ wl_count, const int32_t *__restrict__ wl, int cap,
+                                        int q)
+{
+    const int nf = wl_count[0];
+    return q < nf ? wl[q] : wl[cap - 1 - (q - nf)];
+}
+
+// ---------------------------------------------------------------------------
+// lub_closest_points kernels
+// ---------------------------------------------------------------------------
+template <bool ENS>
+__global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
+                                                       const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
                                                        const int32_t *__restrict__ d_count, int32_t cap,
                                                        double *__restrict__ nout, double *__restrict__ gap,
                                                        uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
@@ -185,134 +381,54 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_con
 {
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
-    const int lane = threadIdx.x & 31;
     // warp-uniform loop bound: the whole warp takes part in the work-list ballot
     for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
         const int k = base + threadIdx.x;
-        int entry = 0x7fffffff;  // none
+        int entry = kNoEntry;
         if (k < count) {
             const int i = __ldg(pi + k), j = __ldg(pj + k);
-            int st = 0, nit = 0;
-            V3<double> n64 = mk<double>(0, 0, 0);
-            double h = 0.0;
-            bool alien;
-            const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-            if (alien || pair_bad(P, D, i, j)) {
-                st = LUB_ST_DEGENERATE;
-            } else if (j < 0) {
-                h = wall_gap(P, D, i, -1 - j, n64);
-            } else {
-                const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
-                const ff dff[3] = {ff_from_double(d.x), ff_from_double(d.y), ff_from_double(d.z)};
-                const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
-                const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
-                const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
-                const ff dd = ff_add(ff_add(ff_mul(dff[0], dff[0]), ff_mul(dff[1], dff[1])), ff_mul(dff[2], dff[2]));
-                if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
-                    st = LUB_ST_DEGENERATE;
-                } else if (rpi == rqi && rpj == rqj) {
-                    // two spheres: n = d/|d|, h = |d| - R_i - R_j
-                    const ff dl = ff_sqrt(dd);
-                    const float inv = 1.0f / dl.hi;
-                    n64 = mk<double>(df.x * inv, df.y * inv, df.z * inv);
-                    h = ff_to_double(ff_sub(ff_sub(dl, ff_make(rpi)), ff_make(rpj)));
-                } else {
-                    const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
-                    const float dl = sqrtf(dd.hi);
-                    V3<float> n = scl(1.0f / dl, df);
-                    if (warm) {
-                        const V3<float> w0 = mk<float>((float)nout[k], (float)nout[C + k], (float)nout[2 * C + k]);
-                        const float wl2 = dot(w0, w0);
-                        // a start on the far hemisphere falls back to the line of centres
-                        if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2) && dot(w0, df) > 0.f) n = scl(rsqrtf(wl2), w0);
-                    }
-                    const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
-                    const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
-                    nit = o.iters;
-                    const float nv[3] = {n.x, n.y, n.z};
-                    h = ff_gap(P, i, j, dff, nv);
-                    // unit normal for the output (|n|^2 - 1 ~ 1e-7)
-                    const float nn = dot(n, n);
-                    const float f = 1.5f - 0.5f * nn;
-                    n64 = mk<double>(n.x * f, n.y * f, n.z * f);
-                    const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
-                    if (!o.converged || !isfinite(h))
-                        entry = -1 - k;
-                    else if (h < (double)fp64_switch * (double)amin)
-                        entry = k;
-                    // consistency check of Sec. III A: the normals point to the other centre
-                    if (entry == 0x7fffffff && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
-                }
-            }
-            if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
-            nout[k] = n64.x;
-            nout[C + k] = n64.y;
-            nout[2 * C + k] = n64.z;
-            gap[k] = h;
-            status[k] = (uint8_t)st;
-            if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+            V3<double> n64;
+            double h;
+            int st, nit;
+            entry = closest_mixed_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
+                                           nit);
+            store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
         }
-        // compacted append to the FP64 work list
-        const bool need = entry != 0x7fffffff;
-        const unsigned m = __ballot_sync(0xffffffffu, need);
-        if (m) {
-            int wbase = 0;
-            const int leader = __ffs(m) - 1;
-            if (lane == leader) wbase = atomicAdd(wl_count, __popc(m));
-            wbase = __shfl_sync(0xffffffffu, wbase, leader);
-            if (need) wl[wbase + __popc(m & ((1u << lane) - 1u))] = entry;
-        }
+        worklist_append(entry, wl_count, wl, cap);
     }
 }
 
-// FP64 refinement of the work list
 template <bool ENS>
-__global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
+__global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_constant__ DView D0, Ens E,
+                                                        const int32_t *__restrict__ pi,
                                                         const int32_t *__restrict__ pj, int32_t cap,
                                                         double *__restrict__ nout, double *__restrict__ gap,
                                                         uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                         int maxit, const int32_t *__restrict__ wl_count,
                                                         const int32_t *__restrict__ wl)
 {
-    const int count = min(*wl_count, cap);
+    const int count = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-        const int v = wl[q];
+        const int v = wl_entry(wl_count, wl, cap, q);
         const bool full = v < 0;
         const int k = full ? -1 - v : v;
-        const int i = pi[k], j = pj[k];
-        bool alien;
-        const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-        const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
-        const double dl = sqrt(dot(d, d));
-        const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
-        V3<double> nn = full ? scl(1.0 / dl, d) : mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
-        const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
-        // from the FP32 normal one Newton step reaches rounding level (quadratic
-        // convergence from |dn| ~ 1e-7); a full solve iterates to 1e-11 rad
-        const NewtonOut o = full ? newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale)
-                                 : newton_sphere<double>(si, sj, d, nn, 1, 1e-5, 1e-14 * scale);
-        const V3<double> n64 = normalized(nn);
-        const double h = dot(n64, d) - support(si, n64) - support(sj, n64);
-        int st = LUB_ST_FP64;
-        if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
-        if (h <= 0.0) st |= LUB_ST_OVERLAP;
-        nout[k] = n64.x;
-        nout[C + k] = n64.y;
-        nout[2 * C + k] = n64.z;
-        gap[k] = h;
-        status[k] = (uint8_t)st;
+        V3<double> n64;
+        double h;
+        int st, nit;
+        refine_one<ENS>(P, D0, E, pi[k], pj[k], full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]), maxit, n64,
+                        h, st, nit);
+        store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
         if (iters) {
-            const int nit = (full ? 0 : iters[k]) + o.iters;
-            iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+            const int total = (full ? 0 : iters[k]) + nit;
+            iters[k] = (uint8_t)(total > 255 ? 255 : total);
         }
     }
 }
 
-// LUB_FP64: everything in double
 template <bool ENS>
-__global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi,
-                                                      const int32_t *__restrict__ pj,
+__global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_constant__ DView D0, Ens E,
+                                                      const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
                                                       const int32_t *__restrict__ d_count, int32_t cap,
                                                       double *__restrict__ nout, double *__restrict__ gap,
                                                       uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
@@ -321,53 +437,177 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_cons
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
-        const int i = __ldg(pi + k), j = __ldg(pj + k);
-        int st = 0, nit = 0;
+        V3<double> n64;
+        double h;
+        int st, nit;
+        closest_fp64_one<ENS>(P, D0, E, __ldg(pi + k), __ldg(pj + k), k, nout, C, warm, maxit, n64, h, st, nit);
+        store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused pass (lub_correct): closest points, resistance and the atomic scatter
+// of each pair without leaving registers.  nout is required (it holds the
+// start normals and carries the FP32 normals to the refinement); gap,
+// status, iters, FT and lever are written where given.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void store_force(T *__restrict__ FT, T *__restrict__ lever, size_t C, int k,
+                                            const T out[12])
+{
+    if (FT)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) FT[a * C + k] = out[a];
+    if (lever)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) lever[a * C + k] = out[6 + a];
+}
+
+// forces of a finished pair and its share of the warp's scatter
+template <typename T>
+__device__ __forceinline__ void force_and_scatter(const PView &P, const RParams &R, bool done, int i, int j,
+                                                  const V3<double> &n64, double h, int &st, T *__restrict__ FT,
+                                                  T *__restrict__ lever, size_t C, int k, T *__restrict__ force,
+                                                  T *__restrict__ torque)
+{
+    T out[12];
+    T ci[6] = {0, 0, 0, 0, 0, 0}, cj[6] = {0, 0, 0, 0, 0, 0};
+    if (done) {
+        const V3<T> n = mk<T>((T)n64.x, (T)n64.y, (T)n64.z);
+        pair_force<T>(P, R, i, j, n, h, st, out);
+        store_force(FT, lever, C, k, out);
+        side_contrib(out, 0, ci);
+        if (j >= 0) side_contrib(out, 1, cj);
+    }
+    // the closest-point solve validated the indices of every pair without DEGENERATE
+    const bool ok = done && !(st & LUB_ST_DEGENERATE);
+    scatter_warp<T>(ok ? i : -1, ok ? j : -1, (size_t)P.n, ci, cj, force, torque);
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(128) k_fused_mixed(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+                                                     const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                     const int32_t *__restrict__ d_count, int32_t cap,
+                                                     double *__restrict__ nout, double *__restrict__ gap,
+                                                     uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                     float *__restrict__ FT, float *__restrict__ lever, int maxit,
+                                                     float tol32, float fp64_switch, int warm,
+                                                     int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
+                                                     float *__restrict__ force, float *__restrict__ torque)
+{
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int k = base + threadIdx.x;
+        int entry = kNoEntry, i = -1, j = -1, st = 0;
         V3<double> n64 = mk<double>(0, 0, 0);
         double h = 0.0;
-        bool alien;
-        const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-        if (alien || pair_bad(P, D, i, j)) {
-            st = LUB_ST_DEGENERATE;
-        } else if (j < 0) {
-            h = wall_gap(P, D, i, -1 - j, n64);
-        } else {
-            const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
-            const double dl = sqrt(dot(d, d));
-            if (!(dl > 0.0) || !isfinite(dl)) {
-                st = LUB_ST_DEGENERATE;
-            } else {
-                const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
-                const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
-                if (rpi == rqi && rpj == rqj) {
-                    n64 = scl(1.0 / dl, d);
-                    h = dl - (double)rpi - (double)rpj;
-                } else {
-                    const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
-                    V3<double> nn = scl(1.0 / dl, d);
-                    if (warm) {
-                        const V3<double> w0 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
-                        const double wl2 = dot(w0, w0);
-                        // a start on the far hemisphere falls back to the line of centres
-                        if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2) && dot(w0, d) > 0.0) nn = w0;
-                    }
-                    const double scale = dl + (double)fmaxf(rpi, rqi) + (double)fmaxf(rpj, rqj);
-                    const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
-                    nit = o.iters;
-                    n64 = normalized(nn);
-                    h = dot(n64, d) - support(si, n64) - support(sj, n64);
-                    if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
-                }
+        if (k < count) {
+            i = __ldg(pi + k);
+            j = __ldg(pj + k);
+            int nit;
+            entry = closest_mixed_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
+                                           nit);
+            if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
+        }
+        const bool done = k < count && entry == kNoEntry;
+        worklist_append(entry, wl_count, wl, cap);
+        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque);
+        if (k < count) store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
+    }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(64) k_fused_refine(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+                                                      const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                      int32_t cap, double *__restrict__ nout,
+                                                      double *__restrict__ gap, uint8_t *__restrict__ status,
+                                                      uint8_t *__restrict__ iters, float *__restrict__ FT,
+                                                      float *__restrict__ lever, int maxit,
+                                                      const int32_t *__restrict__ wl_count,
+                                                      const int32_t *__restrict__ wl, float *__restrict__ force,
+                                                      float *__restrict__ torque)
+{
+    const int count = wl_total(wl_count, cap);
+    const size_t C = (size_t)cap;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int q = base + threadIdx.x;
+        const bool active = q < count;
+        int i = -1, j = -1, k = 0, st = 0, nit = 0;
+        bool full = false;
+        V3<double> n64 = mk<double>(0, 0, 0);
+        double h = 0.0;
+        if (active) {
+            const int v = wl_entry(wl_count, wl, cap, q);
+            full = v < 0;
+            k = full ? -1 - v : v;
+            i = pi[k];
+            j = pj[k];
+            refine_one<ENS>(P, D0, E, i, j, full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]), maxit, n64, h,
+                            st, nit);
+        }
+        force_and_scatter<float>(P, R, active, i, j, n64, h, st, FT, lever, C, k, force, torque);
+        if (active) {
+            store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
+            if (iters) {
+                const int total = (full ? 0 : iters[k]) + nit;
+                iters[k] = (uint8_t)(total > 255 ? 255 : total);
             }
         }
-        if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
-        nout[k] = n64.x;
-        nout[C + k] = n64.y;
-        nout[2 * C + k] = n64.z;
-        gap[k] = h;
-        status[k] = (uint8_t)st;
-        if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
     }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(128) k_fused_fp64(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+                                                    const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                    const int32_t *__restrict__ d_count, int32_t cap,
+                                                    double *__restrict__ nout, double *__restrict__ gap,
+                                                    uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                    double *__restrict__ FT, double *__restrict__ lever, int maxit,
+                                                    int warm, double *__restrict__ force, double *__restrict__ torque)
+{
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int k = base + threadIdx.x;
+        int i = -1, j = -1, st = 0, nit = 0;
+        V3<double> n64 = mk<double>(0, 0, 0);
+        double h = 0.0;
+        if (k < count) {
+            i = __ldg(pi + k);
+            j = __ldg(pj + k);
+            closest_fp64_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, n64, h, st, nit);
+        }
+        force_and_scatter<double>(P, R, k < count, i, j, n64, h, st, FT, lever, C, k, force, torque);
+        if (k < count) store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+// the network's start normals (learned warm start), then whether Newton starts from n
+int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                  const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n,
+                  cudaStream_t st, int *warm)
+{
+    *warm = prm.warm_start == LUB_WARM_PREVIOUS;
+    if (prm.warm_start == LUB_WARM_MLP) {
+        int rc = launch_mlp_start(ctx, P, D, E, pi, pj, d_count, cap, n, nullptr, st);
+        if (rc) return rc;
+        *warm = 1;
+    }
+    return LUB_OK;
+}
+
+// the FP64 work list of the mixed mode: count + up to cap entries in the context scratch
+int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl)
+{
+    int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);
+    if (rc) return rc;
+    *wl_count = (int32_t *)ctx->scratch;
+    *wl = (int32_t *)((char *)ctx->scratch + 256);
+    return lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 8, st), "memset work list");
 }
 
 template <bool ENS>
@@ -375,26 +615,17 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
                      uint8_t *status, uint8_t *iters, cudaStream_t st)
 {
-    int warm = prm.warm_start == LUB_WARM_PREVIOUS;
-    if (prm.warm_start == LUB_WARM_MLP) {
-        // the network's start normal for every pair, then Newton from it
-        int rc = launch_mlp_start(ctx, P, D, E, pi, pj, d_count, cap, n, nullptr, st);
-        if (rc) return rc;
-        warm = 1;
-    }
+    int warm = 0;
+    int rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm);
+    if (rc) return rc;
     if (prm.precision == LUB_MIXED) {
+        int32_t *wl_count, *wl;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        // work list: count + up to cap entries in the context scratch
-        int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);
-        if (rc) return rc;
-        int32_t *wl_count = (int32_t *)ctx->scratch;
-        int32_t *wl = (int32_t *)((char *)ctx->scratch + 256);
-        rc = lub_check_cuda(ctx, cudaMemsetAsync(wl_count, 0, 4, st), "memset work list");
-        if (rc) return rc;
         k_closest_mixed<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
                                                           prm.max_newton, (float)prm.newton_tol,
                                                           (float)prm.fp64_switch, warm, wl_count, wl);
-        // one warp per block so the (short) work list spreads over every SM
+        // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
         k_closest_refine<ENS><<<sr.grid, sr.block, 0, st>>>(P, D, E, pi, pj, cap, n, gap, status, iters,
                                                             prm.max_newton, wl_count, wl);
@@ -404,6 +635,43 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                                                          prm.max_newton, warm);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
+}
+
+template <bool ENS>
+int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                     const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
+                     uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque,
+                     int accumulate, cudaStream_t st)
+{
+    const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
+    int rc;
+    if (!accumulate) {
+        if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 3 * (size_t)P.n * esz, st), "memset force")) ||
+            (rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, 3 * (size_t)P.n * esz, st), "memset torque")))
+            return rc;
+    }
+    if (cap == 0) return LUB_OK;
+    int warm = 0;
+    if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
+    const RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c};
+    if (prm.precision == LUB_MIXED) {
+        int32_t *wl_count, *wl;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
+        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
+        k_fused_mixed<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
+                                                        (float *)FT, (float *)lever, prm.max_newton,
+                                                        (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count,
+                                                        wl, (float *)force, (float *)torque);
+        k_fused_refine<ENS><<<grid_for(cap, 64, ctx->num_sms, 32), 64, 0, st>>>(
+            P, D, E, R, pi, pj, cap, n, gap, status, iters, (float *)FT, (float *)lever, prm.max_newton, wl_count, wl,
+            (float *)force, (float *)torque);
+    } else {
+        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
+        k_fused_fp64<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
+                                                       (double *)FT, (double *)lever, prm.max_newton, warm,
+                                                       (double *)force, (double *)torque);
+    }
+    return lub_check_cuda(ctx, cudaGetLastError(), "fused pass launch");
 }
 
 // Temporal warm start: the previous list's normal of the same pair.  Both
@@ -514,6 +782,17 @@ int launch_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *qi, c
     k_carry_normals<<<grid_for(cap, 256, ctx->num_sms, 16), 256, 0, st>>>(qi, qj, qn, q_count, qcap, rng, n_particles,
                                                                           pi, pj, d_count, cap, n);
     return lub_check_cuda(ctx, cudaGetLastError(), "carry launch");
+}
+
+int launch_correct(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                   const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
+                   uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int accumulate,
+                   cudaStream_t st)
+{
+    return E.nb ? launch_correct_t<true>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, FT, lever,
+                                         force, torque, accumulate, st)
+                : launch_correct_t<false>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, FT, lever,
+                                          force, torque, accumulate, st);
 }
 
 int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,

@@ -302,6 +302,10 @@ __device__ __forceinline__ int pair_count(const int32_t *d_count, int32_t capaci
 int launch_closest(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                    const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n,
                    double *gap, uint8_t *status, uint8_t *iters, cudaStream_t st);
+int launch_correct(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                   const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
+                   uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int accumulate,
+                   cudaStream_t st);
 int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                       const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                       const double *n, const double *gap, uint8_t *status, void *FT, void *lever,

@@ -2,13 +2,14 @@
 // a single pass with decoupled look-back (Merrill & Garland, "Single-pass
 // parallel prefix scan with decoupled look-back", 2016).  Each block takes
 // the next tile by an atomic ticket (so it only ever waits on tiles whose
-// blocks are already running), scans it, publishes the tile total, looks back
-// over the published totals of earlier tiles until one publishes its
-// inclusive prefix, and publishes its own.  Every wait is bounded: on timeout
-// the block sets bit 2 of *err and carries on with what it has (the host
-// reports LUB_ERR_TIMEOUT where it reads the flags).  Used for the cell grid
-// and the per-particle pair counts of the pair builder and for the incidence
-// lists of the deterministic force sum.
+// blocks are already running), scans it and publishes the tile total; one
+// warp then looks back over the published totals of the 32 tiles before it
+// at a time, down to the nearest tile that has published its inclusive
+// prefix, and publishes its own.  Every wait is bounded: on timeout the block
+// sets bit 2 of *err and carries on with what it has (the host reports
+// LUB_ERR_TIMEOUT where it reads the flags).  Used for the cell grid and the
+// per-particle pair counts of the pair builder and for the incidence lists of
+// the deterministic force sum.
 #include "lub_internal.cuh"
 
 namespace {
@@ -74,35 +75,57 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restr
     }
     int tot;
     const int off = block_exclusive(s, tot);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0: publish the tile total, then look back 32 predecessors at a
+        // time (lane l reads tile - 1 - l - 32 r) down to the nearest tile
+        // that has published its inclusive prefix
+        const int lane = threadIdx.x;
         int excl = 0;
         if (tile == 0) {
-            __threadfence();
-            atomicExch(tstate, ST_PREFIX | (unsigned)tot);
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(tstate, ST_PREFIX | (unsigned)tot);
+            }
         } else {
-            __threadfence();
-            atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
+            }
             long spins = 0;
-            for (int p = tile - 1; p >= 0;) {
-                const unsigned long long w = load_state(tstate + p);
+            int top = tile - 1;
+            while (true) {
+                const int p = top - lane;
+                const unsigned long long w = p >= 0 ? load_state(tstate + p) : ST_PREFIX;
                 const unsigned long long flag = w & ~0xffffffffull;
-                if (flag == 0) {
+                const unsigned pre = __ballot_sync(0xffffffffu, flag == ST_PREFIX);
+                const unsigned none = __ballot_sync(0xffffffffu, flag == 0);
+                const int stop = pre ? __ffs(pre) - 1 : 32;  // nearest inclusive prefix in the window
+                const unsigned upto = stop == 32 ? 0xffffffffu : ((2u << stop) - 1u);
+                if (none & upto) {
+                    // a tile up to the stop has not published yet: wait (bounded)
                     if (++spins > kSpinLimit) {
-                        if (err) atomicOr(err, 4);
+                        if (lane == 0 && err) atomicOr(err, 4);
                         break;
                     }
                     __nanosleep(64);
                     continue;
                 }
-                excl += (int)(unsigned)(w & 0xffffffffull);
-                if (flag == ST_PREFIX) break;
-                --p;
+                int v = (lane <= stop) ? (int)(unsigned)(w & 0xffffffffull) : 0;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                excl += v;
+                if (stop < 32) break;
+                top -= 32;
             }
-            __threadfence();
-            atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
+            }
         }
-        prefix_s = excl;
-        if (d_total && (int64_t)(tile + 1) * SCAN_TILE >= n) *d_total = excl + tot;
+        if (lane == 0) {
+            prefix_s = excl;
+            if (d_total && (int64_t)(tile + 1) * SCAN_TILE >= n) *d_total = excl + tot;
+        }
     }
     __syncthreads();
     int run = prefix_s + off;
