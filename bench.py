@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble workload")
     ap.add_argument("--ens-n", type=int, default=256, help="suspensions in the ensemble workload")
     ap.add_argument("--ens-steps", type=int, default=100)
+    ap.add_argument("--no-large", action="store_true", help="skip the large wall-bounded run")
+    ap.add_argument("--large-n", type=int, default=1 << 20)
+    ap.add_argument("--large-steps", type=int, default=1000)
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--fp64-switch", type=float, default=1e-3,
                     help="h/a below which pairs get the FP64 Newton refinement (0: none)")
@@ -358,6 +361,8 @@ def run_ours(args):
         out["learned_vs_plain"] = learned_vs_plain(args, dev, stream, flush)
     if not args.no_ensemble:
         out["ensemble"] = ensemble_bench(args, dev, stream, flush, ws, rank)
+    if not args.no_large:
+        out["large"] = large_bench(args, dev, stream, flush, ws, rank)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(parts, dom)
     if rank == 0:
@@ -576,6 +581,78 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
                            "launches_per_step": "8 per suspension, eager"},
         "speedup_vs_separate": float((all_pairs / step_ms) / (sep_pairs / sep_ms)),
     }
+
+
+def large_bench(args, dev, stream, flush, ws=1, rank=0):
+    """Large run: args.large_n spheroids (aspect ratio log-uniform [1/3, 3]) at
+    phi = 0.35 in a cube periodic in x, y between two plane walls, mixed
+    precision, args.large_steps graph-replayed steps, every particle moved by a
+    small seeded rigid motion between steps; then shorter runs with the
+    learned and the temporal warm start on the same motions.  Under torchrun
+    every rank runs its own copy (another seed): replicas."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1308_6482_gb300 as lub
+    from paper_1308_6482_gb300.mlp import WarmStartMLP
+
+    t0 = time.perf_counter()
+    parts, dom = gen.large_config(N=args.large_n, seed=6 + 1000 * rank)
+    t_gen = time.perf_counter() - t0
+    rmax = float(max(parts["r_par"].max(), parts["r_perp"].max())) + 0.05
+    net = WarmStartMLP.load(device=dev)
+
+    def run(warm, steps):
+        P = lub.DeviceParticles(parts, dev, max_semi_axis=rmax)
+        pl = lub.Pipeline(P, dom, lub.default_params(precision="mixed", warm_start=warm), capacity=1024, device=dev)
+        if warm == lub.LUB_WARM_MLP:
+            net.install(pl.ctx)
+        npairs = pl.build_pairs()
+        pl._alloc(int(npairs * 1.3) + 4096, dev)
+        pl.build_pairs()
+        with torch.cuda.stream(stream):
+            pl.step(stream=stream)
+            pl.step(stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            pl.step(stream=stream)
+        stream.synchronize()
+        g = torch.Generator(device=dev)
+        g.manual_seed(777)
+        counts = torch.zeros(steps, dtype=torch.int32, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                rigid_motion(P, g)
+                graph.replay()
+            for k in range(steps):
+                rigid_motion(P, g)
+                flush.zero_()
+                ev[k][0].record(stream)
+                graph.replay()
+                ev[k][1].record(stream)
+                counts[k].copy_(pl.d_count[0])
+        stream.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        cnt = counts.cpu().numpy().astype(np.float64)
+        walls = int((pl.pair_j[:min(pl.count(), pl.cap)] < 0).sum().item())
+        return ms, cnt, int((cnt > pl.cap).sum()), walls
+
+    ms, cnt, over, walls = run(lub.LUB_WARM_NONE, args.large_steps)
+    step_ms, pairs = aggregate(float(ms.mean()), float(cnt.mean()), ws, dev)
+    out = {"workload": "%d spheroids, aspect ratio log-uniform [1/3,3], phi=0.35, cube %.0f^3 periodic in x,y "
+                       "between walls at z=0 and z=L; %d steps of seeded rigid motions"
+                       % (len(parts["x"]), dom["L"][0], args.large_steps),
+           "precision": "mixed", "pairs_per_step_mean": pairs, "wall_pairs_last_step": walls,
+           "ms_per_step": step_ms, "pairs_per_s": pairs / (step_ms * 1e-3), "capacity_overflows": over,
+           "generation_s": t_gen, "warm_starts": {}}
+    for name, warm in (("learned", lub.LUB_WARM_MLP), ("temporal", lub.LUB_WARM_PREVIOUS)):
+        msw, cntw, _, _ = run(warm, max(10, args.large_steps // 10))
+        wms, wp = aggregate(float(msw.mean()), float(cntw.mean()), ws, dev)
+        out["warm_starts"][name] = {"ms_per_step": wms, "pairs_per_s": wp / (wms * 1e-3), "steps": len(msw)}
+    return out
 
 
 def kernels_in_step(precision, fused):

@@ -235,24 +235,42 @@ def aspect_shapes(N, rng):
     return np.stack([4.5 * lam ** (2.0 / 3.0), 4.5 * lam ** (-1.0 / 3.0)], 1).astype(np.float32)
 
 
-def tile_periodic(parts, dom, k, rng):
-    """k x k x k copies of a periodic suspension side by side: again a periodic
-    suspension (of k^3 times the size), whose pairs across copy boundaries are
-    the periodic-image pairs of the original.  Velocities are drawn afresh."""
+def tile_periodic(parts, dom, k, rng, axes=(0, 1, 2)):
+    """k copies per listed (periodic) axis of a suspension side by side: again
+    a suspension, periodic along those axes and k^len(axes) times the size,
+    whose pairs across copy boundaries are the periodic-image pairs of the
+    original.  Velocities are drawn afresh."""
     if k == 1:
         return parts, dom
     L = np.asarray(dom["L"], np.float64)
-    n = len(parts["x"])
-    sh = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), -1).reshape(-1, 3)
+    for a in axes:
+        assert dom["periodic"][a], "tiling needs a periodic axis"
+    reps = [k if a in axes else 1 for a in range(3)]
+    sh = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3)
     out = {}
     for a, key in enumerate(("x", "y", "z")):
         out[key] = (np.asarray(parts[key])[None, :] + (sh[:, a] * L[a])[:, None]).reshape(-1)
     for key in ("qw", "qx", "qy", "qz", "r_par", "r_perp"):
-        out[key] = np.tile(np.asarray(parts[key]), k ** 3)
+        out[key] = np.tile(np.asarray(parts[key]), len(sh))
     velocities(out, rng)
     d = dict(dom)
-    d["L"] = tuple(float(v) * k for v in L)
+    d["L"] = tuple(float(v) * reps[a] for a, v in enumerate(L))
     return out, d
+
+
+def large_config(N=1 << 20, phi=0.35, seed=6, k=8):
+    """Large run: N spheroids (aspect ratio log-uniform in [1/3, 3], equivalent
+    radius 4.5) in a cube periodic in x, y between plane walls at z = 0 and
+    z = L: an attached random placement of N / k^2 particles in a slab of
+    L/k x L/k x L (walls included), tiled k x k in x and y."""
+    rng = np.random.default_rng(seed)
+    n0 = N // (k * k)
+    sh = aspect_shapes(n0, rng)
+    vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
+    L = (vol * k * k / phi) ** (1.0 / 3.0)
+    base, dom = suspension(sh, (L / k, L / k, L), periodic=(True, True, False), walls=[(0.0, 1), (L, -1)],
+                           attach_prob=0.9, wall_min=1e-3, seed=seed, max_attempts=400000)
+    return tile_periodic(base, dom, k, rng, axes=(0, 1))
 
 
 # pairs per particle of attached suspensions (attach_prob 0.9, list cut-off 1)

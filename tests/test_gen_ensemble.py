@@ -34,3 +34,20 @@ def test_members_are_near_their_target_pair_counts():
         assert 0.3 * target < len(pi) < 3.0 * target
         vol = float(np.sum(4.0 / 3.0 * np.pi * parts["r_par"].astype(np.float64) * parts["r_perp"] ** 2))
         assert abs(vol / np.prod(dom["L"]) - phi) < 1e-6
+
+
+def test_large_config_tiles_the_slab_in_x_and_y_only():
+    parts, dom = gen.large_config(N=2048, phi=0.3, seed=3, k=2)
+    assert len(parts["x"]) == 2048
+    assert dom["periodic"] == (True, True, False) and len(dom["walls"]) == 2
+    L = dom["L"]
+    assert L[0] == L[1] == L[2] and dom["walls"][1][0] == L[2]
+    z = np.asarray(parts["z"])
+    assert z.min() > 0 and z.max() < L[2]
+    # a copy of the base slab: the pairs of the tiled box are 4 x those of the base
+    rng = np.random.default_rng(3)
+    base = {k: np.asarray(v)[:512] for k, v in parts.items()}
+    bdom = dict(dom, L=(L[0] / 2, L[1] / 2, L[2]))
+    pi, pj = oracle.candidates(base, bdom, 1.0)
+    qi, qj = oracle.candidates(parts, dom, 1.0)
+    assert len(qi) == 4 * len(pi) and np.sum(qj < 0) == 4 * np.sum(pj < 0) > 0
