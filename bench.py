@@ -42,6 +42,10 @@ PAIRS_BYTES_PER_PARTICLE = 48.0   # pose + shape read once
 PAIRS_BYTES_PER_PAIR = 8.0        # (i, j) written
 APPLY_BYTES_PER_PAIR = 56.0       # F, T, levers (float) + indices
 APPLY_BYTES_PER_PARTICLE = 24.0   # force + torque written
+# DRAM bytes per call from the ncu launch list of the 32k-particle workload
+# (profiles/launches_mixed_suspension_32k.md: sum over the pair build's kernels,
+# cold cache); valid for the kernels profiled there, for that workload only
+TRAFFIC_PAIRS_BUILD_32K = 7.1457e6
 
 
 def parse():
@@ -305,34 +309,61 @@ def run_ours(args):
     # e2e through the public API: host inputs (pinned) -> device, step, force/torque -> host
     e2e = None
     if not args.no_e2e:
-        host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in parts.items()}
-        hforce = torch.empty(pl.force.numel(), dtype=pl.force.dtype).pin_memory()
-        htorque = torch.empty(pl.torque.numel(), dtype=pl.torque.dtype).pin_memory()
-        bi = sum(t.numel() * t.element_size() for t in host.values())
-        bo = hforce.numel() * hforce.element_size() * 2
+        # the user-facing form: particles in one packed device buffer, the
+        # step's inputs and outputs moved by one copy each way
+        Pk = lub.DeviceParticles(parts, dev, packed=True)
+        ple = lub.Pipeline(Pk, dom, prm, capacity=pl.cap, device=dev)
+        ple.build_pairs()
+        hblob = Pk.host_blob(parts, torch.empty(Pk.blob.numel(), dtype=torch.uint8).pin_memory())
+        hout = torch.empty(ple.ft_particles.numel(), dtype=ple.ft_particles.dtype).pin_memory()
+        bi = hblob.numel()
+        bo = hout.numel() * hout.element_size()
         Ke = min(args.steps, 100)
+
+        def e2e_step():
+            Pk.blob.copy_(hblob, non_blocking=True)
+            ple.step(fused=fused, stream=stream)
+            hout.copy_(ple.ft_particles, non_blocking=True)
+
         with torch.cuda.stream(stream):
             for _ in range(3):
-                for k, t in host.items():
-                    pl.P.t[k].copy_(t, non_blocking=True)
-                pl.step(fused=fused, stream=stream)
-                hforce.copy_(pl.force, non_blocking=True)
-                htorque.copy_(pl.torque, non_blocking=True)
+                e2e_step()
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # eager: the copies and the step's calls launched one by one
         with torch.cuda.stream(stream):
             e0.record(stream)
             for _ in range(Ke):
-                for k, t in host.items():
-                    pl.P.t[k].copy_(t, non_blocking=True)
-                pl.step(fused=fused, stream=stream)
-                hforce.copy_(pl.force, non_blocking=True)
-                htorque.copy_(pl.torque, non_blocking=True)
+                e2e_step()
             e1.record(stream)
         stream.synchronize()
+        eager_ms = e0.elapsed_time(e1) / Ke
+        # graph: the pinned host->device copies, the step and the device->host
+        # copies of force and torque captured together and replayed per step;
+        # the host waits for every step's result before the next
+        ge = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ge, stream=stream):
+            e2e_step()
+        stream.synchronize()
+        for _ in range(3):
+            ge.replay()
+        stream.synchronize()
+        t_e = time.perf_counter()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(Ke):
+                ge.replay()
+                stream.synchronize()
+            e1.record(stream)
+        stream.synchronize()
+        host_ms = (time.perf_counter() - t_e) * 1e3 / Ke
         e2e_ms = e0.elapsed_time(e1) / Ke
+        del ge
         e2e = {"value": npairs / (e2e_ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": int(bi),
-               "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms, "host_wall_ms_per_step": host_ms,
+               "eager_ms_per_step": eager_ms,
+               "how": "packed pinned host particles -> device (one copy), step, force+torque -> pinned host "
+                      "(one copy), one CUDA graph per step, host synchronised on every step's result"}
 
     # max over ranks
     ms_per_step, pairs_all = aggregate(total_ms / args.steps, npairs, ws, dev)
@@ -700,13 +731,18 @@ def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
         return {"kernel": "k_resistance", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_src": "FP32 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+    traffic = None
     if call == "pairs_build":
         b = n * PAIRS_BYTES_PER_PARTICLE + npairs * PAIRS_BYTES_PER_PAIR
+        if n == 32768:
+            traffic = TRAFFIC_PAIRS_BUILD_32K
     else:
         b = npairs * APPLY_BYTES_PER_PAIR + n * APPLY_BYTES_PER_PARTICLE
     ach = b / t / 1e9
     return {"kernel": call, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+            "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_src": pk["src"],
+            "note": "a chain of small dependent launches over 2.5 MB: latency-bound at this size"
+            if call == "pairs_build" else ""}
 
 
 def cpu_baseline(parts, dom, budget_s=20.0):

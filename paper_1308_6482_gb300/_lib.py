@@ -343,17 +343,43 @@ def make_ensemble(suspensions):
     return parts, [d for _, d in suspensions], offsets
 
 
+def _packed_layout(n):
+    """Byte offsets of the 15 particle arrays in one buffer: the three float64
+    centre arrays first, then the float32 ones, each 256-byte aligned."""
+    lay, off = {}, 0
+    for f in _P_FIELDS:
+        dt = np.dtype(np.float64) if f in ("x", "y", "z") else np.dtype(np.float32)
+        lay[f] = (off, dt)
+        off += (n * dt.itemsize + 255) // 256 * 256
+    return lay, max(off, 256)
+
+
 class DeviceParticles:
     """Particle arrays on the GPU (float64 centres, float32 the rest)."""
 
-    def __init__(self, parts, device="cuda", max_semi_axis=None, batch_offsets=None):
+    def __init__(self, parts, device="cuda", max_semi_axis=None, batch_offsets=None, packed=False):
+        """packed=True lays the 15 arrays out as views of one device buffer
+        (self.blob; layout self.layout), so one copy moves a whole pose and
+        velocity update: see host_blob()."""
         import torch
         n = len(parts["x"])
         self.n = n
         # ensemble mode: host offsets [n_batches + 1], kept alive with the struct
         self.offsets = None if batch_offsets is None else np.ascontiguousarray(batch_offsets, np.int32)
         self.t = {}
+        self.blob = None
+        self.layout = None
+        if packed:
+            self.layout, total = _packed_layout(n)
+            self.blob = torch.empty(total, dtype=torch.uint8, device=device)
+            for f in _P_FIELDS:
+                off, dt = self.layout[f]
+                self.t[f] = self.blob[off:off + n * dt.itemsize].view(torch.float64 if dt == np.float64
+                                                                        else torch.float32)
+            self.blob.copy_(torch.as_tensor(self.host_blob(parts)))
         for f in _P_FIELDS:
+            if packed:
+                break
             a = parts.get(f)
             if a is None:
                 a = np.zeros(n)
@@ -363,6 +389,19 @@ class DeviceParticles:
             max_semi_axis = float(max(np.max(parts["r_par"]), np.max(parts["r_perp"]))) if n else 1.0
         self.max_semi_axis = float(max_semi_axis)
         self.refresh()
+
+    def host_blob(self, parts, out=None):
+        """The packed layout of `parts` as host bytes (into `out`, e.g. a pinned
+        uint8 tensor, if given)."""
+        import torch
+        _, total = _packed_layout(self.n)
+        buf = np.zeros(total, np.uint8) if out is None else out.numpy()
+        for f in _P_FIELDS:
+            off, dt = self.layout[f]
+            a = parts.get(f)
+            a = np.zeros(self.n, dt) if a is None else np.ascontiguousarray(a, dt)
+            buf[off:off + self.n * dt.itemsize] = a.view(np.uint8)
+        return out if out is not None else torch.as_tensor(buf)
 
     def refresh(self):
         off = self.offsets
@@ -414,8 +453,10 @@ class Pipeline:
         self.iters = torch.empty(self.cap, dtype=torch.uint8, device=device)
         self.FT = torch.empty(6 * self.cap, dtype=fdt, device=device)
         self.lever = torch.empty(6 * self.cap, dtype=fdt, device=device)
-        self.force = torch.empty(3 * max(self.n, 1), dtype=fdt, device=device)
-        self.torque = torch.empty(3 * max(self.n, 1), dtype=fdt, device=device)
+        # force and torque: two views of one buffer, so one copy reads both back
+        self.ft_particles = torch.empty(6 * max(self.n, 1), dtype=fdt, device=device)
+        self.force = self.ft_particles[:3 * max(self.n, 1)]
+        self.torque = self.ft_particles[3 * max(self.n, 1):]
 
     def build_pairs(self, sync_count=True, grow=True, stream=None):
         h = self.ctx.h

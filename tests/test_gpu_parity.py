@@ -230,3 +230,27 @@ def test_degenerate_pairs_are_flagged_not_faulted():
     assert np.all(g["status"] & 4)
     assert np.all(g["FT"] == 0)
     assert np.all(np.isfinite(g["force"]))
+
+
+def test_packed_particles_give_the_same_results():
+    """One device buffer for all particle arrays (one copy per update) is a
+    layout change only."""
+    import torch
+
+    import paper_1308_6482_gb300 as lub
+    parts, dom = gen.config_mixed_suspension(N=2000, phi=0.3, seed=12)
+    a = run_gpu(parts, dom, "fp64", deterministic=1)
+    P = lub.DeviceParticles(parts, packed=True)
+    hb = P.host_blob(parts)
+    assert hb.numel() == P.blob.numel()
+    np.testing.assert_array_equal(P.t["y"].cpu().numpy(), parts["y"])
+    np.testing.assert_array_equal(P.t["qz"].cpu().numpy(), parts["qz"])
+    pl = lub.Pipeline(P, dom, lub.default_params(precision="fp64"))
+    pl.step(deterministic=1, sync_count=True)
+    torch.cuda.synchronize()
+    b = pl.results()
+    for k in ("pi", "pj", "n", "h", "FT", "force", "torque"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    # force and torque read back in one piece
+    ft = pl.ft_particles.cpu().numpy()
+    np.testing.assert_array_equal(ft[:3 * P.n].reshape(3, -1).T, b["force"])
