@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--form", default="calls", choices=["fused", "calls"],
-                    help="fused: pair build + lub_correct; calls: pair build + the three per-pair calls")
+    ap.add_argument("--form", default="merged", choices=["calls", "merged", "fused"],
+                    help="calls: pair build + closest + resistance + apply; merged: pair build + closest + "
+                         "resistance_apply; fused: pair build + lub_correct")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain warm-start comparison")
@@ -200,10 +201,11 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    fused = args.form == "fused"
+    form = args.form
+    fused = form == "fused"
     # eager step once: per-call launch accounting and results for the work counts
     with torch.cuda.stream(stream):
-        pl.step(fused=fused, stream=stream)
+        pl.step(form=form, stream=stream)
     stream.synchronize()
     res = pl.results()
     mean_it = float(np.mean(res["iters"]))
@@ -214,10 +216,11 @@ def run_ours(args):
     if not args.no_graph:
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            pl.step(fused=fused, stream=stream)
+            pl.step(form=form, stream=stream)
         stream.synchronize()
 
-    calls = ("pairs_build", "correct") if fused else ("pairs_build", "closest", "resistance", "apply")
+    calls = {"fused": ("pairs_build", "correct"), "merged": ("pairs_build", "closest", "resistance_apply"),
+             "calls": ("pairs_build", "closest", "resistance", "apply")}[form]
 
     def step_timed(evs):
         # per-call events (used for the roofline) around the calls
@@ -227,6 +230,12 @@ def run_ours(args):
         if fused:
             pl.correct(stream=stream)
             evs[2].record(stream)
+            return
+        if form == "merged":
+            pl.closest(stream=stream)
+            evs[2].record(stream)
+            pl.resistance_apply(stream=stream)
+            evs[3].record(stream)
             return
         pl.closest(stream=stream)
         evs[2].record(stream)
@@ -241,7 +250,7 @@ def run_ours(args):
             if graph is not None:
                 graph.replay()
             else:
-                pl.step(fused=fused, stream=stream)
+                pl.step(form=form, stream=stream)
     stream.synchronize()
 
     # timed region: K steps of the graph, L2 flushed between steps
@@ -262,7 +271,7 @@ def run_ours(args):
             if graph is not None:
                 graph.replay()
             else:
-                pl.step(fused=fused, stream=stream)
+                pl.step(form=form, stream=stream)
             ends[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -272,28 +281,30 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
 
-    # the other form of the step (three calls instead of the fused pass, or the
-    # reverse), graph-replayed with the same flush, for reference
-    other_ms = None
+    # the other forms of the step, graph-replayed with the same flush, for reference
+    forms_ms = {}
     if graph is not None:
-        g2 = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g2, stream=stream):
-            pl.step(fused=not fused, stream=stream)
-        stream.synchronize()
-        Ko = min(args.steps, 50)
-        eo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ko)]
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                flush.zero_()
-                g2.replay()
-            for a, b in eo:
-                flush.zero_()
-                a.record(stream)
-                g2.replay()
-                b.record(stream)
-        stream.synchronize()
-        other_ms = float(np.mean([a.elapsed_time(b) for a, b in eo]))
-        del g2
+        for other in ("calls", "merged", "fused"):
+            if other == form:
+                continue
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2, stream=stream):
+                pl.step(form=other, stream=stream)
+            stream.synchronize()
+            Ko = min(args.steps, 50)
+            eo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ko)]
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    flush.zero_()
+                    g2.replay()
+                for a, b in eo:
+                    flush.zero_()
+                    a.record(stream)
+                    g2.replay()
+                    b.record(stream)
+            stream.synchronize()
+            forms_ms[other] = float(np.mean([a.elapsed_time(b) for a, b in eo]))
+            del g2
 
     # per-call device times (eager calls, same stream, L2 flushed), for the roofline
     K2 = min(args.steps, 100)
@@ -322,7 +333,7 @@ def run_ours(args):
 
         def e2e_step():
             Pk.blob.copy_(hblob, non_blocking=True)
-            ple.step(fused=fused, stream=stream)
+            ple.step(form=form, stream=stream)
             hout.copy_(ple.ft_particles, non_blocking=True)
 
         with torch.cuda.stream(stream):
@@ -372,14 +383,16 @@ def run_ours(args):
     pk = peaks()
     dom_call = max(call_ms, key=call_ms.get)
     roof = roofline(dom_call, call_ms[dom_call], npairs, args.n, mean_it, fp64_frac, args.precision, pk)
-    kernels_per_step = kernels_in_step(args.precision, fused)
+    kernels_per_step = kernels_in_step(args.precision, form)
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "fp64_switch": args.fp64_switch,
-                   "form": "pair build + fused pass (lub_correct)" if fused else "pair build + three calls",
-                   "other_form_ms_per_step": other_ms,
+                   "form": {"fused": "pair build + fused pass (lub_correct)",
+                            "merged": "pair build + closest points + resistance with scatter (lub_resistance_apply)",
+                            "calls": "pair build + closest points + resistance + apply"}[form],
+                   "other_forms_ms_per_step": forms_ms,
                    "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",
@@ -686,13 +699,13 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
     return out
 
 
-def kernels_in_step(precision, fused):
+def kernels_in_step(precision, form):
     # lub_pairs_build: cells count, scan, cells fill, sweep, scan, compaction = 6;
-    # fused pass (lub_correct): FP32 stage + FP64 work list (mixed) or one FP64 kernel;
-    # separate calls: the same closest-point kernels, lub_resistance 1, lub_apply (atomic) 1.
+    # closest points: FP32 stage + FP64 work list (mixed) or one FP64 kernel (also in the fused pass);
+    # calls: lub_resistance 1 + lub_apply (atomic) 1; merged: lub_resistance_apply 1; fused: 0.
     # Memsets are not counted.
     closest = 2 if precision == "mixed" else 1
-    return 6 + closest + (0 if fused else 2)
+    return 6 + closest + {"calls": 2, "merged": 1, "fused": 0}[form]
 
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
@@ -725,7 +738,7 @@ def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
         return {"kernel": "k_closest", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
                 "peak_src": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
-    if call == "resistance":
+    if call in ("resistance", "resistance_apply"):
         ach = npairs * RES_FP32_FLOP / t / 1e12
         peak = pk["fp32_tflops"]
         return {"kernel": "k_resistance", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",

@@ -327,6 +327,20 @@ int lub_pairs_build_static(const lub_particles *p, const lub_domain *dom, const 
                            void *stream);
 
 /*
+ * lub_resistance and lub_apply (atomic form) in one pass over the pairs: the
+ * pair force is scattered to the particles straight from registers (the
+ * fast path "write straight to force/torque").  Same arguments as
+ * lub_resistance plus force and torque [3][n] (zeroed first unless
+ * accumulate is set); FT and lever are written where given and skipped where
+ * NULL.  Results as lub_resistance + lub_apply up to the order of the atomic
+ * additions.
+ */
+int lub_resistance_apply(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                         const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+                         const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
+                         void *torque, int32_t accumulate, void *stream);
+
+/*
  * Fused pass: lub_closest_points, lub_resistance and lub_apply (atomic form)
  * for every pair in one pass over the pairs, each pair's closest points, gap
  * and resistance staying in registers (Sec. III A, III B, Eq. lub:resistance).

@@ -67,7 +67,8 @@ class lub_params(ctypes.Structure):
 EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_error", "lub_pairs_build",
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
-           "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct")
+           "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
+           "lub_resistance_apply")
 
 _lib = None
 
@@ -120,6 +121,9 @@ def load_library():
     lib.lub_autotune.restype = ctypes.c_int
     lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
                                  vp, vp, vp, vp, i32, vp]
+    lib.lub_resistance_apply.restype = ctypes.c_int
+    lib.lub_resistance_apply.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp,
+                                         vp, vp, vp, vp, vp, i32, vp]
     lib.lub_correct.restype = ctypes.c_int
     lib.lub_correct.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp, vp, vp,
                                 vp, vp, vp, vp, i32, vp]
@@ -268,6 +272,14 @@ def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_cou
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
         _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
         _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_resistance_apply(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, FT,
+                         lever, force, torque, accumulate=0, stream=None):
+    return _check(ctx, load_library().lub_resistance_apply(
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), _ptr(d_count),
+        int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(FT), _ptr(lever), _ptr(force), _ptr(torque),
+        int(accumulate), _stream(stream)))
 
 
 def lub_correct(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, iters, FT, lever,
@@ -528,19 +540,35 @@ class Pipeline:
                     o(self.gap), o(self.status), o(self.iters), o(self.FT), o(self.lever), self.force, self.torque, 0,
                     stream)
 
-    def step(self, build=True, deterministic=0, sync_count=False, fused=False, per_pair=True, stream=None):
-        """One correction step: the pair build, then the three per-pair calls
-        (or, with fused=True, the fused pass; deterministic needs the
-        separate calls).  With warm_start = LUB_WARM_PREVIOUS the normals are
-        carried over from the step before (keep_previous is called at the end
-        of every step)."""
+    def resistance_apply(self, per_pair=True, stream=None):
+        """Resistance and the atomic scatter in one pass (lub_resistance_apply)."""
+        o = (lambda t: t) if per_pair else (lambda t: None)
+        lub_resistance_apply(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count,
+                             self.cap, self.nrm, self.gap, self.status, o(self.FT), o(self.lever), self.force,
+                             self.torque, 0, stream)
+
+    def step(self, build=True, deterministic=0, sync_count=False, fused=False, per_pair=True, form=None,
+             stream=None):
+        """One correction step: the pair build, then the per-pair work in one
+        of three forms: "calls" (closest points, resistance, apply), "merged"
+        (closest points, then resistance + scatter in one pass) or "fused"
+        (all three in one pass; fused=True is the same).  deterministic needs
+        "calls".  With warm_start = LUB_WARM_PREVIOUS the normals are carried
+        over from the step before (keep_previous is called at the end of
+        every step)."""
+        form = form or ("fused" if fused else "calls")
+        if deterministic:
+            form = "calls"
         temporal = self.prm.warm_start == LUB_WARM_PREVIOUS
         if build:
             self.build_pairs(sync_count=sync_count, grow=sync_count, stream=stream)
         if temporal and getattr(self, "prev_cap", None) == self.cap:
             self.carry(stream)
-        if fused and not deterministic:
+        if form == "fused":
             self.correct(per_pair=per_pair, stream=stream)
+        elif form == "merged":
+            self.closest(stream)
+            self.resistance_apply(per_pair=per_pair, stream=stream)
         else:
             self.closest(stream)
             self.resistance(stream)

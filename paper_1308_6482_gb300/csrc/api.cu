@@ -358,6 +358,26 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
                         deterministic, (cudaStream_t)stream);
 }
 
+int lub_resistance_apply(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+                         const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+                         const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
+                         void *torque, int32_t accumulate, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, true)) || (rc = check_params(ctx, prm)) ||
+        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
+        return rc;
+    if (capacity > 0 && (!n || !gap || !status)) return lub_set_error(ctx, LUB_ERR_ARG, "n, gap or status is NULL");
+    if (p->n > 0 && (!force || !torque)) return lub_set_error(ctx, LUB_ERR_ARG, "force or torque is NULL");
+    DView D;
+    Ens E;
+    if ((rc = prepare_domains(ctx, p, dom, (cudaStream_t)stream, &D, &E))) return rc;
+    return launch_resistance_apply(ctx, make_pview(p), D, E, *prm, pair_i, pair_j, d_count, capacity, n, gap, status,
+                                   FT, lever, force, torque, accumulate, (cudaStream_t)stream);
+}
+
 int lub_correct(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
                 const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n,
                 double *gap, uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque,

@@ -306,6 +306,10 @@ int launch_correct(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, c
                    const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
                    uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int accumulate,
                    cudaStream_t st);
+int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                            const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
+                            const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
+                            void *torque, int accumulate, cudaStream_t st);
 int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                       const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                       const double *n, const double *gap, uint8_t *status, void *FT, void *lever,

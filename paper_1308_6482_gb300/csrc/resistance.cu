@@ -50,7 +50,90 @@ __global__ void __launch_bounds__(128) k_resistance(PView P, const __grid_consta
     }
 }
 
+// resistance and the atomic scatter of lub_apply in one pass (FT, lever optional)
+template <typename T, bool ENS>
+__global__ void __launch_bounds__(128) k_resistance_apply(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+                                                          const int32_t *__restrict__ pi,
+                                                          const int32_t *__restrict__ pj,
+                                                          const int32_t *__restrict__ d_count, int32_t cap,
+                                                          const double *__restrict__ nin,
+                                                          const double *__restrict__ gap,
+                                                          uint8_t *__restrict__ status, T *__restrict__ FT,
+                                                          T *__restrict__ lever, T *__restrict__ force,
+                                                          T *__restrict__ torque)
+{
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    // warp-uniform loop bound: the whole warp takes part in the scatter
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int k = base + threadIdx.x;
+        int i = -1, j = -1, st = LUB_ST_DEGENERATE;
+        T out[12];
+        T ci[6] = {0, 0, 0, 0, 0, 0}, cj[6] = {0, 0, 0, 0, 0, 0};
+        if (k < count) {
+            st = status[k];
+            const double h = gap[k];
+            i = __ldg(pi + k);
+            j = __ldg(pj + k);
+            bool alien;
+            const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+            if (alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
+            const V3<T> n = mk<T>((T)nin[k], (T)nin[C + k], (T)nin[2 * C + k]);
+            pair_force<T>(P, R, i, j, n, h, st, out);
+            if (FT)
+#pragma unroll
+                for (int a = 0; a < 6; ++a) FT[a * C + k] = out[a];
+            if (lever)
+#pragma unroll
+                for (int a = 0; a < 6; ++a) lever[a * C + k] = out[6 + a];
+            status[k] = (uint8_t)st;
+            side_contrib(out, 0, ci);
+            if (j >= 0) side_contrib(out, 1, cj);
+        }
+        const bool ok = !(st & LUB_ST_DEGENERATE);
+        scatter_warp<T>(ok ? i : -1, ok ? j : -1, (size_t)P.n, ci, cj, force, torque);
+    }
+}
+
 }  // namespace
+
+int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
+                            const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
+                            const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
+                            void *torque, int accumulate, cudaStream_t st)
+{
+    const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
+    int rc;
+    if (!accumulate && P.n > 0) {
+        if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 3 * (size_t)P.n * esz, st), "memset force")) ||
+            (rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, 3 * (size_t)P.n * esz, st), "memset torque")))
+            return rc;
+    }
+    if (cap == 0) return LUB_OK;
+    RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c};
+    const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
+    const bool ens = E.nb > 0;
+    if (prm.precision == LUB_MIXED) {
+        if (ens)
+            k_resistance_apply<float, true><<<sh.grid, sh.block, 0, st>>>(
+                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
+                (float *)torque);
+        else
+            k_resistance_apply<float, false><<<sh.grid, sh.block, 0, st>>>(
+                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
+                (float *)torque);
+    } else {
+        if (ens)
+            k_resistance_apply<double, true><<<sh.grid, sh.block, 0, st>>>(
+                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
+                (double *)torque);
+        else
+            k_resistance_apply<double, false><<<sh.grid, sh.block, 0, st>>>(
+                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
+                (double *)torque);
+    }
+    return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance_apply launch");
+}
 
 int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                       const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, const double *n,

@@ -153,3 +153,25 @@ def test_fused_degenerate_pairs(lub):
         assert np.all(g["FT"][len(pi):] == 0)
         ok = run(lub, parts, dom, prec, True, pi, pj)
         np.testing.assert_array_equal(g["force"], ok["force"]) if prec == "fp64" else sums_close(g, ok, ok, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_resistance_apply_in_one_pass(lub, prec):
+    """lub_resistance_apply: resistance and the scatter in one pass."""
+    import torch
+    parts, dom = gen.config_prolate_wall(seed=3)
+    sep = run(lub, parts, dom, prec, False)
+    pl = lub.Pipeline(parts, dom, gpu_params(prec))
+    pl.step(form="merged", sync_count=True)
+    torch.cuda.synchronize()
+    mer = pl.results()
+    same_pairs(mer, sep, prec)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    compare(parts, dom, mer, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
+    # FT and lever are optional
+    pl2 = lub.Pipeline(parts, dom, gpu_params(prec))
+    pl2.build_pairs()
+    pl2.closest()
+    pl2.resistance_apply(per_pair=False)
+    torch.cuda.synchronize()
+    sums_close(pl2.results(), mer, mer, prec)
