@@ -243,9 +243,51 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
     return entry;
 }
 
-// LUB_MIXED, FP64 refinement of a work-list pair: one Newton step from the
-// FP32 normal nstart (quadratic convergence from |dn| ~ 1e-7 reaches rounding)
-// or, if full, a complete solve from the line of centres (to 1e-11 rad)
+// One FP64 Newton step of g on the sphere from a normal n accurate to FP32
+// (|dn| ~ 1e-7): the gradient in FP64, the tangent Hessian and the 2x2 solve
+// in FP32.  An approximate Hessian of relative error e makes the step
+// contract the error by a factor e as well, so from 1e-7 one step lands at
+// the FP64 rounding level with a fraction of the FP64 operations of a full
+// FP64 step.  Returns the step length (radians).
+__device__ __forceinline__ double polish_step(const Shape<double> &si, const Shape<double> &sj, const V3<double> &d,
+                                              V3<double> &n)
+{
+    n = normalized(n);
+    const V3<double> t1 = perp_unit(n), t2 = cross(n, t1);
+    const double ci = dot(si.o, n), u1i = dot(si.o, t1), u2i = dot(si.o, t2);
+    const double cj = dot(sj.o, n), u1j = dot(sj.o, t1), u2j = dot(sj.o, t2);
+    const double qi = si.a2 + si.e * ci * ci, qj = sj.a2 + sj.e * cj * cj;
+    const double ri = rsqrt64(qi), rj = rsqrt64(qj);
+    const double ki = si.e * ci * ri, kj = sj.e * cj * rj;
+    const double g1 = dot(t1, d) - ki * u1i - kj * u1j;
+    const double g2 = dot(t2, d) - ki * u2i - kj * u2j;
+    // P = -Hess_t g in FP32
+    const float g = (float)(dot(n, d) - qi * ri - qj * rj);
+    const float rif = (float)ri, rjf = (float)rj;
+    const float Ai = (float)si.a2 * rif, Aj = (float)sj.a2 * rjf;
+    const float Ei = (float)si.e * rif * rif, Ej = (float)sj.e * rjf * rjf;
+    const float a1 = (float)u1i, a2 = (float)u2i, b1 = (float)u1j, b2 = (float)u2j;
+    const float P11 = Ai * (1.f + Ei * a1 * a1) + Aj * (1.f + Ej * b1 * b1) + g;
+    const float P22 = Ai * (1.f + Ei * a2 * a2) + Aj * (1.f + Ej * b2 * b2) + g;
+    const float P12 = Ai * Ei * a1 * a2 + Aj * Ej * b1 * b2;
+    const float det = P11 * P22 - P12 * P12;
+    double s1, s2;
+    if (P11 > 0.f && det > 0.f) {
+        const float idet = 1.0f / det;
+        s1 = ((double)P22 * g1 - (double)P12 * g2) * (double)idet;
+        s2 = ((double)P11 * g2 - (double)P12 * g1) * (double)idet;
+    } else {
+        const double sc = 1.0 / (double)(fabsf(P11) + fabsf(P22) + fabsf(P12) + Ai + Aj);
+        s1 = g1 * sc;
+        s2 = g2 * sc;
+    }
+    n = normalized(axpy(s1, t1, axpy(s2, t2, n)));
+    return sqrt(s1 * s1 + s2 * s2);
+}
+
+// LUB_MIXED, FP64 refinement of a work-list pair: one polish step from the
+// FP32 normal nstart, or, if full, a complete FP64 solve from the line of
+// centres (to 1e-11 rad)
 template <bool ENS>
 __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, bool full,
                                            V3<double> nn, int maxit, V3<double> &n64, double &h, int &st, int &nit)
@@ -255,16 +297,22 @@ __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, cons
     const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
     const double dl = sqrt(dot(d, d));
     const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
-    if (full) nn = scl(1.0 / dl, d);
-    const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
-    const NewtonOut o = full ? newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale)
-                             : newton_sphere<double>(si, sj, d, nn, 1, 1e-5, 1e-14 * scale);
+    bool converged;
+    if (full) {
+        nn = scl(1.0 / dl, d);
+        const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
+        const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
+        converged = o.converged;
+        nit = o.iters;
+    } else {
+        converged = polish_step(si, sj, d, nn) < 1e-5;
+        nit = 1;
+    }
     n64 = normalized(nn);
     h = dot(n64, d) - support(si, n64) - support(sj, n64);
     st = LUB_ST_FP64;
-    if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+    if (!converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
     if (h <= 0.0) st |= LUB_ST_OVERLAP;
-    nit = o.iters;
 }
 
 // LUB_FP64: the whole solve and gap of pair k in double
