@@ -4,11 +4,11 @@
 //      in the cell (atomic), scan of the cell counts, copy of every particle
 //      into cell order as two float4 records: position relative to its cell
 //      centre with Rmax, and symmetry axis with e = R_par^2 - R_perp^2;
-//   2. sweep: one thread per (particle, row of three neighbour cells), nine
-//      rows per particle, particles in cell order so neighbouring threads
-//      read the same cells; each unordered pair is visited once, by the
-//      particle earlier in cell order, and stored for the smaller of its two
-//      indices in that particle's row of KSLOT slots (atomic slot index); the
+//   2. sweep: one thread per (particle, row of the half-shell stencil), five
+//      rows per particle covering the own cell and the 13 forward neighbours,
+//      particles in cell order so neighbouring threads read the same cells;
+//      each unordered pair is visited once and stored for the smaller of its
+//      two indices in that particle's row of KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
 //      caller's pair arrays; the row-0 thread tests the plane walls;
 //   3. one scan over [particle-pair counts | wall-pair counts] gives every
@@ -190,11 +190,20 @@ __device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const 
     return pair_test_fp64(P, D, sorted[s], sorted[t], cutoff_d);
 }
 
-// Sweep of one row of three neighbour cells (dy, dz fixed, dx = -1, 0, 1)
-// around the cell of the particle in slot s (cell order).  Each unordered
-// pair is visited once, by the particle with the smaller slot (t > s; the
-// neighbour relation of cells is symmetric).  emit(t) is called for every
-// partner passing the tests.
+// Half-shell sweep: the 14 cells of the stencil (the own cell and the 13
+// forward neighbours, offsets (dx, dy, dz) lexicographically above zero) in
+// five rows: row 0 = (dz, dy) = (0, 0) with dx = 0, 1; row 1 = (0, 1); rows
+// 2..4 = (1, -1..1), the last four with dx = -1, 0, 1.  Each unordered pair of
+// neighbouring cells is seen from one side only; in the own cell the partner's
+// slot must follow (t > s).  On a periodic axis with fewer than three cells a
+// forward neighbour can be the own cell or coincide with another neighbour
+// under a different image offset: every (cell, offset) is then a distinct
+// periodic image, the own cell at a non-zero offset is tested against every
+// other particle (t != s), and the domain check (L > 2 range) leaves at most
+// one image of a pair within range, so each pair passes exactly once.
+// emit(t) is called for every partner passing the tests.
+constexpr int SWEEP_ROWS = 5;
+
 template <typename Emit>
 __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const Grid &G,
                                           const int32_t *__restrict__ cell_start, const int32_t *__restrict__ sorted,
@@ -202,7 +211,9 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
                                           const float4 a0, const float4 a1, int cx, int cy, int cz, int row,
                                           int cbase, double cutoff_d, Emit emit)
 {
-    const int dy = row % 3 - 1, dz = row / 3 - 1;
+    const int dz = row >= 2 ? 1 : 0;
+    const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
+    const int dx0 = row == 0 ? 0 : -1;
     int yc = cy + dy, zc = cz + dz;
     if (yc < 0 || yc >= G.nc[1]) {
         if (!D.periodic[1]) return;
@@ -212,6 +223,7 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
         if (!D.periodic[2]) return;
         zc += zc < 0 ? G.nc[2] : -G.nc[2];
     }
+    const int own = cbase + (cz * G.nc[1] + cy) * G.nc[0] + cx;
     const float oy = dy * G.cs[1], oz = dz * G.cs[2];
     const int rowbase = cbase + (zc * G.nc[1] + yc) * G.nc[0];
     // skip neighbour cells no partner of particle s can reach: distance from
@@ -222,10 +234,7 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
     const float ez = dz == 0 ? 0.f : fmaxf(fabsf(oz - a0.z) - hz, 0.f);
     const float r2yz = ey * ey + ez * ez;
     if (r2yz > reach * reach) return;
-    // on a periodic axis with fewer than three cells the same cell recurs with
-    // different image offsets; the domain check (L > 2 range) leaves at most
-    // one image within range, so each partner passes at most once
-    for (int dx = -1; dx <= 1; ++dx) {
+    for (int dx = dx0; dx <= 1; ++dx) {
         int xc = cx + dx;
         if (xc < 0 || xc >= G.nc[0]) {
             if (!D.periodic[0]) continue;
@@ -235,9 +244,13 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
         const float ox = dx * G.cs[0];
         const float ex = dx == 0 ? 0.f : fmaxf(fabsf(ox - a0.x) - hx, 0.f);
         if (ex * ex + r2yz > reach * reach) continue;
+        const bool zero_offset = dx == 0 && dy == 0 && dz == 0;
+        const bool self = c2 == own;
         const int e = cell_start[c2 + 1];
-        for (int t = max(cell_start[c2], s + 1); t < e; ++t)
+        for (int t = zero_offset ? s + 1 : cell_start[c2]; t < e; ++t) {
+            if (self && t == s) continue;
             if (pair_test(P, D, G, s, t, a0, a1, rec0[t], rec1[t], ox, oy, oz, cutoff_d, sorted)) emit(t);
+        }
     }
 }
 
@@ -261,8 +274,8 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_const
                                                      double cutoff_d)
 {
     const int N = P.n;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < 9 * N; f += gridDim.x * blockDim.x) {
-        const int s = f / 9, row = f - 9 * s;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < SWEEP_ROWS * N; f += gridDim.x * blockDim.x) {
+        const int s = f / SWEEP_ROWS, row = f - SWEEP_ROWS * s;
         const int i = sorted[s];
         const int b = ENS ? sbat[s] : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, b);
@@ -504,8 +517,8 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
                                             L.cellc, L.sbat);
     // counts start at zero (the overflow counter too: totals[2], cleared with the flags)
     if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (2 * N + 1) * 4, st), "memset counts"))) return rc;
-    Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, 9 * N);
-    if (!ctx) sw.grid = grid_for(9 * N, sw.block, num_sms, kTuneDefaults[LUB_TUNE_SWEEP].per_sm);
+    Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
+    if (!ctx) sw.grid = grid_for(SWEEP_ROWS * N, sw.block, num_sms, kTuneDefaults[LUB_TUNE_SWEEP].per_sm);
     k_pairs_sweep<ENS><<<sw.grid, sw.block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
                                                      L.sbat, L.cnt, L.slots, L.wbits, L.totals + 2, cap, pi, pj,
                                                      prm.list_cutoff);

@@ -254,3 +254,20 @@ def test_packed_particles_give_the_same_results():
     # force and torque read back in one piece
     ft = pl.ft_particles.cpu().numpy()
     np.testing.assert_array_equal(ft[:3 * P.n].reshape(3, -1).T, b["force"])
+
+
+@pytest.mark.parametrize("L", [9.5, 11.5, 14.5])
+def test_small_periodic_boxes_list_every_pair_once(L):
+    """Two or three cells per periodic axis: a neighbour cell can coincide with
+    another under a different image offset; every pair must still be listed
+    exactly once (against the oracle's all-pairs minimum-image search)."""
+    import paper_1308_6482_gb300 as lub
+    rng = np.random.default_rng(int(L * 10))
+    sh = np.tile([[1.8, 1.2]], (14, 1)).astype(np.float32)   # Rmax 1.8: range 2 * 1.8 + 1 = 4.6
+    parts, dom = gen.suspension(sh, (L, L, L), attach_prob=0.7, seed=int(L * 10))
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    g = run_gpu(parts, dom, "fp64")
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    assert len(pi) > 10
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "fp64", pi, pj)
