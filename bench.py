@@ -306,6 +306,35 @@ def run_ours(args):
             forms_ms[other] = float(np.mean([a.elapsed_time(b) for a, b in eo]))
             del g2
 
+    # the "normal only" model (K~33 alone, Sec. IV C) on the same workload: a
+    # second workload of the same path, graph-replayed with the same flush
+    normal_ms = None
+    if graph is not None:
+        pln = lub.Pipeline(lub.DeviceParticles(parts, dev), dom,
+                           lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch, model="normal"),
+                           capacity=pl.cap, device=dev)
+        pln.build_pairs()
+        with torch.cuda.stream(stream):
+            pln.step(form=form, stream=stream)
+        stream.synchronize()
+        g3 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g3, stream=stream):
+            pln.step(form=form, stream=stream)
+        stream.synchronize()
+        e3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                flush.zero_()
+                g3.replay()
+            for a, b in e3:
+                flush.zero_()
+                a.record(stream)
+                g3.replay()
+                b.record(stream)
+        stream.synchronize()
+        normal_ms = float(np.mean([a.elapsed_time(b) for a, b in e3]))
+        del g3, pln
+
     # per-call device times (eager calls, same stream, L2 flushed), for the roofline
     K2 = min(args.steps, 100)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(K2)]
@@ -393,6 +422,7 @@ def run_ours(args):
                             "merged": "pair build + closest points + resistance with scatter (lub_resistance_apply)",
                             "calls": "pair build + closest points + resistance + apply"}[form],
                    "other_forms_ms_per_step": forms_ms,
+                   "normal_only_model_ms_per_step": normal_ms,
                    "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",

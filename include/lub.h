@@ -62,6 +62,8 @@ extern "C" {
 
 /* lub_params.warm_start */
 #define LUB_WARM_NONE     0 /* Newton starts from the line of centres (Sec. III A) */
+#define LUB_MODEL_FULL 0
+#define LUB_MODEL_NORMAL 1
 #define LUB_WARM_PREVIOUS 1 /* Newton starts from the normal passed in n (in/out) */
 #define LUB_WARM_MLP      2 /* Newton starts from the learned network's prediction
                                (lub_mlp_set must have installed a network) */
@@ -120,6 +122,9 @@ typedef struct {
     double newton_tol;    /* step-size tolerance (radians) of the FP32 stage; the FP64
                              stage converges to rounding                                */
     int32_t warm_start;   /* LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP          */
+    int32_t model;        /* LUB_MODEL_FULL: all 16 elements of K~; LUB_MODEL_NORMAL:
+                             the normal element K~33 alone ("normal only" of Sec.
+                             IV C; for two spheres Ladd's Eq. methods:llub)        */
 } lub_params;
 
 /* Ensemble mode.  With particles.batch_offsets set, the particle arrays hold
@@ -139,7 +144,7 @@ typedef struct {
 /* Fill *p with the paper's values: mu = 1/6, Delta_n = 2/3, Delta_t = 1/2,
  * Delta_r = 1/4 (Eq. results:cutoffs), h_c = eps_c = 0, list_cutoff = 1,
  * LUB_MIXED, fp64_switch = 1e-3, max_newton = 32, newton_tol = 2e-5,
- * LUB_WARM_NONE. */
+ * LUB_WARM_NONE, LUB_MODEL_FULL. */
 void lub_default_params(lub_params *p);
 
 /* Create a context (library-owned scratch, grown on demand by the calls that

@@ -28,7 +28,7 @@ ST_DEGENERATE = 4
 
 # cut-offs of Eq. results:cutoffs and mu = rho nu = 1/6 (tau = 1)
 DEFAULT_PARAMS = dict(mu=1.0 / 6.0, delta_n=2.0 / 3.0, delta_t=0.5, delta_r=0.25,
-                      h_c=0.0, eps_c=0.0, list_cutoff=1.0)
+                      h_c=0.0, eps_c=0.0, list_cutoff=1.0, model=0.0)
 
 _FIELDS = ("x", "y", "z", "qw", "qx", "qy", "qz", "r_par", "r_perp",
            "vx", "vy", "vz", "wx", "wy", "wz")
@@ -58,7 +58,7 @@ class _Domain(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
-                ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff")]
+                ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff", "model")]
 
 
 _lib = None
@@ -142,7 +142,7 @@ def _params(prm):
     if prm:
         p.update({k: v for k, v in prm.items() if k in DEFAULT_PARAMS})
     return _Params(*[float(p[k]) for k in
-                     ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff")])
+                     ("mu", "delta_n", "delta_t", "delta_r", "h_c", "eps_c", "list_cutoff", "model")])
 
 
 def _as_particles(parts):

@@ -83,6 +83,7 @@ typedef struct {
 
 typedef struct {
     double mu, delta_n, delta_t, delta_r, h_c, eps_c, list_cutoff;
+    double model;  /* 0: all elements of K~; 1: "normal only" (K~33 alone, Sec. IV C) */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -697,7 +698,9 @@ static void ktilde(const pairgeom_t *G, const orc_params *p, double he, double K
         for (int d = 0; d < 6; ++d) {
             double D = cutoff_of(p, g, d);
             double v = 0.0;
-            if (he < D) {
+            if (p->model == 1.0 && !(g == 2 && d == 2)) {
+                v = 0.0;
+            } else if (he < D) {
                 if (g == 2 && d == 2)
                     v = G->Hcoef33 * (1.0 / he - 1.0 / D);
                 else

@@ -14,7 +14,7 @@ back) the same four calls process every suspension in one launch per stage.
 """
 from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT, LUB_FP64,
                    LUB_MIXED, LUB_OK, LUB_ST_DEGENERATE, LUB_ST_FP64, LUB_ST_NOCONV, LUB_ST_OVERLAP,
-                   LUB_WARM_MLP, LUB_WARM_NONE, LUB_WARM_PREVIOUS, LUB_MLP_PARAMS, Context, DeviceParticles, LubError, Pipeline,
+                   LUB_WARM_MLP, LUB_WARM_NONE, LUB_WARM_PREVIOUS, LUB_MODEL_FULL, LUB_MODEL_NORMAL, LUB_MLP_PARAMS, Context, DeviceParticles, LubError, Pipeline,
                    default_params, library_path, load_library, lub_apply, lub_closest_points,
                    lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_last_error, lub_mlp_adam,
                    lub_mlp_features, lub_mlp_forward_backward, lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static,

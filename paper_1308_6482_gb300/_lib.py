@@ -20,6 +20,8 @@ LUB_MIXED = 1
 LUB_WARM_NONE = 0
 LUB_WARM_PREVIOUS = 1
 LUB_WARM_MLP = 2
+LUB_MODEL_FULL = 0
+LUB_MODEL_NORMAL = 1
 LUB_MLP_PARAMS = 18692
 LUB_MLP_WORK_PER_SAMPLE = 776
 LUB_ST_OVERLAP = 1
@@ -60,7 +62,8 @@ class lub_params(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("delta_n", ctypes.c_double), ("delta_t", ctypes.c_double),
                 ("delta_r", ctypes.c_double), ("h_c", ctypes.c_double), ("eps_c", ctypes.c_double),
                 ("list_cutoff", ctypes.c_double), ("precision", ctypes.c_int32), ("fp64_switch", ctypes.c_double),
-                ("max_newton", ctypes.c_int32), ("newton_tol", ctypes.c_double), ("warm_start", ctypes.c_int32)]
+                ("max_newton", ctypes.c_int32), ("newton_tol", ctypes.c_double), ("warm_start", ctypes.c_int32),
+                ("model", ctypes.c_int32)]
 
 
 # every exported symbol of include/lub.h
@@ -318,6 +321,8 @@ def default_params(**kw):
             v = {"fp64": LUB_FP64, "mixed": LUB_MIXED}[v]
         if k == "warm_start" and isinstance(v, str):
             v = {"none": LUB_WARM_NONE, "previous": LUB_WARM_PREVIOUS, "mlp": LUB_WARM_MLP}[v]
+        if k == "model" and isinstance(v, str):
+            v = {"full": LUB_MODEL_FULL, "normal": LUB_MODEL_NORMAL}[v]
         setattr(p, k, v)
     return p
 

@@ -176,6 +176,8 @@ int check_params(lub_ctx *ctx, const lub_params *p)
     if (!(p->newton_tol > 0.0)) return lub_set_error(ctx, LUB_ERR_ARG, "newton_tol must be > 0");
     if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS && p->warm_start != LUB_WARM_MLP)
         return lub_set_error(ctx, LUB_ERR_ARG, "warm_start must be LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP");
+    if (p->model != LUB_MODEL_FULL && p->model != LUB_MODEL_NORMAL)
+        return lub_set_error(ctx, LUB_ERR_ARG, "model must be LUB_MODEL_FULL or LUB_MODEL_NORMAL");
     return LUB_OK;
 }
 

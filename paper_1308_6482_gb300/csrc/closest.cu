@@ -701,7 +701,7 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (cap == 0) return LUB_OK;
     int warm = 0;
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
-    const RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c};
+    const RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;

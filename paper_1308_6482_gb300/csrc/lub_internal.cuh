@@ -108,6 +108,7 @@ __device__ __forceinline__ const DView &pair_domain(const DView &D, const Ens &E
 
 struct RParams {
     double mu, delta_n, delta_t, delta_r, h_c, eps_c;
+    int model;  // LUB_MODEL_FULL or LUB_MODEL_NORMAL
 };
 
 inline PView make_pview(const lub_particles *p)

@@ -130,6 +130,25 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
             sx = 0;
             cx = 1;
         }
+        if (R.model == LUB_MODEL_NORMAL) {
+            // "normal only" model (Sec. IV C): K~33 alone, H33 (1/h - 1/Delta_n),
+            // plus the contact branch; for two spheres Ladd's Eq. methods:llub
+            const T PI = T(3.14159265358979323846);
+            const T H33 = T(3) * PI / (sqrt_t(l1) * sqrt_t(l2) * (l1 + l2));
+            const T hq = (he < R.delta_n) ? (T)((R.delta_n - he) / (he * R.delta_n)) : T(0);
+            const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
+            const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
+            const T u3 = dot(x3, sub(Vj, add(vi, cross(Wi, rho_i))));
+            T F3 = (T)R.mu * hq * H33 * u3;
+            if (R.h_c > 0.0 && h <= R.h_c) {
+                const double Fr = (h > 0.0) ? R.eps_c * (R.h_c - h) : R.eps_c * R.h_c;
+                F3 -= (T)Fr;
+            }
+            out[0] = F3 * x3.x; out[1] = F3 * x3.y; out[2] = F3 * x3.z;
+            out[6] = rho_i.x; out[7] = rho_i.y; out[8] = rho_i.z;
+            out[9] = rho_j.x; out[10] = rho_j.y; out[11] = rho_j.z;
+            return;
+        }
         // cubic terms
         T beta[4], kap[4];
         m_rot<T>(cf, sf, G0p, T(0), G2p, T(0), beta);

@@ -51,7 +51,8 @@ int main(void) {
          offsetof(lub_domain, wall_dir), offsetof(lub_domain, n_walls));
   printf("%zu %zu %zu %zu\n", offsetof(lub_params, precision), offsetof(lub_params, fp64_switch),
          offsetof(lub_params, newton_tol), offsetof(lub_params, warm_start));
-  printf("%zu %zu\n", offsetof(lub_particles, batch_offsets), offsetof(lub_particles, n_batches));
+  printf("%zu %zu %zu\n", offsetof(lub_particles, batch_offsets), offsetof(lub_particles, n_batches),
+         offsetof(lub_params, model));
   return 0;
 }
 """
@@ -73,6 +74,7 @@ int main(void) {
     assert vals[10] == L.lub_params.warm_start.offset
     assert vals[11] == L.lub_particles.batch_offsets.offset
     assert vals[12] == L.lub_particles.n_batches.offset
+    assert vals[13] == L.lub_params.model.offset
 
 
 def test_default_params_are_the_papers(lib):

@@ -271,3 +271,15 @@ def test_small_periodic_boxes_list_every_pair_once(L):
     np.testing.assert_array_equal(g["pj"], pj)
     assert len(pi) > 10
     compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "fp64", pi, pj)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_normal_only_model_parity(prec):
+    """The "normal only" model (K~33 alone, Sec. IV C) against the oracle's."""
+    parts, dom = gen.config_mixed_suspension(N=3000, phi=0.3, seed=14)
+    g = run_gpu(parts, dom, prec, model=1)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj, model=1.0), prec, pi, pj)
+    assert np.all(g["FT"][:, 3:] == 0)
+    F = g["FT"][:, :3].astype(np.float64)
+    assert np.abs(np.cross(F, g["n"])).max() <= 1e-5 * np.abs(F).max()

@@ -71,6 +71,44 @@ def test_equal_spheres_normal_force_is_ladds(R, h):
 
 
 # --------------------------------------------------------------------------
+# "normal only" model (Sec. IV C): K~33 alone.  For two equal spheres it is
+# Ladd's Eq. methods:llub in full (every velocity component, rotation too)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("R", [2.0, 4.0])
+@pytest.mark.parametrize("h", [1e-3, 0.05, 0.6])
+def test_normal_only_model_is_ladds_form_for_spheres(R, h):
+    rng = np.random.default_rng(int(R * 100 + h * 1000))
+    v = rng.normal(0, 1e-3, (2, 3))
+    w = rng.normal(0, 1e-3, (2, 3))
+    parts = two_spheres(R, R, h, vx=v[:, 0], vy=v[:, 1], vz=v[:, 2], wx=w[:, 0], wy=w[:, 1], wz=w[:, 2])
+    cp, pf, f, t = run_pair(parts, open_domain(), 0, 1, prm=dict(oracle.DEFAULT_PARAMS, model=1.0))
+    rhat = np.array([-1.0, 0.0, 0.0])
+    f_ladd = -(3 * np.pi * MU * R * R / 2) * rhat * np.dot(rhat, v[0] - v[1]) * (1 / h - 1 / C["delta_c_ladd"])
+    tol = 1e-13 + 4e-16 * (2 * R + h) / h
+    np.testing.assert_allclose(f[0], f_ladd, rtol=tol, atol=tol * np.abs(f_ladd).max())
+    np.testing.assert_allclose(f[1], -f_ladd, rtol=tol, atol=tol * np.abs(f_ladd).max())
+    # a central force on spheres: no torque about either centre
+    assert np.abs(t).max() <= 1e-12 * np.abs(f_ladd).max() * R
+
+
+def test_normal_only_model_keeps_the_normal_element_of_the_full_model():
+    parts, dom, pi, pj = gen.pair_stream(30, seed=88, kind="aspect", gap_range=(1e-3, 0.5))
+    cp = oracle.closest(parts, dom, pi, pj)
+    full = oracle.pair_force(parts, dom, None, pi, pj, cp, want_k=True, want_geom=True)
+    nrm = oracle.pair_force(parts, dom, dict(oracle.DEFAULT_PARAMS, model=1.0), pi, pj, cp, want_k=True,
+                            want_geom=True)
+    u3 = full["geom"][:, 29]                   # normal relative velocity at the contact (u_3)
+    expect = MU * full["Kt"][:, 2, 2] * u3      # K~33 u3 along the normal
+    F = nrm["FT"][:, :3]
+    np.testing.assert_allclose(np.einsum("ij,ij->i", F, cp["n"]), expect, rtol=1e-12,
+                               atol=1e-15 * np.abs(expect).max())
+    # along the normal, and no torque about the contact point
+    np.testing.assert_allclose(np.cross(F, cp["n"]), 0.0, atol=1e-12 * np.abs(F).max())
+    assert np.abs(nrm["FT"][:, 3:]).max() == 0.0
+    np.testing.assert_array_equal(nrm["lever"], full["lever"])
+
+
+# --------------------------------------------------------------------------
 # Jeffrey & Onishi (1984) leading singular coefficients, two spheres a, b
 # --------------------------------------------------------------------------
 def _log_coeff(fun, h1=1e-3, h2=1e-4):
