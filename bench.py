@@ -335,6 +335,45 @@ def run_ours(args):
         normal_ms = float(np.mean([a.elapsed_time(b) for a, b in e3]))
         del g3, pln
 
+    # particle sub-stepping (Sec. II) on the same workload with the contact
+    # branch (h_c = 0.01, eps_c = 100): one LB step = the pair build and 10
+    # sub-steps of (closest points, resistance + scatter, rigid update) at
+    # dt = 0.1 under a constant external force, one CUDA graph per LB step
+    substep = None
+    if graph is not None:
+        pls = lub.Pipeline(lub.DeviceParticles(parts, dev), dom,
+                           lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch, h_c=0.01,
+                                              eps_c=100.0), capacity=pl.cap, device=dev)
+        pls.build_pairs()
+        gf = torch.Generator(device=dev)
+        gf.manual_seed(99)
+        fext = 0.01 * torch.randn(3 * pls.n, generator=gf, device=dev, dtype=torch.float32)
+        with torch.cuda.stream(stream):
+            pls.substeps(10, 1.0, 0.1, f_ext=fext, stream=stream)
+        stream.synchronize()
+        g4 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g4, stream=stream):
+            pls.substeps(10, 1.0, 0.1, f_ext=fext, stream=stream)
+        stream.synchronize()
+        e4 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                flush.zero_()
+                g4.replay()
+            for a, b in e4:
+                flush.zero_()
+                a.record(stream)
+                g4.replay()
+                b.record(stream)
+        stream.synchronize()
+        lb_ms = float(np.mean([a.elapsed_time(b) for a, b in e4]))
+        pairs_s = min(pls.count(), pls.cap)
+        substep = {"ms_per_lb_step": lb_ms, "substeps": 10, "pairs": pairs_s,
+                   "pair_corrections_per_s": 10 * pairs_s / (lb_ms * 1e-3),
+                   "note": "h_c=0.01, eps_c=100, dt=0.1, density 1, external force N(0,0.01^2); 29 launches per "
+                           "LB step in one graph"}
+        del g4, pls
+
     # per-call device times (eager calls, same stream, L2 flushed), for the roofline
     K2 = min(args.steps, 100)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(K2)]
@@ -423,6 +462,7 @@ def run_ours(args):
                             "calls": "pair build + closest points + resistance + apply"}[form],
                    "other_forms_ms_per_step": forms_ms,
                    "normal_only_model_ms_per_step": normal_ms,
+                   "substepping": substep,
                    "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",

@@ -382,6 +382,27 @@ int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, 
                       const double *prev_n, const int32_t *prev_count, int32_t prev_capacity, const int32_t *pair_i,
                       const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n, void *stream);
 
+/*
+ * Particle sub-step (Sec. II: the particle update is decoupled from the
+ * lattice-Boltzmann step and runs at a fraction of it, typically 1/10, so the
+ * strongly varying lubrication forces are followed while the forces from the
+ * fluid stay constant over the LB step).  One explicit sub-step of length dt
+ * for every particle, in double precision (semi-implicit Euler):
+ *   v += dt (F_ext + f) / m;  r += dt v;
+ *   L = I_lab w + dt (T_ext + t);  q <- exp(dt w_mid / 2) q with
+ *   w_mid = I_lab(q)^-1 L;  w = I_lab(q_new)^-1 L,
+ * m = density * 4/3 pi R_par R_perp^2, body inertia I_par = 2/5 m R_perp^2
+ * about the symmetry axis and I_perp = 1/5 m (R_par^2 + R_perp^2).
+ * force, torque: the lubrication force and torque [3][n] about the centres
+ * (lub_apply / lub_resistance_apply output; float for LUB_MIXED, double for
+ * LUB_FP64); f_ext, t_ext: [3][n] float or NULL (e.g. the fluid's, constant
+ * over the LB step).  Writes x, y, z, the quaternion and the velocities of p
+ * in place (they must be writable device memory).  Torque-free motion keeps
+ * the angular momentum exactly.
+ */
+int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int32_t precision,
+                   const float *f_ext, const float *t_ext, double density, double dt, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Launch-shape autotuner (no counterpart in the paper).  The tunable kernels
  * are persistent grid-stride loops; their shape is (threads per block, blocks

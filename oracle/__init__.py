@@ -352,3 +352,60 @@ def mlp_loss_grad(x, tgt, w, want_grad=True, wgt=None):
     loss = lib.orc_mlp_loss_grad(len(x), _dp(x), _dp(tgt), _dp(wg) if wg is not None else None, *args, *gargs,
                                  _dp(out))
     return loss, (g if want_grad else None), out
+
+
+# ---------------------------------------------------------------------------
+# particle sub-step (Sec. II), plain numpy in float64
+# ---------------------------------------------------------------------------
+def rigid_step(parts, force, torque, density, dt, f_ext=None, t_ext=None):
+    """One explicit sub-step of every particle: semi-implicit Euler on the
+    rigid-body equations (translation, then angular momentum, orientation,
+    angular velocity).  force, torque [n, 3] (lubrication, about the centres),
+    f_ext, t_ext [n, 3] or None.  Returns new arrays in a copy of parts
+    (float64)."""
+    out = {k: np.array(v, np.float64) for k, v in parts.items()}
+    n = len(out["x"])
+    a = out["r_perp"]
+    c = out["r_par"]
+    m = density * 4.0 / 3.0 * np.pi * c * a * a
+    ipar = 0.4 * m * a * a
+    iperp = 0.2 * m * (c * c + a * a)
+    F = np.asarray(force, np.float64) + (0 if f_ext is None else np.asarray(f_ext, np.float64))
+    T = np.asarray(torque, np.float64) + (0 if t_ext is None else np.asarray(t_ext, np.float64))
+    v = np.stack([out["vx"], out["vy"], out["vz"]], 1) + dt * F / m[:, None]
+    for d, k in enumerate(("x", "y", "z")):
+        out[k] = out[k] + dt * v[:, d]
+    for d, k in enumerate(("vx", "vy", "vz")):
+        out[k] = v[:, d]
+    q = np.stack([out["qw"], out["qx"], out["qy"], out["qz"]], 1)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+
+    def axis(q):
+        w, x, y, z = q.T
+        s = 2.0 / (w * w + x * x + y * y + z * z)
+        return np.stack([s * (x * z + w * y), s * (y * z - w * x), 1 - s * (x * x + y * y)], 1)
+
+    def inertia(o, vec, inverse):
+        on = np.sum(o * vec, 1, keepdims=True)
+        cp = (1.0 / ipar if inverse else ipar)[:, None]
+        cq = (1.0 / iperp if inverse else iperp)[:, None]
+        return cq * (vec - on * o) + cp * on * o
+
+    o = axis(q)
+    w = np.stack([out["wx"], out["wy"], out["wz"]], 1)
+    L = inertia(o, w, False) + dt * T
+    wm = inertia(o, L, True)
+    ang = dt * np.linalg.norm(wm, axis=1)
+    s = np.where(ang > 0, np.sin(0.5 * ang) * dt / np.where(ang > 0, ang, 1.0), 0.0)
+    r = np.stack([np.cos(0.5 * ang), s * wm[:, 0], s * wm[:, 1], s * wm[:, 2]], 1)
+    r0, r1, r2, r3 = r.T
+    q0, q1, q2, q3 = q.T
+    nq = np.stack([r0 * q0 - r1 * q1 - r2 * q2 - r3 * q3, r0 * q1 + r1 * q0 + r2 * q3 - r3 * q2,
+                   r0 * q2 - r1 * q3 + r2 * q0 + r3 * q1, r0 * q3 + r1 * q2 - r2 * q1 + r3 * q0], 1)
+    nq /= np.linalg.norm(nq, axis=1, keepdims=True)
+    for d, k in enumerate(("qw", "qx", "qy", "qz")):
+        out[k] = nq[:, d]
+    wn = inertia(axis(nq), L, True)
+    for d, k in enumerate(("wx", "wy", "wz")):
+        out[k] = wn[:, d]
+    return out

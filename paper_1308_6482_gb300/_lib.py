@@ -71,7 +71,7 @@ EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
            "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
-           "lub_resistance_apply")
+           "lub_resistance_apply", "lub_rigid_step")
 
 _lib = None
 
@@ -124,6 +124,8 @@ def load_library():
     lib.lub_autotune.restype = ctypes.c_int
     lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
                                  vp, vp, vp, vp, i32, vp]
+    lib.lub_rigid_step.restype = ctypes.c_int
+    lib.lub_rigid_step.argtypes = [vp, P(lub_particles), vp, vp, i32, vp, vp, ctypes.c_double, ctypes.c_double, vp]
     lib.lub_resistance_apply.restype = ctypes.c_int
     lib.lub_resistance_apply.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp,
                                          vp, vp, vp, vp, vp, i32, vp]
@@ -275,6 +277,12 @@ def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_cou
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
         _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
         _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_rigid_step(ctx, particles, force, torque, precision, f_ext, t_ext, density, dt, stream=None):
+    return _check(ctx, load_library().lub_rigid_step(ctx, ctypes.byref(particles), _ptr(force), _ptr(torque),
+                                                     int(precision), _ptr(f_ext), _ptr(t_ext), float(density),
+                                                     float(dt), _stream(stream)))
 
 
 def lub_resistance_apply(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, n, gap, status, FT,
@@ -508,6 +516,21 @@ class Pipeline:
     def apply(self, deterministic=0, accumulate=0, stream=None):
         lub_apply(self.ctx.h, self.pair_i, self.pair_j, self.d_count, self.cap, self.FT, self.lever, self.n,
                   self.force, self.torque, self.prm.precision, accumulate, deterministic, stream=stream)
+
+    def rigid_step(self, density, dt, f_ext=None, t_ext=None, stream=None):
+        """One particle sub-step with this step's lubrication force and torque
+        (lub_rigid_step); moves the particles in place."""
+        lub_rigid_step(self.ctx.h, self.P.c, self.force, self.torque, self.prm.precision, f_ext, t_ext, density, dt,
+                       stream)
+
+    def substeps(self, n_sub, density, dt, f_ext=None, t_ext=None, form="merged", stream=None):
+        """One lattice-Boltzmann step of particle motion: the pair list built
+        once, then n_sub sub-steps of (closest points, resistance + scatter,
+        rigid update) at dt each."""
+        self.build_pairs(sync_count=False, grow=False, stream=stream)
+        for _ in range(n_sub):
+            self.step(build=False, form=form, stream=stream)
+            self.rigid_step(density, dt, f_ext, t_ext, stream)
 
     def keep_previous(self, stream=None):
         """Copy this step's pair list and normals aside for the temporal warm start."""

@@ -401,6 +401,21 @@ int lub_correct(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, con
                           FT, lever, force, torque, accumulate, (cudaStream_t)stream);
 }
 
+int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int32_t precision,
+                   const float *f_ext, const float *t_ext, double density, double dt, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, true))) return rc;
+    if (precision != LUB_FP64 && precision != LUB_MIXED)
+        return lub_set_error(ctx, LUB_ERR_ARG, "precision must be LUB_FP64 or LUB_MIXED");
+    if (!(density > 0.0) || !isfinite(density)) return lub_set_error(ctx, LUB_ERR_ARG, "density must be > 0");
+    if (!(dt >= 0.0) || !isfinite(dt)) return lub_set_error(ctx, LUB_ERR_ARG, "dt must be finite and >= 0");
+    if (p->n > 0 && (!force || !torque)) return lub_set_error(ctx, LUB_ERR_ARG, "force or torque is NULL");
+    return launch_rigid_step(ctx, p, force, torque, precision, f_ext, t_ext, density, dt, (cudaStream_t)stream);
+}
+
 int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, const int32_t *prev_j,
                       const double *prev_n, const int32_t *prev_count, int32_t prev_capacity, const int32_t *pair_i,
                       const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n, void *stream)

@@ -325,6 +325,8 @@ int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DVi
                            const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap, int32_t *d_count,
                            cudaStream_t st);
 int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_t st);
+int launch_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int precision,
+                      const float *fext, const float *text, double rho, double dt, cudaStream_t st);
 int launch_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *qi, const int32_t *qj, const double *qn,
                          const int32_t *q_count, int32_t qcap, const int32_t *pi, const int32_t *pj,
                          const int32_t *d_count, int32_t cap, double *n, cudaStream_t st);
