@@ -509,11 +509,12 @@ def learned_vs_plain(args, dev, stream, flush, steps=20, warmup=3):
                        "[1e-4,1] x min semi-axis" % m, "steps": steps}
     for prec in ("fp64", "mixed"):
         res = {}
-        for form in ("plain", "learned"):
-            prm = lub.default_params(precision=prec, warm_start="mlp" if form == "learned" else "none")
+        for form in ("plain", "learned", "learned_tcgen05"):
+            prm = lub.default_params(precision=prec, warm_start="none" if form == "plain" else "mlp")
             pl = lub.Pipeline(P, dom, prm, capacity=m, device=dev)
-            if form == "learned":
+            if form != "plain":
                 net.install(pl.ctx)
+                lub.lub_mlp_engine(pl.ctx.h, "tcgen05" if form == "learned_tcgen05" else "mma_sync")
             pl.set_pairs(pi, pj)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
             with torch.cuda.stream(stream):
@@ -534,6 +535,9 @@ def learned_vs_plain(args, dev, stream, flush, steps=20, warmup=3):
             del pl
         h0, h1 = res["plain"].pop("h"), res["learned"].pop("h")
         s0, s1 = res["plain"].pop("status"), res["learned"].pop("status")
+        h2, s2 = res["learned_tcgen05"].pop("h"), res["learned_tcgen05"].pop("status")
+        res["max_abs_gap_difference_tcgen05"] = float(np.abs(h2 - h0).max())
+        res["speedup_tcgen05"] = res["learned_tcgen05"]["pairs_per_s"] / res["plain"]["pairs_per_s"]
         scale = np.array([max(parts["r_par"][a], parts["r_perp"][a]) + max(parts["r_par"][b], parts["r_perp"][b])
                           for a, b in zip(pi[:4096], pj[:4096])]).max()
         res["max_abs_gap_difference"] = float(np.abs(h1 - h0).max())

@@ -267,6 +267,17 @@ int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const 
  * first call allocates the context's copy. */
 int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const float *istd, void *stream);
 
+/* Tensor-core path of the network (no counterpart in the paper):
+ * LUB_MLP_MMA_SYNC (default) runs it with warp-level mma.sync, one warp per
+ * 32 pairs, activations in registers; LUB_MLP_TCGEN05 with tcgen05.mma, 128
+ * pairs per CTA, accumulators in tensor memory, operands staged in shared
+ * memory (weights by one bulk copy per CTA).  Same results up to the order
+ * of the FP32 accumulation.  A bounded wait of the tcgen05 path that times
+ * out sets bit 3 (value 8) of the context's flags and ends the kernel. */
+#define LUB_MLP_MMA_SYNC 0
+#define LUB_MLP_TCGEN05 1
+int lub_mlp_engine(lub_ctx *ctx, int32_t engine);
+
 /* The network's outputs for every pair on the tensor cores (BF16 weights and
  * activations, FP32 accumulate): pq [4][capacity] float, the predicted
  * corrections to (p_i, q_i, p_j, q_j) of the line-of-centres start;

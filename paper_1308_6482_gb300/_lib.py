@@ -20,6 +20,8 @@ LUB_MIXED = 1
 LUB_WARM_NONE = 0
 LUB_WARM_PREVIOUS = 1
 LUB_WARM_MLP = 2
+LUB_MLP_MMA_SYNC = 0
+LUB_MLP_TCGEN05 = 1
 LUB_MODEL_FULL = 0
 LUB_MODEL_NORMAL = 1
 LUB_MLP_PARAMS = 18692
@@ -71,7 +73,7 @@ EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
            "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
-           "lub_resistance_apply", "lub_rigid_step")
+           "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine")
 
 _lib = None
 
@@ -124,6 +126,8 @@ def load_library():
     lib.lub_autotune.restype = ctypes.c_int
     lib.lub_autotune.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp, vp, vp, vp,
                                  vp, vp, vp, vp, i32, vp]
+    lib.lub_mlp_engine.restype = ctypes.c_int
+    lib.lub_mlp_engine.argtypes = [vp, i32]
     lib.lub_rigid_step.restype = ctypes.c_int
     lib.lub_rigid_step.argtypes = [vp, P(lub_particles), vp, vp, i32, vp, vp, ctypes.c_double, ctypes.c_double, vp]
     lib.lub_resistance_apply.restype = ctypes.c_int
@@ -277,6 +281,12 @@ def lub_autotune(ctx, particles, domain, params, pair_i, pair_j, capacity, d_cou
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j), int(capacity),
         _ptr(d_count), _ptr(n), _ptr(gap), _ptr(status), _ptr(iters), _ptr(FT), _ptr(lever), _ptr(force),
         _ptr(torque), int(reps), _stream(stream)))
+
+
+def lub_mlp_engine(ctx, engine):
+    if isinstance(engine, str):
+        engine = {"mma_sync": LUB_MLP_MMA_SYNC, "tcgen05": LUB_MLP_TCGEN05}[engine]
+    return _check(ctx, load_library().lub_mlp_engine(ctx, int(engine)))
 
 
 def lub_rigid_step(ctx, particles, force, torque, precision, f_ext, t_ext, density, dt, stream=None):

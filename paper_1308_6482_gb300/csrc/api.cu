@@ -444,8 +444,9 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
     if (!ctx->mlp) {
         const size_t bw = (size_t)(8 * 32 + 64 * 32) * sizeof(uint4) + (size_t)(8 * 32) * sizeof(uint2);
         const size_t bf = (size_t)(128 + 128 + 8 + 12 + 12) * sizeof(float);
+        const size_t btc = mlp_tc_image_bytes();
         void *mem = nullptr;
-        cudaError_t e = cudaMalloc(&mem, bw + bf + 256);
+        cudaError_t e = cudaMalloc(&mem, ((bw + 255) & ~(size_t)255) + ((bf + 255) & ~(size_t)255) + btc);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return lub_set_error(ctx, LUB_ERR_NOMEM, "cudaMalloc of the network failed");
@@ -465,6 +466,7 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
         M->b3 = f + 256;
         M->mean = f + 264;
         M->istd = f + 276;
+        M->tc_image = c + ((bw + 255) & ~(size_t)255) + ((bf + 255) & ~(size_t)255);
         ctx->mlp = M;
         ctx->mlp_mem = mem;
     }
@@ -474,8 +476,26 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
                                  "copy mean");
     if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(M.istd, istd, 12 * sizeof(float), cudaMemcpyDeviceToDevice, st),
                                  "copy istd");
+    // the tcgen05 image ends with mean and istd
+    char *tail = (char *)M.tc_image + mlp_tc_image_bytes() - 24 * sizeof(float);
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyAsync(tail, mean, 12 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                                 "copy mean");
+    if (!rc)
+        rc = lub_check_cuda(ctx, cudaMemcpyAsync(tail + 12 * sizeof(float), istd, 12 * sizeof(float),
+                                                 cudaMemcpyDeviceToDevice, st),
+                            "copy istd");
     if (!rc) ctx->mlp_ready = true;
     return rc;
+}
+
+int lub_mlp_engine(lub_ctx *ctx, int32_t engine)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    if (engine != LUB_MLP_MMA_SYNC && engine != LUB_MLP_TCGEN05)
+        return lub_set_error(ctx, LUB_ERR_ARG, "engine must be LUB_MLP_MMA_SYNC or LUB_MLP_TCGEN05");
+    ctx->mlp_engine = engine;
+    return LUB_OK;
 }
 
 int lub_mlp_predict(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const int32_t *pair_i,

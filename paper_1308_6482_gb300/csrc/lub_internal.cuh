@@ -24,6 +24,7 @@ struct lub_ctx {
     void *mlp_mem = nullptr;     // its device storage
     bool mlp_ready = false;
     int mlp_smem_set = 0;        // bit k: shared-memory attribute set for instantiation k
+    int mlp_engine = 0;          // LUB_MLP_MMA_SYNC or LUB_MLP_TCGEN05
     // device copies of the ensemble tables (slot 0: domains, slot 1: cell grids),
     // with the host bytes they were uploaded from; buffers only grow, retired
     // ones are freed with the context

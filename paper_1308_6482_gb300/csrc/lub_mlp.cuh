@@ -17,6 +17,7 @@ struct MlpDevice {
     uint2 *F3;
     float *b1, *b2, *b3;  // [128], [128], [8]
     float *mean, *istd;   // [12] each
+    void *tc_image;       // the tcgen05 kernel's weights: an image of its shared-memory block
 };
 
 static_assert(LUB_MLP_PARAMS == 128 * 12 + 128 + 128 * 128 + 128 + 4 * 128 + 4, "parameter count");
@@ -32,3 +33,4 @@ int launch_mlp_forward_backward(lub_ctx *ctx, const float *params, const float *
 int launch_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, float *v, int n, int t, float lr,
                     float b1, float b2, float eps, cudaStream_t st);
 int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaStream_t st);
+size_t mlp_tc_image_bytes();

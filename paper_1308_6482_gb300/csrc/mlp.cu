@@ -439,6 +439,208 @@ __device__ __forceinline__ V3<float> shifted_normal(const PView &P, int k, const
     return normalized(nl);
 }
 
+// a pair's indices, domain and validity, and its standardised features f
+// (zero for an invalid pair)
+struct PairIn {
+    int i, j;
+    const DView *D;
+    bool ok;
+};
+
+template <bool ENS>
+__device__ __forceinline__ PairIn pair_inputs(const PView &P, const DView &D0, const Ens &E,
+                                              const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int k,
+                                              int count, const float *mean, const float *istd, float f[NI])
+{
+    PairIn in{-1, -1, &D0, false};
+    if (k < count) {
+        in.i = pi[k];
+        in.j = pj[k];
+        bool alien;
+        in.D = &pair_domain<ENS>(D0, E, in.i, in.j, &alien);
+        in.ok = !alien && in.i >= 0 && in.i < P.n && in.j >= 0 && in.j < P.n && in.i != in.j &&
+                shape_ok(P.rpar[in.i], P.rperp[in.i]) && shape_ok(P.rpar[in.j], P.rperp[in.j]);
+    }
+    if (in.ok) {
+        pair_features(P, *in.D, in.i, in.j, mean, istd, f);
+        for (int a = 0; a < NI; ++a)
+            if (!isfinite(f[a])) in.ok = false;
+    }
+    if (!in.ok)
+        for (int a = 0; a < NI; ++a) f[a] = 0.f;
+    return in;
+}
+
+// the network's outputs y of pair k to pq, and Newton's start normal to n0
+__device__ __forceinline__ void pair_outputs(const PView &P, const PairIn &in, const float4 y, int k, int count,
+                                             size_t C, double *__restrict__ n0, float *__restrict__ pq)
+{
+    if (k < count && pq) {
+        pq[k] = in.ok ? y.x : 0.f;
+        pq[C + k] = in.ok ? y.y : 0.f;
+        pq[2 * C + k] = in.ok ? y.z : 0.f;
+        pq[3 * C + k] = in.ok ? y.w : 0.f;
+    }
+    if (k < count && n0) {
+        V3<float> s0 = mk<float>(0, 0, 0);
+        if (in.ok) {
+            // corrections to the parameters of the line-of-centres start
+            const V3<float> d = cvt<float>(min_image(*in.D, sub(load_pos(P, in.j), load_pos(P, in.i))));
+            const V3<float> e = normalized(d);
+            const V3<float> ni = shifted_normal(P, in.i, rot_of(P, in.i), e, y.x, y.y);
+            const V3<float> nj = shifted_normal(P, in.j, rot_of(P, in.j), scl(-1.0f, e), y.z, y.w);
+            const V3<float> s = sub(ni, nj);
+            const float l2 = dot(s, s);
+            if (l2 > 1e-12f && isfinite(l2)) s0 = scl(rsqrtf(l2), s);
+        }
+        n0[k] = s0.x;
+        n0[C + k] = s0.y;
+        n0[2 * C + k] = s0.z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inference on the 5th-generation tensor cores (tcgen05, accumulators in TMEM)
+// ---------------------------------------------------------------------------
+// A CTA of 256 threads takes 128 pairs at a time; warps w and w + 4 share
+// TMEM lane quarter w, so every row (pair) has two threads, each taking 64 of
+// its 128 columns in the epilogues; the first thread of a row also computes
+// the pair's features and its outputs:
+//   features -> X (128 x 16, shared memory)
+//   layer 1:  one tcgen05.mma (M 128, N 128, K 16) into TMEM columns [0, 128)
+//   epilogue: each thread loads its half row (tcgen05.ld), adds the bias,
+//             applies GELU and writes BF16 into H (128 x 128, shared memory)
+//   layer 2:  eight MMAs (K 16 each) into the same columns (the epilogue has
+//             read them), epilogue to H
+//   layer 3:  eight MMAs (N 16: outputs padded 4 -> 16) into columns [0, 16)
+//   outputs:  the first thread of each row loads its four outputs and forms
+//             Newton's start.
+// One elected thread issues the MMAs and commits them to an mbarrier the CTA
+// waits on.  Operands are K-major without swizzle: 8-row x 16-byte core
+// matrices, element (r, k) of an R x K operand at byte
+//   (r / 8) SBO + (k / 8) 128 + (r % 8) 16 + (k % 8) 2,   SBO = K / 8 x 128,
+// so the K-th 16-element step of an MMA starts 256 bytes further.  The
+// weights (B operands) sit in global memory as an image of the shared-memory
+// block and arrive with one bulk copy (cp.async.bulk) per CTA.  Every wait is
+// bounded: a timeout raises an error bit, waits (bounded) for the MMAs in
+// flight, frees the TMEM and returns.
+constexpr int TC_ROWS = 128;
+constexpr int TC_THREADS = 256;           // two threads per row: each takes 64 of its 128 columns
+constexpr uint32_t TC_TMEM_COLS = 128;    // every layer's accumulator in columns [0, 128)
+constexpr long kTcSpinLimit = 1l << 24;
+
+__host__ __device__ constexpr uint32_t cm_offset(int r, int k, int K)
+{
+    return (uint32_t)((r >> 3) * (K / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+struct TcImage {                     // the bytes of one bulk copy (multiple of 16)
+    __nv_bfloat16 W1[128 * 16];      // B of layer 1: N 128 x K 16 (inputs 12 -> 16)
+    __nv_bfloat16 W2[128 * 128];     // B of layer 2
+    __nv_bfloat16 W3[16 * 128];      // B of layer 3: N 16 (outputs 4 -> 16) x K 128
+    float b1[128], b2[128], b3[16];
+    float mean[NI], istd[NI];
+};
+static_assert(sizeof(TcImage) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+struct TcSmem {
+    TcImage w;
+    __nv_bfloat16 X[TC_ROWS * 16];   // A of layer 1
+    __nv_bfloat16 H[TC_ROWS * 128];  // A of layers 2 and 3
+    unsigned long long mbar_w, mbar_mma;
+    uint32_t tmem;
+    int stop;
+    // padding: above 76 KB a third CTA never fits an SM, so two CTAs x 256
+    // columns never exceed the SM's 512 TMEM columns (allocation never waits)
+    unsigned char pad[4096];
+};
+static_assert(sizeof(TcSmem) > 228 * 1024 / 3, "at most two CTAs per SM");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row) byte
+// offsets, the fixed version bits of this architecture, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+// bounded wait for the phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long it = 0; it < kTcSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive TMEM columns of this thread's lane (row)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// epilogue of a hidden layer: TMEM columns [c0, c0 + 64) of this thread's row
+// + bias, GELU, BF16 into the same columns of its row of H
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int c0, const float *bias, __nv_bfloat16 *H,
+                                                   int row)
+{
+#pragma unroll 1
+    for (int c = c0; c < c0 + 64; c += 32) {
+        float v[32];
+        tmem_ld32(trow + c, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint4 u;
+            u.x = gelu2(v[8 * g + 0] + bias[c + 8 * g + 0], v[8 * g + 1] + bias[c + 8 * g + 1]);
+            u.y = gelu2(v[8 * g + 2] + bias[c + 8 * g + 2], v[8 * g + 3] + bias[c + 8 * g + 3]);
+            u.z = gelu2(v[8 * g + 4] + bias[c + 8 * g + 4], v[8 * g + 5] + bias[c + 8 * g + 5]);
+            u.w = gelu2(v[8 * g + 6] + bias[c + 8 * g + 6], v[8 * g + 7] + bias[c + 8 * g + 7]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(H) + cm_offset(row, c + 8 * g, 128)) = u;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -474,49 +676,136 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_mlp_start(PView P, const 
     const size_t C = (size_t)cap;
     for (int base = (blockIdx.x * INF_WARPS + w) * 32; base < count; base += gridDim.x * INF_WARPS * 32) {
         const int k = base + lane;
-        int i = -1, j = -1;
         float f[NI];
-        bool ok = false;
-        const DView *Dp = &D0;
-        if (k < count) {
-            i = pi[k];
-            j = pj[k];
-            bool alien;
-            Dp = &pair_domain<ENS>(D0, E, i, j, &alien);
-            ok = !alien && i >= 0 && i < P.n && j >= 0 && j < P.n && i != j && shape_ok(P.rpar[i], P.rperp[i]) &&
-                 shape_ok(P.rpar[j], P.rperp[j]);
-        }
-        if (ok) {
-            pair_features(P, *Dp, i, j, S.mean, S.istd, f);
-            for (int a = 0; a < NI; ++a)
-                if (!isfinite(f[a])) ok = false;
-        }
-        if (!ok)
-            for (int a = 0; a < NI; ++a) f[a] = 0.f;
+        PairIn in = pair_inputs<ENS>(P, D0, E, pi, pj, k, count, S.mean, S.istd, f);
         const float4 y = warp_mlp(S, S.x[w], S.y[w], f, lane);
-        if (k < count && pq) {
-            pq[k] = ok ? y.x : 0.f;
-            pq[C + k] = ok ? y.y : 0.f;
-            pq[2 * C + k] = ok ? y.z : 0.f;
-            pq[3 * C + k] = ok ? y.w : 0.f;
-        }
-        if (k < count && n0) {
-            V3<float> s0 = mk<float>(0, 0, 0);
-            if (ok) {
-                // corrections to the parameters of the line-of-centres start
-                const V3<float> d = cvt<float>(min_image(*Dp, sub(load_pos(P, j), load_pos(P, i))));
-                const V3<float> e = normalized(d);
-                const V3<float> ni = shifted_normal(P, i, rot_of(P, i), e, y.x, y.y);
-                const V3<float> nj = shifted_normal(P, j, rot_of(P, j), scl(-1.0f, e), y.z, y.w);
-                const V3<float> s = sub(ni, nj);
-                const float l2 = dot(s, s);
-                if (l2 > 1e-12f && isfinite(l2)) s0 = scl(rsqrtf(l2), s);
-            }
-            n0[k] = s0.x;
-            n0[C + k] = s0.y;
-            n0[2 * C + k] = s0.z;
-        }
+        pair_outputs(P, in, y, k, count, C, n0, pq);
     }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(TC_THREADS) k_mlp_start_tc(PView P, const __grid_constant__ DView D0, Ens E,
+                                                          const int32_t *__restrict__ pi,
+                                                          const int32_t *__restrict__ pj,
+                                                          const int32_t *__restrict__ d_count, int32_t cap,
+                                                          const TcImage *__restrict__ img, double *__restrict__ n0,
+                                                          float *__restrict__ pq, int32_t *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TC_ROWS - 1), half = tid >> 7;  // row = 32 (warp % 4) + lane
+    const uint32_t mbw = smem_u32(&S.mbar_w), mbm = smem_u32(&S.mbar_mma);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&S.tmem)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbw));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbm));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.stop = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lane quarter
+    // the weights: one bulk copy into the shared block
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbw),
+                     "r"((uint32_t)sizeof(TcImage)) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(&S.w)), "l"(img), "r"((uint32_t)sizeof(TcImage)), "r"(mbw) : "memory");
+    }
+    bool alive = mbar_wait(mbw, 0);
+    uint32_t phase = 0;
+    const uint32_t sX = smem_u32(S.X), sH = smem_u32(S.H);
+    const uint32_t sW1 = smem_u32(S.w.W1), sW2 = smem_u32(S.w.W2), sW3 = smem_u32(S.w.W3);
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    for (int base = blockIdx.x * TC_ROWS; base < count; base += gridDim.x * TC_ROWS) {
+        if (!alive) S.stop = 1;
+        __syncthreads();
+        if (S.stop) break;
+        const int k = base + row;
+        float f[NI];
+        PairIn in{-1, -1, &D0, false};
+        if (half == 0) {
+            in = pair_inputs<ENS>(P, D0, E, pi, pj, k, count, S.w.mean, S.w.istd, f);
+            uint4 lo, hi;
+            lo.x = pack_bf16(f[0], f[1]);
+            lo.y = pack_bf16(f[2], f[3]);
+            lo.z = pack_bf16(f[4], f[5]);
+            lo.w = pack_bf16(f[6], f[7]);
+            hi.x = pack_bf16(f[8], f[9]);
+            hi.y = pack_bf16(f[10], f[11]);
+            hi.z = 0u;
+            hi.w = 0u;
+            unsigned char *X = reinterpret_cast<unsigned char *>(S.X);
+            *reinterpret_cast<uint4 *>(X + cm_offset(row, 0, 16)) = lo;
+            *reinterpret_cast<uint4 *>(X + cm_offset(row, 8, 16)) = hi;
+        }
+        // layer 1
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            tc_mma(tmem, tc_desc(sX, 128, 256), tc_desc(sW1, 128, 256), tc_idesc(128, 128), 0u);
+            tc_commit(mbm);
+        }
+        alive = mbar_wait(mbm, phase) && alive;
+        phase ^= 1u;
+        tc_fence_after();
+        tc_hidden_epilogue(trow, 64 * half, S.w.b1, S.H, row);
+        // layer 2
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (uint32_t kk = 0; kk < 8; ++kk)
+                tc_mma(tmem, tc_desc(sH + 256 * kk, 128, 2048), tc_desc(sW2 + 256 * kk, 128, 2048),
+                       tc_idesc(128, 128), kk);
+            tc_commit(mbm);
+        }
+        alive = mbar_wait(mbm, phase) && alive;
+        phase ^= 1u;
+        tc_fence_after();
+        // every thread has read its layer-2 input from H before it is overwritten:
+        // the MMAs that read H completed (the wait above)
+        tc_hidden_epilogue(trow, 64 * half, S.w.b2, S.H, row);
+        // layer 3
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (uint32_t kk = 0; kk < 8; ++kk)
+                tc_mma(tmem, tc_desc(sH + 256 * kk, 128, 2048), tc_desc(sW3 + 256 * kk, 128, 2048), tc_idesc(128, 16),
+                       kk);
+            tc_commit(mbm);
+        }
+        alive = mbar_wait(mbm, phase) && alive;
+        phase ^= 1u;
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(trow, v);  // all warps: the load is warp-collective
+        if (half == 0) {
+            const float4 y = make_float4(v[0] + S.w.b3[0], v[1] + S.w.b3[1], v[2] + S.w.b3[2], v[3] + S.w.b3[3]);
+            pair_outputs(P, in, y, k, count, C, n0, pq);
+        }
+        tc_fence_before();
+    }
+    if (!alive && err) atomicOr(err, 8);
+    // a timeout may leave MMAs in flight: wait for the last commit (bounded) before freeing TMEM
+    if (!alive) mbar_wait(mbm, phase);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 size_t mlp_start_smem() { return sizeof(InfSmem); }
@@ -525,6 +814,23 @@ template <bool ENS>
 int launch_mlp_start_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi,
                        const int32_t *pj, const int32_t *d_count, int32_t cap, double *n0, float *pq, cudaStream_t st)
 {
+    if (ctx->mlp_engine == LUB_MLP_TCGEN05) {
+        const size_t smem = sizeof(TcSmem);
+        if (!(ctx->mlp_smem_set & (4 << ENS))) {
+            int rc = lub_check_cuda(ctx,
+                                    cudaFuncSetAttribute(k_mlp_start_tc<ENS>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                    "shared memory attribute");
+            if (rc) return rc;
+            ctx->mlp_smem_set |= 4 << ENS;
+        }
+        const MlpDevice &M = *(const MlpDevice *)ctx->mlp;
+        const int tiles = (cap + TC_ROWS - 1) / TC_ROWS;
+        const int grid = tiles < 2 * ctx->num_sms ? (tiles > 0 ? tiles : 1) : 2 * ctx->num_sms;
+        k_mlp_start_tc<ENS><<<grid, TC_THREADS, smem, st>>>(P, D, E, pi, pj, d_count, cap,
+                                                         (const TcImage *)M.tc_image, n0, pq, ctx->d_flags);
+        return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_start_tc launch");
+    }
     const size_t smem = mlp_start_smem();
     if (!(ctx->mlp_smem_set & (1 << ENS))) {
         int rc = lub_check_cuda(
@@ -605,6 +911,30 @@ __device__ __forceinline__ uint32_t frag_b(const float *W, int nv, int kv, int n
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// the tcgen05 image: W in the core-matrix layout of the B operands, biases,
+// standardisation (mean, istd are copied in by the host after this kernel)
+__global__ void k_mlp_pack_tc(const float *__restrict__ params, TcImage *__restrict__ T)
+{
+    const float *W1 = params, *b1 = W1 + NH * NI, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NO * NH;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NH * NH; e += gridDim.x * blockDim.x) {
+        const int n = e / NH, k = e % NH;
+        T->W2[cm_offset(n, k, 128) / 2] = __float2bfloat16_rn(W2[n * NH + k]);
+        if (e < 128 * 16) {
+            const int n1 = e / 16, k1 = e % 16;
+            T->W1[cm_offset(n1, k1, 16) / 2] = __float2bfloat16_rn(k1 < NI ? W1[n1 * NI + k1] : 0.f);
+        }
+        if (e < 16 * 128) {
+            const int n3 = e / NH, k3 = e % NH;
+            T->W3[cm_offset(n3, k3, 128) / 2] = __float2bfloat16_rn(n3 < NO ? W3[n3 * NH + k3] : 0.f);
+        }
+        if (e < NH) {
+            T->b1[e] = b1[e];
+            T->b2[e] = b2[e];
+        }
+        if (e < 16) T->b3[e] = e < NO ? b3[e] : 0.f;
+    }
+}
+
 __global__ void k_mlp_pack(const float *__restrict__ params, MlpDevice M)
 {
     const float *W1 = params, *b1 = W1 + NH * NI, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NO * NH;
@@ -626,8 +956,11 @@ __global__ void k_mlp_pack(const float *__restrict__ params, MlpDevice M)
     }
 }
 
+size_t mlp_tc_image_bytes() { return sizeof(TcImage); }
+
 int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaStream_t st)
 {
+    k_mlp_pack_tc<<<16, 256, 0, st>>>(params, (TcImage *)M.tc_image);
     k_mlp_pack<<<8, 256, 0, st>>>(params, M);
     return lub_check_cuda(ctx, cudaGetLastError(), "mlp pack launch");
 }

@@ -112,7 +112,8 @@ def bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def test_tensor_core_inference_matches_bf16_reference(env):
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_tensor_core_inference_matches_bf16_reference(env, engine):
     lub, torch = env
     from paper_1308_6482_gb300.mlp import WarmStartMLP, init_params, unpack
     from scipy.special import erf
@@ -126,6 +127,7 @@ def test_tensor_core_inference_matches_bf16_reference(env):
     net = WarmStartMLP(params, mean, istd)
     ctx = lub.Context()
     net.install(ctx)
+    lub.lub_mlp_engine(ctx.h, engine)
     P, D, tpi, tpj = device_pairs(lub, torch, parts, dom, pi, pj)
     m = len(pi)
     dc = torch.tensor([m], dtype=torch.int32, device="cuda")
@@ -161,6 +163,33 @@ def test_zero_network_gives_back_the_cold_start(env):
     warm = pl.results()
     assert np.mean(warm["iters"] != cold["iters"]) < 0.01
     np.testing.assert_allclose(warm["h"], cold["h"], rtol=0, atol=1e-10)
+
+
+def test_tcgen05_engine_gives_the_same_start(env):
+    """The two tensor-core paths: the same outputs up to the order of the FP32
+    accumulation (BF16 activations can round differently), the same Newton
+    results."""
+    lub, torch = env
+    from paper_1308_6482_gb300.mlp import WarmStartMLP
+    parts, dom, pi, pj = gen.pair_stream(3000, seed=74, kind="aspect", gap_range=(1e-4, 1.0), gap_scale="min_axis")
+    net = WarmStartMLP.load(WEIGHTS)
+    out = {}
+    for engine in ("mma_sync", "tcgen05"):
+        pl = lub.Pipeline(parts, dom, lub.default_params(precision="fp64", warm_start="mlp"))
+        net.install(pl.ctx)
+        lub.lub_mlp_engine(pl.ctx.h, engine)
+        pl.set_pairs(pi, pj)
+        pq = torch.zeros(4 * pl.cap, dtype=torch.float32, device="cuda")
+        lub.lub_mlp_predict(pl.ctx.h, pl.P.c, pl.D, pl.pair_i, pl.pair_j, pl.d_count, pl.cap, pq)
+        pl.closest()
+        torch.cuda.synchronize()
+        out[engine] = (pq.cpu().numpy().reshape(4, -1)[:, :len(pi)].T, pl.results())
+    (ya, ra), (yb, rb) = out["mma_sync"], out["tcgen05"]
+    err = np.abs(ya - yb)
+    assert np.median(err) <= 2e-3 * np.abs(ya).max() and err.max() <= 3e-2 * np.abs(ya).max()
+    np.testing.assert_array_equal(ra["status"] & 7, rb["status"] & 7)
+    np.testing.assert_allclose(ra["h"], rb["h"], rtol=0, atol=1e-10)
+    assert abs(ra["iters"].mean() - rb["iters"].mean()) < 0.05
 
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1308_6482_gb300",
