@@ -905,13 +905,20 @@ void orc_surface_pq(const orc_particles *P, int64_t k, const double y[3], double
     pq[1] = atan2(yb[1], yb[0]);
 }
 
-/* The 12 input features of a pair (i, j):
- *   [0..2]  d = r_j - r_i (minimum image) in i's body frame, over R_perp,i
- *   [3..6]  relative rotation q_i^-1 q_j of the normalised quaternions, w >= 0
- *   [7..10] ln R_par,i, ln R_perp,i, ln R_par,j, ln R_perp,j
- *   [11]    asinh(g(d^)/a): the support-function gap estimate along the line
+/* The 12 input features of a pair (i, j).  They describe the pair up to
+ * the motions that leave the targets unchanged: rigid motions of the pair,
+ * rotations of i about its symmetry axis and of j about its own.  Frame: i's
+ * body frame turned about its axis until d = r_j - r_i (minimum image) lies
+ * in the half-plane y = 0, x >= 0 (unturned when d lies on the axis).
+ *   [0]     rho / R_perp,i: distance of d from i's axis
+ *   [1]     d_z / R_perp,i: component of d along i's axis
+ *   [2..4]  j's symmetry axis in that frame
+ *   [5..8]  ln R_par,i, ln R_perp,i, ln R_par,j, ln R_perp,j
+ *   [9]     asinh(g(d^)/a): the support-function gap estimate along the line
  *           of centres, g = |d| - sigma_i(d^) - sigma_j(d^), over the smallest
- *           semi-axis a of the pair. */
+ *           semi-axis a of the pair
+ *   [10,11] ln(sigma_i(d^) / R_perp,i), ln(sigma_j(d^) / R_perp,j): the
+ *           half-widths along the line of centres. */
 void orc_mlp_features(const orc_particles *P, const orc_domain *D, int64_t np, const int32_t *pi,
                       const int32_t *pj, double *feat)
 {
@@ -924,38 +931,30 @@ void orc_mlp_features(const orc_particles *P, const orc_domain *D, int64_t np, c
         min_image(D, si.r, sj.r, d);
         double db[3];
         to_body(&si, d, db);
+        const double rho = sqrt(db[0] * db[0] + db[1] * db[1]);
+        const double c = rho > 0.0 ? db[0] / rho : 1.0, s = rho > 0.0 ? db[1] / rho : 0.0;
+        double oj[3] = {sj.Q[0][2], sj.Q[1][2], sj.Q[2][2]}, ob[3];
+        to_body(&si, oj, ob);
         double *f = feat + 12 * k;
-        for (int a = 0; a < 3; ++a) f[a] = db[a] / si.Rperp;
-        double qa[4] = {P->qw[i], P->qx[i], P->qy[i], P->qz[i]};
-        double qb[4] = {P->qw[j], P->qx[j], P->qy[j], P->qz[j]};
-        double na = sqrt(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
-        double nb = sqrt(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
-        for (int a = 0; a < 4; ++a) {
-            qa[a] /= na;
-            qb[a] /= nb;
-        }
-        /* conj(qa) * qb (Hamilton product) */
-        double w = qa[0] * qb[0] + qa[1] * qb[1] + qa[2] * qb[2] + qa[3] * qb[3];
-        double x = qa[0] * qb[1] - qa[1] * qb[0] - qa[2] * qb[3] + qa[3] * qb[2];
-        double y = qa[0] * qb[2] + qa[1] * qb[3] - qa[2] * qb[0] - qa[3] * qb[1];
-        double z = qa[0] * qb[3] - qa[1] * qb[2] + qa[2] * qb[1] - qa[3] * qb[0];
-        double sg = w < 0.0 ? -1.0 : 1.0;
-        f[3] = sg * w;
-        f[4] = sg * x;
-        f[5] = sg * y;
-        f[6] = sg * z;
-        f[7] = log(si.Rpar);
-        f[8] = log(si.Rperp);
-        f[9] = log(sj.Rpar);
-        f[10] = log(sj.Rperp);
+        f[0] = rho / si.Rperp;
+        f[1] = db[2] / si.Rperp;
+        f[2] = c * ob[0] + s * ob[1];
+        f[3] = -s * ob[0] + c * ob[1];
+        f[4] = ob[2];
+        f[5] = log(si.Rpar);
+        f[6] = log(si.Rperp);
+        f[7] = log(sj.Rpar);
+        f[8] = log(sj.Rperp);
         double dl = norm3(d);
         double e[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
-        double g = dl - support(&si, e) - support(&sj, e);
+        const double wi = support(&si, e), wj = support(&sj, e);
         double a = si.Rpar;
         if (si.Rperp < a) a = si.Rperp;
         if (sj.Rpar < a) a = sj.Rpar;
         if (sj.Rperp < a) a = sj.Rperp;
-        f[11] = asinh(g / a);
+        f[9] = asinh((dl - wi - wj) / a);
+        f[10] = log(wi / si.Rperp);
+        f[11] = log(wj / sj.Rperp);
     }
 }
 

@@ -2,10 +2,13 @@
 // (GELU) mapping a pair's relative pose to the surface parameters
 // (p_i, q_i, p_j, q_j) of Eq. lub:spheroid at its closest points.
 //
-//   features  12 per pair: d in i's body frame over R_perp,i; the relative
-//             rotation q_i^-1 q_j (w >= 0); ln of the four semi-axes; asinh of
-//             the support-function gap estimate along d over the smallest
-//             semi-axis; standardised with the training set's mean and 1/std.
+//   features  12 per pair, invariant under the motions that leave the
+//             targets unchanged (rigid motions, rotations of a particle about
+//             its own axis): d and j's axis in i's body frame turned about
+//             i's axis until d lies in its x-z half-plane; ln of the four
+//             semi-axes; asinh of the support-function gap estimate along d
+//             over the smallest semi-axis; the two half-widths along d;
+//             standardised with the training set's mean and 1/std.
 //   outputs   corrections to the surface parameters of the line-of-centres
 //             start (the support points of i along d^ and of j along -d^), so
 //             a zero output gives back the cold start n0 = d^ exactly and the
@@ -44,49 +47,53 @@ __device__ __forceinline__ float wrap_pi_f(float x)
 // ---------------------------------------------------------------------------
 // features (the same device code for training and inference)
 // ---------------------------------------------------------------------------
+// The 12 features (FP32): in i's body frame turned about its symmetry axis
+// until d lies in the half-plane y = 0, x >= 0: [0] rho / R_perp,i,
+// [1] d_z / R_perp,i, [2..4] j's axis; [5..8] ln of the four semi-axes;
+// [9] asinh(g(d^)/a); [10, 11] ln(sigma(d^) / R_perp) of i and j.  Invariant
+// under rigid motions of the pair and rotations of either particle about its
+// own axis, like the targets.
 __device__ __forceinline__ void pair_features(const PView &P, const DView &D, int i, int j, const float *mean,
                                               const float *istd, float f[NI])
 {
     const V3<double> dd = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
     const V3<float> d = cvt<float>(dd);
     float qa[4] = {P.qw[i], P.qx[i], P.qy[i], P.qz[i]};
-    float qb[4] = {P.qw[j], P.qx[j], P.qy[j], P.qz[j]};
     const float na = rsqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
-    const float nb = rsqrtf(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
-    for (int a = 0; a < 4; ++a) {
-        qa[a] *= na;
-        qb[a] *= nb;
-    }
-    // d in i's body frame: R(q_a)^T d
+    for (int a = 0; a < 4; ++a) qa[a] *= na;
+    // i's rotation R(q_a); body coordinates are R^T applied to lab vectors
     const float w = qa[0], x = qa[1], y = qa[2], z = qa[3];
     const float R00 = 1 - 2 * (y * y + z * z), R01 = 2 * (x * y - w * z), R02 = 2 * (x * z + w * y);
     const float R10 = 2 * (x * y + w * z), R11 = 1 - 2 * (x * x + z * z), R12 = 2 * (y * z - w * x);
     const float R20 = 2 * (x * z - w * y), R21 = 2 * (y * z + w * x), R22 = 1 - 2 * (x * x + y * y);
     const float rpi = P.rpar[i], rqi = P.rperp[i], rpj = P.rpar[j], rqj = P.rperp[j];
+    const float dbx = R00 * d.x + R10 * d.y + R20 * d.z;
+    const float dby = R01 * d.x + R11 * d.y + R21 * d.z;
+    const float dbz = R02 * d.x + R12 * d.y + R22 * d.z;
+    const float rho = sqrtf(dbx * dbx + dby * dby);
+    const float c = rho > 0.f ? dbx / rho : 1.f, s = rho > 0.f ? dby / rho : 0.f;
+    const V3<float> oj = quat_axis<float>(P.qw[j], P.qx[j], P.qy[j], P.qz[j]);
+    const float obx = R00 * oj.x + R10 * oj.y + R20 * oj.z;
+    const float oby = R01 * oj.x + R11 * oj.y + R21 * oj.z;
+    const float obz = R02 * oj.x + R12 * oj.y + R22 * oj.z;
     const float inv = 1.0f / rqi;
-    f[0] = (R00 * d.x + R10 * d.y + R20 * d.z) * inv;
-    f[1] = (R01 * d.x + R11 * d.y + R21 * d.z) * inv;
-    f[2] = (R02 * d.x + R12 * d.y + R22 * d.z) * inv;
-    // conj(qa) * qb
-    float rw = qa[0] * qb[0] + qa[1] * qb[1] + qa[2] * qb[2] + qa[3] * qb[3];
-    float rx = qa[0] * qb[1] - qa[1] * qb[0] - qa[2] * qb[3] + qa[3] * qb[2];
-    float ry = qa[0] * qb[2] + qa[1] * qb[3] - qa[2] * qb[0] - qa[3] * qb[1];
-    float rz = qa[0] * qb[3] - qa[1] * qb[2] + qa[2] * qb[1] - qa[3] * qb[0];
-    const float sg = rw < 0.f ? -1.f : 1.f;
-    f[3] = sg * rw;
-    f[4] = sg * rx;
-    f[5] = sg * ry;
-    f[6] = sg * rz;
-    f[7] = logf(rpi);
-    f[8] = logf(rqi);
-    f[9] = logf(rpj);
-    f[10] = logf(rqj);
+    f[0] = rho * inv;
+    f[1] = dbz * inv;
+    f[2] = c * obx + s * oby;
+    f[3] = -s * obx + c * oby;
+    f[4] = obz;
+    f[5] = logf(rpi);
+    f[6] = logf(rqi);
+    f[7] = logf(rpj);
+    f[8] = logf(rqj);
     const float dl = sqrtf(dot(d, d));
     const V3<float> e = scl(1.0f / dl, d);
     const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
-    const float g = dl - support(si, e) - support(sj, e);
+    const float wi = support(si, e), wj = support(sj, e);
     const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
-    f[11] = asinhf(g / amin);
+    f[9] = asinhf((dl - wi - wj) / amin);
+    f[10] = logf(wi / rqi);
+    f[11] = logf(wj / rqj);
     if (mean)
         for (int a = 0; a < NI; ++a) f[a] = (f[a] - mean[a]) * istd[a];
 }

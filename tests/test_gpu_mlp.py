@@ -52,9 +52,10 @@ def test_features_match_oracle(env):
     torch.cuda.synchronize()
     ref = oracle.mlp_features(parts, dom, pi, pj)
     got = out.cpu().numpy()
-    np.testing.assert_allclose(got[:, :11], ref[:, :11], rtol=0, atol=2e-5 * np.abs(ref[:, :11]).max())
+    reg = [c for c in range(12) if c != 9]
+    np.testing.assert_allclose(got[:, reg], ref[:, reg], rtol=0, atol=2e-5 * np.abs(ref[:, reg]).max())
     # asinh(g/a): g is a difference of lengths ~10 in FP32
-    np.testing.assert_allclose(got[:, 11], ref[:, 11], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(got[:, 9], ref[:, 9], rtol=0, atol=2e-4)
 
 
 def test_forward_backward_match_oracle(env):
@@ -215,8 +216,9 @@ def test_trained_network_saves_fp64_newton_iterations(env):
     torch.cuda.synchronize()
     warm = pl.results()
     it_c, it_w = cold["iters"].mean(), warm["iters"].mean()
-    assert it_w < 0.9 * it_c, (it_c, it_w)
+    # measured on GB300: 4.81 -> 3.71 per pair, 6.4 -> 4.4 for the slowest lane of a warp
+    assert it_w < 0.85 * it_c, (it_c, it_w)
     wmax = lambda it: it[:len(it) // 32 * 32].reshape(-1, 32).max(1).mean()
-    assert wmax(warm["iters"]) < 0.9 * wmax(cold["iters"])
+    assert wmax(warm["iters"]) < 0.8 * wmax(cold["iters"])
     ref = oracle_ref(parts, dom, pi, pj)
     compare(parts, dom, warm, ref, "fp64", pi, pj)

@@ -96,20 +96,49 @@ def test_features_are_invariant_under_rigid_motion():
     np.testing.assert_allclose(f1, f0, rtol=0, atol=1e-9)
 
 
+def test_features_are_invariant_under_rotations_about_each_axis():
+    """Turning i about its own symmetry axis or j about its own changes neither
+    the pair's geometry nor the targets: the features must not change."""
+    parts, dom, pi, pj = gen.pair_stream(40, seed=64, kind="aspect", gap_range=(1e-4, 0.5))
+    parts = {k: np.asarray(v, np.float64) for k, v in parts.items()}
+    f0 = oracle.mlp_features(parts, dom, pi, pj)
+    from helpers import quat_mul
+    for side in (pi, pj):
+        moved = {k: v.copy() for k, v in parts.items()}
+        for t, k in enumerate(side):
+            q = [moved[c][k] for c in ("qw", "qx", "qy", "qz")]
+            spin = axis_angle_quat([0, 0, 1], 0.3 + 0.7 * t)    # about the body z (symmetry) axis
+            nq = quat_mul(q, spin)
+            for c, v in zip(("qw", "qx", "qy", "qz"), nq):
+                moved[c][k] = v
+        f1 = oracle.mlp_features(moved, dom, pi, pj)
+        np.testing.assert_allclose(f1, f0, rtol=0, atol=1e-9)
+
+
 def test_feature_definitions_special_cases():
-    # identity orientations: body frame = lab frame, relative rotation = 1
+    # identity orientations: body frame = lab frame; d = (6, 8, 1) lies at
+    # azimuth atan2(8, 6) about i's axis, so the turned frame maps j's axis
+    # (0, 0, 1) to itself and the distance from the axis is 10
     from helpers import make_parts
-    parts = make_parts([[0, 0, 0], [10.0, 2.0, 1.0]], [[1, 0, 0, 0]] * 2, [6.0, 3.0], [3.0, 6.0])
+    parts = make_parts([[0, 0, 0], [6.0, 8.0, 1.0]], [[1, 0, 0, 0]] * 2, [6.0, 3.0], [3.0, 6.0])
     dom = dict(L=(1e3,) * 3, periodic=(False,) * 3, walls=[])
     f = oracle.mlp_features(parts, dom, np.array([0], np.int32), np.array([1], np.int32))[0]
-    np.testing.assert_allclose(f[:3], np.array([10.0, 2.0, 1.0]) / 3.0)
-    np.testing.assert_allclose(f[3:7], [1, 0, 0, 0])
-    np.testing.assert_allclose(f[7:11], np.log([6.0, 3.0, 3.0, 6.0]))
-    d = np.array([10.0, 2.0, 1.0])
+    np.testing.assert_allclose(f[:2], [10.0 / 3.0, 1.0 / 3.0])
+    np.testing.assert_allclose(f[2:5], [0, 0, 1], atol=1e-15)
+    np.testing.assert_allclose(f[5:9], np.log([6.0, 3.0, 3.0, 6.0]))
+    d = np.array([6.0, 8.0, 1.0])
     e = d / np.linalg.norm(d)
     si = np.sqrt(3.0 ** 2 * (e[0] ** 2 + e[1] ** 2) + 6.0 ** 2 * e[2] ** 2)
     sj = np.sqrt(6.0 ** 2 * (e[0] ** 2 + e[1] ** 2) + 3.0 ** 2 * e[2] ** 2)
-    assert f[11] == pytest.approx(np.arcsinh((np.linalg.norm(d) - si - sj) / 3.0), rel=1e-12)
+    assert f[9] == pytest.approx(np.arcsinh((np.linalg.norm(d) - si - sj) / 3.0), rel=1e-12)
+    np.testing.assert_allclose(f[10:], np.log([si / 3.0, sj / 6.0]), rtol=1e-13)
+    # j's axis tilted in the plane of d and i's axis: its turned components are
+    # (cos, 0, sin) of the tilt measured from the d direction
+    t = 0.4
+    q_tilt = axis_angle_quat([-0.8, 0.6, 0], t)                  # towards d, about the horizontal normal of d
+    parts = make_parts([[0, 0, 0], [6.0, 8.0, 1.0]], [[1, 0, 0, 0], q_tilt], [6.0, 3.0], [3.0, 6.0])
+    f = oracle.mlp_features(parts, dom, np.array([0], np.int32), np.array([1], np.int32))[0]
+    np.testing.assert_allclose(f[2:5], [np.sin(t), 0.0, np.cos(t)], atol=1e-12)
 
 
 def test_pq_labels_reproduce_the_closest_points():
