@@ -119,8 +119,10 @@ typedef struct {
     double fp64_switch;   /* mixed mode: h/a below which Newton is refined in FP64;
                              a = smallest semi-axis of the pair                        */
     int32_t max_newton;   /* Newton iteration cap per precision stage (1..64)          */
-    double newton_tol;    /* step-size tolerance (radians) of the FP32 stage; the FP64
-                             stage converges to rounding                                */
+    double newton_tol;    /* step-size tolerance (radians) of the FP32 stage: Newton
+                             stops after a step shorter than this (quadratic
+                             convergence leaves an error of order tol^2); the FP64
+                             stage stops after a step below 1e-7 rad              */
     int32_t warm_start;   /* LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP          */
     int32_t model;        /* LUB_MODEL_FULL: all 16 elements of K~; LUB_MODEL_NORMAL:
                              the normal element K~33 alone ("normal only" of Sec.
@@ -143,7 +145,7 @@ typedef struct {
 
 /* Fill *p with the paper's values: mu = 1/6, Delta_n = 2/3, Delta_t = 1/2,
  * Delta_r = 1/4 (Eq. results:cutoffs), h_c = eps_c = 0, list_cutoff = 1,
- * LUB_MIXED, fp64_switch = 1e-3, max_newton = 32, newton_tol = 2e-5,
+ * LUB_MIXED, fp64_switch = 1e-3, max_newton = 32, newton_tol = 1e-4,
  * LUB_WARM_NONE, LUB_MODEL_FULL. */
 void lub_default_params(lub_params *p);
 

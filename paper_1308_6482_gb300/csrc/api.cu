@@ -206,7 +206,7 @@ void lub_default_params(lub_params *p)
     p->precision = LUB_MIXED;
     p->fp64_switch = 1e-3;
     p->max_newton = 32;
-    p->newton_tol = 2e-5;
+    p->newton_tol = 1e-4;
     p->warm_start = LUB_WARM_NONE;
 }
 

@@ -36,6 +36,14 @@ struct NewtonOut {
     bool converged;
 };
 
+// FP64 stopping rule: Newton converges quadratically, so after a step of
+// length s the remaining error is about K s^2 (K of order one to ten for
+// these shapes); stopping once a step is below 1e-7 rad leaves an error of
+// order 1e-14 rad in n, so the contact points sit within 1e-12 R of the
+// converged ones (the gap, stationary in n, within R 1e-26), without
+// spending an iteration to confirm it
+constexpr double kTolFp64 = 1e-7;
+
 template <typename T>
 __device__ __forceinline__ V3<T> perp_unit(const V3<T> &n)
 {
@@ -287,7 +295,7 @@ __device__ __forceinline__ double polish_step(const Shape<double> &si, const Sha
 
 // LUB_MIXED, FP64 refinement of a work-list pair: one polish step from the
 // FP32 normal nstart, or, if full, a complete FP64 solve from the line of
-// centres (to 1e-11 rad)
+// centres
 template <bool ENS>
 __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, bool full,
                                            V3<double> nn, int maxit, V3<double> &n64, double &h, int &st, int &nit)
@@ -301,7 +309,7 @@ __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, cons
     if (full) {
         nn = scl(1.0 / dl, d);
         const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
-        const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
+        const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
         converged = o.converged;
         nit = o.iters;
     } else {
@@ -352,7 +360,7 @@ __device__ __forceinline__ void closest_fp64_one(const PView &P, const DView &D0
                     if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2) && dot(w0, d) > 0.0) nn = w0;
                 }
                 const double scale = dl + (double)fmaxf(rpi, rqi) + (double)fmaxf(rpj, rqj);
-                const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, 1e-11, 1e-14 * scale);
+                const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
                 nit = o.iters;
                 n64 = normalized(nn);
                 h = dot(n64, d) - support(si, n64) - support(sj, n64);
