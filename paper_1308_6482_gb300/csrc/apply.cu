@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(256) k_apply_atomic(const int32_t *__restrict_
                                                       const T *__restrict__ FT, const T *__restrict__ lever, int n,
                                                       T *__restrict__ force, T *__restrict__ torque)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     const size_t N = (size_t)n;
@@ -127,19 +129,17 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
     if (n == 0) return LUB_OK;
     if (!deterministic) {
         if (!accumulate) {
-            int rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 3 * (size_t)n * esz, st), "memset force");
-            if (rc) return rc;
-            rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, 3 * (size_t)n * esz, st), "memset torque");
+            const int rc = zero_force_torque(ctx, force, torque, 3 * (size_t)n * esz, st);
             if (rc) return rc;
         }
         if (cap == 0) return LUB_OK;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_APPLY, cap);
         const int grid = sh.grid, block = sh.block;
         if (precision == LUB_MIXED)
-            k_apply_atomic<float><<<grid, block, 0, st>>>(pi, pj, d_count, cap, (const float *)FT,
+            (void)launch_pdl(k_apply_atomic<float>, grid, block, 0, st, pi, pj, d_count, cap, (const float *)FT,
                                                           (const float *)lever, n, (float *)force, (float *)torque);
         else
-            k_apply_atomic<double><<<grid, block, 0, st>>>(pi, pj, d_count, cap, (const double *)FT,
+            (void)launch_pdl(k_apply_atomic<double>, grid, block, 0, st, pi, pj, d_count, cap, (const double *)FT,
                                                            (const double *)lever, n, (double *)force,
                                                            (double *)torque);
         return lub_check_cuda(ctx, cudaGetLastError(), "k_apply_atomic launch");

@@ -435,6 +435,8 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_con
                                                        int maxit, float tol32, float fp64_switch, int warm,
                                                        int32_t *__restrict__ wl_count, int32_t *__restrict__ wl)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     // warp-uniform loop bound: the whole warp takes part in the work-list ballot
@@ -463,6 +465,8 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
                                                         int maxit, const int32_t *__restrict__ wl_count,
                                                         const int32_t *__restrict__ wl)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
@@ -490,6 +494,8 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_cons
                                                       uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                       int maxit, int warm)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
@@ -551,6 +557,8 @@ __global__ void __launch_bounds__(128) k_fused_mixed(PView P, const __grid_const
                                                      int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
                                                      float *__restrict__ force, float *__restrict__ torque)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
@@ -584,6 +592,8 @@ __global__ void __launch_bounds__(64) k_fused_refine(PView P, const __grid_const
                                                       const int32_t *__restrict__ wl, float *__restrict__ force,
                                                       float *__restrict__ torque)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
@@ -622,6 +632,8 @@ __global__ void __launch_bounds__(128) k_fused_fp64(PView P, const __grid_consta
                                                     double *__restrict__ FT, double *__restrict__ lever, int maxit,
                                                     int warm, double *__restrict__ force, double *__restrict__ torque)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
@@ -678,16 +690,16 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         int32_t *wl_count, *wl;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        k_closest_mixed<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
+        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
                                                           prm.max_newton, (float)prm.newton_tol,
                                                           (float)prm.fp64_switch, warm, wl_count, wl);
         // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
-        k_closest_refine<ENS><<<sr.grid, sr.block, 0, st>>>(P, D, E, pi, pj, cap, n, gap, status, iters,
+        (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
                                                             prm.max_newton, wl_count, wl);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
-        k_closest_fp64<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
+        (void)launch_pdl(k_closest_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
                                                          prm.max_newton, warm);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
@@ -702,9 +714,7 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
     int rc;
     if (!accumulate) {
-        if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 3 * (size_t)P.n * esz, st), "memset force")) ||
-            (rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, 3 * (size_t)P.n * esz, st), "memset torque")))
-            return rc;
+        if ((rc = zero_force_torque(ctx, force, torque, 3 * (size_t)P.n * esz, st))) return rc;
     }
     if (cap == 0) return LUB_OK;
     int warm = 0;
@@ -714,16 +724,16 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         int32_t *wl_count, *wl;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        k_fused_mixed<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
+        (void)launch_pdl(k_fused_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
                                                         (float *)FT, (float *)lever, prm.max_newton,
                                                         (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count,
                                                         wl, (float *)force, (float *)torque);
-        k_fused_refine<ENS><<<grid_for(cap, 64, ctx->num_sms, 32), 64, 0, st>>>(
-            P, D, E, R, pi, pj, cap, n, gap, status, iters, (float *)FT, (float *)lever, prm.max_newton, wl_count, wl,
-            (float *)force, (float *)torque);
+        (void)launch_pdl(k_fused_refine<ENS>, grid_for(cap, 64, ctx->num_sms, 32), 64, 0, st, P, D, E, R, pi, pj, cap,
+                         n, gap, status, iters, (float *)FT, (float *)lever, prm.max_newton,
+                         (const int32_t *)wl_count, (const int32_t *)wl, (float *)force, (float *)torque);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
-        k_fused_fp64<ENS><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
+        (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
                                                        (double *)FT, (double *)lever, prm.max_newton, warm,
                                                        (double *)force, (double *)torque);
     }

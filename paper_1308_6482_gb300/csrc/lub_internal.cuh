@@ -333,10 +333,54 @@ int launch_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *qi, c
                          const int32_t *d_count, int32_t cap, double *n, cudaStream_t st);
 
 // device-wide exclusive scan of n int32 values (in place), total -> *d_total
-// (one launch; a bounded wait that times out sets bit 2 (value 4) of *err)
+// (one launch; a bounded wait that times out sets bit 2 (value 4) of *err).
+// Its state, the first scan_state_words(n) words of tmp, must start at zero:
+// the call clears it unless state_zeroed (an earlier kernel of the same
+// stream cleared it).
 int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, void *tmp, size_t tmp_bytes,
-                   cudaStream_t st, int32_t *err = nullptr);
+                   cudaStream_t st, int32_t *err = nullptr, bool state_zeroed = false);
 size_t scan_tmp_bytes(int64_t n);
+inline int64_t scan_state_words(int64_t n) { return (int64_t)(scan_tmp_bytes(n) / 8); }
+
+// zero the per-particle force and torque arrays (bytes each); one memset when
+// the torque array directly follows the force array (one caller buffer)
+inline int zero_force_torque(lub_ctx *ctx, void *force, void *torque, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return LUB_OK;
+    if ((char *)torque == (char *)force + bytes)
+        return lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 2 * bytes, st), "memset force/torque");
+    int rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, bytes, st), "memset force");
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, bytes, st), "memset torque");
+    return rc;
+}
+
+// Programmatic dependent launch (sm_90 and later).  The kernels of a step are
+// launched with programmatic stream serialisation, so the hardware may
+// schedule a kernel's blocks while its predecessor in the stream finishes.
+// Every kernel launched that way calls pdl_wait() before anything else: it
+// returns once the predecessor grid has completed and its memory operations
+// are visible, so the stream order of the data is that of plain launches.
+// pdl_trigger() then lets the successor be scheduled.  Launched without the
+// attribute (or after a memset or a host operation), both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 inline int grid_for(int64_t work, int block, int num_sms, int per_sm = 16)
 {

@@ -89,8 +89,14 @@ __device__ __forceinline__ int cell_axis(double xw, double inv_cs, int nc)
 template <bool ENS>
 __global__ void k_cells_count(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
                               int32_t *__restrict__ cell_cnt, int32_t *__restrict__ cell_of,
-                              int32_t *__restrict__ slot, float rmax_bound, int32_t *__restrict__ flags)
+                              int32_t *__restrict__ slot, float rmax_bound, int32_t *__restrict__ flags,
+                              unsigned long long *__restrict__ zero, int64_t nzero)
 {
+    pdl_wait();
+    pdl_trigger();
+    // state of the cell scan, which runs next
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nzero; k += (int64_t)gridDim.x * blockDim.x)
+        zero[k] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int b = ENS ? batch_of(E, i) : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, b);
@@ -112,8 +118,15 @@ __global__ void k_cells_fill(PView P, const __grid_constant__ DView D0, const __
                              const int32_t *__restrict__ cell_start, const int32_t *__restrict__ cell_of,
                              const int32_t *__restrict__ slot, int32_t *__restrict__ sorted,
                              float4 *__restrict__ rec0, float4 *__restrict__ rec1, int32_t *__restrict__ cellc,
-                             int32_t *__restrict__ sbat)
+                             int32_t *__restrict__ sbat, int32_t *__restrict__ cnt, unsigned long long *__restrict__ zero,
+                             int64_t nzero)
 {
+    pdl_wait();
+    pdl_trigger();
+    // the sweep's counts (2N + 1) and the state of the scan after it start at zero
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * (int64_t)P.n + 1; k += stride) cnt[k] = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nzero; k += stride) zero[k] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int b = ENS ? batch_of(E, i) : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, b);
@@ -153,18 +166,20 @@ __device__ __forceinline__ bool pair_test_fp64(const PView &P, const DView &D, i
     return true;
 }
 
-// decision of one candidate from the cell-order records (FP32 with margin,
-// FP64 when undecided)
-__device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const Grid &G, int s, int t,
-                                          const float4 a0, const float4 a1, const float4 b0, const float4 b1,
-                                          float ox, float oy, float oz, double cutoff_d,
-                                          const int32_t *__restrict__ sorted)
+// decision of one candidate from the cell-order records in FP32 with a
+// margin: kReject, kAccept, or kUndecided inside the margin (then the FP64
+// test decides)
+constexpr int kReject = 0, kAccept = 1, kUndecided = 2;
+
+__device__ __forceinline__ int pair_test(const Grid &G, const float4 a0, const float4 a1, const float4 b0,
+                                         const float4 *__restrict__ b1p, float ox, float oy, float oz)
 {
     const float dx = b0.x - a0.x + ox, dy = b0.y - a0.y + oy, dz = b0.z - a0.z + oz;
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float lim = a0.w + b0.w + G.cutoff;
     const float hi = lim + G.margin;
-    if (r2 > hi * hi) return false;
+    if (r2 > hi * hi) return kReject;  // most candidates end here, before the second record
+    const float4 b1 = *b1p;
     bool sure = true;
     const float lo = lim - G.margin;
     if (r2 >= lo * lo) sure = false;
@@ -181,13 +196,12 @@ __device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const 
         const float sgj = sqrtf(fmaxf(apj + b1.w * cj * cj, 0.f));
         const float t1 = r - sgi - (b0.w + G.cutoff);
         const float t2 = r - sgj - (a0.w + G.cutoff);
-        if (t1 > G.margin || t2 > G.margin) return false;
+        if (t1 > G.margin || t2 > G.margin) return kReject;
         if (t1 >= -G.margin || t2 >= -G.margin) sure = false;
     } else {
         sure = false;
     }
-    if (sure) return true;
-    return pair_test_fp64(P, D, sorted[s], sorted[t], cutoff_d);
+    return sure ? kAccept : kUndecided;
 }
 
 // Half-shell sweep: the 14 cells of the stencil (the own cell and the 13
@@ -201,15 +215,15 @@ __device__ __forceinline__ bool pair_test(const PView &P, const DView &D, const 
 // periodic image, the own cell at a non-zero offset is tested against every
 // other particle (t != s), and the domain check (L > 2 range) leaves at most
 // one image of a pair within range, so each pair passes exactly once.
-// emit(t) is called for every partner passing the tests.
+// emit(t, r) is called for every candidate the FP32 tests accept or leave
+// undecided (r = kAccept or kUndecided).
 constexpr int SWEEP_ROWS = 5;
 
 template <typename Emit>
-__device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const Grid &G,
-                                          const int32_t *__restrict__ cell_start, const int32_t *__restrict__ sorted,
+__device__ __forceinline__ void sweep_row(const DView &D, const Grid &G, const int32_t *__restrict__ cell_start,
                                           const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int s,
                                           const float4 a0, const float4 a1, int cx, int cy, int cz, int row,
-                                          int cbase, double cutoff_d, Emit emit)
+                                          int cbase, Emit emit)
 {
     const int dz = row >= 2 ? 1 : 0;
     const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
@@ -249,7 +263,27 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
         const int e = cell_start[c2 + 1];
         for (int t = zero_offset ? s + 1 : cell_start[c2]; t < e; ++t) {
             if (self && t == s) continue;
-            if (pair_test(P, D, G, s, t, a0, a1, rec0[t], rec1[t], ox, oy, oz, cutoff_d, sorted)) emit(t);
+            const int r = pair_test(G, a0, a1, rec0[t], rec1 + t, ox, oy, oz);
+            if (r != kReject) emit(t, r);
+        }
+    }
+}
+
+// store of one accepted pair (i, j): in the row of the smaller index, or in
+// the overflow list at the tail of the pair arrays
+__device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restrict__ cnt,
+                                                int32_t *__restrict__ slots, int32_t *__restrict__ ovf_n, int32_t cap,
+                                                int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j)
+{
+    const int lo = min(i, j), hi = max(i, j);
+    const int q = atomicAdd(cnt + lo, 1);
+    if (q < KSLOT) {
+        slots[(size_t)lo * KSLOT + q] = hi;
+    } else {
+        const int o = atomicAdd(ovf_n, 1);
+        if (o < cap) {
+            pair_i[cap - 1 - o] = lo;
+            pair_j[cap - 1 - o] = hi;
         }
     }
 }
@@ -258,8 +292,17 @@ __device__ __forceinline__ void sweep_row(const PView &P, const DView &D, const 
 // walls.  cnt: [0, N) pair counts per particle (of the smaller index of each
 // pair), [N, 2N) wall-pair counts; slots [N][KSLOT]; wall bits per particle;
 // overflow entry o at pair_i/pair_j[cap - 1 - o].
+//
+// Candidates inside the FP32 margin are rare; the FP64 test that decides
+// them needs about 30 more registers than the sweep itself, which would cut
+// the resident warps by 40 %.  So the sweep only lists them (slot pairs in
+// und, count in und_n) and the block that finishes last decides them in FP64
+// (each block fences its writes and takes a ticket; no block waits).  Should
+// the list fill up (more than its capacity of borderline candidates in one
+// build), the extra ones are kept as pairs (a gap within the margin of the
+// list cut-off, where every element of K~ is zero) and flag bit 8 is set.
 template <bool ENS>
-__global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
+__global__ void __launch_bounds__(256, 5) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
                                                      const __grid_constant__ Grid G0, Ens E,
                                                      const EnsGrid *__restrict__ EG,
                                                      const int32_t *__restrict__ cell_start,
@@ -271,12 +314,19 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_const
                                                      int32_t *__restrict__ slots, uint8_t *__restrict__ wbits,
                                                      int32_t *__restrict__ ovf_n, int32_t cap,
                                                      int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
-                                                     double cutoff_d)
+                                                     double cutoff_d, int2 *__restrict__ und, int32_t *__restrict__ und_n,
+                                                     int32_t und_cap, unsigned *__restrict__ done,
+                                                     int32_t *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int N = P.n;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < SWEEP_ROWS * N; f += gridDim.x * blockDim.x) {
+    // this block's items
+    const int f0 = blockIdx.x * blockDim.x;
+    const int f1 = min(f0 + (int)blockDim.x, SWEEP_ROWS * N);
+    const int f = f0 + threadIdx.x;
+    if (f < f1) {
         const int s = f / SWEEP_ROWS, row = f - SWEEP_ROWS * s;
-        const int i = sorted[s];
         const int b = ENS ? sbat[s] : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, b);
         const DView &D = dom_ref<ENS>(D0, E, b);
@@ -284,22 +334,22 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_const
         const float4 a0 = rec0[s], a1 = rec1[s];
         const int cc = cellc[s];
         const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
-        sweep_row(P, D, G, cell_start, sorted, rec0, rec1, s, a0, a1, cx, cy, cz, row, base, cutoff_d, [&](int t) {
-            const int j = sorted[t];
-            const int lo = min(i, j), hi = max(i, j);
-            const int q = atomicAdd(cnt + lo, 1);
-            if (q < KSLOT) {
-                slots[(size_t)lo * KSLOT + q] = hi;
+        sweep_row(D, G, cell_start, rec0, rec1, s, a0, a1, cx, cy, cz, row, base, [&](int t, int r) {
+            if (r == kAccept) {
+                store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
             } else {
-                const int o = atomicAdd(ovf_n, 1);
-                if (o < cap) {
-                    pair_i[cap - 1 - o] = lo;
-                    pair_j[cap - 1 - o] = hi;
+                const int u = atomicAdd(und_n, 1);
+                if (u < und_cap) {
+                    und[u] = make_int2(s, t);
+                } else {
+                    atomicOr(flags, 8);
+                    store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
                 }
             }
         });
         if (row == 0) {
             // plane walls (exact double gap)
+            const int i = sorted[s];
             int wf = 0, bits = 0;
             for (int ww = 0; ww < D.n_walls; ++ww) {
                 const Shape<double> si = load_shape<double>(P, i);
@@ -314,6 +364,21 @@ __global__ void __launch_bounds__(256) k_pairs_sweep(PView P, const __grid_const
             wbits[i] = (uint8_t)bits;
         }
     }
+    // the last block to finish decides the listed candidates in FP64
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nu = min(*(volatile int32_t *)und_n, und_cap);
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+        const int2 e = __ldcg(und + u);
+        const int i = sorted[e.x], j = sorted[e.y];
+        const DView &D = dom_ref<ENS>(D0, E, ENS ? sbat[e.x] : 0);
+        if (pair_test_fp64(P, D, i, j, cutoff_d)) store_candidate(i, j, cnt, slots, ovf_n, cap, pair_i, pair_j);
+    }
 }
 
 // Canonical order: each particle's partners, sorted, then its wall pairs, at
@@ -324,13 +389,18 @@ __global__ void __launch_bounds__(256) k_pairs_compact(int32_t n, const int32_t 
                                                        const uint8_t *__restrict__ wbits,
                                                        const int32_t *__restrict__ ovf_n, int32_t cap,
                                                        int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
-                                                       int32_t *__restrict__ d_count)
+                                                       int32_t *__restrict__ d_count, const int32_t *__restrict__ flags,
+                                                       int32_t *__restrict__ flags_out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int total = off[2 * n];
     const int novf = *ovf_n;
     const int64_t need = (int64_t)total + novf;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *d_count = need > cap ? (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX) : total;
+        if (flags_out) *flags_out = *flags;  // this build's flags, for the host-count path
+    }
     if (need > cap) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int b = off[i], m = off[i + 1] - b;
@@ -449,6 +519,8 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
 struct Layout {
     int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
     uint8_t *wbits;
+    int2 *und;  // candidates left to the FP64 test (und_cap entries)
+    int32_t und_cap;
     float4 *rec0, *rec1;
     void *tmp;
     size_t tmp_bytes, total;
@@ -458,13 +530,15 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
 {
     const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((2 * N + 1) * 4);
     const size_t b_slots = align256((size_t)N * KSLOT * 4), b_bits = align256((size_t)N + 1);
+    const int64_t und_cap = 1024 + N / 4;
+    const size_t b_und = align256((size_t)und_cap * 8);
     const size_t b_rec = align256(N * 16),
                  b_tmp = align256(scan_tmp_bytes(ncell + 1 > 2 * N + 1 ? ncell + 1 : 2 * N + 1));
     Layout L;
     char *s = (char *)base;
     L.flags = (int32_t *)s;
     s += 256;
-    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries
+    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries, [3] undecided, [4] blocks done
     s += 256;
     L.cell_cnt = (int32_t *)s;
     s += b_cell;
@@ -488,6 +562,9 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     s += b_rec;
     L.rec1 = (float4 *)s;
     s += b_rec;
+    L.und = (int2 *)s;
+    L.und_cap = (int32_t)und_cap;
+    s += b_und;
     L.tmp = s;
     L.tmp_bytes = b_tmp;
     s += b_tmp;
@@ -500,33 +577,46 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
 template <bool ENS>
 int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PView &P, const DView &D, const Ens &E,
                const EnsGrid *EG, const lub_params &prm, float rmax, int32_t *pi, int32_t *pj, int32_t cap,
-               int32_t *d_count, cudaStream_t st)
+               int32_t *d_count, cudaStream_t st, int32_t *flags_out = nullptr)
 {
     const int64_t N = P.n;
     Layout L = layout(scratch, N, G.ncell, ENS);
-    // the scratch keeps earlier contents: clear what must start at zero
-    int rc = lub_check_cuda(ctx, cudaMemsetAsync(L.flags, 0, 512, st), "memset flags");
-    if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cell_cnt, 0, (G.ncell + 1) * 4, st), "memset cells");
+    // the scratch keeps earlier contents: clear what must start at zero, the
+    // flags, totals and cell counts in one (they are contiguous); the kernels
+    // clear the sweep's counts and the scans' states for the launches after them
+    int rc = lub_check_cuda(ctx, cudaMemsetAsync(L.flags, 0, 512 + (G.ncell + 1) * 4, st), "memset counts");
     if (rc) return rc;
-    if (N == 0) return lub_check_cuda(ctx, cudaMemsetAsync(d_count, 0, 4, st), "memset count");
+    if (N == 0) {
+        rc = lub_check_cuda(ctx, cudaMemsetAsync(d_count, 0, 4, st), "memset count");
+        if (!rc && flags_out) rc = lub_check_cuda(ctx, cudaMemsetAsync(flags_out, 0, 4, st), "memset flags");
+        return rc;
+    }
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 8);
-    k_cells_count<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, rmax, L.flags);
-    if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st, L.flags))) return rc;
-    k_cells_fill<ENS><<<gn, block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted, L.rec0, L.rec1,
-                                            L.cellc, L.sbat);
-    // counts start at zero (the overflow counter too: totals[2], cleared with the flags)
-    if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(L.cnt, 0, (2 * N + 1) * 4, st), "memset counts"))) return rc;
+    const int64_t z1 = scan_state_words(G.ncell + 1), z2 = scan_state_words(2 * N + 1);
+    unsigned long long *scan_state = (unsigned long long *)L.tmp;
+    cudaError_t e = launch_pdl(k_cells_count<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot,
+                               rmax, L.flags, scan_state, z1);
+    if ((rc = lub_check_cuda(ctx, e, "cells count launch"))) return rc;
+    if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st, L.flags, true)))
+        return rc;
+    e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted,
+                   L.rec0, L.rec1, L.cellc, L.sbat, L.cnt, scan_state, z2);
+    if ((rc = lub_check_cuda(ctx, e, "cells fill launch"))) return rc;
+    // one item per thread (no grid-stride loop)
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
-    if (!ctx) sw.grid = grid_for(SWEEP_ROWS * N, sw.block, num_sms, kTuneDefaults[LUB_TUNE_SWEEP].per_sm);
-    k_pairs_sweep<ENS><<<sw.grid, sw.block, 0, st>>>(P, D, G, E, EG, L.cell_cnt, L.sorted, L.rec0, L.rec1, L.cellc,
-                                                     L.sbat, L.cnt, L.slots, L.wbits, L.totals + 2, cap, pi, pj,
-                                                     prm.list_cutoff);
+    sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
+    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, P, D, G, E, EG, (const int32_t *)L.cell_cnt,
+                   (const int32_t *)L.sorted, (const float4 *)L.rec0, (const float4 *)L.rec1,
+                   (const int32_t *)L.cellc, (const int32_t *)L.sbat, L.cnt, L.slots, L.wbits, L.totals + 2, cap, pi,
+                   pj, (double)prm.list_cutoff, L.und, L.totals + 3, L.und_cap, (unsigned *)(L.totals + 4), L.flags);
+    if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
-    if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags))) return rc;
-    k_pairs_compact<<<grid_for(N, 256, num_sms, 16), 256, 0, st>>>((int32_t)N, L.cnt, L.slots, L.wbits,
-                                                                   L.totals + 2, cap, pi, pj, d_count);
-    return lub_check_cuda(ctx, cudaGetLastError(), "pairs build launch");
+    if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;
+    e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 16), 256, 0, st, (int32_t)N, (const int32_t *)L.cnt,
+                   (const int32_t *)L.slots, (const uint8_t *)L.wbits, (const int32_t *)(L.totals + 2), cap, pi, pj,
+                   d_count, (const int32_t *)L.flags, flags_out);
+    return lub_check_cuda(ctx, e, "pairs compact launch");
 }
 
 }  // namespace
@@ -558,11 +648,9 @@ int launch_pairs_build(lub_ctx *ctx, const PView &P, const DView &D, const lub_p
     int rc = lub_ensure_scratch(ctx, need);
     if (rc) return rc;
     const Ens E = {nullptr, 0};
-    rc = build_core<false>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, nullptr, prm, rmax, pi, pj, cap, d_count, st);
-    if (rc) return rc;
-    // flags of this call for the host-count path
-    return lub_check_cuda(ctx, cudaMemcpyAsync(ctx->d_flags, ctx->scratch, 4, cudaMemcpyDeviceToDevice, st),
-                          "copy flags");
+    // the build leaves its flags in ctx->d_flags for the host-count path
+    return build_core<false>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, nullptr, prm, rmax, pi, pj, cap, d_count,
+                             st, ctx->d_flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -612,9 +700,6 @@ int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DVi
     memset(&D, 0, sizeof(D));
     const size_t need = layout(nullptr, P.n, total, true).total;
     if ((rc = lub_ensure_scratch(ctx, need))) return rc;
-    rc = build_core<true>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, (const EnsGrid *)dev, prm, rmax, pi, pj, cap,
-                          d_count, st);
-    if (rc) return rc;
-    return lub_check_cuda(ctx, cudaMemcpyAsync(ctx->d_flags, ctx->scratch, 4, cudaMemcpyDeviceToDevice, st),
-                          "copy flags");
+    return build_core<true>(ctx, ctx->num_sms, ctx->scratch, G, P, D, E, (const EnsGrid *)dev, prm, rmax, pi, pj, cap,
+                            d_count, st, ctx->d_flags);
 }

@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(128) k_resistance(PView P, const __grid_consta
                                                     uint8_t *__restrict__ status, T *__restrict__ FT,
                                                     T *__restrict__ lever)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
@@ -62,6 +64,8 @@ __global__ void __launch_bounds__(128) k_resistance_apply(PView P, const __grid_
                                                           T *__restrict__ lever, T *__restrict__ force,
                                                           T *__restrict__ torque)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = pair_count(d_count, cap);
     const size_t C = (size_t)cap;
     // warp-uniform loop bound: the whole warp takes part in the scatter
@@ -105,9 +109,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
     const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
     int rc;
     if (!accumulate && P.n > 0) {
-        if ((rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 3 * (size_t)P.n * esz, st), "memset force")) ||
-            (rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, 3 * (size_t)P.n * esz, st), "memset torque")))
-            return rc;
+        if ((rc = zero_force_torque(ctx, force, torque, 3 * (size_t)P.n * esz, st))) return rc;
     }
     if (cap == 0) return LUB_OK;
     RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
@@ -115,20 +117,20 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
         if (ens)
-            k_resistance_apply<float, true><<<sh.grid, sh.block, 0, st>>>(
+            (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, 
                 P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
                 (float *)torque);
         else
-            k_resistance_apply<float, false><<<sh.grid, sh.block, 0, st>>>(
+            (void)launch_pdl(k_resistance_apply<float, false>, sh.grid, sh.block, 0, st, 
                 P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
                 (float *)torque);
     } else {
         if (ens)
-            k_resistance_apply<double, true><<<sh.grid, sh.block, 0, st>>>(
+            (void)launch_pdl(k_resistance_apply<double, true>, sh.grid, sh.block, 0, st, 
                 P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
                 (double *)torque);
         else
-            k_resistance_apply<double, false><<<sh.grid, sh.block, 0, st>>>(
+            (void)launch_pdl(k_resistance_apply<double, false>, sh.grid, sh.block, 0, st, 
                 P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
                 (double *)torque);
     }
@@ -145,17 +147,17 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
         if (ens)
-            k_resistance<float, true><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+            (void)launch_pdl(k_resistance<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
                                                                     (float *)FT, (float *)lever);
         else
-            k_resistance<float, false><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+            (void)launch_pdl(k_resistance<float, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
                                                                      (float *)FT, (float *)lever);
     } else {
         if (ens)
-            k_resistance<double, true><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap,
+            (void)launch_pdl(k_resistance<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap,
                                                                      status, (double *)FT, (double *)lever);
         else
-            k_resistance<double, false><<<sh.grid, sh.block, 0, st>>>(P, D, E, R, pi, pj, d_count, cap, n, gap,
+            (void)launch_pdl(k_resistance<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap,
                                                                       status, (double *)FT, (double *)lever);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance launch");

@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restr
                                                                 int32_t *__restrict__ d_total,
                                                                 int32_t *__restrict__ err)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int tile_s, prefix_s;
     if (threadIdx.x == 0) tile_s = (int)atomicAdd(state, 1ull);
     __syncthreads();
@@ -147,12 +149,16 @@ int64_t tiles_of(int64_t n)
 size_t scan_tmp_bytes(int64_t n) { return (size_t)(tiles_of(n) + 1) * sizeof(unsigned long long); }
 
 int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, void *tmp, size_t tmp_bytes,
-                   cudaStream_t st, int32_t *err)
+                   cudaStream_t st, int32_t *err, bool state_zeroed)
 {
     if (tmp_bytes < scan_tmp_bytes(n)) return lub_set_error(ctx, LUB_ERR_ARG, "scan: temp too small");
     const int64_t nt = tiles_of(n);
-    int rc = lub_check_cuda(ctx, cudaMemsetAsync(tmp, 0, scan_tmp_bytes(n), st), "scan state");
-    if (rc) return rc;
-    k_scan_lookback<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(data, n, (unsigned long long *)tmp, d_total, err);
-    return lub_check_cuda(ctx, cudaGetLastError(), "scan launch");
+    if (!state_zeroed) {
+        const int rc = lub_check_cuda(ctx, cudaMemsetAsync(tmp, 0, scan_tmp_bytes(n), st), "scan state");
+        if (rc) return rc;
+    }
+    return lub_check_cuda(ctx,
+                          launch_pdl(k_scan_lookback, (int)nt, SCAN_THREADS, 0, st, data, n,
+                                     (unsigned long long *)tmp, d_total, err),
+                          "scan launch");
 }

@@ -115,7 +115,9 @@ def test_optional_outputs_and_accumulate(lub):
                     None, None, None, pl.force, pl.torque, 1)
     torch.cuda.synchronize()
     twice = pl.results()
-    np.testing.assert_allclose(twice["force"], 2 * full["force"], rtol=1e-5, atol=1e-12)
+    # the same pair terms summed twice, in another order of atomic additions
+    half = dict(twice, force=twice["force"] / 2, torque=twice["torque"] / 2)
+    sums_close(half, full, full, "mixed")
 
 
 def test_fused_ensemble_and_warm_starts(lub):
