@@ -573,8 +573,8 @@ def rigid_motion(P, g, sig_r=0.01, sig_t=0.005):
 
 def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     """Batched ensemble: args.ens_n independent periodic suspensions of mixed
-    spheroids (aspect ratio log-uniform [1/3, 3], phi uniform [0.1, 0.35],
-    pair counts log-uniform [1e3, 2e5]) stepped together: one CUDA graph per
+    spheroids (growth packings, aspect ratio log-uniform [1/3, 3], phi uniform
+    [0.1, 0.5], pair counts log-uniform [1e3, 2e5]) stepped together: one CUDA graph per
     step (the four calls, one launch per stage for all suspensions), launch
     shapes from the autotuner, every particle moved by a small seeded rigid
     motion between steps.  Against it: the same suspensions stepped one by one
@@ -684,7 +684,7 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     sep_ms, sep_pairs = aggregate(sep_ms, sep_pairs, ws, dev)
     n_all = aggregate(0.0, float(len(parts["x"])), ws, dev)[1]
     return {
-        "workload": "%d periodic suspensions, phi uniform [0.1,0.35], aspect ratio log-uniform [1/3,3], pair "
+        "workload": "%d periodic suspensions (growth packings), phi uniform [0.1,0.5], aspect ratio log-uniform [1/3,3], pair "
                     "counts log-uniform [1e3,2e5]; %d particles, %d steps of seeded rigid motions "
                     "(dr ~ N(0,0.01^2), dtheta ~ N(0,0.005^2))" % (args.ens_n, int(n_all), args.ens_steps),
         "precision": "mixed", "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
@@ -703,7 +703,8 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
 
 def large_bench(args, dev, stream, flush, ws=1, rank=0):
     """Large run: args.large_n spheroids (aspect ratio log-uniform [1/3, 3]) at
-    phi = 0.35 in a cube periodic in x, y between two plane walls, mixed
+    phi = 0.5 (growth packing) in a 1024^3 cube periodic in x, y between two
+    plane walls, mixed
     precision, args.large_steps graph-replayed steps, every particle moved by a
     small seeded rigid motion between steps; then shorter runs with the
     learned and the temporal warm start on the same motions.  Under torchrun
@@ -760,7 +761,7 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
 
     ms, cnt, over, walls = run(lub.LUB_WARM_NONE, args.large_steps)
     step_ms, pairs = aggregate(float(ms.mean()), float(cnt.mean()), ws, dev)
-    out = {"workload": "%d spheroids, aspect ratio log-uniform [1/3,3], phi=0.35, cube %.0f^3 periodic in x,y "
+    out = {"workload": "%d spheroids, aspect ratio log-uniform [1/3,3], phi=0.5 (growth packing), cube %.0f^3 periodic in x,y "
                        "between walls at z=0 and z=L; %d steps of seeded rigid motions"
                        % (len(parts["x"]), dom["L"][0], args.large_steps),
            "precision": "mixed", "pairs_per_step_mean": pairs, "wall_pairs_last_step": walls,

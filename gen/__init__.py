@@ -22,6 +22,16 @@ Sec. IV):
     attached to an earlier one at a gap drawn log-uniform in [1e-4, 1].
   * ``pair_stream``: independent pairs at gaps drawn log-uniform (optionally
     scaled by the smaller semi-axis), each pair far from all others.
+  * ``ensemble``: 256 periodic suspensions of spheroids (aspect ratio
+    log-uniform in [1/3, 3]) at volume fractions uniform in [0.1, 0.5], sized
+    for pair counts log-uniform in [1e3, 2e5]: growth packings tiled k^3.
+  * ``large_config``: 2^20 such spheroids at Phi = 0.5 in a 1024^3 cube
+    between two walls: a growth packing of a slab, tiled 8 x 8.
+
+Dense suspensions come from ``grow``, the growth method of the paper's
+Sec. IV (random placement at 30 % of the sizes, growth with overlap
+repulsion and damped motion to slightly beyond full size, sizes reset);
+random sequential placement (``suspension``) jams near Phi = 0.4.
 """
 import ctypes
 import os
@@ -41,7 +51,11 @@ def build(force=False):
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     tmp = _SO + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    try:  # OpenMP for the growth sweeps (results do not depend on the thread count)
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                              stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -59,6 +73,12 @@ def _load():
                                 ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
                                 P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                 P(ctypes.c_float)]
+        lib.gen_grow.restype = ctypes.c_int64
+        lib.gen_grow.argtypes = [ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int32,
+                                 P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_float),
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                 ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                 P(ctypes.c_float), P(ctypes.c_int64)]
         _lib = lib
     return _lib
 
@@ -152,6 +172,44 @@ def suspension(shapes, L, periodic=(True, True, True), walls=(), attach_prob=0.0
     return parts, dom
 
 
+def grow(shapes, L, periodic=(True, True, True), walls=(), seed=1, s0=0.3, s_over=1.02, g0=0.01,
+         max_sweeps=20000):
+    """Growth packing (the paper's initialisation of dense suspensions, Sec. IV):
+    random placement at s0 of the linear sizes, growth with overlap repulsion
+    and overdamped motion to s_over, sizes reset to 1.  Every gap ends at
+    least about (s_over - 1) times the particle sizes.  Returns (parts, dom);
+    Returns (parts, dom, sweeps)."""
+    lib = _load()
+    shapes = np.asarray(shapes, np.float32)
+    N = len(shapes)
+    r_par = np.ascontiguousarray(shapes[:, 0])
+    r_perp = np.ascontiguousarray(shapes[:, 1])
+    Lc = np.asarray(L, np.float64)
+    per = np.asarray([int(bool(p)) for p in periodic], np.int32)
+    wz = np.zeros(2)
+    wd = np.zeros(2, np.int32)
+    for w, (zz, dd) in enumerate(walls):
+        wz[w], wd[w] = zz, dd
+    x, y, z = np.zeros(N), np.zeros(N), np.zeros(N)
+    q = np.zeros((N, 4), np.float32)
+    sweeps = np.zeros(1, np.int64)
+    rc = lib.gen_grow(N, _ptr(Lc, ctypes.c_double), _ptr(per, ctypes.c_int32), len(walls),
+                      _ptr(wz, ctypes.c_double), _ptr(wd, ctypes.c_int32), _ptr(r_par, ctypes.c_float),
+                      _ptr(r_perp, ctypes.c_float), float(s0), float(s_over), float(g0), int(max_sweeps),
+                      int(seed) & ((1 << 64) - 1), _ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double),
+                      _ptr(z, ctypes.c_double), _ptr(q, ctypes.c_float), _ptr(sweeps, ctypes.c_int64))
+    if rc == -1:
+        raise RuntimeError("placement at %g of the sizes stalled" % s0)
+    if rc < -1:
+        raise RuntimeError("growth stalled: %d contacts still overlap after %d sweeps" % (-2 - rc, sweeps[0]))
+    parts = dict(x=x, y=y, z=z, qw=q[:, 0].copy(), qx=q[:, 1].copy(), qy=q[:, 2].copy(),
+                 qz=q[:, 3].copy(), r_par=r_par.copy(), r_perp=r_perp.copy())
+    velocities(parts, np.random.default_rng(seed + 7919))
+    dom = dict(L=tuple(float(v) for v in L), periodic=tuple(bool(p) for p in periodic),
+               walls=[(float(a), int(b)) for a, b in walls])
+    return parts, dom, int(sweeps[0])
+
+
 def config_prolate_wall(seed=1, N=64, L=42.0):
     """64 prolates (R_par=6, R_perp=3) in an L^3 box, periodic in x, y, wall at z=0."""
     shapes = np.tile([[6.0, 3.0]], (N, 1))
@@ -229,10 +287,11 @@ def pair_stream(P, seed=3, kind="mixed", gap_range=(1e-4, 1.0), gap_scale="absol
     return parts, dom, a.astype(np.int32), b.astype(np.int32)
 
 
-def aspect_shapes(N, rng):
-    """Spheroids with aspect ratio log-uniform in [1/3, 3], equivalent radius 4.5."""
+def aspect_shapes(N, rng, r_eq=4.5):
+    """Spheroids with aspect ratio log-uniform in [1/3, 3] and equivalent radius
+    r_eq (R_par R_perp^2 = r_eq^3)."""
     lam = np.exp(rng.uniform(np.log(1 / 3), np.log(3.0), N))
-    return np.stack([4.5 * lam ** (2.0 / 3.0), 4.5 * lam ** (-1.0 / 3.0)], 1).astype(np.float32)
+    return np.stack([r_eq * lam ** (2.0 / 3.0), r_eq * lam ** (-1.0 / 3.0)], 1).astype(np.float32)
 
 
 def tile_periodic(parts, dom, k, rng, axes=(0, 1, 2)):
@@ -258,30 +317,31 @@ def tile_periodic(parts, dom, k, rng, axes=(0, 1, 2)):
     return out, d
 
 
-def large_config(N=1 << 20, phi=0.35, seed=6, k=8):
-    """Large run: N spheroids (aspect ratio log-uniform in [1/3, 3], equivalent
-    radius 4.5) in a cube periodic in x, y between plane walls at z = 0 and
-    z = L: an attached random placement of N / k^2 particles in a slab of
-    L/k x L/k x L (walls included), tiled k x k in x and y."""
+def large_config(N=1 << 20, phi=0.5, seed=6, k=8, L=1024.0):
+    """Large dense run: N spheroids (aspect ratio log-uniform in [1/3, 3]) at
+    volume fraction phi in an L^3 cube periodic in x, y between plane walls
+    at z = 0 and z = L; the equivalent radius fills the cube at phi
+    (4.96 for 2^20 particles in 1024^3 at 0.5).  A growth packing of N / k^2
+    particles in a slab of L/k x L/k x L (walls included), tiled k x k in x
+    and y."""
     rng = np.random.default_rng(seed)
+    r_eq = (phi * L ** 3 / (N * 4.0 / 3.0 * np.pi)) ** (1.0 / 3.0)
     n0 = N // (k * k)
-    sh = aspect_shapes(n0, rng)
-    vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
-    L = (vol * k * k / phi) ** (1.0 / 3.0)
-    base, dom = suspension(sh, (L / k, L / k, L), periodic=(True, True, False), walls=[(0.0, 1), (L, -1)],
-                           attach_prob=0.9, wall_min=1e-3, seed=seed, max_attempts=400000)
+    sh = aspect_shapes(n0, rng, r_eq)
+    base, dom, _ = grow(sh, (L / k, L / k, L), periodic=(True, True, False), walls=[(0.0, 1), (L, -1)], seed=seed)
     return tile_periodic(base, dom, k, rng, axes=(0, 1))
 
 
-# pairs per particle of attached suspensions (attach_prob 0.9, list cut-off 1)
-# at volume fraction phi, fitted on spheroids of aspect ratio 1/3..3
+# candidate pairs per particle of growth packings of these spheroids (list
+# cut-off 1, equivalent radius 4.5) at volume fraction phi, fitted on 800-
+# particle packings at phi = 0.1 .. 0.5 (0.80, 1.58, 2.45, 3.32, 4.26)
 def _pairs_per_particle(phi):
-    return 1.29 + 4.9 * (phi - 0.1)
+    return 8.65 * phi - 0.065
 
 
 def ensemble_member(args):
     """One suspension of the ensemble workload: (seed, phi, target pairs) ->
-    (parts, dom), an attached RSA base of 128..1024 spheroids tiled k^3 times."""
+    (parts, dom), a growth packing of 128..1024 spheroids tiled k^3 times."""
     seed, phi, target = args
     rng = np.random.default_rng(seed)
     n_all = target / _pairs_per_particle(phi)
@@ -290,11 +350,17 @@ def ensemble_member(args):
     sh = aspect_shapes(n0, rng)
     vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
     L = (vol / phi) ** (1.0 / 3.0)
-    parts, dom = suspension(sh, (L, L, L), attach_prob=0.9, seed=seed, max_attempts=400000)
+    parts, dom, _ = grow(sh, (L, L, L), seed=seed)
     return tile_periodic(parts, dom, k, rng)
 
 
-def ensemble(n_susp=256, seed=4, phi_range=(0.1, 0.35), pairs_range=(1e3, 2e5), processes=None):
+def _pool_member(args):
+    # one thread per pool process (set before the generator library loads)
+    os.environ["OMP_NUM_THREADS"] = "1"
+    return ensemble_member(args)
+
+
+def ensemble(n_susp=256, seed=4, phi_range=(0.1, 0.5), pairs_range=(1e3, 2e5), processes=None):
     """Independent periodic suspensions of mixed spheroids (aspect ratio
     log-uniform in [1/3, 3]) at volume fractions uniform in phi_range, sized
     for pair counts log-uniform in pairs_range.  Returns ([(parts, dom)], meta).
@@ -307,7 +373,7 @@ def ensemble(n_susp=256, seed=4, phi_range=(0.1, 0.35), pairs_range=(1e3, 2e5), 
     procs = processes if processes is not None else min(16, os.cpu_count() or 1)
     if procs > 1:
         with mp.get_context("spawn").Pool(procs) as pool:
-            sus = pool.map(ensemble_member, jobs, chunksize=1)
+            sus = pool.map(_pool_member, jobs, chunksize=1)
     else:
         sus = [ensemble_member(j) for j in jobs]
     return sus, dict(phi=phi, target_pairs=target)

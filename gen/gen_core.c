@@ -299,3 +299,375 @@ int64_t gen_rsa(int64_t N, const double L[3], const int32_t periodic[3], int32_t
     free(Ms);
     return placed;
 }
+
+/* ---------------------------------------------------------------------------
+ * Growth packing, for suspensions denser than random sequential placement
+ * reaches (it jams near Phi = 0.4 for these spheroids).  The particles start
+ * at a fraction s0 of their linear size, placed one by one at random (easy at
+ * that size), and grow: every step multiplies all sizes by (1 + g), then
+ * relaxation sweeps push overlapping particles apart, with walls, by a
+ * Hookean repulsion proportional to the overlap depth acting at the contact
+ * point, in the overdamped limit of damped motion (the displacement and the
+ * rotation of a sweep are proportional to the summed force and torque; no
+ * inertia, no velocities kept).  The growth goes on to s_over slightly above
+ * 1; there the sweeps continue until nothing overlaps, and the sizes are
+ * reset to 1, which leaves every gap at least about (s_over - 1) times the
+ * particle sizes.  g adapts: it grows while the sweeps keep the overlaps
+ * small and shrinks when they do not.
+ *
+ * Overlap from the Perram-Wertheim contact function of the scaled shapes,
+ * F(l) = l (1 - l) d^T G(l)^{-1} d, G(l) = (1 - l) A + l B, maximised over
+ * l in (0, 1) (concave: Newton on F'(l) = 0, bisection safeguard): the bodies
+ * overlap exactly when F < 1, the depth along the centre line is
+ * |d| (1/sqrt(F) - 1) (exact for spheres), and at the maximiser the contact
+ * point is r_i + (1 - l) A x with x = G^{-1} d, where both surfaces have
+ * normal x / |x| (from i towards j).
+ *
+ * Deterministic: every sweep computes all pushes from the positions of the
+ * sweep before (Jacobi), each particle summing over its neighbours in a fixed
+ * order, so the result does not depend on the number of threads.
+ * ------------------------------------------------------------------------- */
+
+/* x = G^{-1} d for symmetric positive definite G (Cramer); returns d.x */
+static double solve3(const double G[3][3], const double d[3], double x[3])
+{
+    double c00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+    double c01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+    double c02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+    double det = G[0][0] * c00 + G[0][1] * c01 + G[0][2] * c02;
+    double inv[3][3];
+    inv[0][0] = c00;
+    inv[0][1] = G[0][2] * G[2][1] - G[0][1] * G[2][2];
+    inv[0][2] = G[0][1] * G[1][2] - G[0][2] * G[1][1];
+    inv[1][0] = c01;
+    inv[1][1] = G[0][0] * G[2][2] - G[0][2] * G[2][0];
+    inv[1][2] = G[0][2] * G[1][0] - G[0][0] * G[1][2];
+    inv[2][0] = c02;
+    inv[2][1] = G[0][1] * G[2][0] - G[0][0] * G[2][1];
+    inv[2][2] = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+    for (int i = 0; i < 3; ++i) x[i] = (inv[i][0] * d[0] + inv[i][1] * d[1] + inv[i][2] * d[2]) / det;
+    return d[0] * x[0] + d[1] * x[1] + d[2] * x[2];
+}
+
+/* PW maximisation; returns F, sets l and x = G(l)^{-1} d */
+static double pw_newton(const double A[3][3], const double B[3][3], const double d[3], double *lam, double x[3])
+{
+    double BA[3][3], G[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) BA[i][j] = B[i][j] - A[i][j];
+    double lo = 0.0, hi = 1.0, l = 0.5, F = 0.0;
+    for (int it = 0; it < 30; ++it) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) G[i][j] = A[i][j] + l * BA[i][j];
+        const double dx = solve3(G, d, x);
+        double Bx[3], y[3];
+        matvec(BA, x, Bx);
+        const double xBx = x[0] * Bx[0] + x[1] * Bx[1] + x[2] * Bx[2];
+        solve3(G, Bx, y); /* y = G^{-1} (B - A) x */
+        const double yBx = y[0] * Bx[0] + y[1] * Bx[1] + y[2] * Bx[2];
+        F = l * (1.0 - l) * dx;
+        const double F1 = (1.0 - 2.0 * l) * dx - l * (1.0 - l) * xBx;
+        const double F2 = -2.0 * dx - 2.0 * (1.0 - 2.0 * l) * xBx + 2.0 * l * (1.0 - l) * yBx;
+        if (F1 > 0.0) lo = l; else hi = l;
+        double ln = (F2 < 0.0) ? l - F1 / F2 : 0.5 * (lo + hi);
+        if (!(ln > lo && ln < hi)) ln = 0.5 * (lo + hi);
+        if (fabs(ln - l) < 1e-12 || hi - lo < 1e-12) {
+            l = ln;
+            break;
+        }
+        l = ln;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) G[i][j] = A[i][j] + l * BA[i][j];
+    F = l * (1.0 - l) * solve3(G, d, x);
+    *lam = l;
+    return F;
+}
+
+typedef struct {
+    int nc[3];
+    double cs[3];
+    int64_t *head, *next;
+} grid_t;
+
+static void grid_fill(grid_t *g, int64_t N, const double *pos, const double L[3], double range)
+{
+    for (int a = 0; a < 3; ++a) {
+        g->nc[a] = (int)floor(L[a] / range);
+        if (g->nc[a] < 1) g->nc[a] = 1;
+        if (g->nc[a] > 256) g->nc[a] = 256;
+        g->cs[a] = L[a] / g->nc[a];
+    }
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    for (int64_t c = 0; c < ncell; ++c) g->head[c] = -1;
+    for (int64_t k = N - 1; k >= 0; --k) {
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            ci[a] = (int)floor(pos[3 * k + a] / g->cs[a]);
+            if (ci[a] < 0) ci[a] = 0;
+            if (ci[a] >= g->nc[a]) ci[a] = g->nc[a] - 1;
+        }
+        int64_t c = ((int64_t)ci[0] * g->nc[1] + ci[1]) * g->nc[2] + ci[2];
+        g->next[k] = g->head[c];
+        g->head[c] = k;
+    }
+}
+
+static double maxd(double a, double b) { return a > b ? a : b; }
+
+/* pairs are pushed apart while their gap is below this fraction of the
+   smaller semi-axes (so that the sweeps end with no overlap left, instead of
+   approaching contact from the overlapping side) */
+#define GROW_SKIN 1e-3
+/* growth continues while the deepest overlap after a sweep stays below this
+   fraction of the smaller semi-axis, and slows down above three times it */
+#define GROW_LOOSE 0.1
+
+/* one relaxation sweep at scale s: pushes from the current state into dr, dth;
+   returns the largest overlap depth relative to the particle sizes */
+static double grow_sweep(int64_t N, const double L[3], const int32_t periodic[3], int32_t n_walls,
+                         const double wall_z[2], const int32_t wall_dir[2], const float *r_par, const float *r_perp,
+                         double s, const double *pos, double (*M)[3][3], const grid_t *g, double *dr, double *dth,
+                         int64_t *n_over)
+{
+    double worst = 0.0;
+    int64_t over = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : worst) reduction(+ : over)
+    for (int64_t i = 0; i < N; ++i) {
+        const double ri = maxd(r_par[i], r_perp[i]), rmin = r_par[i] < r_perp[i] ? r_par[i] : r_perp[i];
+        double A[3][3], f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] = s * s * M[i][a][b];
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            ci[a] = (int)floor(pos[3 * i + a] / g->cs[a]);
+            if (ci[a] < 0) ci[a] = 0;
+            if (ci[a] >= g->nc[a]) ci[a] = g->nc[a] - 1;
+        }
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    int cc[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz}, skip = 0;
+                    for (int a = 0; a < 3; ++a)
+                        if (cc[a] < 0 || cc[a] >= g->nc[a]) {
+                            if (periodic[a]) cc[a] = (cc[a] + g->nc[a]) % g->nc[a];
+                            else skip = 1;
+                        }
+                    if (skip) continue;
+                    /* a cell met twice (fewer than 3 cells along an axis) is tested once */
+                    int dup = 0;
+                    const int small = g->nc[0] < 3 || g->nc[1] < 3 || g->nc[2] < 3;
+                    for (int ex = -1; small && ex <= dx && !dup; ++ex)
+                        for (int ey = -1; ey <= 1 && !dup; ++ey)
+                            for (int ez = -1; ez <= 1 && !dup; ++ez) {
+                                if (ex == dx && (ey > dy || (ey == dy && ez >= dz))) continue;
+                                int ee[3] = {ci[0] + ex, ci[1] + ey, ci[2] + ez}, sk = 0;
+                                for (int a = 0; a < 3; ++a)
+                                    if (ee[a] < 0 || ee[a] >= g->nc[a]) {
+                                        if (periodic[a]) ee[a] = (ee[a] + g->nc[a]) % g->nc[a];
+                                        else sk = 1;
+                                    }
+                                if (!sk && ee[0] == cc[0] && ee[1] == cc[1] && ee[2] == cc[2]) dup = 1;
+                            }
+                    if (dup) continue;
+                    int64_t cell = ((int64_t)cc[0] * g->nc[1] + cc[1]) * g->nc[2] + cc[2];
+                    for (int64_t j = g->head[cell]; j >= 0; j = g->next[j]) {
+                        if (j == i) continue;
+                        double d[3];
+                        for (int a = 0; a < 3; ++a) {
+                            d[a] = pos[3 * j + a] - pos[3 * i + a];
+                            if (periodic[a]) d[a] -= L[a] * floor(d[a] / L[a] + 0.5);
+                        }
+                        const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                        const double rj = maxd(r_par[j], r_perp[j]);
+                        const double rminj = r_par[j] < r_perp[j] ? r_par[j] : r_perp[j];
+                        const double skin = GROW_SKIN * s * 0.5 * (rmin + rminj);
+                        if (dist >= s * (ri + rj) + skin) continue;
+                        double B[3][3];
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) B[a][b] = s * s * M[j][a][b];
+                        if (dist > 0.0) {
+                            /* half-widths along the centre line: no overlap when they fit */
+                            const double e[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+                            if (dist > sqrt(quad(A, e)) + sqrt(quad(B, e)) + skin) continue;
+                        }
+                        double lam, x[3], n[3];
+                        double depth, Fpw;
+                        if (dist > 0.0) {
+                            Fpw = pw_newton(A, B, d, &lam, x);
+                            const double h = dist * (1.0 - 1.0 / sqrt(Fpw));  /* gap estimate */
+                            if (h >= skin) continue;
+                            if (h < 0.0) ++over;
+                            depth = skin - h;
+                        } else {
+                            ++over;
+                            lam = 0.5;
+                            x[0] = 1.0; x[1] = 0.0; x[2] = 0.0;
+                            depth = s * (ri + rj);
+                        }
+                        const double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                        for (int a = 0; a < 3; ++a) n[a] = x[a] / xn;
+                        double rho[3];
+                        matvec(A, x, rho);
+                        for (int a = 0; a < 3; ++a) rho[a] *= (1.0 - lam);
+                        /* push on i: half the depth, away from j, at the contact point */
+                        const double pf[3] = {-0.5 * depth * n[0], -0.5 * depth * n[1], -0.5 * depth * n[2]};
+                        for (int a = 0; a < 3; ++a) f[a] += pf[a];
+                        t[0] += rho[1] * pf[2] - rho[2] * pf[1];
+                        t[1] += rho[2] * pf[0] - rho[0] * pf[2];
+                        t[2] += rho[0] * pf[1] - rho[1] * pf[0];
+                        const double rel = depth / (s * rmin);
+                        if (rel > worst) worst = rel;
+                    }
+                }
+        /* walls: the support extent of the scaled body along z */
+        for (int w = 0; w < n_walls; ++w) {
+            const double ez[3] = {0.0, 0.0, 1.0};
+            const double sz = sqrt(quad(A, ez));
+            const double skin = GROW_SKIN * s * rmin;
+            const double hw = wall_dir[w] * (pos[3 * i + 2] - wall_z[w]) - sz - skin;
+            if (hw >= 0.0) continue;
+            if (hw + skin < 0.0) ++over;
+            double Mz[3];
+            matvec(A, ez, Mz);
+            const double rho[3] = {-wall_dir[w] * Mz[0] / sz, -wall_dir[w] * Mz[1] / sz, -wall_dir[w] * Mz[2] / sz};
+            const double pf[3] = {0.0, 0.0, -hw * wall_dir[w]};
+            f[2] += pf[2];
+            t[0] += rho[1] * pf[2];
+            t[1] += -rho[0] * pf[2];
+            const double rel = -hw / (s * rmin);
+            if (rel > worst) worst = rel;
+        }
+        /* overdamped response, under-relaxed and clamped (several contacts at once) */
+        double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        const double cap = 0.1 * s * rmin, c1 = fl * 0.6 > cap ? cap / fl : 0.6;
+        for (int a = 0; a < 3; ++a) dr[3 * i + a] = c1 * f[a];
+        const double ir2 = 1.0 / (s * s * ri * ri);
+        double tl = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]) * 0.3 * ir2;
+        const double c2 = tl > 0.05 ? 0.05 / tl : 1.0;
+        for (int a = 0; a < 3; ++a) dth[3 * i + a] = c2 * 0.3 * ir2 * t[a];
+    }
+    *n_over = over;
+    return worst;
+}
+
+/*
+ * Returns the number of particles (N) on success; -1 when the first
+ * placement at s0 stalls; -2 - k when k pairs or wall contacts still overlap
+ * after max_sweeps.  Outputs x, y, z (double) and q ([N][4] float, scalar
+ * first); *sweeps_out = relaxation sweeps used.
+ */
+int64_t gen_grow(int64_t N, const double L[3], const int32_t periodic[3], int32_t n_walls, const double wall_z[2],
+                 const int32_t wall_dir[2], const float *r_par, const float *r_perp, double s0, double s_over,
+                 double g0, int64_t max_sweeps, uint64_t seed, double *x, double *y, double *z, float *q,
+                 int64_t *sweeps_out)
+{
+    if (N <= 0) return 0;
+    float *sp = (float *)malloc(sizeof(float) * N), *sq = (float *)malloc(sizeof(float) * N);
+    double rmax = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        sp[k] = (float)(s0 * r_par[k]);
+        sq[k] = (float)(s0 * r_perp[k]);
+        rmax = maxd(rmax, maxd(r_par[k], r_perp[k]));
+    }
+    /* walls: keep centres at least a full-size half-width away while placing */
+    const int64_t placed = gen_rsa(N, L, periodic, n_walls, wall_z, wall_dir, sp, sq, 0.0, 1e-4, 1.0, 0.0, 100000,
+                                   seed, x, y, z, q);
+    free(sp);
+    free(sq);
+    if (placed != N) return -1;
+    double *pos = (double *)malloc(sizeof(double) * 3 * N), *dr = (double *)malloc(sizeof(double) * 3 * N),
+           *dth = (double *)malloc(sizeof(double) * 3 * N), *qd = (double *)malloc(sizeof(double) * 4 * N);
+    double(*M)[3][3] = malloc(sizeof(double[3][3]) * N);
+    grid_t gr;
+    int64_t ncell_max = 1;
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)floor(L[a] / (2.0 * s0 * rmax));
+        ncell_max *= nc < 1 ? 1 : (nc > 256 ? 256 : nc);
+    }
+    gr.head = (int64_t *)malloc(sizeof(int64_t) * ncell_max);
+    gr.next = (int64_t *)malloc(sizeof(int64_t) * N);
+    for (int64_t k = 0; k < N; ++k) {
+        pos[3 * k] = x[k];
+        pos[3 * k + 1] = y[k];
+        pos[3 * k + 2] = z[k];
+        for (int a = 0; a < 4; ++a) qd[4 * k + a] = q[4 * k + a];
+    }
+    double s = s0, g = g0;
+    int64_t sweeps = 0, n_over = 0;
+    int done = 0;
+    while (!done && sweeps < max_sweeps) {
+        const int at_top = s >= s_over;
+        /* shape matrices from the current orientations, cells for range 2 s Rmax */
+        for (int64_t k = 0; k < N; ++k) {
+            double w = qd[4 * k], a = qd[4 * k + 1], b = qd[4 * k + 2], c = qd[4 * k + 3];
+            double t = 2.0 / (w * w + a * a + b * b + c * c);
+            double Q[3][3] = {{1.0 - t * (b * b + c * c), t * (a * b - w * c), t * (a * c + w * b)},
+                              {t * (a * b + w * c), 1.0 - t * (a * a + c * c), t * (b * c - w * a)},
+                              {t * (a * c - w * b), t * (b * c + w * a), 1.0 - t * (a * a + b * b)}};
+            double dd[3] = {(double)r_perp[k] * r_perp[k], (double)r_perp[k] * r_perp[k], (double)r_par[k] * r_par[k]};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    M[k][i][j] = 0.0;
+                    for (int m = 0; m < 3; ++m) M[k][i][j] += Q[i][m] * dd[m] * Q[j][m];
+                }
+        }
+        grid_fill(&gr, N, pos, L, 2.0 * s * rmax * 1.0000001);
+        const double worst = grow_sweep(N, L, periodic, n_walls, wall_z, wall_dir, r_par, r_perp, s, pos, M, &gr, dr,
+                                        dth, &n_over);
+        ++sweeps;
+        if (at_top && n_over == 0) {
+            done = 1;
+            break;
+        }
+        /* apply the pushes */
+        for (int64_t k = 0; k < N; ++k) {
+            for (int a = 0; a < 3; ++a) {
+                double v = pos[3 * k + a] + dr[3 * k + a];
+                if (periodic[a]) v -= L[a] * floor(v / L[a]);
+                else if (v < 0.0) v = 0.0;
+                else if (v >= L[a]) v = L[a] * (1.0 - 1e-12);
+                pos[3 * k + a] = v;
+            }
+            const double th[3] = {dth[3 * k], dth[3 * k + 1], dth[3 * k + 2]};
+            const double ang = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+            if (ang > 0.0) {
+                const double cs = cos(0.5 * ang), sn = sin(0.5 * ang) / ang;
+                const double r0 = cs, r1 = sn * th[0], r2 = sn * th[1], r3 = sn * th[2];
+                const double q0 = qd[4 * k], q1 = qd[4 * k + 1], q2 = qd[4 * k + 2], q3 = qd[4 * k + 3];
+                double n0 = r0 * q0 - r1 * q1 - r2 * q2 - r3 * q3, n1 = r0 * q1 + r1 * q0 + r2 * q3 - r3 * q2;
+                double n2 = r0 * q2 - r1 * q3 + r2 * q0 + r3 * q1, n3 = r0 * q3 + r1 * q2 - r2 * q1 + r3 * q0;
+                const double nn = 1.0 / sqrt(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+                qd[4 * k] = n0 * nn;
+                qd[4 * k + 1] = n1 * nn;
+                qd[4 * k + 2] = n2 * nn;
+                qd[4 * k + 3] = n3 * nn;
+            }
+        }
+        /* grow while the overlaps stay small */
+        if (!at_top) {
+            if (worst < GROW_LOOSE) {
+                s *= 1.0 + g;
+                if (s > s_over) s = s_over;
+                g = g * 1.25 > 0.02 ? 0.02 : g * 1.25;
+            } else if (worst > 3 * GROW_LOOSE) {
+                g = g * 0.5 < 1e-4 ? 1e-4 : g * 0.5;
+            }
+        }
+    }
+    for (int64_t k = 0; k < N; ++k) {
+        x[k] = pos[3 * k];
+        y[k] = pos[3 * k + 1];
+        z[k] = pos[3 * k + 2];
+        for (int a = 0; a < 4; ++a) q[4 * k + a] = (float)qd[4 * k + a];
+    }
+    free(pos);
+    free(dr);
+    free(dth);
+    free(qd);
+    free(M);
+    free(gr.head);
+    free(gr.next);
+    if (sweeps_out) *sweeps_out = sweeps;
+    return done ? N : -2 - n_over;
+}

@@ -1,6 +1,7 @@
-"""The ensemble workload's generator: periodic tiling keeps the suspension's
-pair structure (each pair of the tiled box is a periodic-image pair of the
-base, so the pair count grows exactly by k^3), and members hit their targets."""
+"""The ensemble and large workloads' generators: periodic tiling keeps the
+suspension's pair structure (each pair of the tiled box is a periodic-image
+pair of the base, so the pair count grows exactly by k^3), members (growth
+packings) hit their targets, and the large run is a tiled slab."""
 import numpy as np
 
 import gen
@@ -37,7 +38,7 @@ def test_members_are_near_their_target_pair_counts():
 
 
 def test_large_config_tiles_the_slab_in_x_and_y_only():
-    parts, dom = gen.large_config(N=2048, phi=0.3, seed=3, k=2)
+    parts, dom = gen.large_config(N=2048, phi=0.3, seed=3, k=2, L=137.5)   # equivalent radius 4.5
     assert len(parts["x"]) == 2048
     assert dom["periodic"] == (True, True, False) and len(dom["walls"]) == 2
     L = dom["L"]
