@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--form", default="merged", choices=["calls", "merged", "fused"],
                     help="calls: pair build + closest + resistance + apply; merged: pair build + closest + "
                          "resistance_apply; fused: pair build + lub_correct")
@@ -203,6 +204,12 @@ def run_ours(args):
 
     form = args.form
     fused = form == "fused"
+    # launch shapes of this step's kernels from the library's autotuner
+    shapes = None
+    if not args.no_tune:
+        with torch.cuda.stream(stream):
+            shapes = pl.autotune(reps=5, stream=stream)
+        stream.synchronize()
     # eager step once: per-call launch accounting and results for the work counts
     with torch.cuda.stream(stream):
         pl.step(form=form, stream=stream)
@@ -467,7 +474,8 @@ def run_ours(args):
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "cuda_graph": graph is not None, "parallelism": "independent replicas" if ws > 1 else "1 GPU",
                    "newton_iters_mean": mean_it, "fp64_refined_fraction": fp64_frac,
-                   "call_ms": call_ms, "wall_s_timed": wall},
+                   "call_ms": call_ms, "wall_s_timed": wall,
+                   "autotuned_shapes": {k: list(v) for k, v in shapes.items()} if shapes else None},
         "roofline": roof, "clocks": clocks, "gpu_launches": kernels_per_step * args.steps,
         "e2e": e2e,
     }

@@ -243,6 +243,7 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
                 entry = -1 - k;
             else if (h < (double)fp64_switch * (double)amin)
                 entry = k;
+            if (entry != kNoEntry) st |= LUB_ST_FP64;  // on the FP64 work list (refined next)
             // consistency check of Sec. III A: the normals point to the other centre
             if (entry == kNoEntry && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
         }
@@ -546,59 +547,40 @@ __device__ __forceinline__ void force_and_scatter(const PView &P, const RParams 
     scatter_warp<T>(ok ? i : -1, ok ? j : -1, (size_t)P.n, ci, cj, force, torque);
 }
 
+// The fused pass in mixed precision after the FP32 stage (k_closest_mixed,
+// which leaves every pair's normal, gap and status and marks the work-list
+// pairs with LUB_ST_FP64): warps take 32 items at a time from two queues,
+// the work-list entries (the FP64 refinement, then the pair's force and
+// scatter; the first warp of every block, before anything else), then the
+// other pairs (force and scatter from the stored normal and gap; all warps).  The FP64 chains of the first queue, too few to fill the GPU,
+// run beside the resistance of the second instead of in a launch of their
+// own.  queue: two counters, zero at the launch.
 template <bool ENS>
-__global__ void __launch_bounds__(128) k_fused_mixed(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
-                                                     const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-                                                     const int32_t *__restrict__ d_count, int32_t cap,
-                                                     double *__restrict__ nout, double *__restrict__ gap,
-                                                     uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
-                                                     float *__restrict__ FT, float *__restrict__ lever, int maxit,
-                                                     float tol32, float fp64_switch, int warm,
-                                                     int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
-                                                     float *__restrict__ force, float *__restrict__ torque)
+__global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+                                                       const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                       const int32_t *__restrict__ d_count, int32_t cap,
+                                                       double *__restrict__ nout, double *__restrict__ gap,
+                                                       uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
+                                                       float *__restrict__ FT, float *__restrict__ lever, int maxit,
+                                                       const int32_t *__restrict__ wl_count,
+                                                       const int32_t *__restrict__ wl, int32_t *__restrict__ queue,
+                                                       float *__restrict__ force, float *__restrict__ torque)
 {
     pdl_wait();
     pdl_trigger();
-    const int count = pair_count(d_count, cap);
+    const int count = pair_count(d_count, cap), nwl = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-        const int k = base + threadIdx.x;
-        int entry = kNoEntry, i = -1, j = -1, st = 0;
-        V3<double> n64 = mk<double>(0, 0, 0);
-        double h = 0.0;
-        if (k < count) {
-            i = __ldg(pi + k);
-            j = __ldg(pj + k);
-            int nit;
-            entry = closest_mixed_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
-                                           nit);
-            if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
-        }
-        const bool done = k < count && entry == kNoEntry;
-        worklist_append(entry, wl_count, wl, cap);
-        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque);
-        if (k < count) store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
-    }
-}
-
-template <bool ENS>
-__global__ void __launch_bounds__(64) k_fused_refine(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
-                                                      const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-                                                      int32_t cap, double *__restrict__ nout,
-                                                      double *__restrict__ gap, uint8_t *__restrict__ status,
-                                                      uint8_t *__restrict__ iters, float *__restrict__ FT,
-                                                      float *__restrict__ lever, int maxit,
-                                                      const int32_t *__restrict__ wl_count,
-                                                      const int32_t *__restrict__ wl, float *__restrict__ force,
-                                                      float *__restrict__ torque)
-{
-    pdl_wait();
-    pdl_trigger();
-    const int count = wl_total(wl_count, cap);
-    const size_t C = (size_t)cap;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-        const int q = base + threadIdx.x;
-        const bool active = q < count;
+    const int lane = threadIdx.x & 31;
+    // one warp per block on the first queue, so that its FP64 work spreads
+    // over every SM (the FP64 pipe is the scarce unit) instead of filling the
+    // first blocks to start
+    for (; threadIdx.x < 32;) {
+        int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(queue, 32);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= nwl) break;
+        const int q = q0 + lane;
+        const bool active = q < nwl;
         int i = -1, j = -1, k = 0, st = 0, nit = 0;
         bool full = false;
         V3<double> n64 = mk<double>(0, 0, 0);
@@ -620,6 +602,29 @@ __global__ void __launch_bounds__(64) k_fused_refine(PView P, const __grid_const
                 iters[k] = (uint8_t)(total > 255 ? 255 : total);
             }
         }
+    }
+    for (;;) {
+        int k0 = 0;
+        if (lane == 0) k0 = atomicAdd(queue + 1, 32);
+        k0 = __shfl_sync(0xffffffffu, k0, 0);
+        if (k0 >= count) break;
+        const int k = k0 + lane;
+        int i = -1, j = -1, st = 0;
+        bool done = k < count;
+        V3<double> n64 = mk<double>(0, 0, 0);
+        double h = 0.0;
+        if (done) {
+            st = status[k];
+            if (st & LUB_ST_FP64) {
+                done = false;  // a work-list pair: the first queue's
+            } else {
+                i = __ldg(pi + k);
+                j = __ldg(pj + k);
+                n64 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
+                h = gap[k];
+            }
+        }
+        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque);
     }
 }
 
@@ -669,13 +674,22 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
 }
 
 // the FP64 work list of the mixed mode: count + up to cap entries in the context scratch
-int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl)
+// The FP64 work list in the context scratch: counters [front, back, queue 0,
+// queue 1] and cap entries; with gap_in/status_in, also a gap and a status
+// array for callers that pass none (the fused pass needs them between its
+// kernels).
+int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl,
+              double **gap_in = nullptr, uint8_t **status_in = nullptr)
 {
-    int rc = lub_ensure_scratch(ctx, 256 + 4 * (size_t)cap);
+    const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = 8 * (size_t)cap;
+    int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_gap + (size_t)cap);
     if (rc) return rc;
-    *wl_count = (int32_t *)ctx->scratch;
-    *wl = (int32_t *)((char *)ctx->scratch + 256);
-    return lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 8, st), "memset work list");
+    char *base = (char *)ctx->scratch;
+    *wl_count = (int32_t *)base;
+    *wl = (int32_t *)(base + 256);
+    if (gap_in && !*gap_in) *gap_in = (double *)(base + 256 + b_wl);
+    if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
+    return lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 16, st), "memset work list");
 }
 
 template <bool ENS>
@@ -721,16 +735,18 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
     const RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
     if (prm.precision == LUB_MIXED) {
+        // the FP32 stage, then the FP64 work list and every pair's force in one
+        // queue-driven launch (gap and status in the context when not given)
         int32_t *wl_count, *wl;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        (void)launch_pdl(k_fused_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
-                                                        (float *)FT, (float *)lever, prm.max_newton,
-                                                        (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count,
-                                                        wl, (float *)force, (float *)torque);
-        (void)launch_pdl(k_fused_refine<ENS>, grid_for(cap, 64, ctx->num_sms, 32), 64, 0, st, P, D, E, R, pi, pj, cap,
-                         n, gap, status, iters, (float *)FT, (float *)lever, prm.max_newton,
-                         (const int32_t *)wl_count, (const int32_t *)wl, (float *)force, (float *)torque);
+        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
+                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl);
+        const Shape2 sr = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
+        const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
+        (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+                         iters, (float *)FT, (float *)lever, prm.max_newton, (const int32_t *)wl_count,
+                         (const int32_t *)wl, wl_count + 2, (float *)force, (float *)torque);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
         (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
