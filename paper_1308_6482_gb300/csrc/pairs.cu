@@ -269,6 +269,75 @@ __device__ __forceinline__ void sweep_row(const DView &D, const Grid &G, const i
     }
 }
 
+// The candidates of one item (slot s, row) as up to three runs of slots, one
+// per cell of the row: beg[k], num[k] for the cell at dx = dx0 + k, bit k of
+// self set when that cell is the own cell under a periodic image offset
+// (t != s).  Cells beyond the particle's reach are left empty.
+struct Runs {
+    int beg[3], num[3];
+    int dx0, self;
+    float oy, oz;
+};
+
+__device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const int32_t *__restrict__ cell_start, int s,
+                                         const float4 a0, int cx, int cy, int cz, int row, int cbase)
+{
+    Runs R;
+    R.beg[0] = R.beg[1] = R.beg[2] = 0;
+    R.num[0] = R.num[1] = R.num[2] = 0;
+    R.self = 0;
+    const int dz = row >= 2 ? 1 : 0;
+    const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
+    R.dx0 = row == 0 ? 0 : -1;
+    R.oy = dy * G.cs[1];
+    R.oz = dz * G.cs[2];
+    int yc = cy + dy, zc = cz + dz;
+    if (yc < 0 || yc >= G.nc[1]) {
+        if (!D.periodic[1]) return R;
+        yc += yc < 0 ? G.nc[1] : -G.nc[1];
+    }
+    if (zc < 0 || zc >= G.nc[2]) {
+        if (!D.periodic[2]) return R;
+        zc += zc < 0 ? G.nc[2] : -G.nc[2];
+    }
+    const int own = cbase + (cz * G.nc[1] + cy) * G.nc[0] + cx;
+    const int rowbase = cbase + (zc * G.nc[1] + yc) * G.nc[0];
+    // skip neighbour cells no partner of particle s can reach: distance from
+    // the particle to the cell's box against Rmax_s + Rmax + Delta_L
+    const float reach = a0.w + G.rmax + G.cutoff + G.margin;
+    const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2], hx = 0.5f * G.cs[0];
+    const float ey = dy == 0 ? 0.f : fmaxf(fabsf(R.oy - a0.y) - hy, 0.f);
+    const float ez = dz == 0 ? 0.f : fmaxf(fabsf(R.oz - a0.z) - hz, 0.f);
+    const float r2yz = ey * ey + ez * ez;
+    if (r2yz > reach * reach) return R;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int dx = R.dx0 + k;
+        if (dx > 1) continue;
+        int xc = cx + dx;
+        if (xc < 0 || xc >= G.nc[0]) {
+            if (!D.periodic[0]) continue;
+            xc += xc < 0 ? G.nc[0] : -G.nc[0];
+        }
+        const float ex = dx == 0 ? 0.f : fmaxf(fabsf(dx * G.cs[0] - a0.x) - hx, 0.f);
+        if (ex * ex + r2yz > reach * reach) continue;
+        const int c2 = rowbase + xc;
+        const bool zero_offset = dx == 0 && dy == 0 && dz == 0;
+        if (!zero_offset && c2 == own) R.self |= 1 << k;
+        const int e = cell_start[c2 + 1];
+        R.beg[k] = zero_offset ? s + 1 : cell_start[c2];
+        R.num[k] = e > R.beg[k] ? e - R.beg[k] : 0;
+    }
+    return R;
+}
+
+// an item's data for the lanes that test its candidates (one per thread)
+struct ItemSlot {
+    float4 a0, a1;
+    int s, beg0, beg1, beg2, num0, num1, dx0self;
+    float cs0, oy, oz;
+};
+
 // store of one accepted pair (i, j): in the row of the smaller index, or in
 // the overflow list at the tail of the pair arrays
 __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restrict__ cnt,
@@ -301,8 +370,8 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
 // the list fill up (more than its capacity of borderline candidates in one
 // build), the extra ones are kept as pairs (a gap within the margin of the
 // list cut-off, where every element of K~ is zero) and flag bit 8 is set.
-template <bool ENS>
-__global__ void __launch_bounds__(256, 5) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
+template <bool ENS, bool FLAT>
+__global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
                                                      const __grid_constant__ Grid G0, Ens E,
                                                      const EnsGrid *__restrict__ EG,
                                                      const int32_t *__restrict__ cell_start,
@@ -321,32 +390,55 @@ __global__ void __launch_bounds__(256, 5) k_pairs_sweep(PView P, const __grid_co
     pdl_wait();
     pdl_trigger();
     const int N = P.n;
-    // this block's items
-    const int f0 = blockIdx.x * blockDim.x;
-    const int f1 = min(f0 + (int)blockDim.x, SWEEP_ROWS * N);
-    const int f = f0 + threadIdx.x;
-    if (f < f1) {
+    __shared__ ItemSlot items[FLAT ? 256 : 1];
+    const int lane = threadIdx.x & 31;
+    // one candidate that passed (or is undecided by) the FP32 tests
+    auto decide = [&](int s, int t, int r) {
+        if (r == kAccept) {
+            store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
+        } else {
+            const int w = atomicAdd(und_n, 1);
+            if (w < und_cap) {
+                und[w] = make_int2(s, t);
+            } else {
+                atomicOr(flags, 8);
+                store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
+            }
+        }
+    };
+    // each thread's own item: its runs of candidates and its wall tests
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    int total = 0;
+    if (f < SWEEP_ROWS * N) {
         const int s = f / SWEEP_ROWS, row = f - SWEEP_ROWS * s;
         const int b = ENS ? sbat[s] : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, b);
         const DView &D = dom_ref<ENS>(D0, E, b);
         const int base = cell_base<ENS>(EG, b);
-        const float4 a0 = rec0[s], a1 = rec1[s];
+        const float4 a0 = rec0[s];
         const int cc = cellc[s];
         const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
-        sweep_row(D, G, cell_start, rec0, rec1, s, a0, a1, cx, cy, cz, row, base, [&](int t, int r) {
-            if (r == kAccept) {
-                store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
-            } else {
-                const int u = atomicAdd(und_n, 1);
-                if (u < und_cap) {
-                    und[u] = make_int2(s, t);
-                } else {
-                    atomicOr(flags, 8);
-                    store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
-                }
-            }
-        });
+        if (!FLAT) {
+            // sparse suspensions (a few candidates per item): the thread walks its row
+            sweep_row(D, G, cell_start, rec0, rec1, s, a0, rec1[s], cx, cy, cz, row, base,
+                      [&](int t, int r) { decide(s, t, r); });
+        } else {
+        const Runs R = row_runs(D, G, cell_start, s, a0, cx, cy, cz, row, base);
+        total = R.num[0] + R.num[1] + R.num[2];
+        ItemSlot &it = items[FLAT ? threadIdx.x : 0];
+        it.a0 = a0;
+        it.a1 = rec1[s];
+        it.s = s;
+        it.beg0 = R.beg[0];
+        it.beg1 = R.beg[1];
+        it.beg2 = R.beg[2];
+        it.num0 = R.num[0];
+        it.num1 = R.num[1];
+        it.dx0self = (R.dx0 + 1) | (R.self << 2);
+        it.cs0 = G.cs[0];
+        it.oy = R.oy;
+        it.oz = R.oz;
+        }
         if (row == 0) {
             // plane walls (exact double gap)
             const int i = sorted[s];
@@ -363,6 +455,44 @@ __global__ void __launch_bounds__(256, 5) k_pairs_sweep(PView P, const __grid_co
             cnt[N + i] = wf;
             wbits[i] = (uint8_t)bits;
         }
+    }
+    // The warp's 32 items' candidates, laid end to end (inclusive prefix
+    // incl over the lanes), tested 32 at a time: lane q's candidate belongs
+    // to the item of the first lane whose incl exceeds it.  A thread walking
+    // its own item's candidates would leave most of its warp idle (the runs
+    // differ in length from item to item), and the lanes read the runs'
+    // records coalesced.
+    if (FLAT) {
+    int incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    const int wbase = threadIdx.x & ~31;
+    __syncwarp();
+    for (int r0 = 0; r0 < wtotal; r0 += 32) {
+        const int q = r0 + lane;
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+            if (v <= q) o += step;
+        }
+        const int first = __shfl_sync(0xffffffffu, incl - total, o & 31);
+        if (q >= wtotal) continue;
+        const ItemSlot &it = items[wbase + o];
+        const int u = q - first;
+        const int k = u < it.num0 ? 0 : (u < it.num0 + it.num1 ? 1 : 2);
+        const int t = k == 0 ? it.beg0 + u : (k == 1 ? it.beg1 + u - it.num0 : it.beg2 + u - it.num0 - it.num1);
+        const int s = it.s;
+        if (((it.dx0self >> (2 + k)) & 1) && t == s) continue;
+        const float ox = (float)((it.dx0self & 3) - 1 + k) * it.cs0;
+        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[s] : 0);
+        const int r = pair_test(G, it.a0, it.a1, rec0[t], rec1 + t, ox, it.oy, it.oz);
+        if (r != kReject) decide(s, t, r);
+    }
     }
     // the last block to finish decides the listed candidates in FP64
     __shared__ int last;
@@ -603,13 +733,18 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted,
                    L.rec0, L.rec1, L.cellc, L.sbat, L.cnt, scan_state, z2);
     if ((rc = lub_check_cuda(ctx, e, "cells fill launch"))) return rc;
-    // one item per thread (no grid-stride loop)
+    // one item per thread (no grid-stride loop); the warps share out their
+    // items' candidates when a row holds more than a few (three cells of
+    // N / ncell particles each; measured: 1.66 per cell walks faster, 4.8 and
+    // 10 share out faster)
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
     sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
-    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, P, D, G, E, EG, (const int32_t *)L.cell_cnt,
-                   (const int32_t *)L.sorted, (const float4 *)L.rec0, (const float4 *)L.rec1,
-                   (const int32_t *)L.cellc, (const int32_t *)L.sbat, L.cnt, L.slots, L.wbits, L.totals + 2, cap, pi,
-                   pj, (double)prm.list_cutoff, L.und, L.totals + 3, L.und_cap, (unsigned *)(L.totals + 4), L.flags);
+    const bool flat = (double)N >= 2.0 * (double)(G.ncell > 0 ? G.ncell : 1);
+    e = launch_pdl(flat ? k_pairs_sweep<ENS, true> : k_pairs_sweep<ENS, false>, sw.grid, sw.block, 0, st, P, D, G, E,
+                   EG, (const int32_t *)L.cell_cnt, (const int32_t *)L.sorted, (const float4 *)L.rec0,
+                   (const float4 *)L.rec1, (const int32_t *)L.cellc, (const int32_t *)L.sbat, L.cnt, L.slots, L.wbits,
+                   L.totals + 2, cap, pi, pj, (double)prm.list_cutoff, L.und, L.totals + 3, L.und_cap,
+                   (unsigned *)(L.totals + 4), L.flags);
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;

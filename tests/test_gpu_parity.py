@@ -310,3 +310,38 @@ def test_candidates_at_the_list_cutoff(P):
     h = oracle.closest(parts, dom, extra[:, 0], extra[:, 1])["h"]
     rmax = float(np.max(parts["r_par"]))
     assert np.all(h >= 1.0) and np.all(h - 1.0 <= 1e-5 * (2 * rmax + 2.0))
+
+
+@pytest.mark.parametrize("case", ["periodic", "walls", "five_cells"])
+def test_dense_packings(case):
+    """Growth packings at Phi = 0.5 of spheroids with aspect ratios in
+    [1/3, 3]: the longest set the cell range 2 Rmax + Delta_L (about 19.7), so
+    a cell holds about 10 particles and every (particle, row) item of the
+    sweep has some 30 candidates (the build then gives each item a group of
+    lanes).  The pair list must be the oracle's, with full parity;
+    'five_cells' is a small periodic box (two cells per axis)."""
+    rng = np.random.default_rng({"periodic": 21, "walls": 22, "five_cells": 23}[case])
+    if case == "five_cells":
+        sh = gen.aspect_shapes(400, rng)
+        rmax = float(sh.max())
+        side = 5.2 * (2 * rmax + 1.0) / 2          # floor(side / (range / 2)) = 5
+        vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
+        n = int(min(400, 0.5 * side ** 3 / (vol / 400)))
+        sh = sh[:n]
+        L, per, walls = (side, side, side), (True, True, True), []
+    else:
+        sh = gen.aspect_shapes(3000, rng)
+        vol = float(np.sum(4.0 / 3.0 * np.pi * sh[:, 0].astype(np.float64) * sh[:, 1] ** 2))
+        if case == "walls":
+            a = (vol / 0.5 / 2.0) ** (1.0 / 3.0)
+            L, per, walls = (a, a, 2 * a), (True, True, False), [(0.0, 1), (2 * a, -1)]
+        else:
+            a = (vol / 0.5) ** (1.0 / 3.0)
+            L, per, walls = (a, a, a), (True, True, True), []
+    parts, dom, _ = gen.grow(sh, L, periodic=per, walls=walls, seed=5)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert len(pi) > 2 * len(sh)
+    g = run_gpu(parts, dom, "mixed")
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
