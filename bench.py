@@ -784,10 +784,11 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
 
 def kernels_in_step(precision, form):
     # lub_pairs_build: cells count, scan, cells fill, sweep, scan, compaction = 6;
-    # closest points: FP32 stage + FP64 work list (mixed) or one FP64 kernel (also in the fused pass);
-    # calls: lub_resistance 1 + lub_apply (atomic) 1; merged: lub_resistance_apply 1; fused: 0.
+    # closest points, mixed: float-float positions, FP32 stage, FP64 work list (the fused pass: the
+    # positions, the FP32 stage and one kernel for the work list and the forces); FP64: one kernel;
+    # calls: lub_resistance 1 + lub_apply (atomic) 1; merged: lub_resistance_apply 1.
     # Memsets are not counted.
-    closest = 2 if precision == "mixed" else 1
+    closest = 3 if precision == "mixed" else 1
     return 6 + closest + {"calls": 2, "merged": 1, "fused": 0}[form]
 
 

@@ -162,6 +162,27 @@ __device__ __forceinline__ double ff_gap(const PView &P, int i, int j, const ff 
     return ff_to_double(h);
 }
 
+// Minimum-image separation r_j - r_i in float-float from the particles'
+// float-float positions (pff: [3][N] (hi, lo)); the image shift is taken from
+// the float part (listed pairs are far from the ambiguous half box).  About
+// 48 bits: an absolute error near 2^-48 |r| (4e-12 at |r| = 1000), against
+// the FP64 subtraction and splitting it replaces (some 24 FP64 operations per
+// pair, at 1/64 of the FP32 rate).
+__device__ __forceinline__ void ff_separation(const float2 *__restrict__ pff, size_t N, int i, int j,
+                                              const DView &D, ff d[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 pi = __ldg(pff + a * N + i), pj = __ldg(pff + a * N + j);
+        ff da = ff_sub(ff{pj.x, pj.y}, ff{pi.x, pi.y});
+        if (D.periodic[a]) {
+            const float k = rintf(da.hi * D.invLf[a]);
+            if (k != 0.f) da = ff_sub(da, ff{k * D.Lff[a][0], k * D.Lff[a][1]});
+        }
+        d[a] = da;
+    }
+}
+
 __device__ __forceinline__ bool pair_bad(const PView &P, const DView &D, int i, int j)
 {
     bool bad = (i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i);
@@ -188,7 +209,8 @@ constexpr int kNoEntry = 0x7fffffff;
 // Returns the FP64 work-list entry: k (refine from the FP32 normal), -1-k
 // (full FP64 solve from the line of centres) or kNoEntry.
 template <bool ENS>
-__device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E, int i, int j, int k,
+__device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E,
+                                                 const float2 *__restrict__ pff, int i, int j, int k,
                                                  const double *__restrict__ nin, size_t C, int warm, int maxit,
                                                  float tol32, float fp64_switch, V3<double> &n64, double &h, int &st,
                                                  int &nit)
@@ -205,8 +227,8 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
     } else if (j < 0) {
         h = wall_gap(P, D, i, -1 - j, n64);
     } else {
-        const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
-        const ff dff[3] = {ff_from_double(d.x), ff_from_double(d.y), ff_from_double(d.z)};
+        ff dff[3];
+        ff_separation(pff, (size_t)P.n, i, j, D, dff);
         const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
         const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
         const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
@@ -427,6 +449,23 @@ __device__ __forceinline__ int wl_entry(const int32_t *__restrict__ wl_count, co
 // ---------------------------------------------------------------------------
 // lub_closest_points kernels
 // ---------------------------------------------------------------------------
+// float-float copies (hi, lo) of the particle positions, [3][n], for the
+// separations of the FP32 stage
+__global__ void __launch_bounds__(256) k_pos_ff(PView P, float2 *__restrict__ out)
+{
+    pdl_wait();
+    pdl_trigger();
+    const size_t N = (size_t)P.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const double v[3] = {P.x[i], P.y[i], P.z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float hi = (float)v[a];
+            out[a * N + i] = make_float2(hi, (float)(v[a] - (double)hi));
+        }
+    }
+}
+
 template <bool ENS>
 __global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
                                                        const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
@@ -434,7 +473,8 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_con
                                                        double *__restrict__ nout, double *__restrict__ gap,
                                                        uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                        int maxit, float tol32, float fp64_switch, int warm,
-                                                       int32_t *__restrict__ wl_count, int32_t *__restrict__ wl)
+                                                       int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
+                                                       const float2 *__restrict__ pff)
 {
     pdl_wait();
     pdl_trigger();
@@ -449,7 +489,7 @@ __global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_con
             V3<double> n64;
             double h;
             int st, nit;
-            entry = closest_mixed_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
+            entry = closest_mixed_one<ENS>(P, D0, E, pff, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
                                            nit);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
         }
@@ -679,17 +719,25 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
 // array for callers that pass none (the fused pass needs them between its
 // kernels).
 int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl,
-              double **gap_in = nullptr, uint8_t **status_in = nullptr)
+              double **gap_in = nullptr, uint8_t **status_in = nullptr, const PView *P = nullptr,
+              float2 **pff = nullptr)
 {
-    const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = 8 * (size_t)cap;
-    int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_gap + (size_t)cap);
+    const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = ((8 * (size_t)cap + 255) / 256) * 256,
+                 b_st = (((size_t)cap + 255) / 256) * 256, b_pos = P ? 24 * (size_t)P->n : 0;
+    int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_gap + b_st + b_pos);
     if (rc) return rc;
     char *base = (char *)ctx->scratch;
     *wl_count = (int32_t *)base;
     *wl = (int32_t *)(base + 256);
     if (gap_in && !*gap_in) *gap_in = (double *)(base + 256 + b_wl);
     if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
-    return lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 16, st), "memset work list");
+    rc = lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 16, st), "memset work list");
+    if (rc || !P) return rc;
+    // the particles' float-float positions for the FP32 stage
+    *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
+    if (P->n == 0) return LUB_OK;
+    return lub_check_cuda(ctx, launch_pdl(k_pos_ff, grid_for(P->n, 256, ctx->num_sms, 8), 256, 0, st, *P, *pff),
+                          "positions launch");
 }
 
 template <bool ENS>
@@ -702,11 +750,12 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (rc) return rc;
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl))) return rc;
+        float2 *pff = nullptr;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, nullptr, nullptr, &P, &pff))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
-                                                          prm.max_newton, (float)prm.newton_tol,
-                                                          (float)prm.fp64_switch, warm, wl_count, wl);
+        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
+                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl,
+                         (const float2 *)pff);
         // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
         (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
@@ -738,10 +787,12 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         // the FP32 stage, then the FP64 work list and every pair's force in one
         // queue-driven launch (gap and status in the context when not given)
         int32_t *wl_count, *wl;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status))) return rc;
+        float2 *pff = nullptr;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status, &P, &pff))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
         (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
-                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl);
+                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl,
+                         (const float2 *)pff);
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
         const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
         (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,

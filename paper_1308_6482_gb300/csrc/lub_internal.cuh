@@ -64,6 +64,12 @@ struct DView {
     int32_t n_walls;
     double wall_z[2];
     int32_t wall_dir[2];
+    // the box lengths as float-float (hi, lo) and 1/L in float, for the
+    // separations of the FP32 stage; pad keeps the struct free of padding
+    // bytes (ensemble tables are compared bytewise)
+    float Lff[3][2];
+    float invLf[3];
+    int32_t pad;
 };
 
 // ensemble mode: per-suspension domain and particle range [p0, p1)
@@ -137,6 +143,12 @@ inline DView make_dview(const lub_domain *d)
         v.wall_z[k] = d->wall_z[k];
         v.wall_dir[k] = d->wall_dir[k];
     }
+    for (int k = 0; k < 3; ++k) {
+        v.Lff[k][0] = (float)d->L[k];
+        v.Lff[k][1] = (float)(d->L[k] - (double)v.Lff[k][0]);
+        v.invLf[k] = (float)(1.0 / d->L[k]);
+    }
+    v.pad = 0;
     return v;
 }
 

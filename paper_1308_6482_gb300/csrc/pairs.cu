@@ -440,14 +440,24 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
         it.oz = R.oz;
         }
         if (row == 0) {
-            // plane walls (exact double gap)
+            // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
+            // records (one double subtraction for z - z_w), decided in FP64 only
+            // within the margin (the exact test costs some 60 FP64 operations, a
+            // warp's worth of FP64 pipe time on this GPU for a fifth of its lanes)
             const int i = sorted[s];
+            const float4 o = rec1[s];
+            const float rm2 = a0.w * a0.w;
+            const float sz = sqrtf(fmaxf((o.w > 0.f ? rm2 - o.w : rm2) + o.w * o.z * o.z, 0.f));
             int wf = 0, bits = 0;
             for (int ww = 0; ww < D.n_walls; ++ww) {
-                const Shape<double> si = load_shape<double>(P, i);
-                const double hw =
-                    (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0));
-                if (hw < cutoff_d) {
+                const float hw = (float)D.wall_dir[ww] * (float)(P.z[i] - D.wall_z[ww]) - sz;
+                bool in = hw < G.cutoff - G.margin;
+                if (!in && hw <= G.cutoff + G.margin) {
+                    const Shape<double> si = load_shape<double>(P, i);
+                    in = (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0)) <
+                         cutoff_d;
+                }
+                if (in) {
                     bits |= 1 << ww;
                     ++wf;
                 }
