@@ -782,7 +782,7 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (cap == 0) return LUB_OK;
     int warm = 0;
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
-    const RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
+    const RParams R = make_rparams(prm);
     if (prm.precision == LUB_MIXED) {
         // the FP32 stage, then the FP64 work list and every pair's force in one
         // queue-driven launch (gap and status in the context when not given)

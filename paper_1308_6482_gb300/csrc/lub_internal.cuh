@@ -116,7 +116,23 @@ __device__ __forceinline__ const DView &pair_domain(const DView &D, const Ens &E
 struct RParams {
     double mu, delta_n, delta_t, delta_r, h_c, eps_c;
     int model;  // LUB_MODEL_FULL or LUB_MODEL_NORMAL
+    // the cut-offs and h_c as float-float (hi, lo), for the FP32 path
+    float dn_ff[2], dt_ff[2], dr_ff[2], hc_ff[2];
 };
+
+inline RParams make_rparams(const lub_params &p)
+{
+    RParams R{p.mu, p.delta_n, p.delta_t, p.delta_r, p.h_c, p.eps_c, p.model, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    auto split = [](double v, float o[2]) {
+        o[0] = (float)v;
+        o[1] = (float)(v - (double)o[0]);
+    };
+    split(p.delta_n, R.dn_ff);
+    split(p.delta_t, R.dt_ff);
+    split(p.delta_r, R.dr_ff);
+    split(p.h_c, R.hc_ff);
+    return R;
+}
 
 inline PView make_pview(const lub_particles *p)
 {

@@ -6,6 +6,7 @@
 // (Eq. lub:resistance).  See resistance.cu and apply.cu for the formulas.
 #pragma once
 
+#include "ff.cuh"
 #include "lub_internal.cuh"
 
 namespace {
@@ -52,6 +53,59 @@ __device__ __forceinline__ Surf<T> surface_at(const Shape<T> &s, const V3<T> &rh
     return o;
 }
 
+// The gap's terms at the element cut-offs (Eq. lub:resistance-correction) in
+// the arithmetic of T: he = h, or h_c where the contact model clips a
+// smaller gap; d_x = he - Delta_x for the three cut-offs, which cancels near
+// each cut-off; in_x = he < Delta_x; fr = h_c - h where the contact force
+// acts (h <= h_c with h_c > 0), else 0.  T = double: double arithmetic.
+// T = float: the double gap is split once into float-float (four FP64
+// operations, against a dozen for the double comparisons, differences and
+// conversions, on a pipe 1/64 as fast) and the rest runs in float-float, so
+// d_x keeps its relative accuracy near the cut-off.
+template <typename T>
+struct CutTerms {
+    T he, dn, dt, dr, fr;
+    bool in_n, in_t, in_r, contact;
+};
+
+__device__ __forceinline__ CutTerms<double> cut_terms(const RParams &R, double h, double)
+{
+    CutTerms<double> c;
+    c.he = (R.h_c > 0.0 && h < R.h_c) ? R.h_c : h;
+    c.dn = c.he - R.delta_n;
+    c.dt = c.he - R.delta_t;
+    c.dr = c.he - R.delta_r;
+    c.in_n = c.he < R.delta_n;
+    c.in_t = c.he < R.delta_t;
+    c.in_r = c.he < R.delta_r;
+    c.contact = R.h_c > 0.0 && h <= R.h_c;
+    c.fr = c.contact ? (h > 0.0 ? R.h_c - h : R.h_c) : 0.0;
+    return c;
+}
+
+__device__ __forceinline__ CutTerms<float> cut_terms(const RParams &R, double h, float)
+{
+    const float hi = (float)h;
+    ff he{hi, (float)(h - (double)hi)};
+    const ff hc{R.hc_ff[0], R.hc_ff[1]};
+    const ff dc = ff_sub(he, hc);
+    const float dcf = dc.hi + dc.lo;  // h - h_c
+    CutTerms<float> c;
+    c.contact = R.hc_ff[0] > 0.f && dcf <= 0.f;
+    if (R.hc_ff[0] > 0.f && dcf < 0.f) he = hc;
+    c.he = he.hi + he.lo;
+    const ff dn = ff_sub(he, ff{R.dn_ff[0], R.dn_ff[1]}), dt = ff_sub(he, ff{R.dt_ff[0], R.dt_ff[1]}),
+             dr = ff_sub(he, ff{R.dr_ff[0], R.dr_ff[1]});
+    c.dn = dn.hi + dn.lo;
+    c.dt = dt.hi + dt.lo;
+    c.dr = dr.hi + dr.lo;
+    c.in_n = c.dn < 0.f;
+    c.in_t = c.dt < 0.f;
+    c.in_r = c.dr < 0.f;
+    c.fr = c.contact ? (hi > 0.f ? -dcf : R.hc_ff[0]) : 0.f;
+    return c;
+}
+
 // Appendix: coefficients m_0..m_3 of a cubic given in a frame rotated by
 // alpha (cos c, sin s), in the unrotated frame.
 template <typename T>
@@ -81,7 +135,7 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         skip = true;
     }
     if (!skip) {
-        const double he = (R.h_c > 0.0 && h < R.h_c) ? R.h_c : h;
+        const CutTerms<T> cut = cut_terms(R, h, T(0));
         const Shape<T> si = load_shape<T>(P, i);
         const V3<T> rho_i = support_offset(si, n);
         const Surf<T> A = surface_at(si, rho_i, n);
@@ -135,15 +189,12 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
             // plus the contact branch; for two spheres Ladd's Eq. methods:llub
             const T PI = T(3.14159265358979323846);
             const T H33 = T(3) * PI / (sqrt_t(l1) * sqrt_t(l2) * (l1 + l2));
-            const T hq = (he < R.delta_n) ? (T)(R.delta_n - he) / ((T)he * (T)R.delta_n) : T(0);
+            const T hq = cut.in_n ? -cut.dn / (cut.he * (T)R.delta_n) : T(0);
             const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
             const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
             const T u3 = dot(x3, sub(Vj, add(vi, cross(Wi, rho_i))));
             T F3 = (T)R.mu * hq * H33 * u3;
-            if (R.h_c > 0.0 && h <= R.h_c) {
-                const double Fr = (h > 0.0) ? R.eps_c * (R.h_c - h) : R.eps_c * R.h_c;
-                F3 -= (T)Fr;
-            }
+            if (cut.contact) F3 -= (T)R.eps_c * cut.fr;
             out[0] = F3 * x3.x; out[1] = F3 * x3.y; out[2] = F3 * x3.z;
             out[6] = rho_i.x; out[7] = rho_i.y; out[8] = rho_i.z;
             out[9] = rho_j.x; out[10] = rho_j.y; out[11] = rho_j.z;
@@ -199,12 +250,10 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         const T L34 = pre34 * (Bq * cx - Aq * sx);
         const T L35 = -pre34 * (Aq * cx + Bq * sx);
         // K~: subtract the value at the element's cut-off (Eq. lub:resistance-correction);
-        // h - Delta is formed in double, where it cancels near the cut-off, and the
-        // quotients in T (in FP32 they keep the relative accuracy of h - Delta
-        // without the FP64 divisions, whose throughput is 1/64 of FP32 here)
-        const T lt = (he < R.delta_t) ? log1p_t((T)(he - R.delta_t) / (T)R.delta_t) : T(0);
-        const T lr = (he < R.delta_r) ? log1p_t((T)(he - R.delta_r) / (T)R.delta_r) : T(0);
-        const T hq = (he < R.delta_n) ? (T)(R.delta_n - he) / ((T)he * (T)R.delta_n) : T(0);
+        // he - Delta from cut_terms (accurate where it cancels), the quotients in T
+        const T lt = cut.in_t ? log1p_t(cut.dt / (T)R.delta_t) : T(0);
+        const T lr = cut.in_r ? log1p_t(cut.dr / (T)R.delta_r) : T(0);
+        const T hq = cut.in_n ? -cut.dn / (cut.he * (T)R.delta_n) : T(0);
         // relative surface velocities in the local frame
         const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
         const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
@@ -219,10 +268,7 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         T T4 = mu * (lt * (L14 * u1 + L24 * u2 + L34 * u3) + lr * (L44 * u4 + L45 * u5));
         T T5 = mu * (lt * (L15 * u1 + L25 * u2 + L35 * u3) + lr * (L45 * u4 + L55 * u5));
         T T6 = mu * (lt * (L36 * u3));
-        if (R.h_c > 0.0 && h <= R.h_c) {
-            const double Fr = (h > 0.0) ? R.eps_c * (R.h_c - h) : R.eps_c * R.h_c;
-            F3 -= (T)Fr;
-        }
+        if (cut.contact) F3 -= (T)R.eps_c * cut.fr;
         const V3<T> F = axpy(F1, x1, axpy(F2, x2, scl(F3, x3)));
         const V3<T> Tq = axpy(T4, x1, axpy(T5, x2, scl(T6, x3)));
         out[0] = F.x; out[1] = F.y; out[2] = F.z;

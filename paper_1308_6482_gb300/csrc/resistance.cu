@@ -112,7 +112,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
         if ((rc = zero_force_torque(ctx, force, torque, 3 * (size_t)P.n * esz, st))) return rc;
     }
     if (cap == 0) return LUB_OK;
-    RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
+    const RParams R = make_rparams(prm);
     const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
@@ -142,7 +142,7 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
                       const double *gap, uint8_t *status, void *FT, void *lever, cudaStream_t st)
 {
     if (cap == 0) return LUB_OK;
-    RParams R{prm.mu, prm.delta_n, prm.delta_t, prm.delta_r, prm.h_c, prm.eps_c, prm.model};
+    const RParams R = make_rparams(prm);
     const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
