@@ -82,6 +82,9 @@ def _load():
         lib.orc_apply.argtypes = [ctypes.c_int64, ctypes.c_int64, ip, ip, dp, dp, dp, dp]
         lib.orc_surface_geometry.restype = None
         lib.orc_surface_geometry.argtypes = [P(_Particles), ctypes.c_int64, dp, dp, dp]
+        lib.orc_links.restype = None
+        lib.orc_links.argtypes = [P(_Particles), P(_Domain), ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                  ip, ip, dp, dp, ip]
         lib.orc_g.restype = ctypes.c_double
         lib.orc_g.argtypes = [P(_Particles), P(_Domain), ctypes.c_int32, ctypes.c_int32, dp]
         lib.orc_surface_pq.restype = None
@@ -229,6 +232,25 @@ def apply(nparticles, pi, pj, FT, lever):
     t = np.zeros((nparticles, 3))
     lib.orc_apply(nparticles, len(pi), _ip(pi), _ip(pj), _dp(FT), _dp(lever), _dp(f), _dp(t))
     return f, t
+
+
+def links(parts, dom, pi, pj, mu=1.0 / 6.0, qbar=0.6):
+    """Link-based lubrication of Ding and Aidun (Eq. methods:dlub) per pair:
+    dict(F [m,3] force on i, T [m,6] torques on i and j about their centres,
+    links [m] contributing links).  See orc_links for the readings."""
+    lib = _load()
+    P = _as_particles(parts)
+    D = _domain(dom)
+    pi = np.ascontiguousarray(pi, np.int32)
+    pj = np.ascontiguousarray(pj, np.int32)
+    m = len(pi)
+    F = np.zeros((m, 3))
+    T = np.zeros((m, 6))
+    nl = np.zeros(m, np.int32)
+    if m:
+        lib.orc_links(ctypes.byref(P.c), ctypes.byref(D), float(mu), float(qbar), m, _ip(pi), _ip(pj), _dp(F),
+                      _dp(T), _ip(nl))
+    return dict(F=F, T=T, links=nl)
 
 
 def surface_geometry(parts, k, y, nrm):

@@ -1084,3 +1084,162 @@ void orc_mlp_baseline(const orc_particles *P, const orc_domain *D, int64_t np, c
         orc_surface_pq(P, pj[k], y, out + 4 * k + 2);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Link-based lubrication of Ding and Aidun, as the paper summarises  */
+/* it in Sec. II (Eq. methods:dlub), for comparison with the          */
+/* contact-based corrections.  For every D3Q19 link c_r (18 nonzero   */
+/* lattice vectors, c_r = 1 or sqrt 2) that ends on a site of          */
+/* particle i and stems from a site of particle j, or from a fluid    */
+/* site midway along 2 c_r from a site of j, a partial force on i     */
+/*   df = -3 qbar mu / (2 c_r^2 lambda*) c^ (c^ . (v_bi - v_bj))        */
+/*        (1 / h*^2 - 1 / c_r^2),        applied where h* < c_r,        */
+/* and -df on j.  h* is the distance along the link (or pair of links) */
+/* between the point where it leaves j's surface and the point where  */
+/* it enters i's; v_b are the rigid-body velocities there; lambda* is */
+/* the mean of the two surfaces' mean curvatures there.               */
+/* Readings: lattice sites are the integer points of the box          */
+/* coordinates (spacing 1); a site belongs to a particle when it lies */
+/* in or on its spheroid, and to neither when it lies in both (then   */
+/* it is no stem); particle j is taken at its minimum image from i; a */
+/* fluid site lies in neither particle of the pair; only 0 < h* < c_r */
+/* counts (h* <= 0: the surfaces overlap along the link); the forces  */
+/* act at the two intersection points (torques about the centres);    */
+/* walls give nothing.  Brute force: every site of i's bounding box,  */
+/* every link.                                                         */
+/* ------------------------------------------------------------------ */
+static int in_spheroid(const shape_t *s, const double x[3])
+{
+    double u[3] = {x[0] - s->r[0], x[1] - s->r[1], x[2] - s->r[2]}, b[3];
+    to_body(s, u, b);
+    double a2 = s->Rperp * s->Rperp, c2 = s->Rpar * s->Rpar;
+    return b[0] * b[0] / a2 + b[1] * b[1] / a2 + b[2] * b[2] / c2 <= 1.0;
+}
+
+/* the line x0 + t e (|e| = 1) meets the spheroid's surface at t_lo <= t_hi;
+   returns 0 when it misses */
+static int line_surface(const shape_t *s, const double x0[3], const double e[3], double *t_lo, double *t_hi)
+{
+    double u[3] = {x0[0] - s->r[0], x0[1] - s->r[1], x0[2] - s->r[2]}, ub[3], eb[3];
+    to_body(s, u, ub);
+    to_body(s, e, eb);
+    double R2[3] = {s->Rperp * s->Rperp, s->Rperp * s->Rperp, s->Rpar * s->Rpar};
+    double A = 0.0, B = 0.0, C = -1.0;
+    for (int k = 0; k < 3; ++k) {
+        A += eb[k] * eb[k] / R2[k];
+        B += 2.0 * ub[k] * eb[k] / R2[k];
+        C += ub[k] * ub[k] / R2[k];
+    }
+    double disc = B * B - 4.0 * A * C;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    *t_lo = (-B - sq) / (2.0 * A);
+    *t_hi = (-B + sq) / (2.0 * A);
+    return 1;
+}
+
+/* mean curvature (1/S1 + 1/S2) / 2 at the surface point y (radii of
+   curvature of Eq. lub:curvature-radii) */
+static double mean_curvature(const shape_t *s, const double y[3])
+{
+    double rel[3] = {y[0] - s->r[0], y[1] - s->r[1], y[2] - s->r[2]}, yb[3];
+    to_body(s, rel, yb);
+    double Rp = s->Rpar, Rq = s->Rperp;
+    double p = atan2(yb[2] / Rp, sqrt(yb[0] * yb[0] + yb[1] * yb[1]) / Rq);
+    double sp = sin(p), cp = cos(p);
+    double s1 = sqrt(Rq * Rq * sp * sp + Rp * Rp * cp * cp);
+    double S1 = s1 * s1 * s1 / (Rp * Rq), S2 = Rq * s1 / Rp;
+    return 0.5 * (1.0 / S1 + 1.0 / S2);
+}
+
+static const int orc_d3q19[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                     {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
+                                     {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+/* one pair: force on i F[3], torques on i and j about their centres T[6],
+   number of contributing links */
+static int links_one(const orc_particles *P, const orc_domain *D, double mu, double qbar, int32_t i, int32_t j,
+                     double F[3], double T[6])
+{
+    for (int k = 0; k < 3; ++k) F[k] = 0.0;
+    for (int k = 0; k < 6; ++k) T[k] = 0.0;
+    if (j < 0 || i < 0 || i >= P->n || j >= P->n || i == j) return 0;
+    shape_t si, sj;
+    load_shape(P, i, &si);
+    load_shape(P, j, &sj);
+    double d[3];
+    min_image(D, si.r, sj.r, d);
+    for (int k = 0; k < 3; ++k) sj.r[k] = si.r[k] + d[k];
+    const double vi[3] = {P->vx[i], P->vy[i], P->vz[i]}, wi[3] = {P->wx[i], P->wy[i], P->wz[i]};
+    const double vj[3] = {P->vx[j], P->vy[j], P->vz[j]}, wj[3] = {P->wx[j], P->wy[j], P->wz[j]};
+    int64_t lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        double ek[3] = {0.0, 0.0, 0.0};
+        ek[k] = 1.0;
+        double w = support(&si, ek);
+        lo[k] = (int64_t)ceil(si.r[k] - w);
+        hi[k] = (int64_t)floor(si.r[k] + w);
+    }
+    int nlinks = 0;
+    for (int64_t a = lo[0]; a <= hi[0]; ++a)
+        for (int64_t b = lo[1]; b <= hi[1]; ++b)
+            for (int64_t c = lo[2]; c <= hi[2]; ++c) {
+                double x[3] = {(double)a, (double)b, (double)c};
+                if (!in_spheroid(&si, x)) continue;
+                for (int r = 0; r < 18; ++r) {
+                    const double cv[3] = {(double)orc_d3q19[r][0], (double)orc_d3q19[r][1],
+                                          (double)orc_d3q19[r][2]};
+                    double y1[3] = {x[0] - cv[0], x[1] - cv[1], x[2] - cv[2]};
+                    double y2[3] = {x[0] - 2.0 * cv[0], x[1] - 2.0 * cv[1], x[2] - 2.0 * cv[2]};
+                    int kind = 0;
+                    const int y1i = in_spheroid(&si, y1), y1j = in_spheroid(&sj, y1);
+                    if (y1j && !y1i)
+                        kind = 1;
+                    else if (!y1j && !y1i && in_spheroid(&sj, y2) && !in_spheroid(&si, y2))
+                        kind = 2;
+                    if (!kind) continue;
+                    const double cr = norm3(cv);
+                    const double e[3] = {cv[0] / cr, cv[1] / cr, cv[2] / cr};
+                    const double *x0 = kind == 1 ? y1 : y2;
+                    double tjl, tjh, til, tih;
+                    if (!line_surface(&sj, x0, e, &tjl, &tjh) || !line_surface(&si, x0, e, &til, &tih)) continue;
+                    const double hstar = til - tjh;
+                    if (!(hstar > 0.0 && hstar < cr)) continue;
+                    double pi_[3], pj_[3];
+                    for (int k = 0; k < 3; ++k) {
+                        pi_[k] = x0[k] + til * e[k];
+                        pj_[k] = x0[k] + tjh * e[k];
+                    }
+                    double ri[3] = {pi_[0] - si.r[0], pi_[1] - si.r[1], pi_[2] - si.r[2]};
+                    double rj[3] = {pj_[0] - sj.r[0], pj_[1] - sj.r[1], pj_[2] - sj.r[2]};
+                    double wri[3], wrj[3];
+                    cross3(wi, ri, wri);
+                    cross3(wj, rj, wrj);
+                    double dv[3];
+                    for (int k = 0; k < 3; ++k) dv[k] = (vi[k] + wri[k]) - (vj[k] + wrj[k]);
+                    const double lam = 0.5 * (mean_curvature(&si, pi_) + mean_curvature(&sj, pj_));
+                    const double coef =
+                        -3.0 * qbar * mu / (2.0 * cr * cr * lam) * (1.0 / (hstar * hstar) - 1.0 / (cr * cr)) *
+                        dot3(e, dv);
+                    double df[3] = {coef * e[0], coef * e[1], coef * e[2]}, mdf[3] = {-df[0], -df[1], -df[2]};
+                    double ti[3], tj[3];
+                    cross3(ri, df, ti);
+                    cross3(rj, mdf, tj);
+                    for (int k = 0; k < 3; ++k) {
+                        F[k] += df[k];
+                        T[k] += ti[k];
+                        T[3 + k] += tj[k];
+                    }
+                    ++nlinks;
+                }
+            }
+    return nlinks;
+}
+
+/* per pair: force on i F[np][3], torques on i and j T[np][6], links[np] */
+void orc_links(const orc_particles *P, const orc_domain *D, double mu, double qbar, int64_t np, const int32_t *pi,
+               const int32_t *pj, double *F, double *T, int32_t *links)
+{
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t k = 0; k < np; ++k) links[k] = links_one(P, D, mu, qbar, pi[k], pj[k], F + 3 * k, T + 6 * k);
+}
