@@ -342,6 +342,28 @@ def run_ours(args):
         normal_ms = float(np.mean([a.elapsed_time(b) for a, b in e3]))
         del g3, pln
 
+    # the comparison model of Sec. II: the link-based lubrication of Ding and
+    # Aidun (lub_links) on the same pair list, one call per step, L2 flushed
+    link = None
+    if graph is not None:
+        with torch.cuda.stream(stream):
+            F_l, T_l, nl_l = pl.links(0.6, stream=stream)
+        stream.synchronize()
+        e5 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+        with torch.cuda.stream(stream):
+            for a, b in e5:
+                flush.zero_()
+                a.record(stream)
+                pl.links(0.6, stream=stream)
+                b.record(stream)
+        stream.synchronize()
+        link_ms = float(np.mean([a.elapsed_time(b) for a, b in e5]))
+        nl_host = nl_l[:npairs].cpu().numpy()
+        link = {"ms_per_call": link_ms, "pairs_per_s": npairs / (link_ms * 1e-3),
+                "links_per_pair": float(nl_host.mean()), "pairs_with_links": float((nl_host > 0).mean()),
+                "note": "Eq. methods:dlub on a unit lattice, D3Q19 links, q_bar = 0.6, FP64 per link; the pair list "
+                        "of the step (gaps up to Delta_L = 1), one warp per pair"}
+
     # particle sub-stepping (Sec. II) on the same workload with the contact
     # branch (h_c = 0.01, eps_c = 100): one LB step = the pair build and 10
     # sub-steps of (closest points, resistance + scatter, rigid update) at
@@ -469,6 +491,7 @@ def run_ours(args):
                             "calls": "pair build + closest points + resistance + apply"}[form],
                    "other_forms_ms_per_step": forms_ms,
                    "normal_only_model_ms_per_step": normal_ms,
+                   "comparison_link_model": link,
                    "substepping": substep,
                    "pairs_per_step": int(npairs),
                    "particles": args.n, "l2": "flushed between timed steps (256 MB write outside the step events)",

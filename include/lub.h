@@ -400,6 +400,33 @@ int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, 
                       const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n, void *stream);
 
 /*
+ * Link-based lubrication of Ding and Aidun (Sec. II, Eq. methods:dlub), the
+ * correction the paper compares against, on a synthetic lattice: lattice
+ * sites are the integer points of the box coordinates (spacing 1) and a site
+ * belongs to a particle when it lies in or on its spheroid.  For every pair
+ * (i, j) of the list and every D3Q19 link c_r (the 18 nonzero lattice
+ * vectors, c_r = 1 or sqrt 2) that ends on a site of i and stems from a site
+ * of j (not also in i), or from a fluid site (in neither particle) midway
+ * along 2 c_r from a site of j, the partial force
+ *   df = -3 q_bar mu / (2 c_r^2 lambda*) c^ (c^.(v_bi - v_bj)) (1/h*^2 - 1/c_r^2)
+ * acts on i where 0 < h* < c_r, and -df on j.  h*: the distance along the
+ * link(s) from where it leaves j's surface to where it enters i's; v_b: the
+ * rigid-body velocities there; lambda*: the mean of the two surfaces' mean
+ * curvatures there; j is taken at its minimum image from i.  Outputs, per
+ * pair k (device arrays the caller owns):
+ *   force   [3][capacity] double: the sum of df on i
+ *   torque  [6][capacity] double: torque on i, then on j, about the centres
+ *   n_links [capacity] int32 (may be NULL): the links that contributed
+ * Wall pairs (j < 0) and invalid pairs give zeros.  mu is prm->mu; q_bar the
+ * empirical weight (0.6 in the paper); the particles need v and w.  One warp
+ * per pair; site membership in FP32 with an FP64 re-test near the surface,
+ * the qualifying links in FP64.  Asynchronous on `stream`.
+ */
+int lub_links(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+              const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+              double q_bar, double *force, double *torque, int32_t *n_links, void *stream);
+
+/*
  * Particle sub-step (Sec. II: the particle update is decoupled from the
  * lattice-Boltzmann step and runs at a fraction of it, typically 1/10, so the
  * strongly varying lubrication forces are followed while the forces from the

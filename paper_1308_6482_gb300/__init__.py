@@ -18,7 +18,7 @@ from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, L
                    default_params, library_path, load_library, lub_apply, lub_closest_points,
                    lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_last_error, lub_mlp_adam,
                    lub_mlp_features, lub_mlp_forward_backward, lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static,
-                   lub_resistance, make_domain, make_ensemble, lub_autotune, lub_get_launch_shape, lub_set_launch_shape, lub_carry_normals, lub_correct, lub_resistance_apply, lub_rigid_step, lub_mlp_engine, LUB_MLP_MMA_SYNC, LUB_MLP_TCGEN05,
+                   lub_resistance, make_domain, make_ensemble, lub_autotune, lub_get_launch_shape, lub_set_launch_shape, lub_carry_normals, lub_correct, lub_resistance_apply, lub_rigid_step, lub_links, lub_mlp_engine, LUB_MLP_MMA_SYNC, LUB_MLP_TCGEN05,
                    LUB_TUNE_CLOSEST_MIXED, LUB_TUNE_CLOSEST_REFINE, LUB_TUNE_CLOSEST_FP64, LUB_TUNE_RESISTANCE,
                    LUB_TUNE_APPLY, LUB_TUNE_SWEEP, LUB_TUNE_COUNT, TUNE_NAMES)
 

@@ -73,7 +73,7 @@ EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
            "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
-           "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine")
+           "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine", "lub_links")
 
 _lib = None
 
@@ -108,6 +108,9 @@ def load_library():
     lib.lub_closest_points.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp,
                                        vp, vp, vp, vp]
     lib.lub_resistance.restype = ctypes.c_int
+    lib.lub_links.restype = i32
+    lib.lub_links.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, ctypes.c_double,
+                              vp, vp, vp, vp]
     lib.lub_resistance.argtypes = [vp, P(lub_particles), P(lub_domain), P(lub_params), vp, vp, vp, i32, vp, vp,
                                    vp, vp, vp, vp]
     lib.lub_apply.restype = ctypes.c_int
@@ -266,6 +269,13 @@ def lub_resistance(ctx, particles, domain, params, pair_i, pair_j, d_count, capa
     return _check(ctx, load_library().lub_resistance(
         ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
         _ptr(d_count), int(capacity), _ptr(n), _ptr(gap), _ptr(status), _ptr(FT), _ptr(lever), _stream(stream)))
+
+
+def lub_links(ctx, particles, domain, params, pair_i, pair_j, d_count, capacity, q_bar, force, torque, n_links=None,
+              stream=None):
+    return _check(ctx, load_library().lub_links(
+        ctx, ctypes.byref(particles), _dom(domain), ctypes.byref(params), _ptr(pair_i), _ptr(pair_j),
+        _ptr(d_count), int(capacity), float(q_bar), _ptr(force), _ptr(torque), _ptr(n_links), _stream(stream)))
 
 
 def lub_apply(ctx, pair_i, pair_j, d_count, capacity, FT, lever, n, force, torque, precision, accumulate=0,
@@ -522,6 +532,21 @@ class Pipeline:
     def resistance(self, stream=None):
         lub_resistance(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap,
                        self.nrm, self.gap, self.status, self.FT, self.lever, stream=stream)
+
+    def links(self, q_bar=0.6, stream=None):
+        """Link-based lubrication of Ding and Aidun on this step's pair list
+        (lub_links): per-pair force on i [3][cap], torques on i and j [6][cap]
+        and link counts [cap], double and int32 device tensors."""
+        import torch
+        dev = self.pair_i.device
+        if getattr(self, "_links_cap", None) != self.cap:
+            self.link_force = torch.zeros(3 * self.cap, dtype=torch.float64, device=dev)
+            self.link_torque = torch.zeros(6 * self.cap, dtype=torch.float64, device=dev)
+            self.link_count = torch.zeros(self.cap, dtype=torch.int32, device=dev)
+            self._links_cap = self.cap
+        lub_links(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap, q_bar,
+                  self.link_force, self.link_torque, self.link_count, stream=stream)
+        return self.link_force, self.link_torque, self.link_count
 
     def apply(self, deterministic=0, accumulate=0, stream=None):
         lub_apply(self.ctx.h, self.pair_i, self.pair_j, self.d_count, self.cap, self.FT, self.lever, self.n,

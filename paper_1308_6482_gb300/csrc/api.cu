@@ -343,6 +343,25 @@ int lub_resistance(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, 
                              lever, (cudaStream_t)stream);
 }
 
+int lub_links(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
+              const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
+              double q_bar, double *force, double *torque, int32_t *n_links, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, true)) || (rc = check_params(ctx, prm)) ||
+        (rc = check_pairs(ctx, pair_i, pair_j, d_count, capacity)))
+        return rc;
+    if (capacity > 0 && (!force || !torque)) return lub_set_error(ctx, LUB_ERR_ARG, "force or torque is NULL");
+    if (!(q_bar >= 0.0) || !isfinite(q_bar)) return lub_set_error(ctx, LUB_ERR_ARG, "q_bar must be finite and >= 0");
+    DView D;
+    Ens E;
+    if ((rc = prepare_domains(ctx, p, dom, (cudaStream_t)stream, &D, &E))) return rc;
+    return launch_links(ctx, make_pview(p), D, E, pair_i, pair_j, d_count, capacity, prm->mu, q_bar, force, torque,
+                        n_links, (cudaStream_t)stream);
+}
+
 int lub_apply(lub_ctx *ctx, const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity,
               const void *FT, const void *lever, int32_t n, void *force, void *torque, int32_t precision,
               int32_t accumulate, int32_t deterministic, void *stream)

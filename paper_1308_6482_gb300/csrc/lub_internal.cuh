@@ -340,6 +340,9 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
                             void *torque, int accumulate, cudaStream_t st);
+int launch_links(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi, const int32_t *pj,
+                 const int32_t *d_count, int32_t cap, double mu, double qbar, double *force, double *torque,
+                 int32_t *nlinks, cudaStream_t st);
 int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                       const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                       const double *n, const double *gap, uint8_t *status, void *FT, void *lever,
