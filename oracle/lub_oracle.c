@@ -35,6 +35,10 @@
  *                      (V_i = v_i + w_i x (y*_i - r_i), t_i = T_i + ... x F_i).
  *   orc_apply          per-particle sums, with Newton's third law of
  *                      Eq. lub:resistance for particle j.
+ *   orc_links          the link-based lubrication of Ding and Aidun that the
+ *                      paper compares against (Sec. II, Eq. methods:dlub),
+ *                      by brute force over the lattice sites and D3Q19 links
+ *                      of a pair (readings in the section's comment).
  *
  * Readings of the paper that the code takes (each is also a test):
  *   - x1 is the unit vector along d y~/dp (increasing p), x3 the outward
