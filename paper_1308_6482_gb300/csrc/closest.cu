@@ -460,8 +460,8 @@ __global__ void __launch_bounds__(256) k_pos_ff(PView P, float2 *__restrict__ ou
         const double v[3] = {P.x[i], P.y[i], P.z[i]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float hi = (float)v[a];
-            out[a * N + i] = make_float2(hi, (float)(v[a] - (double)hi));
+            const ff p = ff_from_double(v[a]);
+            out[a * N + i] = make_float2(p.hi, p.lo);
         }
     }
 }
