@@ -345,3 +345,48 @@ def test_dense_packings(case):
     np.testing.assert_array_equal(g["pi"], pi)
     np.testing.assert_array_equal(g["pj"], pj)
     compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
+
+
+def test_wall_pairs_at_the_list_cutoff():
+    """Particles whose wall gap lies within 1e-4 of Delta_L = 1: the FP32 wall
+    pre-filter leaves them inside its margin and the exact FP64 test decides;
+    the wall pairs must be the oracle's."""
+    rng = np.random.default_rng(91)
+    n = 200
+    L = 400.0
+    r_par = rng.uniform(2.0, 8.0, n).astype(np.float32)
+    r_perp = rng.uniform(2.0, 8.0, n).astype(np.float32)
+    q = gen.random_quaternions(n, rng)
+    # half-width along z of each spheroid, then z so that the gap to the wall
+    # at z = 0 is 1 + u, |u| < 1e-4
+    o_z = 1.0 - 2.0 * (q[:, 1].astype(np.float64) ** 2 + q[:, 2].astype(np.float64) ** 2)
+    o_z /= (q.astype(np.float64) ** 2).sum(1)
+    sz = np.sqrt(r_perp.astype(np.float64) ** 2 + (r_par.astype(np.float64) ** 2 - r_perp.astype(np.float64) ** 2) * o_z ** 2)
+    u = rng.uniform(-1e-4, 1e-4, n)
+    side = int(np.ceil(np.sqrt(n)))
+    idx = np.arange(n)
+    parts = dict(x=(idx % side + 0.5) * (L / side), y=(idx // side + 0.5) * (L / side), z=sz + 1.0 + u,
+                 qw=q[:, 0].copy(), qx=q[:, 1].copy(), qy=q[:, 2].copy(), qz=q[:, 3].copy(), r_par=r_par,
+                 r_perp=r_perp)
+    gen.velocities(parts, rng)
+    dom = dict(L=(L, L, L), periodic=(True, True, False), walls=[(0.0, 1)])
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert 0.25 * n < np.sum(pj < 0) < 0.75 * n          # both sides of the cut-off
+    g = run_gpu(parts, dom, "fp64")
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+
+
+@pytest.mark.parametrize("offset", [0.0, 2000.0])
+def test_mixed_precision_far_from_the_origin(offset):
+    """The FP32 stage takes its separations from float-float positions (about
+    48 bits, 2e-12 absolute at |r| = 2000): pairs placed near |r| = 2000 keep
+    gap and force parity in mixed precision, including the gaps just above
+    the FP64 switch that the float-float gap decides alone."""
+    parts, dom, pi, pj = gen.pair_stream(2000, seed=93, kind="aspect", gap_range=(1e-3, 1.0), gap_scale="min_axis")
+    parts = dict(parts)
+    for k in ("x", "y", "z"):
+        parts[k] = np.asarray(parts[k], np.float64) + offset
+    dom = dict(dom, L=tuple(v + 2 * offset for v in dom["L"]))
+    g = run_gpu(parts, dom, "mixed", pi, pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
