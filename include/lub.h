@@ -278,7 +278,10 @@ int lub_mlp_set(lub_ctx *ctx, const float *params, const float *mean, const floa
  * 32 pairs, activations in registers; LUB_MLP_TCGEN05 with tcgen05.mma, 128
  * pairs per CTA, accumulators in tensor memory, operands staged in shared
  * memory (weights by one bulk copy per CTA).  Same results up to the order
- * of the FP32 accumulation.  A bounded wait of the tcgen05 path that times
+ * of the FP32 accumulation.  With LUB_MLP_MMA_SYNC, lub_closest runs the
+ * network inside its own kernel (each warp infers the start normals of its
+ * 32 pairs and solves them in the same launch); with LUB_MLP_TCGEN05 the
+ * network is a launch of its own before the solve.  A bounded wait of the tcgen05 path that times
  * out sets bit 3 (value 8) of the context's flags and ends the kernel. */
 #define LUB_MLP_MMA_SYNC 0
 #define LUB_MLP_TCGEN05 1

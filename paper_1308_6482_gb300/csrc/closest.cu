@@ -27,6 +27,7 @@
 // LUB_FP64: the whole solve and gap in double.
 #include "ff.cuh"
 #include "lub_mlp.cuh"
+#include "mlp_infer.cuh"
 #include "pair_force.cuh"
 
 namespace {
@@ -549,6 +550,91 @@ __global__ void __launch_bounds__(128) k_closest_fp64(PView P, const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
+// the learned warm start inside the closest-point kernels (the mma.sync
+// engine): every warp runs the network for its 32 pairs on the tensor cores,
+// forms Newton's start normals from the outputs, writes them to n (the solve
+// reads them back from there: the same thread, cached) and solves; one launch
+// instead of the network's own, no start normals through HBM in between.
+// ---------------------------------------------------------------------------
+template <bool ENS>
+__global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_mixed_learned(
+    PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+    const int32_t *__restrict__ d_count, int32_t cap, double *__restrict__ nout, double *__restrict__ gap,
+    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, float tol32, float fp64_switch,
+    int32_t *__restrict__ wl_count, int32_t *__restrict__ wl, const float2 *__restrict__ pff, MlpDevice M)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InfSmem &S = *reinterpret_cast<InfSmem *>(smem_raw);
+    stage_weights(S, M);
+    __syncthreads();
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = (blockIdx.x * INF_WARPS + w) * 32; base < count; base += gridDim.x * INF_WARPS * 32) {
+        const int k = base + lane;
+        float f[NI];
+        const PairIn in = pair_inputs<ENS>(P, D0, E, pi, pj, k, count, S.mean, S.istd, f);
+        const float4 y = warp_mlp(S, S.x[w], S.y[w], f, lane);
+        pair_outputs(P, in, y, k, count, C, nout, nullptr);
+        int entry = kNoEntry;
+        if (k < count) {
+            V3<double> n64;
+            double h;
+            int st, nit;
+            entry = closest_mixed_one<ENS>(P, D0, E, pff, __ldg(pi + k), __ldg(pj + k), k, nout, C, 1, maxit, tol32,
+                                           fp64_switch, n64, h, st, nit);
+            store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+        }
+        worklist_append(entry, wl_count, wl, cap);
+    }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_fp64_learned(
+    PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+    const int32_t *__restrict__ d_count, int32_t cap, double *__restrict__ nout, double *__restrict__ gap,
+    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, MlpDevice M)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InfSmem &S = *reinterpret_cast<InfSmem *>(smem_raw);
+    stage_weights(S, M);
+    __syncthreads();
+    const int count = pair_count(d_count, cap);
+    const size_t C = (size_t)cap;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = (blockIdx.x * INF_WARPS + w) * 32; base < count; base += gridDim.x * INF_WARPS * 32) {
+        const int k = base + lane;
+        float f[NI];
+        const PairIn in = pair_inputs<ENS>(P, D0, E, pi, pj, k, count, S.mean, S.istd, f);
+        const float4 y = warp_mlp(S, S.x[w], S.y[w], f, lane);
+        pair_outputs(P, in, y, k, count, C, nout, nullptr);
+        if (k < count) {
+            V3<double> n64;
+            double h;
+            int st, nit;
+            closest_fp64_one<ENS>(P, D0, E, __ldg(pi + k), __ldg(pj + k), k, nout, C, 1, maxit, n64, h, st, nit);
+            store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+        }
+    }
+}
+
+// the shared-memory size of the learned kernels, set once per kernel (bits 16..)
+template <typename K>
+int learned_smem(lub_ctx *ctx, K kernel, int bit)
+{
+    if (ctx->mlp_smem_set & bit) return LUB_OK;
+    const int rc = lub_check_cuda(
+        ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InfSmem)),
+        "shared memory attribute");
+    if (!rc) ctx->mlp_smem_set |= bit;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // fused pass (lub_correct): closest points, resistance and the atomic scatter
 // of each pair without leaving registers.  nout is required (it holds the
 // start normals and carries the FP32 normals to the refinement); gap,
@@ -745,25 +831,40 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
                      uint8_t *status, uint8_t *iters, cudaStream_t st)
 {
-    int warm = 0;
-    int rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm);
-    if (rc) return rc;
+    int warm = 0, rc;
+    // the learned start on the mma.sync engine runs inside the solve's kernel
+    const bool fused_mlp = prm.warm_start == LUB_WARM_MLP && ctx->mlp_engine == LUB_MLP_MMA_SYNC;
+    if (fused_mlp && !ctx->mlp_ready)
+        return lub_set_error(ctx, LUB_ERR_ARG, "the learned warm start needs lub_mlp_set first");
+    if (!fused_mlp && (rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
+    const int learned_grid = 2 * ctx->num_sms;
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl, nullptr, nullptr, &P, &pff))) return rc;
-        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
-                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl,
-                         (const float2 *)pff);
+        if (fused_mlp) {
+            if ((rc = learned_smem(ctx, k_closest_mixed_learned<ENS>, 16 << ENS))) return rc;
+            (void)launch_pdl(k_closest_mixed_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E,
+                             pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton, (float)prm.newton_tol,
+                             (float)prm.fp64_switch, wl_count, wl, (const float2 *)pff, *(const MlpDevice *)ctx->mlp);
+        } else {
+            const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
+            (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap,
+                             status, iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm,
+                             wl_count, wl, (const float2 *)pff);
+        }
         // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
         (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
                                                             prm.max_newton, wl_count, wl);
+    } else if (fused_mlp) {
+        if ((rc = learned_smem(ctx, k_closest_fp64_learned<ENS>, 64 << ENS))) return rc;
+        (void)launch_pdl(k_closest_fp64_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E, pi,
+                         pj, d_count, cap, n, gap, status, iters, prm.max_newton, *(const MlpDevice *)ctx->mlp);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
-        (void)launch_pdl(k_closest_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status, iters,
-                                                         prm.max_newton, warm);
+        (void)launch_pdl(k_closest_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
+                         iters, prm.max_newton, warm);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
 }
