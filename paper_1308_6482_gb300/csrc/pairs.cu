@@ -1,12 +1,16 @@
 // K0: candidate pairs by a cell list with the pre-filters of Sec. III A.
 //
-//   1. cell of every particle (cell edge >= 2 Rmax + Delta_L) and its slot
-//      in the cell (atomic), scan of the cell counts, copy of every particle
-//      into cell order as two float4 records: position relative to its cell
-//      centre with Rmax, and symmetry axis with e = R_par^2 - R_perp^2;
+//   1. cell of every particle (cell edge >= 2 Rmax + Delta_L in y and z, an
+//      eighth of that in x) and its slot in the cell (atomic), scan of the
+//      cell counts, copy of every particle into cell order as two float4
+//      records: position relative to its cell centre with Rmax, and symmetry
+//      axis with e = R_par^2 - R_perp^2;
 //   2. sweep: one thread per (particle, row of the half-shell stencil), five
-//      rows per particle covering the own cell and the 13 forward neighbours,
-//      particles in cell order so neighbouring threads read the same cells;
+//      rows (y, z columns of cells) per particle covering the own column and
+//      the 4 forward neighbours; in each row the x cells within the
+//      particle's reach form a run of slots; each warp shares out its 32
+//      items' candidates over its lanes and queues those that pass the
+//      bounding-sphere test for the full test, 32 at a time;
 //      each unordered pair is visited once and stored for the smaller of its
 //      two indices in that particle's row of KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
@@ -32,7 +36,7 @@
 namespace {
 
 struct Grid {
-    int nc[3];
+    int nc[3];      // x: fine cells (xsub per coarse column); y, z: coarse
     float cs[3];
     double csd[3];
     double inv_cs[3];
@@ -41,7 +45,15 @@ struct Grid {
     float cutoff;  // Delta_L
     float margin;  // absolute FP32 error allowance of the tests
     float rmax;    // bound of every particle's Rmax
+    int xsub;      // fine x cells per cell edge of the interaction range
 };
+
+// Fine cells along x: a row of the stencil (one y, z column of cells) is cut
+// into x cells a fraction of the interaction range wide, so each particle
+// tests only the candidates in the x window its reach allows in that row
+// (|dx| <= sqrt(reach^2 - dyz^2), dyz the distance to the row's y, z cells),
+// a contiguous run of cells and so of slots, instead of three whole cells.
+constexpr int kXSub = 8;
 
 // partner slots per particle in the sweep; more go to the overflow list
 constexpr int KSLOT = 16;
@@ -171,15 +183,19 @@ __device__ __forceinline__ bool pair_test_fp64(const PView &P, const DView &D, i
 // test decides)
 constexpr int kReject = 0, kAccept = 1, kUndecided = 2;
 
-__device__ __forceinline__ int pair_test(const Grid &G, const float4 a0, const float4 a1, const float4 b0,
-                                         const float4 *__restrict__ b1p, float ox, float oy, float oz)
+// first test: the bounding spheres (with the margin); d = b - a + offset
+__device__ __forceinline__ bool pair_near(const Grid &G, float aw, float bw, float r2)
 {
-    const float dx = b0.x - a0.x + ox, dy = b0.y - a0.y + oy, dz = b0.z - a0.z + oz;
+    const float hi = aw + bw + G.cutoff + G.margin;
+    return r2 <= hi * hi;  // most candidates end here, before the second record
+}
+
+// the rest of the decision for a candidate that passed pair_near
+__device__ __forceinline__ int pair_decide(const Grid &G, const float4 a0, const float4 a1, float bw, const float4 b1,
+                                           float dx, float dy, float dz)
+{
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float lim = a0.w + b0.w + G.cutoff;
-    const float hi = lim + G.margin;
-    if (r2 > hi * hi) return kReject;  // most candidates end here, before the second record
-    const float4 b1 = *b1p;
+    const float lim = a0.w + bw + G.cutoff;
     bool sure = true;
     const float lo = lim - G.margin;
     if (r2 >= lo * lo) sure = false;
@@ -191,10 +207,10 @@ __device__ __forceinline__ int pair_test(const Grid &G, const float4 a0, const f
         const float ci = (a1.x * dx + a1.y * dy + a1.z * dz) * ir;
         const float cj = (b1.x * dx + b1.y * dy + b1.z * dz) * ir;
         const float api = a1.w > 0.f ? a0.w * a0.w - a1.w : a0.w * a0.w;
-        const float apj = b1.w > 0.f ? b0.w * b0.w - b1.w : b0.w * b0.w;
+        const float apj = b1.w > 0.f ? bw * bw - b1.w : bw * bw;
         const float sgi = sqrtf(fmaxf(api + a1.w * ci * ci, 0.f));
         const float sgj = sqrtf(fmaxf(apj + b1.w * cj * cj, 0.f));
-        const float t1 = r - sgi - (b0.w + G.cutoff);
+        const float t1 = r - sgi - (bw + G.cutoff);
         const float t2 = r - sgj - (a0.w + G.cutoff);
         if (t1 > G.margin || t2 > G.margin) return kReject;
         if (t1 >= -G.margin || t2 >= -G.margin) sure = false;
@@ -204,78 +220,29 @@ __device__ __forceinline__ int pair_test(const Grid &G, const float4 a0, const f
     return sure ? kAccept : kUndecided;
 }
 
-// Half-shell sweep: the 14 cells of the stencil (the own cell and the 13
-// forward neighbours, offsets (dx, dy, dz) lexicographically above zero) in
-// five rows: row 0 = (dz, dy) = (0, 0) with dx = 0, 1; row 1 = (0, 1); rows
-// 2..4 = (1, -1..1), the last four with dx = -1, 0, 1.  Each unordered pair of
-// neighbouring cells is seen from one side only; in the own cell the partner's
-// slot must follow (t > s).  On a periodic axis with fewer than three cells a
-// forward neighbour can be the own cell or coincide with another neighbour
-// under a different image offset: every (cell, offset) is then a distinct
-// periodic image, the own cell at a non-zero offset is tested against every
-// other particle (t != s), and the domain check (L > 2 range) leaves at most
-// one image of a pair within range, so each pair passes exactly once.
-// emit(t, r) is called for every candidate the FP32 tests accept or leave
-// undecided (r = kAccept or kUndecided).
+// Half-shell sweep: the 14 coarse cells of the stencil (the own cell and the
+// 13 forward neighbours, offsets (dx, dy, dz) lexicographically above zero)
+// as five rows of the y, z columns: row 0 = (dz, dy) = (0, 0), forward in x
+// only; row 1 = (0, 1); rows 2..4 = (1, -1..1), the last four both ways in x.
+// Along a row the fine x cells of the particle's window form one run of
+// slots (up to three on a periodic x axis: the cells below 0 and above
+// nx - 1 belong to the images at -L_x and +L_x).  Each unordered pair is seen
+// from one side only: in another row from the particle whose forward rows
+// hold the other; in row 0 from the one in the lower x cell, or, in the same
+// cell, from the lower slot (the run of row 0 starts right after the
+// particle's own slot).  A run at a non-zero image never pairs a particle
+// with itself (t != s); on a periodic axis the domain check (L > 2 range)
+// leaves at most one image of a pair within range, so each pair passes
+// exactly once.
 constexpr int SWEEP_ROWS = 5;
 
-template <typename Emit>
-__device__ __forceinline__ void sweep_row(const DView &D, const Grid &G, const int32_t *__restrict__ cell_start,
-                                          const float4 *__restrict__ rec0, const float4 *__restrict__ rec1, int s,
-                                          const float4 a0, const float4 a1, int cx, int cy, int cz, int row,
-                                          int cbase, Emit emit)
-{
-    const int dz = row >= 2 ? 1 : 0;
-    const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-    const int dx0 = row == 0 ? 0 : -1;
-    int yc = cy + dy, zc = cz + dz;
-    if (yc < 0 || yc >= G.nc[1]) {
-        if (!D.periodic[1]) return;
-        yc += yc < 0 ? G.nc[1] : -G.nc[1];
-    }
-    if (zc < 0 || zc >= G.nc[2]) {
-        if (!D.periodic[2]) return;
-        zc += zc < 0 ? G.nc[2] : -G.nc[2];
-    }
-    const int own = cbase + (cz * G.nc[1] + cy) * G.nc[0] + cx;
-    const float oy = dy * G.cs[1], oz = dz * G.cs[2];
-    const int rowbase = cbase + (zc * G.nc[1] + yc) * G.nc[0];
-    // skip neighbour cells no partner of particle s can reach: distance from
-    // the particle to the cell's box against Rmax_s + Rmax + Delta_L
-    const float reach = a0.w + G.rmax + G.cutoff + G.margin;
-    const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2], hx = 0.5f * G.cs[0];
-    const float ey = dy == 0 ? 0.f : fmaxf(fabsf(oy - a0.y) - hy, 0.f);
-    const float ez = dz == 0 ? 0.f : fmaxf(fabsf(oz - a0.z) - hz, 0.f);
-    const float r2yz = ey * ey + ez * ez;
-    if (r2yz > reach * reach) return;
-    for (int dx = dx0; dx <= 1; ++dx) {
-        int xc = cx + dx;
-        if (xc < 0 || xc >= G.nc[0]) {
-            if (!D.periodic[0]) continue;
-            xc += xc < 0 ? G.nc[0] : -G.nc[0];
-        }
-        const int c2 = rowbase + xc;
-        const float ox = dx * G.cs[0];
-        const float ex = dx == 0 ? 0.f : fmaxf(fabsf(ox - a0.x) - hx, 0.f);
-        if (ex * ex + r2yz > reach * reach) continue;
-        const bool zero_offset = dx == 0 && dy == 0 && dz == 0;
-        const bool self = c2 == own;
-        const int e = cell_start[c2 + 1];
-        for (int t = zero_offset ? s + 1 : cell_start[c2]; t < e; ++t) {
-            if (self && t == s) continue;
-            const int r = pair_test(G, a0, a1, rec0[t], rec1 + t, ox, oy, oz);
-            if (r != kReject) emit(t, r);
-        }
-    }
-}
-
-// The candidates of one item (slot s, row) as up to three runs of slots, one
-// per cell of the row: beg[k], num[k] for the cell at dx = dx0 + k, bit k of
-// self set when that cell is the own cell under a periodic image offset
-// (t != s).  Cells beyond the particle's reach are left empty.
+// The candidates of one item (slot s, row): up to three runs of slots,
+// beg[k], num[k], run k holding x cells of the image at (k - 1) L_x; the
+// offset of candidate t in x is (cell_x(t) + xb + k nx) cs_x.  Runs beyond
+// the particle's reach are empty.
 struct Runs {
     int beg[3], num[3];
-    int dx0, self;
+    int xb, nx;
     float oy, oz;
 };
 
@@ -285,10 +252,11 @@ __device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const in
     Runs R;
     R.beg[0] = R.beg[1] = R.beg[2] = 0;
     R.num[0] = R.num[1] = R.num[2] = 0;
-    R.self = 0;
+    const int nx = G.nc[0];
+    R.nx = nx;
+    R.xb = -nx - cx;
     const int dz = row >= 2 ? 1 : 0;
     const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-    R.dx0 = row == 0 ? 0 : -1;
     R.oy = dy * G.cs[1];
     R.oz = dz * G.cs[2];
     int yc = cy + dy, zc = cz + dz;
@@ -300,33 +268,36 @@ __device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const in
         if (!D.periodic[2]) return R;
         zc += zc < 0 ? G.nc[2] : -G.nc[2];
     }
-    const int own = cbase + (cz * G.nc[1] + cy) * G.nc[0] + cx;
-    const int rowbase = cbase + (zc * G.nc[1] + yc) * G.nc[0];
-    // skip neighbour cells no partner of particle s can reach: distance from
-    // the particle to the cell's box against Rmax_s + Rmax + Delta_L
+    const int rowbase = cbase + (zc * G.nc[1] + yc) * nx;
+    // the window: partners of s lie within reach = Rmax_s + Rmax + Delta_L
+    // (+ margin); dyz is the distance from the particle to the row's cells
     const float reach = a0.w + G.rmax + G.cutoff + G.margin;
-    const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2], hx = 0.5f * G.cs[0];
+    const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2];
     const float ey = dy == 0 ? 0.f : fmaxf(fabsf(R.oy - a0.y) - hy, 0.f);
     const float ez = dz == 0 ? 0.f : fmaxf(fabsf(R.oz - a0.z) - hz, 0.f);
     const float r2yz = ey * ey + ez * ez;
     if (r2yz > reach * reach) return R;
+    const float w = sqrtf(reach * reach - r2yz);
+    const float inv = 1.0f / G.cs[0];
+    int lo = row == 0 ? cx : cx + (int)floorf((a0.x - w) * inv + 0.5f);
+    int hi = cx + (int)floorf((a0.x + w) * inv + 0.5f);
+    if (row == 0 && hi < cx) hi = cx;
+    if (!D.periodic[0]) {
+        lo = min(max(lo, 0), nx - 1);
+        hi = min(max(hi, 0), nx - 1);
+    } else {
+        lo = max(lo, -nx);
+        hi = min(hi, 2 * nx - 1);
+    }
+    // run k: the unwrapped cells [max(lo, (k-1) nx), min(hi, k nx - 1)]
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int dx = R.dx0 + k;
-        if (dx > 1) continue;
-        int xc = cx + dx;
-        if (xc < 0 || xc >= G.nc[0]) {
-            if (!D.periodic[0]) continue;
-            xc += xc < 0 ? G.nc[0] : -G.nc[0];
-        }
-        const float ex = dx == 0 ? 0.f : fmaxf(fabsf(dx * G.cs[0] - a0.x) - hx, 0.f);
-        if (ex * ex + r2yz > reach * reach) continue;
-        const int c2 = rowbase + xc;
-        const bool zero_offset = dx == 0 && dy == 0 && dz == 0;
-        if (!zero_offset && c2 == own) R.self |= 1 << k;
-        const int e = cell_start[c2 + 1];
-        R.beg[k] = zero_offset ? s + 1 : cell_start[c2];
-        R.num[k] = e > R.beg[k] ? e - R.beg[k] : 0;
+        const int a = max(lo, (k - 1) * nx), b = min(hi, k * nx - 1);
+        if (a > b) continue;
+        const int e = cell_start[rowbase + b - (k - 1) * nx + 1];
+        const int g = (row == 0 && k == 1) ? s + 1 : cell_start[rowbase + a - (k - 1) * nx];
+        R.beg[k] = g;
+        R.num[k] = e > g ? e - g : 0;
     }
     return R;
 }
@@ -334,7 +305,7 @@ __device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const in
 // an item's data for the lanes that test its candidates (one per thread)
 struct ItemSlot {
     float4 a0, a1;
-    int s, beg0, beg1, beg2, num0, num1, dx0self;
+    int s, beg0, beg1, beg2, num0, num1, xb, nx;
     float cs0, oy, oz;
 };
 
@@ -370,8 +341,8 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
 // the list fill up (more than its capacity of borderline candidates in one
 // build), the extra ones are kept as pairs (a gap within the margin of the
 // list cut-off, where every element of K~ is zero) and flag bit 8 is set.
-template <bool ENS, bool FLAT>
-__global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
+template <bool ENS>
+__global__ void __launch_bounds__(256, 6) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
                                                      const __grid_constant__ Grid G0, Ens E,
                                                      const EnsGrid *__restrict__ EG,
                                                      const int32_t *__restrict__ cell_start,
@@ -390,7 +361,7 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
     pdl_wait();
     pdl_trigger();
     const int N = P.n;
-    __shared__ ItemSlot items[FLAT ? 256 : 1];
+    __shared__ ItemSlot items[256];
     const int lane = threadIdx.x & 31;
     // one candidate that passed (or is undecided by) the FP32 tests
     auto decide = [&](int s, int t, int r) {
@@ -418,14 +389,9 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
         const float4 a0 = rec0[s];
         const int cc = cellc[s];
         const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
-        if (!FLAT) {
-            // sparse suspensions (a few candidates per item): the thread walks its row
-            sweep_row(D, G, cell_start, rec0, rec1, s, a0, rec1[s], cx, cy, cz, row, base,
-                      [&](int t, int r) { decide(s, t, r); });
-        } else {
         const Runs R = row_runs(D, G, cell_start, s, a0, cx, cy, cz, row, base);
         total = R.num[0] + R.num[1] + R.num[2];
-        ItemSlot &it = items[FLAT ? threadIdx.x : 0];
+        ItemSlot &it = items[threadIdx.x];
         it.a0 = a0;
         it.a1 = rec1[s];
         it.s = s;
@@ -434,11 +400,11 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
         it.beg2 = R.beg[2];
         it.num0 = R.num[0];
         it.num1 = R.num[1];
-        it.dx0self = (R.dx0 + 1) | (R.self << 2);
+        it.xb = R.xb;
+        it.nx = R.nx;
         it.cs0 = G.cs[0];
         it.oy = R.oy;
         it.oz = R.oz;
-        }
         if (row == 0) {
             // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
             // records (one double subtraction for z - z_w), decided in FP64 only
@@ -471,8 +437,13 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
     // to the item of the first lane whose incl exceeds it.  A thread walking
     // its own item's candidates would leave most of its warp idle (the runs
     // differ in length from item to item), and the lanes read the runs'
-    // records coalesced.
-    if (FLAT) {
+    // records coalesced.  The few candidates that pass the bounding-sphere
+    // test (about one in eight) queue up in shared memory and take the rest
+    // of the test and the store 32 at a time, with every lane busy.
+    {
+    __shared__ float4 qd[8][64];   // d (x, y, z) and Rmax of the candidate
+    __shared__ int qt[8][64];      // candidate slot t
+    __shared__ uint8_t qo[8][64];  // lane of its item
     int incl = total;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -480,7 +451,18 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
         if (lane >= o) incl += y;
     }
     const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    const int wbase = threadIdx.x & ~31;
+    const int wbase = threadIdx.x & ~31, wq = threadIdx.x >> 5;
+    // the full test and the store of queue entry e
+    auto drain = [&](int e) {
+        const float4 d = qd[wq][e];
+        const int t = qt[wq][e];
+        const ItemSlot &it = items[wbase + qo[wq][e]];
+        const int s = it.s;
+        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[s] : 0);
+        const int r = pair_decide(G, it.a0, it.a1, d.w, rec1[t], d.x, d.y, d.z);
+        if (r != kReject) decide(s, t, r);
+    };
+    int qn = 0;
     __syncwarp();
     for (int r0 = 0; r0 < wtotal; r0 += 32) {
         const int q = r0 + lane;
@@ -491,18 +473,45 @@ __global__ void __launch_bounds__(256, FLAT ? 4 : 5) k_pairs_sweep(PView P, cons
             if (v <= q) o += step;
         }
         const int first = __shfl_sync(0xffffffffu, incl - total, o & 31);
-        if (q >= wtotal) continue;
-        const ItemSlot &it = items[wbase + o];
-        const int u = q - first;
-        const int k = u < it.num0 ? 0 : (u < it.num0 + it.num1 ? 1 : 2);
-        const int t = k == 0 ? it.beg0 + u : (k == 1 ? it.beg1 + u - it.num0 : it.beg2 + u - it.num0 - it.num1);
-        const int s = it.s;
-        if (((it.dx0self >> (2 + k)) & 1) && t == s) continue;
-        const float ox = (float)((it.dx0self & 3) - 1 + k) * it.cs0;
-        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[s] : 0);
-        const int r = pair_test(G, it.a0, it.a1, rec0[t], rec1 + t, ox, it.oy, it.oz);
-        if (r != kReject) decide(s, t, r);
+        bool pass = false;
+        float4 d;
+        int t = 0;
+        if (q < wtotal) {
+            const ItemSlot &it = items[wbase + o];
+            const int u = q - first;
+            const int k = u < it.num0 ? 0 : (u < it.num0 + it.num1 ? 1 : 2);
+            t = k == 0 ? it.beg0 + u : (k == 1 ? it.beg1 + u - it.num0 : it.beg2 + u - it.num0 - it.num1);
+            if (t != it.s) {
+                const float ox = (float)((cellc[t] & 1023) + it.xb + k * it.nx) * it.cs0;
+                const float4 b0 = rec0[t];
+                d = make_float4(b0.x - it.a0.x + ox, b0.y - it.a0.y + it.oy, b0.z - it.a0.z + it.oz, b0.w);
+                const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[it.s] : 0);
+                pass = pair_near(G, it.a0.w, b0.w, d.x * d.x + d.y * d.y + d.z * d.z);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+            const int e = qn + __popc(m & ((1u << lane) - 1u));
+            qd[wq][e] = d;
+            qt[wq][e] = t;
+            qo[wq][e] = (uint8_t)o;
+        }
+        qn += __popc(m);
+        if (qn >= 32) {
+            __syncwarp();
+            drain(lane);
+            __syncwarp();
+            if (lane < qn - 32) {
+                qd[wq][lane] = qd[wq][32 + lane];
+                qt[wq][lane] = qt[wq][32 + lane];
+                qo[wq][lane] = qo[wq][32 + lane];
+            }
+            qn -= 32;
+            __syncwarp();
+        }
     }
+    __syncwarp();
+    if (lane < qn) drain(lane);
     }
     // the last block to finish decides the listed candidates in FP64
     __shared__ int last;
@@ -642,6 +651,13 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
             G.nc[a] = nc < 1 ? 1 : nc;
         }
     }
+    // fine x cells within the same limits (at most 1024 per axis: the packed
+    // cell coordinates of the sweep hold 10 bits each)
+    const int64_t ncoarse = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
+    int xs = kXSub;
+    while (xs > 1 && ((int64_t)G.nc[0] * xs > 1024 || ncoarse * xs > limit)) --xs;
+    G.xsub = xs;
+    G.nc[0] *= xs;
     for (int a = 0; a < 3; ++a) {
         G.csd[a] = D.L[a] / G.nc[a];
         G.cs[a] = (float)G.csd[a];
@@ -743,15 +759,10 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted,
                    L.rec0, L.rec1, L.cellc, L.sbat, L.cnt, scan_state, z2);
     if ((rc = lub_check_cuda(ctx, e, "cells fill launch"))) return rc;
-    // one item per thread (no grid-stride loop); the warps share out their
-    // items' candidates when a row holds more than a few (three cells of
-    // N / ncell particles each; measured: 1.66 per cell walks faster, 4.8 and
-    // 10 share out faster)
+    // one item per thread (no grid-stride loop)
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
     sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
-    const bool flat = (double)N >= 2.0 * (double)(G.ncell > 0 ? G.ncell : 1);
-    e = launch_pdl(flat ? k_pairs_sweep<ENS, true> : k_pairs_sweep<ENS, false>, sw.grid, sw.block, 0, st, P, D, G, E,
-                   EG, (const int32_t *)L.cell_cnt, (const int32_t *)L.sorted, (const float4 *)L.rec0,
+    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, P, D, G, E, EG, (const int32_t *)L.cell_cnt, (const int32_t *)L.sorted, (const float4 *)L.rec0,
                    (const float4 *)L.rec1, (const int32_t *)L.cellc, (const int32_t *)L.sbat, L.cnt, L.slots, L.wbits,
                    L.totals + 2, cap, pi, pj, (double)prm.list_cutoff, L.und, L.totals + 3, L.und_cap,
                    (unsigned *)(L.totals + 4), L.flags);
