@@ -48,6 +48,11 @@ APPLY_BYTES_PER_PARTICLE = 24.0   # force + torque written
 TRAFFIC_PAIRS_BUILD_32K = 7.1457e6
 
 
+FORM_NAMES = {"fused": "pair build + fused pass (lub_correct)",
+              "merged": "pair build + closest points + resistance with scatter (lub_resistance_apply)",
+              "calls": "pair build + closest points + resistance + apply"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -68,9 +73,13 @@ def parse():
     ap.add_argument("--ens-n", type=int, default=256, help="suspensions in the ensemble workload")
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-large", action="store_true", help="skip the large wall-bounded run")
+    ap.add_argument("--large-form", default="merged", choices=["calls", "merged", "fused"])
+    ap.add_argument("--ens-form", default="merged", choices=["calls", "merged", "fused"])
     ap.add_argument("--large-n", type=int, default=1 << 20)
     ap.add_argument("--large-steps", type=int, default=1000)
     ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--only", default=None, choices=["step", "large", "ensemble", "learned"],
+                    help="run only that workload and print its results (for profiling; no bench line)")
     ap.add_argument("--fp64-switch", type=float, default=1e-3,
                     help="h/a below which pairs get the FP64 Newton refinement (0: none)")
     return ap.parse_args()
@@ -193,6 +202,16 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    if args.only:
+        stream = torch.cuda.Stream(device=dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        leg = {"step": lambda: eager_steps(args, dev, stream),
+               "large": lambda: large_bench(args, dev, stream, flush, ws, rank),
+               "ensemble": lambda: ensemble_bench(args, dev, stream, flush, ws, rank),
+               "learned": lambda: learned_vs_plain(args, dev, stream, flush)}[args.only]()
+        if rank == 0:
+            print(json.dumps({"only": args.only, args.only: leg}))
+        return
     parts, dom = make_workload(args.n, rank_seed(rank))
     prm = lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch)
     pl = lub.Pipeline(parts, dom, prm, device=dev)
@@ -517,6 +536,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def eager_steps(args, dev, stream):
+    """The main workload's step, args.steps times, eagerly on one stream (no
+    tuning, no graph): a short, fixed launch sequence for a profiler."""
+    import torch
+
+    import paper_1308_6482_gb300 as lub
+
+    parts, dom = make_workload(args.n, rank_seed(0))
+    prm = lub.default_params(precision=args.precision, fp64_switch=args.fp64_switch)
+    pl = lub.Pipeline(parts, dom, prm, device=dev)
+    npairs = pl.build_pairs()
+    pl._alloc(int(npairs * 1.1) + 1024, dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            pl.step(form=args.form, stream=stream)
+    stream.synchronize()
+    return {"pairs": int(npairs), "steps": args.steps, "form": args.form}
+
+
 def learned_vs_plain(args, dev, stream, flush, steps=20, warmup=3):
     """Learned warm start against the plain (line-of-centres) start on fresh
     spheroid pairs: aspect ratios log-uniform in [1/3, 3], gaps log-uniform in
@@ -646,12 +684,12 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
         with torch.cuda.stream(stream):
             if tune:
                 pl.autotune(reps=2, stream=stream)
-            pl.step(fused=True, stream=stream)
-            pl.step(fused=True, stream=stream)
+            pl.step(form=args.ens_form, stream=stream)
+            pl.step(form=args.ens_form, stream=stream)
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            pl.step(fused=True, stream=stream)
+            pl.step(form=args.ens_form, stream=stream)
         stream.synchronize()
         g = torch.Generator(device=dev)
         g.manual_seed(12345)
@@ -701,12 +739,12 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for q in sep:
-            q.step(fused=True, stream=stream)
+            q.step(form=args.ens_form, stream=stream)
         flush.zero_()
         e0.record(stream)
         for _ in range(Ks):
             for q in sep:
-                q.step(fused=True, stream=stream)
+                q.step(form=args.ens_form, stream=stream)
         e1.record(stream)
     stream.synchronize()
     sep_ms = e0.elapsed_time(e1) / Ks
@@ -721,8 +759,8 @@ def ensemble_bench(args, dev, stream, flush, ws=1, rank=0):
         "precision": "mixed", "pairs_per_step_mean": all_pairs, "ms_per_step": step_ms,
         "pairs_per_s": all_pairs / (step_ms * 1e-3), "newton_iters_per_pair": it_plain,
         "capacity_overflows": over, "ranks": ws,
-        "launch": "one CUDA graph per step (pair build + fused pass), one persistent launch per stage for all "
-                  "suspensions",
+        "launch": "one CUDA graph per step (%s), one persistent launch per stage for all suspensions"
+                  % FORM_NAMES[args.ens_form],
         "autotuned_shapes": {lub.TUNE_NAMES[q]: list(v) for q, v in enumerate(shapes)},
         "autotune_and_run_s": t_run, "generation_s": t_gen,
         "warm_starts": warm_forms,
@@ -762,12 +800,12 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
         pl._alloc(int(npairs * 1.3) + 4096, dev)
         pl.build_pairs()
         with torch.cuda.stream(stream):
-            pl.step(stream=stream)
-            pl.step(stream=stream)
+            pl.step(form=args.large_form, stream=stream)
+            pl.step(form=args.large_form, stream=stream)
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            pl.step(stream=stream)
+            pl.step(form=args.large_form, stream=stream)
         stream.synchronize()
         g = torch.Generator(device=dev)
         g.manual_seed(777)
@@ -795,7 +833,8 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
     out = {"workload": "%d spheroids, aspect ratio log-uniform [1/3,3], phi=0.5 (growth packing), cube %.0f^3 periodic in x,y "
                        "between walls at z=0 and z=L; %d steps of seeded rigid motions"
                        % (len(parts["x"]), dom["L"][0], args.large_steps),
-           "precision": "mixed", "pairs_per_step_mean": pairs, "wall_pairs_last_step": walls,
+           "precision": "mixed", "form": FORM_NAMES[args.large_form],
+           "pairs_per_step_mean": pairs, "wall_pairs_last_step": walls,
            "ms_per_step": step_ms, "pairs_per_s": pairs / (step_ms * 1e-3), "capacity_overflows": over,
            "generation_s": t_gen, "warm_starts": {}}
     for name, warm in (("learned", lub.LUB_WARM_MLP), ("temporal", lub.LUB_WARM_PREVIOUS)):

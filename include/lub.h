@@ -460,7 +460,8 @@ int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, cons
 #define LUB_TUNE_CLOSEST_FP64 2    /* lub_closest_points, LUB_FP64 */
 #define LUB_TUNE_RESISTANCE 3      /* lub_resistance */
 #define LUB_TUNE_APPLY 4           /* lub_apply, atomic form */
-#define LUB_TUNE_SWEEP 5           /* lub_pairs_build, the two cell sweeps */
+#define LUB_TUNE_SWEEP 5           /* lub_pairs_build, the cell sweep (one thread per
+                                      item: only the block counts, the grid follows) */
 #define LUB_TUNE_COUNT 6
 
 /* Time every candidate shape of the kernels a step with these arguments runs

@@ -107,6 +107,8 @@ int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, co
         for (int block : blocks_of(id)) {
             for (int per_sm : kBlocksPerSm) {
                 if (block * per_sm > 32768) continue;  // 16 waves of resident threads: as good as any larger grid
+                // the sweep runs one thread per item: its grid follows from the block
+                if (id == LUB_TUNE_SWEEP && per_sm != kBlocksPerSm[0]) continue;
                 ctx->tune_block[id] = block;
                 ctx->tune_per_sm[id] = per_sm;
                 if ((rc = run(id))) break;  // warm-up
