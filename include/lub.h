@@ -57,8 +57,11 @@ extern "C" {
 
 /* lub_params.precision */
 #define LUB_FP64  0 /* every step in double precision */
-#define LUB_MIXED 1 /* FP32 Newton, curvature, K~ and sums; FP64 gap always,
-                       FP64 Newton refinement when h/a < fp64_switch */
+#define LUB_MIXED 1 /* FP32 Newton, curvature, K~ and sums; the gap in
+                       float-float (~48 bits) always; when h/a < fp64_switch
+                       one float-float Newton step refines the normal, and a
+                       pair whose FP32 Newton did not converge is solved in
+                       FP64 */
 
 /* lub_params.warm_start */
 #define LUB_WARM_NONE     0 /* Newton starts from the line of centres (Sec. III A) */
@@ -72,7 +75,9 @@ extern "C" {
 #define LUB_ST_OVERLAP    1  /* h <= 0 */
 #define LUB_ST_NOCONV     2  /* Newton did not converge within max_newton */
 #define LUB_ST_DEGENERATE 4  /* bad index, non-positive or non-finite shape, coincident centres */
-#define LUB_ST_FP64       8  /* mixed mode: refined by FP64 Newton (h/a < fp64_switch) */
+#define LUB_ST_FP64       8  /* mixed mode: refined beyond FP32 (h/a < fp64_switch:
+                                 float-float Newton step; FP32 not converged:
+                                 FP64 solve) */
 
 typedef struct lub_ctx lub_ctx;
 
@@ -116,13 +121,13 @@ typedef struct {
     double eps_c;         /* stiffness of the Hookean repulsion, Eq. lub:frep         */
     double list_cutoff;   /* Delta_L: pairs with a possible gap below this are listed */
     int32_t precision;    /* LUB_FP64 or LUB_MIXED                                     */
-    double fp64_switch;   /* mixed mode: h/a below which Newton is refined in FP64;
-                             a = smallest semi-axis of the pair                        */
+    double fp64_switch;   /* mixed mode: h/a below which Newton is refined beyond
+                             FP32; a = smallest semi-axis of the pair              */
     int32_t max_newton;   /* Newton iteration cap per precision stage (1..64)          */
     double newton_tol;    /* step-size tolerance (radians) of the FP32 stage: Newton
                              stops after a step shorter than this (quadratic
-                             convergence leaves an error of order tol^2); the FP64
-                             stage stops after a step below 1e-7 rad              */
+                             convergence leaves an error of order tol^2); an FP64
+                             solve stops after a step below 1e-7 rad              */
     int32_t warm_start;   /* LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP          */
     int32_t model;        /* LUB_MODEL_FULL: all 16 elements of K~; LUB_MODEL_NORMAL:
                              the normal element K~33 alone ("normal only" of Sec.

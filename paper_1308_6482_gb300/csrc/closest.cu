@@ -275,75 +275,116 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
     return entry;
 }
 
-// One FP64 Newton step of g on the sphere from a normal n accurate to FP32
-// (|dn| ~ 1e-7): the gradient in FP64, the tangent Hessian and the 2x2 solve
-// in FP32.  An approximate Hessian of relative error e makes the step
-// contract the error by a factor e as well, so from 1e-7 one step lands at
-// the FP64 rounding level with a fraction of the FP64 operations of a full
-// FP64 step.  Returns the step length (radians).
-__device__ __forceinline__ double polish_step(const Shape<double> &si, const Shape<double> &sj, const V3<double> &d,
-                                              V3<double> &n)
+// One Newton step of g from the FP32 normal n of a work-list pair, in
+// float-float on the FP32 pipe (about 48 bits; this GPU runs FP64 at 1/64 of
+// the FP32 rate).  It works on the homogeneous g(m) = m.d - sigma_i(m) -
+// sigma_j(m), sigma(m) = sqrt(a2 |m|^2 + e (o.m)^2), at m = n itself (an exact
+// float vector, |n|^2 = 1 + O(1e-7)), with
+//   t.grad sigma = (a2 (t.n) + e (o.n)(o.t)) / sigma.
+// The tangents t1, t2 (FP32) are orthogonal to n to about 1e-7 only, so the
+// gradient is projected: G_a = t_a.grad g - (t_a.n) g / |n|^2 (n.grad g = g by
+// Euler's theorem), which vanishes exactly at the stationary point.  G to
+// about 1e-14 absolute; the tangent Hessian and the 2x2 solve in FP32, whose
+// relative error e makes the step contract the error by e as well, so from
+// 1e-7 one step lands near 1e-14.  The refined unit normal goes to n64.
+// Returns the step length (radians), or infinity when the normal does not
+// point from i towards j.
+__device__ __forceinline__ float polish_ff(const PView &P, const float2 *__restrict__ pff, const DView &D, int i,
+                                           int j, const V3<float> n, V3<double> &n64)
 {
-    n = normalized(n);
-    const V3<double> t1 = perp_unit(n), t2 = cross(n, t1);
-    const double ci = dot(si.o, n), u1i = dot(si.o, t1), u2i = dot(si.o, t2);
-    const double cj = dot(sj.o, n), u1j = dot(sj.o, t1), u2j = dot(sj.o, t2);
-    const double qi = si.a2 + si.e * ci * ci, qj = sj.a2 + sj.e * cj * cj;
-    const double ri = rsqrt64(qi), rj = rsqrt64(qj);
-    const double ki = si.e * ci * ri, kj = sj.e * cj * rj;
-    const double g1 = dot(t1, d) - ki * u1i - kj * u1j;
-    const double g2 = dot(t2, d) - ki * u2i - kj * u2j;
-    // P = -Hess_t g in FP32
-    const float g = (float)(dot(n, d) - qi * ri - qj * rj);
-    const float rif = (float)ri, rjf = (float)rj;
-    const float Ai = (float)si.a2 * rif, Aj = (float)sj.a2 * rjf;
-    const float Ei = (float)si.e * rif * rif, Ej = (float)sj.e * rjf * rjf;
-    const float a1 = (float)u1i, a2 = (float)u2i, b1 = (float)u1j, b2 = (float)u2j;
-    const float P11 = Ai * (1.f + Ei * a1 * a1) + Aj * (1.f + Ej * b1 * b1) + g;
-    const float P22 = Ai * (1.f + Ei * a2 * a2) + Aj * (1.f + Ej * b2 * b2) + g;
-    const float P12 = Ai * Ei * a1 * a2 + Aj * Ej * b1 * b2;
+    ff d[3], oi[3], oj[3];
+    ff_separation(pff, (size_t)P.n, i, j, D, d);
+    ff_axis(__ldg(P.qw + i), __ldg(P.qx + i), __ldg(P.qy + i), __ldg(P.qz + i), oi);
+    ff_axis(__ldg(P.qw + j), __ldg(P.qx + j), __ldg(P.qy + j), __ldg(P.qz + j), oj);
+    const float api = __ldg(P.rperp + i), cpi = __ldg(P.rpar + i);
+    const float apj = __ldg(P.rperp + j), cpj = __ldg(P.rpar + j);
+    const ff a2i = two_prod(api, api), ei = ff_sub(two_prod(cpi, cpi), a2i);
+    const ff a2j = two_prod(apj, apj), ej = ff_sub(two_prod(cpj, cpj), a2j);
+    const float nv[3] = {n.x, n.y, n.z};
+    const ff nn = ff_dot3_exact(nv, nv);
+    const ff ci = ff_dot3f(oi, nv), cj = ff_dot3f(oj, nv);
+    const ff si = ff_sqrt(ff_add(ff_mul(a2i, nn), ff_mul(ei, ff_mul(ci, ci))));
+    const ff sj = ff_sqrt(ff_add(ff_mul(a2j, nn), ff_mul(ej, ff_mul(cj, cj))));
+    const ff ri = ff_rcp(si), rj = ff_rcp(sj);
+    const ff g = ff_sub(ff_sub(ff_dot3f(d, nv), si), sj);
+    const float lam = __fdiv_rn(g.hi, nn.hi);
+    const V3<float> t1 = perp_unit(n), t2 = cross(n, t1);
+    const float tv1[3] = {t1.x, t1.y, t1.z}, tv2[3] = {t2.x, t2.y, t2.z};
+    // projected tangential gradient along t, and o_i.t, o_j.t in FP32 for the Hessian
+    auto grad_t = [&](const float tv[3], float &uti, float &utj) -> float {
+        const ff tn = ff_dot3_exact(tv, nv);
+        const ff toi = ff_dot3f(oi, tv), toj = ff_dot3f(oj, tv);
+        uti = toi.hi;
+        utj = toj.hi;
+        const ff gi = ff_mul(ff_add(ff_mul(a2i, tn), ff_mul(ei, ff_mul(ci, toi))), ri);
+        const ff gj = ff_mul(ff_add(ff_mul(a2j, tn), ff_mul(ej, ff_mul(cj, toj))), rj);
+        const ff G = ff_sub(ff_sub(ff_dot3f(d, tv), gi), gj);
+        return __fadd_rn(__fsub_rn(G.hi, __fmul_rn(tn.hi, lam)), G.lo);
+    };
+    float u1i, u1j, u2i, u2j;
+    const float G1 = grad_t(tv1, u1i, u1j), G2 = grad_t(tv2, u2i, u2j);
+    // P = -Hess_t g in FP32 (as in newton_sphere)
+    const float rif = ri.hi, rjf = rj.hi;
+    const float Ai = a2i.hi * rif, Aj = a2j.hi * rjf;
+    const float Ei = ei.hi * rif * rif, Ej = ej.hi * rjf * rjf;
+    const float P11 = Ai * (1.f + Ei * u1i * u1i) + Aj * (1.f + Ej * u1j * u1j) + g.hi;
+    const float P22 = Ai * (1.f + Ei * u2i * u2i) + Aj * (1.f + Ej * u2j * u2j) + g.hi;
+    const float P12 = Ai * Ei * u1i * u2i + Aj * Ej * u1j * u2j;
     const float det = P11 * P22 - P12 * P12;
-    double s1, s2;
+    float s1, s2;
     if (P11 > 0.f && det > 0.f) {
         const float idet = 1.0f / det;
-        s1 = ((double)P22 * g1 - (double)P12 * g2) * (double)idet;
-        s2 = ((double)P11 * g2 - (double)P12 * g1) * (double)idet;
+        s1 = (P22 * G1 - P12 * G2) * idet;
+        s2 = (P11 * G2 - P12 * G1) * idet;
     } else {
-        const double sc = 1.0 / (double)(fabsf(P11) + fabsf(P22) + fabsf(P12) + Ai + Aj);
-        s1 = g1 * sc;
-        s2 = g2 * sc;
+        const float sc = 1.0f / (fabsf(P11) + fabsf(P22) + fabsf(P12) + Ai + Aj);
+        s1 = G1 * sc;
+        s2 = G2 * sc;
     }
-    n = normalized(axpy(s1, t1, axpy(s2, t2, n)));
-    return sqrt(s1 * s1 + s2 * s2);
+    // n + s1 t1 + s2 t2 in float-float (the step is of order 1e-7), normalised
+    ff m[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m[a] = two_sum(nv[a], __fmaf_rn(s1, tv1[a], __fmul_rn(s2, tv2[a])));
+    const ff m2 = ff_add(ff_add(ff_mul(m[0], m[0]), ff_mul(m[1], m[1])), ff_mul(m[2], m[2]));
+    const ff im = ff_rcp(ff_sqrt(m2));
+    n64 = mk<double>(ff_to_double(ff_mul(m[0], im)), ff_to_double(ff_mul(m[1], im)), ff_to_double(ff_mul(m[2], im)));
+    const float step = sqrtf(s1 * s1 + s2 * s2);
+    const float nd = m[0].hi * d[0].hi + m[1].hi * d[1].hi + m[2].hi * d[2].hi;
+    return (nd > 0.f && isfinite(step)) ? step : INFINITY;
 }
 
-// LUB_MIXED, FP64 refinement of a work-list pair: one polish step from the
-// FP32 normal nstart, or, if full, a complete FP64 solve from the line of
-// centres
+// LUB_MIXED, refinement of a work-list pair: one float-float Newton step from
+// the FP32 normal nn (the gap h_in of the FP32 stage stands: g is stationary
+// in n, so the FP32 normal's error of ~1e-7 rad changes it by ~1e-14 of the
+// sizes), or, if full, a complete FP64 solve and gap from the line of centres
 template <bool ENS>
-__device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, bool full,
-                                           V3<double> nn, int maxit, V3<double> &n64, double &h, int &st, int &nit)
+__device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E,
+                                           const float2 *__restrict__ pff, int i, int j, bool full, V3<double> nn,
+                                           double h_in, int st_in, int maxit, V3<double> &n64, double &h, int &st,
+                                           int &nit)
 {
     bool alien;
     const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+    if (!full) {
+        const V3<float> n32 = mk<float>((float)nn.x, (float)nn.y, (float)nn.z);
+        const bool converged = polish_ff(P, pff, D, i, j, n32, n64) < 1e-5f;
+        nit = 1;
+        h = h_in;
+        st = st_in | LUB_ST_FP64;
+        if (!converged) st |= LUB_ST_NOCONV;
+        return;
+    }
     const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
     const double dl = sqrt(dot(d, d));
     const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
-    bool converged;
-    if (full) {
-        nn = scl(1.0 / dl, d);
-        const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
-        const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
-        converged = o.converged;
-        nit = o.iters;
-    } else {
-        converged = polish_step(si, sj, d, nn) < 1e-5;
-        nit = 1;
-    }
+    nn = scl(1.0 / dl, d);
+    const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
+    const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
+    nit = o.iters;
     n64 = normalized(nn);
     h = dot(n64, d) - support(si, n64) - support(sj, n64);
     st = LUB_ST_FP64;
-    if (!converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
+    if (!o.converged || !(dot(n64, d) > 0.0) || !isfinite(h)) st |= LUB_ST_NOCONV;
     if (h <= 0.0) st |= LUB_ST_OVERLAP;
 }
 
@@ -505,7 +546,8 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
                                                         double *__restrict__ nout, double *__restrict__ gap,
                                                         uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                         int maxit, const int32_t *__restrict__ wl_count,
-                                                        const int32_t *__restrict__ wl)
+                                                        const int32_t *__restrict__ wl,
+                                                        const float2 *__restrict__ pff)
 {
     pdl_wait();
     pdl_trigger();
@@ -518,8 +560,8 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
         V3<double> n64;
         double h;
         int st, nit;
-        refine_one<ENS>(P, D0, E, pi[k], pj[k], full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]), maxit, n64,
-                        h, st, nit);
+        refine_one<ENS>(P, D0, E, pff, pi[k], pj[k], full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]),
+                        full ? 0.0 : gap[k], full ? 0 : status[k], maxit, n64, h, st, nit);
         store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
         if (iters) {
             const int total = (full ? 0 : iters[k]) + nit;
@@ -676,11 +718,9 @@ __device__ __forceinline__ void force_and_scatter(const PView &P, const RParams 
 // The fused pass in mixed precision after the FP32 stage (k_closest_mixed,
 // which leaves every pair's normal, gap and status and marks the work-list
 // pairs with LUB_ST_FP64): warps take 32 items at a time from two queues,
-// the work-list entries (the FP64 refinement, then the pair's force and
-// scatter; the first warp of every block, before anything else), then the
-// other pairs (force and scatter from the stored normal and gap; all warps).  The FP64 chains of the first queue, too few to fill the GPU,
-// run beside the resistance of the second instead of in a launch of their
-// own.  queue: two counters, zero at the launch.
+// the work-list entries (the refinement, then the pair's force and scatter),
+// then the other pairs (force and scatter from the stored normal and gap).
+// queue: two counters, zero at the launch.
 template <bool ENS>
 __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
                                                        const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
@@ -690,17 +730,17 @@ __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_con
                                                        float *__restrict__ FT, float *__restrict__ lever, int maxit,
                                                        const int32_t *__restrict__ wl_count,
                                                        const int32_t *__restrict__ wl, int32_t *__restrict__ queue,
-                                                       float *__restrict__ force, float *__restrict__ torque)
+                                                       float *__restrict__ force, float *__restrict__ torque,
+                                                       const float2 *__restrict__ pff)
 {
     pdl_wait();
     pdl_trigger();
     const int count = pair_count(d_count, cap), nwl = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     const int lane = threadIdx.x & 31;
-    // one warp per block on the first queue, so that its FP64 work spreads
-    // over every SM (the FP64 pipe is the scarce unit) instead of filling the
-    // first blocks to start
-    for (; threadIdx.x < 32;) {
+    // every warp takes work-list entries first (the refinement is FP32-pipe
+    // work), then the other pairs
+    for (;;) {
         int q0 = 0;
         if (lane == 0) q0 = atomicAdd(queue, 32);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
@@ -717,8 +757,8 @@ __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_con
             k = full ? -1 - v : v;
             i = pi[k];
             j = pj[k];
-            refine_one<ENS>(P, D0, E, i, j, full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]), maxit, n64, h,
-                            st, nit);
+            refine_one<ENS>(P, D0, E, pff, i, j, full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]),
+                            full ? 0.0 : gap[k], full ? 0 : status[k], maxit, n64, h, st, nit);
         }
         force_and_scatter<float>(P, R, active, i, j, n64, h, st, FT, lever, C, k, force, torque);
         if (active) {
@@ -856,7 +896,7 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
         (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
-                                                            prm.max_newton, wl_count, wl);
+                         prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl, (const float2 *)pff);
     } else if (fused_mlp) {
         if ((rc = learned_smem(ctx, k_closest_fp64_learned<ENS>, 64 << ENS))) return rc;
         (void)launch_pdl(k_closest_fp64_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E, pi,
@@ -898,7 +938,7 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
         (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
                          iters, (float *)FT, (float *)lever, prm.max_newton, (const int32_t *)wl_count,
-                         (const int32_t *)wl, wl_count + 2, (float *)force, (float *)torque);
+                         (const int32_t *)wl, wl_count + 2, (float *)force, (float *)torque, (const float2 *)pff);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
         (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,

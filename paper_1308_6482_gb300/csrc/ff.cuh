@@ -101,6 +101,27 @@ __device__ __forceinline__ ff ff_sqrt(ff x)
     return fast_two_sum(s, r);
 }
 
+// reciprocal: r = 1 / hi, one Newton correction r (1 - x r) with the
+// residual 1 - x r formed in float-float
+__device__ __forceinline__ ff ff_rcp(ff x)
+{
+    const float r = __fdiv_rn(1.0f, x.hi);
+    const ff e = ff_sub(ff_make(1.0f), ff_mulf(x, r));
+    return fast_two_sum(r, __fmul_rn(r, e.hi));
+}
+
+// a . b for a float-float vector a and a float vector b
+__device__ __forceinline__ ff ff_dot3f(const ff a[3], const float b[3])
+{
+    return ff_add(ff_add(ff_mulf(a[0], b[0]), ff_mulf(a[1], b[1])), ff_mulf(a[2], b[2]));
+}
+
+// a . b of two float vectors, the products exact
+__device__ __forceinline__ ff ff_dot3_exact(const float a[3], const float b[3])
+{
+    return ff_add(ff_add(two_prod(a[0], b[0]), two_prod(a[1], b[1])), two_prod(a[2], b[2]));
+}
+
 __device__ __forceinline__ ff ff_from_double(double d)
 {
     const float hi = __double2float_rn(d);
