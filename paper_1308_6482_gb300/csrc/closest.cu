@@ -153,14 +153,13 @@ __device__ __forceinline__ ff ff_support(const PView &P, int k, const float n[3]
 
 // g at the unit vector n/|n|, in float-float: g is homogeneous of degree one,
 // so g(n/|n|) = g(n) / |n| = g(n) (1 - (|n|^2 - 1)/2 + ...), |n|^2 - 1 ~ 1e-7
-__device__ __forceinline__ double ff_gap(const PView &P, int i, int j, const ff d[3], const float n[3])
+__device__ __forceinline__ ff ff_gap(const PView &P, int i, int j, const ff d[3], const float n[3])
 {
     const ff nn = ff_add(ff_add(two_prod(n[0], n[0]), two_prod(n[1], n[1])), two_prod(n[2], n[2]));
     const ff nd = ff_add(ff_add(ff_mulf(d[0], n[0]), ff_mulf(d[1], n[1])), ff_mulf(d[2], n[2]));
     const ff G = ff_sub(ff_sub(nd, ff_support(P, i, n, nn)), ff_support(P, j, n, nn));
     const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);
-    const ff h = ff_sub(G, ff_make(__fmul_rn(G.hi, __fmul_rn(0.5f, eps))));
-    return ff_to_double(h);
+    return ff_sub(G, ff_make(__fmul_rn(G.hi, __fmul_rn(0.5f, eps))));
 }
 
 // Minimum-image separation r_j - r_i in float-float from the particles'
@@ -256,15 +255,17 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
             nit = o.iters;
             const float nv[3] = {n.x, n.y, n.z};
-            h = ff_gap(P, i, j, dff, nv);
+            const ff hff = ff_gap(P, i, j, dff, nv);
+            h = ff_to_double(hff);
             // unit normal for the output (|n|^2 - 1 ~ 1e-7)
             const float nn = dot(n, n);
             const float f = 1.5f - 0.5f * nn;
             n64 = mk<double>(n.x * f, n.y * f, n.z * f);
             const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
-            if (!o.converged || !isfinite(h))
+            // (the switch compared in FP32: a heuristic threshold, no FP64 pipe)
+            if (!o.converged || !isfinite(hff.hi))
                 entry = -1 - k;
-            else if (h < (double)fp64_switch * (double)amin)
+            else if (hff.hi < fp64_switch * amin)
                 entry = k;
             if (entry != kNoEntry) st |= LUB_ST_FP64;  // on the FP64 work list (refined next)
             // consistency check of Sec. III A: the normals point to the other centre
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(256) k_pos_ff(PView P, float2 *__restrict__ ou
 }
 
 template <bool ENS>
-__global__ void __launch_bounds__(128) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
+__global__ void __launch_bounds__(128, 6) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
                                                        const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
                                                        const int32_t *__restrict__ d_count, int32_t cap,
                                                        double *__restrict__ nout, double *__restrict__ gap,

@@ -98,22 +98,48 @@ __device__ __forceinline__ int cell_axis(double xw, double inv_cs, int nc)
     return (int)f;
 }
 
+// Everything the pair build's kernels read and write, passed by value as one
+// __grid_constant__ kernel parameter: the particles, the domain and grid (of
+// the single suspension; the ensemble tables through E and EG), the
+// workspace and the caller's outputs.
+struct BuildView {
+    PView P;
+    DView D;
+    Grid G;
+    Ens E;
+    const EnsGrid *EG;
+    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
+    uint8_t *wbits;
+    int2 *und;
+    float4 *rec0, *rec1;
+    unsigned long long *scan_state;
+    int64_t z1, z2;  // state words of the cell scan and of the pair-count scan
+    double cutoff_d;
+    int32_t *pair_i, *pair_j, *d_count, *flags_out;
+    float rmax_bound;
+    int32_t und_cap, cap;
+};
+
 template <bool ENS>
-__global__ void k_cells_count(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
-                              int32_t *__restrict__ cell_cnt, int32_t *__restrict__ cell_of,
-                              int32_t *__restrict__ slot, float rmax_bound, int32_t *__restrict__ flags,
-                              unsigned long long *__restrict__ zero, int64_t nzero)
+__device__ __forceinline__ void cells_count(const BuildView &V)
 {
-    pdl_wait();
-    pdl_trigger();
+    const PView &P = V.P;
+    const Ens &E = V.E;
+    int32_t *__restrict__ cell_cnt = V.cell_cnt;
+    int32_t *__restrict__ cell_of = V.cell_of;
+    int32_t *__restrict__ slot = V.slot;
+    int32_t *__restrict__ flags = V.flags;
+    unsigned long long *__restrict__ zero = V.scan_state;
+    const int64_t nzero = V.z1;
+    const float rmax_bound = V.rmax_bound;
     // state of the cell scan, which runs next
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nzero; k += (int64_t)gridDim.x * blockDim.x)
         zero[k] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int b = ENS ? batch_of(E, i) : 0;
-        const Grid &G = grid_ref<ENS>(G0, EG, b);
-        const DView &D = dom_ref<ENS>(D0, E, b);
-        const int base = cell_base<ENS>(EG, b);
+        const Grid &G = grid_ref<ENS>(V.G, V.EG, b);
+        const DView &D = dom_ref<ENS>(V.D, E, b);
+        const int base = cell_base<ENS>(V.EG, b);
         const int cx = cell_axis(wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]), G.inv_cs[0], G.nc[0]);
         const int cy = cell_axis(wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]), G.inv_cs[1], G.nc[1]);
         const int cz = cell_axis(wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]), G.inv_cs[2], G.nc[2]);
@@ -126,24 +152,38 @@ __global__ void k_cells_count(PView P, const __grid_constant__ DView D0, const _
 }
 
 template <bool ENS>
-__global__ void k_cells_fill(PView P, const __grid_constant__ DView D0, const __grid_constant__ Grid G0, Ens E, const EnsGrid *__restrict__ EG,
-                             const int32_t *__restrict__ cell_start, const int32_t *__restrict__ cell_of,
-                             const int32_t *__restrict__ slot, int32_t *__restrict__ sorted,
-                             float4 *__restrict__ rec0, float4 *__restrict__ rec1, int32_t *__restrict__ cellc,
-                             int32_t *__restrict__ sbat, int32_t *__restrict__ cnt, unsigned long long *__restrict__ zero,
-                             int64_t nzero)
+__global__ void k_cells_count(const __grid_constant__ BuildView V)
 {
     pdl_wait();
     pdl_trigger();
+    cells_count<ENS>(V);
+}
+
+template <bool ENS>
+__device__ __forceinline__ void cells_fill(const BuildView &V)
+{
+    const PView &P = V.P;
+    const Ens &E = V.E;
+    const int32_t *__restrict__ cell_start = V.cell_cnt;
+    const int32_t *__restrict__ cell_of = V.cell_of;
+    const int32_t *__restrict__ slot = V.slot;
+    int32_t *__restrict__ sorted = V.sorted;
+    float4 *__restrict__ rec0 = V.rec0;
+    float4 *__restrict__ rec1 = V.rec1;
+    int32_t *__restrict__ cellc = V.cellc;
+    int32_t *__restrict__ sbat = V.sbat;
+    int32_t *__restrict__ cnt = V.cnt;
+    unsigned long long *__restrict__ zero = V.scan_state;
+    const int64_t nzero = V.z2;
     // the sweep's counts (2N + 1) and the state of the scan after it start at zero
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * (int64_t)P.n + 1; k += stride) cnt[k] = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nzero; k += stride) zero[k] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int b = ENS ? batch_of(E, i) : 0;
-        const Grid &G = grid_ref<ENS>(G0, EG, b);
-        const DView &D = dom_ref<ENS>(D0, E, b);
-        const int base = cell_base<ENS>(EG, b);
+        const Grid &G = grid_ref<ENS>(V.G, V.EG, b);
+        const DView &D = dom_ref<ENS>(V.D, E, b);
+        const int base = cell_base<ENS>(V.EG, b);
         const int cg = cell_of[i];
         const int s = cell_start[cg] + slot[i];
         const int c = cg - base;
@@ -160,6 +200,14 @@ __global__ void k_cells_fill(PView P, const __grid_constant__ DView D0, const __
                               (float)(zw - (cz + 0.5) * G.csd[2]), fmaxf(rpar, rperp));
         rec1[s] = make_float4(o.x, o.y, o.z, rpar * rpar - rperp * rperp);
     }
+}
+
+template <bool ENS>
+__global__ void k_cells_fill(const __grid_constant__ BuildView V)
+{
+    pdl_wait();
+    pdl_trigger();
+    cells_fill<ENS>(V);
 }
 
 // exact (double) form of the three tests, as in the definition
@@ -342,24 +390,31 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
 // build), the extra ones are kept as pairs (a gap within the margin of the
 // list cut-off, where every element of K~ is zero) and flag bit 8 is set.
 template <bool ENS>
-__global__ void __launch_bounds__(256, 6) k_pairs_sweep(PView P, const __grid_constant__ DView D0,
-                                                     const __grid_constant__ Grid G0, Ens E,
-                                                     const EnsGrid *__restrict__ EG,
-                                                     const int32_t *__restrict__ cell_start,
-                                                     const int32_t *__restrict__ sorted,
-                                                     const float4 *__restrict__ rec0,
-                                                     const float4 *__restrict__ rec1,
-                                                     const int32_t *__restrict__ cellc,
-                                                     const int32_t *__restrict__ sbat, int32_t *__restrict__ cnt,
-                                                     int32_t *__restrict__ slots, uint8_t *__restrict__ wbits,
-                                                     int32_t *__restrict__ ovf_n, int32_t cap,
-                                                     int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
-                                                     double cutoff_d, int2 *__restrict__ und, int32_t *__restrict__ und_n,
-                                                     int32_t und_cap, unsigned *__restrict__ done,
-                                                     int32_t *__restrict__ flags)
+__device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
 {
-    pdl_wait();
-    pdl_trigger();
+    const PView &P = V.P;
+    const DView &D0 = V.D;
+    const Grid &G0 = V.G;
+    const Ens &E = V.E;
+    const EnsGrid *__restrict__ EG = V.EG;
+    const int32_t *__restrict__ cell_start = V.cell_cnt;
+    const int32_t *__restrict__ sorted = V.sorted;
+    const float4 *__restrict__ rec0 = V.rec0;
+    const float4 *__restrict__ rec1 = V.rec1;
+    const int32_t *__restrict__ cellc = V.cellc;
+    const int32_t *__restrict__ sbat = V.sbat;
+    int32_t *__restrict__ cnt = V.cnt;
+    int32_t *__restrict__ slots = V.slots;
+    uint8_t *__restrict__ wbits = V.wbits;
+    int32_t *__restrict__ ovf_n = V.totals + 2;
+    const int32_t cap = V.cap;
+    int32_t *__restrict__ pair_i = V.pair_i;
+    int32_t *__restrict__ pair_j = V.pair_j;
+    const double cutoff_d = V.cutoff_d;
+    int2 *__restrict__ und = V.und;
+    int32_t *__restrict__ und_n = V.totals + 3;
+    const int32_t und_cap = V.und_cap;
+    int32_t *__restrict__ flags = V.flags;
     const int N = P.n;
     __shared__ ItemSlot items[256];
     const int lane = threadIdx.x & 31;
@@ -378,7 +433,7 @@ __global__ void __launch_bounds__(256, 6) k_pairs_sweep(PView P, const __grid_co
         }
     };
     // each thread's own item: its runs of candidates and its wall tests
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = (int)(f0 + threadIdx.x);
     int total = 0;
     if (f < SWEEP_ROWS * N) {
         const int s = f / SWEEP_ROWS, row = f - SWEEP_ROWS * s;
@@ -513,36 +568,55 @@ __global__ void __launch_bounds__(256, 6) k_pairs_sweep(PView P, const __grid_co
     __syncwarp();
     if (lane < qn) drain(lane);
     }
+}
+
+// the FP64 decisions of the listed candidates, entries t0, t0 + stride, ...
+template <bool ENS>
+__device__ __forceinline__ void decide_listed(const BuildView &V, int64_t t0, int64_t stride)
+{
+    const int nu = min(*(volatile int32_t *)(V.totals + 3), V.und_cap);
+    for (int64_t u = t0; u < nu; u += stride) {
+        const int2 e = __ldcg(V.und + u);
+        const int i = V.sorted[e.x], j = V.sorted[e.y];
+        const DView &D = dom_ref<ENS>(V.D, V.E, ENS ? V.sbat[e.x] : 0);
+        if (pair_test_fp64(V.P, D, i, j, V.cutoff_d))
+            store_candidate(i, j, V.cnt, V.slots, V.totals + 2, V.cap, V.pair_i, V.pair_j);
+    }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(256, 6) k_pairs_sweep(const __grid_constant__ BuildView V)
+{
+    pdl_wait();
+    pdl_trigger();
+    sweep_items<ENS>(V, (int64_t)blockIdx.x * blockDim.x);
     // the last block to finish decides the listed candidates in FP64
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd((unsigned *)(V.totals + 4), 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int nu = min(*(volatile int32_t *)und_n, und_cap);
-    for (int u = threadIdx.x; u < nu; u += blockDim.x) {
-        const int2 e = __ldcg(und + u);
-        const int i = sorted[e.x], j = sorted[e.y];
-        const DView &D = dom_ref<ENS>(D0, E, ENS ? sbat[e.x] : 0);
-        if (pair_test_fp64(P, D, i, j, cutoff_d)) store_candidate(i, j, cnt, slots, ovf_n, cap, pair_i, pair_j);
-    }
+    decide_listed<ENS>(V, threadIdx.x, blockDim.x);
 }
 
 // Canonical order: each particle's partners, sorted, then its wall pairs, at
 // the offsets of the scan (off = the scanned counts, off[2N] = the total).
 // The count is the total, or total + overflow entries when they do not fit.
-__global__ void __launch_bounds__(256) k_pairs_compact(int32_t n, const int32_t *__restrict__ off,
-                                                       const int32_t *__restrict__ slots,
-                                                       const uint8_t *__restrict__ wbits,
-                                                       const int32_t *__restrict__ ovf_n, int32_t cap,
-                                                       int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j,
-                                                       int32_t *__restrict__ d_count, const int32_t *__restrict__ flags,
-                                                       int32_t *__restrict__ flags_out)
+__device__ __forceinline__ void pairs_compact(const BuildView &V)
 {
-    pdl_wait();
-    pdl_trigger();
+    const int32_t n = V.P.n;
+    const int32_t *__restrict__ off = V.cnt;
+    const int32_t *__restrict__ slots = V.slots;
+    const uint8_t *__restrict__ wbits = V.wbits;
+    const int32_t *__restrict__ ovf_n = V.totals + 2;
+    const int32_t cap = V.cap;
+    int32_t *__restrict__ pair_i = V.pair_i;
+    int32_t *__restrict__ pair_j = V.pair_j;
+    int32_t *__restrict__ d_count = V.d_count;
+    const int32_t *__restrict__ flags = V.flags;
+    int32_t *__restrict__ flags_out = V.flags_out;
     const int total = off[2 * n];
     const int novf = *ovf_n;
     const int64_t need = (int64_t)total + novf;
@@ -609,6 +683,13 @@ __global__ void __launch_bounds__(256) k_pairs_compact(int32_t n, const int32_t 
                 ++c;
             }
     }
+}
+
+__global__ void __launch_bounds__(256) k_pairs_compact(const __grid_constant__ BuildView V)
+{
+    pdl_wait();
+    pdl_trigger();
+    pairs_compact(V);
 }
 
 __global__ void k_max_semi(PView P, unsigned int *__restrict__ out)
@@ -747,31 +828,55 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
         if (!rc && flags_out) rc = lub_check_cuda(ctx, cudaMemsetAsync(flags_out, 0, 4, st), "memset flags");
         return rc;
     }
+    BuildView V;
+    memset(&V, 0, sizeof(V));
+    V.P = P;
+    V.D = D;
+    V.G = G;
+    V.E = E;
+    V.EG = EG;
+    V.flags = L.flags;
+    V.cell_cnt = L.cell_cnt;
+    V.cell_of = L.cell_of;
+    V.slot = L.slot;
+    V.sorted = L.sorted;
+    V.cellc = L.cellc;
+    V.sbat = L.sbat;
+    V.cnt = L.cnt;
+    V.totals = L.totals;
+    V.slots = L.slots;
+    V.wbits = L.wbits;
+    V.und = L.und;
+    V.rec0 = L.rec0;
+    V.rec1 = L.rec1;
+    V.scan_state = (unsigned long long *)L.tmp;
+    V.z1 = scan_state_words(G.ncell + 1);
+    V.z2 = scan_state_words(2 * N + 1);
+    V.cutoff_d = prm.list_cutoff;
+    V.pair_i = pi;
+    V.pair_j = pj;
+    V.d_count = d_count;
+    V.flags_out = flags_out;
+    V.rmax_bound = rmax;
+    V.und_cap = L.und_cap;
+    V.cap = cap;
+    cudaError_t e;
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 8);
-    const int64_t z1 = scan_state_words(G.ncell + 1), z2 = scan_state_words(2 * N + 1);
-    unsigned long long *scan_state = (unsigned long long *)L.tmp;
-    cudaError_t e = launch_pdl(k_cells_count<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot,
-                               rmax, L.flags, scan_state, z1);
+    e = launch_pdl(k_cells_count<ENS>, gn, block, 0, st, V);
     if ((rc = lub_check_cuda(ctx, e, "cells count launch"))) return rc;
     if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st, L.flags, true)))
         return rc;
-    e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, P, D, G, E, EG, L.cell_cnt, L.cell_of, L.slot, L.sorted,
-                   L.rec0, L.rec1, L.cellc, L.sbat, L.cnt, scan_state, z2);
+    e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, V);
     if ((rc = lub_check_cuda(ctx, e, "cells fill launch"))) return rc;
     // one item per thread (no grid-stride loop)
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
     sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
-    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, P, D, G, E, EG, (const int32_t *)L.cell_cnt, (const int32_t *)L.sorted, (const float4 *)L.rec0,
-                   (const float4 *)L.rec1, (const int32_t *)L.cellc, (const int32_t *)L.sbat, L.cnt, L.slots, L.wbits,
-                   L.totals + 2, cap, pi, pj, (double)prm.list_cutoff, L.und, L.totals + 3, L.und_cap,
-                   (unsigned *)(L.totals + 4), L.flags);
+    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, V);
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;
-    e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 16), 256, 0, st, (int32_t)N, (const int32_t *)L.cnt,
-                   (const int32_t *)L.slots, (const uint8_t *)L.wbits, (const int32_t *)(L.totals + 2), cap, pi, pj,
-                   d_count, (const int32_t *)L.flags, flags_out);
+    e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 16), 256, 0, st, V);
     return lub_check_cuda(ctx, e, "pairs compact launch");
 }
 

@@ -317,8 +317,8 @@ def test_dense_packings(case):
     """Growth packings at Phi = 0.5 of spheroids with aspect ratios in
     [1/3, 3]: the longest set the cell range 2 Rmax + Delta_L (about 19.7), so
     a cell holds about 10 particles and every (particle, row) item of the
-    sweep has some 30 candidates (the build then gives each item a group of
-    lanes).  The pair list must be the oracle's, with full parity;
+    sweep has some 30 candidates in its x window (the warp shares them out
+    over its lanes).  The pair list must be the oracle's, with full parity;
     'five_cells' is a small periodic box (two cells per axis)."""
     rng = np.random.default_rng({"periodic": 21, "walls": 22, "five_cells": 23}[case])
     if case == "five_cells":
@@ -341,6 +341,27 @@ def test_dense_packings(case):
     parts, dom, _ = gen.grow(sh, L, periodic=per, walls=walls, seed=5)
     pi, pj = oracle.candidates(parts, dom, 1.0)
     assert len(pi) > 2 * len(sh)
+    g = run_gpu(parts, dom, "mixed")
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
+
+
+@pytest.mark.parametrize("shift", [(0.0, 0.0, 0.0), (-0.3, 0.25, -0.1)])
+def test_open_box_with_particles_outside_it(shift):
+    """A box open on every axis (no periodic image, no wall): the sweep's x
+    windows are clamped to the grid instead of wrapped.  Shifted by a
+    fraction of the box, a quarter of the particles lie outside [0, L) on
+    some axis and sit in the edge cells; every pair must still be listed
+    exactly once (against the oracle's all-pairs search)."""
+    rng = np.random.default_rng(31)
+    sh = gen.aspect_shapes(1500, rng)
+    L = 120.0
+    parts, dom = gen.suspension(sh, (L, L, L), periodic=(False, False, False), attach_prob=0.8, seed=32)
+    for k, f in zip(("x", "y", "z"), shift):
+        parts[k] = parts[k] + f * L
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert len(pi) > len(sh)
     g = run_gpu(parts, dom, "mixed")
     np.testing.assert_array_equal(g["pi"], pi)
     np.testing.assert_array_equal(g["pj"], pj)
