@@ -31,6 +31,7 @@
 // run once over all suspensions, and no pair crosses two of them.
 #include <string.h>
 
+#include "ff.cuh"
 #include "lub_internal.cuh"
 
 namespace {
@@ -46,6 +47,8 @@ struct Grid {
     float margin;  // absolute FP32 error allowance of the tests
     float rmax;    // bound of every particle's Rmax
     int xsub;      // fine x cells per cell edge of the interaction range
+    float csff[3][2];  // cell edges as float-float (hi, lo)
+    float inv_csf[3];
 };
 
 // Fine cells along x: a row of the stencil (one y, z column of cells) is cut
@@ -85,19 +88,6 @@ __device__ __forceinline__ int cell_base(const EnsGrid *EG, int b)
     return ENS ? __ldg(&EG[b].cell_base) : 0;
 }
 
-__device__ __forceinline__ double wrap_axis(double x, double L, double invL, int periodic)
-{
-    return periodic ? x - L * floor(x * invL) : x;
-}
-
-__device__ __forceinline__ int cell_axis(double xw, double inv_cs, int nc)
-{
-    double f = floor(xw * inv_cs);
-    if (!(f >= 0.0)) f = 0.0;  // also catches NaN
-    if (f > (double)(nc - 1)) f = (double)(nc - 1);
-    return (int)f;
-}
-
 // Everything the pair build's kernels read and write, passed by value as one
 // __grid_constant__ kernel parameter: the particles, the domain and grid (of
 // the single suspension; the ensemble tables through E and EG), the
@@ -111,6 +101,7 @@ struct BuildView {
     int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
     uint8_t *wbits;
     int2 *und;
+    float4 *rel;  // each particle's position relative to its cell's centre (cells count -> cells fill)
     float4 *rec0, *rec1;
     unsigned long long *scan_state;
     int64_t z1, z2;  // state words of the cell scan and of the pair-count scan
@@ -119,6 +110,60 @@ struct BuildView {
     float rmax_bound;
     int32_t und_cap, cap;
 };
+
+// x < 0 in float-float
+__device__ __forceinline__ bool ff_neg_(const ff x) { return x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f); }
+
+// Cell of one coordinate and the position relative to the cell's centre.  The
+// double coordinate is split once into float-float (four FP64-pipe
+// operations; this GPU runs FP64 at 1/64 of the FP32 rate) and the rest runs
+// on the FP32 pipe: the wrap into [0, L) on a periodic axis, the cell
+// floor(x / cs) in FP32, corrected by the exact sign of the float-float
+// remainder x - c cs (so a cell holds its positions to about 1e-14 of its
+// edges, well inside the 1e-9 allowance of the cell size), and the clamp to
+// the edge cells of an open axis (a position outside the box then lies
+// beyond its cell).  NaN goes to cell 0.
+struct AxisCell {
+    int c;
+    float rel;
+};
+
+__device__ __forceinline__ AxisCell axis_cell(double x, const DView &D, const Grid &G, int a)
+{
+    const float hi = __double2float_rn(x);
+    ff p;
+    p.hi = hi;
+    p.lo = __double2float_rn(x - (double)hi);
+    if (D.periodic[a]) {
+        const ff L = {D.Lff[a][0], D.Lff[a][1]};
+        const float k = floorf(p.hi * D.invLf[a]);
+        if (k != 0.f && isfinite(k)) p = ff_sub(p, ff_mulf(L, k));
+        if (ff_neg_(p))
+            p = ff_add(p, L);
+        else if (!ff_neg_(ff_sub(p, L)))
+            p = ff_sub(p, L);
+    }
+    const int nc = G.nc[a];
+    const ff cs = {G.csff[a][0], G.csff[a][1]};
+    float f = floorf(p.hi * G.inv_csf[a]);
+    if (!(f >= -1.f)) f = -1.f;  // also catches NaN
+    if (f > (float)nc) f = (float)nc;
+    int c = (int)f;
+    ff r = ff_sub(p, ff_mulf(cs, (float)c));
+    if (ff_neg_(r)) {
+        --c;
+        r = ff_add(r, cs);
+    } else if (!ff_neg_(ff_sub(r, cs))) {
+        ++c;
+        r = ff_sub(r, cs);
+    }
+    if (c < 0 || c > nc - 1) {
+        c = c < 0 ? 0 : nc - 1;
+        r = ff_sub(p, ff_mulf(cs, (float)c));
+    }
+    const ff rel = ff_sub(r, ff_mulf(cs, 0.5f));
+    return AxisCell{c, __fadd_rn(rel.hi, rel.lo)};
+}
 
 template <bool ENS>
 __device__ __forceinline__ void cells_count(const BuildView &V)
@@ -140,11 +185,11 @@ __device__ __forceinline__ void cells_count(const BuildView &V)
         const Grid &G = grid_ref<ENS>(V.G, V.EG, b);
         const DView &D = dom_ref<ENS>(V.D, E, b);
         const int base = cell_base<ENS>(V.EG, b);
-        const int cx = cell_axis(wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]), G.inv_cs[0], G.nc[0]);
-        const int cy = cell_axis(wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]), G.inv_cs[1], G.nc[1]);
-        const int cz = cell_axis(wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]), G.inv_cs[2], G.nc[2]);
-        const int c = base + (cz * G.nc[1] + cy) * G.nc[0] + cx;
+        const AxisCell ax = axis_cell(P.x[i], D, G, 0), ay = axis_cell(P.y[i], D, G, 1),
+                       az = axis_cell(P.z[i], D, G, 2);
+        const int c = base + (az.c * G.nc[1] + ay.c) * G.nc[0] + ax.c;
         cell_of[i] = c;
+        V.rel[i] = make_float4(ax.rel, ay.rel, az.rel, 0.f);
         slot[i] = atomicAdd(cell_cnt + c, 1);
         const float rm = fmaxf(P.rpar[i], P.rperp[i]);
         if (!(rm <= rmax_bound)) atomicOr(flags, 1);  // bound violated or NaN shape
@@ -182,22 +227,18 @@ __device__ __forceinline__ void cells_fill(const BuildView &V)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const int b = ENS ? batch_of(E, i) : 0;
         const Grid &G = grid_ref<ENS>(V.G, V.EG, b);
-        const DView &D = dom_ref<ENS>(V.D, E, b);
         const int base = cell_base<ENS>(V.EG, b);
         const int cg = cell_of[i];
         const int s = cell_start[cg] + slot[i];
         const int c = cg - base;
         const int cx = c % G.nc[0], cy = (c / G.nc[0]) % G.nc[1], cz = c / (G.nc[0] * G.nc[1]);
-        const double xw = wrap_axis(P.x[i], D.L[0], G.invL[0], D.periodic[0]);
-        const double yw = wrap_axis(P.y[i], D.L[1], G.invL[1], D.periodic[1]);
-        const double zw = wrap_axis(P.z[i], D.L[2], G.invL[2], D.periodic[2]);
+        const float4 r = V.rel[i];
         const float rpar = P.rpar[i], rperp = P.rperp[i];
         const V3<float> o = quat_axis<float>(P.qw[i], P.qx[i], P.qy[i], P.qz[i]);
         sorted[s] = i;
         if (ENS) sbat[s] = b;
         cellc[s] = cx | (cy << 10) | (cz << 20);  // nc <= 1024 per axis
-        rec0[s] = make_float4((float)(xw - (cx + 0.5) * G.csd[0]), (float)(yw - (cy + 0.5) * G.csd[1]),
-                              (float)(zw - (cz + 0.5) * G.csd[2]), fmaxf(rpar, rperp));
+        rec0[s] = make_float4(r.x, r.y, r.z, fmaxf(rpar, rperp));
         rec1[s] = make_float4(o.x, o.y, o.z, rpar * rpar - rperp * rperp);
     }
 }
@@ -744,6 +785,9 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
         G.cs[a] = (float)G.csd[a];
         G.inv_cs[a] = G.nc[a] / D.L[a];
         G.invL[a] = 1.0 / D.L[a];
+        G.csff[a][0] = (float)G.csd[a];
+        G.csff[a][1] = (float)(G.csd[a] - (double)G.csff[a][0]);
+        G.inv_csf[a] = (float)G.inv_cs[a];
     }
     G.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
     G.cutoff = (float)prm.list_cutoff;
@@ -758,7 +802,7 @@ struct Layout {
     uint8_t *wbits;
     int2 *und;  // candidates left to the FP64 test (und_cap entries)
     int32_t und_cap;
-    float4 *rec0, *rec1;
+    float4 *rel, *rec0, *rec1;
     void *tmp;
     size_t tmp_bytes, total;
 };
@@ -792,6 +836,7 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     L.cnt = (int32_t *)s;
     s += b_n2;
     L.slots = (int32_t *)s;
+    L.rel = (float4 *)s;  // shares the slots' storage: read by the cells fill, before the sweep fills the slots
     s += b_slots;
     L.wbits = (uint8_t *)s;
     s += b_bits;
@@ -847,6 +892,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.slots = L.slots;
     V.wbits = L.wbits;
     V.und = L.und;
+    V.rel = L.rel;
     V.rec0 = L.rec0;
     V.rec1 = L.rec1;
     V.scan_state = (unsigned long long *)L.tmp;
