@@ -176,10 +176,7 @@ const char *lub_last_error(const lub_ctx *ctx);
  * Particle w-wall pair (i, -1-w) is listed when the exact gap
  * wall_dir (z_i - wall_z) - sigma_i(e_z) < Delta_L.  The decisions are those
  * of double precision arithmetic: FP32 tests with a margin of 1e-5 (2 Rmax +
- * Delta_L + 1), and candidates inside the margin decided again in FP64 (up
- * to 1024 + n/4 of them per call; beyond that, which takes that many test
- * values within the margin of a threshold, the extra ones are listed: their
- * gap is within the margin of Delta_L, where the corrections vanish).
+ * Delta_L + 1), and every candidate inside the margin decided again in FP64.
  *
  * Order: particle pairs by (i, j) ascending, then wall pairs by (i, w).
  * Writes pair_i[k], pair_j[k] for k < min(count, capacity) and *d_count =

@@ -100,7 +100,6 @@ struct BuildView {
     const EnsGrid *EG;
     int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
     uint8_t *wbits;
-    int2 *und;
     float4 *rel;  // each particle's position relative to its cell's centre (cells count -> cells fill)
     float4 *rec0, *rec1;
     unsigned long long *scan_state;
@@ -108,7 +107,7 @@ struct BuildView {
     double cutoff_d;
     int32_t *pair_i, *pair_j, *d_count, *flags_out;
     float rmax_bound;
-    int32_t und_cap, cap;
+    int32_t cap;
 };
 
 // x < 0 in float-float
@@ -422,14 +421,11 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
 // pair), [N, 2N) wall-pair counts; slots [N][KSLOT]; wall bits per particle;
 // overflow entry o at pair_i/pair_j[cap - 1 - o].
 //
-// Candidates inside the FP32 margin are rare; the FP64 test that decides
-// them needs about 30 more registers than the sweep itself, which would cut
-// the resident warps by 40 %.  So the sweep only lists them (slot pairs in
-// und, count in und_n) and the block that finishes last decides them in FP64
-// (each block fences its writes and takes a ticket; no block waits).  Should
-// the list fill up (more than its capacity of borderline candidates in one
-// build), the extra ones are kept as pairs (a gap within the margin of the
-// list cut-off, where every element of K~ is zero) and flag bit 8 is set.
+// Candidates inside the FP32 margin (about one in 10^4) are decided on the
+// spot by the FP64 test, in the lane that holds them: that code path runs
+// rarely and spills at the sweep's register budget, which costs less than
+// listing them for a block that finishes last (a fence and a ticket per
+// block: 7 us of a 0.08 ms step at 32k particles).
 template <bool ENS>
 __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
 {
@@ -452,10 +448,6 @@ __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
     int32_t *__restrict__ pair_i = V.pair_i;
     int32_t *__restrict__ pair_j = V.pair_j;
     const double cutoff_d = V.cutoff_d;
-    int2 *__restrict__ und = V.und;
-    int32_t *__restrict__ und_n = V.totals + 3;
-    const int32_t und_cap = V.und_cap;
-    int32_t *__restrict__ flags = V.flags;
     const int N = P.n;
     __shared__ ItemSlot items[256];
     const int lane = threadIdx.x & 31;
@@ -464,13 +456,9 @@ __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
         if (r == kAccept) {
             store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
         } else {
-            const int w = atomicAdd(und_n, 1);
-            if (w < und_cap) {
-                und[w] = make_int2(s, t);
-            } else {
-                atomicOr(flags, 8);
-                store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
-            }
+            const int i = sorted[s], j = sorted[t];
+            if (pair_test_fp64(P, dom_ref<ENS>(D0, E, ENS ? sbat[s] : 0), i, j, cutoff_d))
+                store_candidate(i, j, cnt, slots, ovf_n, cap, pair_i, pair_j);
         }
     };
     // each thread's own item: its runs of candidates and its wall tests
@@ -611,35 +599,12 @@ __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
     }
 }
 
-// the FP64 decisions of the listed candidates, entries t0, t0 + stride, ...
-template <bool ENS>
-__device__ __forceinline__ void decide_listed(const BuildView &V, int64_t t0, int64_t stride)
-{
-    const int nu = min(*(volatile int32_t *)(V.totals + 3), V.und_cap);
-    for (int64_t u = t0; u < nu; u += stride) {
-        const int2 e = __ldcg(V.und + u);
-        const int i = V.sorted[e.x], j = V.sorted[e.y];
-        const DView &D = dom_ref<ENS>(V.D, V.E, ENS ? V.sbat[e.x] : 0);
-        if (pair_test_fp64(V.P, D, i, j, V.cutoff_d))
-            store_candidate(i, j, V.cnt, V.slots, V.totals + 2, V.cap, V.pair_i, V.pair_j);
-    }
-}
-
 template <bool ENS>
 __global__ void __launch_bounds__(256, 6) k_pairs_sweep(const __grid_constant__ BuildView V)
 {
     pdl_wait();
     pdl_trigger();
     sweep_items<ENS>(V, (int64_t)blockIdx.x * blockDim.x);
-    // the last block to finish decides the listed candidates in FP64
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd((unsigned *)(V.totals + 4), 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    decide_listed<ENS>(V, threadIdx.x, blockDim.x);
 }
 
 // Canonical order: each particle's partners, sorted, then its wall pairs, at
@@ -800,8 +765,6 @@ Grid make_grid(const DView &D, const lub_params &prm, float rmax, int64_t n, int
 struct Layout {
     int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
     uint8_t *wbits;
-    int2 *und;  // candidates left to the FP64 test (und_cap entries)
-    int32_t und_cap;
     float4 *rel, *rec0, *rec1;
     void *tmp;
     size_t tmp_bytes, total;
@@ -811,15 +774,13 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
 {
     const size_t b_cell = align256((ncell + 1) * 4), b_n = align256((N + 1) * 4), b_n2 = align256((2 * N + 1) * 4);
     const size_t b_slots = align256((size_t)N * KSLOT * 4), b_bits = align256((size_t)N + 1);
-    const int64_t und_cap = 1024 + N / 4;
-    const size_t b_und = align256((size_t)und_cap * 8);
     const size_t b_rec = align256(N * 16),
                  b_tmp = align256(scan_tmp_bytes(ncell + 1 > 2 * N + 1 ? ncell + 1 : 2 * N + 1));
     Layout L;
     char *s = (char *)base;
     L.flags = (int32_t *)s;
     s += 256;
-    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries, [3] undecided, [4] blocks done
+    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries
     s += 256;
     L.cell_cnt = (int32_t *)s;
     s += b_cell;
@@ -844,9 +805,6 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     s += b_rec;
     L.rec1 = (float4 *)s;
     s += b_rec;
-    L.und = (int2 *)s;
-    L.und_cap = (int32_t)und_cap;
-    s += b_und;
     L.tmp = s;
     L.tmp_bytes = b_tmp;
     s += b_tmp;
@@ -891,7 +849,6 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.totals = L.totals;
     V.slots = L.slots;
     V.wbits = L.wbits;
-    V.und = L.und;
     V.rel = L.rel;
     V.rec0 = L.rec0;
     V.rec1 = L.rec1;
@@ -904,7 +861,6 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.d_count = d_count;
     V.flags_out = flags_out;
     V.rmax_bound = rmax;
-    V.und_cap = L.und_cap;
     V.cap = cap;
     cudaError_t e;
     const int block = 256;
