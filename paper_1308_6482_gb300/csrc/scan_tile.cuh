@@ -5,7 +5,9 @@
 // totals of the 32 tiles before it at a time, down to the nearest tile that
 // has published its inclusive prefix, then publishes its own.  Tiles must be
 // taken in order (an atomic ticket), so that a block only waits on tiles whose
-// blocks are already running.  Every wait is bounded: on timeout the block
+// blocks are already running.  A published word carries its flag and value
+// together (one 64-bit exchange), so no other memory needs ordering before
+// it and no fence precedes it.  Every wait is bounded: on timeout the block
 // sets bit 2 of *err and carries on with what it has.
 #pragma once
 
@@ -18,7 +20,7 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr unsigned long long ST_AGG = 1ull << 32;     // tile total published
 constexpr unsigned long long ST_PREFIX = 2ull << 32;  // inclusive prefix published
-constexpr long kSpinLimit = 1l << 22;                 // ~0.3 s of 64 ns naps
+constexpr long kSpinLimit = 1l << 22;                 // ~2 s of L2 round trips
 
 __host__ __device__ inline int64_t tiles_of(int64_t n)
 {
@@ -84,15 +86,9 @@ __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n
         const int lane = threadIdx.x;
         int excl = 0;
         if (tile == 0) {
-            if (lane == 0) {
-                __threadfence();
-                atomicExch(tstate, ST_PREFIX | (unsigned)tot);
-            }
+            if (lane == 0) atomicExch(tstate, ST_PREFIX | (unsigned)tot);
         } else {
-            if (lane == 0) {
-                __threadfence();
-                atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
-            }
+            if (lane == 0) atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
             long spins = 0;
             int top = tile - 1;
             while (true) {
@@ -109,7 +105,6 @@ __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n
                         if (lane == 0 && err) atomicOr(err, 4);
                         break;
                     }
-                    __nanosleep(64);
                     continue;
                 }
                 int x = (lane <= stop) ? (int)(unsigned)(w & 0xffffffffull) : 0;
@@ -119,10 +114,7 @@ __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n
                 if (stop < 32) break;
                 top -= 32;
             }
-            if (lane == 0) {
-                __threadfence();
-                atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
-            }
+            if (lane == 0) atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
         }
         if (lane == 0) {
             prefix_s = excl;
