@@ -155,7 +155,7 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
     int32_t *inc = (int32_t *)(s + b_cnt + b_fill);
     int32_t *tot = (int32_t *)(s + b_cnt + b_fill + b_inc);
     void *tmp = s + b_cnt + b_fill + b_inc + b_tot;
-    rc = lub_check_cuda(ctx, cudaMemsetAsync(cnt, 0, b_cnt + b_fill, st), "memset inc counts");
+    rc = zero_async(ctx, ctx->num_sms, cnt, b_cnt + b_fill, st);
     if (rc) return rc;
     const int block = 256;
     const int gp = grid_for(cap > 0 ? cap : 1, block, ctx->num_sms, 8);

@@ -858,7 +858,7 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     *wl = (int32_t *)(base + 256);
     if (gap_in && !*gap_in) *gap_in = (double *)(base + 256 + b_wl);
     if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
-    rc = lub_check_cuda(ctx, cudaMemsetAsync(*wl_count, 0, 16, st), "memset work list");
+    rc = zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
     if (rc || !P) return rc;
     // the particles' float-float positions for the FP32 stage
     *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);

@@ -373,15 +373,21 @@ int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, voi
 size_t scan_tmp_bytes(int64_t n);
 inline int64_t scan_state_words(int64_t n) { return (int64_t)(scan_tmp_bytes(n) / 8); }
 
-// zero the per-particle force and torque arrays (bytes each); one memset when
+// Zero `bytes` of device memory with a kernel in the chain of programmatic
+// dependent launches (a memset between two kernels would make the second wait
+// for the memset's completion and launch): it waits for the kernel before it,
+// like every kernel of a step, and releases the next one.  num_sms sizes the
+// grid.
+int zero_async(lub_ctx *ctx, int num_sms, void *ptr, size_t bytes, cudaStream_t st);
+
+// zero the per-particle force and torque arrays (bytes each); one launch when
 // the torque array directly follows the force array (one caller buffer)
 inline int zero_force_torque(lub_ctx *ctx, void *force, void *torque, size_t bytes, cudaStream_t st)
 {
     if (bytes == 0) return LUB_OK;
-    if ((char *)torque == (char *)force + bytes)
-        return lub_check_cuda(ctx, cudaMemsetAsync(force, 0, 2 * bytes, st), "memset force/torque");
-    int rc = lub_check_cuda(ctx, cudaMemsetAsync(force, 0, bytes, st), "memset force");
-    if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(torque, 0, bytes, st), "memset torque");
+    if ((char *)torque == (char *)force + bytes) return zero_async(ctx, ctx->num_sms, force, 2 * bytes, st);
+    int rc = zero_async(ctx, ctx->num_sms, force, bytes, st);
+    if (!rc) rc = zero_async(ctx, ctx->num_sms, torque, bytes, st);
     return rc;
 }
 

@@ -824,7 +824,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     // the scratch keeps earlier contents: clear what must start at zero, the
     // flags, totals and cell counts in one (they are contiguous); the kernels
     // clear the sweep's counts and the scans' states for the launches after them
-    int rc = lub_check_cuda(ctx, cudaMemsetAsync(L.flags, 0, 512 + (G.ncell + 1) * 4, st), "memset counts");
+    int rc = zero_async(ctx, num_sms, L.flags, 512 + (G.ncell + 1) * 4, st);
     if (rc) return rc;
     if (N == 0) {
         rc = lub_check_cuda(ctx, cudaMemsetAsync(d_count, 0, 4, st), "memset count");

@@ -31,7 +31,38 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restr
     scan_one_tile(a, n, state + 1, tile_s, d_total, err);
 }
 
+// the aligned body in 16-byte words, the unaligned head and tail bytes by
+// block 0
+__global__ void __launch_bounds__(256) k_zero(uint4 *__restrict__ body, int64_t n16, unsigned char *__restrict__ head,
+                                              int nhead, unsigned char *__restrict__ tail, int ntail)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n16; k += (int64_t)gridDim.x * blockDim.x)
+        body[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0) {
+        if ((int)threadIdx.x < nhead) head[threadIdx.x] = 0;
+        if ((int)threadIdx.x < ntail) tail[threadIdx.x] = 0;
+    }
+}
+
 }  // namespace
+
+int zero_async(lub_ctx *ctx, int num_sms, void *ptr, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return LUB_OK;
+    unsigned char *p = (unsigned char *)ptr;
+    const size_t mis = (size_t)(((uintptr_t)p) & 15u);
+    size_t nhead = mis ? 16 - mis : 0;
+    if (nhead > bytes) nhead = bytes;
+    const int64_t n16 = (int64_t)((bytes - nhead) / 16);
+    const size_t ntail = bytes - nhead - (size_t)n16 * 16;
+    const int grid = grid_for(n16 > 0 ? n16 : 1, 256, num_sms > 0 ? num_sms : 1, 4);
+    return lub_check_cuda(ctx,
+                          launch_pdl(k_zero, grid, 256, 0, st, (uint4 *)(p + nhead), n16, p, (int)nhead,
+                                     p + nhead + (size_t)n16 * 16, (int)ntail),
+                          "zero launch");
+}
 
 size_t scan_tmp_bytes(int64_t n) { return (size_t)(tiles_of(n) + 1) * sizeof(unsigned long long); }
 
@@ -41,7 +72,7 @@ int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, voi
     if (tmp_bytes < scan_tmp_bytes(n)) return lub_set_error(ctx, LUB_ERR_ARG, "scan: temp too small");
     const int64_t nt = tiles_of(n);
     if (!state_zeroed) {
-        const int rc = lub_check_cuda(ctx, cudaMemsetAsync(tmp, 0, scan_tmp_bytes(n), st), "scan state");
+        const int rc = zero_async(ctx, ctx ? ctx->num_sms : 1, tmp, scan_tmp_bytes(n), st);
         if (rc) return rc;
     }
     return lub_check_cuda(ctx,
