@@ -44,9 +44,9 @@ APPLY_BYTES_PER_PAIR = 56.0       # F, T, levers (float) + indices
 APPLY_BYTES_PER_PARTICLE = 24.0   # force + torque written
 # DRAM bytes per call from one ncu capture of the 32k-particle workload
 # (profiles/kernels_mixed_suspension_32k.md: dram__bytes_read.sum +
-# dram__bytes_write.sum summed over the pair build's six kernels, cold cache);
+# dram__bytes_write.sum summed over the pair build's seven kernels, cold cache);
 # valid for the kernels profiled there, for that workload only
-TRAFFIC_PAIRS_BUILD_32K = 9.3606e6
+TRAFFIC_PAIRS_BUILD_32K = 9.1005e6
 
 
 FORM_NAMES = {"fused": "pair build + fused pass (lub_correct)",
