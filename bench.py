@@ -827,8 +827,32 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
         ms = np.array([a.elapsed_time(b) for a, b in ev])
         cnt = counts.cpu().numpy().astype(np.float64)
         walls = int((pl.pair_j[:min(pl.count(), pl.cap)] < 0).sum().item())
+        if warm == lub.LUB_WARM_NONE and args.large_form == "merged":
+            # the three calls of the merged step timed one by one (events
+            # between the calls, L2 flushed before each step), for the roofline
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            tcall = {"pairs_build": [], "closest": [], "resistance_apply": []}
+            with torch.cuda.stream(stream):
+                for _ in range(8):
+                    flush.zero_()
+                    evs[0].record(stream)
+                    pl.build_pairs(sync_count=False, grow=False, stream=stream)
+                    evs[1].record(stream)
+                    pl.closest(stream=stream)
+                    evs[2].record(stream)
+                    pl.resistance_apply(stream=stream)
+                    evs[3].record(stream)
+                    stream.synchronize()
+                    for q, name in enumerate(tcall):
+                        tcall[name].append(evs[q].elapsed_time(evs[q + 1]))
+            m = min(pl.count(), pl.cap)
+            calls_ms["ms"] = {k: float(np.median(v[2:])) for k, v in tcall.items()}
+            calls_ms["pairs"] = m
+            calls_ms["mean_it"] = float(pl.iters[:m].float().mean().item())
+            calls_ms["fp64_frac"] = float(((pl.status[:m] & lub.LUB_ST_FP64) != 0).float().mean().item())
         return ms, cnt, int((cnt > pl.cap).sum()), walls
 
+    calls_ms = {}
     ms, cnt, over, walls = run(lub.LUB_WARM_NONE, args.large_steps)
     step_ms, pairs = aggregate(float(ms.mean()), float(cnt.mean()), ws, dev)
     out = {"workload": "%d spheroids, aspect ratio log-uniform [1/3,3], phi=0.5 (growth packing), cube %.0f^3 periodic in x,y "
@@ -838,6 +862,15 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
            "pairs_per_step_mean": pairs, "wall_pairs_last_step": walls,
            "ms_per_step": step_ms, "pairs_per_s": pairs / (step_ms * 1e-3), "capacity_overflows": over,
            "generation_s": t_gen, "warm_starts": {}}
+    if calls_ms:
+        # the roofline of the call that takes longest at this size
+        pk = peaks()
+        dom_call = max(calls_ms["ms"], key=calls_ms["ms"].get)
+        roof = roofline(dom_call, calls_ms["ms"][dom_call], calls_ms["pairs"], len(parts["x"]), calls_ms["mean_it"],
+                        calls_ms["fp64_frac"], "mixed", pk)
+        roof["note"] = "eager calls, events between them, L2 flushed before each step"
+        out["call_ms"] = calls_ms["ms"]
+        out["roofline"] = roof
     for name, warm in (("learned", lub.LUB_WARM_MLP), ("temporal", lub.LUB_WARM_PREVIOUS)):
         msw, cntw, _, _ = run(warm, max(10, args.large_steps // 10))
         wms, wp = aggregate(float(msw.mean()), float(cntw.mean()), ws, dev)
