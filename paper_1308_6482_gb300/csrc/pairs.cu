@@ -1,10 +1,11 @@
 // K0: candidate pairs by a cell list with the pre-filters of Sec. III A.
 //
 //   1. cell of every particle (cell edge >= 2 Rmax + Delta_L in y and z, an
-//      eighth of that in x) and its slot in the cell (atomic), scan of the
-//      cell counts, copy of every particle into cell order as two float4
-//      records: position relative to its cell centre with Rmax, and symmetry
-//      axis with e = R_par^2 - R_perp^2;
+//      eighth of that in x; from the coordinates split into float-float) and
+//      its slot in the cell (atomic), scan of the cell counts, copy of every
+//      particle into cell order as two float4 records: position relative to
+//      its cell centre with Rmax, and symmetry axis with e = R_par^2 -
+//      R_perp^2;
 //   2. sweep: one thread per (particle, row of the half-shell stencil), five
 //      rows (y, z columns of cells) per particle covering the own column and
 //      the 4 forward neighbours; in each row the x cells within the
@@ -27,7 +28,7 @@
 //
 // Ensemble mode: every suspension has its own cell grid (from its own box);
 // the grids are laid out back to back in one global cell index space
-// (cell_base of each suspension), so the same counting sort, sweeps and scan
+// (cell_base of each suspension), so the same counting sort, sweep and scans
 // run once over all suspensions, and no pair crosses two of them.
 #include <string.h>
 
