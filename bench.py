@@ -879,13 +879,17 @@ def large_bench(args, dev, stream, flush, ws=1, rank=0):
 
 
 def kernels_in_step(precision, form):
-    # lub_pairs_build: cells count, scan, cells fill, sweep, scan, compaction = 6;
-    # closest points, mixed: float-float positions, FP32 stage, FP64 work list (the fused pass: the
-    # positions, the FP32 stage and one kernel for the work list and the forces); FP64: one kernel;
-    # calls: lub_resistance 1 + lub_apply (atomic) 1; merged: lub_resistance_apply 1.
-    # Memsets are not counted.
-    closest = 3 if precision == "mixed" else 1
-    return 6 + closest + {"calls": 2, "merged": 1, "fused": 0}[form]
+    # lub_pairs_build: zeroing of its counters, cells count, scan, cells fill,
+    # sweep, scan, compaction = 7.  Closest points, mixed: zeroing of the work
+    # list, float-float positions, FP32 stage, refinement = 4; FP64: 1.
+    # merged: zeroing of the sums + lub_resistance_apply = 2; calls:
+    # lub_resistance + zeroing + lub_apply (atomic) = 3.  fused (lub_correct):
+    # zeroing of the sums, then mixed: zeroing of the work list, positions,
+    # FP32 stage, refinement with the forces = 5; FP64: one kernel = 2.
+    if form == "fused":
+        return 7 + (5 if precision == "mixed" else 2)
+    closest = 4 if precision == "mixed" else 1
+    return 7 + closest + {"calls": 3, "merged": 2}[form]
 
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):

@@ -458,7 +458,7 @@ int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, cons
  * per SM), the grid being min(work / block, blocks_per_sm x SMs).
  * ------------------------------------------------------------------------- */
 #define LUB_TUNE_CLOSEST_MIXED 0   /* lub_closest_points, LUB_MIXED, FP32 stage */
-#define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, FP64 work list */
+#define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, work-list refinement */
 #define LUB_TUNE_CLOSEST_FP64 2    /* lub_closest_points, LUB_FP64 */
 #define LUB_TUNE_RESISTANCE 3      /* lub_resistance */
 #define LUB_TUNE_APPLY 4           /* lub_apply, atomic form */
@@ -481,7 +481,7 @@ int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, co
  * default.  lub_set_launch_shape with block = blocks_per_sm = 0 restores it;
  * otherwise block must be one of the kernel's candidates (a multiple of 32 up
  * to its limit: 128 for the closest-point and resistance kernels, 32 for the
- * FP64 work list, 256 for lub_apply and the sweeps) and 1 <= blocks_per_sm <= 256. */
+ * work-list refinement, 256 for lub_apply and the sweep) and 1 <= blocks_per_sm <= 256. */
 int lub_get_launch_shape(const lub_ctx *ctx, int32_t kernel, int32_t *block, int32_t *blocks_per_sm);
 int lub_set_launch_shape(lub_ctx *ctx, int32_t kernel, int32_t block, int32_t blocks_per_sm);
 

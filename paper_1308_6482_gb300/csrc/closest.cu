@@ -267,7 +267,7 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
                 entry = -1 - k;
             else if (hff.hi < fp64_switch * amin)
                 entry = k;
-            if (entry != kNoEntry) st |= LUB_ST_FP64;  // on the FP64 work list (refined next)
+            if (entry != kNoEntry) st |= LUB_ST_FP64;  // on the work list (refined next)
             // consistency check of Sec. III A: the normals point to the other centre
             if (entry == kNoEntry && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
         }
@@ -449,7 +449,7 @@ __device__ __forceinline__ void store_pair(double *__restrict__ nout, double *__
     if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
 }
 
-// Compacted append to the FP64 work list (warp-collective).  One-step
+// Compacted append to the work list (warp-collective).  One-step
 // polishes (entry k) fill the list from the front, full solves (entry -1-k,
 // several iterations each) from the back, so each kind runs in warps of its
 // own instead of every warp waiting for one full solve.  wl_count[0]: front
@@ -840,8 +840,7 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
     return LUB_OK;
 }
 
-// the FP64 work list of the mixed mode: count + up to cap entries in the context scratch
-// The FP64 work list in the context scratch: counters [front, back, queue 0,
+// The work list of the mixed mode in the context scratch: counters [front, back, queue 0,
 // queue 1] and cap entries; with gap_in/status_in, also a gap and a status
 // array for callers that pass none (the fused pass needs them between its
 // kernels).
@@ -926,8 +925,8 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
     const RParams R = make_rparams(prm);
     if (prm.precision == LUB_MIXED) {
-        // the FP32 stage, then the FP64 work list and every pair's force in one
-        // queue-driven launch (gap and status in the context when not given)
+        // the FP32 stage, then the work list's refinement and every pair's force
+        // in one queue-driven launch (gap and status in the context when not given)
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status, &P, &pff))) return rc;

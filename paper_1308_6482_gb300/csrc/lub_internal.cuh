@@ -437,7 +437,7 @@ struct TuneDefault {
 };
 // defaults: grids large enough that the hardware block scheduler, not the
 // grid-stride loop, balances the uneven per-pair work (Newton iteration
-// counts, FP64 refinement) on large inputs
+// counts, refinement) on large inputs
 constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
     {128, 64, 128},  // LUB_TUNE_CLOSEST_MIXED
     {32, 64, 32},    // LUB_TUNE_CLOSEST_REFINE
