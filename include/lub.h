@@ -190,7 +190,8 @@ const char *lub_last_error(const lub_ctx *ctx);
  * inside the build that times out gives LUB_ERR_TIMEOUT on that path.
  * Without h_count_or_null the call does not synchronise (unless
  * max_semi_axis is 0) and overflow is visible only through *d_count.
- * Periodic axes need L >= 2 (2 Rmax + Delta_L) (else LUB_ERR_ARG).
+ * Periodic axes need L >= 2 (2 Rmax + Delta_L), and n <= 429,496,524 (five
+ * sweep items per particle, indexed in int32) (else LUB_ERR_ARG).
  * Uses context scratch (cell grid, counts), grown with cudaMalloc as needed.
  */
 int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,

@@ -260,6 +260,9 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
     if (!d_count) return lub_set_error(ctx, LUB_ERR_ARG, "d_count is NULL");
     if (capacity < 0 || (capacity > 0 && (!pair_i || !pair_j)))
         return lub_set_error(ctx, LUB_ERR_ARG, "bad pair arrays or capacity");
+    // the sweep indexes its five items per particle in int32
+    if (p->n > (INT32_MAX - 1024) / 5)
+        return lub_set_error(ctx, LUB_ERR_ARG, "the pair build takes at most %d particles", (INT32_MAX - 1024) / 5);
     cudaStream_t st = (cudaStream_t)stream;
     PView P = make_pview(p);
     DView D;
