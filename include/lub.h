@@ -202,12 +202,13 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
  * Closest points and signed gap (Sec. III A, with the overlap extension).
  * For each pair, n* maximises g(n) = n.d - sigma_i(n) - sigma_j(n) over unit
  * n (d = minimum-image r_j - r_i), solved by Newton iteration on the sphere
- * from n = d/|d| (the paper's line-of-centres start) or, with
- * LUB_WARM_PREVIOUS, from the n passed in.  Outputs:
+ * from n = d/|d| (the paper's line-of-centres start), with
+ * LUB_WARM_PREVIOUS from the n passed in, or with LUB_WARM_MLP from the
+ * installed network's prediction (lub_mlp_set).  Outputs:
  *   n     [3][capacity] double: unit outward normal of i at y*_i (points i -> j)
  *   gap   [capacity] double: h = g(n*) (< 0 for overlap); y*_j - y*_i = h n
  *   status[capacity] uint8: LUB_ST_* bits
- *   iters [capacity] uint8: Newton iterations taken (FP32 + FP64 stages), or NULL
+ *   iters [capacity] uint8: Newton iterations taken (FP32 + refinement stages), or NULL
  * Walls and two spheres use their closed forms (0 iterations).
  * y*_i = r_i + M_i n / sigma_i(n), y*_j = r_j - M_j n / sigma_j(n), with
  * M = Q diag(r_perp^2, r_perp^2, r_par^2) Q^T.
