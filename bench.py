@@ -33,7 +33,8 @@ WORKLOAD = ("mixed suspension: N=32768 (50% spheres r=4.5, 50% oblates 6,6,3), p
             "L=357.7, 90% of particles attached to an earlier one at a gap log-uniform in [1e-4,1], "
             "pairs with possible gap < 1 (Delta_L=1)")
 
-# algorithmic work per unit ("Roofline"), used for the dominant call
+# algorithmic work per unit (what the method must compute or move, counted
+# from the per-pair formulas), used for the roofline of the dominant call
 FP32_NEWTON_FLOP = 170.0      # one FP32 Newton iteration on the sphere
 FP64_GAP_FLOP = 70.0          # FP64 gap: 2 axes from quaternions, 2 support functions, n.d
 FP64_NEWTON_FLOP = 170.0      # one FP64 Newton iteration (refinement below the switch)
