@@ -95,7 +95,7 @@ def peaks():
             d = json.load(f)
         out.update(d)
         out["src"] = "measured"
-    # non-tensor pipes, measured on this machine's GB300 with an FMA-chain probe
+    # non-tensor pipes, measured on a GB300 with an FMA-chain probe
     out.setdefault("fp32_tflops", 74.6)
     out.setdefault("fp64_tflops", 1.20)
     return out
@@ -908,7 +908,7 @@ def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
         peak = pk["fp64_tflops"]
         return {"kernel": "k_fused (closest + resistance + scatter)", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
-                "peak_src": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+                "peak_src": "FP64 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
     if call == "closest":
         if precision == "mixed":
             f32 = npairs * mean_it * FP32_NEWTON_FLOP
@@ -922,13 +922,13 @@ def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
         peak = pk["fp64_tflops"]
         return {"kernel": "k_closest", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
-                "peak_src": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+                "peak_src": "FP64 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
     if call in ("resistance", "resistance_apply"):
         ach = npairs * RES_FP32_FLOP / t / 1e12
         peak = pk["fp32_tflops"]
         return {"kernel": "k_resistance", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_src": "FP32 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"}
+                "peak_src": "FP32 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
     traffic = None
     if call == "pairs_build":
         b = n * PAIRS_BYTES_PER_PARTICLE + npairs * PAIRS_BYTES_PER_PAIR

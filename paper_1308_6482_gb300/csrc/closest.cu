@@ -277,7 +277,7 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
 }
 
 // One Newton step of g from the FP32 normal n of a work-list pair, in
-// float-float on the FP32 pipe (about 48 bits; this GPU runs FP64 at 1/64 of
+// float-float on the FP32 pipe (about 48 bits; GB300 runs FP64 at 1/64 of
 // the FP32 rate).  It works on the homogeneous g(m) = m.d - sigma_i(m) -
 // sigma_j(m), sigma(m) = sqrt(a2 |m|^2 + e (o.m)^2), at m = n itself (an exact
 // float vector, |n|^2 = 1 + O(1e-7)), with

@@ -116,7 +116,7 @@ __device__ __forceinline__ bool ff_neg_(const ff x) { return x.hi < 0.f || (x.hi
 
 // Cell of one coordinate and the position relative to the cell's centre.  The
 // double coordinate is split once into float-float (four FP64-pipe
-// operations; this GPU runs FP64 at 1/64 of the FP32 rate) and the rest runs
+// operations; GB300 runs FP64 at 1/64 of the FP32 rate) and the rest runs
 // on the FP32 pipe: the wrap into [0, L) on a periodic axis, the cell
 // floor(x / cs) in FP32, corrected by the exact sign of the float-float
 // remainder x - c cs (so a cell holds its positions to about 1e-14 of its
@@ -494,7 +494,7 @@ __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
             // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
             // records (one double subtraction for z - z_w), decided in FP64 only
             // within the margin (the exact test costs some 60 FP64 operations, a
-            // warp's worth of FP64 pipe time on this GPU for a fifth of its lanes)
+            // warp's worth of FP64 pipe time on GB300 for a fifth of its lanes)
             const int i = sorted[s];
             const float4 o = rec1[s];
             const float rm2 = a0.w * a0.w;
