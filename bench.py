@@ -36,8 +36,10 @@ WORKLOAD = ("mixed suspension: N=32768 (50% spheres r=4.5, 50% oblates 6,6,3), p
 # algorithmic work per unit (what the method must compute or move, counted
 # from the per-pair formulas), used for the roofline of the dominant call
 FP32_NEWTON_FLOP = 170.0      # one FP32 Newton iteration on the sphere
-FP64_GAP_FLOP = 70.0          # FP64 gap: 2 axes from quaternions, 2 support functions, n.d
-FP64_NEWTON_FLOP = 170.0      # one FP64 Newton iteration (refinement below the switch)
+FP64_GAP_FLOP = 70.0          # the gap: 2 axes from quaternions, 2 support functions, n.d (FP64 mode)
+FF_GAP_FP32_FLOP = 4 * 70.0   # the same gap in float-float (mixed): about 4 FP32 operations per operation
+FF_STEP_FP32_FLOP = 600.0     # one float-float Newton step (the refinement below the switch, mixed)
+FP64_NEWTON_FLOP = 170.0      # one FP64 Newton iteration (FP64 mode)
 RES_FP32_FLOP = 900.0         # K2 per pair: 2 surface frames, eigenproblem, cubic rotation, K~, u, forces
 PAIRS_BYTES_PER_PARTICLE = 48.0   # pose + shape read once
 PAIRS_BYTES_PER_PAIR = 8.0        # (i, j) written
@@ -895,33 +897,24 @@ def kernels_in_step(precision, form):
 
 def roofline(call, ms, npairs, n, mean_it, fp64_frac, precision, pk):
     t = ms * 1e-3
-    if call == "correct":
-        # fused pass: Newton (FP32 and the FP64 refinement, or FP64), resistance in the mode's precision
+    if call in ("correct", "closest"):
+        # mixed: FP32 Newton, the float-float gap and the float-float refinement
+        # of the pairs below the switch, all on the FP32 pipe; FP64 mode: FP64
+        # Newton and gap (the fused pass adds the resistance in the mode's precision)
+        res = RES_FP32_FLOP if call == "correct" else 0.0
+        name = "k_fused (closest + resistance + scatter)" if call == "correct" else "k_closest"
         if precision == "mixed":
-            f32 = npairs * (mean_it * FP32_NEWTON_FLOP + RES_FP32_FLOP)
-            f64 = npairs * FP64_GAP_FLOP + npairs * fp64_frac * 2 * FP64_NEWTON_FLOP
-        else:
-            f32 = 0.0
-            f64 = npairs * (mean_it * FP64_NEWTON_FLOP + FP64_GAP_FLOP + RES_FP32_FLOP)
-        eq = f64 + f32 * pk["fp64_tflops"] / pk["fp32_tflops"]
-        ach = eq / t / 1e12
+            f32 = npairs * (mean_it * FP32_NEWTON_FLOP + FF_GAP_FP32_FLOP + fp64_frac * FF_STEP_FP32_FLOP + res)
+            ach = f32 / t / 1e12
+            peak = pk["fp32_tflops"]
+            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP32)",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_src": "FP32 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
+        f64 = npairs * (mean_it * FP64_NEWTON_FLOP + FP64_GAP_FLOP + res)
+        ach = f64 / t / 1e12
         peak = pk["fp64_tflops"]
-        return {"kernel": "k_fused (closest + resistance + scatter)", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
-                "peak_src": "FP64 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
-    if call == "closest":
-        if precision == "mixed":
-            f32 = npairs * mean_it * FP32_NEWTON_FLOP
-            f64 = npairs * FP64_GAP_FLOP + npairs * fp64_frac * 2 * FP64_NEWTON_FLOP
-        else:
-            f32 = 0.0
-            f64 = npairs * (mean_it * FP64_NEWTON_FLOP + FP64_GAP_FLOP)
-        # FP64-equivalent work: the time the two pipes need at peak, in FP64 units
-        eq = f64 + f32 * pk["fp64_tflops"] / pk["fp32_tflops"]
-        ach = eq / t / 1e12
-        peak = pk["fp64_tflops"]
-        return {"kernel": "k_closest", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak, "traffic": None,
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64)",
+                "frac": ach / peak, "traffic": None,
                 "peak_src": "FP64 FMA-chain probe on a GB300 (not in MEASURED_PEAKS.json)"}
     if call in ("resistance", "resistance_apply"):
         ach = npairs * RES_FP32_FLOP / t / 1e12
