@@ -317,18 +317,21 @@ def tile_periodic(parts, dom, k, rng, axes=(0, 1, 2)):
     return out, d
 
 
-def large_config(N=1 << 20, phi=0.5, seed=6, k=8, L=1024.0):
+def large_config(N=1 << 20, phi=0.5, seed=6, k=8, L=1024.0, base_only=False):
     """Large dense run: N spheroids (aspect ratio log-uniform in [1/3, 3]) at
     volume fraction phi in an L^3 cube periodic in x, y between plane walls
     at z = 0 and z = L; the equivalent radius fills the cube at phi
     (4.96 for 2^20 particles in 1024^3 at 0.5).  A growth packing of N / k^2
     particles in a slab of L/k x L/k x L (walls included), tiled k x k in x
-    and y."""
+    and y.  base_only: the slab itself (periodic in x, y with period L/k),
+    whose pairs are the large run's pairs up to the tiling."""
     rng = np.random.default_rng(seed)
     r_eq = (phi * L ** 3 / (N * 4.0 / 3.0 * np.pi)) ** (1.0 / 3.0)
     n0 = N // (k * k)
     sh = aspect_shapes(n0, rng, r_eq)
     base, dom, _ = grow(sh, (L / k, L / k, L), periodic=(True, True, False), walls=[(0.0, 1), (L, -1)], seed=seed)
+    if base_only:
+        return base, dom
     return tile_periodic(base, dom, k, rng, axes=(0, 1))
 
 

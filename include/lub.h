@@ -57,11 +57,11 @@ extern "C" {
 
 /* lub_params.precision */
 #define LUB_FP64  0 /* every step in double precision */
-#define LUB_MIXED 1 /* FP32 Newton, curvature, K~ and sums; the gap in
-                       float-float (~48 bits) always; when h/a < fp64_switch
-                       one float-float Newton step refines the normal, and a
-                       pair whose FP32 Newton did not converge is solved in
-                       FP64 */
+#define LUB_MIXED 1 /* FP32 Newton, curvature, K~ and sums; for every pair
+                       the gap and one float-float Newton step of the normal
+                       (~48 bits, on the FP32 pipe) and the normal relative
+                       surface velocity in float-float; a pair whose FP32
+                       Newton did not converge is solved again in FP64 */
 
 /* lub_params.warm_start */
 #define LUB_WARM_NONE     0 /* Newton starts from the line of centres (Sec. III A) */
@@ -75,9 +75,8 @@ extern "C" {
 #define LUB_ST_OVERLAP    1  /* h <= 0 */
 #define LUB_ST_NOCONV     2  /* Newton did not converge within max_newton */
 #define LUB_ST_DEGENERATE 4  /* bad index, non-positive or non-finite shape, coincident centres */
-#define LUB_ST_FP64       8  /* mixed mode: refined beyond FP32 (h/a < fp64_switch:
-                                 float-float Newton step; FP32 not converged:
-                                 FP64 solve) */
+#define LUB_ST_FP64       8  /* mixed mode: the FP32 Newton did not converge and
+                                 the pair was solved again in FP64 */
 
 typedef struct lub_ctx lub_ctx;
 
@@ -121,8 +120,9 @@ typedef struct {
     double eps_c;         /* stiffness of the Hookean repulsion, Eq. lub:frep         */
     double list_cutoff;   /* Delta_L: pairs with a possible gap below this are listed */
     int32_t precision;    /* LUB_FP64 or LUB_MIXED                                     */
-    double fp64_switch;   /* mixed mode: h/a below which Newton is refined beyond
-                             FP32; a = smallest semi-axis of the pair              */
+    double fp64_switch;   /* reserved (kept for the layout): mixed mode refines
+                             every pair's normal beyond FP32, since the force
+                             bound needs it at every gap                          */
     int32_t max_newton;   /* Newton iteration cap per precision stage (1..64)          */
     double newton_tol;    /* step-size tolerance (radians) of the FP32 stage: Newton
                              stops after a step shorter than this (quadratic
@@ -208,7 +208,7 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
  *   n     [3][capacity] double: unit outward normal of i at y*_i (points i -> j)
  *   gap   [capacity] double: h = g(n*) (< 0 for overlap); y*_j - y*_i = h n
  *   status[capacity] uint8: LUB_ST_* bits
- *   iters [capacity] uint8: Newton iterations taken (FP32 + refinement stages), or NULL
+ *   iters [capacity] uint8: Newton iterations taken (the FP32 stage; the FP64 solve for a LUB_ST_FP64 pair), or NULL
  * Walls and two spheres use their closed forms (0 iterations).
  * y*_i = r_i + M_i n / sigma_i(n), y*_j = r_j - M_j n / sigma_j(n), with
  * M = Q diag(r_perp^2, r_perp^2, r_par^2) Q^T.
@@ -460,7 +460,7 @@ int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, cons
  * per SM), the grid being min(work / block, blocks_per_sm x SMs).
  * ------------------------------------------------------------------------- */
 #define LUB_TUNE_CLOSEST_MIXED 0   /* lub_closest_points, LUB_MIXED, FP32 stage */
-#define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, work-list refinement */
+#define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, work list of FP64 solves */
 #define LUB_TUNE_CLOSEST_FP64 2    /* lub_closest_points, LUB_FP64 */
 #define LUB_TUNE_RESISTANCE 3      /* lub_resistance */
 #define LUB_TUNE_APPLY 4           /* lub_apply, atomic form */

@@ -16,14 +16,19 @@
 // LUB_MIXED, one thread per pair:
 //   * Newton iterations in FP32 from the line of centres (or the normal
 //     passed in, for a warm start);
-//   * the gap of every pair in float-float arithmetic (about 48 bits, on the
-//     FP32 pipe): h is stationary in n, so the FP32 normal costs only
-//     O(dn^2), while the subtraction n.d - sigma_i - sigma_j cancels far
-//     beyond FP32 for small gaps;
-//   * pairs with h/a below fp64_switch (and pairs whose FP32 Newton did not
-//     converge) are appended to a compacted work list (one atomic per warp)
-//     and refined by FP64 Newton in a second kernel, so only full warps of
-//     such pairs use the slow FP64 pipe.
+//   * then, for every pair, the gap and one more Newton step with the
+//     gradient in float-float arithmetic (about 48 bits, on the FP32 pipe).
+//     h is stationary in n, so the FP32 normal costs the gap only O(dn^2),
+//     while n.d - sigma_i - sigma_j cancels far beyond FP32 for small gaps.
+//     The normal itself must be better than FP32 at every gap: the normal
+//     relative surface velocity n.(V_j - V_i) is a difference of terms of the
+//     size of the velocities, so an error dn of the normal is an error of
+//     dn |V_j - V_i| in it, and where it nearly cancels a 1e-5 force bound
+//     relative to it needs dn near 1e-9 rad; the float-float step lands
+//     near 1e-13;
+//   * pairs whose FP32 Newton did not converge are appended to a compacted
+//     work list (one atomic per warp) and solved again in FP64 by a second
+//     kernel, so only full warps of such pairs use the slow FP64 pipe.
 // LUB_FP64: the whole solve and gap in double.
 #include "ff.cuh"
 #include "lub_mlp.cuh"
@@ -138,30 +143,6 @@ __device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o
     o[2] = ff_sub(ff_make(1.0f), ff_mul(s, ff_add(two_prod(x, x), two_prod(y, y))));
 }
 
-// sigma(n) = sqrt(R_perp^2 |n|^2 + (R_par^2 - R_perp^2) (o.n)^2) in float-float,
-// for an exactly represented (not necessarily unit) float n with |n|^2 = nn
-__device__ __forceinline__ ff ff_support(const PView &P, int k, const float n[3], ff nn)
-{
-    ff o[3];
-    ff_axis(__ldg(P.qw + k), __ldg(P.qx + k), __ldg(P.qy + k), __ldg(P.qz + k), o);
-    const float a = __ldg(P.rperp + k), c = __ldg(P.rpar + k);
-    const ff on = ff_add(ff_add(ff_mulf(o[0], n[0]), ff_mulf(o[1], n[1])), ff_mulf(o[2], n[2]));
-    const ff a2 = two_prod(a, a);
-    const ff e = ff_sub(two_prod(c, c), a2);
-    return ff_sqrt(ff_add(ff_mul(a2, nn), ff_mul(e, ff_mul(on, on))));
-}
-
-// g at the unit vector n/|n|, in float-float: g is homogeneous of degree one,
-// so g(n/|n|) = g(n) / |n| = g(n) (1 - (|n|^2 - 1)/2 + ...), |n|^2 - 1 ~ 1e-7
-__device__ __forceinline__ ff ff_gap(const PView &P, int i, int j, const ff d[3], const float n[3])
-{
-    const ff nn = ff_add(ff_add(two_prod(n[0], n[0]), two_prod(n[1], n[1])), two_prod(n[2], n[2]));
-    const ff nd = ff_add(ff_add(ff_mulf(d[0], n[0]), ff_mulf(d[1], n[1])), ff_mulf(d[2], n[2]));
-    const ff G = ff_sub(ff_sub(nd, ff_support(P, i, n, nn)), ff_support(P, j, n, nn));
-    const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);
-    return ff_sub(G, ff_make(__fmul_rn(G.hi, __fmul_rn(0.5f, eps))));
-}
-
 // Minimum-image separation r_j - r_i in float-float from the particles'
 // float-float positions (pff: [3][N] (hi, lo)); the image shift is taken from
 // the float part (listed pairs are far from the ambiguous half box).  About
@@ -205,131 +186,62 @@ __device__ __forceinline__ double wall_gap(const PView &P, const DView &D, int i
 // ---------------------------------------------------------------------------
 constexpr int kNoEntry = 0x7fffffff;
 
-// LUB_MIXED, FP32 stage of pair k = (i, j): FP32 Newton + float-float gap.
-// Returns the FP64 work-list entry: k (refine from the FP32 normal), -1-k
-// (full FP64 solve from the line of centres) or kNoEntry.
-template <bool ENS>
-__device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E,
-                                                 const float2 *__restrict__ pff, int i, int j, int k,
-                                                 const double *__restrict__ nin, size_t C, int warm, int maxit,
-                                                 float tol32, float fp64_switch, V3<double> &n64, double &h, int &st,
-                                                 int &nit)
+// The FP32 stage's finish for a particle pair, in float-float on the FP32
+// pipe (GB300 runs FP64 at 1/64 of the FP32 rate): the gap at the FP32 Newton
+// normal n and one Newton step from n with the gradient in float-float.  n
+// is an exact float vector with |n|^2 = 1 + O(1e-7).  With sigma(m) =
+// sqrt(a2 |m|^2 + e (o.m)^2) and M m = a2 m + e (o.m) o, the homogeneous
+// g(m) = m.d - sigma_i(m) - sigma_j(m) has
+//   grad g = R = d - M_i n / sigma_i - M_j n / sigma_j  (y_j - y_i at n),
+//   g(n) = n.R  (Euler: n.M n / sigma = sigma),
+// so the gap at the unit normal is n.R (1 - (|n|^2 - 1)/2 + ...), and the
+// gradient on the sphere is the part of R normal to n, R_t = R - (n.R /
+// |n|^2) n, formed in float-float: it is exactly normal to n, so its FP32
+// components along the FP32 tangents t1, t2 (orthogonal to n to ~1e-7 only)
+// give the tangential gradient to ~1e-14 |d|.  The tangent Hessian and the
+// 2x2 solve run in FP32; their relative error e makes the step contract the
+// error by e as well, so from the FP32 normal's ~1e-7 rad one step lands
+// near 1e-13 rad.  Out: n64 the unit refined normal, h the gap.  Returns the
+// step length (radians), or infinity when the refined normal does not point
+// from i towards j.
+__device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], const ff oj[3], float api, float cpi,
+                                               float apj, float cpj, const V3<float> n, V3<double> &n64, double &h)
 {
-    int entry = kNoEntry;
-    st = 0;
-    nit = 0;
-    n64 = mk<double>(0, 0, 0);
-    h = 0.0;
-    bool alien;
-    const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-    if (alien || pair_bad(P, D, i, j)) {
-        st = LUB_ST_DEGENERATE;
-    } else if (j < 0) {
-        h = wall_gap(P, D, i, -1 - j, n64);
-    } else {
-        ff dff[3];
-        ff_separation(pff, (size_t)P.n, i, j, D, dff);
-        const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
-        const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
-        const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
-        const ff dd = ff_add(ff_add(ff_mul(dff[0], dff[0]), ff_mul(dff[1], dff[1])), ff_mul(dff[2], dff[2]));
-        if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
-            st = LUB_ST_DEGENERATE;
-        } else if (rpi == rqi && rpj == rqj) {
-            // two spheres: n = d/|d|, h = |d| - R_i - R_j
-            const ff dl = ff_sqrt(dd);
-            const float inv = 1.0f / dl.hi;
-            n64 = mk<double>(df.x * inv, df.y * inv, df.z * inv);
-            h = ff_to_double(ff_sub(ff_sub(dl, ff_make(rpi)), ff_make(rpj)));
-        } else {
-            const Shape<float> si = load_shape<float>(P, i), sj = load_shape<float>(P, j);
-            const float dl = sqrtf(dd.hi);
-            V3<float> n = scl(1.0f / dl, df);
-            if (warm) {
-                const V3<float> w0 = mk<float>((float)nin[k], (float)nin[C + k], (float)nin[2 * C + k]);
-                const float wl2 = dot(w0, w0);
-                // a start on the far hemisphere falls back to the line of centres
-                if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2) && dot(w0, df) > 0.f) n = scl(rsqrtf(wl2), w0);
-            }
-            const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
-            const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
-            nit = o.iters;
-            const float nv[3] = {n.x, n.y, n.z};
-            const ff hff = ff_gap(P, i, j, dff, nv);
-            h = ff_to_double(hff);
-            // unit normal for the output (|n|^2 - 1 ~ 1e-7)
-            const float nn = dot(n, n);
-            const float f = 1.5f - 0.5f * nn;
-            n64 = mk<double>(n.x * f, n.y * f, n.z * f);
-            const float amin = fminf(fminf(rpi, rqi), fminf(rpj, rqj));
-            // (the switch compared in FP32: a heuristic threshold, no FP64 pipe)
-            if (!o.converged || !isfinite(hff.hi))
-                entry = -1 - k;
-            else if (hff.hi < fp64_switch * amin)
-                entry = k;
-            if (entry != kNoEntry) st |= LUB_ST_FP64;  // on the work list (refined next)
-            // consistency check of Sec. III A: the normals point to the other centre
-            if (entry == kNoEntry && !(dot(n, df) > 0.f)) st |= LUB_ST_NOCONV;
-        }
-    }
-    if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
-    return entry;
-}
-
-// One Newton step of g from the FP32 normal n of a work-list pair, in
-// float-float on the FP32 pipe (about 48 bits; GB300 runs FP64 at 1/64 of
-// the FP32 rate).  It works on the homogeneous g(m) = m.d - sigma_i(m) -
-// sigma_j(m), sigma(m) = sqrt(a2 |m|^2 + e (o.m)^2), at m = n itself (an exact
-// float vector, |n|^2 = 1 + O(1e-7)), with
-//   t.grad sigma = (a2 (t.n) + e (o.n)(o.t)) / sigma.
-// The tangents t1, t2 (FP32) are orthogonal to n to about 1e-7 only, so the
-// gradient is projected: G_a = t_a.grad g - (t_a.n) g / |n|^2 (n.grad g = g by
-// Euler's theorem), which vanishes exactly at the stationary point.  G to
-// about 1e-14 absolute; the tangent Hessian and the 2x2 solve in FP32, whose
-// relative error e makes the step contract the error by e as well, so from
-// 1e-7 one step lands near 1e-14.  The refined unit normal goes to n64.
-// Returns the step length (radians), or infinity when the normal does not
-// point from i towards j.
-__device__ __forceinline__ float polish_ff(const PView &P, const float2 *__restrict__ pff, const DView &D, int i,
-                                           int j, const V3<float> n, V3<double> &n64)
-{
-    ff d[3], oi[3], oj[3];
-    ff_separation(pff, (size_t)P.n, i, j, D, d);
-    ff_axis(__ldg(P.qw + i), __ldg(P.qx + i), __ldg(P.qy + i), __ldg(P.qz + i), oi);
-    ff_axis(__ldg(P.qw + j), __ldg(P.qx + j), __ldg(P.qy + j), __ldg(P.qz + j), oj);
-    const float api = __ldg(P.rperp + i), cpi = __ldg(P.rpar + i);
-    const float apj = __ldg(P.rperp + j), cpj = __ldg(P.rpar + j);
     const ff a2i = two_prod(api, api), ei = ff_sub(two_prod(cpi, cpi), a2i);
     const ff a2j = two_prod(apj, apj), ej = ff_sub(two_prod(cpj, cpj), a2j);
     const float nv[3] = {n.x, n.y, n.z};
     const ff nn = ff_dot3_exact(nv, nv);
     const ff ci = ff_dot3f(oi, nv), cj = ff_dot3f(oj, nv);
-    const ff si = ff_sqrt(ff_add(ff_mul(a2i, nn), ff_mul(ei, ff_mul(ci, ci))));
-    const ff sj = ff_sqrt(ff_add(ff_mul(a2j, nn), ff_mul(ej, ff_mul(cj, cj))));
-    const ff ri = ff_rcp(si), rj = ff_rcp(sj);
-    const ff g = ff_sub(ff_sub(ff_dot3f(d, nv), si), sj);
-    const float lam = __fdiv_rn(g.hi, nn.hi);
+    const ff ri = ff_rsqrt(ff_add(ff_mul(a2i, nn), ff_mul(ei, ff_mul(ci, ci))));  // 1 / sigma_i
+    const ff rj = ff_rsqrt(ff_add(ff_mul(a2j, nn), ff_mul(ej, ff_mul(cj, cj))));
+    const ff al = ff_add(ff_mul(a2i, ri), ff_mul(a2j, rj));  // a2_i / sigma_i + a2_j / sigma_j
+    const ff bi = ff_mul(ff_mul(ei, ci), ri), bj = ff_mul(ff_mul(ej, cj), rj);
+    ff R[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        R[a] = ff_sub(ff_sub(ff_sub(d[a], ff_mulf(al, nv[a])), ff_mul(bi, oi[a])), ff_mul(bj, oj[a]));
+    const ff nR = ff_dot3f(R, nv);
+    const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);  // |n|^2 - 1
+    h = ff_to_double(ff_sub(nR, ff_make(__fmul_rn(nR.hi, __fmul_rn(0.5f, eps)))));
+    // n.R / |n|^2 to ~eps^2 relative; R_t in float-float
+    const ff lam = ff_sub(nR, ff_make(__fmul_rn(nR.hi, eps)));
+    float Rt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const ff r = ff_sub(R[a], ff_mulf(lam, nv[a]));
+        Rt[a] = __fadd_rn(r.hi, r.lo);
+    }
     const V3<float> t1 = perp_unit(n), t2 = cross(n, t1);
-    const float tv1[3] = {t1.x, t1.y, t1.z}, tv2[3] = {t2.x, t2.y, t2.z};
-    // projected tangential gradient along t, and o_i.t, o_j.t in FP32 for the Hessian
-    auto grad_t = [&](const float tv[3], float &uti, float &utj) -> float {
-        const ff tn = ff_dot3_exact(tv, nv);
-        const ff toi = ff_dot3f(oi, tv), toj = ff_dot3f(oj, tv);
-        uti = toi.hi;
-        utj = toj.hi;
-        const ff gi = ff_mul(ff_add(ff_mul(a2i, tn), ff_mul(ei, ff_mul(ci, toi))), ri);
-        const ff gj = ff_mul(ff_add(ff_mul(a2j, tn), ff_mul(ej, ff_mul(cj, toj))), rj);
-        const ff G = ff_sub(ff_sub(ff_dot3f(d, tv), gi), gj);
-        return __fadd_rn(__fsub_rn(G.hi, __fmul_rn(tn.hi, lam)), G.lo);
-    };
-    float u1i, u1j, u2i, u2j;
-    const float G1 = grad_t(tv1, u1i, u1j), G2 = grad_t(tv2, u2i, u2j);
+    const float G1 = t1.x * Rt[0] + t1.y * Rt[1] + t1.z * Rt[2];
+    const float G2 = t2.x * Rt[0] + t2.y * Rt[1] + t2.z * Rt[2];
     // P = -Hess_t g in FP32 (as in newton_sphere)
-    const float rif = ri.hi, rjf = rj.hi;
+    const V3<float> ofi = mk<float>(oi[0].hi, oi[1].hi, oi[2].hi), ofj = mk<float>(oj[0].hi, oj[1].hi, oj[2].hi);
+    const float u1i = dot(ofi, t1), u2i = dot(ofi, t2), u1j = dot(ofj, t1), u2j = dot(ofj, t2);
+    const float rif = ri.hi, rjf = rj.hi, g = nR.hi;
     const float Ai = a2i.hi * rif, Aj = a2j.hi * rjf;
     const float Ei = ei.hi * rif * rif, Ej = ej.hi * rjf * rjf;
-    const float P11 = Ai * (1.f + Ei * u1i * u1i) + Aj * (1.f + Ej * u1j * u1j) + g.hi;
-    const float P22 = Ai * (1.f + Ei * u2i * u2i) + Aj * (1.f + Ej * u2j * u2j) + g.hi;
+    const float P11 = Ai * (1.f + Ei * u1i * u1i) + Aj * (1.f + Ej * u1j * u1j) + g;
+    const float P22 = Ai * (1.f + Ei * u2i * u2i) + Aj * (1.f + Ej * u2j * u2j) + g;
     const float P12 = Ai * Ei * u1i * u2i + Aj * Ej * u1j * u2j;
     const float det = P11 * P22 - P12 * P12;
     float s1, s2;
@@ -343,42 +255,93 @@ __device__ __forceinline__ float polish_ff(const PView &P, const float2 *__restr
         s2 = G2 * sc;
     }
     // n + s1 t1 + s2 t2 in float-float (the step is of order 1e-7), normalised
+    const float tv1[3] = {t1.x, t1.y, t1.z}, tv2[3] = {t2.x, t2.y, t2.z};
     ff m[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) m[a] = two_sum(nv[a], __fmaf_rn(s1, tv1[a], __fmul_rn(s2, tv2[a])));
-    const ff m2 = ff_add(ff_add(ff_mul(m[0], m[0]), ff_mul(m[1], m[1])), ff_mul(m[2], m[2]));
-    const ff im = ff_rcp(ff_sqrt(m2));
+    const ff im = ff_rsqrt(ff_dot3(m, m));
     n64 = mk<double>(ff_to_double(ff_mul(m[0], im)), ff_to_double(ff_mul(m[1], im)), ff_to_double(ff_mul(m[2], im)));
     const float step = sqrtf(s1 * s1 + s2 * s2);
     const float nd = m[0].hi * d[0].hi + m[1].hi * d[1].hi + m[2].hi * d[2].hi;
     return (nd > 0.f && isfinite(step)) ? step : INFINITY;
 }
 
-// LUB_MIXED, refinement of a work-list pair: one float-float Newton step from
-// the FP32 normal nn (the gap h_in of the FP32 stage stands: g is stationary
-// in n, so the FP32 normal's error of ~1e-7 rad changes it by ~1e-14 of the
-// sizes), or, if full, a complete FP64 solve and gap from the line of centres
+// LUB_MIXED, FP32 stage of pair k = (i, j): FP32 Newton, then the
+// float-float gap and Newton step (spheres: the float-float line of centres).
+// Returns the FP64 work-list entry -1-k (a full FP64 solve from the line of
+// centres, for a pair whose FP32 Newton did not converge) or kNoEntry.
 template <bool ENS>
-__device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E,
-                                           const float2 *__restrict__ pff, int i, int j, bool full, V3<double> nn,
-                                           double h_in, int st_in, int maxit, V3<double> &n64, double &h, int &st,
-                                           int &nit)
+__device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E,
+                                                 const float2 *__restrict__ pff, int i, int j, int k,
+                                                 const double *__restrict__ nin, size_t C, int warm, int maxit,
+                                                 float tol32, V3<double> &n64, double &h, int &st, int &nit)
+{
+    int entry = kNoEntry;
+    st = 0;
+    nit = 0;
+    n64 = mk<double>(0, 0, 0);
+    h = 0.0;
+    bool alien;
+    const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
+    if (alien || pair_bad(P, D, i, j)) {
+        st = LUB_ST_DEGENERATE;
+    } else if (j < 0) {
+        h = wall_gap(P, D, i, -1 - j, n64);
+    } else {
+        const size_t N = (size_t)P.n;
+        ff dff[3];
+        ff_separation(pff, N, i, j, D, dff);
+        const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
+        const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
+        const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
+        const ff dd = ff_dot3(dff, dff);
+        if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
+            st = LUB_ST_DEGENERATE;
+        } else if (rpi == rqi && rpj == rqj) {
+            // two spheres: n = d/|d|, h = |d| - R_i - R_j, in float-float
+            const ff rs = ff_rsqrt(dd);
+            n64 = mk<double>(ff_to_double(ff_mul(dff[0], rs)), ff_to_double(ff_mul(dff[1], rs)),
+                             ff_to_double(ff_mul(dff[2], rs)));
+            h = ff_to_double(ff_sub(ff_sub(ff_mul(dd, rs), ff_make(rpi)), ff_make(rpj)));
+        } else {
+            ff oi[3], oj[3];
+            ff_axis_of(pff, N, i, oi);
+            ff_axis_of(pff, N, j, oj);
+            const Shape<float> si = shape_ff(oi, rpi, rqi), sj = shape_ff(oj, rpj, rqj);
+            const float dl = sqrtf(dd.hi);
+            V3<float> n = scl(1.0f / dl, df);
+            if (warm) {
+                const V3<float> w0 = mk<float>((float)nin[k], (float)nin[C + k], (float)nin[2 * C + k]);
+                const float wl2 = dot(w0, w0);
+                // a start on the far hemisphere falls back to the line of centres
+                if (wl2 > 0.25f && wl2 < 4.0f && isfinite(wl2) && dot(w0, df) > 0.f) n = scl(rsqrtf(wl2), w0);
+            }
+            const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
+            const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
+            nit = o.iters;
+            const float step = polish_gap_ff(dff, oi, oj, rqi, rpi, rqj, rpj, n, n64, h);
+            if (!o.converged || !(step < 1e-5f) || !isfinite(h)) {
+                entry = -1 - k;
+                st |= LUB_ST_FP64;  // on the work list (solved again in FP64 next)
+            }
+        }
+    }
+    if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
+    return entry;
+}
+
+// LUB_MIXED, a work-list pair (its FP32 Newton did not converge): a
+// complete FP64 solve and gap from the line of centres
+template <bool ENS>
+__device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, int maxit,
+                                           V3<double> &n64, double &h, int &st, int &nit)
 {
     bool alien;
     const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-    if (!full) {
-        const V3<float> n32 = mk<float>((float)nn.x, (float)nn.y, (float)nn.z);
-        const bool converged = polish_ff(P, pff, D, i, j, n32, n64) < 1e-5f;
-        nit = 1;
-        h = h_in;
-        st = st_in | LUB_ST_FP64;
-        if (!converged) st |= LUB_ST_NOCONV;
-        return;
-    }
     const V3<double> d = min_image(D, sub(load_pos(P, j), load_pos(P, i)));
     const double dl = sqrt(dot(d, d));
     const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
-    nn = scl(1.0 / dl, d);
+    V3<double> nn = scl(1.0 / dl, d);
     const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
     const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
     nit = o.iters;
@@ -449,52 +412,38 @@ __device__ __forceinline__ void store_pair(double *__restrict__ nout, double *__
     if (iters) iters[k] = (uint8_t)(nit > 255 ? 255 : nit);
 }
 
-// Compacted append to the work list (warp-collective).  One-step
-// polishes (entry k) fill the list from the front, full solves (entry -1-k,
-// several iterations each) from the back, so each kind runs in warps of its
-// own instead of every warp waiting for one full solve.  wl_count[0]: front
-// entries, wl_count[1]: back entries; the list holds cap entries.
+// Compacted append to the work list (warp-collective): entries -1-k (full
+// FP64 solves), one atomic per warp.  wl_count[0]: entries; the list holds
+// cap entries.
 __device__ __forceinline__ void worklist_append(int entry, int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
                                                 int cap)
 {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    const bool polish = entry != kNoEntry && entry >= 0, full = entry != kNoEntry && entry < 0;
-    const unsigned mp = __ballot_sync(0xffffffffu, polish), mf = __ballot_sync(0xffffffffu, full);
-    if (mp) {
-        int wbase = 0;
-        const int leader = __ffs(mp) - 1;
-        if (lane == leader) wbase = atomicAdd(wl_count, __popc(mp));
-        wbase = __shfl_sync(0xffffffffu, wbase, leader);
-        if (polish) wl[wbase + __popc(mp & below)] = entry;
-    }
+    const bool full = entry != kNoEntry;
+    const unsigned mf = __ballot_sync(0xffffffffu, full);
     if (mf) {
         int wbase = 0;
         const int leader = __ffs(mf) - 1;
-        if (lane == leader) wbase = atomicAdd(wl_count + 1, __popc(mf));
+        if (lane == leader) wbase = atomicAdd(wl_count, __popc(mf));
         wbase = __shfl_sync(0xffffffffu, wbase, leader);
-        if (full) wl[cap - 1 - (wbase + __popc(mf & below))] = entry;
+        if (full) wl[wbase + __popc(mf & below)] = entry;
     }
 }
 
-// work-list entry q of [front entries | back entries], q < wl_total(...)
 __device__ __forceinline__ int wl_total(const int32_t *__restrict__ wl_count, int cap)
 {
-    return min(wl_count[0] + wl_count[1], cap);
-}
-__device__ __forceinline__ int wl_entry(const int32_t *__restrict__ wl_count, const int32_t *__restrict__ wl, int cap,
-                                        int q)
-{
-    const int nf = wl_count[0];
-    return q < nf ? wl[q] : wl[cap - 1 - (q - nf)];
+    return min(wl_count[0], cap);
 }
 
 // ---------------------------------------------------------------------------
 // lub_closest_points kernels
 // ---------------------------------------------------------------------------
-// float-float copies (hi, lo) of the particle positions, [3][n], for the
-// separations of the FP32 stage
-__global__ void __launch_bounds__(256) k_pos_ff(PView P, float2 *__restrict__ out)
+// The per-call particle table of the FP32 stage and the FP32 resistance:
+// float-float copies (hi, lo) of the positions, [3][n], then of the
+// symmetry axes, [3][n] (one float-float axis per particle instead of one per
+// pair and side)
+__global__ void __launch_bounds__(256) k_particles_ff(PView P, float2 *__restrict__ out)
 {
     pdl_wait();
     pdl_trigger();
@@ -506,6 +455,10 @@ __global__ void __launch_bounds__(256) k_pos_ff(PView P, float2 *__restrict__ ou
             const ff p = ff_from_double(v[a]);
             out[a * N + i] = make_float2(p.hi, p.lo);
         }
+        ff o[3];
+        ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[(3 + a) * N + i] = make_float2(o[a].hi, o[a].lo);
     }
 }
 
@@ -515,7 +468,7 @@ __global__ void __launch_bounds__(128, 6) k_closest_mixed(PView P, const __grid_
                                                        const int32_t *__restrict__ d_count, int32_t cap,
                                                        double *__restrict__ nout, double *__restrict__ gap,
                                                        uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
-                                                       int maxit, float tol32, float fp64_switch, int warm,
+                                                       int maxit, float tol32, int warm,
                                                        int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
                                                        const float2 *__restrict__ pff)
 {
@@ -532,8 +485,7 @@ __global__ void __launch_bounds__(128, 6) k_closest_mixed(PView P, const __grid_
             V3<double> n64;
             double h;
             int st, nit;
-            entry = closest_mixed_one<ENS>(P, D0, E, pff, i, j, k, nout, C, warm, maxit, tol32, fp64_switch, n64, h, st,
-                                           nit);
+            entry = closest_mixed_one<ENS>(P, D0, E, pff, i, j, k, nout, C, warm, maxit, tol32, n64, h, st, nit);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
         }
         worklist_append(entry, wl_count, wl, cap);
@@ -547,27 +499,19 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
                                                         double *__restrict__ nout, double *__restrict__ gap,
                                                         uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                         int maxit, const int32_t *__restrict__ wl_count,
-                                                        const int32_t *__restrict__ wl,
-                                                        const float2 *__restrict__ pff)
+                                                        const int32_t *__restrict__ wl)
 {
     pdl_wait();
     pdl_trigger();
     const int count = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-        const int v = wl_entry(wl_count, wl, cap, q);
-        const bool full = v < 0;
-        const int k = full ? -1 - v : v;
+        const int k = -1 - wl[q];
         V3<double> n64;
         double h;
         int st, nit;
-        refine_one<ENS>(P, D0, E, pff, pi[k], pj[k], full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]),
-                        full ? 0.0 : gap[k], full ? 0 : status[k], maxit, n64, h, st, nit);
-        store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
-        if (iters) {
-            const int total = (full ? 0 : iters[k]) + nit;
-            iters[k] = (uint8_t)(total > 255 ? 255 : total);
-        }
+        refine_one<ENS>(P, D0, E, pi[k], pj[k], maxit, n64, h, st, nit);
+        store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
     }
 }
 
@@ -603,8 +547,7 @@ template <bool ENS>
 __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_mixed_learned(
     PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
     const int32_t *__restrict__ d_count, int32_t cap, double *__restrict__ nout, double *__restrict__ gap,
-    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, float tol32, float fp64_switch,
-    int32_t *__restrict__ wl_count, int32_t *__restrict__ wl, const float2 *__restrict__ pff, MlpDevice M)
+    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, float tol32, int32_t *__restrict__ wl_count, int32_t *__restrict__ wl, const float2 *__restrict__ pff, MlpDevice M)
 {
     pdl_wait();
     pdl_trigger();
@@ -627,7 +570,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_mixed_learned(
             double h;
             int st, nit;
             entry = closest_mixed_one<ENS>(P, D0, E, pff, __ldg(pi + k), __ldg(pj + k), k, nout, C, 1, maxit, tol32,
-                                           fp64_switch, n64, h, st, nit);
+                                           n64, h, st, nit);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
         }
         worklist_append(entry, wl_count, wl, cap);
@@ -700,13 +643,12 @@ template <typename T>
 __device__ __forceinline__ void force_and_scatter(const PView &P, const RParams &R, bool done, int i, int j,
                                                   const V3<double> &n64, double h, int &st, T *__restrict__ FT,
                                                   T *__restrict__ lever, size_t C, int k, T *__restrict__ force,
-                                                  T *__restrict__ torque)
+                                                  T *__restrict__ torque, const float2 *__restrict__ pff)
 {
     T out[12];
     T ci[6] = {0, 0, 0, 0, 0, 0}, cj[6] = {0, 0, 0, 0, 0, 0};
     if (done) {
-        const V3<T> n = mk<T>((T)n64.x, (T)n64.y, (T)n64.z);
-        pair_force<T>(P, R, i, j, n, h, st, out);
+        pair_force<T>(P, R, i, j, n64, h, st, out, pff);
         store_force(FT, lever, C, k, out);
         side_contrib(out, 0, ci);
         if (j >= 0) side_contrib(out, 1, cj);
@@ -719,7 +661,7 @@ __device__ __forceinline__ void force_and_scatter(const PView &P, const RParams 
 // The fused pass in mixed precision after the FP32 stage (k_closest_mixed,
 // which leaves every pair's normal, gap and status and marks the work-list
 // pairs with LUB_ST_FP64): warps take 32 items at a time from two queues,
-// the work-list entries (the refinement, then the pair's force and scatter),
+// the work-list entries (the FP64 solve, then the pair's force and scatter),
 // then the other pairs (force and scatter from the stored normal and gap).
 // queue: two counters, zero at the launch.
 template <bool ENS>
@@ -739,8 +681,8 @@ __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_con
     const int count = pair_count(d_count, cap), nwl = wl_total(wl_count, cap);
     const size_t C = (size_t)cap;
     const int lane = threadIdx.x & 31;
-    // every warp takes work-list entries first (the refinement is FP32-pipe
-    // work), then the other pairs
+    // every warp takes work-list entries first (the longest items), then the
+    // other pairs
     for (;;) {
         int q0 = 0;
         if (lane == 0) q0 = atomicAdd(queue, 32);
@@ -749,26 +691,16 @@ __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_con
         const int q = q0 + lane;
         const bool active = q < nwl;
         int i = -1, j = -1, k = 0, st = 0, nit = 0;
-        bool full = false;
         V3<double> n64 = mk<double>(0, 0, 0);
         double h = 0.0;
         if (active) {
-            const int v = wl_entry(wl_count, wl, cap, q);
-            full = v < 0;
-            k = full ? -1 - v : v;
+            k = -1 - wl[q];
             i = pi[k];
             j = pj[k];
-            refine_one<ENS>(P, D0, E, pff, i, j, full, mk<double>(nout[k], nout[C + k], nout[2 * C + k]),
-                            full ? 0.0 : gap[k], full ? 0 : status[k], maxit, n64, h, st, nit);
+            refine_one<ENS>(P, D0, E, i, j, maxit, n64, h, st, nit);
         }
-        force_and_scatter<float>(P, R, active, i, j, n64, h, st, FT, lever, C, k, force, torque);
-        if (active) {
-            store_pair(nout, gap, status, nullptr, C, k, n64, h, st, 0);
-            if (iters) {
-                const int total = (full ? 0 : iters[k]) + nit;
-                iters[k] = (uint8_t)(total > 255 ? 255 : total);
-            }
-        }
+        force_and_scatter<float>(P, R, active, i, j, n64, h, st, FT, lever, C, k, force, torque, pff);
+        if (active) store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
     }
     for (;;) {
         int k0 = 0;
@@ -791,7 +723,7 @@ __global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_con
                 h = gap[k];
             }
         }
-        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque);
+        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque, pff);
     }
 }
 
@@ -818,7 +750,7 @@ __global__ void __launch_bounds__(128) k_fused_fp64(PView P, const __grid_consta
             j = __ldg(pj + k);
             closest_fp64_one<ENS>(P, D0, E, i, j, k, nout, C, warm, maxit, n64, h, st, nit);
         }
-        force_and_scatter<double>(P, R, k < count, i, j, n64, h, st, FT, lever, C, k, force, torque);
+        force_and_scatter<double>(P, R, k < count, i, j, n64, h, st, FT, lever, C, k, force, torque, nullptr);
         if (k < count) store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
     }
 }
@@ -840,16 +772,28 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
     return LUB_OK;
 }
 
-// The work list of the mixed mode in the context scratch: counters [front, back, queue 0,
-// queue 1] and cap entries; with gap_in/status_in, also a gap and a status
-// array for callers that pass none (the fused pass needs them between its
-// kernels).
+}  // namespace
+
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st)
+{
+    if (P.n == 0) return LUB_OK;
+    return lub_check_cuda(ctx, launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P, out),
+                          "particle table launch");
+}
+
+namespace {
+
+// The work list of the mixed mode in the context scratch: counters [entries,
+// unused, queue 0, queue 1] and cap entries; with gap_in/status_in, also a
+// gap and a status array for callers that pass none (the fused pass needs
+// them between its kernels); with P, the per-call particle table (pff:
+// float-float positions and axes, 48 bytes per particle).
 int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl,
               double **gap_in = nullptr, uint8_t **status_in = nullptr, const PView *P = nullptr,
               float2 **pff = nullptr)
 {
     const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = ((8 * (size_t)cap + 255) / 256) * 256,
-                 b_st = (((size_t)cap + 255) / 256) * 256, b_pos = P ? 24 * (size_t)P->n : 0;
+                 b_st = (((size_t)cap + 255) / 256) * 256, b_pos = P ? particles_ff_bytes(P->n) : 0;
     int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_gap + b_st + b_pos);
     if (rc) return rc;
     char *base = (char *)ctx->scratch;
@@ -859,11 +803,8 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
     rc = zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
     if (rc || !P) return rc;
-    // the particles' float-float positions for the FP32 stage
     *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
-    if (P->n == 0) return LUB_OK;
-    return lub_check_cuda(ctx, launch_pdl(k_pos_ff, grid_for(P->n, 256, ctx->num_sms, 8), 256, 0, st, *P, *pff),
-                          "positions launch");
+    return launch_particles_ff(ctx, *P, *pff, st);
 }
 
 template <bool ENS>
@@ -886,17 +827,17 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
             if ((rc = learned_smem(ctx, k_closest_mixed_learned<ENS>, 16 << ENS))) return rc;
             (void)launch_pdl(k_closest_mixed_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E,
                              pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton, (float)prm.newton_tol,
-                             (float)prm.fp64_switch, wl_count, wl, (const float2 *)pff, *(const MlpDevice *)ctx->mlp);
+                             wl_count, wl, (const float2 *)pff, *(const MlpDevice *)ctx->mlp);
         } else {
             const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
             (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap,
-                             status, iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm,
-                             wl_count, wl, (const float2 *)pff);
+                             status, iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl,
+                             (const float2 *)pff);
         }
         // small blocks so the (short) work list spreads over every SM
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
         (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
-                         prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl, (const float2 *)pff);
+                         prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl);
     } else if (fused_mlp) {
         if ((rc = learned_smem(ctx, k_closest_fp64_learned<ENS>, 64 << ENS))) return rc;
         (void)launch_pdl(k_closest_fp64_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E, pi,
@@ -925,15 +866,14 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
     const RParams R = make_rparams(prm);
     if (prm.precision == LUB_MIXED) {
-        // the FP32 stage, then the work list's refinement and every pair's force
+        // the FP32 stage, then the work list's FP64 solves and every pair's force
         // in one queue-driven launch (gap and status in the context when not given)
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status, &P, &pff))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
         (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
-                         iters, prm.max_newton, (float)prm.newton_tol, (float)prm.fp64_switch, warm, wl_count, wl,
-                         (const float2 *)pff);
+                         iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl, (const float2 *)pff);
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
         const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
         (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,

@@ -110,6 +110,21 @@ __device__ __forceinline__ ff ff_rcp(ff x)
     return fast_two_sum(r, __fmul_rn(r, e.hi));
 }
 
+// 1 / sqrt(x) of a positive value: r = rsqrt(hi), one Newton correction
+// r + r (1 - x r^2) / 2 with the residual 1 - x r^2 formed in float-float
+__device__ __forceinline__ ff ff_rsqrt(ff x)
+{
+    const float r = rsqrtf(x.hi);
+    const ff e = ff_sub(ff_make(1.0f), ff_mulf(ff_mulf(x, r), r));
+    return fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e.hi));
+}
+
+// a . b of two float-float vectors
+__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3])
+{
+    return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
 // a . b for a float-float vector a and a float vector b
 __device__ __forceinline__ ff ff_dot3f(const ff a[3], const float b[3])
 {

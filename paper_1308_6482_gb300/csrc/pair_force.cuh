@@ -11,6 +11,73 @@
 
 namespace {
 
+// the float-float symmetry axis of particle k from a per-call particle table
+// (pff: [3][N] float-float positions, then [3][N] float-float axes)
+__device__ __forceinline__ void ff_axis_of(const float2 *__restrict__ pff, size_t N, int k, ff o[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 v = __ldg(pff + (3 + a) * N + k);
+        o[a] = ff{v.x, v.y};
+    }
+}
+
+// FP32 shape with the axis rounded from its float-float value
+__device__ __forceinline__ Shape<float> shape_ff(const ff o[3], float rpar, float rperp)
+{
+    Shape<float> s;
+    s.o = mk<float>(o[0].hi, o[1].hi, o[2].hi);
+    s.rpar = rpar;
+    s.rperp = rperp;
+    s.a2 = rperp * rperp;
+    s.e = rpar * rpar - s.a2;
+    return s;
+}
+
+// n.(w x rho) for the support offset rho = +-M n / sigma(n) of a spheroid (+
+// for i at n, - for j at -n), without its sign: M n = a2 n + e (o.n) o and
+// n.(w x n) = 0, so only k n.(w x o) with k = e (o.n) / sigma(n) remains.
+// Float-float, for a unit float-float n, the float-float axis o and the
+// (exact) float angular velocity w; zero for a sphere (e = 0).
+__device__ __forceinline__ ff rot_normal_ff(const ff n[3], const ff o[3], float rpar, float rperp, float wx, float wy,
+                                            float wz)
+{
+    if (rpar == rperp) return ff_make(0.0f);
+    const ff a2 = two_prod(rperp, rperp), e = ff_sub(two_prod(rpar, rpar), a2);
+    const ff c = ff_dot3(o, n);
+    const ff k = ff_mul(ff_mul(e, c), ff_rsqrt(ff_add(a2, ff_mul(e, ff_mul(c, c)))));
+    const ff wo[3] = {ff_sub(ff_mulf(o[2], wy), ff_mulf(o[1], wz)), ff_sub(ff_mulf(o[0], wz), ff_mulf(o[2], wx)),
+                      ff_sub(ff_mulf(o[1], wx), ff_mulf(o[0], wy))};
+    return ff_mul(k, ff_dot3(n, wo));
+}
+
+// The normal relative surface velocity u3 = n.(V_j - V_i), V = v + w x (y* - r)
+// (Sec. III B), in float-float.  It is a difference of terms of the size of
+// the velocities and nearly cancels for some pairs, where the force bound
+// relative to it asks for more than FP32: with rho_i = M_i n / sigma_i,
+// rho_j = -M_j n / sigma_j,
+//   u3 = n.(v_j - v_i) - k_i n.(w_i x o_i) - k_j n.(w_j x o_j),
+// v_j - v_i exact (TwoSum), the rest in float-float.  j < 0: a wall at rest.
+__device__ __forceinline__ float normal_velocity_ff(const PView &P, const float2 *__restrict__ pff, int i, int j,
+                                                    const ff n[3], const ff oi[3], const ff oj[3])
+{
+    const float vi[3] = {__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i)};
+    float vj[3] = {0.f, 0.f, 0.f};
+    ff u = ff_make(0.0f);
+    if (j >= 0) {
+        vj[0] = __ldg(P.vx + j);
+        vj[1] = __ldg(P.vy + j);
+        vj[2] = __ldg(P.vz + j);
+        u = ff_neg(rot_normal_ff(n, oj, __ldg(P.rpar + j), __ldg(P.rperp + j), __ldg(P.wx + j), __ldg(P.wy + j),
+                                 __ldg(P.wz + j)));
+    }
+    const ff dv[3] = {two_sum(vj[0], -vi[0]), two_sum(vj[1], -vi[1]), two_sum(vj[2], -vi[2])};
+    u = ff_add(u, ff_dot3(n, dv));
+    u = ff_sub(u, rot_normal_ff(n, oi, __ldg(P.rpar + i), __ldg(P.rperp + i), __ldg(P.wx + i), __ldg(P.wy + i),
+                                __ldg(P.wz + i)));
+    return __fadd_rn(u.hi, u.lo);
+}
+
 template <typename T>
 struct Surf {
     V3<T> x1;
@@ -119,13 +186,17 @@ __device__ __forceinline__ void m_rot(T c, T s, T a0, T a1, T a2, T a3, T m[4])
 }
 
 // Force and torque on i (lab frame, torque about y*_i) and the lever arms of
-// one pair from its normal n (direction of h, outward from i) and gap h:
+// one pair from its normal n64 (direction of h, outward from i) and gap h:
 // out = (F_i, T_i, y*_i - r_i, y*_j - r_j).  st carries the pair's status
 // bits in and gains OVERLAP when h <= 0 without a contact model; pairs with
-// NOCONV or DEGENERATE (or such an overlap) give zeros.
+// NOCONV or DEGENERATE (or such an overlap) give zeros.  T = float (mixed
+// mode) needs the per-call particle table pff (float-float axes): the frames,
+// curvatures and K~ run in FP32 with the axes rounded from it, the normal
+// relative velocity u3 in float-float (normal_velocity_ff).  T = double
+// ignores pff.
 template <typename T>
-__device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int i, int j, const V3<T> &n, double h,
-                                           int &st, T out[12])
+__device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int i, int j, const V3<double> &n64,
+                                           double h, int &st, T out[12], const float2 *__restrict__ pff)
 {
 #pragma unroll
     for (int a = 0; a < 12; ++a) out[a] = T(0);
@@ -135,8 +206,17 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         skip = true;
     }
     if (!skip) {
+        constexpr bool MIXED = sizeof(T) == 4;
         const CutTerms<T> cut = cut_terms(R, h, T(0));
-        const Shape<T> si = load_shape<T>(P, i);
+        const V3<T> n = mk<T>((T)n64.x, (T)n64.y, (T)n64.z);
+        ff oi[3], oj[3];
+        Shape<T> si;
+        if constexpr (MIXED) {
+            ff_axis_of(pff, (size_t)P.n, i, oi);
+            si = shape_ff(oi, __ldg(P.rpar + i), __ldg(P.rperp + i));
+        } else {
+            si = load_shape<T>(P, i);
+        }
         const V3<T> rho_i = support_offset(si, n);
         const Surf<T> A = surface_at(si, rho_i, n);
         const V3<T> x1 = A.x1, x3 = n, x2 = cross(x3, x1);
@@ -144,7 +224,13 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         V3<T> rho_j = mk<T>(0, 0, 0);
         V3<T> Vj = mk<T>(0, 0, 0), Wj = mk<T>(0, 0, 0);
         if (j >= 0) {
-            const Shape<T> sj = load_shape<T>(P, j);
+            Shape<T> sj;
+            if constexpr (MIXED) {
+                ff_axis_of(pff, (size_t)P.n, j, oj);
+                sj = shape_ff(oj, __ldg(P.rpar + j), __ldg(P.rperp + j));
+            } else {
+                sj = load_shape<T>(P, j);
+            }
             rho_j = scl(T(-1), support_offset(sj, n));
             const Surf<T> B = surface_at(sj, rho_j, scl(T(-1), n));
             c1p = B.c1;
@@ -192,7 +278,13 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
             const T hq = cut.in_n ? -cut.dn / (cut.he * (T)R.delta_n) : T(0);
             const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
             const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
-            const T u3 = dot(x3, sub(Vj, add(vi, cross(Wi, rho_i))));
+            T u3;
+            if constexpr (MIXED) {
+                const ff nf[3] = {ff_from_double(n64.x), ff_from_double(n64.y), ff_from_double(n64.z)};
+                u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
+            } else {
+                u3 = dot(x3, sub(Vj, add(vi, cross(Wi, rho_i))));
+            }
             T F3 = (T)R.mu * hq * H33 * u3;
             if (cut.contact) F3 -= (T)R.eps_c * cut.fr;
             out[0] = F3 * x3.x; out[1] = F3 * x3.y; out[2] = F3 * x3.z;
@@ -259,7 +351,14 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
         const V3<T> Vi = add(vi, cross(Wi, rho_i));
         const V3<T> dV = sub(Vj, Vi), dW = sub(Wj, Wi);
-        const T u1 = dot(x1, dV), u2 = dot(x2, dV), u3 = dot(x3, dV);
+        const T u1 = dot(x1, dV), u2 = dot(x2, dV);
+        T u3;
+        if constexpr (MIXED) {
+            const ff nf[3] = {ff_from_double(n64.x), ff_from_double(n64.y), ff_from_double(n64.z)};
+            u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
+        } else {
+            u3 = dot(x3, dV);
+        }
         const T u4 = dot(x1, dW), u5 = dot(x2, dW), u6 = dot(x3, dW);
         const T mu = (T)R.mu;
         T F1 = mu * (lt * (L11 * u1 + L12 * u2 + L13 * u3 + L14 * u4 + L15 * u5));

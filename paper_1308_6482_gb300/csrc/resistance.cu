@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance(PVie
                                                     const int32_t *__restrict__ d_count, int32_t cap,
                                                     const double *__restrict__ nin, const double *__restrict__ gap,
                                                     uint8_t *__restrict__ status, T *__restrict__ FT,
-                                                    T *__restrict__ lever)
+                                                    T *__restrict__ lever, const float2 *__restrict__ pff)
 {
     pdl_wait();
     pdl_trigger();
@@ -40,9 +40,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance(PVie
         bool alien;
         const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
         if (alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
-        const V3<T> n = mk<T>((T)nin[k], (T)nin[C + k], (T)nin[2 * C + k]);
+        const V3<double> n = mk<double>(nin[k], nin[C + k], nin[2 * C + k]);
         T out[12];
-        pair_force<T>(P, R, i, j, n, h, st, out);
+        pair_force<T>(P, R, i, j, n, h, st, out, pff);
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             FT[a * C + k] = out[a];
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance_appl
                                                           const double *__restrict__ gap,
                                                           uint8_t *__restrict__ status, T *__restrict__ FT,
                                                           T *__restrict__ lever, T *__restrict__ force,
-                                                          T *__restrict__ torque)
+                                                          T *__restrict__ torque, const float2 *__restrict__ pff)
 {
     pdl_wait();
     pdl_trigger();
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance_appl
             bool alien;
             const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
             if (alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
-            const V3<T> n = mk<T>((T)nin[k], (T)nin[C + k], (T)nin[2 * C + k]);
-            pair_force<T>(P, R, i, j, n, h, st, out);
+            const V3<double> n = mk<double>(nin[k], nin[C + k], nin[2 * C + k]);
+            pair_force<T>(P, R, i, j, n, h, st, out, pff);
             if (FT)
 #pragma unroll
                 for (int a = 0; a < 6; ++a) FT[a * C + k] = out[a];
@@ -101,6 +101,15 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance_appl
 
 }  // namespace
 
+// the mixed mode's per-call particle table (float-float axes) in the context scratch
+static int particle_table(lub_ctx *ctx, const PView &P, cudaStream_t st, const float2 **pff)
+{
+    int rc = lub_ensure_scratch(ctx, particles_ff_bytes(P.n));
+    if (rc) return rc;
+    *pff = (const float2 *)ctx->scratch;
+    return launch_particles_ff(ctx, P, (float2 *)ctx->scratch, st);
+}
+
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
@@ -116,23 +125,24 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
     const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
+        const float2 *pff = nullptr;
+        if ((rc = particle_table(ctx, P, st, &pff))) return rc;
         if (ens)
-            (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, 
-                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
-                (float *)torque);
+            (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
+                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
         else
-            (void)launch_pdl(k_resistance_apply<float, false>, sh.grid, sh.block, 0, st, 
-                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (float *)FT, (float *)lever, (float *)force,
-                (float *)torque);
+            (void)launch_pdl(k_resistance_apply<float, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
+                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
     } else {
+        const float2 *none = nullptr;
         if (ens)
-            (void)launch_pdl(k_resistance_apply<double, true>, sh.grid, sh.block, 0, st, 
-                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
-                (double *)torque);
+            (void)launch_pdl(k_resistance_apply<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
+                             cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
+                             none);
         else
-            (void)launch_pdl(k_resistance_apply<double, false>, sh.grid, sh.block, 0, st, 
-                P, D, E, R, pi, pj, d_count, cap, n, gap, status, (double *)FT, (double *)lever, (double *)force,
-                (double *)torque);
+            (void)launch_pdl(k_resistance_apply<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
+                             cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
+                             none);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance_apply launch");
 }
@@ -146,19 +156,23 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
     const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
+        const float2 *pff = nullptr;
+        int rc = particle_table(ctx, P, st, &pff);
+        if (rc) return rc;
         if (ens)
-            (void)launch_pdl(k_resistance<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
-                                                                    (float *)FT, (float *)lever);
+            (void)launch_pdl(k_resistance<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
+                             gap, status, (float *)FT, (float *)lever, pff);
         else
-            (void)launch_pdl(k_resistance<float, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
-                                                                     (float *)FT, (float *)lever);
+            (void)launch_pdl(k_resistance<float, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
+                             gap, status, (float *)FT, (float *)lever, pff);
     } else {
+        const float2 *none = nullptr;
         if (ens)
-            (void)launch_pdl(k_resistance<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap,
-                                                                     status, (double *)FT, (double *)lever);
+            (void)launch_pdl(k_resistance<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
+                             gap, status, (double *)FT, (double *)lever, none);
         else
-            (void)launch_pdl(k_resistance<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap,
-                                                                      status, (double *)FT, (double *)lever);
+            (void)launch_pdl(k_resistance<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
+                             gap, status, (double *)FT, (double *)lever, none);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance launch");
 }

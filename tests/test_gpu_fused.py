@@ -10,7 +10,10 @@ import pytest
 
 import gen
 import oracle
-from parity import EPS, compare, gpu_params, oracle_ref
+from parity import compare, gpu_params, oracle_ref
+
+# unit roundoff of each mode's arithmetic, for sums of the same terms in another order
+EPS = {"fp64": 2.0 ** -53, "mixed": 2.0 ** -24}
 
 pytestmark = pytest.mark.gpu
 
@@ -73,7 +76,7 @@ def same_pairs(a, b, prec):
     np.testing.assert_array_equal(a["pj"], b["pj"])
     np.testing.assert_array_equal(a["status"] & 7, b["status"] & 7)
     ok = (b["status"] & 6) == 0
-    tol_n = 1e-12 if prec == "fp64" else 2e-6
+    tol_n = 1e-12 if prec == "fp64" else 1e-11
     assert np.abs(a["n"] - b["n"])[ok].max(initial=0) <= tol_n
     sc = np.abs(b["h"]) + 10.0
     assert np.all(np.abs(a["h"] - b["h"])[ok] <= 1e-10 * sc[ok])
@@ -96,8 +99,30 @@ def test_fused_matches_separate_calls_and_oracle(lub, prec, case):
     if pi is None:
         pi, pj = oracle.candidates(parts, dom, 1.0)
     compare(parts, dom, fus, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
-    if prec == "mixed" and case == "stream":
-        assert np.any(fus["status"] & lub.LUB_ST_FP64)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_mixed_fp64_fallback(lub, fused):
+    """Mixed mode with an FP32 Newton tolerance it cannot reach: every
+    spheroid pair goes to the work list and is solved again in FP64 from the
+    line of centres (LUB_ST_FP64), with oracle parity."""
+    import torch
+    parts, dom, pi, pj = gen.pair_stream(2000, seed=37, kind="aspect", gap_range=(1e-4, 1.0),
+                                         gap_scale="min_axis")
+    P = lub.DeviceParticles(parts)
+    pl = lub.Pipeline(P, dom, gpu_params("mixed", newton_tol=1e-12))
+    pl.set_pairs(pi, pj)
+    if fused:
+        pl.correct()
+    else:
+        pl.closest()
+        pl.resistance()
+        pl.apply()
+    torch.cuda.synchronize()
+    g = pl.results()
+    sph = (parts["r_par"][pi] == parts["r_perp"][pi]) & (parts["r_par"][pj] == parts["r_perp"][pj])
+    assert np.all((g["status"][~sph] & lub.LUB_ST_FP64) != 0)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
 
 
 def test_optional_outputs_and_accumulate(lub):
