@@ -68,8 +68,16 @@ extern "C" {
 #define LUB_MODEL_FULL 0
 #define LUB_MODEL_NORMAL 1
 #define LUB_WARM_PREVIOUS 1 /* Newton starts from the normal passed in n (in/out) */
-#define LUB_WARM_MLP      2 /* Newton starts from the learned network's prediction
-                               (lub_mlp_set must have installed a network) */
+#define LUB_WARM_MLP      2 /* every FP64 Newton solve starts from the learned
+                               network's prediction (lub_mlp_set must have
+                               installed a network): in LUB_FP64 every pair's;
+                               in LUB_MIXED the FP32 stage starts from the line
+                               of centres and only the pairs it fails (solved
+                               again in FP64) start from the network, since an
+                               FP32 iteration costs less than the network */
+#define LUB_WARM_MLP_ALL  3 /* every Newton solve starts from the network's
+                               prediction, the FP32 stage of LUB_MIXED too (the
+                               same as LUB_WARM_MLP in LUB_FP64) */
 
 /* per-pair status bits */
 #define LUB_ST_OVERLAP    1  /* h <= 0 */
@@ -378,7 +386,10 @@ int lub_resistance_apply(lub_ctx *ctx, const lub_particles *p, const lub_domain 
  * differently inside the one kernel; the particle sums also add in another
  * order), with fewer launches and no per-pair round trip through memory.  n [3][cap]
  * is required: it holds the start normals of a warm start (LUB_WARM_PREVIOUS,
- * LUB_WARM_MLP) and receives the normals.  gap, status, iters, FT and lever
+ * LUB_WARM_MLP_ALL, LUB_WARM_MLP in LUB_FP64) and receives the normals.  In
+ * LUB_MIXED, LUB_WARM_MLP runs no network here: the few pairs the FP32 stage
+ * fails are solved again in FP64 inside the force pass, from the line of
+ * centres.  gap, status, iters, FT and lever
  * are written where given and skipped where NULL.  force and torque [3][n]
  * (float in LUB_MIXED, double in LUB_FP64) are zeroed first unless
  * accumulate is set.  Ensemble mode as for the separate calls.
@@ -454,6 +465,25 @@ int lub_links(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const
 int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int32_t precision,
                    const float *f_ext, const float *t_ext, double density, double dt, void *stream);
 
+/*
+ * Seeded random rigid motions (no counterpart in the paper: the input
+ * preparation of time-stepped workloads, on the device so that a loop of
+ * motions and correction steps can be captured into one CUDA graph).  Every
+ * particle k is moved by a displacement with N(0, sigma_r^2) components and
+ * rotated by exp(theta / 2) q, theta with N(0, sigma_t^2) components
+ * (lattice units, radians).  The six normal draws come from Philox4x32-10
+ * (Salmon et al., SC 2011) with counter (k, s, draw) and key seed, by the
+ * Box-Muller transform, s = step + *step_dev (step_dev: NULL or a device
+ * int64): the same (seed, s) gives the same motion on every call.  next_dev
+ * (NULL or a device int64 other than step_dev) receives s + 1, so a graph
+ * that captures several calls alternating two counters (step_dev, next_dev
+ * = c0, c1, then c1, c0, ...) replays a fresh sequence of motions each time.
+ * Writes x, y, z and the quaternion of p in place (writable device memory);
+ * asynchronous on stream.  Errors: LUB_ERR_ARG.
+ */
+int lub_random_motion(lub_ctx *ctx, const lub_particles *p, uint64_t seed, int64_t step, const int64_t *step_dev,
+                      int64_t *next_dev, double sigma_r, double sigma_t, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Launch-shape autotuner (no counterpart in the paper).  The tunable kernels
  * are persistent grid-stride loops; their shape is (threads per block, blocks
@@ -486,6 +516,39 @@ int lub_autotune(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, co
  * work-list refinement, 256 for lub_apply and the sweep) and 1 <= blocks_per_sm <= 256. */
 int lub_get_launch_shape(const lub_ctx *ctx, int32_t kernel, int32_t *block, int32_t *blocks_per_sm);
 int lub_set_launch_shape(lub_ctx *ctx, int32_t kernel, int32_t block, int32_t blocks_per_sm);
+
+/* ---------------------------------------------------------------------------
+ * Kernel trace and pipe probes (no counterpart in the paper): measurement
+ * support for per-kernel rooflines.
+ * ------------------------------------------------------------------------- */
+#define LUB_TRACE_SWEEP      0  /* lub_pairs_build: the cell sweep (k_pairs_sweep) */
+#define LUB_TRACE_CLOSEST    1  /* lub_closest_points: the solve (FP32 stage, FP64 or learned kernel) */
+#define LUB_TRACE_RESISTANCE 2  /* lub_resistance / lub_resistance_apply: the pair-force kernel */
+#define LUB_TRACE_APPLY      3  /* lub_apply: the scatter kernel */
+#define LUB_TRACE_COUNT      4
+
+/* on != 0: from now on every eager call records a CUDA event on its stream
+ * right before and right after each traced kernel (LUB_TRACE_*); nothing is
+ * recorded while the stream is being captured into a graph.  The events
+ * break the programmatic dependent-launch overlap around the traced kernels,
+ * so traced calls are a little slower; the intervals are the kernels' own.
+ * on = 0: stop and release the events.  Errors: LUB_ERR_ARG. */
+int lub_trace_enable(lub_ctx *ctx, int32_t on);
+
+/* Waits for the events of traced kernel `kernel` recorded since the last
+ * read, then returns in *ms_total the sum of their intervals (milliseconds)
+ * and in *launches their number, and forgets them.  Blocks the host.
+ * Errors: LUB_ERR_ARG, LUB_ERR_CUDA. */
+int lub_trace_read(lub_ctx *ctx, int32_t kernel, double *ms_total, int64_t *launches);
+
+#define LUB_PROBE_FP32 0
+#define LUB_PROBE_FP64 1
+/* Sustained fused-multiply-add throughput of one pipe (LUB_PROBE_FP32 or
+ * LUB_PROBE_FP64) at the current clocks, in TFLOP/s (2 FLOP per FMA): eight
+ * independent FMA chains per thread, eight blocks of 256 threads per SM,
+ * best of three timed launches after one warm-up (about 20 ms each).
+ * Synchronises the stream.  Errors: LUB_ERR_ARG, LUB_ERR_CUDA. */
+int lub_probe_peak(lub_ctx *ctx, int32_t pipe, double *tflops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -12,14 +12,19 @@ runs the four calls of one correction step on the current CUDA stream.  With
 particles made by ``make_ensemble`` (many independent suspensions back to
 back) the same four calls process every suspension in one launch per stage.
 """
-from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT, LUB_FP64,
-                   LUB_MIXED, LUB_OK, LUB_ST_DEGENERATE, LUB_ST_FP64, LUB_ST_NOCONV, LUB_ST_OVERLAP,
-                   LUB_WARM_MLP, LUB_WARM_NONE, LUB_WARM_PREVIOUS, LUB_MODEL_FULL, LUB_MODEL_NORMAL, LUB_MLP_PARAMS, Context, DeviceParticles, LubError, Pipeline,
-                   default_params, library_path, load_library, lub_apply, lub_closest_points,
-                   lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_last_error, lub_mlp_adam,
-                   lub_mlp_features, lub_mlp_forward_backward, lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static,
-                   lub_resistance, make_domain, make_ensemble, lub_autotune, lub_get_launch_shape, lub_set_launch_shape, lub_carry_normals, lub_correct, lub_resistance_apply, lub_rigid_step, lub_links, lub_mlp_engine, LUB_MLP_MMA_SYNC, LUB_MLP_TCGEN05,
-                   LUB_TUNE_CLOSEST_MIXED, LUB_TUNE_CLOSEST_REFINE, LUB_TUNE_CLOSEST_FP64, LUB_TUNE_RESISTANCE,
-                   LUB_TUNE_APPLY, LUB_TUNE_SWEEP, LUB_TUNE_COUNT, TUNE_NAMES)
+from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT,
+                   LUB_FP64, LUB_MIXED, LUB_MLP_MMA_SYNC, LUB_MLP_PARAMS, LUB_MLP_TCGEN05, LUB_MODEL_FULL,
+                   LUB_MODEL_NORMAL, LUB_OK, LUB_PROBE_FP32, LUB_PROBE_FP64, LUB_ST_DEGENERATE, LUB_ST_FP64,
+                   LUB_ST_NOCONV, LUB_ST_OVERLAP, LUB_TRACE_APPLY, LUB_TRACE_CLOSEST, LUB_TRACE_COUNT,
+                   LUB_TRACE_RESISTANCE, LUB_TRACE_SWEEP, LUB_TUNE_APPLY, LUB_TUNE_CLOSEST_FP64,
+                   LUB_TUNE_CLOSEST_MIXED, LUB_TUNE_CLOSEST_REFINE, LUB_TUNE_COUNT, LUB_TUNE_RESISTANCE,
+                   LUB_TUNE_SWEEP, LUB_WARM_MLP, LUB_WARM_MLP_ALL, LUB_WARM_NONE, LUB_WARM_PREVIOUS, TRACE_NAMES,
+                   TUNE_NAMES, Context, DeviceParticles, LubError, Pipeline, default_params, library_path,
+                   load_library, lub_apply, lub_autotune, lub_carry_normals, lub_closest_points, lub_correct,
+                   lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_get_launch_shape, lub_last_error,
+                   lub_links, lub_mlp_adam, lub_mlp_engine, lub_mlp_features, lub_mlp_forward_backward,
+                   lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static, lub_probe_peak, lub_random_motion,
+                   lub_resistance, lub_resistance_apply, lub_rigid_step, lub_set_launch_shape, lub_trace_enable,
+                   lub_trace_read, make_domain, make_ensemble)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -20,6 +20,7 @@ LUB_MIXED = 1
 LUB_WARM_NONE = 0
 LUB_WARM_PREVIOUS = 1
 LUB_WARM_MLP = 2
+LUB_WARM_MLP_ALL = 3
 LUB_MLP_MMA_SYNC = 0
 LUB_MLP_TCGEN05 = 1
 LUB_MODEL_FULL = 0
@@ -37,6 +38,14 @@ LUB_TUNE_RESISTANCE = 3
 LUB_TUNE_APPLY = 4
 LUB_TUNE_SWEEP = 5
 LUB_TUNE_COUNT = 6
+LUB_TRACE_SWEEP = 0
+LUB_TRACE_CLOSEST = 1
+LUB_TRACE_RESISTANCE = 2
+LUB_TRACE_APPLY = 3
+LUB_TRACE_COUNT = 4
+TRACE_NAMES = ("sweep", "closest", "resistance", "apply")
+LUB_PROBE_FP32 = 0
+LUB_PROBE_FP64 = 1
 TUNE_NAMES = ("closest_mixed", "closest_refine", "closest_fp64", "resistance", "apply", "sweep")
 
 _P_FIELDS = ("x", "y", "z", "qw", "qx", "qy", "qz", "r_par", "r_perp", "vx", "vy", "vz", "wx", "wy", "wz")
@@ -73,7 +82,8 @@ EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_
            "lub_closest_points", "lub_resistance", "lub_apply", "lub_pairs_build_static", "lub_mlp_set",
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
            "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
-           "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine", "lub_links")
+           "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine", "lub_links", "lub_trace_enable",
+           "lub_trace_read", "lub_probe_peak", "lub_random_motion")
 
 _lib = None
 
@@ -147,6 +157,15 @@ def load_library():
     lib.lub_set_launch_shape.argtypes = [vp, i32, i32, i32]
     lib.lub_pairs_build_static.restype = ctypes.c_int
     lib.lub_pairs_build_static.argtypes = [P(lub_particles), P(lub_domain), P(lub_params), vp, vp, i32, vp, vp]
+    lib.lub_trace_enable.restype = ctypes.c_int
+    lib.lub_trace_enable.argtypes = [vp, i32]
+    lib.lub_trace_read.restype = ctypes.c_int
+    lib.lub_trace_read.argtypes = [vp, i32, P(ctypes.c_double), P(ctypes.c_int64)]
+    lib.lub_random_motion.restype = ctypes.c_int
+    lib.lub_random_motion.argtypes = [vp, P(lub_particles), ctypes.c_uint64, ctypes.c_int64, vp, vp,
+                                      ctypes.c_double, ctypes.c_double, vp]
+    lib.lub_probe_peak.restype = ctypes.c_int
+    lib.lub_probe_peak.argtypes = [vp, i32, P(ctypes.c_double), vp]
     _lib = lib
     return lib
 
@@ -339,6 +358,30 @@ def lub_set_launch_shape(ctx, kernel, block, blocks_per_sm):
     return _check(ctx, load_library().lub_set_launch_shape(ctx, int(kernel), int(block), int(blocks_per_sm)))
 
 
+def lub_trace_enable(ctx, on):
+    return _check(ctx, load_library().lub_trace_enable(ctx, int(bool(on))))
+
+
+def lub_trace_read(ctx, kernel):
+    """(total milliseconds, launches) of traced kernel `kernel` since the last read."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(ctx, load_library().lub_trace_read(ctx, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def lub_random_motion(ctx, particles, seed, step, sigma_r, sigma_t, step_dev=None, next_dev=None, stream=None):
+    return _check(ctx, load_library().lub_random_motion(ctx, ctypes.byref(particles), int(seed) & ((1 << 64) - 1),
+                                                        int(step), _ptr(step_dev), _ptr(next_dev), float(sigma_r),
+                                                        float(sigma_t), _stream(stream)))
+
+
+def lub_probe_peak(ctx, pipe, stream=None):
+    """Sustained FMA throughput of the FP32 (pipe 0) or FP64 (pipe 1) pipe, TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    _check(ctx, load_library().lub_probe_peak(ctx, int(pipe), ctypes.byref(t), _stream(stream)))
+    return t.value
+
+
 # ---------------------------------------------------------------------------
 # conveniences: device particles, domain, params, a context, one step
 # ---------------------------------------------------------------------------
@@ -348,7 +391,8 @@ def default_params(**kw):
         if k == "precision" and isinstance(v, str):
             v = {"fp64": LUB_FP64, "mixed": LUB_MIXED}[v]
         if k == "warm_start" and isinstance(v, str):
-            v = {"none": LUB_WARM_NONE, "previous": LUB_WARM_PREVIOUS, "mlp": LUB_WARM_MLP}[v]
+            v = {"none": LUB_WARM_NONE, "previous": LUB_WARM_PREVIOUS, "mlp": LUB_WARM_MLP,
+                 "mlp_all": LUB_WARM_MLP_ALL}[v]
         if k == "model" and isinstance(v, str):
             v = {"full": LUB_MODEL_FULL, "normal": LUB_MODEL_NORMAL}[v]
         setattr(p, k, v)

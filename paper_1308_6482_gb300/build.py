@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "liblub.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "scan.cu", "pairs.cu", "pairs_static.cu", "closest.cu", "resistance.cu", "apply.cu", "mlp.cu", "tune.cu", "rigid.cu", "links.cu"]
+SOURCES = ["api.cu", "scan.cu", "pairs.cu", "pairs_static.cu", "closest.cu", "resistance.cu", "apply.cu", "mlp.cu", "tune.cu", "rigid.cu", "links.cu", "trace.cu"]
 
 
 def nvcc():

@@ -174,8 +174,10 @@ int check_params(lub_ctx *ctx, const lub_params *p)
         return lub_set_error(ctx, LUB_ERR_ARG, "list_cutoff must be finite and >= 0");
     if (p->max_newton < 1 || p->max_newton > 64) return lub_set_error(ctx, LUB_ERR_ARG, "max_newton must be 1..64");
     if (!(p->newton_tol > 0.0)) return lub_set_error(ctx, LUB_ERR_ARG, "newton_tol must be > 0");
-    if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS && p->warm_start != LUB_WARM_MLP)
-        return lub_set_error(ctx, LUB_ERR_ARG, "warm_start must be LUB_WARM_NONE, LUB_WARM_PREVIOUS or LUB_WARM_MLP");
+    if (p->warm_start != LUB_WARM_NONE && p->warm_start != LUB_WARM_PREVIOUS && p->warm_start != LUB_WARM_MLP &&
+        p->warm_start != LUB_WARM_MLP_ALL)
+        return lub_set_error(ctx, LUB_ERR_ARG,
+                             "warm_start must be LUB_WARM_NONE, LUB_WARM_PREVIOUS, LUB_WARM_MLP or LUB_WARM_MLP_ALL");
     if (p->model != LUB_MODEL_FULL && p->model != LUB_MODEL_NORMAL)
         return lub_set_error(ctx, LUB_ERR_ARG, "model must be LUB_MODEL_FULL or LUB_MODEL_NORMAL");
     return LUB_OK;
@@ -239,6 +241,7 @@ int lub_ctx_destroy(lub_ctx *ctx)
     for (auto &T : ctx->table)
         if (T.dev) cudaFree(T.dev);
     for (void *r : ctx->retired) cudaFree(r);
+    lub_trace_free(ctx);
     delete ctx;
     return LUB_OK;
 }
@@ -436,6 +439,20 @@ int lub_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, cons
     if (!(dt >= 0.0) || !isfinite(dt)) return lub_set_error(ctx, LUB_ERR_ARG, "dt must be finite and >= 0");
     if (p->n > 0 && (!force || !torque)) return lub_set_error(ctx, LUB_ERR_ARG, "force or torque is NULL");
     return launch_rigid_step(ctx, p, force, torque, precision, f_ext, t_ext, density, dt, (cudaStream_t)stream);
+}
+
+int lub_random_motion(lub_ctx *ctx, const lub_particles *p, uint64_t seed, int64_t step, const int64_t *step_dev,
+                      int64_t *next_dev, double sigma_r, double sigma_t, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    ctx->err.clear();
+    int rc;
+    if ((rc = check_particles(ctx, p, false))) return rc;
+    if (!(sigma_r >= 0.0) || !(sigma_t >= 0.0) || !isfinite(sigma_r) || !isfinite(sigma_t))
+        return lub_set_error(ctx, LUB_ERR_ARG, "sigma_r and sigma_t must be finite and >= 0");
+    if (step_dev && next_dev && step_dev == next_dev)
+        return lub_set_error(ctx, LUB_ERR_ARG, "step_dev and next_dev must be different addresses");
+    return launch_random_motion(ctx, p, seed, step, step_dev, next_dev, sigma_r, sigma_t, (cudaStream_t)stream);
 }
 
 int lub_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *prev_i, const int32_t *prev_j,

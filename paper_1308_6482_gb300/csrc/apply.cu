@@ -135,6 +135,7 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
         if (cap == 0) return LUB_OK;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_APPLY, cap);
         const int grid = sh.grid, block = sh.block;
+        lub_trace_mark(ctx, LUB_TRACE_APPLY, st);
         if (precision == LUB_MIXED)
             (void)launch_pdl(k_apply_atomic<float>, grid, block, 0, st, pi, pj, d_count, cap, (const float *)FT,
                                                           (const float *)lever, n, (float *)force, (float *)torque);
@@ -142,6 +143,7 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
             (void)launch_pdl(k_apply_atomic<double>, grid, block, 0, st, pi, pj, d_count, cap, (const double *)FT,
                                                            (const double *)lever, n, (double *)force,
                                                            (double *)torque);
+        lub_trace_mark(ctx, LUB_TRACE_APPLY, st);
         return lub_check_cuda(ctx, cudaGetLastError(), "k_apply_atomic launch");
     }
     // scratch: cnt/start [n], fill [n], inc [2 cap], total [1], scan temp

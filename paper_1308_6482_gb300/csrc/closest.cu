@@ -331,10 +331,12 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
 }
 
 // LUB_MIXED, a work-list pair (its FP32 Newton did not converge): a
-// complete FP64 solve and gap from the line of centres
+// complete FP64 solve and gap from the line of centres, or, with w0 (the
+// network's start), from w0 unless it lies on the far hemisphere
 template <bool ENS>
 __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, const Ens &E, int i, int j, int maxit,
-                                           V3<double> &n64, double &h, int &st, int &nit)
+                                           V3<double> &n64, double &h, int &st, int &nit,
+                                           const V3<double> *w0 = nullptr)
 {
     bool alien;
     const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
@@ -342,6 +344,10 @@ __device__ __forceinline__ void refine_one(const PView &P, const DView &D0, cons
     const double dl = sqrt(dot(d, d));
     const Shape<double> si = load_shape<double>(P, i), sj = load_shape<double>(P, j);
     V3<double> nn = scl(1.0 / dl, d);
+    if (w0) {
+        const double wl2 = dot(*w0, *w0);
+        if (wl2 > 0.25 && wl2 < 4.0 && isfinite(wl2) && dot(*w0, d) > 0.0) nn = *w0;
+    }
     const double scale = dl + (double)fmaxf(P.rpar[i], P.rperp[i]) + (double)fmaxf(P.rpar[j], P.rperp[j]);
     const NewtonOut o = newton_sphere<double>(si, sj, d, nn, maxit, kTolFp64, 1e-14 * scale);
     nit = o.iters;
@@ -608,6 +614,46 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_fp64_learned(
     }
 }
 
+// LUB_WARM_MLP in mixed precision: the FP64 solves of the work list start
+// from the network's prediction (mma.sync engine; every warp runs the
+// network for 32 entries, writes the start normals to n and solves them)
+template <bool ENS>
+__global__ void __launch_bounds__(32 * INF_WARPS) k_closest_refine_learned(
+    PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+    int32_t cap, double *__restrict__ nout, double *__restrict__ gap, uint8_t *__restrict__ status,
+    uint8_t *__restrict__ iters, int maxit, const int32_t *__restrict__ wl_count, const int32_t *__restrict__ wl,
+    MlpDevice M)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int nwl = wl_total(wl_count, cap);
+    if (nwl == 0) return;  // the usual case: no weights to stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InfSmem &S = *reinterpret_cast<InfSmem *>(smem_raw);
+    stage_weights(S, M);
+    __syncthreads();
+    const size_t C = (size_t)cap;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = (blockIdx.x * INF_WARPS + w) * 32; base < nwl; base += gridDim.x * INF_WARPS * 32) {
+        const int q = base + lane;
+        const bool act = q < nwl;
+        const int k = act ? -1 - wl[q] : 0;
+        const int cnt = act ? k + 1 : 0;  // pair k is valid for the helpers iff act
+        float f[NI];
+        const PairIn in = pair_inputs<ENS>(P, D0, E, pi, pj, k, cnt, S.mean, S.istd, f);
+        const float4 y = warp_mlp(S, S.x[w], S.y[w], f, lane);
+        pair_outputs(P, in, y, k, cnt, C, nout, nullptr);
+        if (act) {
+            const V3<double> w0 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
+            V3<double> n64;
+            double h;
+            int st, nit;
+            refine_one<ENS>(P, D0, E, pi[k], pj[k], maxit, n64, h, st, nit, &w0);
+            store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+        }
+    }
+}
+
 // the shared-memory size of the learned kernels, set once per kernel (bits 16..)
 template <typename K>
 int learned_smem(lub_ctx *ctx, K kernel, int bit)
@@ -758,13 +804,21 @@ __global__ void __launch_bounds__(128) k_fused_fp64(PView P, const __grid_consta
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// the network's start normals (learned warm start), then whether Newton starts from n
+// whether the network starts every pair's Newton solve (LUB_WARM_MLP_ALL,
+// or LUB_WARM_MLP in FP64) or only the FP64 solves of the mixed work list
+inline bool net_every_pair(const lub_params &prm)
+{
+    return prm.warm_start == LUB_WARM_MLP_ALL || (prm.warm_start == LUB_WARM_MLP && prm.precision == LUB_FP64);
+}
+
+// the network's start normals for every pair (learned warm start), then
+// whether Newton starts from n
 int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                   const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n,
                   cudaStream_t st, int *warm)
 {
     *warm = prm.warm_start == LUB_WARM_PREVIOUS;
-    if (prm.warm_start == LUB_WARM_MLP) {
+    if (net_every_pair(prm)) {
         int rc = launch_mlp_start(ctx, P, D, E, pi, pj, d_count, cap, n, nullptr, st);
         if (rc) return rc;
         *warm = 1;
@@ -813,16 +867,19 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                      uint8_t *status, uint8_t *iters, cudaStream_t st)
 {
     int warm = 0, rc;
-    // the learned start on the mma.sync engine runs inside the solve's kernel
-    const bool fused_mlp = prm.warm_start == LUB_WARM_MLP && ctx->mlp_engine == LUB_MLP_MMA_SYNC;
-    if (fused_mlp && !ctx->mlp_ready)
+    const bool net_all = net_every_pair(prm);
+    const bool net_wl = prm.warm_start == LUB_WARM_MLP && prm.precision == LUB_MIXED;
+    if ((net_all || net_wl) && !ctx->mlp_ready)
         return lub_set_error(ctx, LUB_ERR_ARG, "the learned warm start needs lub_mlp_set first");
+    // the learned start of every pair on the mma.sync engine runs inside the solve's kernel
+    const bool fused_mlp = net_all && ctx->mlp_engine == LUB_MLP_MMA_SYNC;
     if (!fused_mlp && (rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
     const int learned_grid = 2 * ctx->num_sms;
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl, nullptr, nullptr, &P, &pff))) return rc;
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         if (fused_mlp) {
             if ((rc = learned_smem(ctx, k_closest_mixed_learned<ENS>, 16 << ENS))) return rc;
             (void)launch_pdl(k_closest_mixed_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E,
@@ -834,18 +891,31 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                              status, iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl,
                              (const float2 *)pff);
         }
-        // small blocks so the (short) work list spreads over every SM
-        const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
-        (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status, iters,
-                         prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
+        if (net_wl) {
+            // the work list's FP64 solves from the network's start (returns at once when it is empty)
+            if ((rc = learned_smem(ctx, k_closest_refine_learned<ENS>, 256 << ENS))) return rc;
+            (void)launch_pdl(k_closest_refine_learned<ENS>, ctx->num_sms, 32 * INF_WARPS, sizeof(InfSmem), st, P, D,
+                             E, pi, pj, cap, n, gap, status, iters, prm.max_newton, (const int32_t *)wl_count,
+                             (const int32_t *)wl, *(const MlpDevice *)ctx->mlp);
+        } else {
+            // small blocks so the (short) work list spreads over every SM
+            const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
+            (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status,
+                             iters, prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl);
+        }
     } else if (fused_mlp) {
         if ((rc = learned_smem(ctx, k_closest_fp64_learned<ENS>, 64 << ENS))) return rc;
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         (void)launch_pdl(k_closest_fp64_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E, pi,
                          pj, d_count, cap, n, gap, status, iters, prm.max_newton, *(const MlpDevice *)ctx->mlp);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         (void)launch_pdl(k_closest_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
                          iters, prm.max_newton, warm);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
     }
     return lub_check_cuda(ctx, cudaGetLastError(), "k_closest launch");
 }
@@ -872,13 +942,17 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         float2 *pff = nullptr;
         if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status, &P, &pff))) return rc;
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
                          iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl, (const float2 *)pff);
+        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         const Shape2 sr = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
         const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
                          iters, (float *)FT, (float *)lever, prm.max_newton, (const int32_t *)wl_count,
                          (const int32_t *)wl, wl_count + 2, (float *)force, (float *)torque, (const float2 *)pff);
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
     } else {
         const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
         (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,

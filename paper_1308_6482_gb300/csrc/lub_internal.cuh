@@ -37,7 +37,17 @@ struct lub_ctx {
     // launch shapes chosen by lub_autotune (0 = built-in default)
     int tune_block[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int tune_per_sm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // kernel trace (lub_trace_enable): events recorded around each traced
+    // kernel since the last read (start, end, start, end, ...), and spares
+    bool trace = false;
+    std::vector<cudaEvent_t> trace_ev[LUB_TRACE_COUNT];
+    std::vector<cudaEvent_t> trace_pool;
 };
+
+// one trace event of kernel `id` on st (before or after its launch); no-op
+// unless tracing is on and st is not capturing
+void lub_trace_mark(lub_ctx *ctx, int id, cudaStream_t st);
+void lub_trace_free(lub_ctx *ctx);
 
 // device copy of a host table, re-uploaded only when its bytes change
 int lub_upload_table(lub_ctx *ctx, int slot, const void *host, size_t bytes, cudaStream_t st, const void **dev);
@@ -359,6 +369,8 @@ int launch_pairs_build_ens(lub_ctx *ctx, const PView &P, const Ens &E, const DVi
 int launch_max_semi_axis(lub_ctx *ctx, const PView &P, float *h_out, cudaStream_t st);
 int launch_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int precision,
                       const float *fext, const float *text, double rho, double dt, cudaStream_t st);
+int launch_random_motion(lub_ctx *ctx, const lub_particles *p, uint64_t seed, int64_t step, const int64_t *step_dev,
+                         int64_t *next_dev, double sig_r, double sig_t, cudaStream_t st);
 int launch_carry_normals(lub_ctx *ctx, int32_t n_particles, const int32_t *qi, const int32_t *qj, const double *qn,
                          const int32_t *q_count, int32_t qcap, const int32_t *pi, const int32_t *pj,
                          const int32_t *d_count, int32_t cap, double *n, cudaStream_t st);

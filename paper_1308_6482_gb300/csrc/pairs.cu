@@ -875,7 +875,9 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     // one item per thread (no grid-stride loop)
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
     sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
+    lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
     e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, V);
+    lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;

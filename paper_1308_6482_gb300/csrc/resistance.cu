@@ -127,6 +127,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
     if (prm.precision == LUB_MIXED) {
         const float2 *pff = nullptr;
         if ((rc = particle_table(ctx, P, st, &pff))) return rc;
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
                              cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
@@ -135,6 +136,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
                              cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
     } else {
         const float2 *none = nullptr;
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance_apply<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
                              cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
@@ -144,6 +146,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
                              cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
                              none);
     }
+    lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance_apply launch");
 }
 
@@ -159,6 +162,7 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
         const float2 *pff = nullptr;
         int rc = particle_table(ctx, P, st, &pff);
         if (rc) return rc;
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
                              gap, status, (float *)FT, (float *)lever, pff);
@@ -167,6 +171,7 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
                              gap, status, (float *)FT, (float *)lever, pff);
     } else {
         const float2 *none = nullptr;
+        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
                              gap, status, (double *)FT, (double *)lever, none);
@@ -174,5 +179,6 @@ int launch_resistance(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E
             (void)launch_pdl(k_resistance<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n,
                              gap, status, (double *)FT, (double *)lever, none);
     }
+    lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance launch");
 }

@@ -110,7 +110,95 @@ __global__ void k_rigid_step(int n, double *__restrict__ x, double *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// seeded random rigid motions (no counterpart in the paper): the input
+// preparation of the time-stepped workloads, on the device so that a loop of
+// motion + correction steps can be captured into one CUDA graph.
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC 2011): ten rounds of two 32x32 -> 64-bit multiplies,
+// the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += W0;
+            k.y += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// two standard normal draws from two 32-bit words (Box-Muller on uniforms in (0, 1])
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
+{
+    const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(b >> 8) * 0x1p-24f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// particle k, step s = step0 (+ *step_dev): counter (k, s low, s high, draw),
+// key = seed; six normals: the displacement (sigma_r each) and the rotation
+// vector (sigma_t each); q <- exp(theta / 2) q, renormalised.  next_dev
+// (another address) receives s + 1.
+__global__ void __launch_bounds__(256) k_random_motion(int n, double *__restrict__ x, double *__restrict__ y,
+                                                       double *__restrict__ z, float *__restrict__ qw,
+                                                       float *__restrict__ qx, float *__restrict__ qy,
+                                                       float *__restrict__ qz, uint2 key, int64_t step0,
+                                                       const int64_t *__restrict__ step_dev,
+                                                       int64_t *__restrict__ next_dev, float sig_r, float sig_t)
+{
+    const uint64_t step = (uint64_t)(step0 + (step_dev ? *step_dev : 0));
+    if (next_dev && blockIdx.x == 0 && threadIdx.x == 0) *next_dev = (int64_t)step + 1;
+    const uint32_t step_lo = (uint32_t)step, step_hi = (uint32_t)(step >> 32);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint4 r0 = philox4x32_10(make_uint4((uint32_t)k, step_lo, step_hi, 0u), key);
+        const uint4 r1 = philox4x32_10(make_uint4((uint32_t)k, step_lo, step_hi, 1u), key);
+        const float2 g0 = box_muller(r0.x, r0.y), g1 = box_muller(r0.z, r0.w), g2 = box_muller(r1.x, r1.y);
+        x[k] += (double)(sig_r * g0.x);
+        y[k] += (double)(sig_r * g0.y);
+        z[k] += (double)(sig_r * g1.x);
+        const float t0 = sig_t * g1.y, t1 = sig_t * g2.x, t2 = sig_t * g2.y;
+        const float a = sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
+        float sh, ch;
+        sincosf(0.5f * a, &sh, &ch);
+        const float sc = a > 0.f ? sh / a : 0.5f;
+        const float dw = ch, dx = sc * t0, dy = sc * t1, dz = sc * t2;
+        const float w = qw[k], xx = qx[k], yy = qy[k], zz = qz[k];
+        const float nw = dw * w - dx * xx - dy * yy - dz * zz;
+        const float nx = dw * xx + dx * w + dy * zz - dz * yy;
+        const float ny = dw * yy - dx * zz + dy * w + dz * xx;
+        const float nz = dw * zz + dx * yy - dy * xx + dz * w;
+        const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
+        qw[k] = nw * inv;
+        qx[k] = nx * inv;
+        qy[k] = ny * inv;
+        qz[k] = nz * inv;
+    }
+}
+
 }  // namespace
+
+int launch_random_motion(lub_ctx *ctx, const lub_particles *p, uint64_t seed, int64_t step, const int64_t *step_dev,
+                         int64_t *next_dev, double sig_r, double sig_t, cudaStream_t st)
+{
+    if (p->n == 0 && !next_dev) return LUB_OK;
+    double *x = const_cast<double *>(p->x), *y = const_cast<double *>(p->y), *z = const_cast<double *>(p->z);
+    float *qw = const_cast<float *>(p->qw), *qx = const_cast<float *>(p->qx), *qy = const_cast<float *>(p->qy),
+          *qz = const_cast<float *>(p->qz);
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    k_random_motion<<<grid_for(p->n, 256, ctx->num_sms, 8), 256, 0, st>>>(
+        p->n, x, y, z, qw, qx, qy, qz, key, step, step_dev, next_dev, (float)sig_r, (float)sig_t);
+    return lub_check_cuda(ctx, cudaGetLastError(), "k_random_motion launch");
+}
 
 int launch_rigid_step(lub_ctx *ctx, const lub_particles *p, const void *force, const void *torque, int precision,
                       const float *fext, const float *text, double rho, double dt, cudaStream_t st)

@@ -5,9 +5,14 @@ forces it leads to are defined by the paper alone (Sec. III A: the common
 normal and the gap h; Sec. III B and the Appendix: the resistance), so each
 learned form must meet the same element-by-element bounds as the cold start:
 
-* mixed precision (FP32 Newton from the network's start, the float-float
-  step, FP32 resistance) on fresh min-axis-scaled pairs, with both tensor-core
-  engines (mma.sync inside the solve's kernel, tcgen05 as a launch of its own);
+* mixed precision with the network starting every pair (LUB_WARM_MLP_ALL:
+  FP32 Newton from the network's start, the float-float step, FP32
+  resistance) on fresh min-axis-scaled pairs, with both tensor-core engines
+  (mma.sync inside the solve's kernel, tcgen05 as a launch of its own);
+* mixed precision with the network starting only the FP64 solves of the
+  pairs the FP32 stage fails (LUB_WARM_MLP), every spheroid pair made to fail
+  by an FP32 tolerance it cannot reach: those FP64 solves take fewer
+  iterations than from the line of centres and give the same results;
 * the ensemble (many suspensions in one launch per stage), every member
   against the oracle run on it alone, in both precisions;
 * a window of the large dense run: its growth-packed base slab (16,384
@@ -42,10 +47,11 @@ def env():
     return lub, torch, WarmStartMLP.load(WEIGHTS)
 
 
-def learned(env, parts, dom, prec, pi=None, pj=None, engine="mma_sync", offsets=None):
+def learned(env, parts, dom, prec, pi=None, pj=None, engine="mma_sync", offsets=None, warm="mlp_all", **kw):
     lub, torch, net = env
     P = lub.DeviceParticles(parts, batch_offsets=offsets)
-    pl = lub.Pipeline(P, dom, gpu_params(prec, warm_start=lub.LUB_WARM_MLP))
+    pl = lub.Pipeline(P, dom, gpu_params(prec, warm_start={"mlp": lub.LUB_WARM_MLP, "mlp_all": lub.LUB_WARM_MLP_ALL,
+                                                          "none": lub.LUB_WARM_NONE}[warm], **kw))
     net.install(pl.ctx)
     lub.lub_mlp_engine(pl.ctx.h, engine)
     if pi is None:
@@ -69,6 +75,19 @@ def test_learned_mixed_fresh_pairs(env, engine):
     compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
 
 
+def test_learned_start_of_the_fp64_fallback(env):
+    lub = env[0]
+    parts, dom, pi, pj = gen.pair_stream(4000, seed=9003, kind="aspect", gap_range=(1e-4, 1.0),
+                                         gap_scale="min_axis")
+    cold = learned(env, parts, dom, "mixed", pi, pj, warm="none", newton_tol=1e-12)
+    warm = learned(env, parts, dom, "mixed", pi, pj, warm="mlp", newton_tol=1e-12)
+    fell = (warm["status"] & lub.LUB_ST_FP64) != 0
+    assert fell.mean() > 0.9 and np.array_equal(fell, (cold["status"] & lub.LUB_ST_FP64) != 0)
+    # the FP64 iterations from the network's start against those from the line of centres
+    assert warm["iters"][fell].mean() < 0.85 * cold["iters"][fell].mean()
+    compare(parts, dom, warm, oracle_ref(parts, dom, pi, pj), "mixed", pi, pj)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_learned_ensemble_every_member(env, prec):
     lub = env[0]
@@ -84,7 +103,7 @@ def test_learned_ensemble_every_member(env, prec):
         p, d, _ = gen.grow(sh, (Lb, Lb, Lb), periodic=per, walls=walls, seed=70 + seed)
         rng_members.append((p, d))
     parts, doms, off = lub.make_ensemble(rng_members)
-    res = learned(env, parts, doms, prec, offsets=off)
+    res = learned(env, parts, doms, prec, offsets=off, warm="mlp_all" if prec == "mixed" else "mlp")
     for b, (p, d) in enumerate(rng_members):
         o0, o1 = int(off[b]), int(off[b + 1])
         sel = (res["pi"] >= o0) & (res["pi"] < o1)
