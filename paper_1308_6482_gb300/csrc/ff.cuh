@@ -147,3 +147,35 @@ __device__ __forceinline__ ff ff_from_double(double d)
 }
 
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
+
+// Float-float split of a double with integer and FP32 operations only (no
+// FP64-pipe conversion): hi = d truncated to 24 significant bits, lo = the
+// next 23 bits, |hi + lo - d| < 2^-46 |d|.  Doubles with |d| < 2^-126
+// (zero included) give 0 + 0; |d| >= 2^128 gives +-infinity.
+__device__ __forceinline__ ff ff_split_bits(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    const unsigned int sign = hw & 0x80000000u;
+    const int ef = (int)((hw >> 20) & 0x7FFu) - 1023 + 127;  // the float exponent of hi
+    ff r;
+    if (ef <= 0) {
+        r.hi = 0.0f;
+        r.lo = 0.0f;
+        return r;
+    }
+    if (ef >= 255) {
+        r.hi = __int_as_float(sign | 0x7F800000u);
+        r.lo = 0.0f;
+        return r;
+    }
+    // the fraction's top 23 bits (20 of the high word, 3 of the low word)
+    r.hi = __int_as_float(sign | ((unsigned int)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    // the next 23 bits as an exact float (2^23 + m - 2^23), times 2^(e - 46)
+    const unsigned int m = (lw & 0x1FFFFFFFu) >> 6;
+    const int el = ef - 46;
+    float lo = 0.0f;
+    if (el > 0) lo = __fmul_rn(__fsub_rn(__int_as_float(0x4B000000u | m), 8388608.0f), __int_as_float((unsigned int)el << 23));
+    r.lo = sign ? -lo : lo;
+    return r;
+}

@@ -125,14 +125,19 @@ __device__ __forceinline__ const DView &pair_domain(const DView &D, const Ens &E
 
 struct RParams {
     double mu, delta_n, delta_t, delta_r, h_c, eps_c;
-    int model;  // LUB_MODEL_FULL or LUB_MODEL_NORMAL
-    // the cut-offs and h_c as float-float (hi, lo), for the FP32 path
+    int model;    // LUB_MODEL_FULL or LUB_MODEL_NORMAL
+    int contact;  // h_c > 0: the contact model (clip and Hookean repulsion) is on
+    // for the FP32 path: the cut-offs and h_c as float-float (hi, lo), mu,
+    // eps_c and the reciprocals of the cut-offs as float (no FP64 per pair)
     float dn_ff[2], dt_ff[2], dr_ff[2], hc_ff[2];
+    float mu_f, eps_f, idn_f, idt_f, idr_f;
 };
 
 inline RParams make_rparams(const lub_params &p)
 {
-    RParams R{p.mu, p.delta_n, p.delta_t, p.delta_r, p.h_c, p.eps_c, p.model, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    RParams R{p.mu, p.delta_n, p.delta_t, p.delta_r, p.h_c, p.eps_c, p.model, p.h_c > 0.0 ? 1 : 0,
+              {0, 0}, {0, 0}, {0, 0}, {0, 0}, (float)p.mu, (float)p.eps_c, (float)(1.0 / p.delta_n),
+              (float)(1.0 / p.delta_t), (float)(1.0 / p.delta_r)};
     auto split = [](double v, float o[2]) {
         o[0] = (float)v;
         o[1] = (float)(v - (double)o[0]);
@@ -236,12 +241,30 @@ __device__ __forceinline__ double rsqrt64(double a)
     return y;
 }
 
+// Reciprocal and square root of the FP32 resistance path: the hardware
+// approximations (about 1 ulp), far inside the accuracy the path needs; the
+// FP64 path keeps the Newton-refined double versions.
+__device__ __forceinline__ float rcp_fast(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double rcp_fast(double v) { return rcp64(v); }
+__device__ __forceinline__ float sqrt_fast(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt64(v); }
 __device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
 __device__ __forceinline__ double sqrt_t(double v) { return v > 0.0 ? v * rsqrt64(v) : 0.0; }
 __device__ __forceinline__ float rcp_t(float v) { return 1.0f / v; }
 __device__ __forceinline__ double rcp_t(double v) { return rcp64(v); }
+__device__ __forceinline__ double sqrt_fast(double v) { return sqrt_t(v); }
 
 template <typename T>
 __device__ __forceinline__ V3<T> normalized(const V3<T> &a)

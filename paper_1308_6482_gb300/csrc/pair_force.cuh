@@ -92,11 +92,12 @@ template <typename T>
 __device__ __forceinline__ Surf<T> surface_at(const Shape<T> &s, const V3<T> &rho, const V3<T> &nrm)
 {
     Surf<T> o;
+    const T ipar = rcp_fast(s.rpar), iperp = rcp_fast(s.rperp);
     const T zt = dot(rho, s.o);
     const V3<T> rp = axpy(-zt, s.o, rho);  // component normal to the axis
     const T rr2 = dot(rp, rp);
-    const T spr = zt / s.rpar;                       // sin p, unnormalised
-    const T cpr = sqrt_t(rr2) / s.rperp;             // cos p, unnormalised
+    const T spr = zt * ipar;                         // sin p, unnormalised
+    const T cpr = sqrt_fast(rr2) * iperp;            // cos p, unnormalised
     const T hn = rsqrt_t(spr * spr + cpr * cpr);
     const T sp = spr * hn, cp = cpr * hn;
     V3<T> er;
@@ -113,10 +114,10 @@ __device__ __forceinline__ Surf<T> surface_at(const Shape<T> &s, const V3<T> &rh
     const T is1 = rsqrt_t(s1sq);
     const T is2 = is1 * is1;
     o.c1 = s.rpar * s.rperp * is1 * is2;            // 1/S1 = R_par R_perp / s1^3
-    o.c2 = s.rpar / s.rperp * is1;                  // 1/S2 = R_par / (R_perp s1)
+    o.c2 = s.rpar * iperp * is1;                    // 1/S2 = R_par / (R_perp s1)
     const T kk = T(0.5) * s.e * sp * cp;            // (R_par^2 - R_perp^2) sin p cos p / 2
     o.G0 = kk * s.rpar * s.rperp * is2 * is2 * is2;  // / s1^6
-    o.G2 = kk * s.rpar / s.rperp * is2 * is2;       // / (R_perp s1^4)
+    o.G2 = kk * s.rpar * iperp * is2 * is2;         // / (R_perp s1^4)
     return o;
 }
 
@@ -124,42 +125,43 @@ __device__ __forceinline__ Surf<T> surface_at(const Shape<T> &s, const V3<T> &rh
 // the arithmetic of T: he = h, or h_c where the contact model clips a
 // smaller gap; d_x = he - Delta_x for the three cut-offs, which cancels near
 // each cut-off; in_x = he < Delta_x; fr = h_c - h where the contact force
-// acts (h <= h_c with h_c > 0), else 0.  T = double: double arithmetic.
-// T = float: the double gap is split once into float-float (four FP64
-// operations, against a dozen for the double comparisons, differences and
-// conversions, on a pipe 1/64 as fast) and the rest runs in float-float, so
-// d_x keeps its relative accuracy near the cut-off.
+// acts (h <= h_c with h_c > 0), else 0; le0 = h <= 0.  T = double: double
+// arithmetic.  T = float: the double gap is split into float-float with
+// integer operations (no FP64-pipe work) and the rest runs in float-float,
+// so d_x keeps its relative accuracy near the cut-off.
 template <typename T>
 struct CutTerms {
     T he, dn, dt, dr, fr;
-    bool in_n, in_t, in_r, contact;
+    bool in_n, in_t, in_r, contact, le0;
 };
 
 __device__ __forceinline__ CutTerms<double> cut_terms(const RParams &R, double h, double)
 {
     CutTerms<double> c;
-    c.he = (R.h_c > 0.0 && h < R.h_c) ? R.h_c : h;
+    c.he = (R.contact && h < R.h_c) ? R.h_c : h;
     c.dn = c.he - R.delta_n;
     c.dt = c.he - R.delta_t;
     c.dr = c.he - R.delta_r;
     c.in_n = c.he < R.delta_n;
     c.in_t = c.he < R.delta_t;
     c.in_r = c.he < R.delta_r;
-    c.contact = R.h_c > 0.0 && h <= R.h_c;
+    c.contact = R.contact && h <= R.h_c;
     c.fr = c.contact ? (h > 0.0 ? R.h_c - h : R.h_c) : 0.0;
+    c.le0 = h <= 0.0;
     return c;
 }
 
 __device__ __forceinline__ CutTerms<float> cut_terms(const RParams &R, double h, float)
 {
-    const float hi = (float)h;
-    ff he{hi, (float)(h - (double)hi)};
+    ff he = ff_split_bits(h);
+    CutTerms<float> c;
+    c.le0 = he.hi <= 0.f;
+    const float hi = he.hi;
     const ff hc{R.hc_ff[0], R.hc_ff[1]};
     const ff dc = ff_sub(he, hc);
     const float dcf = dc.hi + dc.lo;  // h - h_c
-    CutTerms<float> c;
-    c.contact = R.hc_ff[0] > 0.f && dcf <= 0.f;
-    if (R.hc_ff[0] > 0.f && dcf < 0.f) he = hc;
+    c.contact = R.contact && dcf <= 0.f;
+    if (R.contact && dcf < 0.f) he = hc;
     c.he = he.hi + he.lo;
     const ff dn = ff_sub(he, ff{R.dn_ff[0], R.dn_ff[1]}), dt = ff_sub(he, ff{R.dt_ff[0], R.dt_ff[1]}),
              dr = ff_sub(he, ff{R.dr_ff[0], R.dr_ff[1]});
@@ -192,68 +194,94 @@ __device__ __forceinline__ void m_rot(T c, T s, T a0, T a1, T a2, T a3, T m[4])
 // NOCONV or DEGENERATE (or such an overlap) give zeros.  T = float (mixed
 // mode) needs the per-call particle table pff (float-float axes): the frames,
 // curvatures and K~ run in FP32 with the axes rounded from it, the normal
-// relative velocity u3 in float-float (normal_velocity_ff).  T = double
-// ignores pff.
+// relative velocity u3 in float-float (normal_velocity_ff), and no step uses
+// the FP64 pipe.  T = double ignores pff.  The local relative velocities u
+// come first and each group of K~ elements is applied to them as soon as it
+// is formed, which keeps few values live at a time.
 template <typename T>
 __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int i, int j, const V3<double> &n64,
                                            double h, int &st, T out[12], const float2 *__restrict__ pff)
 {
+    constexpr bool MIXED = sizeof(T) == 4;
 #pragma unroll
     for (int a = 0; a < 12; ++a) out[a] = T(0);
-    bool skip = (st & (LUB_ST_NOCONV | LUB_ST_DEGENERATE)) != 0;
-    if (!skip && R.h_c <= 0.0 && h <= 0.0) {
+    if (st & (LUB_ST_NOCONV | LUB_ST_DEGENERATE)) return;
+    const CutTerms<T> cut = cut_terms(R, h, T(0));
+    if (!R.contact && cut.le0) {
         st |= LUB_ST_OVERLAP;
-        skip = true;
+        return;
     }
-    if (!skip) {
-        constexpr bool MIXED = sizeof(T) == 4;
-        const CutTerms<T> cut = cut_terms(R, h, T(0));
-        const V3<T> n = mk<T>((T)n64.x, (T)n64.y, (T)n64.z);
-        ff oi[3], oj[3];
-        Shape<T> si;
-        if constexpr (MIXED) {
-            ff_axis_of(pff, (size_t)P.n, i, oi);
-            si = shape_ff(oi, __ldg(P.rpar + i), __ldg(P.rperp + i));
-        } else {
-            si = load_shape<T>(P, i);
-        }
-        const V3<T> rho_i = support_offset(si, n);
-        const Surf<T> A = surface_at(si, rho_i, n);
-        const V3<T> x1 = A.x1, x3 = n, x2 = cross(x3, x1);
-        T c1p = 0, c2p = 0, G0p = 0, G2p = 0, cf = 1, sf = 0;
-        V3<T> rho_j = mk<T>(0, 0, 0);
-        V3<T> Vj = mk<T>(0, 0, 0), Wj = mk<T>(0, 0, 0);
+    // the normal (x3) and the shapes
+    V3<T> n;
+    ff nf[3], oi[3], oj[3];
+    Shape<T> si, sj;
+    if constexpr (MIXED) {
+        nf[0] = ff_split_bits(n64.x);
+        nf[1] = ff_split_bits(n64.y);
+        nf[2] = ff_split_bits(n64.z);
+        n = mk<T>(nf[0].hi, nf[1].hi, nf[2].hi);
+        ff_axis_of(pff, (size_t)P.n, i, oi);
+        si = shape_ff(oi, __ldg(P.rpar + i), __ldg(P.rperp + i));
         if (j >= 0) {
-            Shape<T> sj;
-            if constexpr (MIXED) {
-                ff_axis_of(pff, (size_t)P.n, j, oj);
-                sj = shape_ff(oj, __ldg(P.rpar + j), __ldg(P.rperp + j));
-            } else {
-                sj = load_shape<T>(P, j);
-            }
-            rho_j = scl(T(-1), support_offset(sj, n));
-            const Surf<T> B = surface_at(sj, rho_j, scl(T(-1), n));
-            c1p = B.c1;
-            c2p = B.c2;
-            G0p = B.G0;
-            G2p = B.G2;
-            cf = dot(B.x1, x1);
-            sf = dot(B.x1, x2);
-            const T r = rsqrt_t(cf * cf + sf * sf);
-            cf *= r;
-            sf *= r;
-            const V3<T> vj = mk<T>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j));
-            Wj = mk<T>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
-            Vj = add(vj, cross(Wj, rho_j));
+            ff_axis_of(pff, (size_t)P.n, j, oj);
+            sj = shape_ff(oj, __ldg(P.rpar + j), __ldg(P.rperp + j));
         }
-        // combined-gap matrix and its eigen-decomposition (Appendix)
-        const T A11 = T(0.5) * (A.c1 + cf * cf * c1p + sf * sf * c2p);
-        const T A12 = T(0.5) * sf * cf * (c1p - c2p);
-        const T A22 = T(0.5) * (A.c2 + sf * sf * c1p + cf * cf * c2p);
-        const T hd = T(0.5) * (A11 - A22);
-        const T rad = sqrt_t(hd * hd + A12 * A12);
-        const T l1 = T(0.5) * (A11 + A22) + rad;
-        const T l2 = (A11 * A22 - A12 * A12) / l1;
+    } else {
+        n = n64;
+        si = load_shape<T>(P, i);
+        if (j >= 0) sj = load_shape<T>(P, j);
+    }
+    T u3 = T(0);
+    if constexpr (MIXED) u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
+    // geometry at y*_i, the local frame x1, x2, x3 = n, and the relative velocities
+    const V3<T> rho_i = support_offset(si, n);
+    const Surf<T> A = surface_at(si, rho_i, n);
+    const V3<T> x1 = A.x1, x2 = cross(n, x1);
+    const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
+    V3<T> dV = scl(T(-1), add(mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i)), cross(Wi, rho_i)));
+    V3<T> dW = scl(T(-1), Wi);
+    T c1p = 0, c2p = 0, G0p = 0, G2p = 0, cf = 1, sf = 0;
+    V3<T> rho_j = mk<T>(0, 0, 0);
+    if (j >= 0) {
+        rho_j = scl(T(-1), support_offset(sj, n));
+        const Surf<T> B = surface_at(sj, rho_j, scl(T(-1), n));
+        c1p = B.c1;
+        c2p = B.c2;
+        G0p = B.G0;
+        G2p = B.G2;
+        cf = dot(B.x1, x1);
+        sf = dot(B.x1, x2);
+        const T r = rsqrt_t(cf * cf + sf * sf);
+        cf *= r;
+        sf *= r;
+        const V3<T> Wj = mk<T>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
+        dV = add(dV, add(mk<T>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j)), cross(Wj, rho_j)));
+        dW = add(dW, Wj);
+    }
+    const T u1 = dot(x1, dV), u2 = dot(x2, dV);
+    if constexpr (!MIXED) u3 = dot(n, dV);
+    const T u4 = dot(x1, dW), u5 = dot(x2, dW), u6 = dot(n, dW);
+    out[6] = rho_i.x; out[7] = rho_i.y; out[8] = rho_i.z;
+    out[9] = rho_j.x; out[10] = rho_j.y; out[11] = rho_j.z;
+    // combined-gap matrix and its eigen-decomposition (Appendix)
+    const T A11 = T(0.5) * (A.c1 + cf * cf * c1p + sf * sf * c2p);
+    const T A12 = T(0.5) * sf * cf * (c1p - c2p);
+    const T A22 = T(0.5) * (A.c2 + sf * sf * c1p + cf * cf * c2p);
+    const T hd = T(0.5) * (A11 - A22);
+    const T rad = sqrt_fast(hd * hd + A12 * A12);
+    const T l1 = T(0.5) * (A11 + A22) + rad;
+    const T il1 = rcp_fast(l1);
+    const T l2 = (A11 * A22 - A12 * A12) * il1;
+    const T il2 = rcp_fast(l2);
+    const T mu = MIXED ? (T)R.mu_f : (T)R.mu;
+    const T PI = T(3.14159265358979323846);
+    const T r1 = sqrt_fast(l1), r2 = sqrt_fast(l2);
+    const T isq = rcp_fast(r1 * r2);
+    const T il12 = rcp_fast(l1 + l2);
+    const T H33 = T(3) * PI * isq * il12;
+    const T hq = cut.in_n ? -cut.dn * rcp_fast(cut.he) * (MIXED ? (T)R.idn_f : rcp_fast((T)R.delta_n)) : T(0);
+    T F1 = 0, F2 = 0, F3 = hq * H33 * u3, T4 = 0, T5 = 0, T6 = 0;
+    if (R.model != LUB_MODEL_NORMAL) {
         T v0 = A12, v1 = l2 - A11;
         const T w0 = l2 - A22, w1 = A12;
         if (w0 * w0 + w1 * w1 > v0 * v0 + v1 * v1) {
@@ -270,111 +298,84 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
             sx = 0;
             cx = 1;
         }
-        if (R.model == LUB_MODEL_NORMAL) {
-            // "normal only" model (Sec. IV C): K~33 alone, H33 (1/h - 1/Delta_n),
-            // plus the contact branch; for two spheres Ladd's Eq. methods:llub
-            const T PI = T(3.14159265358979323846);
-            const T H33 = T(3) * PI / (sqrt_t(l1) * sqrt_t(l2) * (l1 + l2));
-            const T hq = cut.in_n ? -cut.dn / (cut.he * (T)R.delta_n) : T(0);
-            const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
-            const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
-            T u3;
-            if constexpr (MIXED) {
-                const ff nf[3] = {ff_from_double(n64.x), ff_from_double(n64.y), ff_from_double(n64.z)};
-                u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
-            } else {
-                u3 = dot(x3, sub(Vj, add(vi, cross(Wi, rho_i))));
-            }
-            T F3 = (T)R.mu * hq * H33 * u3;
-            if (cut.contact) F3 -= (T)R.eps_c * cut.fr;
-            out[0] = F3 * x3.x; out[1] = F3 * x3.y; out[2] = F3 * x3.z;
-            out[6] = rho_i.x; out[7] = rho_i.y; out[8] = rho_i.z;
-            out[9] = rho_j.x; out[10] = rho_j.y; out[11] = rho_j.z;
-            return;
-        }
-        // cubic terms
-        T beta[4], kap[4];
-        m_rot<T>(cf, sf, G0p, T(0), G2p, T(0), beta);
-        m_rot<T>(cx, sx, A.G0 + beta[0], beta[1], A.G2 + beta[2], beta[3], kap);
-        const T r1 = sqrt_t(l1), r2 = sqrt_t(l2);
-        const T ir1 = T(1) / r1, ir2 = T(1) / r2;
-        kap[0] *= ir1 * ir1 * ir1;
-        kap[1] *= ir1 * ir1 * ir2;
-        kap[2] *= ir1 * ir2 * ir2;
-        kap[3] *= ir2 * ir2 * ir2;
+        const T lt = cut.in_t ? log1p_t(cut.dt * (MIXED ? (T)R.idt_f : rcp_fast((T)R.delta_t))) : T(0);
+        const T lr = cut.in_r ? log1p_t(cut.dr * (MIXED ? (T)R.idr_f : rcp_fast((T)R.delta_r))) : T(0);
         // K: ln h coefficients (Appendix, (1 - lambda S)/S = c - lambda)
-        const T PI = T(3.14159265358979323846);
-        const T isq = T(1) / (r1 * r2);
-        const T iD1 = T(1) / ((T(3) * l1 + T(2) * l2) * l1);
-        const T iD2 = T(1) / ((T(2) * l1 + T(3) * l2) * l2);
+        const T iD1 = rcp_fast((T(3) * l1 + T(2) * l2) * l1);
+        const T iD2 = rcp_fast((T(2) * l1 + T(3) * l2) * l2);
         const T c2x = cx * cx, s2x = sx * sx, scx = sx * cx;
         const T c1 = A.c1, c2 = A.c2;
         const T a1 = c1 - l1, a2 = c1 - l2, b1 = c2 - l1, b2 = c2 - l2;
-        const T il12 = T(1) / (l1 + l2);
         const T p3 = T(3) * PI * isq;
-        const T L11 = -PI * isq * (T(3) * c2x * a1 * a1 * iD1 + T(3) * s2x * a2 * a2 * iD2 + T(1));
-        const T L12 = p3 * scx * (a1 * b1 * iD1 - a2 * b2 * iD2);
-        const T L14 = p3 * scx * (a1 * iD1 - a2 * iD2);
-        const T L15 = p3 * (c2x * a1 * iD1 + s2x * a2 * iD2);
-        const T L22 = -PI * isq * (T(3) * s2x * b1 * b1 * iD1 + T(3) * c2x * b2 * b2 * iD2 + T(1));
-        const T L24 = -p3 * (s2x * b1 * iD1 + c2x * b2 * iD2);
-        const T L25 = p3 * scx * (-b1 * iD1 + b2 * iD2);
-        const T L44 = -p3 * (s2x * iD1 + c2x * iD2);
-        const T L45 = p3 * scx * (-iD1 + iD2);
-        const T L55 = -p3 * (c2x * iD1 + s2x * iD2);
-        const T L36 = T(-1.5) * PI * isq * il12 * scx * (c1 - c2) * (T(1) / l1 - T(1) / l2);
-        const T H33 = T(3) * PI * isq * il12;
-        // cubic couplings K13, K23, K34, K35 (Gamma_1 = Gamma_3 = 0)
-        const T i3 = T(1) / (T(3) * l1 + T(2) * l2), i2 = T(1) / (T(2) * l1 + T(3) * l2);
-        const T Q0 = T(3) * kap[0] * l1 + kap[2] * l2;                     // 3 k0 l1 + k2 l2
-        const T Q1 = kap[1] * l1 + T(3) * kap[3] * l2;                     // k1 l1 + 3 k3 l2
-        const T Sa = (T(7) * l1 + T(2) * l2) * kap[0] + (l1 + T(2) * l2) * kap[2];
-        const T Sb = (T(2) * l1 + l2) * kap[1] + (T(2) * l1 + T(7) * l2) * kap[3];
-        const T pre13 = T(-1.5) * PI * isq * il12;
-        const T L13 = pre13 * ((T(2) * r1 * Q0 - T(1.5) * c1 * ir1 * Sa) * cx * i3 +
-                               (T(2) * r2 * Q1 - T(1.5) * c1 * ir2 * Sb) * sx * i2 +
-                               T(3) * A.G0 * (c2x / l1 + s2x / l2) + A.G2 * (s2x / l1 + c2x / l2));
-        const T L23 = pre13 * ((T(-2) * r1 * Q0 + T(1.5) * c2 * ir1 * Sa) * sx * i3 +
-                               (T(2) * r2 * Q1 - T(1.5) * c2 * ir2 * Sb) * cx * i2 +
-                               T(2) * A.G2 * scx * (T(1) / l2 - T(1) / l1));
-        const T pre34 = T(2.25) * PI * isq * il12;
-        const T Bq = Sb * ir2 * i2, Aq = Sa * ir1 * i3;
-        const T L34 = pre34 * (Bq * cx - Aq * sx);
-        const T L35 = -pre34 * (Aq * cx + Bq * sx);
-        // K~: subtract the value at the element's cut-off (Eq. lub:resistance-correction);
-        // he - Delta from cut_terms (accurate where it cancels), the quotients in T
-        const T lt = cut.in_t ? log1p_t(cut.dt / (T)R.delta_t) : T(0);
-        const T lr = cut.in_r ? log1p_t(cut.dr / (T)R.delta_r) : T(0);
-        const T hq = cut.in_n ? -cut.dn / (cut.he * (T)R.delta_n) : T(0);
-        // relative surface velocities in the local frame
-        const V3<T> vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
-        const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
-        const V3<T> Vi = add(vi, cross(Wi, rho_i));
-        const V3<T> dV = sub(Vj, Vi), dW = sub(Wj, Wi);
-        const T u1 = dot(x1, dV), u2 = dot(x2, dV);
-        T u3;
-        if constexpr (MIXED) {
-            const ff nf[3] = {ff_from_double(n64.x), ff_from_double(n64.y), ff_from_double(n64.z)};
-            u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
-        } else {
-            u3 = dot(x3, dV);
+        {  // translation-translation
+            const T L11 = -PI * isq * (T(3) * c2x * a1 * a1 * iD1 + T(3) * s2x * a2 * a2 * iD2 + T(1));
+            const T L12 = p3 * scx * (a1 * b1 * iD1 - a2 * b2 * iD2);
+            const T L22 = -PI * isq * (T(3) * s2x * b1 * b1 * iD1 + T(3) * c2x * b2 * b2 * iD2 + T(1));
+            F1 += lt * (L11 * u1 + L12 * u2);
+            F2 += lt * (L12 * u1 + L22 * u2);
         }
-        const T u4 = dot(x1, dW), u5 = dot(x2, dW), u6 = dot(x3, dW);
-        const T mu = (T)R.mu;
-        T F1 = mu * (lt * (L11 * u1 + L12 * u2 + L13 * u3 + L14 * u4 + L15 * u5));
-        T F2 = mu * (lt * (L12 * u1 + L22 * u2 + L23 * u3 + L24 * u4 + L25 * u5));
-        T F3 = mu * (lt * (L13 * u1 + L23 * u2 + L34 * u4 + L35 * u5 + L36 * u6) + hq * H33 * u3);
-        T T4 = mu * (lt * (L14 * u1 + L24 * u2 + L34 * u3) + lr * (L44 * u4 + L45 * u5));
-        T T5 = mu * (lt * (L15 * u1 + L25 * u2 + L35 * u3) + lr * (L45 * u4 + L55 * u5));
-        T T6 = mu * (lt * (L36 * u3));
-        if (cut.contact) F3 -= (T)R.eps_c * cut.fr;
-        const V3<T> F = axpy(F1, x1, axpy(F2, x2, scl(F3, x3)));
-        const V3<T> Tq = axpy(T4, x1, axpy(T5, x2, scl(T6, x3)));
-        out[0] = F.x; out[1] = F.y; out[2] = F.z;
-        out[3] = Tq.x; out[4] = Tq.y; out[5] = Tq.z;
-        out[6] = rho_i.x; out[7] = rho_i.y; out[8] = rho_i.z;
-        out[9] = rho_j.x; out[10] = rho_j.y; out[11] = rho_j.z;
+        {  // translation-rotation
+            const T L14 = p3 * scx * (a1 * iD1 - a2 * iD2);
+            const T L15 = p3 * (c2x * a1 * iD1 + s2x * a2 * iD2);
+            const T L24 = -p3 * (s2x * b1 * iD1 + c2x * b2 * iD2);
+            const T L25 = p3 * scx * (-b1 * iD1 + b2 * iD2);
+            F1 += lt * (L14 * u4 + L15 * u5);
+            F2 += lt * (L24 * u4 + L25 * u5);
+            T4 += lt * (L14 * u1 + L24 * u2);
+            T5 += lt * (L15 * u1 + L25 * u2);
+        }
+        {  // rotation-rotation
+            const T L44 = -p3 * (s2x * iD1 + c2x * iD2);
+            const T L45 = p3 * scx * (-iD1 + iD2);
+            const T L55 = -p3 * (c2x * iD1 + s2x * iD2);
+            T4 += lr * (L44 * u4 + L45 * u5);
+            T5 += lr * (L45 * u4 + L55 * u5);
+        }
+        {  // normal-twist coupling
+            const T L36 = T(-1.5) * PI * isq * il12 * scx * (c1 - c2) * (il1 - il2);
+            F3 += lt * L36 * u6;
+            T6 += lt * L36 * u3;
+        }
+        {  // cubic couplings K13, K23, K34, K35 (Gamma_1 = Gamma_3 = 0)
+            T beta[4], kap[4];
+            m_rot<T>(cf, sf, G0p, T(0), G2p, T(0), beta);
+            m_rot<T>(cx, sx, A.G0 + beta[0], beta[1], A.G2 + beta[2], beta[3], kap);
+            const T ir1 = rcp_fast(r1), ir2 = rcp_fast(r2);
+            kap[0] *= ir1 * ir1 * ir1;
+            kap[1] *= ir1 * ir1 * ir2;
+            kap[2] *= ir1 * ir2 * ir2;
+            kap[3] *= ir2 * ir2 * ir2;
+            const T i3 = rcp_fast(T(3) * l1 + T(2) * l2), i2 = rcp_fast(T(2) * l1 + T(3) * l2);
+            const T Q0 = T(3) * kap[0] * l1 + kap[2] * l2;  // 3 k0 l1 + k2 l2
+            const T Q1 = kap[1] * l1 + T(3) * kap[3] * l2;  // k1 l1 + 3 k3 l2
+            const T Sa = (T(7) * l1 + T(2) * l2) * kap[0] + (l1 + T(2) * l2) * kap[2];
+            const T Sb = (T(2) * l1 + l2) * kap[1] + (T(2) * l1 + T(7) * l2) * kap[3];
+            const T pre13 = T(-1.5) * PI * isq * il12;
+            const T L13 = pre13 * ((T(2) * r1 * Q0 - T(1.5) * c1 * ir1 * Sa) * cx * i3 +
+                                   (T(2) * r2 * Q1 - T(1.5) * c1 * ir2 * Sb) * sx * i2 +
+                                   T(3) * A.G0 * (c2x * il1 + s2x * il2) + A.G2 * (s2x * il1 + c2x * il2));
+            const T L23 = pre13 * ((T(-2) * r1 * Q0 + T(1.5) * c2 * ir1 * Sa) * sx * i3 +
+                                   (T(2) * r2 * Q1 - T(1.5) * c2 * ir2 * Sb) * cx * i2 +
+                                   T(2) * A.G2 * scx * (il2 - il1));
+            const T pre34 = T(2.25) * PI * isq * il12;
+            const T Bq = Sb * ir2 * i2, Aq = Sa * ir1 * i3;
+            const T L34 = pre34 * (Bq * cx - Aq * sx);
+            const T L35 = -pre34 * (Aq * cx + Bq * sx);
+            F1 += lt * L13 * u3;
+            F2 += lt * L23 * u3;
+            F3 += lt * (L13 * u1 + L23 * u2 + L34 * u4 + L35 * u5);
+            T4 += lt * L34 * u3;
+            T5 += lt * L35 * u3;
+        }
     }
+    F1 *= mu;
+    F2 *= mu;
+    F3 *= mu;
+    if (cut.contact) F3 -= (MIXED ? (T)R.eps_f : (T)R.eps_c) * cut.fr;
+    const V3<T> F = axpy(F1, x1, axpy(F2, x2, scl(F3, n)));
+    const V3<T> Tq = scl(mu, axpy(T4, x1, axpy(T5, x2, scl(T6, n))));
+    out[0] = F.x; out[1] = F.y; out[2] = F.z;
+    out[3] = Tq.x; out[4] = Tq.y; out[5] = Tq.z;
 }
 
 // contribution of a pair to particle i (side 0) or j (side 1) from
