@@ -162,6 +162,16 @@ typedef struct {
  * LUB_WARM_NONE, LUB_MODEL_FULL. */
 void lub_default_params(lub_params *p);
 
+/* Waits for the stream, then reports whether a bounded device wait of any
+ * call on this context timed out since the previous lub_sync_status (the
+ * look-back of a scan in lub_pairs_build or deterministic lub_apply, an
+ * mbarrier wait of the tcgen05 network), and clears that record.  A wait
+ * that runs out sets a bit in the context's device status word and returns
+ * instead of spinning on; the results of that call are then unreliable.
+ * No counterpart in the paper.  Errors: LUB_ERR_TIMEOUT, LUB_ERR_CUDA,
+ * LUB_ERR_ARG. */
+int lub_sync_status(lub_ctx *ctx, void *stream);
+
 /* Create a context (library-owned scratch, grown on demand by the calls that
  * need it: lub_pairs_build and deterministic lub_apply).  *ctx receives the
  * handle.  Errors: LUB_ERR_ARG (ctx NULL), LUB_ERR_NOMEM. */

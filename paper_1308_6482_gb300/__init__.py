@@ -24,7 +24,7 @@ from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, L
                    lub_ctx_create, lub_ctx_destroy, lub_default_params, lub_get_launch_shape, lub_last_error,
                    lub_links, lub_mlp_adam, lub_mlp_engine, lub_mlp_features, lub_mlp_forward_backward,
                    lub_mlp_predict, lub_mlp_set, lub_pairs_build, lub_pairs_build_static, lub_probe_peak, lub_random_motion,
-                   lub_resistance, lub_resistance_apply, lub_rigid_step, lub_set_launch_shape, lub_trace_enable,
+                   lub_resistance, lub_resistance_apply, lub_rigid_step, lub_set_launch_shape, lub_sync_status, lub_trace_enable,
                    lub_trace_read, make_domain, make_ensemble)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -5,7 +5,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "liblub.so")
+# LUB_LIBRARY selects another build of the library (the tests of the bounded
+# waits load the test build, liblub_testing.so, in a process of their own)
+_SO = os.environ.get("LUB_LIBRARY") or os.path.join(_HERE, "liblub.so")
 
 LUB_OK = 0
 LUB_ERR_ARG = -1
@@ -83,7 +85,7 @@ EXPORTS = ("lub_default_params", "lub_ctx_create", "lub_ctx_destroy", "lub_last_
            "lub_mlp_predict", "lub_mlp_features", "lub_mlp_forward_backward", "lub_mlp_adam", "lub_autotune",
            "lub_get_launch_shape", "lub_set_launch_shape", "lub_carry_normals", "lub_correct",
            "lub_resistance_apply", "lub_rigid_step", "lub_mlp_engine", "lub_links", "lub_trace_enable",
-           "lub_trace_read", "lub_probe_peak", "lub_random_motion")
+           "lub_trace_read", "lub_probe_peak", "lub_random_motion", "lub_sync_status")
 
 _lib = None
 
@@ -161,6 +163,8 @@ def load_library():
     lib.lub_trace_enable.argtypes = [vp, i32]
     lib.lub_trace_read.restype = ctypes.c_int
     lib.lub_trace_read.argtypes = [vp, i32, P(ctypes.c_double), P(ctypes.c_int64)]
+    lib.lub_sync_status.restype = ctypes.c_int
+    lib.lub_sync_status.argtypes = [vp, vp]
     lib.lub_random_motion.restype = ctypes.c_int
     lib.lub_random_motion.argtypes = [vp, P(lub_particles), ctypes.c_uint64, ctypes.c_int64, vp, vp,
                                       ctypes.c_double, ctypes.c_double, vp]
@@ -356,6 +360,11 @@ def lub_get_launch_shape(ctx, kernel):
 
 def lub_set_launch_shape(ctx, kernel, block, blocks_per_sm):
     return _check(ctx, load_library().lub_set_launch_shape(ctx, int(kernel), int(block), int(blocks_per_sm)))
+
+
+def lub_sync_status(ctx, stream=None):
+    """Raises LubError(LUB_ERR_TIMEOUT) if a bounded device wait timed out since the last check."""
+    return _check(ctx, load_library().lub_sync_status(ctx, _stream(stream)))
 
 
 def lub_trace_enable(ctx, on):

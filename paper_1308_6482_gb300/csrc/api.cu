@@ -221,6 +221,7 @@ int lub_ctx_create(lub_ctx **out)
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flags, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_flags, 0, 256);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         delete ctx;
@@ -243,6 +244,21 @@ int lub_ctx_destroy(lub_ctx *ctx)
     for (void *r : ctx->retired) cudaFree(r);
     lub_trace_free(ctx);
     delete ctx;
+    return LUB_OK;
+}
+
+int lub_sync_status(lub_ctx *ctx, void *stream)
+{
+    if (!ctx) return LUB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t word = 0;
+    int rc = lub_check_cuda(ctx, cudaMemcpyAsync(&word, ctx->d_flags + 1, 4, cudaMemcpyDeviceToHost, st),
+                            "copy status");
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemsetAsync(ctx->d_flags + 1, 0, 4, st), "clear status");
+    if (!rc) rc = lub_check_cuda(ctx, cudaStreamSynchronize(st), "sync");
+    if (rc) return rc;
+    if (word & 4) return lub_set_error(ctx, LUB_ERR_TIMEOUT, "a bounded wait of a scan look-back timed out");
+    if (word & 8) return lub_set_error(ctx, LUB_ERR_TIMEOUT, "a bounded mbarrier wait of the tcgen05 network timed out");
     return LUB_OK;
 }
 

@@ -75,8 +75,13 @@ __global__ void k_inc_fill(const int32_t *__restrict__ pi, const int32_t *__rest
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
         const int i = pi[k], j = pj[k];
         if (i < 0 || i >= n) continue;
-        inc[start[i] + atomicAdd(fill + i, 1)] = 2 * k;
-        if (j >= 0 && j < n) inc[start[j] + atomicAdd(fill + j, 1)] = 2 * k + 1;
+        // the slots stay inside the 2 cap entries even if the scan's offsets were wrong (a timed-out wait)
+        const int si = start[i] + atomicAdd(fill + i, 1);
+        if (si >= 0 && si < 2 * cap) inc[si] = 2 * k;
+        if (j >= 0 && j < n) {
+            const int sj = start[j] + atomicAdd(fill + j, 1);
+            if (sj >= 0 && sj < 2 * cap) inc[sj] = 2 * k + 1;
+        }
     }
 }
 
@@ -87,8 +92,8 @@ __global__ void k_inc_sum(const int32_t *__restrict__ start, const int32_t *__re
 {
     const size_t C = (size_t)cap, N = (size_t)n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int b = start[p];
-        const int e = (p + 1 < n) ? start[p + 1] : *total;
+        const int b = max(0, min(start[p], 2 * cap));
+        const int e = max(b, min((p + 1 < n) ? start[p + 1] : *total, 2 * cap));
         // insertion sort of this particle's entries (pair index, side)
         for (int a = b + 1; a < e; ++a) {
             const int v = inc[a];
@@ -162,7 +167,7 @@ int launch_apply(lub_ctx *ctx, const int32_t *pi, const int32_t *pj, const int32
     const int block = 256;
     const int gp = grid_for(cap > 0 ? cap : 1, block, ctx->num_sms, 8);
     k_inc_count<<<gp, block, 0, st>>>(pi, pj, d_count, cap, n, cnt);
-    rc = scan_exclusive(ctx, cnt, n, tot, tmp, b_tmp, st, nullptr);
+    rc = scan_exclusive(ctx, cnt, n, tot, tmp, b_tmp, st, ctx->d_flags + 1);
     if (rc) return rc;
     k_inc_fill<<<gp, block, 0, st>>>(pi, pj, d_count, cap, n, cnt, fill, inc);
     const int gn = grid_for(n, block, ctx->num_sms, 8);

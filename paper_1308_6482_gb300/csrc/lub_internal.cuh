@@ -19,7 +19,8 @@ struct lub_ctx {
     // growable device scratch
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
-    int32_t *d_flags = nullptr;  // [0]: overflow / error flags of the last call
+    int32_t *d_flags = nullptr;  // [0]: the last pair build's flags; [1]: timed-out waits since
+                                 // the last lub_sync_status (bit 2: a scan, bit 3: the tcgen05 network)
     void *mlp = nullptr;         // MlpDevice of the learned warm start (lub_mlp_set)
     void *mlp_mem = nullptr;     // its device storage
     bool mlp_ready = false;

@@ -218,7 +218,16 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 256;           // two threads per row: each takes 64 of its 128 columns
 constexpr uint32_t TC_TMEM_COLS = 128;    // every layer's accumulator in columns [0, 128)
-constexpr long kTcSpinLimit = 1l << 24;
+// bound of every mbarrier wait, in polls; a test build compiles a short one in
+#ifndef LUB_TC_SPIN_LIMIT
+#define LUB_TC_SPIN_LIMIT (1l << 24)
+#endif
+constexpr long kTcSpinLimit = LUB_TC_SPIN_LIMIT;
+#ifdef LUB_TESTING
+// a test build's hook: the elected thread issues no MMA and no commit, so
+// every wait for an MMA runs out (with no MMA in flight when TMEM is freed)
+__device__ int g_test_skip_mma = 0;
+#endif
 
 __host__ __device__ constexpr uint32_t cm_offset(int r, int k, int K)
 {
@@ -398,6 +407,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_start_tc(PView P, const __gr
     }
     bool alive = mbar_wait(mbw, 0);
     uint32_t phase = 0;
+#ifdef LUB_TESTING
+    const bool skip_mma = g_test_skip_mma != 0;
+#else
+    constexpr bool skip_mma = false;
+#endif
     const uint32_t sX = smem_u32(S.X), sH = smem_u32(S.H);
     const uint32_t sW1 = smem_u32(S.w.W1), sW2 = smem_u32(S.w.W2), sW3 = smem_u32(S.w.W3);
     const int count = pair_count(d_count, cap);
@@ -429,7 +443,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_start_tc(PView P, const __gr
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             tc_mma(tmem, tc_desc(sX, 128, 256), tc_desc(sW1, 128, 256), tc_idesc(128, 128), 0u);
             tc_commit(mbm);
         }
@@ -442,7 +456,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_start_tc(PView P, const __gr
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             for (uint32_t kk = 0; kk < 8; ++kk)
                 tc_mma(tmem, tc_desc(sH + 256 * kk, 128, 2048), tc_desc(sW2 + 256 * kk, 128, 2048),
                        tc_idesc(128, 128), kk);
@@ -459,7 +473,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_start_tc(PView P, const __gr
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             for (uint32_t kk = 0; kk < 8; ++kk)
                 tc_mma(tmem, tc_desc(sH + 256 * kk, 128, 2048), tc_desc(sW3 + 256 * kk, 128, 2048), tc_idesc(128, 16),
                        kk);
@@ -505,7 +519,7 @@ int launch_mlp_start_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &
         const int tiles = (cap + TC_ROWS - 1) / TC_ROWS;
         const int grid = tiles < 2 * ctx->num_sms ? (tiles > 0 ? tiles : 1) : 2 * ctx->num_sms;
         k_mlp_start_tc<ENS><<<grid, TC_THREADS, smem, st>>>(P, D, E, pi, pj, d_count, cap,
-                                                         (const TcImage *)M.tc_image, n0, pq, ctx->d_flags);
+                                                         (const TcImage *)M.tc_image, n0, pq, ctx->d_flags + 1);
         return lub_check_cuda(ctx, cudaGetLastError(), "k_mlp_start_tc launch");
     }
     const size_t smem = mlp_start_smem();
@@ -641,3 +655,12 @@ int launch_mlp_pack(lub_ctx *ctx, const float *params, const MlpDevice &M, cudaS
     k_mlp_pack<<<8, 256, 0, st>>>(params, M);
     return lub_check_cuda(ctx, cudaGetLastError(), "mlp pack launch");
 }
+
+#ifdef LUB_TESTING
+// Test build only (no counterpart in the product library): on != 0 makes the
+// tcgen05 network issue no MMA, so that its bounded mbarrier waits run out.
+extern "C" int lub_test_skip_tc_mma(int32_t on)
+{
+    return cudaMemcpyToSymbol(g_test_skip_mma, &on, sizeof(int)) == cudaSuccess ? LUB_OK : LUB_ERR_CUDA;
+}
+#endif

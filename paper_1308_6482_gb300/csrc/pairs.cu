@@ -629,7 +629,10 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
     const int64_t need = (int64_t)total + novf;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *d_count = need > cap ? (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX) : total;
-        if (flags_out) *flags_out = *flags;  // this build's flags, for the host-count path
+        if (flags_out) {
+            *flags_out = *flags;  // this build's flags, for the host-count path
+            if (*flags & 4) atomicOr(flags_out + 1, 4);  // a timed-out wait, for lub_sync_status
+        }
     }
     if (need > cap) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

@@ -17,6 +17,11 @@ namespace {
 
 using namespace scan_tile;
 
+#ifdef LUB_TESTING
+// a test build's hook: the tile that never publishes (-1: none)
+__device__ int g_test_mute_tile = -1;
+#endif
+
 // state: [0] ticket counter, [1 ..] one word per tile (zeroed before the launch)
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restrict__ a, int64_t n,
                                                                 unsigned long long *__restrict__ state,
@@ -28,7 +33,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(int32_t *__restr
     __shared__ int tile_s;
     if (threadIdx.x == 0) tile_s = (int)atomicAdd(state, 1ull);
     __syncthreads();
+#ifdef LUB_TESTING
+    scan_one_tile(a, n, state + 1, tile_s, d_total, err, g_test_mute_tile);
+#else
     scan_one_tile(a, n, state + 1, tile_s, d_total, err);
+#endif
 }
 
 // the aligned body in 16-byte words, the unaligned head and tail bytes by
@@ -80,3 +89,25 @@ int scan_exclusive(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, voi
                                      (unsigned long long *)tmp, d_total, err),
                           "scan launch");
 }
+
+#ifdef LUB_TESTING
+// Test build only (no counterpart in the product library): one exclusive scan
+// of n int32 values at data, in place, with tile mute_tile never publishing
+// (-1: a plain scan); a timed-out look-back raises the context's timeout
+// word, which lub_sync_status reports.
+extern "C" int lub_test_scan(lub_ctx *ctx, int32_t *data, int64_t n, int32_t *d_total, int32_t mute_tile, void *stream)
+{
+    if (!ctx || !data || n < 1) return LUB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = lub_ensure_scratch(ctx, scan_tmp_bytes(n));
+    if (rc) return rc;
+    rc = lub_check_cuda(ctx, cudaMemcpyToSymbolAsync(g_test_mute_tile, &mute_tile, sizeof(int), 0,
+                                                     cudaMemcpyHostToDevice, st), "mute tile");
+    if (!rc) rc = scan_exclusive(ctx, data, n, d_total, ctx->scratch, ctx->scratch_bytes, st, ctx->d_flags + 1);
+    const int none = -1;
+    if (!rc) rc = lub_check_cuda(ctx, cudaMemcpyToSymbolAsync(g_test_mute_tile, &none, sizeof(int), 0,
+                                                              cudaMemcpyHostToDevice, st), "mute tile");
+    if (!rc) rc = lub_check_cuda(ctx, cudaStreamSynchronize(st), "sync");
+    return rc;
+}
+#endif

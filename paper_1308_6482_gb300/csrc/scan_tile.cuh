@@ -20,7 +20,12 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr unsigned long long ST_AGG = 1ull << 32;     // tile total published
 constexpr unsigned long long ST_PREFIX = 2ull << 32;  // inclusive prefix published
-constexpr long kSpinLimit = 1l << 22;                 // ~2 s of L2 round trips
+// bound of every look-back wait, in polls (~2 s of L2 round trips); a test
+// build compiles a short one in
+#ifndef LUB_SCAN_SPIN_LIMIT
+#define LUB_SCAN_SPIN_LIMIT (1l << 22)
+#endif
+constexpr long kSpinLimit = LUB_SCAN_SPIN_LIMIT;
 
 __host__ __device__ inline int64_t tiles_of(int64_t n)
 {
@@ -64,10 +69,14 @@ __device__ __forceinline__ unsigned long long load_state(const unsigned long lon
 
 // Scan tile `tile` of a[0, n) in place.  tstate: one word per tile, zero
 // before the scan.  The tile holding the last element writes the total to
-// *d_total.  All SCAN_THREADS threads of the block call it.
+// *d_total.  All SCAN_THREADS threads of the block call it.  mute_tile (a
+// test build's hook, -1 otherwise): that tile never publishes, as if its
+// block never ran, so that the next tile's look-back runs out.
 __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n, unsigned long long *tstate, int tile,
-                                              int32_t *__restrict__ d_total, int32_t *__restrict__ err)
+                                              int32_t *__restrict__ d_total, int32_t *__restrict__ err,
+                                              int mute_tile = -1)
 {
+    const bool mute = tile == mute_tile;
     __shared__ int prefix_s;
     const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
@@ -86,9 +95,9 @@ __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n
         const int lane = threadIdx.x;
         int excl = 0;
         if (tile == 0) {
-            if (lane == 0) atomicExch(tstate, ST_PREFIX | (unsigned)tot);
+            if (lane == 0 && !mute) atomicExch(tstate, ST_PREFIX | (unsigned)tot);
         } else {
-            if (lane == 0) atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
+            if (lane == 0 && !mute) atomicExch(tstate + tile, ST_AGG | (unsigned)tot);
             long spins = 0;
             int top = tile - 1;
             while (true) {
@@ -114,7 +123,7 @@ __device__ __forceinline__ void scan_one_tile(int32_t *__restrict__ a, int64_t n
                 if (stop < 32) break;
                 top -= 32;
             }
-            if (lane == 0) atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
+            if (lane == 0 && !mute) atomicExch(tstate + tile, ST_PREFIX | (unsigned)(excl + tot));
         }
         if (lane == 0) {
             prefix_s = excl;
