@@ -53,9 +53,11 @@
  *   - With h_c = 0 a pair with h <= 0 contributes nothing (status OVERLAP).
  *   - The appendix signs of K13, K23, K34, K35 are used as printed.
  *
- * Parity unpinned: the joint overall sign of the pair (K13, K23) and of the
- * pair (K34, K35).  Exchange symmetry fixes each element's sign relative to
- * the others in its pair, but not a simultaneous flip of both.
+ * The joint overall sign of the pair (K13, K23) and of the pair (K34, K35),
+ * which the exchange symmetry cannot see, is pinned (with the elements'
+ * values) by lubrication theory solved numerically: the Reynolds equation
+ * for a squeeze between the exact spheroid surfaces, the ln h coefficient of
+ * the force and torque on i taken from two small gaps (the thin-film tests).
  */
 #include <math.h>
 #include <stdint.h>
