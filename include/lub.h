@@ -343,10 +343,11 @@ int lub_mlp_adam(lub_ctx *ctx, float *params, const float *grads, float *m, floa
 /*
  * The pair build of lub_pairs_build, for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is an interface for host codes
- * that capture their whole time step into a CUDA graph (cudaMalloc cannot be
- * captured) or that own a fixed device-memory budget and forbid allocation
- * after start-up (cudaMalloc synchronises the device and can fail mid-run).
- * Such callers cannot create a lub_ctx, so this call takes none.
+ * that own a fixed device-memory budget and forbid allocation after
+ * start-up, for instance because cudaMalloc synchronises the whole device
+ * (stalling the other streams of a running simulation) and can fail in the
+ * middle of a run.  Such callers cannot create a lub_ctx, so this call
+ * takes none.
  *
  * It computes exactly what lub_pairs_build computes (same arguments, same
  * output order and *d_count), on a scratch array of LUB_STATIC_SCRATCH_BYTES

@@ -17,6 +17,7 @@ LUB_ERR_TIMEOUT = -4
 LUB_ERR_NOMEM = -5
 LUB_ERR_LIMIT = -6
 LUB_STATIC_MAX_PARTICLES = 65536
+LUB_STATIC_MAX_CELLS = 262144
 LUB_FP64 = 0
 LUB_MIXED = 1
 LUB_WARM_NONE = 0

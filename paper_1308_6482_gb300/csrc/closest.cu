@@ -449,17 +449,19 @@ __device__ __forceinline__ int wl_total(const int32_t *__restrict__ wl_count, in
 // float-float copies (hi, lo) of the positions, [3][n], then of the
 // symmetry axes, [3][n] (one float-float axis per particle instead of one per
 // pair and side)
-__global__ void __launch_bounds__(256) k_particles_ff(PView P, float2 *__restrict__ out)
+__global__ void __launch_bounds__(256) k_particles_ff(PView P, float2 *__restrict__ out, int with_positions)
 {
     pdl_wait();
     pdl_trigger();
     const size_t N = (size_t)P.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const double v[3] = {P.x[i], P.y[i], P.z[i]};
+        if (with_positions) {
+            const double v[3] = {P.x[i], P.y[i], P.z[i]};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const ff p = ff_from_double(v[a]);
-            out[a * N + i] = make_float2(p.hi, p.lo);
+            for (int a = 0; a < 3; ++a) {
+                const ff p = ff_from_double(v[a]);
+                out[a * N + i] = make_float2(p.hi, p.lo);
+            }
         }
         ff o[3];
         ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
@@ -828,10 +830,12 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
 
 }  // namespace
 
-int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st)
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st, bool with_positions)
 {
     if (P.n == 0) return LUB_OK;
-    return lub_check_cuda(ctx, launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P, out),
+    return lub_check_cuda(ctx,
+                          launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P, out,
+                                     with_positions ? 1 : 0),
                           "particle table launch");
 }
 
@@ -858,7 +862,7 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     rc = zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
     if (rc || !P) return rc;
     *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
-    return launch_particles_ff(ctx, *P, *pff, st);
+    return launch_particles_ff(ctx, *P, *pff, st, true);
 }
 
 template <bool ENS>

@@ -44,11 +44,12 @@ __device__ __forceinline__ ff rot_normal_ff(const ff n[3], const ff o[3], float 
 {
     if (rpar == rperp) return ff_make(0.0f);
     const ff a2 = two_prod(rperp, rperp), e = ff_sub(two_prod(rpar, rpar), a2);
-    const ff c = ff_dot3(o, n);
+    const ff c = ff_dot3_c(o, n);
     const ff k = ff_mul(ff_mul(e, c), ff_rsqrt(ff_add(a2, ff_mul(e, ff_mul(c, c)))));
-    const ff wo[3] = {ff_sub(ff_mulf(o[2], wy), ff_mulf(o[1], wz)), ff_sub(ff_mulf(o[0], wz), ff_mulf(o[2], wx)),
-                      ff_sub(ff_mulf(o[1], wx), ff_mulf(o[0], wy))};
-    return ff_mul(k, ff_dot3(n, wo));
+    // w x o, each component compensated (w is exact)
+    const ff wo[3] = {ff_cross_comp_f(wy, o[2], wz, o[1]), ff_cross_comp_f(wz, o[0], wx, o[2]),
+                      ff_cross_comp_f(wx, o[1], wy, o[0])};
+    return ff_mul(k, ff_dot3_c(n, wo));
 }
 
 // The normal relative surface velocity u3 = n.(V_j - V_i), V = v + w x (y* - r)
@@ -72,7 +73,7 @@ __device__ __forceinline__ float normal_velocity_ff(const PView &P, const float2
                                  __ldg(P.wz + j)));
     }
     const ff dv[3] = {two_sum(vj[0], -vi[0]), two_sum(vj[1], -vi[1]), two_sum(vj[2], -vi[2])};
-    u = ff_add(u, ff_dot3(n, dv));
+    u = ff_add(u, ff_dot3_c(n, dv));
     u = ff_sub(u, rot_normal_ff(n, oi, __ldg(P.rpar + i), __ldg(P.rperp + i), __ldg(P.wx + i), __ldg(P.wy + i),
                                 __ldg(P.wz + i)));
     return __fadd_rn(u.hi, u.lo);
@@ -394,29 +395,31 @@ __device__ __forceinline__ void side_contrib(const T out[12], int side, T c[6])
 
 // Warp-collective (every lane of the warp calls it): atomic adds of the i-
 // and j-side contributions ci, cj to force/torque [3][n].  Lanes with i < 0
-// add nothing, lanes with j < 0 (walls) add no j side.  Lanes that share i
-// (pairs sorted by i) are summed first with a segmented warp reduction, so
-// the i side needs one atomic per run of equal i.
+// add nothing, lanes with j < 0 (walls) add no j side.  The i sides of a run
+// of lanes with equal i (pairs sorted by i) are summed first by a segmented
+// warp scan (five shuffle steps, the same for every lane; runs are told
+// apart by their index among the warp's runs, so that equal i in two
+// separate runs never mix), and the run's last lane makes one atomic add.
 template <typename T>
 __device__ __forceinline__ void scatter_warp(int i, int j, size_t N, T ci[6], const T cj[6], T *__restrict__ force,
                                              T *__restrict__ torque)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(0xffffffffu, i);
-    const int leader = __ffs(peers) - 1;
+    const int iprev = __shfl_up_sync(0xffffffffu, i, 1), inext = __shfl_down_sync(0xffffffffu, i, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || i != iprev);
+    const int run = __popc(heads & (0xffffffffu >> (31 - lane)));  // runs started at or before this lane
 #pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        const T v = ci[a];
-        T s = T(0);
-        unsigned m = peers;
-        while (m) {
-            const int src = __ffs(m) - 1;
-            m &= m - 1;
-            s += __shfl_sync(peers, v, src);
+    for (int off = 1; off < 32; off <<= 1) {
+        const int rup = __shfl_up_sync(0xffffffffu, run, off);
+        const bool same = lane >= off && rup == run;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const T y = __shfl_up_sync(0xffffffffu, ci[a], off);
+            if (same) ci[a] += y;
         }
-        ci[a] = s;
     }
-    if (i >= 0 && lane == leader) {
+    const bool tail = lane == 31 || inext != i;
+    if (i >= 0 && tail) {
         atomicAdd(force + i, ci[0]);
         atomicAdd(force + N + i, ci[1]);
         atomicAdd(force + 2 * N + i, ci[2]);

@@ -1,11 +1,10 @@
 // lub_pairs_build_static: the candidate-pair build without any allocation.
 //
-// Some callers cannot allocate device memory while they run: a simulation
-// that captures its whole time step into a CUDA graph (cudaMalloc cannot be
-// captured), or a host code that owns a fixed device-memory budget and
-// forbids allocation after start-up (cudaMalloc synchronises the device and
-// may fail mid-run).  They cannot create a lub_ctx either, since that
-// allocates.  This entry point runs the same kernels as lub_pairs_build on a
+// Some callers cannot allocate device memory while they run: a host code
+// that owns a fixed device-memory budget and forbids allocation after
+// start-up, for instance because cudaMalloc synchronises the whole device
+// (stalling its other streams) and may fail mid-run.  They cannot create a
+// lub_ctx either, since that allocates.  This entry point runs the same kernels as lub_pairs_build on a
 // fixed scratch array that lives in this file as a static __device__ array:
 // every GPU that loads the library holds it (LUB_STATIC_SCRATCH_BYTES) until
 // the process exits.

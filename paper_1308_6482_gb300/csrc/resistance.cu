@@ -107,7 +107,7 @@ static int particle_table(lub_ctx *ctx, const PView &P, cudaStream_t st, const f
     int rc = lub_ensure_scratch(ctx, particles_ff_bytes(P.n));
     if (rc) return rc;
     *pff = (const float2 *)ctx->scratch;
-    return launch_particles_ff(ctx, P, (float2 *)ctx->scratch, st);
+    return launch_particles_ff(ctx, P, (float2 *)ctx->scratch, st, false);
 }
 
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,

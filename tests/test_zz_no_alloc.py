@@ -1,11 +1,14 @@
 """lub_pairs_build_static: the pair build for callers that cannot allocate
-device memory (a host code that captures its whole time step into a CUDA
-graph, or one that forbids allocation after start-up).  It runs on a fixed
-static device array of the library instead of a context's scratch.
+device memory (a host code that owns a fixed device-memory budget and
+forbids allocation after start-up, since cudaMalloc synchronises the device
+and can fail mid-run).  It runs on a fixed static device array of the
+library instead of a context's scratch.
 
 Checked through the C ABI against lub_pairs_build on two calls in a row with
 different inputs (the array keeps the previous call's contents, so the second
-call shows that what must start at zero is cleared), plus the size limit.
+call shows that what must start at zero is cleared), on a sparse box whose
+natural cell grid exceeds the array's cell limit (the coarsened grid), plus
+the size limit.
 """
 import ctypes
 
@@ -56,6 +59,25 @@ def test_static_scratch_matches_context_build_twice(lub):
     parts2, dom2 = gen.config_prolate_wall(seed=3)
     m2 = _static_vs_context(lub, parts2, dom2)
     assert m1 > 10000 and m2 > 0
+
+
+def test_static_coarsens_a_grid_beyond_its_cell_limit(lub):
+    # 20,000 unit spheres placed uniformly in a periodic 400^3 box: cells of
+    # the full range (2 r + Delta_L = 3) would be 133^3 = 2.4M, above
+    # LUB_STATIC_MAX_CELLS; the static build coarsens its grid and must still
+    # list the same pairs as the context build
+    rng = np.random.default_rng(17)
+    n, L = 20000, 400.0
+    c = rng.uniform(0.0, L, size=(n, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    parts = dict(x=c[:, 0], y=c[:, 1], z=c[:, 2], qw=q[:, 0].astype(np.float32), qx=q[:, 1].astype(np.float32),
+                 qy=q[:, 2].astype(np.float32), qz=q[:, 3].astype(np.float32),
+                 r_par=np.ones(n, np.float32), r_perp=np.ones(n, np.float32))
+    gen.velocities(parts, rng)
+    dom = dict(L=(L, L, L), periodic=(True, True, True), walls=[])
+    assert n <= lub._lib.LUB_STATIC_MAX_PARTICLES and (L / 3.0) ** 3 > lub._lib.LUB_STATIC_MAX_CELLS
+    assert _static_vs_context(lub, parts, dom) > 100
 
 
 def test_static_rejects_sizes_beyond_its_limit(lub):
