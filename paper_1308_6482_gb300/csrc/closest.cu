@@ -144,18 +144,19 @@ __device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o
 }
 
 // Minimum-image separation r_j - r_i in float-float from the particles'
-// float-float positions (pff: [3][N] (hi, lo)); the image shift is taken from
-// the float part (listed pairs are far from the ambiguous half box).  About
-// 48 bits: an absolute error near 2^-48 |r| (4e-12 at |r| = 1000), against
-// the FP64 subtraction and splitting it replaces (some 24 FP64 operations per
-// pair, at 1/64 of the FP32 rate).
-__device__ __forceinline__ void ff_separation(const float2 *__restrict__ pff, size_t N, int i, int j,
-                                              const DView &D, ff d[3])
+// records (rec_ld 0 and 1: the float-float centres); the image shift is
+// taken from the float part (listed pairs are far from the ambiguous half
+// box).  About 48 bits: an absolute error near 2^-48 |r| (4e-12 at |r| =
+// 1000), against the FP64 subtraction and splitting it replaces (some 24
+// FP64 operations per pair, at 1/64 of the FP32 rate).
+__device__ __forceinline__ void ff_separation(const float4 &ri0, const float4 &ri1, const float4 &rj0,
+                                              const float4 &rj1, const DView &D, ff d[3])
 {
+    const ff pi[3] = {{ri0.x, ri0.y}, {ri0.z, ri0.w}, {ri1.x, ri1.y}};
+    const ff pj[3] = {{rj0.x, rj0.y}, {rj0.z, rj0.w}, {rj1.x, rj1.y}};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float2 pi = __ldg(pff + a * N + i), pj = __ldg(pff + a * N + j);
-        ff da = ff_sub(ff{pj.x, pj.y}, ff{pi.x, pi.y});
+        ff da = ff_sub(pj[a], pi[a]);
         if (D.periodic[a]) {
             const float k = rintf(da.hi * D.invLf[a]);
             if (k != 0.f) da = ff_sub(da, ff{k * D.Lff[a][0], k * D.Lff[a][1]});
@@ -288,12 +289,11 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
     } else if (j < 0) {
         h = wall_gap(P, D, i, -1 - j, n64);
     } else {
-        const size_t N = (size_t)P.n;
+        const float4 ri0 = rec_ld(pff, i, 0), ri1 = rec_ld(pff, i, 1), rj0 = rec_ld(pff, j, 0), rj1 = rec_ld(pff, j, 1);
         ff dff[3];
-        ff_separation(pff, N, i, j, D, dff);
+        ff_separation(ri0, ri1, rj0, rj1, D, dff);
         const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
-        const float rpi = __ldg(P.rpar + i), rqi = __ldg(P.rperp + i);
-        const float rpj = __ldg(P.rpar + j), rqj = __ldg(P.rperp + j);
+        const float rpi = ri1.z, rqi = ri1.w, rpj = rj1.z, rqj = rj1.w;
         const ff dd = ff_dot3(dff, dff);
         if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
             st = LUB_ST_DEGENERATE;
@@ -305,8 +305,8 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             h = ff_to_double(ff_sub(ff_sub(ff_mul(dd, rs), ff_make(rpi)), ff_make(rpj)));
         } else {
             ff oi[3], oj[3];
-            ff_axis_of(pff, N, i, oi);
-            ff_axis_of(pff, N, j, oj);
+            ff_axis_rec(rec_ld(pff, i, 2), rec_ld(pff, i, 3), oi);
+            ff_axis_rec(rec_ld(pff, j, 2), rec_ld(pff, j, 3), oj);
             const Shape<float> si = shape_ff(oi, rpi, rqi), sj = shape_ff(oj, rpj, rqj);
             const float dl = sqrtf(dd.hi);
             V3<float> n = scl(1.0f / dl, df);
@@ -445,28 +445,33 @@ __device__ __forceinline__ int wl_total(const int32_t *__restrict__ wl_count, in
 // ---------------------------------------------------------------------------
 // lub_closest_points kernels
 // ---------------------------------------------------------------------------
-// The per-call particle table of the FP32 stage and the FP32 resistance:
-// float-float copies (hi, lo) of the positions, [3][n], then of the
-// symmetry axes, [3][n] (one float-float axis per particle instead of one per
-// pair and side)
-__global__ void __launch_bounds__(256) k_particles_ff(PView P, float2 *__restrict__ out, int with_positions)
+// The per-call particle records of the FP32 stage and the FP32 resistance
+// (rec_ld): float-float centre and symmetry axis, semi-axes and velocities,
+// five float4 per particle (one float-float axis per particle instead of one
+// per pair and side; four 16-byte loads fetch what a kernel needs)
+__global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restrict__ out)
 {
     pdl_wait();
     pdl_trigger();
-    const size_t N = (size_t)P.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        if (with_positions) {
-            const double v[3] = {P.x[i], P.y[i], P.z[i]};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const ff p = ff_from_double(v[a]);
-                out[a * N + i] = make_float2(p.hi, p.lo);
-            }
-        }
+        const ff x = ff_from_double(P.x[i]), y = ff_from_double(P.y[i]), z = ff_from_double(P.z[i]);
         ff o[3];
         ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) out[(3 + a) * N + i] = make_float2(o[a].hi, o[a].lo);
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (P.vx) {
+            v[0] = P.vx[i];
+            v[1] = P.vy[i];
+            v[2] = P.vz[i];
+            v[3] = P.wx[i];
+            v[4] = P.wy[i];
+            v[5] = P.wz[i];
+        }
+        float4 *r = out + (size_t)i * kRec;
+        r[0] = make_float4(x.hi, x.lo, y.hi, y.lo);
+        r[1] = make_float4(z.hi, z.lo, P.rpar[i], P.rperp[i]);
+        r[2] = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+        r[3] = make_float4(o[2].hi, o[2].lo, v[0], v[1]);
+        r[4] = make_float4(v[2], v[3], v[4], v[5]);
     }
 }
 
@@ -830,12 +835,12 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
 
 }  // namespace
 
-int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st, bool with_positions)
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st)
 {
     if (P.n == 0) return LUB_OK;
     return lub_check_cuda(ctx,
-                          launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P, out,
-                                     with_positions ? 1 : 0),
+                          launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P,
+                                     reinterpret_cast<float4 *>(out)),
                           "particle table launch");
 }
 
@@ -862,7 +867,7 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     rc = zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
     if (rc || !P) return rc;
     *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
-    return launch_particles_ff(ctx, *P, *pff, st, true);
+    return launch_particles_ff(ctx, *P, *pff, st);
 }
 
 template <bool ENS>

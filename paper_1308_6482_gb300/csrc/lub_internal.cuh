@@ -495,12 +495,12 @@ inline Shape2 tuned_shape(const lub_ctx *ctx, int id, int64_t work)
     return s;
 }
 
-// The per-call particle table of the mixed mode: float-float (hi, lo)
-// positions [3][n] then symmetry axes [3][n] (float2 each), written by one
-// kernel on the stream; `out` holds particles_ff_bytes(n) bytes.  Without
-// positions only the axes are written (the resistance reads no positions).
-inline size_t particles_ff_bytes(int64_t n) { return 48 * (size_t)(n > 0 ? n : 0); }
-int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st, bool with_positions);
+// The per-call particle records of the mixed mode (five float4 per
+// particle: float-float centre and axis, semi-axes, velocities; see rec_ld),
+// written by one kernel on the stream; `out` (16-byte aligned) holds
+// particles_ff_bytes(n) bytes.
+inline size_t particles_ff_bytes(int64_t n) { return 80 * (size_t)(n > 0 ? n : 0); }
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st);
 
 // pair build on caller-provided scratch (no allocation)
 size_t pairs_scratch_bytes(int64_t n, int64_t max_cells);

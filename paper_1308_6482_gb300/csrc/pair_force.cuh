@@ -11,15 +11,25 @@
 
 namespace {
 
-// the float-float symmetry axis of particle k from a per-call particle table
-// (pff: [3][N] float-float positions, then [3][N] float-float axes)
-__device__ __forceinline__ void ff_axis_of(const float2 *__restrict__ pff, size_t N, int k, ff o[3])
+// The per-call particle record of the mixed mode (pff, written by
+// k_particles_ff): five float4 per particle, so that a kernel fetches a
+// particle's data with four 16-byte loads from two or three sectors instead
+// of a dozen scalar loads from as many arrays:
+//   [0] x.hi x.lo y.hi y.lo    [1] z.hi z.lo r_par r_perp
+//   [2] ox.hi ox.lo oy.hi oy.lo [3] oz.hi oz.lo vx vy    [4] vz wx wy wz
+// (float-float centre and symmetry axis, semi-axes, velocities).
+constexpr int kRec = 5;
+__device__ __forceinline__ float4 rec_ld(const float2 *__restrict__ pff, int k, int q)
 {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float2 v = __ldg(pff + (3 + a) * N + k);
-        o[a] = ff{v.x, v.y};
-    }
+    return __ldg(reinterpret_cast<const float4 *>(pff) + (size_t)k * kRec + q);
+}
+
+// the float-float symmetry axis from records 2 and 3
+__device__ __forceinline__ void ff_axis_rec(const float4 &r2, const float4 &r3, ff o[3])
+{
+    o[0] = ff{r2.x, r2.y};
+    o[1] = ff{r2.z, r2.w};
+    o[2] = ff{r3.x, r3.y};
 }
 
 // FP32 shape with the axis rounded from its float-float value
@@ -59,23 +69,20 @@ __device__ __forceinline__ ff rot_normal_ff(const ff n[3], const ff o[3], float 
 // rho_j = -M_j n / sigma_j,
 //   u3 = n.(v_j - v_i) - k_i n.(w_i x o_i) - k_j n.(w_j x o_j),
 // v_j - v_i exact (TwoSum), the rest in float-float.  j < 0: a wall at rest.
-__device__ __forceinline__ float normal_velocity_ff(const PView &P, const float2 *__restrict__ pff, int i, int j,
-                                                    const ff n[3], const ff oi[3], const ff oj[3])
+// (shapes, velocities and angular velocities as floats; j < 0: a wall at rest)
+__device__ __forceinline__ float normal_velocity_ff(const ff n[3], const ff oi[3], float rpi, float rqi,
+                                                    const V3<float> &vi, const V3<float> &wi, int j, const ff oj[3],
+                                                    float rpj, float rqj, const V3<float> &vj, const V3<float> &wj)
 {
-    const float vi[3] = {__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i)};
-    float vj[3] = {0.f, 0.f, 0.f};
     ff u = ff_make(0.0f);
+    V3<float> vjj = mk<float>(0.f, 0.f, 0.f);
     if (j >= 0) {
-        vj[0] = __ldg(P.vx + j);
-        vj[1] = __ldg(P.vy + j);
-        vj[2] = __ldg(P.vz + j);
-        u = ff_neg(rot_normal_ff(n, oj, __ldg(P.rpar + j), __ldg(P.rperp + j), __ldg(P.wx + j), __ldg(P.wy + j),
-                                 __ldg(P.wz + j)));
+        vjj = vj;
+        u = ff_neg(rot_normal_ff(n, oj, rpj, rqj, wj.x, wj.y, wj.z));
     }
-    const ff dv[3] = {two_sum(vj[0], -vi[0]), two_sum(vj[1], -vi[1]), two_sum(vj[2], -vi[2])};
+    const ff dv[3] = {two_sum(vjj.x, -vi.x), two_sum(vjj.y, -vi.y), two_sum(vjj.z, -vi.z)};
     u = ff_add(u, ff_dot3_c(n, dv));
-    u = ff_sub(u, rot_normal_ff(n, oi, __ldg(P.rpar + i), __ldg(P.rperp + i), __ldg(P.wx + i), __ldg(P.wy + i),
-                                __ldg(P.wz + i)));
+    u = ff_sub(u, rot_normal_ff(n, oi, rpi, rqi, wi.x, wi.y, wi.z));
     return __fadd_rn(u.hi, u.lo);
 }
 
@@ -193,7 +200,7 @@ __device__ __forceinline__ void m_rot(T c, T s, T a0, T a1, T a2, T a3, T m[4])
 // out = (F_i, T_i, y*_i - r_i, y*_j - r_j).  st carries the pair's status
 // bits in and gains OVERLAP when h <= 0 without a contact model; pairs with
 // NOCONV or DEGENERATE (or such an overlap) give zeros.  T = float (mixed
-// mode) needs the per-call particle table pff (float-float axes): the frames,
+// mode) needs the per-call particle records pff (rec_ld): the frames,
 // curvatures and K~ run in FP32 with the axes rounded from it, the normal
 // relative velocity u3 in float-float (normal_velocity_ff), and no step uses
 // the FP64 pipe.  T = double ignores pff.  The local relative velocities u
@@ -212,34 +219,45 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         st |= LUB_ST_OVERLAP;
         return;
     }
-    // the normal (x3) and the shapes
-    V3<T> n;
-    ff nf[3], oi[3], oj[3];
-    Shape<T> si, sj;
+    // the normal (x3), the shapes and the velocities
+    V3<T> n, vi, Wi, vj = mk<T>(0, 0, 0), Wj = mk<T>(0, 0, 0);
+    Shape<T> si, sj = {};
+    T u3 = T(0);
     if constexpr (MIXED) {
+        ff nf[3], oi[3], oj[3];
         nf[0] = ff_split_bits(n64.x);
         nf[1] = ff_split_bits(n64.y);
         nf[2] = ff_split_bits(n64.z);
         n = mk<T>(nf[0].hi, nf[1].hi, nf[2].hi);
-        ff_axis_of(pff, (size_t)P.n, i, oi);
-        si = shape_ff(oi, __ldg(P.rpar + i), __ldg(P.rperp + i));
+        const float4 a1 = rec_ld(pff, i, 1), a2 = rec_ld(pff, i, 2), a3 = rec_ld(pff, i, 3), a4 = rec_ld(pff, i, 4);
+        ff_axis_rec(a2, a3, oi);
+        si = shape_ff(oi, a1.z, a1.w);
+        vi = mk<T>(a3.z, a3.w, a4.x);
+        Wi = mk<T>(a4.y, a4.z, a4.w);
         if (j >= 0) {
-            ff_axis_of(pff, (size_t)P.n, j, oj);
-            sj = shape_ff(oj, __ldg(P.rpar + j), __ldg(P.rperp + j));
+            const float4 b1 = rec_ld(pff, j, 1), b2 = rec_ld(pff, j, 2), b3 = rec_ld(pff, j, 3), b4 = rec_ld(pff, j, 4);
+            ff_axis_rec(b2, b3, oj);
+            sj = shape_ff(oj, b1.z, b1.w);
+            vj = mk<T>(b3.z, b3.w, b4.x);
+            Wj = mk<T>(b4.y, b4.z, b4.w);
         }
+        u3 = normal_velocity_ff(nf, oi, si.rpar, si.rperp, vi, Wi, j, oj, sj.rpar, sj.rperp, vj, Wj);
     } else {
         n = n64;
         si = load_shape<T>(P, i);
-        if (j >= 0) sj = load_shape<T>(P, j);
+        vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
+        Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
+        if (j >= 0) {
+            sj = load_shape<T>(P, j);
+            vj = mk<T>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j));
+            Wj = mk<T>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
+        }
     }
-    T u3 = T(0);
-    if constexpr (MIXED) u3 = normal_velocity_ff(P, pff, i, j, nf, oi, oj);
     // geometry at y*_i, the local frame x1, x2, x3 = n, and the relative velocities
     const V3<T> rho_i = support_offset(si, n);
     const Surf<T> A = surface_at(si, rho_i, n);
     const V3<T> x1 = A.x1, x2 = cross(n, x1);
-    const V3<T> Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
-    V3<T> dV = scl(T(-1), add(mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i)), cross(Wi, rho_i)));
+    V3<T> dV = scl(T(-1), add(vi, cross(Wi, rho_i)));
     V3<T> dW = scl(T(-1), Wi);
     T c1p = 0, c2p = 0, G0p = 0, G2p = 0, cf = 1, sf = 0;
     V3<T> rho_j = mk<T>(0, 0, 0);
@@ -255,8 +273,7 @@ __device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int
         const T r = rsqrt_t(cf * cf + sf * sf);
         cf *= r;
         sf *= r;
-        const V3<T> Wj = mk<T>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
-        dV = add(dV, add(mk<T>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j)), cross(Wj, rho_j)));
+        dV = add(dV, add(vj, cross(Wj, rho_j)));
         dW = add(dW, Wj);
     }
     const T u1 = dot(x1, dV), u2 = dot(x2, dV);

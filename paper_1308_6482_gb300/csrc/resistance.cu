@@ -101,13 +101,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance_appl
 
 }  // namespace
 
-// the mixed mode's per-call particle table (float-float axes) in the context scratch
+// the mixed mode's per-call particle records in the context scratch
 static int particle_table(lub_ctx *ctx, const PView &P, cudaStream_t st, const float2 **pff)
 {
     int rc = lub_ensure_scratch(ctx, particles_ff_bytes(P.n));
     if (rc) return rc;
     *pff = (const float2 *)ctx->scratch;
-    return launch_particles_ff(ctx, P, (float2 *)ctx->scratch, st, false);
+    return launch_particles_ff(ctx, P, (float2 *)ctx->scratch, st);
 }
 
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
