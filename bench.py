@@ -63,6 +63,9 @@ PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 TRAFFIC = {}
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")
+# the form of the timed step: lub_pairs_build, then lub_correct (closest
+# points, resistance and scatter in one call)
+STEP_FORM = "fused"
 MOTION_SEED = 777
 SIG_R, SIG_T = 0.01, 0.005
 
@@ -230,15 +233,15 @@ def large_pipeline(lub, parts, dom, dev, rmax, warm, net, packed=False):
 
 
 def run_steps(lub, torch, np, pl, P, stream, flush, steps, warmup):
-    """One CUDA graph of one step (the merged form).  Per step: the seeded
+    """One CUDA graph of one step (STEP_FORM).  Per step: the seeded
     motion of every particle and an L2 flush, outside the events, then the
     graph between two events.  Returns ms [steps], pair counts [steps], the
     mean Newton iterations per pair and the capacity overflows."""
     with torch.cuda.stream(stream):
-        pl.step(form="merged", stream=stream)
-        pl.step(form="merged", stream=stream)
+        pl.step(form=STEP_FORM, stream=stream)
+        pl.step(form=STEP_FORM, stream=stream)
     stream.synchronize()
-    g = graph_of(torch, stream, lambda: pl.step(form="merged", stream=stream))
+    g = graph_of(torch, stream, lambda: pl.step(form=STEP_FORM, stream=stream))
     dev = P.t["x"].device
     counts = torch.zeros(steps, dtype=torch.int32, device=dev)
     its = torch.zeros(steps, dtype=torch.float64, device=dev)
@@ -276,10 +279,10 @@ def run_multi(lub, torch, np, pl, P, stream, G, replays, step0):
         for j in range(G):
             lub.lub_random_motion(pl.ctx.h, P.c, MOTION_SEED, 0, SIG_R, SIG_T, step_dev=ctr[j % 2:],
                                   next_dev=ctr[(j + 1) % 2:], stream=stream)
-            pl.step(form="merged", stream=stream)
+            pl.step(form=STEP_FORM, stream=stream)
 
     with torch.cuda.stream(stream):
-        pl.step(form="merged", stream=stream)
+        pl.step(form=STEP_FORM, stream=stream)
     stream.synchronize()
     g = graph_of(torch, stream, body)
     ev = event_pairs(torch, replays)
@@ -295,12 +298,16 @@ def run_multi(lub, torch, np, pl, P, stream, G, replays, step0):
     return ms
 
 
-def kernels_in_step(form="merged", precision="mixed"):
+def kernels_in_step(form=None, precision="mixed"):
     # lub_pairs_build: zeroing of its counters, cells count, scan, cells fill,
-    # sweep, scan, compaction = 7.  lub_closest_points, mixed: zeroing of the
-    # work list, particle table, FP32 stage, work-list FP64 solves = 4; FP64: 1.
-    # lub_resistance_apply, mixed: zeroing of the sums, particle table, the
-    # kernel = 3; FP64: 2.
+    # sweep, scan, compaction = 7.  lub_correct (the fused form), mixed:
+    # zeroing of the sums, zeroing of the work list, particle table, FP32
+    # stage, work-list FP64 solves, resistance with scatter = 6; FP64: zeroing
+    # and the one pass = 2.  The merged form (lub_closest_points, then
+    # lub_resistance_apply), mixed: 4 + 3 (a second particle table); FP64: 1 + 2.
+    form = form or STEP_FORM
+    if form == "fused":
+        return 7 + (6 if precision == "mixed" else 2)
     if precision == "mixed":
         return 7 + 4 + 3
     return 7 + 1 + 2
@@ -414,6 +421,22 @@ def large_headline(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
             # the step with several steps (and their motions) per graph
             multi_ms = run_multi(lub, torch, np, pl, P, stream, args.graph_steps, max(5, steps // args.graph_steps),
                                  2 * 10 ** 6)
+            # the other forms of the same step (the same calls, the same motions)
+            other_ms = {}
+            for f2 in ("merged", "calls"):
+                g2 = graph_of(torch, stream, lambda f2=f2: pl.step(form=f2, stream=stream))
+                e2 = event_pairs(torch, 20)
+                with torch.cuda.stream(stream):
+                    for k, (a, b) in enumerate(e2):
+                        lub.lub_random_motion(pl.ctx.h, P.c, MOTION_SEED, 4 * 10 ** 6 + k, SIG_R, SIG_T,
+                                              stream=stream)
+                        flush.zero_()
+                        a.record(stream)
+                        g2.replay()
+                        b.record(stream)
+                stream.synchronize()
+                other_ms[f2] = float(np.mean([a.elapsed_time(b) for a, b in e2[3:]]))
+                del g2
             # the motion kernel alone
             evm = event_pairs(torch, 20)
             with torch.cuda.stream(stream):
@@ -431,6 +454,7 @@ def large_headline(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
     dominant = {"sweep": "pairs_build", "closest": "k_closest_mixed", "resistance": "k_resistance_apply"}[dom_k]
     out = {"value": lead["pairs_per_s"], "ms_per_step": lead["ms_per_step"], "pairs_per_step": lead["pairs_per_step"],
            "particles": n, "clocks": clocks, "forms": res, "call_ms": call_ms, "kernel_ms": kernel_ms,
+           "other_forms_ms_per_step": other_ms,
            "steps_per_graph": {"1": lead["ms_per_step"], str(args.graph_steps): multi_ms,
                                "motion_ms": motion_ms,
                                "note": "%d steps per graph: ms per step with each step's seeded motion inside the "
@@ -456,7 +480,7 @@ def e2e_large(args, lub, torch, np, parts, dom, dev, stream, rmax, net):
 
     def e2e_step():
         Pk.blob.copy_(hblob, non_blocking=True)
-        ple.step(form="merged", stream=stream)
+        ple.step(form=STEP_FORM, stream=stream)
         hout.copy_(ple.ft_particles, non_blocking=True)
 
     with torch.cuda.stream(stream):
@@ -586,7 +610,7 @@ def suspension_32k(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
     pln = lub.Pipeline(lub.DeviceParticles(parts, dev), dom, lub.default_params(precision="mixed", model="normal"),
                        capacity=pl.cap, device=dev)
     pln.build_pairs()
-    normal_ms = time_graph(lambda: pln.step(form="merged", stream=stream), 50)
+    normal_ms = time_graph(lambda: pln.step(form=STEP_FORM, stream=stream), 50)
     del pln
     # the link-based model of Ding and Aidun (Sec. II) on the same pair list
     with torch.cuda.stream(stream):
@@ -613,7 +637,7 @@ def suspension_32k(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
     lb_ms = time_graph(lambda: pls.substeps(10, 1.0, 0.1, f_ext=fext, stream=stream), 20)
     pairs_s = min(pls.count(), pls.cap)
     del pls
-    ms, pairs_all = aggregate(forms["merged"], npairs, ws, dev)
+    ms, pairs_all = aggregate(forms[STEP_FORM], npairs, ws, dev)
     return {"workload": WORKLOAD_32K, "ms_per_step": ms, "pairs_per_s": pairs_all / (ms * 1e-3),
             "pairs_per_step": int(npairs), "forms_ms_per_step": forms, "call_ms": call_ms, "kernel_ms": kernel_ms,
             "rooflines": roof, "newton_iters_mean": float(np.mean(res["iters"])),
@@ -682,9 +706,11 @@ def learned_vs_plain(args, lub, torch, np, dev, stream, flush, steps=20, warmup=
                 net_ms[engine] = timed(lambda: lub.lub_mlp_predict(pl.ctx.h, pl.P.c, pl.D, pl.pair_i, pl.pair_j,
                                                                    pl.d_count, pl.cap, pq, stream=stream))
             it = pl.iters[:m].cpu().numpy().astype(np.float64)
+            stt = pl.status[:m].cpu().numpy()
             res[form] = {"pairs_per_s": m / (ms * 1e-3), "ms": ms, "newton_iters_mean": float(it.mean()),
                          "warp_max_iters_mean": float(it[:m - m % 32].reshape(-1, 32).max(1).mean()),
-                         "h": pl.gap[:m].cpu().numpy(), "status": pl.status[:m].cpu().numpy()}
+                         "fp64_fallback_fraction": float(np.mean((stt & lub.LUB_ST_FP64) != 0)),
+                         "h": pl.gap[:m].cpu().numpy(), "status": stt}
             del pl
         h0, s0 = res["plain"].pop("h"), res["plain"].pop("status")
         for form in list(res):
@@ -785,12 +811,12 @@ def ensemble_bench(args, lub, torch, np, dev, stream, flush, ws=1, rank=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for q in sep:
-            q.step(form="merged", stream=stream)
+            q.step(form=STEP_FORM, stream=stream)
         flush.zero_()
         e0.record(stream)
         for _ in range(Ks):
             for q in sep:
-                q.step(form="merged", stream=stream)
+                q.step(form=STEP_FORM, stream=stream)
         e1.record(stream)
     stream.synchronize()
     sep_ms = e0.elapsed_time(e1) / Ks
@@ -855,7 +881,7 @@ def only_leg(args, lub, torch, np, dev, stream):
         return {"pairs": len(pi), "steps": args.steps}
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            pl.step(form="merged", stream=stream)
+            pl.step(form=STEP_FORM, stream=stream)
     stream.synchronize()
     return {"pairs": int(min(pl.count(), pl.cap)), "steps": args.steps}
 
@@ -903,6 +929,7 @@ def run_ours(args):
                    "forms": head["forms"], "speedup_learned_vs_plain": head["speedup_learned_vs_plain"],
                    "speedup_learned_vs_temporal": head["speedup_learned_vs_temporal"],
                    "steps_per_graph": head["steps_per_graph"], "call_ms": head["call_ms"],
+                   "other_forms_ms_per_step": head["other_forms_ms_per_step"],
                    "kernel_ms": head["kernel_ms"], "generation_s": head["generation_s"]},
         "roofline": head["roofline"], "rooflines": head["rooflines"], "peaks": {
             k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "fp32_tflops", "fp64_tflops",

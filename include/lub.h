@@ -54,6 +54,8 @@ extern "C" {
 #define LUB_ERR_TIMEOUT  (-4) /* a bounded device wait ran out */
 #define LUB_ERR_NOMEM    (-5) /* the context could not allocate its scratch */
 #define LUB_ERR_LIMIT    (-6) /* input larger than a fixed limit of lub_pairs_build_static */
+#define LUB_ERR_INTERNAL (-7) /* a kernel's own range check failed: a defect of the library; the
+                                 call's outputs are invalid (reported by lub_pairs_build) */
 
 /* lub_params.precision */
 #define LUB_FP64  0 /* every step in double precision */
@@ -389,21 +391,25 @@ int lub_resistance_apply(lub_ctx *ctx, const lub_particles *p, const lub_domain 
                          void *torque, int32_t accumulate, void *stream);
 
 /*
- * Fused pass: lub_closest_points, lub_resistance and lub_apply (atomic form)
- * for every pair in one pass over the pairs, each pair's closest points, gap
- * and resistance staying in registers (Sec. III A, III B, Eq. lub:resistance).
- * The same arguments and results as the three calls, up to rounding (the
- * same arithmetic, which the compiler may contract into multiply-adds
- * differently inside the one kernel; the particle sums also add in another
- * order), with fewer launches and no per-pair round trip through memory.  n [3][cap]
- * is required: it holds the start normals of a warm start (LUB_WARM_PREVIOUS,
- * LUB_WARM_MLP_ALL, LUB_WARM_MLP in LUB_FP64) and receives the normals.  In
- * LUB_MIXED, LUB_WARM_MLP runs no network here: the few pairs the FP32 stage
- * fails are solved again in FP64 inside the force pass, from the line of
- * centres.  gap, status, iters, FT and lever
- * are written where given and skipped where NULL.  force and torque [3][n]
- * (float in LUB_MIXED, double in LUB_FP64) are zeroed first unless
- * accumulate is set.  Ensemble mode as for the separate calls.
+ * One call for the per-pair work of a step: lub_closest_points, lub_resistance
+ * and lub_apply (atomic form) on the same arguments (Sec. III A, III B, Eq.
+ * lub:resistance).
+ *   - LUB_FP64: one pass over the pairs, each pair's closest points, gap and
+ *     resistance staying in registers; the results are those of the three
+ *     calls up to rounding (the same arithmetic, which the compiler may
+ *     contract into multiply-adds differently inside the one kernel; the
+ *     particle sums also add in another order).
+ *   - LUB_MIXED: the kernels of lub_closest_points followed by those of
+ *     lub_resistance_apply, on one set of per-call particle records (built
+ *     once instead of once per call); the results are those of the two calls,
+ *     the particle sums up to the order of the atomic additions.
+ * n [3][cap] is required: it holds the start normals of a warm start
+ * (LUB_WARM_PREVIOUS, LUB_WARM_MLP_ALL, LUB_WARM_MLP) and receives the
+ * normals.  gap, status, iters, FT and lever are written where given and
+ * skipped where NULL (in LUB_MIXED the context scratch holds gap and status
+ * between the kernels when they are NULL).  force and torque [3][n] (float in
+ * LUB_MIXED, double in LUB_FP64) are zeroed first unless accumulate is set.
+ * Ensemble mode as for the separate calls.
  */
 int lub_correct(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom, const lub_params *prm,
                 const int32_t *pair_i, const int32_t *pair_j, const int32_t *d_count, int32_t capacity, double *n,

@@ -12,7 +12,7 @@ runs the four calls of one correction step on the current CUDA stream.  With
 particles made by ``make_ensemble`` (many independent suspensions back to
 back) the same four calls process every suspension in one launch per stage.
 """
-from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT,
+from ._lib import (LUB_ERR_ARG, LUB_ERR_CAPACITY, LUB_ERR_CUDA, LUB_ERR_INTERNAL, LUB_ERR_LIMIT, LUB_ERR_NOMEM, LUB_ERR_TIMEOUT,
                    LUB_FP64, LUB_MIXED, LUB_MLP_MMA_SYNC, LUB_MLP_PARAMS, LUB_MLP_TCGEN05, LUB_MODEL_FULL,
                    LUB_MODEL_NORMAL, LUB_OK, LUB_PROBE_FP32, LUB_PROBE_FP64, LUB_ST_DEGENERATE, LUB_ST_FP64,
                    LUB_ST_NOCONV, LUB_ST_OVERLAP, LUB_TRACE_APPLY, LUB_TRACE_CLOSEST, LUB_TRACE_COUNT,

@@ -16,6 +16,7 @@ LUB_ERR_CUDA = -3
 LUB_ERR_TIMEOUT = -4
 LUB_ERR_NOMEM = -5
 LUB_ERR_LIMIT = -6
+LUB_ERR_INTERNAL = -7
 LUB_STATIC_MAX_PARTICLES = 65536
 LUB_STATIC_MAX_CELLS = 262144
 LUB_FP64 = 0
@@ -650,7 +651,7 @@ class Pipeline:
         return {TUNE_NAMES[k]: lub_get_launch_shape(self.ctx.h, k) for k in range(LUB_TUNE_COUNT)}
 
     def correct(self, per_pair=True, stream=None):
-        """Closest points, resistance and scatter in the fused pass (lub_correct);
+        """Closest points, resistance and scatter in one call (lub_correct);
         per_pair=False skips the per-pair outputs other than the normals."""
         o = (lambda t: t) if per_pair else (lambda t: None)
         lub_correct(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap, self.nrm,
@@ -669,7 +670,9 @@ class Pipeline:
         """One correction step: the pair build, then the per-pair work in one
         of three forms: "calls" (closest points, resistance, apply), "merged"
         (closest points, then resistance + scatter in one pass) or "fused"
-        (all three in one pass; fused=True is the same).  deterministic needs
+        (one lub_correct call: in FP64 all three in one pass, in mixed
+        precision the merged kernels on one set of particle records;
+        fused=True is the same).  deterministic needs
         "calls".  With warm_start = LUB_WARM_PREVIOUS the normals are carried
         over from the step before (keep_previous is called at the end of
         every step)."""

@@ -321,6 +321,8 @@ int lub_pairs_build(lub_ctx *ctx, const lub_particles *p, const lub_domain *dom,
             return lub_set_error(ctx, LUB_ERR_TIMEOUT, "a bounded wait of the scan timed out");
         if (flags & 1)
             return lub_set_error(ctx, LUB_ERR_ARG, "a semi-axis exceeds max_semi_axis = %g (or is not finite)", rmax);
+        if (flags & 16)
+            return lub_set_error(ctx, LUB_ERR_INTERNAL, "the pair sweep met a cell or slot index outside its range");
         if (*h_count_or_null > capacity)
             return lub_set_error(ctx, LUB_ERR_CAPACITY, "%d candidate pairs exceed capacity %d", *h_count_or_null,
                                  capacity);

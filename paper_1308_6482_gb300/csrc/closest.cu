@@ -711,75 +711,6 @@ __device__ __forceinline__ void force_and_scatter(const PView &P, const RParams 
     scatter_warp<T>(ok ? i : -1, ok ? j : -1, (size_t)P.n, ci, cj, force, torque);
 }
 
-// The fused pass in mixed precision after the FP32 stage (k_closest_mixed,
-// which leaves every pair's normal, gap and status and marks the work-list
-// pairs with LUB_ST_FP64): warps take 32 items at a time from two queues,
-// the work-list entries (the FP64 solve, then the pair's force and scatter),
-// then the other pairs (force and scatter from the stored normal and gap).
-// queue: two counters, zero at the launch.
-template <bool ENS>
-__global__ void __launch_bounds__(128) k_refine_resist(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
-                                                       const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-                                                       const int32_t *__restrict__ d_count, int32_t cap,
-                                                       double *__restrict__ nout, double *__restrict__ gap,
-                                                       uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
-                                                       float *__restrict__ FT, float *__restrict__ lever, int maxit,
-                                                       const int32_t *__restrict__ wl_count,
-                                                       const int32_t *__restrict__ wl, int32_t *__restrict__ queue,
-                                                       float *__restrict__ force, float *__restrict__ torque,
-                                                       const float2 *__restrict__ pff)
-{
-    pdl_wait();
-    pdl_trigger();
-    const int count = pair_count(d_count, cap), nwl = wl_total(wl_count, cap);
-    const size_t C = (size_t)cap;
-    const int lane = threadIdx.x & 31;
-    // every warp takes work-list entries first (the longest items), then the
-    // other pairs
-    for (;;) {
-        int q0 = 0;
-        if (lane == 0) q0 = atomicAdd(queue, 32);
-        q0 = __shfl_sync(0xffffffffu, q0, 0);
-        if (q0 >= nwl) break;
-        const int q = q0 + lane;
-        const bool active = q < nwl;
-        int i = -1, j = -1, k = 0, st = 0, nit = 0;
-        V3<double> n64 = mk<double>(0, 0, 0);
-        double h = 0.0;
-        if (active) {
-            k = -1 - wl[q];
-            i = pi[k];
-            j = pj[k];
-            refine_one<ENS>(P, D0, E, i, j, maxit, n64, h, st, nit);
-        }
-        force_and_scatter<float>(P, R, active, i, j, n64, h, st, FT, lever, C, k, force, torque, pff);
-        if (active) store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
-    }
-    for (;;) {
-        int k0 = 0;
-        if (lane == 0) k0 = atomicAdd(queue + 1, 32);
-        k0 = __shfl_sync(0xffffffffu, k0, 0);
-        if (k0 >= count) break;
-        const int k = k0 + lane;
-        int i = -1, j = -1, st = 0;
-        bool done = k < count;
-        V3<double> n64 = mk<double>(0, 0, 0);
-        double h = 0.0;
-        if (done) {
-            st = status[k];
-            if (st & LUB_ST_FP64) {
-                done = false;  // a work-list pair: the first queue's
-            } else {
-                i = __ldg(pi + k);
-                j = __ldg(pj + k);
-                n64 = mk<double>(nout[k], nout[C + k], nout[2 * C + k]);
-                h = gap[k];
-            }
-        }
-        force_and_scatter<float>(P, R, done, i, j, n64, h, st, FT, lever, C, k, force, torque, pff);
-    }
-}
-
 template <bool ENS>
 __global__ void __launch_bounds__(128) k_fused_fp64(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
                                                     const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
@@ -870,10 +801,19 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     return launch_particles_ff(ctx, *P, *pff, st);
 }
 
+// What lub_correct hands from the closest-point kernels of the mixed mode to
+// the force pass: the gap and status arrays (the caller's, or the context
+// scratch's where it passes none) and the per-call particle records.
+struct ClosestKeep {
+    double *gap;
+    uint8_t *status;
+    const float2 *pff;
+};
+
 template <bool ENS>
 int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
-                     uint8_t *status, uint8_t *iters, cudaStream_t st)
+                     uint8_t *status, uint8_t *iters, cudaStream_t st, ClosestKeep *keep = nullptr)
 {
     int warm = 0, rc;
     const bool net_all = net_every_pair(prm);
@@ -887,7 +827,9 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, nullptr, nullptr, &P, &pff))) return rc;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, keep ? &gap : nullptr, keep ? &status : nullptr, &P, &pff)))
+            return rc;
+        if (keep) *keep = ClosestKeep{gap, status, pff};
         lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         if (fused_mlp) {
             if ((rc = learned_smem(ctx, k_closest_mixed_learned<ENS>, 16 << ENS))) return rc;
@@ -941,33 +883,21 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
         if ((rc = zero_force_torque(ctx, force, torque, 3 * (size_t)P.n * esz, st))) return rc;
     }
     if (cap == 0) return LUB_OK;
+    if (prm.precision == LUB_MIXED) {
+        // the kernels of lub_closest_points, then those of lub_resistance_apply
+        // on the same per-call particle records (built once)
+        ClosestKeep keep;
+        if ((rc = launch_closest_t<ENS>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, st, &keep)))
+            return rc;
+        return launch_resistance_apply(ctx, P, D, E, prm, pi, pj, d_count, cap, n, keep.gap, keep.status, FT, lever,
+                                       force, torque, 1, st, keep.pff);
+    }
     int warm = 0;
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;
     const RParams R = make_rparams(prm);
-    if (prm.precision == LUB_MIXED) {
-        // the FP32 stage, then the work list's FP64 solves and every pair's force
-        // in one queue-driven launch (gap and status in the context when not given)
-        int32_t *wl_count, *wl;
-        float2 *pff = nullptr;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, &gap, &status, &P, &pff))) return rc;
-        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
-        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
-        (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap, status,
-                         iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl, (const float2 *)pff);
-        lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
-        const Shape2 sr = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
-        const int grid = sr.grid < 8 * ctx->num_sms ? sr.grid : 8 * ctx->num_sms;
-        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
-        (void)launch_pdl(k_refine_resist<ENS>, grid, sr.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
-                         iters, (float *)FT, (float *)lever, prm.max_newton, (const int32_t *)wl_count,
-                         (const int32_t *)wl, wl_count + 2, (float *)force, (float *)torque, (const float2 *)pff);
-        lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
-    } else {
-        const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
-        (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status, iters,
-                                                       (double *)FT, (double *)lever, prm.max_newton, warm,
-                                                       (double *)force, (double *)torque);
-    }
+    const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_FP64, cap);
+    (void)launch_pdl(k_fused_fp64<ENS>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count, cap, n, gap, status,
+                     iters, (double *)FT, (double *)lever, prm.max_newton, warm, (double *)force, (double *)torque);
     return lub_check_cuda(ctx, cudaGetLastError(), "fused pass launch");
 }
 

@@ -19,8 +19,10 @@ struct lub_ctx {
     // growable device scratch
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
-    int32_t *d_flags = nullptr;  // [0]: the last pair build's flags; [1]: timed-out waits since
-                                 // the last lub_sync_status (bit 2: a scan, bit 3: the tcgen05 network)
+    int32_t *d_flags = nullptr;  // [0]: the last pair build's flags (bit 0: a semi-axis above the
+                                 // bound; bit 2: a scan timed out; bit 4: the sweep's range check);
+                                 // [1]: timed-out waits since the last lub_sync_status (bit 2: a
+                                 // scan, bit 3: the tcgen05 network)
     void *mlp = nullptr;         // MlpDevice of the learned warm start (lub_mlp_set)
     void *mlp_mem = nullptr;     // its device storage
     bool mlp_ready = false;
@@ -370,10 +372,12 @@ int launch_correct(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, c
                    const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
                    uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int accumulate,
                    cudaStream_t st);
+// pff: the mixed mode's per-call particle records when the caller has built
+// them on this stream (lub_correct), else null (built here)
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
-                            void *torque, int accumulate, cudaStream_t st);
+                            void *torque, int accumulate, cudaStream_t st, const float2 *pff = nullptr);
 int launch_links(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi, const int32_t *pj,
                  const int32_t *d_count, int32_t cap, double mu, double qbar, double *force, double *torque,
                  int32_t *nlinks, cudaStream_t st);

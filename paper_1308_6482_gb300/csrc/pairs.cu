@@ -6,16 +6,17 @@
 //      particle into cell order as two float4 records: position relative to
 //      its cell centre with Rmax, and symmetry axis with e = R_par^2 -
 //      R_perp^2;
-//   2. sweep: one thread per (particle, row of the half-shell stencil), five
-//      rows (y, z columns of cells) per particle covering the own column and
-//      the 4 forward neighbours; in each row the x cells within the
-//      particle's reach form a run of slots; each warp shares out its 32
-//      items' candidates over its lanes and queues those that pass the
-//      bounding-sphere test for the full test, 32 at a time;
+//   2. sweep: one thread per slot, the slots in groups of 8 (a quarter warp);
+//      the five rows of the half-shell stencil (y, z columns of cells: the
+//      own column and the 4 forward neighbours) in turn; in each row the x
+//      cells within reach of a group's particles form one run of slots,
+//      staged 32 at a time in shared memory, and each lane tests its own
+//      particle against every staged candidate; those that pass the
+//      bounding-sphere test queue up for the full test, 32 at a time;
 //      each unordered pair is visited once and stored for the smaller of its
 //      two indices in that particle's row of KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
-//      caller's pair arrays; the row-0 thread tests the plane walls;
+//      caller's pair arrays; each thread also tests its particle's plane walls;
 //   3. one scan over [particle-pair counts | wall-pair counts] gives every
 //      offset (wall pairs land after all particle pairs);
 //   4. compaction: each particle sorts its partners (canonical (i, j) order)
@@ -109,6 +110,7 @@ struct BuildView {
     int32_t *pair_i, *pair_j, *d_count, *flags_out;
     float rmax_bound;
     int32_t cap;
+    int64_t ncell_total;  // cells of all grids (the cell counts hold one more entry)
 };
 
 // x < 0 in float-float
@@ -272,102 +274,83 @@ __device__ __forceinline__ bool pair_test_fp64(const PView &P, const DView &D, i
 // test decides)
 constexpr int kReject = 0, kAccept = 1, kUndecided = 2;
 
-// first test: the bounding spheres (with the margin); d = b - a + offset
-__device__ __forceinline__ bool pair_near(const Grid &G, float aw, float bw, float r2)
-{
-    const float hi = aw + bw + G.cutoff + G.margin;
-    return r2 <= hi * hi;  // most candidates end here, before the second record
-}
-
-// the rest of the decision for a candidate that passed pair_near
-__device__ __forceinline__ int pair_decide(const Grid &G, const float4 a0, const float4 a1, float bw, const float4 b1,
-                                           float dx, float dy, float dz)
+// the decision of a candidate that passed the bounding-sphere prefilter: aw
+// and a1 the first particle's Rmax and record, bw and b1 the second's, d the
+// vector between their centres; margin the absolute FP32 error allowance
+__device__ __forceinline__ int pair_decide(float cutoff, float margin, float aw, const float4 a1, float bw,
+                                           const float4 b1, float dx, float dy, float dz)
 {
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float lim = a0.w + bw + G.cutoff;
+    const float lim = aw + bw + cutoff;
     bool sure = true;
-    const float lo = lim - G.margin;
+    const float lo = lim - margin;
     if (r2 >= lo * lo) sure = false;
-    const float r = sqrtf(r2);
+    // approximate square roots and reciprocal (relative error ~1e-7, far
+    // inside the margin)
+    const float r = sqrt_fast(r2);
     if (r > 0.f) {
-        const float ir = 1.0f / r;
+        const float ir = rcp_fast(r);
         // half-widths along the line of centres: sigma^2 = R_perp^2 + e (o.e)^2,
         // with R_perp^2 = Rmax^2 - e for prolates (e > 0) and Rmax^2 for oblates
         const float ci = (a1.x * dx + a1.y * dy + a1.z * dz) * ir;
         const float cj = (b1.x * dx + b1.y * dy + b1.z * dz) * ir;
-        const float api = a1.w > 0.f ? a0.w * a0.w - a1.w : a0.w * a0.w;
+        const float api = a1.w > 0.f ? aw * aw - a1.w : aw * aw;
         const float apj = b1.w > 0.f ? bw * bw - b1.w : bw * bw;
-        const float sgi = sqrtf(fmaxf(api + a1.w * ci * ci, 0.f));
-        const float sgj = sqrtf(fmaxf(apj + b1.w * cj * cj, 0.f));
-        const float t1 = r - sgi - (bw + G.cutoff);
-        const float t2 = r - sgj - (a0.w + G.cutoff);
-        if (t1 > G.margin || t2 > G.margin) return kReject;
-        if (t1 >= -G.margin || t2 >= -G.margin) sure = false;
+        const float sgi = sqrt_fast(fmaxf(api + a1.w * ci * ci, 0.f));
+        const float sgj = sqrt_fast(fmaxf(apj + b1.w * cj * cj, 0.f));
+        const float t1 = r - sgi - (bw + cutoff);
+        const float t2 = r - sgj - (aw + cutoff);
+        if (t1 > margin || t2 > margin) return kReject;
+        if (t1 >= -margin || t2 >= -margin) sure = false;
     } else {
         sure = false;
     }
     return sure ? kAccept : kUndecided;
 }
 
-// Half-shell sweep: the 14 coarse cells of the stencil (the own cell and the
-// 13 forward neighbours, offsets (dx, dy, dz) lexicographically above zero)
-// as five rows of the y, z columns: row 0 = (dz, dy) = (0, 0), forward in x
-// only; row 1 = (0, 1); rows 2..4 = (1, -1..1), the last four both ways in x.
-// Along a row the fine x cells of the particle's window form one run of
-// slots (up to three on a periodic x axis: the cells below 0 and above
-// nx - 1 belong to the images at -L_x and +L_x).  Each unordered pair is seen
-// from one side only: in another row from the particle whose forward rows
-// hold the other; in row 0 from the one in the lower x cell, or, in the same
-// cell, from the lower slot (the run of row 0 starts right after the
-// particle's own slot).  A run at a non-zero image never pairs a particle
-// with itself (t != s); on a periodic axis the domain check (L > 2 range)
-// leaves at most one image of a pair within range, so each pair passes
-// exactly once.
+// Half-shell stencil: the 14 coarse cells (the own cell and the 13 forward
+// neighbours, offsets (dx, dy, dz) lexicographically above zero) as five rows
+// of the y, z columns: row 0 = (dz, dy) = (0, 0), forward in x only; row 1 =
+// (0, 1); rows 2..4 = (1, -1..1), the last four both ways in x.  Each
+// unordered pair is seen from one side only: in another row from the particle
+// whose forward rows hold the other; in row 0 from the one earlier in the
+// column's slot order (the slots of a column run along x, cell by cell), the
+// slots of the image at +L_x counting as later.  On a periodic axis the domain
+// check (L > 2 range) leaves at most one image of a pair within range, so
+// each pair passes exactly once.
 constexpr int SWEEP_ROWS = 5;
+constexpr int GL = 8;         // lanes (consecutive slots) per group
+constexpr int NG = 32 / GL;   // groups per warp
+constexpr int SC = 32;        // candidates a group stages per round
+constexpr int SW = 8;         // warps per block at most
+constexpr float kFar = 1e18f;  // x of an unused staging entry: fails every test
+constexpr int kNone = 1 << 30;
 
-// The candidates of one item (slot s, row): up to three runs of slots,
-// beg[k], num[k], run k holding x cells of the image at (k - 1) L_x; the
-// offset of candidate t in x is (cell_x(t) + xb + k nx) cs_x.  Runs beyond
-// the particle's reach are empty.
-struct Runs {
-    int beg[3], num[3];
-    int xb, nx;
-    float oy, oz;
-};
-
-__device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const int32_t *__restrict__ cell_start, int s,
-                                         const float4 a0, int cx, int cy, int cz, int row, int cbase)
+__device__ __forceinline__ void row_offsets(int row, int &dy, int &dz)
 {
-    Runs R;
-    R.beg[0] = R.beg[1] = R.beg[2] = 0;
-    R.num[0] = R.num[1] = R.num[2] = 0;
-    const int nx = G.nc[0];
-    R.nx = nx;
-    R.xb = -nx - cx;
-    const int dz = row >= 2 ? 1 : 0;
-    const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-    R.oy = dy * G.cs[1];
-    R.oz = dz * G.cs[2];
-    int yc = cy + dy, zc = cz + dz;
-    if (yc < 0 || yc >= G.nc[1]) {
-        if (!D.periodic[1]) return R;
-        yc += yc < 0 ? G.nc[1] : -G.nc[1];
-    }
-    if (zc < 0 || zc >= G.nc[2]) {
-        if (!D.periodic[2]) return R;
-        zc += zc < 0 ? G.nc[2] : -G.nc[2];
-    }
-    const int rowbase = cbase + (zc * G.nc[1] + yc) * nx;
-    // the window: partners of s lie within reach = Rmax_s + Rmax + Delta_L
-    // (+ margin); dyz is the distance from the particle to the row's cells
+    dz = row >= 2 ? 1 : 0;
+    dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
+}
+
+// A particle's window in a row: the unwrapped fine x cells [lo, hi] within
+// reach = Rmax_s + Rmax + Delta_L (+ margin) of it, given the distance from
+// the particle to the row's y, z cells (lo > hi: none); cells below 0 and
+// above nx - 1 belong to the images at -L_x and +L_x.  Row 0 starts at the
+// particle's own cell.
+__device__ __forceinline__ int2 row_window(const DView &D, const Grid &G, const float4 a0, int cx, int row)
+{
+    int dy, dz;
+    row_offsets(row, dy, dz);
+    const float oy = dy * G.cs[1], oz = dz * G.cs[2];
     const float reach = a0.w + G.rmax + G.cutoff + G.margin;
     const float hy = 0.5f * G.cs[1], hz = 0.5f * G.cs[2];
-    const float ey = dy == 0 ? 0.f : fmaxf(fabsf(R.oy - a0.y) - hy, 0.f);
-    const float ez = dz == 0 ? 0.f : fmaxf(fabsf(R.oz - a0.z) - hz, 0.f);
+    const float ey = dy == 0 ? 0.f : fmaxf(fabsf(oy - a0.y) - hy, 0.f);
+    const float ez = dz == 0 ? 0.f : fmaxf(fabsf(oz - a0.z) - hz, 0.f);
     const float r2yz = ey * ey + ez * ez;
-    if (r2yz > reach * reach) return R;
+    if (r2yz > reach * reach) return make_int2(kNone, -kNone);
     const float w = sqrtf(reach * reach - r2yz);
     const float inv = 1.0f / G.cs[0];
+    const int nx = G.nc[0];
     int lo = row == 0 ? cx : cx + (int)floorf((a0.x - w) * inv + 0.5f);
     int hi = cx + (int)floorf((a0.x + w) * inv + 0.5f);
     if (row == 0 && hi < cx) hi = cx;
@@ -378,25 +361,8 @@ __device__ __forceinline__ Runs row_runs(const DView &D, const Grid &G, const in
         lo = max(lo, -nx);
         hi = min(hi, 2 * nx - 1);
     }
-    // run k: the unwrapped cells [max(lo, (k-1) nx), min(hi, k nx - 1)]
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int a = max(lo, (k - 1) * nx), b = min(hi, k * nx - 1);
-        if (a > b) continue;
-        const int e = cell_start[rowbase + b - (k - 1) * nx + 1];
-        const int g = (row == 0 && k == 1) ? s + 1 : cell_start[rowbase + a - (k - 1) * nx];
-        R.beg[k] = g;
-        R.num[k] = e > g ? e - g : 0;
-    }
-    return R;
+    return make_int2(lo, hi);
 }
-
-// an item's data for the lanes that test its candidates (one per thread)
-struct ItemSlot {
-    float4 a0, a1;
-    int s, beg0, beg1, beg2, num0, num1, xb, nx;
-    float cs0, oy, oz;
-};
 
 // store of one accepted pair (i, j): in the row of the smaller index, or in
 // the overflow list at the tail of the pair arrays
@@ -417,18 +383,36 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
     }
 }
 
-// One thread per (slot s in cell order, row); the row-0 thread also tests the
+// One thread per slot s (cell order); the thread also tests its particle's
 // walls.  cnt: [0, N) pair counts per particle (of the smaller index of each
 // pair), [N, 2N) wall-pair counts; slots [N][KSLOT]; wall bits per particle;
 // overflow entry o at pair_i/pair_j[cap - 1 - o].
 //
+// Each quarter warp is a group of 8 consecutive slots.  The group's slots in
+// one column (all of them, but for the few groups that straddle two columns,
+// which take one pass per column) share their rows: per row, the union of
+// their windows is one run of slots (up to three on a periodic x axis), which
+// the group stages in shared memory 32 candidates at a time, x taken relative
+// to the cell of the group's first slot; every lane then tests its own
+// particle against the staged ones by broadcast reads (the bounding spheres,
+// with the margin), a candidate outside its own window failing like any other
+// distant one.  Staging a candidate once for 8 particles, instead of fetching
+// it and its run bookkeeping per (particle, candidate), keeps the load/store
+// pipe, the bound of a per-candidate share-out, mostly free.  (Groups of 16
+// test more candidates outside their particles' windows; groups of 4 reading
+// the runs straight from L1 spend more instructions per test.)  The few
+// candidates that pass (about 12 per particle, a third of them pairs) queue up
+// per warp, one per lane and round, and take the rest of the test and the
+// store 32 at a time, every lane busy.
+// The group-relative x of a particle or candidate within E of the group's
+// cell carries an FP32 error of a few ulp(E); the group's margin adds
+// E 2^-20 to the grid's, so that every decision inside it still goes to the
+// FP64 test.
+//
 // Candidates inside the FP32 margin (about one in 10^4) are decided on the
-// spot by the FP64 test, in the lane that holds them: that code path runs
-// rarely and spills at the sweep's register budget, which costs less than
-// listing them for a block that finishes last (a fence and a ticket per
-// block: 7 us of a 0.08 ms step at 32k particles).
+// spot by the FP64 test, in the lane that holds them.
 template <bool ENS>
-__device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
+__device__ __forceinline__ void sweep_groups(const BuildView &V)
 {
     const PView &P = V.P;
     const DView &D0 = V.D;
@@ -450,162 +434,252 @@ __device__ __forceinline__ void sweep_items(const BuildView &V, int64_t f0)
     int32_t *__restrict__ pair_j = V.pair_j;
     const double cutoff_d = V.cutoff_d;
     const int N = P.n;
-    __shared__ ItemSlot items[256];
-    const int lane = threadIdx.x & 31;
+    constexpr unsigned FULL = 0xffffffffu;
+    // staging rows padded by one entry: the groups' broadcast reads fall in
+    // different banks
+    __shared__ float4 cand[SW][NG * (SC + 1)];
+    __shared__ int cand_t[SW][NG * (SC + 1)];
+    __shared__ float4 own1[SW * 32];  // each lane's symmetry axis and e
+    __shared__ float2 ownw[SW * 32];  // each lane's Rmax and its group's margin
+    __shared__ float4 qd[SW][64];     // queued: d (x, y, z) and Rmax of the candidate
+    __shared__ int qt[SW][64];        // queued: candidate slot t
+    __shared__ uint8_t qo[SW][64];    // queued: lane of the particle
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, g = lane / GL;
+    const int wbase = threadIdx.x & ~31;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s0w = s - lane;
+    const bool valid = s < N;
     // one candidate that passed (or is undecided by) the FP32 tests
-    auto decide = [&](int s, int t, int r) {
+    auto decide = [&](int sa, int t, int r) {
         if (r == kAccept) {
-            store_candidate(sorted[s], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
+            store_candidate(sorted[sa], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
         } else {
-            const int i = sorted[s], j = sorted[t];
-            if (pair_test_fp64(P, dom_ref<ENS>(D0, E, ENS ? sbat[s] : 0), i, j, cutoff_d))
+            const int i = sorted[sa], j = sorted[t];
+            if (pair_test_fp64(P, dom_ref<ENS>(D0, E, ENS ? sbat[sa] : 0), i, j, cutoff_d))
                 store_candidate(i, j, cnt, slots, ovf_n, cap, pair_i, pair_j);
         }
     };
-    // each thread's own item: its runs of candidates and its wall tests
-    const int f = (int)(f0 + threadIdx.x);
-    int total = 0;
-    if (f < SWEEP_ROWS * N) {
-        const int s = f / SWEEP_ROWS, row = f - SWEEP_ROWS * s;
-        const int b = ENS ? sbat[s] : 0;
-        const Grid &G = grid_ref<ENS>(G0, EG, b);
-        const DView &D = dom_ref<ENS>(D0, E, b);
-        const int base = cell_base<ENS>(EG, b);
-        const float4 a0 = rec0[s];
-        const int cc = cellc[s];
-        const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
-        const Runs R = row_runs(D, G, cell_start, s, a0, cx, cy, cz, row, base);
-        total = R.num[0] + R.num[1] + R.num[2];
-        ItemSlot &it = items[threadIdx.x];
-        it.a0 = a0;
-        it.a1 = rec1[s];
-        it.s = s;
-        it.beg0 = R.beg[0];
-        it.beg1 = R.beg[1];
-        it.beg2 = R.beg[2];
-        it.num0 = R.num[0];
-        it.num1 = R.num[1];
-        it.xb = R.xb;
-        it.nx = R.nx;
-        it.cs0 = G.cs[0];
-        it.oy = R.oy;
-        it.oz = R.oz;
-        if (row == 0) {
-            // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
-            // records (one double subtraction for z - z_w), decided in FP64 only
-            // within the margin (the exact test costs some 60 FP64 operations, a
-            // warp's worth of FP64 pipe time on GB300 for a fifth of its lanes)
-            const int i = sorted[s];
-            const float4 o = rec1[s];
-            const float rm2 = a0.w * a0.w;
-            const float sz = sqrtf(fmaxf((o.w > 0.f ? rm2 - o.w : rm2) + o.w * o.z * o.z, 0.f));
-            int wf = 0, bits = 0;
-            for (int ww = 0; ww < D.n_walls; ++ww) {
-                const float hw = (float)D.wall_dir[ww] * (float)(P.z[i] - D.wall_z[ww]) - sz;
-                bool in = hw < G.cutoff - G.margin;
-                if (!in && hw <= G.cutoff + G.margin) {
-                    const Shape<double> si = load_shape<double>(P, i);
-                    in = (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0)) <
-                         cutoff_d;
-                }
-                if (in) {
-                    bits |= 1 << ww;
-                    ++wf;
-                }
-            }
-            cnt[N + i] = wf;
-            wbits[i] = (uint8_t)bits;
-        }
-    }
-    // The warp's 32 items' candidates, laid end to end (inclusive prefix
-    // incl over the lanes), tested 32 at a time: lane q's candidate belongs
-    // to the item of the first lane whose incl exceeds it.  A thread walking
-    // its own item's candidates would leave most of its warp idle (the runs
-    // differ in length from item to item), and the lanes read the runs'
-    // records coalesced.  The few candidates that pass the bounding-sphere
-    // test (about one in eight) queue up in shared memory and take the rest
-    // of the test and the store 32 at a time, with every lane busy.
-    {
-    __shared__ float4 qd[8][64];   // d (x, y, z) and Rmax of the candidate
-    __shared__ int qt[8][64];      // candidate slot t
-    __shared__ uint8_t qo[8][64];  // lane of its item
-    int incl = total;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    const int wbase = threadIdx.x & ~31, wq = threadIdx.x >> 5;
     // the full test and the store of queue entry e
     auto drain = [&](int e) {
         const float4 d = qd[wq][e];
         const int t = qt[wq][e];
-        const ItemSlot &it = items[wbase + qo[wq][e]];
-        const int s = it.s;
-        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[s] : 0);
-        const int r = pair_decide(G, it.a0, it.a1, d.w, rec1[t], d.x, d.y, d.z);
-        if (r != kReject) decide(s, t, r);
+        const int o = qo[wq][e];
+        const int so = s0w + o;
+        const float2 wm = ownw[wbase + o];
+        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[so] : 0);
+        const int r = pair_decide(G.cutoff, wm.y, wm.x, own1[wbase + o], d.w, rec1[t], d.x, d.y, d.z);
+        if (r != kReject) decide(so, t, r);
     };
+    int b = 0, cc = 0, colkey = -1;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    if (valid) {
+        b = ENS ? sbat[s] : 0;
+        const Grid &G = grid_ref<ENS>(G0, EG, b);
+        const DView &D = dom_ref<ENS>(D0, E, b);
+        a0 = rec0[s];
+        a1 = rec1[s];
+        cc = cellc[s];
+        const int cy = (cc >> 10) & 1023, cz = cc >> 20;
+        colkey = cell_base<ENS>(EG, b) + (cz * G.nc[1] + cy) * G.nc[0];  // first cell of the column
+        // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
+        // records (one double subtraction for z - z_w), decided in FP64 only
+        // within the margin (the exact test costs some 60 FP64 operations)
+        const int i = sorted[s];
+        const float rm2 = a0.w * a0.w;
+        const float sz = sqrtf(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
+        int wf = 0, bits = 0;
+        for (int ww = 0; ww < D.n_walls; ++ww) {
+            const float hw = (float)D.wall_dir[ww] * (float)(P.z[i] - D.wall_z[ww]) - sz;
+            bool in = hw < G.cutoff - G.margin;
+            if (!in && hw <= G.cutoff + G.margin) {
+                const Shape<double> si = load_shape<double>(P, i);
+                in = (double)D.wall_dir[ww] * (P.z[i] - D.wall_z[ww]) - support(si, mk<double>(0.0, 0.0, 1.0)) <
+                     cutoff_d;
+            }
+            if (in) {
+                bits |= 1 << ww;
+                ++wf;
+            }
+        }
+        cnt[N + i] = wf;
+        wbits[i] = (uint8_t)bits;
+    }
+    const int cx = cc & 1023;
+    float4 *const cg = &cand[wq][g * (SC + 1)];
+    int *const ctg = &cand_t[wq][g * (SC + 1)];
     int qn = 0;
-    __syncwarp();
-    for (int r0 = 0; r0 < wtotal; r0 += 32) {
-        const int q = r0 + lane;
-        int o = 0;
+    bool done = !valid;
+    // one pass per column among each group's slots (one for most groups)
+    while (__any_sync(FULL, !done)) {
+        const unsigned pend = __ballot_sync(FULL, !done);
+        const unsigned gp = pend & (((1u << GL) - 1u) << (GL * g));
+        const int leader = gp ? __ffs(gp) - 1 : lane;
+        // every lane takes part in every shuffle (none inside a condition)
+        const int lkey = __shfl_sync(FULL, colkey, leader);
+        const bool act = gp != 0 && !done && colkey == lkey;
+        // the group's column, suspension and reference cell: its leader's
+        const int lcc = __shfl_sync(FULL, cc, leader);
+        int lb = ENS ? __shfl_sync(FULL, b, leader) : 0;
+        if (ENS && (lb < 0 || lb >= E.nb)) {  // range check: never taken by a correct sweep
+            atomicOr(V.flags, 16);
+            lb = 0;
+        }
+        const int lcx = lcc & 1023, lcy = (lcc >> 10) & 1023, lcz = (lcc >> 20) & 1023;
+        const int s_lead = s0w + leader;
+        const Grid &G = grid_ref<ENS>(G0, EG, lb);
+        const DView &D = dom_ref<ENS>(D0, E, lb);
+        const int nx = G.nc[0];
+        const float cs0 = G.cs[0];
+        int span = act ? cx - lcx : 0;
 #pragma unroll
-        for (int step = 16; step; step >>= 1) {
-            const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
-            if (v <= q) o += step;
+        for (int o = GL / 2; o; o >>= 1) span = max(span, __shfl_xor_sync(FULL, span, o));
+        // every x of the pass lies within E of the group's cell
+        const float Ex = (float)(span + 2) * cs0 + 2.f * G.rmax + G.cutoff + G.margin;
+        const float marg = G.margin + Ex * 0x1p-20f;
+        const float ax = a0.x + (float)(cx - lcx) * cs0;
+        const float awc = a0.w + G.cutoff + marg;
+        if (act) {
+            own1[threadIdx.x] = a1;
+            ownw[threadIdx.x] = make_float2(a0.w, marg);
         }
-        const int first = __shfl_sync(0xffffffffu, incl - total, o & 31);
-        bool pass = false;
-        float4 d;
-        int t = 0;
-        if (q < wtotal) {
-            const ItemSlot &it = items[wbase + o];
-            const int u = q - first;
-            const int k = u < it.num0 ? 0 : (u < it.num0 + it.num1 ? 1 : 2);
-            t = k == 0 ? it.beg0 + u : (k == 1 ? it.beg1 + u - it.num0 : it.beg2 + u - it.num0 - it.num1);
-            if (t != it.s) {
-                const float ox = (float)((cellc[t] & 1023) + it.xb + k * it.nx) * it.cs0;
-                const float4 b0 = rec0[t];
-                d = make_float4(b0.x - it.a0.x + ox, b0.y - it.a0.y + it.oy, b0.z - it.a0.z + it.oz, b0.w);
-                const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[it.s] : 0);
-                pass = pair_near(G, it.a0.w, b0.w, d.x * d.x + d.y * d.y + d.z * d.z);
+        for (int row = 0; row < SWEEP_ROWS; ++row) {
+            int dy, dz;
+            row_offsets(row, dy, dz);
+            int yc = lcy + dy, zc = lcz + dz;
+            bool exists = gp != 0;
+            if (yc < 0 || yc >= G.nc[1]) {
+                if (!D.periodic[1]) exists = false;
+                yc += yc < 0 ? G.nc[1] : -G.nc[1];
+            }
+            if (zc < 0 || zc >= G.nc[2]) {
+                if (!D.periodic[2]) exists = false;
+                zc += zc < 0 ? G.nc[2] : -G.nc[2];
+            }
+            int2 w = make_int2(kNone, -kNone);
+            if (act && exists) w = row_window(D, G, a0, cx, row);
+#pragma unroll
+            for (int o = GL / 2; o; o >>= 1) {
+                w.x = min(w.x, __shfl_xor_sync(FULL, w.x, o));
+                w.y = max(w.y, __shfl_xor_sync(FULL, w.y, o));
+            }
+            // the union's runs: run k holds the x cells of the image at (k - 1) L_x
+            int beg[3] = {0, 0, 0}, num[3] = {0, 0, 0};
+            const int rowbase = cell_base<ENS>(EG, lb) + (zc * G.nc[1] + yc) * nx;
+            if (exists && (rowbase < 0 || (int64_t)rowbase + nx > V.ncell_total)) {  // range check, as above
+                atomicOr(V.flags, 16);
+                exists = false;
+            }
+            if (exists && w.x <= w.y) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int lo = max(w.x, (k - 1) * nx), hi = min(w.y, k * nx - 1);
+                    if (lo > hi) continue;
+                    const int e = cell_start[rowbase + hi - (k - 1) * nx + 1];
+                    const int st = (row == 0 && k == 1) ? s_lead + 1 : cell_start[rowbase + lo - (k - 1) * nx];
+                    beg[k] = st;
+                    num[k] = e > st ? e - st : 0;
+                    if (st < 0 || (int64_t)st + num[k] > N) {  // range check, as above
+                        atomicOr(V.flags, 16);
+                        num[k] = 0;
+                    }
+                }
+            }
+            const int T = num[0] + num[1] + num[2];
+            int Tw = T;
+#pragma unroll
+            for (int o = GL; o < 32; o <<= 1) Tw = max(Tw, __shfl_xor_sync(FULL, Tw, o));
+            const float oy = dy * G.cs[1], oz = dz * G.cs[2];
+            for (int c0 = 0; c0 < Tw; c0 += SC) {
+                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < SC / GL; ++h) {
+                    const int q = (lane % GL) + GL * h, u = c0 + q;
+                    float4 v = make_float4(kFar, 0.f, 0.f, 0.f);
+                    int tk = 0;
+                    if (u < T) {
+                        const int k = u < num[0] ? 0 : (u < num[0] + num[1] ? 1 : 2);
+                        const int t = k == 0 ? beg[0] + u : (k == 1 ? beg[1] + u - num[0] : beg[2] + u - num[0] - num[1]);
+                        const float4 r0 = rec0[t];
+                        const int dc = (cellc[t] & 1023) + (k - 1) * nx - lcx;
+                        v = make_float4(r0.x + (float)dc * cs0, r0.y + oy, r0.z + oz, r0.w);
+                        // row 0: the image at +L_x comes after every slot
+                        tk = (row == 0 && k == 2) ? (int)((unsigned)t | 0x80000000u) : t;
+                    }
+                    cg[q] = v;
+                    ctg[q] = tk;
+                }
+                __syncwarp();
+                // the bounding spheres of the lane's particle and the staged
+                // candidates, in blocks of 8 up to the warp's longest run (the
+                // rest of a shorter group's staging holds far entries)
+                const int cn = min(SC, Tw - c0);
+                unsigned m = 0;
+                if (act) {
+                    for (int c8 = 0; c8 < cn; c8 += 8) {
+                        unsigned mb = 0;
+                        if (row == 0) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float4 q = cg[c8 + j];
+                                const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
+                                const float hi = awc + q.w;
+                                const int tk = ctg[c8 + j];
+                                const bool p = ex * ex + ey * ey + ez * ez <= hi * hi && (tk < 0 || tk > s);
+                                mb |= (unsigned)p << j;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float4 q = cg[c8 + j];
+                                const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
+                                const float hi = awc + q.w;
+                                mb |= (unsigned)(ex * ex + ey * ey + ez * ez <= hi * hi) << j;
+                            }
+                        }
+                        m |= mb << c8;
+                    }
+                }
+                // the passes into the warp's queue, one per lane and round
+                while (__any_sync(FULL, m != 0)) {
+                    const bool have = m != 0;
+                    const unsigned bal = __ballot_sync(FULL, have);
+                    if (have) {
+                        const int c = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int e = qn + __popc(bal & ((1u << lane) - 1u));
+                        const float4 q = cg[c];
+                        qd[wq][e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
+                        qt[wq][e] = ctg[c] & 0x7fffffff;
+                        qo[wq][e] = (uint8_t)lane;
+                    }
+                    qn += __popc(bal);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        drain(lane);
+                        __syncwarp();
+                        if (lane < qn - 32) {
+                            qd[wq][lane] = qd[wq][32 + lane];
+                            qt[wq][lane] = qt[wq][32 + lane];
+                            qo[wq][lane] = qo[wq][32 + lane];
+                        }
+                        qn -= 32;
+                        __syncwarp();
+                    }
+                }
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, pass);
-        if (pass) {
-            const int e = qn + __popc(m & ((1u << lane) - 1u));
-            qd[wq][e] = d;
-            qt[wq][e] = t;
-            qo[wq][e] = (uint8_t)o;
-        }
-        qn += __popc(m);
-        if (qn >= 32) {
-            __syncwarp();
-            drain(lane);
-            __syncwarp();
-            if (lane < qn - 32) {
-                qd[wq][lane] = qd[wq][32 + lane];
-                qt[wq][lane] = qt[wq][32 + lane];
-                qo[wq][lane] = qo[wq][32 + lane];
-            }
-            qn -= 32;
-            __syncwarp();
-        }
+        done = done || act;
     }
     __syncwarp();
     if (lane < qn) drain(lane);
-    }
 }
 
 template <bool ENS>
-__global__ void __launch_bounds__(256, 6) k_pairs_sweep(const __grid_constant__ BuildView V)
+__global__ void __launch_bounds__(256, 4) k_pairs_sweep(const __grid_constant__ BuildView V)
 {
     pdl_wait();
     pdl_trigger();
-    sweep_items<ENS>(V, (int64_t)blockIdx.x * blockDim.x);
+    sweep_groups<ENS>(V);
 }
 
 // Canonical order: each particle's partners, sorted, then its wall pairs, at
@@ -866,6 +940,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.flags_out = flags_out;
     V.rmax_bound = rmax;
     V.cap = cap;
+    V.ncell_total = G.ncell;
     cudaError_t e;
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 8);
@@ -875,9 +950,9 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
         return rc;
     e = launch_pdl(k_cells_fill<ENS>, gn, block, 0, st, V);
     if ((rc = lub_check_cuda(ctx, e, "cells fill launch"))) return rc;
-    // one item per thread (no grid-stride loop)
-    Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, SWEEP_ROWS * N);
-    sw.grid = (int)((SWEEP_ROWS * N + sw.block - 1) / sw.block);
+    // one slot per thread (no grid-stride loop)
+    Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, N);
+    sw.grid = (int)((N + sw.block - 1) / sw.block);
     lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
     e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, V);
     lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);

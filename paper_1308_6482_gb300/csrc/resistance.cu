@@ -113,7 +113,7 @@ static int particle_table(lub_ctx *ctx, const PView &P, cudaStream_t st, const f
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
-                            void *torque, int accumulate, cudaStream_t st)
+                            void *torque, int accumulate, cudaStream_t st, const float2 *pff)
 {
     const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
     int rc;
@@ -125,8 +125,7 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
     const Shape2 sh = tuned_shape(ctx, LUB_TUNE_RESISTANCE, cap);
     const bool ens = E.nb > 0;
     if (prm.precision == LUB_MIXED) {
-        const float2 *pff = nullptr;
-        if ((rc = particle_table(ctx, P, st, &pff))) return rc;
+        if (!pff && (rc = particle_table(ctx, P, st, &pff))) return rc;
         lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,

@@ -1,6 +1,7 @@
-"""The fused pass (lub_correct: closest points, resistance and the atomic
-scatter in one pass over the pairs) against the oracle (full parity), and
-against the three separate calls: the same pair lists and statuses, normals
+"""lub_correct (closest points, resistance and the atomic scatter in one
+call: one pass over the pairs in FP64; in mixed precision the kernels of
+lub_closest_points and lub_resistance_apply on one set of particle records)
+against the oracle (full parity), and against the three separate calls: the same pair lists and statuses, normals
 and gaps equal up to rounding (the compiler may contract the same arithmetic
 into multiply-adds differently inside the fused kernel), particle sums equal
 up to the order of the atomic additions where the pair terms are the same.
