@@ -2,8 +2,8 @@
 """Throughput benchmark of the lubrication correction (pairs per second).
 
 One step = one pass of the whole path over one suspension, enqueued on one
-stream: lub_pairs_build (cell list + Sec. III A pre-filters),
-lub_closest_points (Sec. III A) and lub_resistance_apply (Sec. III B and the
+stream: lub_pairs_build (cell list + Sec. III A pre-filters), then
+lub_correct (the closest points of Sec. III A, then Sec. III B and the
 Appendix: resistance, forces and their scatter to the particles), captured
 once into a CUDA graph and replayed.
 
@@ -60,7 +60,12 @@ PAIRS_BYTES_PER_PARTICLE = 64.0  # pose + shape read once (48 B) + cell index an
 PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu
 # captures, valid while the kernel's sources hash to the recorded value
-TRAFFIC = {}
+# (profiles/launches_large_1m_particles.md: the last step of `bench.py --only
+# large --steps 3`, dram__bytes_read.sum + dram__bytes_write.sum per kernel)
+TRAFFIC = {
+    "large": {"sources": "dd9c75a3b355ffb9",
+              "bytes": {"pairs_build": 329113600, "k_closest_mixed": 262222848, "k_resistance_apply": 534075136}},
+}
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")
 # the form of the timed step: lub_pairs_build, then lub_correct (closest
@@ -93,6 +98,8 @@ def parse():
     ap.add_argument("--ens-n", type=int, default=256, help="suspensions in the ensemble workload")
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--n", type=int, default=32768, help="particles of the mixed suspension (secondary)")
+    ap.add_argument("--mlp-engine", default="mma_sync", choices=["mma_sync", "tcgen05"],
+                    help="tensor-core engine of the network in --only learned")
     ap.add_argument("--only", default=None, choices=["large", "step", "ensemble", "learned"],
                     help="run only that workload eagerly, a few steps, and print a summary (for profilers; no "
                          "bench line)")
@@ -873,6 +880,7 @@ def only_leg(args, lub, torch, np, dev, stream):
         pl = lub.Pipeline(parts, dom, lub.default_params(precision="mixed", warm_start="mlp_all"),
                           capacity=len(pi), device=dev)
         WarmStartMLP.load(device=dev).install(pl.ctx)
+        lub.lub_mlp_engine(pl.ctx.h, args.mlp_engine)
         pl.set_pairs(pi, pj)
         with torch.cuda.stream(stream):
             for _ in range(args.steps):
