@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restric
 }
 
 template <bool ENS>
-__global__ void __launch_bounds__(128, 6) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
+__global__ void __launch_bounds__(128, 8) k_closest_mixed(PView P, const __grid_constant__ DView D0, Ens E,
                                                        const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
                                                        const int32_t *__restrict__ d_count, int32_t cap,
                                                        double *__restrict__ nout, double *__restrict__ gap,

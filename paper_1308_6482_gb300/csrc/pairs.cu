@@ -14,7 +14,7 @@
 //      particle against every staged candidate; those that pass the
 //      bounding-sphere test queue up for the full test, 32 at a time;
 //      each unordered pair is visited once and stored for the smaller of its
-//      two indices in that particle's row of KSLOT slots (atomic slot index); the
+//      two indices in one of that particle's KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
 //      caller's pair arrays; each thread also tests its particle's plane walls;
 //   3. one scan over [particle-pair counts | wall-pair counts] gives every
@@ -326,6 +326,11 @@ constexpr int SW = 8;         // warps per block at most
 constexpr float kFar = 1e18f;  // x of an unused staging entry: fails every test
 constexpr int kNone = 1 << 30;
 
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
+
 __device__ __forceinline__ void row_offsets(int row, int &dy, int &dz)
 {
     dz = row >= 2 ? 1 : 0;
@@ -364,16 +369,17 @@ __device__ __forceinline__ int2 row_window(const DView &D, const Grid &G, const 
     return make_int2(lo, hi);
 }
 
-// store of one accepted pair (i, j): in the row of the smaller index, or in
-// the overflow list at the tail of the pair arrays
-__device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restrict__ cnt,
+// store of one accepted pair (i, j): in slot q of the smaller index (slot
+// q of particle i at slots[q N + i]), or in the overflow list at the tail of
+// the pair arrays
+__device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__restrict__ cnt,
                                                 int32_t *__restrict__ slots, int32_t *__restrict__ ovf_n, int32_t cap,
                                                 int32_t *__restrict__ pair_i, int32_t *__restrict__ pair_j)
 {
     const int lo = min(i, j), hi = max(i, j);
     const int q = atomicAdd(cnt + lo, 1);
     if (q < KSLOT) {
-        slots[(size_t)lo * KSLOT + q] = hi;
+        slots[(size_t)q * N + lo] = hi;
     } else {
         const int o = atomicAdd(ovf_n, 1);
         if (o < cap) {
@@ -385,7 +391,9 @@ __device__ __forceinline__ void store_candidate(int i, int j, int32_t *__restric
 
 // One thread per slot s (cell order); the thread also tests its particle's
 // walls.  cnt: [0, N) pair counts per particle (of the smaller index of each
-// pair), [N, 2N) wall-pair counts; slots [N][KSLOT]; wall bits per particle;
+// pair), [N, 2N) wall-pair counts; slots [KSLOT][N] (slot-major, so that the
+// compaction's reads of the first few slots of consecutive particles are
+// coalesced and touch only the slots in use); wall bits per particle;
 // overflow entry o at pair_i/pair_j[cap - 1 - o].
 //
 // Each quarter warp is a group of 8 consecutive slots.  The group's slots in
@@ -452,11 +460,11 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     // one candidate that passed (or is undecided by) the FP32 tests
     auto decide = [&](int sa, int t, int r) {
         if (r == kAccept) {
-            store_candidate(sorted[sa], sorted[t], cnt, slots, ovf_n, cap, pair_i, pair_j);
+            store_candidate(sorted[sa], sorted[t], N, cnt, slots, ovf_n, cap, pair_i, pair_j);
         } else {
             const int i = sorted[sa], j = sorted[t];
             if (pair_test_fp64(P, dom_ref<ENS>(D0, E, ENS ? sbat[sa] : 0), i, j, cutoff_d))
-                store_candidate(i, j, cnt, slots, ovf_n, cap, pair_i, pair_j);
+                store_candidate(i, j, N, cnt, slots, ovf_n, cap, pair_i, pair_j);
         }
     };
     // the full test and the store of queue entry e
@@ -589,84 +597,104 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
 #pragma unroll
             for (int o = GL; o < 32; o <<= 1) Tw = max(Tw, __shfl_xor_sync(FULL, Tw, o));
             const float oy = dy * G.cs[1], oz = dz * G.cs[2];
-            for (int c0 = 0; c0 < Tw; c0 += SC) {
-                __syncwarp();
+            // ONE: every group of the warp has one run in this row, the image
+            // at 0 (no periodic wrap): slot t = beg[1] + u, and in row 0 the
+            // order test needs no stored slot
+            auto rounds = [&](auto one) {
+                constexpr bool ONE = decltype(one)::value;
+                for (int c0 = 0; c0 < Tw; c0 += SC) {
+                    __syncwarp();
 #pragma unroll
-                for (int h = 0; h < SC / GL; ++h) {
-                    const int q = (lane % GL) + GL * h, u = c0 + q;
-                    float4 v = make_float4(kFar, 0.f, 0.f, 0.f);
-                    int tk = 0;
-                    if (u < T) {
-                        const int k = u < num[0] ? 0 : (u < num[0] + num[1] ? 1 : 2);
-                        const int t = k == 0 ? beg[0] + u : (k == 1 ? beg[1] + u - num[0] : beg[2] + u - num[0] - num[1]);
-                        const float4 r0 = rec0[t];
-                        const int dc = (cellc[t] & 1023) + (k - 1) * nx - lcx;
-                        v = make_float4(r0.x + (float)dc * cs0, r0.y + oy, r0.z + oz, r0.w);
-                        // row 0: the image at +L_x comes after every slot
-                        tk = (row == 0 && k == 2) ? (int)((unsigned)t | 0x80000000u) : t;
-                    }
-                    cg[q] = v;
-                    ctg[q] = tk;
-                }
-                __syncwarp();
-                // the bounding spheres of the lane's particle and the staged
-                // candidates, in blocks of 8 up to the warp's longest run (the
-                // rest of a shorter group's staging holds far entries)
-                const int cn = min(SC, Tw - c0);
-                unsigned m = 0;
-                if (act) {
-                    for (int c8 = 0; c8 < cn; c8 += 8) {
-                        unsigned mb = 0;
-                        if (row == 0) {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float4 q = cg[c8 + j];
-                                const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
-                                const float hi = awc + q.w;
-                                const int tk = ctg[c8 + j];
-                                const bool p = ex * ex + ey * ey + ez * ez <= hi * hi && (tk < 0 || tk > s);
-                                mb |= (unsigned)p << j;
+                    for (int h = 0; h < SC / GL; ++h) {
+                        const int q = (lane % GL) + GL * h, u = c0 + q;
+                        float4 v = make_float4(kFar, 0.f, 0.f, 0.f);
+                        int tk = 0;
+                        if (u < T) {
+                            int k = 1, t = beg[1] + u;
+                            if (!ONE) {
+                                k = u < num[0] ? 0 : (u < num[0] + num[1] ? 1 : 2);
+                                t = k == 0 ? beg[0] + u : (k == 1 ? beg[1] + u - num[0] : beg[2] + u - num[0] - num[1]);
                             }
-                        } else {
+                            const float4 r0 = rec0[t];
+                            const int dc = (cellc[t] & 1023) + (k - 1) * nx - lcx;
+                            v = make_float4(r0.x + (float)dc * cs0, r0.y + oy, r0.z + oz, r0.w);
+                            // row 0: the image at +L_x comes after every slot
+                            tk = (row == 0 && k == 2) ? (int)((unsigned)t | 0x80000000u) : t;
+                        }
+                        cg[q] = v;
+                        if (!ONE) ctg[q] = tk;
+                    }
+                    __syncwarp();
+                    // the bounding spheres of the lane's particle and the staged
+                    // candidates, in blocks of 8 up to the warp's longest run (the
+                    // rest of a shorter group's staging holds far entries)
+                    const int cn = min(SC, Tw - c0);
+                    const int kb = beg[1] + c0 - s;  // ONE, row 0: candidate c comes after s iff c + kb > 0
+                    unsigned m = 0;
+                    if (act) {
+                        for (int c8 = 0; c8 < cn; c8 += 8) {
+                            unsigned mb = 0;
+                            if (row == 0) {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float4 q = cg[c8 + j];
-                                const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
-                                const float hi = awc + q.w;
-                                mb |= (unsigned)(ex * ex + ey * ey + ez * ez <= hi * hi) << j;
+                                for (int j = 0; j < 8; ++j) {
+                                    const float4 q = cg[c8 + j];
+                                    const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
+                                    const float hi = awc + q.w;
+                                    bool later;
+                                    if (ONE) {
+                                        later = c8 + j + kb > 0;
+                                    } else {
+                                        const int tk = ctg[c8 + j];
+                                        later = tk < 0 || tk > s;
+                                    }
+                                    const bool p = ex * ex + ey * ey + ez * ez <= hi * hi && later;
+                                    mb |= (unsigned)p << j;
+                                }
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const float4 q = cg[c8 + j];
+                                    const float ex = q.x - ax, ey = q.y - a0.y, ez = q.z - a0.z;
+                                    const float hi = awc + q.w;
+                                    mb |= (unsigned)(ex * ex + ey * ey + ez * ez <= hi * hi) << j;
+                                }
                             }
+                            m |= mb << c8;
                         }
-                        m |= mb << c8;
+                    }
+                    // the passes into the warp's queue, one per lane and round
+                    while (__any_sync(FULL, m != 0)) {
+                        const bool have = m != 0;
+                        const unsigned bal = __ballot_sync(FULL, have);
+                        if (have) {
+                            const int c = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int e = qn + __popc(bal & ((1u << lane) - 1u));
+                            const float4 q = cg[c];
+                            qd[wq][e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
+                            qt[wq][e] = ONE ? beg[1] + c0 + c : (ctg[c] & 0x7fffffff);
+                            qo[wq][e] = (uint8_t)lane;
+                        }
+                        qn += __popc(bal);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            drain(lane);
+                            __syncwarp();
+                            if (lane < qn - 32) {
+                                qd[wq][lane] = qd[wq][32 + lane];
+                                qt[wq][lane] = qt[wq][32 + lane];
+                                qo[wq][lane] = qo[wq][32 + lane];
+                            }
+                            qn -= 32;
+                            __syncwarp();
+                        }
                     }
                 }
-                // the passes into the warp's queue, one per lane and round
-                while (__any_sync(FULL, m != 0)) {
-                    const bool have = m != 0;
-                    const unsigned bal = __ballot_sync(FULL, have);
-                    if (have) {
-                        const int c = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int e = qn + __popc(bal & ((1u << lane) - 1u));
-                        const float4 q = cg[c];
-                        qd[wq][e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
-                        qt[wq][e] = ctg[c] & 0x7fffffff;
-                        qo[wq][e] = (uint8_t)lane;
-                    }
-                    qn += __popc(bal);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        drain(lane);
-                        __syncwarp();
-                        if (lane < qn - 32) {
-                            qd[wq][lane] = qd[wq][32 + lane];
-                            qt[wq][lane] = qt[wq][32 + lane];
-                            qo[wq][lane] = qo[wq][32 + lane];
-                        }
-                        qn -= 32;
-                        __syncwarp();
-                    }
-                }
-            }
+            };
+            if (__all_sync(FULL, num[0] == 0 && num[2] == 0))
+                rounds(BoolTag<true>{});
+            else
+                rounds(BoolTag<false>{});
         }
         done = done || act;
     }
@@ -715,7 +743,7 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
             // sort in registers: compare-exchange passes (m is small, mostly 0..4)
             int v[KSLOT];
 #pragma unroll
-            for (int q = 0; q < KSLOT; ++q) v[q] = q < m ? slots[(size_t)i * KSLOT + q] : INT32_MAX;
+            for (int q = 0; q < KSLOT; ++q) v[q] = q < m ? slots[(size_t)q * n + i] : INT32_MAX;
             if (m > 1) {
 #pragma unroll
                 for (int q = 1; q < KSLOT; ++q) {
@@ -738,7 +766,7 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
             // the slots, then this particle's overflow entries, then sort in place
             for (int q = 0; q < KSLOT; ++q) {
                 pair_i[b + q] = i;
-                pair_j[b + q] = slots[(size_t)i * KSLOT + q];
+                pair_j[b + q] = slots[(size_t)q * n + i];
             }
             int c = KSLOT;
             for (int o = 0; o < novf && c < m; ++o)

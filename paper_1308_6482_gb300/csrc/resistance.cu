@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance(PVie
 
 // resistance and the atomic scatter of lub_apply in one pass (FT, lever optional)
 template <typename T, bool ENS>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 1) k_resistance_apply(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_resistance_apply(PView P, const __grid_constant__ DView D0, Ens E, RParams R,
                                                           const int32_t *__restrict__ pi,
                                                           const int32_t *__restrict__ pj,
                                                           const int32_t *__restrict__ d_count, int32_t cap,
