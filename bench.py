@@ -308,15 +308,16 @@ def run_multi(lub, torch, np, pl, P, stream, G, replays, step0):
 def kernels_in_step(form=None, precision="mixed"):
     # lub_pairs_build: zeroing of its counters, cells count, scan, cells fill,
     # sweep, scan, compaction = 7.  lub_correct (the fused form), mixed:
-    # zeroing of the sums, zeroing of the work list, particle table, FP32
-    # stage, work-list FP64 solves, resistance with scatter = 6; FP64: zeroing
+    # particle table (which also clears the sums and the work list), FP32
+    # stage, work-list FP64 solves, resistance with scatter = 4; FP64: zeroing
     # and the one pass = 2.  The merged form (lub_closest_points, then
-    # lub_resistance_apply), mixed: 4 + 3 (a second particle table); FP64: 1 + 2.
+    # lub_resistance_apply), mixed: 3 + 3 (zeroing and a second particle
+    # table); FP64: 1 + 2.
     form = form or STEP_FORM
     if form == "fused":
-        return 7 + (6 if precision == "mixed" else 2)
+        return 7 + (4 if precision == "mixed" else 2)
     if precision == "mixed":
-        return 7 + 4 + 3
+        return 7 + 3 + 3
     return 7 + 1 + 2
 
 

@@ -449,11 +449,26 @@ __device__ __forceinline__ int wl_total(const int32_t *__restrict__ wl_count, in
 // (rec_ld): float-float centre and symmetry axis, semi-axes and velocities,
 // five float4 per particle (one float-float axis per particle instead of one
 // per pair and side; four 16-byte loads fetch what a kernel needs)
-__global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restrict__ out)
+// With zero16, zf, zt: also clears four counter words and the force and
+// torque sums [3][n] of the pass that follows (one launch instead of three).
+__global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restrict__ out, int32_t *__restrict__ zero16,
+                                                      float *__restrict__ zf, float *__restrict__ zt)
 {
     pdl_wait();
     pdl_trigger();
+    if (zero16 && blockIdx.x == 0 && threadIdx.x < 4) zero16[threadIdx.x] = 0;
+    const size_t n = (size_t)P.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        if (zf) {
+            zf[i] = 0.f;
+            zf[n + i] = 0.f;
+            zf[2 * n + i] = 0.f;
+        }
+        if (zt) {
+            zt[i] = 0.f;
+            zt[n + i] = 0.f;
+            zt[2 * n + i] = 0.f;
+        }
         const ff x = ff_from_double(P.x[i]), y = ff_from_double(P.y[i]), z = ff_from_double(P.z[i]);
         ff o[3];
         ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
@@ -766,12 +781,16 @@ int start_normals(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, co
 
 }  // namespace
 
-int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st)
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st, int32_t *zero16, float *zf,
+                        float *zt)
 {
-    if (P.n == 0) return LUB_OK;
+    if (P.n == 0) {
+        if (!zero16) return LUB_OK;
+        return zero_async(ctx, ctx->num_sms, zero16, 16, st);
+    }
     return lub_check_cuda(ctx,
-                          launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 8), 256, 0, st, P,
-                                     reinterpret_cast<float4 *>(out)),
+                          launch_pdl(k_particles_ff, grid_for(P.n, 256, ctx->num_sms, 32), 256, 0, st, P,
+                                     reinterpret_cast<float4 *>(out), zero16, zf, zt),
                           "particle table launch");
 }
 
@@ -784,7 +803,7 @@ namespace {
 // float-float positions and axes, 48 bytes per particle).
 int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl,
               double **gap_in = nullptr, uint8_t **status_in = nullptr, const PView *P = nullptr,
-              float2 **pff = nullptr)
+              float2 **pff = nullptr, float *zf = nullptr, float *zt = nullptr)
 {
     const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = ((8 * (size_t)cap + 255) / 256) * 256,
                  b_st = (((size_t)cap + 255) / 256) * 256, b_pos = P ? particles_ff_bytes(P->n) : 0;
@@ -795,10 +814,10 @@ int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, in
     *wl = (int32_t *)(base + 256);
     if (gap_in && !*gap_in) *gap_in = (double *)(base + 256 + b_wl);
     if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
-    rc = zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
-    if (rc || !P) return rc;
+    if (!P) return zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
+    // the particle table's kernel also clears the counters (and the sums zf, zt)
     *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
-    return launch_particles_ff(ctx, *P, *pff, st);
+    return launch_particles_ff(ctx, *P, *pff, st, *wl_count, zf, zt);
 }
 
 // What lub_correct hands from the closest-point kernels of the mixed mode to
@@ -813,7 +832,8 @@ struct ClosestKeep {
 template <bool ENS>
 int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                      const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap, double *n, double *gap,
-                     uint8_t *status, uint8_t *iters, cudaStream_t st, ClosestKeep *keep = nullptr)
+                     uint8_t *status, uint8_t *iters, cudaStream_t st, ClosestKeep *keep = nullptr,
+                     float *zero_force = nullptr, float *zero_torque = nullptr)
 {
     int warm = 0, rc;
     const bool net_all = net_every_pair(prm);
@@ -827,7 +847,8 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, keep ? &gap : nullptr, keep ? &status : nullptr, &P, &pff)))
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, keep ? &gap : nullptr, keep ? &status : nullptr, &P, &pff,
+                            zero_force, zero_torque)))
             return rc;
         if (keep) *keep = ClosestKeep{gap, status, pff};
         lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
@@ -879,15 +900,18 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
 {
     const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
     int rc;
-    if (!accumulate) {
+    if (!accumulate && (prm.precision != LUB_MIXED || cap == 0)) {
         if ((rc = zero_force_torque(ctx, force, torque, 3 * (size_t)P.n * esz, st))) return rc;
     }
     if (cap == 0) return LUB_OK;
     if (prm.precision == LUB_MIXED) {
         // the kernels of lub_closest_points, then those of lub_resistance_apply
-        // on the same per-call particle records (built once)
+        // on the same per-call particle records (built once; their kernel also
+        // clears the sums unless accumulate is set)
         ClosestKeep keep;
-        if ((rc = launch_closest_t<ENS>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, st, &keep)))
+        if ((rc = launch_closest_t<ENS>(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, status, iters, st, &keep,
+                                        accumulate ? nullptr : (float *)force,
+                                        accumulate ? nullptr : (float *)torque)))
             return rc;
         return launch_resistance_apply(ctx, P, D, E, prm, pi, pj, d_count, cap, n, keep.gap, keep.status, FT, lever,
                                        force, torque, 1, st, keep.pff);

@@ -504,7 +504,9 @@ inline Shape2 tuned_shape(const lub_ctx *ctx, int id, int64_t work)
 // written by one kernel on the stream; `out` (16-byte aligned) holds
 // particles_ff_bytes(n) bytes.
 inline size_t particles_ff_bytes(int64_t n) { return 80 * (size_t)(n > 0 ? n : 0); }
-int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st);
+// zero16 (4 words) and zf, zt ([3][n] floats each): cleared by the same launch
+int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t st, int32_t *zero16 = nullptr,
+                        float *zf = nullptr, float *zt = nullptr);
 
 // pair build on caller-provided scratch (no allocation)
 size_t pairs_scratch_bytes(int64_t n, int64_t max_cells);

@@ -971,7 +971,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.ncell_total = G.ncell;
     cudaError_t e;
     const int block = 256;
-    const int gn = grid_for(N, block, num_sms, 8);
+    const int gn = grid_for(N, block, num_sms, 32);  // one particle per thread up to 1.2M
     e = launch_pdl(k_cells_count<ENS>, gn, block, 0, st, V);
     if ((rc = lub_check_cuda(ctx, e, "cells count launch"))) return rc;
     if ((rc = scan_exclusive(ctx, L.cell_cnt, G.ncell + 1, L.totals + 1, L.tmp, L.tmp_bytes, st, L.flags, true)))
@@ -987,7 +987,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;
-    e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 16), 256, 0, st, V);
+    e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 32), 256, 0, st, V);
     return lub_check_cuda(ctx, e, "pairs compact launch");
 }
 
