@@ -60,8 +60,8 @@ PAIRS_BYTES_PER_PARTICLE = 64.0  # pose + shape read once (48 B) + cell index an
 PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu
 # captures, valid while the kernel's sources hash to the recorded value
-# (profiles/launches_large_1m_particles.md: the last step of `bench.py --only
-# large --steps 3`, dram__bytes_read.sum + dram__bytes_write.sum per kernel)
+# (one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum per kernel
+# over `bench.py --only large --steps 3`, the last of its three steps)
 TRAFFIC = {
     "large": {"sources": "dd9c75a3b355ffb9",
               "bytes": {"pairs_build": 329113600, "k_closest_mixed": 262222848, "k_resistance_apply": 534075136}},
@@ -100,7 +100,7 @@ def parse():
     ap.add_argument("--n", type=int, default=32768, help="particles of the mixed suspension (secondary)")
     ap.add_argument("--mlp-engine", default="mma_sync", choices=["mma_sync", "tcgen05"],
                     help="tensor-core engine of the network in --only learned")
-    ap.add_argument("--only", default=None, choices=["large", "step", "ensemble", "learned"],
+    ap.add_argument("--only", default=None, choices=["large", "step", "ensemble", "learned", "probe"],
                     help="run only that workload eagerly, a few steps, and print a summary (for profilers; no "
                          "bench line)")
     return ap.parse_args()
@@ -858,6 +858,24 @@ def only_leg(args, lub, torch, np, dev, stream):
     short, fixed launch sequence for a profiler."""
     import gen
     from paper_1308_6482_gb300.mlp import WarmStartMLP
+    if args.only == "probe":
+        # the ALU roofline denominators: lub_probe_peak repeated, with the SM
+        # clocks sampled while it runs
+        ctx = lub.Context()
+        props = torch.cuda.get_device_properties(dev)
+        clocks = ClockSampler(dev.index or 0)
+        clocks.start()
+        runs = {"fp32": [], "fp64": []}
+        for _ in range(max(3, args.steps)):
+            runs["fp32"].append(lub.lub_probe_peak(ctx.h, lub.LUB_PROBE_FP32))
+            runs["fp64"].append(lub.lub_probe_peak(ctx.h, lub.LUB_PROBE_FP64))
+        clk = clocks.stop()
+        return {"device": props.name, "sms": props.multi_processor_count,
+                "tflops": {k: {"median": float(np.median(v)), "min": float(np.min(v)), "max": float(np.max(v)),
+                               "runs": len(v)} for k, v in runs.items()},
+                "clocks": clk,
+                "method": "8 independent FMA chains per thread, 8 blocks of 256 threads per SM, 2^17 (FP32) / "
+                          "2^12 (FP64) iterations, best of 3 timed launches after one warm-up (CUDA events)"}
     if args.only == "large":
         parts, dom = gen.large_config(N=args.large_n, seed=6)
         rmax = float(max(parts["r_par"].max(), parts["r_perp"].max())) + 0.05
