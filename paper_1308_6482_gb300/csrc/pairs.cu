@@ -449,7 +449,8 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     __shared__ int cand_t[SW][NG * (SC + 1)];
     __shared__ float4 own1[SW * 32];  // each lane's symmetry axis and e
     __shared__ float2 ownw[SW * 32];  // each lane's Rmax and its group's margin
-    __shared__ float4 qd[SW][64];     // queued: d (x, y, z) and Rmax of the candidate
+    __shared__ int own_i[SW * 32];    // each lane's particle index
+    __shared__ float4 qd[SW][64];     // queued (a ring per warp): d (x, y, z) and Rmax of the candidate
     __shared__ int qt[SW][64];        // queued: candidate slot t
     __shared__ uint8_t qo[SW][64];    // queued: lane of the particle
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, g = lane / GL;
@@ -457,28 +458,25 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int s0w = s - lane;
     const bool valid = s < N;
-    // one candidate that passed (or is undecided by) the FP32 tests
-    auto decide = [&](int sa, int t, int r) {
-        if (r == kAccept) {
-            store_candidate(sorted[sa], sorted[t], N, cnt, slots, ovf_n, cap, pair_i, pair_j);
-        } else {
-            const int i = sorted[sa], j = sorted[t];
-            if (pair_test_fp64(P, dom_ref<ENS>(D0, E, ENS ? sbat[sa] : 0), i, j, cutoff_d))
-                store_candidate(i, j, N, cnt, slots, ovf_n, cap, pair_i, pair_j);
-        }
-    };
-    // the full test and the store of queue entry e
+    // the full test and the store of queue entry e (the candidate's record
+    // and index are fetched together, before the decision needs them)
     auto drain = [&](int e) {
         const float4 d = qd[wq][e];
         const int t = qt[wq][e];
         const int o = qo[wq][e];
-        const int so = s0w + o;
+        const float4 b1 = rec1[t];
+        const int jj = sorted[t];
+        const int ii = own_i[wbase + o];
         const float2 wm = ownw[wbase + o];
-        const Grid &G = grid_ref<ENS>(G0, EG, ENS ? sbat[so] : 0);
-        const int r = pair_decide(G.cutoff, wm.y, wm.x, own1[wbase + o], d.w, rec1[t], d.x, d.y, d.z);
-        if (r != kReject) decide(so, t, r);
+        const int bo = ENS ? sbat[s0w + o] : 0;
+        const Grid &G = grid_ref<ENS>(G0, EG, bo);
+        const int r = pair_decide(G.cutoff, wm.y, wm.x, own1[wbase + o], d.w, b1, d.x, d.y, d.z);
+        // inside the margin the FP64 test decides
+        if (r == kAccept ||
+            (r == kUndecided && pair_test_fp64(P, dom_ref<ENS>(D0, E, bo), ii, jj, cutoff_d)))
+            store_candidate(ii, jj, N, cnt, slots, ovf_n, cap, pair_i, pair_j);
     };
-    int b = 0, cc = 0, colkey = -1;
+    int b = 0, cc = 0, colkey = -1, pidx = -1;
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
     if (valid) {
         b = ENS ? sbat[s] : 0;
@@ -493,6 +491,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         // records (one double subtraction for z - z_w), decided in FP64 only
         // within the margin (the exact test costs some 60 FP64 operations)
         const int i = sorted[s];
+        pidx = i;
         const float rm2 = a0.w * a0.w;
         const float sz = sqrtf(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
         int wf = 0, bits = 0;
@@ -515,7 +514,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     const int cx = cc & 1023;
     float4 *const cg = &cand[wq][g * (SC + 1)];
     int *const ctg = &cand_t[wq][g * (SC + 1)];
-    int qn = 0;
+    int qn = 0, qh = 0;  // the warp's queue: qn entries from qh on (a ring of 64)
     bool done = !valid;
     // one pass per column among each group's slots (one for most groups)
     while (__any_sync(FULL, !done)) {
@@ -549,6 +548,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         if (act) {
             own1[threadIdx.x] = a1;
             ownw[threadIdx.x] = make_float2(a0.w, marg);
+            own_i[threadIdx.x] = pidx;
         }
         for (int row = 0; row < SWEEP_ROWS; ++row) {
             int dy, dz;
@@ -669,7 +669,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
                         if (have) {
                             const int c = __ffs(m) - 1;
                             m &= m - 1;
-                            const int e = qn + __popc(bal & ((1u << lane) - 1u));
+                            const int e = (qh + qn + __popc(bal & ((1u << lane) - 1u))) & 63;
                             const float4 q = cg[c];
                             qd[wq][e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
                             qt[wq][e] = ONE ? beg[1] + c0 + c : (ctg[c] & 0x7fffffff);
@@ -678,15 +678,10 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
                         qn += __popc(bal);
                         if (qn >= 32) {
                             __syncwarp();
-                            drain(lane);
+                            drain((qh + lane) & 63);
                             __syncwarp();
-                            if (lane < qn - 32) {
-                                qd[wq][lane] = qd[wq][32 + lane];
-                                qt[wq][lane] = qt[wq][32 + lane];
-                                qo[wq][lane] = qo[wq][32 + lane];
-                            }
+                            qh = (qh + 32) & 63;
                             qn -= 32;
-                            __syncwarp();
                         }
                     }
                 }
@@ -699,7 +694,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         done = done || act;
     }
     __syncwarp();
-    if (lane < qn) drain(lane);
+    if (lane < qn) drain((qh + lane) & 63);
 }
 
 template <bool ENS>
