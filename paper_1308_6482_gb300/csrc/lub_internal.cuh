@@ -479,10 +479,10 @@ struct TuneDefault {
 // grid-stride loop, balances the uneven per-pair work (Newton iteration
 // counts, refinement) on large inputs
 constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
-    {128, 64, 128},  // LUB_TUNE_CLOSEST_MIXED
+    {64, 256, 128},  // LUB_TUNE_CLOSEST_MIXED (the autotuner's choice at 1M and 32k particles)
     {32, 64, 32},    // LUB_TUNE_CLOSEST_REFINE
     {128, 64, 128},  // LUB_TUNE_CLOSEST_FP64
-    {128, 64, 128},  // LUB_TUNE_RESISTANCE
+    {64, 256, 128},  // LUB_TUNE_RESISTANCE (the autotuner's choice at 1M particles)
     {256, 32, 256},  // LUB_TUNE_APPLY
     {256, 32, 256},  // LUB_TUNE_SWEEP
 };
