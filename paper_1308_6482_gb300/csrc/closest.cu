@@ -146,9 +146,10 @@ __device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o
 // Minimum-image separation r_j - r_i in float-float from the particles'
 // records (rec_ld 0 and 1: the float-float centres); the image shift is
 // taken from the float part (listed pairs are far from the ambiguous half
-// box).  About 48 bits: an absolute error near 2^-48 |r| (4e-12 at |r| =
-// 1000), against the FP64 subtraction and splitting it replaces (some 24
-// FP64 operations per pair, at 1/64 of the FP32 rate).
+// box).  The centres carry 46 bits (split from their bits): an absolute
+// error below 2^-46 |r| each (1.5e-11 at |r| = 1000), against the FP64
+// subtraction and splitting it replaces (some 24 FP64 operations per pair,
+// at 1/74 of the FP32 rate).
 __device__ __forceinline__ void ff_separation(const float4 &ri0, const float4 &ri1, const float4 &rj0,
                                               const float4 &rj1, const DView &D, ff d[3])
 {
@@ -469,7 +470,8 @@ __global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restric
             zt[n + i] = 0.f;
             zt[2 * n + i] = 0.f;
         }
-        const ff x = ff_from_double(P.x[i]), y = ff_from_double(P.y[i]), z = ff_from_double(P.z[i]);
+        // the centre split from its bits (46 bits: 1.5e-11 at |r| = 1024; no FP64 pipe)
+        const ff x = ff_split_bits_nan(P.x[i]), y = ff_split_bits_nan(P.y[i]), z = ff_split_bits_nan(P.z[i]);
         ff o[3];
         ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
         float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

@@ -211,3 +211,17 @@ __device__ __forceinline__ ff ff_split_bits(double d)
     r.lo = sign ? -lo : lo;
     return r;
 }
+
+// ff_split_bits with NaN kept as NaN (ff_split_bits gives infinity for it):
+// positions split without the FP64 pipe, a NaN still failing every test
+__device__ __forceinline__ ff ff_split_bits_nan(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
+    if (b > 0x7FF0000000000000ull) {
+        ff r;
+        r.hi = __int_as_float(0x7FC00000);
+        r.lo = 0.0f;
+        return r;
+    }
+    return ff_split_bits(d);
+}

@@ -117,14 +117,15 @@ struct BuildView {
 __device__ __forceinline__ bool ff_neg_(const ff x) { return x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f); }
 
 // Cell of one coordinate and the position relative to the cell's centre.  The
-// double coordinate is split once into float-float (four FP64-pipe
-// operations; GB300 runs FP64 at 1/64 of the FP32 rate) and the rest runs
-// on the FP32 pipe: the wrap into [0, L) on a periodic axis, the cell
-// floor(x / cs) in FP32, corrected by the exact sign of the float-float
-// remainder x - c cs (so a cell holds its positions to about 1e-14 of its
-// edges, well inside the 1e-9 allowance of the cell size), and the clamp to
-// the edge cells of an open axis (a position outside the box then lies
-// beyond its cell).  NaN goes to cell 0.
+// double coordinate is split into float-float from its bits (46 significant
+// bits: within 1.5e-11 at |x| = 1024, on the integer pipes; GB300 runs FP64
+// at 1/74 of the FP32 rate) and the rest runs on the FP32 pipe: the wrap
+// into [0, L) on a periodic axis, the cell floor(x / cs) in FP32, corrected
+// by the exact sign of the float-float remainder x - c cs (so a cell holds
+// its positions to within the split's error of its edges, far inside the
+// 1e-9 allowance of the cell size), and the clamp to the edge cells of an
+// open axis (a position outside the box then lies beyond its cell).  NaN
+// goes to cell 0.
 struct AxisCell {
     int c;
     float rel;
@@ -132,10 +133,7 @@ struct AxisCell {
 
 __device__ __forceinline__ AxisCell axis_cell(double x, const DView &D, const Grid &G, int a)
 {
-    const float hi = __double2float_rn(x);
-    ff p;
-    p.hi = hi;
-    p.lo = __double2float_rn(x - (double)hi);
+    ff p = ff_split_bits_nan(x);
     if (D.periodic[a]) {
         const ff L = {D.Lff[a][0], D.Lff[a][1]};
         const float k = floorf(p.hi * D.invLf[a]);
