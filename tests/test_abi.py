@@ -101,3 +101,17 @@ def test_no_cpu_fallback_in_the_product_package():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_header_constants_match_the_binding():
+    """Every integer constant of the header has the same value in the
+    binding (return codes, modes, status bits, limits)."""
+    import paper_1308_6482_gb300._lib as L
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = dict(re.findall(r"^#define\s+(LUB_[A-Z0-9_]+)\s+\(?(-?\d+)\)?\s*$", src, flags=re.M))
+    assert len(consts) > 30
+    for name, value in consts.items():
+        if name == "LUB_STATIC_SCRATCH_BYTES":
+            continue  # the size of the static array: host code never passes it
+        assert hasattr(L, name), name
+        assert getattr(L, name) == int(value), (name, getattr(L, name), value)
