@@ -71,6 +71,11 @@ TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", 
 # the form of the timed step: lub_pairs_build, then lub_correct (closest
 # points, resistance and scatter in one call)
 STEP_FORM = "fused"
+# the timed step writes every output: the per-particle force and torque sums,
+# the normals, gaps, statuses, iteration counts and the per-pair forces and
+# lever arms; the same step without the last two (optional outputs) is
+# reported beside it
+PAIR_FORCES = True
 MOTION_SEED = 777
 SIG_R, SIG_T = 0.01, 0.005
 
@@ -247,10 +252,10 @@ def run_steps(lub, torch, np, pl, P, stream, flush, steps, warmup):
     graph between two events.  Returns ms [steps], pair counts [steps], the
     mean Newton iterations per pair and the capacity overflows."""
     with torch.cuda.stream(stream):
-        pl.step(form=STEP_FORM, stream=stream)
-        pl.step(form=STEP_FORM, stream=stream)
+        pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
+        pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
     stream.synchronize()
-    g = graph_of(torch, stream, lambda: pl.step(form=STEP_FORM, stream=stream))
+    g = graph_of(torch, stream, lambda: pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream))
     dev = P.t["x"].device
     counts = torch.zeros(steps, dtype=torch.int32, device=dev)
     its = torch.zeros(steps, dtype=torch.float64, device=dev)
@@ -288,10 +293,10 @@ def run_multi(lub, torch, np, pl, P, stream, G, replays, step0):
         for j in range(G):
             lub.lub_random_motion(pl.ctx.h, P.c, MOTION_SEED, 0, SIG_R, SIG_T, step_dev=ctr[j % 2:],
                                   next_dev=ctr[(j + 1) % 2:], stream=stream)
-            pl.step(form=STEP_FORM, stream=stream)
+            pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
 
     with torch.cuda.stream(stream):
-        pl.step(form=STEP_FORM, stream=stream)
+        pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
     stream.synchronize()
     g = graph_of(torch, stream, body)
     ev = event_pairs(torch, replays)
@@ -436,8 +441,13 @@ def large_headline(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
                                  2 * 10 ** 6)
             # the other forms of the same step (the same calls, the same motions)
             other_ms = {}
-            for f2 in ("merged", "calls"):
-                g2 = graph_of(torch, stream, lambda f2=f2: pl.step(form=f2, stream=stream))
+            # the forms of the step measured side by side (20 graph replays each, the
+            # motions inside the loop): the timed one, the same without the
+            # per-pair forces and lever arms, and the two forms of separate calls
+            for f2 in ("fused", "fused_without_pair_forces", "merged", "calls"):
+                pf = PAIR_FORCES if f2 == "fused" else f2 != "fused_without_pair_forces"
+                g2 = graph_of(torch, stream, lambda f2=f2, pf=pf: pl.step(form=f2.split("_with")[0], pair_forces=pf,
+                                                                          stream=stream))
                 e2 = event_pairs(torch, 20)
                 with torch.cuda.stream(stream):
                     for k, (a, b) in enumerate(e2):
@@ -493,7 +503,7 @@ def e2e_large(args, lub, torch, np, parts, dom, dev, stream, rmax, net):
 
     def e2e_step():
         Pk.blob.copy_(hblob, non_blocking=True)
-        ple.step(form=STEP_FORM, stream=stream)
+        ple.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
         hout.copy_(ple.ft_particles, non_blocking=True)
 
     with torch.cuda.stream(stream):
@@ -594,7 +604,9 @@ def suspension_32k(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
     K = max(20, min(args.steps, 200))
-    forms = {f: time_graph(lambda f=f: pl.step(form=f, stream=stream), K) for f in ("merged", "calls", "fused")}
+    forms = {f: time_graph(lambda f=f: pl.step(form=f, pair_forces=(PAIR_FORCES if f == STEP_FORM else True),
+                                               stream=stream), K)
+             for f in ("merged", "calls", "fused")}
     res = pl.results()
     # per-call and per-kernel times of eager steps
     lub.lub_trace_enable(pl.ctx.h, 1)
@@ -623,7 +635,7 @@ def suspension_32k(args, lub, torch, np, dev, stream, flush, ws, rank, pk):
     pln = lub.Pipeline(lub.DeviceParticles(parts, dev), dom, lub.default_params(precision="mixed", model="normal"),
                        capacity=pl.cap, device=dev)
     pln.build_pairs()
-    normal_ms = time_graph(lambda: pln.step(form=STEP_FORM, stream=stream), 50)
+    normal_ms = time_graph(lambda: pln.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream), 50)
     del pln
     # the link-based model of Ding and Aidun (Sec. II) on the same pair list
     with torch.cuda.stream(stream):
@@ -824,12 +836,12 @@ def ensemble_bench(args, lub, torch, np, dev, stream, flush, ws=1, rank=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for q in sep:
-            q.step(form=STEP_FORM, stream=stream)
+            q.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
         flush.zero_()
         e0.record(stream)
         for _ in range(Ks):
             for q in sep:
-                q.step(form=STEP_FORM, stream=stream)
+                q.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
         e1.record(stream)
     stream.synchronize()
     sep_ms = e0.elapsed_time(e1) / Ks
@@ -913,7 +925,7 @@ def only_leg(args, lub, torch, np, dev, stream):
         return {"pairs": len(pi), "steps": args.steps}
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            pl.step(form=STEP_FORM, stream=stream)
+            pl.step(form=STEP_FORM, pair_forces=PAIR_FORCES, stream=stream)
     stream.synchronize()
     return {"pairs": int(min(pl.count(), pl.cap)), "steps": args.steps}
 

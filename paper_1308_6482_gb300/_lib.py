@@ -650,12 +650,15 @@ class Pipeline:
                      stream)
         return {TUNE_NAMES[k]: lub_get_launch_shape(self.ctx.h, k) for k in range(LUB_TUNE_COUNT)}
 
-    def correct(self, per_pair=True, stream=None):
+    def correct(self, per_pair=True, pair_forces=True, stream=None):
         """Closest points, resistance and scatter in one call (lub_correct);
-        per_pair=False skips the per-pair outputs other than the normals."""
+        per_pair=False skips the per-pair outputs other than the normals,
+        pair_forces=False only the per-pair forces and lever arms (FT,
+        lever): the per-particle sums are the step's result either way."""
         o = (lambda t: t) if per_pair else (lambda t: None)
+        f = (lambda t: t) if (per_pair and pair_forces) else (lambda t: None)
         lub_correct(self.ctx.h, self.P.c, self.D, self.prm, self.pair_i, self.pair_j, self.d_count, self.cap, self.nrm,
-                    o(self.gap), o(self.status), o(self.iters), o(self.FT), o(self.lever), self.force, self.torque, 0,
+                    o(self.gap), o(self.status), o(self.iters), f(self.FT), f(self.lever), self.force, self.torque, 0,
                     stream)
 
     def resistance_apply(self, per_pair=True, stream=None):
@@ -666,7 +669,7 @@ class Pipeline:
                              self.torque, 0, stream)
 
     def step(self, build=True, deterministic=0, sync_count=False, fused=False, per_pair=True, form=None,
-             stream=None):
+             pair_forces=True, stream=None):
         """One correction step: the pair build, then the per-pair work in one
         of three forms: "calls" (closest points, resistance, apply), "merged"
         (closest points, then resistance + scatter in one pass) or "fused"
@@ -675,7 +678,8 @@ class Pipeline:
         fused=True is the same).  deterministic needs
         "calls".  With warm_start = LUB_WARM_PREVIOUS the normals are carried
         over from the step before (keep_previous is called at the end of
-        every step)."""
+        every step).  pair_forces=False: the fused form writes no per-pair
+        forces and lever arms (the other forms always do)."""
         form = form or ("fused" if fused else "calls")
         if deterministic:
             form = "calls"
@@ -685,7 +689,7 @@ class Pipeline:
         if temporal and getattr(self, "prev_cap", None) == self.cap:
             self.carry(stream)
         if form == "fused":
-            self.correct(per_pair=per_pair, stream=stream)
+            self.correct(per_pair=per_pair, pair_forces=pair_forces, stream=stream)
         elif form == "merged":
             self.closest(stream)
             self.resistance_apply(per_pair=per_pair, stream=stream)
