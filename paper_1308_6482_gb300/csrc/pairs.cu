@@ -486,15 +486,18 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const int cy = (cc >> 10) & 1023, cz = cc >> 20;
         colkey = cell_base<ENS>(EG, b) + (cz * G.nc[1] + cy) * G.nc[0];  // first cell of the column
         // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
-        // records (one double subtraction for z - z_w), decided in FP64 only
-        // within the margin (the exact test costs some 60 FP64 operations)
+        // records (z - z_w in float-float), decided in FP64 only within the
+        // margin (the exact test costs some 60 FP64 operations)
         const int i = sorted[s];
         pidx = i;
         const float rm2 = a0.w * a0.w;
         const float sz = sqrtf(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
         int wf = 0, bits = 0;
+        // z - z_w in float-float from the bits of both (no FP64 pipe)
+        const ff zf = ff_split_bits_nan(P.z[i]);
         for (int ww = 0; ww < D.n_walls; ++ww) {
-            const float hw = (float)D.wall_dir[ww] * (float)(P.z[i] - D.wall_z[ww]) - sz;
+            const ff dzw = ff_sub(zf, ff_split_bits_nan(D.wall_z[ww]));
+            const float hw = (float)D.wall_dir[ww] * (dzw.hi + dzw.lo) - sz;
             bool in = hw < G.cutoff - G.margin;
             if (!in && hw <= G.cutoff + G.margin) {
                 const Shape<double> si = load_shape<double>(P, i);
