@@ -1,15 +1,16 @@
 // Float-float ("double-single") arithmetic on the FP32 pipe.
 //
-// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
-// about 48 significant bits.  The building blocks are the error-free
-// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2), Fast2Sum (Dekker 1971)
-// and TwoProduct with a fused multiply-add (the product's rounding error is
-// fma(a, b, -a*b)); addition, multiplication and the square root with one
-// Newton correction follow Dekker, "A floating-point technique for extending
-// the available precision", Numer. Math. 18 (1971).  GB300 runs FP32 about 60
-// times faster than FP64, so a float-float operation of 10-20 FP32
-// instructions costs less than one FP64 operation.  The _rn intrinsics keep
-// the compiler from contracting or reordering the error terms.
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (|lo| < ulp(hi) for a double split from its bits, ff_split_bits), about 48
+// significant bits.  The building blocks are the error-free transformations
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2), Fast2Sum (Dekker 1971) and TwoProduct
+// with a fused multiply-add (the product's rounding error is
+// fma(a, b, -a*b)); addition, multiplication and the reciprocal square root
+// with one Newton correction follow Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18 (1971).  GB300 runs
+// FP32 about 74 times faster than FP64, so a float-float operation of 10-20
+// FP32 instructions costs less than one FP64 operation.  The _rn intrinsics
+// keep the compiler from contracting or reordering the error terms.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -91,25 +92,6 @@ __device__ __forceinline__ ff ff_mulf(ff x, float y)
     return fast_two_sum(p.hi, e);
 }
 
-// square root of a positive value: s = sqrt(hi), one Newton correction
-// (x - s^2) / (2 s) with x - s^2 formed exactly
-__device__ __forceinline__ ff ff_sqrt(ff x)
-{
-    const float s = __fsqrt_rn(x.hi);
-    const ff p = two_prod(s, s);
-    const float r = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo), __fdiv_rn(0.5f, s));
-    return fast_two_sum(s, r);
-}
-
-// reciprocal: r = 1 / hi, one Newton correction r (1 - x r) with the
-// residual 1 - x r formed in float-float
-__device__ __forceinline__ ff ff_rcp(ff x)
-{
-    const float r = __fdiv_rn(1.0f, x.hi);
-    const ff e = ff_sub(ff_make(1.0f), ff_mulf(x, r));
-    return fast_two_sum(r, __fmul_rn(r, e.hi));
-}
-
 // 1 / sqrt(x) of a positive value: r = rsqrt(hi), one Newton correction
 // r + r (1 - x r^2) / 2 with the residual 1 - x r^2 formed in float-float
 __device__ __forceinline__ ff ff_rsqrt(ff x)
@@ -168,16 +150,6 @@ __device__ __forceinline__ ff ff_dot3_exact(const float a[3], const float b[3])
 {
     return ff_add(ff_add(two_prod(a[0], b[0]), two_prod(a[1], b[1])), two_prod(a[2], b[2]));
 }
-
-__device__ __forceinline__ ff ff_from_double(double d)
-{
-    const float hi = __double2float_rn(d);
-    ff r;
-    r.hi = hi;
-    r.lo = __double2float_rn(d - (double)hi);
-    return r;
-}
-
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
 // Float-float split of a double with integer and FP32 operations only (no
