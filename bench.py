@@ -964,7 +964,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+ff32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed (FP32; float-float gap, normal and normal velocity; "
                                                       "FP64 for pairs the FP32 Newton fails)",
-                   "form": "pair build + closest points + resistance with scatter, one CUDA graph per step",
+                   "form": "lub_pairs_build, then lub_correct (closest points, resistance, scatter), one CUDA "
+                           "graph per step",
                    "warm_start": "learned (LUB_WARM_MLP: the network starts the FP64 solves; FP32 Newton from the "
                                  "line of centres)",
                    "particles": head["particles"], "pairs_per_step": head["pairs_per_step"],
