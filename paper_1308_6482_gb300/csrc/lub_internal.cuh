@@ -484,7 +484,7 @@ constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
     {128, 64, 128},  // LUB_TUNE_CLOSEST_FP64
     {64, 256, 128},  // LUB_TUNE_RESISTANCE (the autotuner's choice at 1M particles)
     {256, 32, 256},  // LUB_TUNE_APPLY
-    {256, 32, 256},  // LUB_TUNE_SWEEP
+    {128, 32, 256},  // LUB_TUNE_SWEEP (the autotuner's choice at 1M particles)
 };
 inline Shape2 tuned_shape(const lub_ctx *ctx, int id, int64_t work)
 {

@@ -320,7 +320,6 @@ constexpr int SWEEP_ROWS = 5;
 constexpr int GL = 8;         // lanes (consecutive slots) per group
 constexpr int NG = 32 / GL;   // groups per warp
 constexpr int SC = 32;        // candidates a group stages per round
-constexpr int SW = 8;         // warps per block at most
 constexpr float kFar = 1e18f;  // x of an unused staging entry: fails every test
 constexpr int kNone = 1 << 30;
 
@@ -417,6 +416,22 @@ __device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__
 //
 // Candidates inside the FP32 margin (about one in 10^4) are decided on the
 // spot by the FP64 test, in the lane that holds them.
+// One warp's shared memory in the sweep (the block holds blockDim.x / 32 of
+// them, dynamic): the groups' staging (rows padded by one entry, so that the
+// groups' broadcast reads fall in different banks), each lane's particle,
+// and the warp's queue of candidates for the full test (a ring of 64).
+struct SweepWarp {
+    float4 cand[NG * (SC + 1)];
+    float4 own1[32];  // each lane's symmetry axis and e
+    float4 qd[64];    // queued: d (x, y, z) and Rmax of the candidate
+    float2 ownw[32];  // each lane's Rmax and its group's margin
+    int cand_t[NG * (SC + 1)];
+    int own_i[32];    // each lane's particle index
+    int qt[64];       // queued: candidate slot t
+    uint8_t qo[64];   // queued: lane of the particle
+};
+static_assert(sizeof(SweepWarp) % 16 == 0, "warp blocks stay 16-byte aligned");
+
 template <bool ENS>
 __device__ __forceinline__ void sweep_groups(const BuildView &V)
 {
@@ -441,34 +456,26 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     const double cutoff_d = V.cutoff_d;
     const int N = P.n;
     constexpr unsigned FULL = 0xffffffffu;
-    // staging rows padded by one entry: the groups' broadcast reads fall in
-    // different banks
-    __shared__ float4 cand[SW][NG * (SC + 1)];
-    __shared__ int cand_t[SW][NG * (SC + 1)];
-    __shared__ float4 own1[SW * 32];  // each lane's symmetry axis and e
-    __shared__ float2 ownw[SW * 32];  // each lane's Rmax and its group's margin
-    __shared__ int own_i[SW * 32];    // each lane's particle index
-    __shared__ float4 qd[SW][64];     // queued (a ring per warp): d (x, y, z) and Rmax of the candidate
-    __shared__ int qt[SW][64];        // queued: candidate slot t
-    __shared__ uint8_t qo[SW][64];    // queued: lane of the particle
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, g = lane / GL;
-    const int wbase = threadIdx.x & ~31;
+    // this warp's part of the block's dynamic shared memory
+    extern __shared__ float4 sweep_smem[];
+    SweepWarp &W = reinterpret_cast<SweepWarp *>(sweep_smem)[wq];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int s0w = s - lane;
     const bool valid = s < N;
     // the full test and the store of queue entry e (the candidate's record
     // and index are fetched together, before the decision needs them)
     auto drain = [&](int e) {
-        const float4 d = qd[wq][e];
-        const int t = qt[wq][e];
-        const int o = qo[wq][e];
+        const float4 d = W.qd[e];
+        const int t = W.qt[e];
+        const int o = W.qo[e];
         const float4 b1 = rec1[t];
         const int jj = sorted[t];
-        const int ii = own_i[wbase + o];
-        const float2 wm = ownw[wbase + o];
+        const int ii = W.own_i[o];
+        const float2 wm = W.ownw[o];
         const int bo = ENS ? sbat[s0w + o] : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, bo);
-        const int r = pair_decide(G.cutoff, wm.y, wm.x, own1[wbase + o], d.w, b1, d.x, d.y, d.z);
+        const int r = pair_decide(G.cutoff, wm.y, wm.x, W.own1[o], d.w, b1, d.x, d.y, d.z);
         // inside the margin the FP64 test decides
         if (r == kAccept ||
             (r == kUndecided && pair_test_fp64(P, dom_ref<ENS>(D0, E, bo), ii, jj, cutoff_d)))
@@ -513,8 +520,8 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         wbits[i] = (uint8_t)bits;
     }
     const int cx = cc & 1023;
-    float4 *const cg = &cand[wq][g * (SC + 1)];
-    int *const ctg = &cand_t[wq][g * (SC + 1)];
+    float4 *const cg = &W.cand[g * (SC + 1)];
+    int *const ctg = &W.cand_t[g * (SC + 1)];
     int qn = 0, qh = 0;  // the warp's queue: qn entries from qh on (a ring of 64)
     bool done = !valid;
     // one pass per column among each group's slots (one for most groups)
@@ -547,9 +554,9 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const float ax = a0.x + (float)(cx - lcx) * cs0;
         const float awc = a0.w + G.cutoff + marg;
         if (act) {
-            own1[threadIdx.x] = a1;
-            ownw[threadIdx.x] = make_float2(a0.w, marg);
-            own_i[threadIdx.x] = pidx;
+            W.own1[lane] = a1;
+            W.ownw[lane] = make_float2(a0.w, marg);
+            W.own_i[lane] = pidx;
         }
         for (int row = 0; row < SWEEP_ROWS; ++row) {
             int dy, dz;
@@ -672,9 +679,9 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
                             m &= m - 1;
                             const int e = (qh + qn + __popc(bal & ((1u << lane) - 1u))) & 63;
                             const float4 q = cg[c];
-                            qd[wq][e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
-                            qt[wq][e] = ONE ? beg[1] + c0 + c : (ctg[c] & 0x7fffffff);
-                            qo[wq][e] = (uint8_t)lane;
+                            W.qd[e] = make_float4(q.x - ax, q.y - a0.y, q.z - a0.z, q.w);
+                            W.qt[e] = ONE ? beg[1] + c0 + c : (ctg[c] & 0x7fffffff);
+                            W.qo[e] = (uint8_t)lane;
                         }
                         qn += __popc(bal);
                         if (qn >= 32) {
@@ -698,6 +705,8 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     if (lane < qn) drain((qh + lane) & 63);
 }
 
+// 64 registers: four blocks of 256 or eight of 128 per SM (the shared memory
+// follows the block: blockDim.x / 32 SweepWarp)
 template <bool ENS>
 __global__ void __launch_bounds__(256, 4) k_pairs_sweep(const __grid_constant__ BuildView V)
 {
@@ -978,7 +987,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     Shape2 sw = tuned_shape(ctx, LUB_TUNE_SWEEP, N);
     sw.grid = (int)((N + sw.block - 1) / sw.block);
     lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
-    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, 0, st, V);
+    e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, (size_t)(sw.block / 32) * sizeof(SweepWarp), st, V);
     lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
