@@ -63,8 +63,8 @@ PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # (one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum per kernel
 # over `bench.py --only large --steps 3`, the last of its three steps)
 TRAFFIC = {
-    "large": {"sources": "27778eea9aa52df9",
-              "bytes": {"pairs_build": 277848064, "k_closest_mixed": 254221312, "k_resistance_apply": 497347328}},
+    "large": {"sources": "343a5896a6f8ab2a",
+              "bytes": {"pairs_build": 277604608, "k_closest_mixed": 262335744, "k_resistance_apply": 498268672}},
 }
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")
