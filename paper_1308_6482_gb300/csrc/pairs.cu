@@ -742,13 +742,27 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
         }
     }
     if (need > cap) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int b = off[i], m = off[i + 1] - b;
+    // warp-uniform loop bound: every lane of a warp takes part in the
+    // reduction of its largest partner count
+    const int n_up = (n + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += gridDim.x * blockDim.x) {
+        const bool live = i < n;
+        const int b = live ? off[i] : 0, m = live ? off[i + 1] - b : 0;
+        // the unrolled slot loads and pair stores stop at the warp's largest
+        // count (mostly 4..8 of the 16), so the loads and stores beyond it
+        // are skipped, not issued with every lane predicated off
+        const int mw = __reduce_max_sync(0xffffffffu, m < KSLOT ? m : KSLOT);
+        if (!live) continue;
         if (m <= KSLOT) {
             // sort in registers: compare-exchange passes (m is small, mostly 0..4)
             int v[KSLOT];
 #pragma unroll
-            for (int q = 0; q < KSLOT; ++q) v[q] = q < m ? slots[(size_t)q * n + i] : INT32_MAX;
+            for (int q = 0; q < KSLOT; ++q) v[q] = INT32_MAX;
+#pragma unroll
+            for (int q = 0; q < KSLOT; ++q) {
+                if (q >= mw) break;
+                if (q < m) v[q] = slots[(size_t)q * n + i];
+            }
             if (m > 1) {
 #pragma unroll
                 for (int q = 1; q < KSLOT; ++q) {
@@ -762,11 +776,13 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
                 }
             }
 #pragma unroll
-            for (int q = 0; q < KSLOT; ++q)
+            for (int q = 0; q < KSLOT; ++q) {
+                if (q >= mw) break;
                 if (q < m) {
                     pair_i[b + q] = i;
                     pair_j[b + q] = v[q];
                 }
+            }
         } else {
             // the slots, then this particle's overflow entries, then sort in place
             for (int q = 0; q < KSLOT; ++q) {
