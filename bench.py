@@ -112,9 +112,9 @@ def parse():
 
 
 def peaks(lub=None, dev=None):
-    """Roofline denominators: HBM and BF16 from MEASURED_PEAKS.json (driver-
-    measured on this machine), FP32 and FP64 from the library's FMA-chain probe
-    run now on this GPU (lub_probe_peak)."""
+    """Roofline denominators: HBM (a STREAM-style copy) and BF16 (cuBLAS) from
+    MEASURED_PEAKS.json, measured on these GPUs, FP32 and FP64 from the
+    library's FMA-chain probe run now on this GPU (lub_probe_peak)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
     if os.path.exists(p):
