@@ -509,10 +509,12 @@ int lub_random_motion(lub_ctx *ctx, const lub_particles *p, uint64_t seed, int64
 #define LUB_TUNE_CLOSEST_MIXED 0   /* lub_closest_points, LUB_MIXED, FP32 stage */
 #define LUB_TUNE_CLOSEST_REFINE 1  /* lub_closest_points, LUB_MIXED, work list of FP64 solves */
 #define LUB_TUNE_CLOSEST_FP64 2    /* lub_closest_points, LUB_FP64 */
-#define LUB_TUNE_RESISTANCE 3      /* lub_resistance */
+#define LUB_TUNE_RESISTANCE 3      /* lub_resistance, lub_resistance_apply (and so
+                                      lub_correct in LUB_MIXED) */
 #define LUB_TUNE_APPLY 4           /* lub_apply, atomic form */
 #define LUB_TUNE_SWEEP 5           /* lub_pairs_build, the cell sweep (one thread per
-                                      item: only the block counts, the grid follows) */
+                                      particle slot: only the block counts, the grid
+                                      follows) */
 #define LUB_TUNE_COUNT 6
 
 /* Time every candidate shape of the kernels a step with these arguments runs
