@@ -87,7 +87,9 @@ def scale_of(parts, dom, pi, pj):
 
 
 def compare(parts, dom, g, ref, prec, pi, pj, check_particles=True):
-    """Assert parity of a GPU result dict against an oracle reference."""
+    """Assert parity of a GPU result dict against an oracle reference.
+    check_particles: True (every particle), False (none) or an index array
+    (those particles only: the ones whose pairs are all among pi, pj)."""
     tol = TOL[prec]
     cp, pf = ref["cp"], ref["pf"]
     st_ref = pf["status"] & 7
@@ -114,7 +116,8 @@ def compare(parts, dom, g, ref, prec, pi, pj, check_particles=True):
     ltol = (1e-12 if prec == "fp64" else 2e-6) * rmax[pi][:, None]
     act = (pf["FT"] != 0).any(1)
     assert np.all(np.abs(g["lever"] - pf["lever"])[act] <= ltol[act]), "lever"
-    if check_particles:
+    if check_particles is not False:
+        sel = slice(None) if check_particles is True else np.asarray(check_particles)
         n = len(parts["x"])
         BF = np.zeros(n)
         BT = np.zeros(n)
@@ -123,8 +126,9 @@ def compare(parts, dom, g, ref, prec, pi, pj, check_particles=True):
         wj = pj >= 0
         np.add.at(BF, pj[wj], allow_f[wj])
         np.add.at(BT, pj[wj], (allow_t + levj * allow_f)[wj])
-        ef = np.linalg.norm(g["force"] - ref["force"], axis=1)
-        et = np.linalg.norm(g["torque"] - ref["torque"], axis=1)
+        ef = np.linalg.norm(g["force"][sel] - ref["force"][sel], axis=1)
+        et = np.linalg.norm(g["torque"][sel] - ref["torque"][sel], axis=1)
+        BF, BT = BF[sel], BT[sel]
         assert np.all(ef <= BF + 1e-30), ("particle force", float((ef / (BF + 1e-300)).max()))
         assert np.all(et <= BT + 1e-30), ("particle torque", float((et / (BT + 1e-300)).max()))
     return dict(max_rf=float(rf.max(initial=0)), max_rt=float(rt.max(initial=0)))
