@@ -189,49 +189,69 @@ __device__ __forceinline__ double wall_gap(const PView &P, const DView &D, int i
 constexpr int kNoEntry = 0x7fffffff;
 
 // The FP32 stage's finish for a particle pair, in float-float on the FP32
-// pipe (GB300 runs FP64 at 1/64 of the FP32 rate): the gap at the FP32 Newton
+// pipe (GB300 runs FP64 at 1/74 of the FP32 rate): the gap at the FP32 Newton
 // normal n and one Newton step from n with the gradient in float-float.  n
-// is an exact float vector with |n|^2 = 1 + O(1e-7).  With sigma(m) =
-// sqrt(a2 |m|^2 + e (o.m)^2) and M m = a2 m + e (o.m) o, the homogeneous
-// g(m) = m.d - sigma_i(m) - sigma_j(m) has
-//   grad g = R = d - M_i n / sigma_i - M_j n / sigma_j  (y_j - y_i at n),
-//   g(n) = n.R  (Euler: n.M n / sigma = sigma),
-// so the gap at the unit normal is n.R (1 - (|n|^2 - 1)/2 + ...), and the
-// gradient on the sphere is the part of R normal to n, R_t = R - (n.R /
-// |n|^2) n, formed in float-float: it is exactly normal to n, so its FP32
-// components along the FP32 tangents t1, t2 (orthogonal to n to ~1e-7 only)
-// give the tangential gradient to ~1e-14 |d|.  The tangent Hessian and the
-// 2x2 solve run in FP32; their relative error e makes the step contract the
-// error by e as well, so from the FP32 normal's ~1e-7 rad one step lands
-// near 1e-13 rad.  Out: n64 the unit refined normal, h the gap.  Returns the
-// step length (radians), or infinity when the refined normal does not point
-// from i towards j.
+// is an exact float vector with |n|^2 = 1 + eps, eps of order 1e-7.  With
+// sigma(m) = sqrt(a2 |m|^2 + e (o.m)^2) and M m = a2 m + e (o.m) o, the
+// homogeneous g(m) = m.d - sigma_i(m) - sigma_j(m) has
+//   grad g = R = R' - al n,  R' = d - b_i o_i - b_j o_j  (y_j - y_i at n),
+//   b = e (o.n) / sigma,  al = a2_i / sigma_i + a2_j / sigma_j,
+//   g(n) = n.R = n.R' - al (1 + eps)  (Euler: n.M n / sigma = sigma),
+// so the gap at the unit normal is g(n) (1 - eps/2 + ...), and the gradient
+// on the sphere is the part of R normal to n, which is that of R' (al n
+// lies along n): R_t = R' - (n.R' / |n|^2) n.  R' and n.R' are formed in
+// float-float by compensated sums (the products of the high parts exact,
+// every rounding error gathered in one FP32 term); R_t, exactly normal to n
+// and small, is rounded to FP32 once formed, so its components along the
+// FP32 tangents t1, t2 (orthogonal to n to ~1e-7 only) give the tangential
+// gradient to ~1e-14 |d|.  The tangent Hessian and the 2x2 solve run in
+// FP32; their relative error e makes the step contract the error by e as
+// well, so from the FP32 normal's ~1e-7 rad one step lands near 1e-13 rad.
+// The stepped normal m = n + s is normalised by 1 - (|m|^2 - 1)/2, |m|^2 - 1
+// of order 1e-7 (the next term is below 1e-14).  Out: nf the unit refined
+// normal, hf the gap (float-float).  Returns the step length (radians), or
+// infinity when the refined normal does not point from i towards j.
 __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], const ff oj[3], float api, float cpi,
-                                               float apj, float cpj, const V3<float> n, V3<double> &n64, double &h)
+                                               float apj, float cpj, const V3<float> n, ff nf[3], ff &hf)
 {
     const ff a2i = two_prod(api, api), ei = ff_sub(two_prod(cpi, cpi), a2i);
     const ff a2j = two_prod(apj, apj), ej = ff_sub(two_prod(cpj, cpj), a2j);
     const float nv[3] = {n.x, n.y, n.z};
     const ff nn = ff_dot3_exact(nv, nv);
-    const ff ci = ff_dot3f(oi, nv), cj = ff_dot3f(oj, nv);
-    const ff ri = ff_rsqrt(ff_add(ff_mul(a2i, nn), ff_mul(ei, ff_mul(ci, ci))));  // 1 / sigma_i
-    const ff rj = ff_rsqrt(ff_add(ff_mul(a2j, nn), ff_mul(ej, ff_mul(cj, cj))));
-    const ff al = ff_add(ff_mul(a2i, ri), ff_mul(a2j, rj));  // a2_i / sigma_i + a2_j / sigma_j
+    const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);  // |n|^2 - 1 (nn.hi - 1 is exact)
+    const ff ci = ff_dot3f_c(oi, nv), cj = ff_dot3f_c(oj, nv);
+    // sigma^2 = a2 + e c^2 + a2 eps
+    ff si2 = ff_add(a2i, ff_mul(ei, ff_mul(ci, ci))), sj2 = ff_add(a2j, ff_mul(ej, ff_mul(cj, cj)));
+    si2 = fast_two_sum(si2.hi, __fmaf_rn(a2i.hi, eps, si2.lo));
+    sj2 = fast_two_sum(sj2.hi, __fmaf_rn(a2j.hi, eps, sj2.lo));
+    const ff ri = ff_rsqrt(si2), rj = ff_rsqrt(sj2);  // 1 / sigma
+    const ff al = ff_add(ff_mul(a2i, ri), ff_mul(a2j, rj));
     const ff bi = ff_mul(ff_mul(ei, ci), ri), bj = ff_mul(ff_mul(ej, cj), rj);
-    ff R[3];
+    ff Rp[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        R[a] = ff_sub(ff_sub(ff_sub(d[a], ff_mulf(al, nv[a])), ff_mul(bi, oi[a])), ff_mul(bj, oj[a]));
-    const ff nR = ff_dot3f(R, nv);
-    const float eps = __fadd_rn(__fsub_rn(nn.hi, 1.0f), nn.lo);  // |n|^2 - 1
-    h = ff_to_double(ff_sub(nR, ff_make(__fmul_rn(nR.hi, __fmul_rn(0.5f, eps)))));
-    // n.R / |n|^2 to ~eps^2 relative; R_t in float-float
-    const ff lam = ff_sub(nR, ff_make(__fmul_rn(nR.hi, eps)));
+    for (int a = 0; a < 3; ++a) {
+        // d - b_i o_i - b_j o_j: the high products exact, the rest gathered in e
+        const ff p = two_prod(bi.hi, oi[a].hi), q = two_prod(bj.hi, oj[a].hi);
+        const ff t = two_sum(d[a].hi, -p.hi);
+        const ff u = two_sum(t.hi, -q.hi);
+        float e = __fadd_rn(__fadd_rn(d[a].lo, t.lo), __fsub_rn(u.lo, __fadd_rn(p.lo, q.lo)));
+        e = __fsub_rn(e, __fmaf_rn(bi.hi, oi[a].lo, __fmul_rn(bi.lo, oi[a].hi)));
+        e = __fsub_rn(e, __fmaf_rn(bj.hi, oj[a].lo, __fmul_rn(bj.lo, oj[a].hi)));
+        Rp[a] = fast_two_sum(u.hi, e);
+    }
+    const ff nRp = ff_dot3f_c(Rp, nv);
+    // g(n) = n.R' - al - al eps (n.R'.hi - al.hi cancels exactly)
+    const ff tg = two_sum(nRp.hi, -al.hi);
+    const ff g = fast_two_sum(tg.hi, __fsub_rn(__fadd_rn(tg.lo, __fsub_rn(nRp.lo, al.lo)), __fmul_rn(al.hi, eps)));
+    hf = fast_two_sum(g.hi, __fmaf_rn(__fmul_rn(-0.5f, eps), g.hi, g.lo));
+    // n.R' / |n|^2 to ~eps^2 relative; R_t = R' - that n, rounded to FP32
+    // once formed (R'.hi - p.hi is exact or its rounding is that of R_t)
+    const ff lam = fast_two_sum(nRp.hi, __fmaf_rn(-eps, nRp.hi, nRp.lo));
     float Rt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const ff r = ff_sub(R[a], ff_mulf(lam, nv[a]));
-        Rt[a] = __fadd_rn(r.hi, r.lo);
+        const ff p = two_prod(lam.hi, nv[a]);
+        Rt[a] = __fadd_rn(__fsub_rn(Rp[a].hi, p.hi), __fsub_rn(__fsub_rn(Rp[a].lo, p.lo), __fmul_rn(lam.lo, nv[a])));
     }
     const V3<float> t1 = perp_unit(n), t2 = cross(n, t1);
     const float G1 = t1.x * Rt[0] + t1.y * Rt[1] + t1.z * Rt[2];
@@ -239,11 +259,11 @@ __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], co
     // P = -Hess_t g in FP32 (as in newton_sphere)
     const V3<float> ofi = mk<float>(oi[0].hi, oi[1].hi, oi[2].hi), ofj = mk<float>(oj[0].hi, oj[1].hi, oj[2].hi);
     const float u1i = dot(ofi, t1), u2i = dot(ofi, t2), u1j = dot(ofj, t1), u2j = dot(ofj, t2);
-    const float rif = ri.hi, rjf = rj.hi, g = nR.hi;
+    const float rif = ri.hi, rjf = rj.hi, gf = g.hi;
     const float Ai = a2i.hi * rif, Aj = a2j.hi * rjf;
     const float Ei = ei.hi * rif * rif, Ej = ej.hi * rjf * rjf;
-    const float P11 = Ai * (1.f + Ei * u1i * u1i) + Aj * (1.f + Ej * u1j * u1j) + g;
-    const float P22 = Ai * (1.f + Ei * u2i * u2i) + Aj * (1.f + Ej * u2j * u2j) + g;
+    const float P11 = Ai * (1.f + Ei * u1i * u1i) + Aj * (1.f + Ej * u1j * u1j) + gf;
+    const float P22 = Ai * (1.f + Ei * u2i * u2i) + Aj * (1.f + Ej * u2j * u2j) + gf;
     const float P12 = Ai * Ei * u1i * u2i + Aj * Ej * u1j * u2j;
     const float det = P11 * P22 - P12 * P12;
     float s1, s2;
@@ -256,13 +276,21 @@ __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], co
         s1 = G1 * sc;
         s2 = G2 * sc;
     }
-    // n + s1 t1 + s2 t2 in float-float (the step is of order 1e-7), normalised
+    // m = n + s1 t1 + s2 t2 in float-float (the step is of order 1e-7), then
+    // m (1 - em/2) with em = |m|^2 - 1 = eps + 2 n.s + |s|^2
     const float tv1[3] = {t1.x, t1.y, t1.z}, tv2[3] = {t2.x, t2.y, t2.z};
+    float sv[3];
     ff m[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) m[a] = two_sum(nv[a], __fmaf_rn(s1, tv1[a], __fmul_rn(s2, tv2[a])));
-    const ff im = ff_rsqrt(ff_dot3(m, m));
-    n64 = mk<double>(ff_to_double(ff_mul(m[0], im)), ff_to_double(ff_mul(m[1], im)), ff_to_double(ff_mul(m[2], im)));
+    for (int a = 0; a < 3; ++a) {
+        sv[a] = __fmaf_rn(s1, tv1[a], __fmul_rn(s2, tv2[a]));
+        m[a] = two_sum(nv[a], sv[a]);
+    }
+    const float ns = nv[0] * sv[0] + nv[1] * sv[1] + nv[2] * sv[2];
+    const float ss = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+    const float hem = -0.5f * (eps + (2.0f * ns + ss));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nf[a] = fast_two_sum(m[a].hi, __fmaf_rn(hem, m[a].hi, m[a].lo));
     const float step = sqrtf(s1 * s1 + s2 * s2);
     const float nd = m[0].hi * d[0].hi + m[1].hi * d[1].hi + m[2].hi * d[2].hi;
     return (nd > 0.f && isfinite(step)) ? step : INFINITY;
@@ -270,25 +298,31 @@ __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], co
 
 // LUB_MIXED, FP32 stage of pair k = (i, j): FP32 Newton, then the
 // float-float gap and Newton step (spheres: the float-float line of centres).
-// Returns the FP64 work-list entry -1-k (a full FP64 solve from the line of
-// centres, for a pair whose FP32 Newton did not converge) or kNoEntry.
+// The normal and gap in double (n64, h) and in float-float (nf, hf: what the
+// fused pass hands to the force kernel).  Returns the FP64 work-list entry
+// -1-k (a full FP64 solve from the line of centres, for a pair whose FP32
+// Newton did not converge) or kNoEntry.
 template <bool ENS>
 __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0, const Ens &E,
                                                  const float2 *__restrict__ pff, int i, int j, int k,
                                                  const double *__restrict__ nin, size_t C, int warm, int maxit,
-                                                 float tol32, V3<double> &n64, double &h, int &st, int &nit)
+                                                 float tol32, V3<double> &n64, double &h, ff nf[3], ff &hf,
+                                                 int &st, int &nit)
 {
     int entry = kNoEntry;
     st = 0;
     nit = 0;
     n64 = mk<double>(0, 0, 0);
     h = 0.0;
+    nf[0] = nf[1] = nf[2] = hf = ff_make(0.0f);
     bool alien;
     const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
     if (alien || pair_bad(P, D, i, j)) {
         st = LUB_ST_DEGENERATE;
     } else if (j < 0) {
         h = wall_gap(P, D, i, -1 - j, n64);
+        nf[2] = ff_make((float)n64.z);  // +-1
+        hf = ff_split_bits(h);
     } else {
         const float4 ri0 = rec_ld(pff, i, 0), ri1 = rec_ld(pff, i, 1), rj0 = rec_ld(pff, j, 0), rj1 = rec_ld(pff, j, 1);
         ff dff[3];
@@ -301,9 +335,11 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
         } else if (rpi == rqi && rpj == rqj) {
             // two spheres: n = d/|d|, h = |d| - R_i - R_j, in float-float
             const ff rs = ff_rsqrt(dd);
-            n64 = mk<double>(ff_to_double(ff_mul(dff[0], rs)), ff_to_double(ff_mul(dff[1], rs)),
-                             ff_to_double(ff_mul(dff[2], rs)));
-            h = ff_to_double(ff_sub(ff_sub(ff_mul(dd, rs), ff_make(rpi)), ff_make(rpj)));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nf[a] = ff_mul(dff[a], rs);
+            hf = ff_sub(ff_sub(ff_mul(dd, rs), ff_make(rpi)), ff_make(rpj));
+            n64 = mk<double>(ff_to_double(nf[0]), ff_to_double(nf[1]), ff_to_double(nf[2]));
+            h = ff_to_double(hf);
         } else {
             ff oi[3], oj[3];
             ff_axis_rec(rec_ld(pff, i, 2), rec_ld(pff, i, 3), oi);
@@ -320,7 +356,9 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
             const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
             nit = o.iters;
-            const float step = polish_gap_ff(dff, oi, oj, rqi, rpi, rqj, rpj, n, n64, h);
+            const float step = polish_gap_ff(dff, oi, oj, rqi, rpi, rqj, rpj, n, nf, hf);
+            n64 = mk<double>(ff_to_double(nf[0]), ff_to_double(nf[1]), ff_to_double(nf[2]));
+            h = ff_to_double(hf);
             if (!o.converged || !(step < 1e-5f) || !isfinite(h)) {
                 entry = -1 - k;
                 st |= LUB_ST_FP64;  // on the work list (solved again in FP64 next)
@@ -405,6 +443,23 @@ __device__ __forceinline__ void closest_fp64_one(const PView &P, const DView &D0
         }
     }
     if (!(st & LUB_ST_DEGENERATE) && h <= 0.0) st |= LUB_ST_OVERLAP;
+}
+
+// The fused pass's hand-over of pair k's unit normal and gap to the force
+// kernel in float-float (no conversion from double there): nh[k] = (n_x,
+// n_y), nh[C + k] = (n_z, h), each value as (hi, lo).
+__device__ __forceinline__ void store_nh(float4 *__restrict__ nh, size_t C, int k, const ff nf[3], ff hf)
+{
+    nh[k] = make_float4(nf[0].hi, nf[0].lo, nf[1].hi, nf[1].lo);
+    nh[C + k] = make_float4(nf[2].hi, nf[2].lo, hf.hi, hf.lo);
+}
+
+// the same from a double normal and gap (the FP64 solves of the work list),
+// split with integer operations
+__device__ __forceinline__ void store_nh(float4 *__restrict__ nh, size_t C, int k, const V3<double> &n64, double h)
+{
+    const ff nf[3] = {ff_split_bits(n64.x), ff_split_bits(n64.y), ff_split_bits(n64.z)};
+    store_nh(nh, C, k, nf, ff_split_bits(h));
 }
 
 __device__ __forceinline__ void store_pair(double *__restrict__ nout, double *__restrict__ gap,
@@ -500,7 +555,7 @@ __global__ void __launch_bounds__(128, 8) k_closest_mixed(PView P, const __grid_
                                                        uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                        int maxit, float tol32, int warm,
                                                        int32_t *__restrict__ wl_count, int32_t *__restrict__ wl,
-                                                       const float2 *__restrict__ pff)
+                                                       const float2 *__restrict__ pff, float4 *__restrict__ nh)
 {
     pdl_wait();
     pdl_trigger();
@@ -514,9 +569,12 @@ __global__ void __launch_bounds__(128, 8) k_closest_mixed(PView P, const __grid_
             const int i = __ldg(pi + k), j = __ldg(pj + k);
             V3<double> n64;
             double h;
+            ff nf[3], hf;
             int st, nit;
-            entry = closest_mixed_one<ENS>(P, D0, E, pff, i, j, k, nout, C, warm, maxit, tol32, n64, h, st, nit);
+            entry = closest_mixed_one<ENS>(P, D0, E, pff, i, j, k, nout, C, warm, maxit, tol32, n64, h, nf, hf, st,
+                                           nit);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+            if (nh) store_nh(nh, C, k, nf, hf);
         }
         worklist_append(entry, wl_count, wl, cap);
     }
@@ -529,7 +587,7 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
                                                         double *__restrict__ nout, double *__restrict__ gap,
                                                         uint8_t *__restrict__ status, uint8_t *__restrict__ iters,
                                                         int maxit, const int32_t *__restrict__ wl_count,
-                                                        const int32_t *__restrict__ wl)
+                                                        const int32_t *__restrict__ wl, float4 *__restrict__ nh)
 {
     pdl_wait();
     pdl_trigger();
@@ -542,6 +600,7 @@ __global__ void __launch_bounds__(32) k_closest_refine(PView P, const __grid_con
         int st, nit;
         refine_one<ENS>(P, D0, E, pi[k], pj[k], maxit, n64, h, st, nit);
         store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+        if (nh) store_nh(nh, C, k, n64, h);
     }
 }
 
@@ -577,7 +636,8 @@ template <bool ENS>
 __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_mixed_learned(
     PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
     const int32_t *__restrict__ d_count, int32_t cap, double *__restrict__ nout, double *__restrict__ gap,
-    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, float tol32, int32_t *__restrict__ wl_count, int32_t *__restrict__ wl, const float2 *__restrict__ pff, MlpDevice M)
+    uint8_t *__restrict__ status, uint8_t *__restrict__ iters, int maxit, float tol32, int32_t *__restrict__ wl_count,
+    int32_t *__restrict__ wl, const float2 *__restrict__ pff, float4 *__restrict__ nh, MlpDevice M)
 {
     pdl_wait();
     pdl_trigger();
@@ -598,10 +658,12 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) k_closest_mixed_learned(
         if (k < count) {
             V3<double> n64;
             double h;
+            ff nf[3], hf;
             int st, nit;
             entry = closest_mixed_one<ENS>(P, D0, E, pff, __ldg(pi + k), __ldg(pj + k), k, nout, C, 1, maxit, tol32,
-                                           n64, h, st, nit);
+                                           n64, h, nf, hf, st, nit);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+            if (nh) store_nh(nh, C, k, nf, hf);
         }
         worklist_append(entry, wl_count, wl, cap);
     }
@@ -646,7 +708,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_closest_refine_learned(
     PView P, const __grid_constant__ DView D0, Ens E, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
     int32_t cap, double *__restrict__ nout, double *__restrict__ gap, uint8_t *__restrict__ status,
     uint8_t *__restrict__ iters, int maxit, const int32_t *__restrict__ wl_count, const int32_t *__restrict__ wl,
-    MlpDevice M)
+    float4 *__restrict__ nh, MlpDevice M)
 {
     pdl_wait();
     pdl_trigger();
@@ -674,6 +736,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_closest_refine_learned(
             int st, nit;
             refine_one<ENS>(P, D0, E, pi[k], pj[k], maxit, n64, h, st, nit, &w0);
             store_pair(nout, gap, status, iters, C, k, n64, h, st, nit);
+            if (nh) store_nh(nh, C, k, n64, h);
         }
     }
 }
@@ -799,36 +862,37 @@ int launch_particles_ff(lub_ctx *ctx, const PView &P, float2 *out, cudaStream_t 
 namespace {
 
 // The work list of the mixed mode in the context scratch: counters [entries,
-// unused, queue 0, queue 1] and cap entries; with gap_in/status_in, also a
-// gap and a status array for callers that pass none (the fused pass needs
-// them between its kernels); with P, the per-call particle table (pff:
-// float-float positions and axes, 48 bytes per particle).
+// unused, queue 0, queue 1] and cap entries; with nh and status_in (the
+// fused pass), also the hand-over of normals and gaps in float-float (32
+// bytes a pair, store_nh) and a status array for callers that pass none;
+// with P, the per-call particle table (pff: 80 bytes per particle).
 int work_list(lub_ctx *ctx, int32_t cap, cudaStream_t st, int32_t **wl_count, int32_t **wl,
-              double **gap_in = nullptr, uint8_t **status_in = nullptr, const PView *P = nullptr,
+              float4 **nh = nullptr, uint8_t **status_in = nullptr, const PView *P = nullptr,
               float2 **pff = nullptr, float *zf = nullptr, float *zt = nullptr)
 {
-    const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_gap = ((8 * (size_t)cap + 255) / 256) * 256,
+    const size_t b_wl = ((4 * (size_t)cap + 255) / 256) * 256, b_nh = nh ? ((32 * (size_t)cap + 255) / 256) * 256 : 0,
                  b_st = (((size_t)cap + 255) / 256) * 256, b_pos = P ? particles_ff_bytes(P->n) : 0;
-    int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_gap + b_st + b_pos);
+    int rc = lub_ensure_scratch(ctx, 256 + b_wl + b_nh + b_st + b_pos);
     if (rc) return rc;
     char *base = (char *)ctx->scratch;
     *wl_count = (int32_t *)base;
     *wl = (int32_t *)(base + 256);
-    if (gap_in && !*gap_in) *gap_in = (double *)(base + 256 + b_wl);
-    if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_gap);
+    if (nh) *nh = (float4 *)(base + 256 + b_wl);
+    if (status_in && !*status_in) *status_in = (uint8_t *)(base + 256 + b_wl + b_nh);
     if (!P) return zero_async(ctx, ctx->num_sms, *wl_count, 16, st);
     // the particle table's kernel also clears the counters (and the sums zf, zt)
-    *pff = (float2 *)(base + 256 + b_wl + b_gap + b_st);
+    *pff = (float2 *)(base + 256 + b_wl + b_nh + b_st);
     return launch_particles_ff(ctx, *P, *pff, st, *wl_count, zf, zt);
 }
 
 // What lub_correct hands from the closest-point kernels of the mixed mode to
-// the force pass: the gap and status arrays (the caller's, or the context
-// scratch's where it passes none) and the per-call particle records.
+// the force pass: the status array (the caller's, or the context scratch's
+// where it passes none), the per-call particle records and the normals and
+// gaps in float-float.
 struct ClosestKeep {
-    double *gap;
     uint8_t *status;
     const float2 *pff;
+    const float4 *nh;
 };
 
 template <bool ENS>
@@ -849,21 +913,22 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
     if (prm.precision == LUB_MIXED) {
         int32_t *wl_count, *wl;
         float2 *pff = nullptr;
-        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, keep ? &gap : nullptr, keep ? &status : nullptr, &P, &pff,
+        float4 *nh = nullptr;
+        if ((rc = work_list(ctx, cap, st, &wl_count, &wl, keep ? &nh : nullptr, keep ? &status : nullptr, &P, &pff,
                             zero_force, zero_torque)))
             return rc;
-        if (keep) *keep = ClosestKeep{gap, status, pff};
+        if (keep) *keep = ClosestKeep{status, pff, nh};
         lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         if (fused_mlp) {
             if ((rc = learned_smem(ctx, k_closest_mixed_learned<ENS>, 16 << ENS))) return rc;
             (void)launch_pdl(k_closest_mixed_learned<ENS>, learned_grid, 32 * INF_WARPS, sizeof(InfSmem), st, P, D, E,
                              pi, pj, d_count, cap, n, gap, status, iters, prm.max_newton, (float)prm.newton_tol,
-                             wl_count, wl, (const float2 *)pff, *(const MlpDevice *)ctx->mlp);
+                             wl_count, wl, (const float2 *)pff, nh, *(const MlpDevice *)ctx->mlp);
         } else {
             const Shape2 sh = tuned_shape(ctx, LUB_TUNE_CLOSEST_MIXED, cap);
             (void)launch_pdl(k_closest_mixed<ENS>, sh.grid, sh.block, 0, st, P, D, E, pi, pj, d_count, cap, n, gap,
                              status, iters, prm.max_newton, (float)prm.newton_tol, warm, wl_count, wl,
-                             (const float2 *)pff);
+                             (const float2 *)pff, nh);
         }
         lub_trace_mark(ctx, LUB_TRACE_CLOSEST, st);
         if (net_wl) {
@@ -871,12 +936,12 @@ int launch_closest_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
             if ((rc = learned_smem(ctx, k_closest_refine_learned<ENS>, 256 << ENS))) return rc;
             (void)launch_pdl(k_closest_refine_learned<ENS>, ctx->num_sms, 32 * INF_WARPS, sizeof(InfSmem), st, P, D,
                              E, pi, pj, cap, n, gap, status, iters, prm.max_newton, (const int32_t *)wl_count,
-                             (const int32_t *)wl, *(const MlpDevice *)ctx->mlp);
+                             (const int32_t *)wl, nh, *(const MlpDevice *)ctx->mlp);
         } else {
             // small blocks so the (short) work list spreads over every SM
             const Shape2 sr = tuned_shape(ctx, LUB_TUNE_CLOSEST_REFINE, cap);
             (void)launch_pdl(k_closest_refine<ENS>, sr.grid, sr.block, 0, st, P, D, E, pi, pj, cap, n, gap, status,
-                             iters, prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl);
+                             iters, prm.max_newton, (const int32_t *)wl_count, (const int32_t *)wl, nh);
         }
     } else if (fused_mlp) {
         if ((rc = learned_smem(ctx, k_closest_fp64_learned<ENS>, 64 << ENS))) return rc;
@@ -915,8 +980,8 @@ int launch_correct_t(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E,
                                         accumulate ? nullptr : (float *)force,
                                         accumulate ? nullptr : (float *)torque)))
             return rc;
-        return launch_resistance_apply(ctx, P, D, E, prm, pi, pj, d_count, cap, n, keep.gap, keep.status, FT, lever,
-                                       force, torque, 1, st, keep.pff);
+        return launch_resistance_apply(ctx, P, D, E, prm, pi, pj, d_count, cap, n, gap, keep.status, FT, lever,
+                                       force, torque, 1, st, keep.pff, keep.nh);
     }
     int warm = 0;
     if ((rc = start_normals(ctx, P, D, E, prm, pi, pj, d_count, cap, n, st, &warm))) return rc;

@@ -373,11 +373,14 @@ int launch_correct(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, c
                    uint8_t *status, uint8_t *iters, void *FT, void *lever, void *force, void *torque, int accumulate,
                    cudaStream_t st);
 // pff: the mixed mode's per-call particle records when the caller has built
-// them on this stream (lub_correct), else null (built here)
+// them on this stream (lub_correct), else null (built here); nh: the
+// closest-point kernels' normals and gaps in float-float (lub_correct, mixed
+// mode: n and gap are then not read), else null
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
-                            void *torque, int accumulate, cudaStream_t st, const float2 *pff = nullptr);
+                            void *torque, int accumulate, cudaStream_t st, const float2 *pff = nullptr,
+                            const float4 *nh = nullptr);
 int launch_links(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const int32_t *pi, const int32_t *pj,
                  const int32_t *d_count, int32_t cap, double mu, double qbar, double *force, double *torque,
                  int32_t *nlinks, cudaStream_t st);

@@ -134,9 +134,10 @@ __device__ __forceinline__ Surf<T> surface_at(const Shape<T> &s, const V3<T> &rh
 // smaller gap; d_x = he - Delta_x for the three cut-offs, which cancels near
 // each cut-off; in_x = he < Delta_x; fr = h_c - h where the contact force
 // acts (h <= h_c with h_c > 0), else 0; le0 = h <= 0.  T = double: double
-// arithmetic.  T = float: the double gap is split into float-float with
-// integer operations (no FP64-pipe work) and the rest runs in float-float,
-// so d_x keeps its relative accuracy near the cut-off.
+// arithmetic.  T = float: from a float-float gap (the fused pass hands it
+// over as such; a double gap is split with integer operations, no FP64-pipe
+// work), the differences in float-float, so d_x keeps its relative accuracy
+// near the cut-off.
 template <typename T>
 struct CutTerms {
     T he, dn, dt, dr, fr;
@@ -159,9 +160,8 @@ __device__ __forceinline__ CutTerms<double> cut_terms(const RParams &R, double h
     return c;
 }
 
-__device__ __forceinline__ CutTerms<float> cut_terms(const RParams &R, double h, float)
+__device__ __forceinline__ CutTerms<float> cut_terms_ff(const RParams &R, ff he)
 {
-    ff he = ff_split_bits(h);
     CutTerms<float> c;
     c.le0 = he.hi <= 0.f;
     const float hi = he.hi;
@@ -195,64 +195,109 @@ __device__ __forceinline__ void m_rot(T c, T s, T a0, T a1, T a2, T a3, T m[4])
     m[3] = a0 * s2 * s + a1 * c * s2 + a2 * c2 * s + a3 * c2 * c;
 }
 
-// Force and torque on i (lab frame, torque about y*_i) and the lever arms of
-// one pair from its normal n64 (direction of h, outward from i) and gap h:
-// out = (F_i, T_i, y*_i - r_i, y*_j - r_j).  st carries the pair's status
-// bits in and gains OVERLAP when h <= 0 without a contact model; pairs with
-// NOCONV or DEGENERATE (or such an overlap) give zeros.  T = float (mixed
-// mode) needs the per-call particle records pff (rec_ld): the frames,
-// curvatures and K~ run in FP32 with the axes rounded from it, the normal
-// relative velocity u3 in float-float (normal_velocity_ff), and no step uses
-// the FP64 pipe.  T = double ignores pff.  The local relative velocities u
-// come first and each group of K~ elements is applied to them as soon as it
-// is formed, which keeps few values live at a time.
+// The normal (x3), the shapes and the velocities of a pair's particles in the
+// arithmetic of T, and (mixed mode) the normal relative surface velocity u3
+// formed in float-float; FP64 mode forms u3 with the rest.
 template <typename T>
-__device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int i, int j, const V3<double> &n64,
-                                           double h, int &st, T out[12], const float2 *__restrict__ pff)
+struct PairKin {
+    V3<T> n, vi, Wi, vj, Wj;
+    Shape<T> si, sj;
+    T u3;
+};
+
+template <typename T>
+__device__ __forceinline__ void pair_force_body(const RParams &R, int j, const CutTerms<T> &cut, const PairKin<T> &K,
+                                                T out[12]);
+
+// Force and torque on i (lab frame, torque about y*_i) and the lever arms of
+// one pair, mixed mode, from its unit normal nf (direction of h, outward
+// from i) and gap hf in float-float: out = (F_i, T_i, y*_i - r_i, y*_j -
+// r_j).  st carries the pair's status bits in and gains OVERLAP when h <= 0
+// without a contact model; pairs with NOCONV or DEGENERATE (or such an
+// overlap) give zeros.  Needs the per-call particle records pff (rec_ld):
+// the frames, curvatures and K~ run in FP32 with the axes rounded from it,
+// the normal relative velocity u3 in float-float (normal_velocity_ff), and
+// no step uses the FP64 pipe.  The local relative velocities u come first
+// and each group of K~ elements is applied to them as soon as it is formed,
+// which keeps few values live at a time.
+__device__ __forceinline__ void pair_force_ff(const RParams &R, int i, int j, const ff nf[3], ff hf, int &st,
+                                              float out[12], const float2 *__restrict__ pff)
 {
-    constexpr bool MIXED = sizeof(T) == 4;
 #pragma unroll
-    for (int a = 0; a < 12; ++a) out[a] = T(0);
+    for (int a = 0; a < 12; ++a) out[a] = 0.f;
     if (st & (LUB_ST_NOCONV | LUB_ST_DEGENERATE)) return;
-    const CutTerms<T> cut = cut_terms(R, h, T(0));
+    const CutTerms<float> cut = cut_terms_ff(R, hf);
     if (!R.contact && cut.le0) {
         st |= LUB_ST_OVERLAP;
         return;
     }
-    // the normal (x3), the shapes and the velocities
-    V3<T> n, vi, Wi, vj = mk<T>(0, 0, 0), Wj = mk<T>(0, 0, 0);
-    Shape<T> si, sj = {};
-    T u3 = T(0);
-    if constexpr (MIXED) {
-        ff nf[3], oi[3], oj[3];
-        nf[0] = ff_split_bits(n64.x);
-        nf[1] = ff_split_bits(n64.y);
-        nf[2] = ff_split_bits(n64.z);
-        n = mk<T>(nf[0].hi, nf[1].hi, nf[2].hi);
-        const float4 a1 = rec_ld(pff, i, 1), a2 = rec_ld(pff, i, 2), a3 = rec_ld(pff, i, 3), a4 = rec_ld(pff, i, 4);
-        ff_axis_rec(a2, a3, oi);
-        si = shape_ff(oi, a1.z, a1.w);
-        vi = mk<T>(a3.z, a3.w, a4.x);
-        Wi = mk<T>(a4.y, a4.z, a4.w);
-        if (j >= 0) {
-            const float4 b1 = rec_ld(pff, j, 1), b2 = rec_ld(pff, j, 2), b3 = rec_ld(pff, j, 3), b4 = rec_ld(pff, j, 4);
-            ff_axis_rec(b2, b3, oj);
-            sj = shape_ff(oj, b1.z, b1.w);
-            vj = mk<T>(b3.z, b3.w, b4.x);
-            Wj = mk<T>(b4.y, b4.z, b4.w);
-        }
-        u3 = normal_velocity_ff(nf, oi, si.rpar, si.rperp, vi, Wi, j, oj, sj.rpar, sj.rperp, vj, Wj);
-    } else {
-        n = n64;
-        si = load_shape<T>(P, i);
-        vi = mk<T>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
-        Wi = mk<T>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
-        if (j >= 0) {
-            sj = load_shape<T>(P, j);
-            vj = mk<T>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j));
-            Wj = mk<T>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
-        }
+    PairKin<float> K;
+    ff oi[3], oj[3];
+    K.n = mk<float>(nf[0].hi, nf[1].hi, nf[2].hi);
+    const float4 a1 = rec_ld(pff, i, 1), a2 = rec_ld(pff, i, 2), a3 = rec_ld(pff, i, 3), a4 = rec_ld(pff, i, 4);
+    ff_axis_rec(a2, a3, oi);
+    K.si = shape_ff(oi, a1.z, a1.w);
+    K.vi = mk<float>(a3.z, a3.w, a4.x);
+    K.Wi = mk<float>(a4.y, a4.z, a4.w);
+    K.sj = {};
+    K.vj = K.Wj = mk<float>(0.f, 0.f, 0.f);
+    if (j >= 0) {
+        const float4 b1 = rec_ld(pff, j, 1), b2 = rec_ld(pff, j, 2), b3 = rec_ld(pff, j, 3), b4 = rec_ld(pff, j, 4);
+        ff_axis_rec(b2, b3, oj);
+        K.sj = shape_ff(oj, b1.z, b1.w);
+        K.vj = mk<float>(b3.z, b3.w, b4.x);
+        K.Wj = mk<float>(b4.y, b4.z, b4.w);
     }
+    K.u3 = normal_velocity_ff(nf, oi, K.si.rpar, K.si.rperp, K.vi, K.Wi, j, oj, K.sj.rpar, K.sj.rperp, K.vj, K.Wj);
+    pair_force_body<float>(R, j, cut, K, out);
+}
+
+// The same from a double normal n64 and gap h: T = float splits them into
+// float-float (integer operations) for pair_force_ff; T = double is the FP64
+// mode (pff unused).
+template <typename T>
+__device__ __forceinline__ void pair_force(const PView &P, const RParams &R, int i, int j, const V3<double> &n64,
+                                           double h, int &st, T out[12], const float2 *__restrict__ pff)
+{
+    if constexpr (sizeof(T) == 4) {
+        const ff nf[3] = {ff_split_bits(n64.x), ff_split_bits(n64.y), ff_split_bits(n64.z)};
+        pair_force_ff(R, i, j, nf, ff_split_bits(h), st, out, pff);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 12; ++a) out[a] = 0.0;
+        if (st & (LUB_ST_NOCONV | LUB_ST_DEGENERATE)) return;
+        const CutTerms<double> cut = cut_terms(R, h, 0.0);
+        if (!R.contact && cut.le0) {
+            st |= LUB_ST_OVERLAP;
+            return;
+        }
+        PairKin<double> K;
+        K.n = n64;
+        K.si = load_shape<double>(P, i);
+        K.vi = mk<double>(__ldg(P.vx + i), __ldg(P.vy + i), __ldg(P.vz + i));
+        K.Wi = mk<double>(__ldg(P.wx + i), __ldg(P.wy + i), __ldg(P.wz + i));
+        K.sj = {};
+        K.vj = K.Wj = mk<double>(0.0, 0.0, 0.0);
+        if (j >= 0) {
+            K.sj = load_shape<double>(P, j);
+            K.vj = mk<double>(__ldg(P.vx + j), __ldg(P.vy + j), __ldg(P.vz + j));
+            K.Wj = mk<double>(__ldg(P.wx + j), __ldg(P.wy + j), __ldg(P.wz + j));
+        }
+        K.u3 = 0.0;
+        pair_force_body<double>(R, j, cut, K, out);
+    }
+}
+
+// the geometry at both contact points, K~ and the lab-frame force and torque
+// (out must hold zeros on entry)
+template <typename T>
+__device__ __forceinline__ void pair_force_body(const RParams &R, int j, const CutTerms<T> &cut, const PairKin<T> &K,
+                                                T out[12])
+{
+    constexpr bool MIXED = sizeof(T) == 4;
+    const V3<T> n = K.n, vi = K.vi, Wi = K.Wi, vj = K.vj, Wj = K.Wj;
+    const Shape<T> &si = K.si, &sj = K.sj;
+    T u3 = K.u3;
     // geometry at y*_i, the local frame x1, x2, x3 = n, and the relative velocities
     const V3<T> rho_i = support_offset(si, n);
     const Surf<T> A = surface_at(si, rho_i, n);

@@ -386,6 +386,22 @@ __device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__
     }
 }
 
+// One warp's shared memory in the sweep (the block holds blockDim.x / 32 of
+// them, dynamic): the groups' staging (rows padded by one entry, so that the
+// groups' broadcast reads fall in different banks), each lane's particle,
+// and the warp's queue of candidates for the full test (a ring of 64).
+struct SweepWarp {
+    float4 cand[NG * (SC + 1)];
+    float4 own1[32];  // each lane's symmetry axis and e
+    float4 qd[64];    // queued: d (x, y, z) and Rmax of the candidate
+    float2 ownw[32];  // each lane's Rmax and its group's margin
+    int cand_t[NG * (SC + 1)];
+    int own_i[32];    // each lane's particle index
+    int qt[64];       // queued: candidate slot t
+    uint8_t qo[64];   // queued: lane of the particle
+};
+static_assert(sizeof(SweepWarp) % 16 == 0, "warp blocks stay 16-byte aligned");
+
 // One thread per slot s (cell order); the thread also tests its particle's
 // walls.  cnt: [0, N) pair counts per particle (of the smaller index of each
 // pair), [N, 2N) wall-pair counts; slots [KSLOT][N] (slot-major, so that the
@@ -416,21 +432,6 @@ __device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__
 //
 // Candidates inside the FP32 margin (about one in 10^4) are decided on the
 // spot by the FP64 test, in the lane that holds them.
-// One warp's shared memory in the sweep (the block holds blockDim.x / 32 of
-// them, dynamic): the groups' staging (rows padded by one entry, so that the
-// groups' broadcast reads fall in different banks), each lane's particle,
-// and the warp's queue of candidates for the full test (a ring of 64).
-struct SweepWarp {
-    float4 cand[NG * (SC + 1)];
-    float4 own1[32];  // each lane's symmetry axis and e
-    float4 qd[64];    // queued: d (x, y, z) and Rmax of the candidate
-    float2 ownw[32];  // each lane's Rmax and its group's margin
-    int cand_t[NG * (SC + 1)];
-    int own_i[32];    // each lane's particle index
-    int qt[64];       // queued: candidate slot t
-    uint8_t qo[64];   // queued: lane of the particle
-};
-static_assert(sizeof(SweepWarp) % 16 == 0, "warp blocks stay 16-byte aligned");
 
 template <bool ENS>
 __device__ __forceinline__ void sweep_groups(const BuildView &V)

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_resistance_appl
                                                           const double *__restrict__ gap,
                                                           uint8_t *__restrict__ status, T *__restrict__ FT,
                                                           T *__restrict__ lever, T *__restrict__ force,
-                                                          T *__restrict__ torque, const float2 *__restrict__ pff)
+                                                          T *__restrict__ torque, const float2 *__restrict__ pff,
+                                                          const float4 *__restrict__ nh)
 {
     pdl_wait();
     pdl_trigger();
@@ -76,14 +77,24 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_resistance_appl
         T ci[6] = {0, 0, 0, 0, 0, 0}, cj[6] = {0, 0, 0, 0, 0, 0};
         if (k < count) {
             st = status[k];
-            const double h = gap[k];
             i = __ldg(pi + k);
             j = __ldg(pj + k);
             bool alien;
             const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
             if (alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i) st |= LUB_ST_DEGENERATE;
-            const V3<double> n = mk<double>(nin[k], nin[C + k], nin[2 * C + k]);
-            pair_force<T>(P, R, i, j, n, h, st, out, pff);
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                if (nh) {  // the fused pass: normal and gap in float-float from the closest-point kernels
+                    const float4 a = nh[k], b = nh[C + k];
+                    const ff nf[3] = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}};
+                    pair_force_ff(R, i, j, nf, ff{b.z, b.w}, st, out, pff);
+                    done = true;
+                }
+            }
+            if (!done) {
+                const V3<double> n = mk<double>(nin[k], nin[C + k], nin[2 * C + k]);
+                pair_force<T>(P, R, i, j, n, gap[k], st, out, pff);
+            }
             if (FT)
 #pragma unroll
                 for (int a = 0; a < 6; ++a) FT[a * C + k] = out[a];
@@ -113,7 +124,7 @@ static int particle_table(lub_ctx *ctx, const PView &P, cudaStream_t st, const f
 int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const Ens &E, const lub_params &prm,
                             const int32_t *pi, const int32_t *pj, const int32_t *d_count, int32_t cap,
                             const double *n, const double *gap, uint8_t *status, void *FT, void *lever, void *force,
-                            void *torque, int accumulate, cudaStream_t st, const float2 *pff)
+                            void *torque, int accumulate, cudaStream_t st, const float2 *pff, const float4 *nh)
 {
     const size_t esz = prm.precision == LUB_MIXED ? sizeof(float) : sizeof(double);
     int rc;
@@ -129,21 +140,24 @@ int launch_resistance_apply(lub_ctx *ctx, const PView &P, const DView &D, const 
         lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance_apply<float, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
-                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
+                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff,
+                             nh);
         else
             (void)launch_pdl(k_resistance_apply<float, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
-                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff);
+                             cap, n, gap, status, (float *)FT, (float *)lever, (float *)force, (float *)torque, pff,
+                             nh);
     } else {
         const float2 *none = nullptr;
+        const float4 *no_nh = nullptr;
         lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
         if (ens)
             (void)launch_pdl(k_resistance_apply<double, true>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
                              cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
-                             none);
+                             none, no_nh);
         else
             (void)launch_pdl(k_resistance_apply<double, false>, sh.grid, sh.block, 0, st, P, D, E, R, pi, pj, d_count,
                              cap, n, gap, status, (double *)FT, (double *)lever, (double *)force, (double *)torque,
-                             none);
+                             none, no_nh);
     }
     lub_trace_mark(ctx, LUB_TRACE_RESISTANCE, st);
     return lub_check_cuda(ctx, cudaGetLastError(), "k_resistance_apply launch");
