@@ -317,23 +317,35 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
     nf[0] = nf[1] = nf[2] = hf = ff_make(0.0f);
     bool alien;
     const DView &D = pair_domain<ENS>(D0, E, i, j, &alien);
-    if (alien || pair_bad(P, D, i, j)) {
+    // the indices first; the shapes from the records (the same floats as P's)
+    bool bad = alien || i < 0 || i >= P.n || j >= P.n || j < -D.n_walls || j == i;
+    float4 ri1 = make_float4(0.f, 0.f, 0.f, 0.f), rj1 = ri1;
+    if (!bad) {
+        ri1 = rec_ld(pff, i, 1);
+        bad = !shape_ok(ri1.z, ri1.w);
+        if (!bad && j >= 0) {
+            rj1 = rec_ld(pff, j, 1);
+            bad = !shape_ok(rj1.z, rj1.w);
+        }
+    }
+    if (bad) {
         st = LUB_ST_DEGENERATE;
     } else if (j < 0) {
         h = wall_gap(P, D, i, -1 - j, n64);
         nf[2] = ff_make((float)n64.z);  // +-1
         hf = ff_split_bits(h);
     } else {
-        const float4 ri0 = rec_ld(pff, i, 0), ri1 = rec_ld(pff, i, 1), rj0 = rec_ld(pff, j, 0), rj1 = rec_ld(pff, j, 1);
+        const float4 ri0 = rec_ld(pff, i, 0), rj0 = rec_ld(pff, j, 0);
         ff dff[3];
         ff_separation(ri0, ri1, rj0, rj1, D, dff);
         const V3<float> df = mk<float>(dff[0].hi, dff[1].hi, dff[2].hi);
         const float rpi = ri1.z, rqi = ri1.w, rpj = rj1.z, rqj = rj1.w;
-        const ff dd = ff_dot3(dff, dff);
-        if (!(dd.hi > 0.f) || !isfinite(dd.hi)) {
+        const float dd2 = dot(df, df);  // |d|^2 in FP32 (float-float for spheres only)
+        if (!(dd2 > 0.f) || !isfinite(dd2)) {
             st = LUB_ST_DEGENERATE;
         } else if (rpi == rqi && rpj == rqj) {
             // two spheres: n = d/|d|, h = |d| - R_i - R_j, in float-float
+            const ff dd = ff_dot3(dff, dff);
             const ff rs = ff_rsqrt(dd);
 #pragma unroll
             for (int a = 0; a < 3; ++a) nf[a] = ff_mul(dff[a], rs);
@@ -345,7 +357,7 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             ff_axis_rec(rec_ld(pff, i, 2), rec_ld(pff, i, 3), oi);
             ff_axis_rec(rec_ld(pff, j, 2), rec_ld(pff, j, 3), oj);
             const Shape<float> si = shape_ff(oi, rpi, rqi), sj = shape_ff(oj, rpj, rqj);
-            const float dl = sqrtf(dd.hi);
+            const float dl = sqrtf(dd2);
             V3<float> n = scl(1.0f / dl, df);
             if (warm) {
                 const V3<float> w0 = mk<float>((float)nin[k], (float)nin[C + k], (float)nin[2 * C + k]);
