@@ -93,12 +93,19 @@ __device__ __forceinline__ ff ff_mulf(ff x, float y)
 }
 
 // 1 / sqrt(x) of a positive value: r = rsqrt(hi), one Newton correction
-// r + r (1 - x r^2) / 2 with the residual 1 - x r^2 formed in float-float
+// r + r (1 - x r^2) / 2.  The residual 1 - x r^2, of order 1e-7, by fused
+// multiply-adds: hi r = u + v exactly (v from an FMA), 1 - u r by one FMA
+// (one rounding of a number of order 1e-7), then - v r - lo r^2; about 11
+// instructions against 29 with the residual formed by float-float products
 __device__ __forceinline__ ff ff_rsqrt(ff x)
 {
     const float r = rsqrtf(x.hi);
-    const ff e = ff_sub(ff_make(1.0f), ff_mulf(ff_mulf(x, r), r));
-    return fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e.hi));
+    const float u = __fmul_rn(x.hi, r);
+    const float v = __fmaf_rn(x.hi, r, -u);
+    float e = __fmaf_rn(-u, r, 1.0f);
+    e = __fmaf_rn(-v, r, e);
+    e = __fmaf_rn(-__fmul_rn(x.lo, r), r, e);
+    return fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e));
 }
 
 // a . b of two float-float vectors

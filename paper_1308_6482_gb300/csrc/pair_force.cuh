@@ -459,9 +459,10 @@ __device__ __forceinline__ void side_contrib(const T out[12], int side, T c[6])
 // and j-side contributions ci, cj to force/torque [3][n].  Lanes with i < 0
 // add nothing, lanes with j < 0 (walls) add no j side.  The i sides of a run
 // of lanes with equal i (pairs sorted by i) are summed first by a segmented
-// warp scan (five shuffle steps, the same for every lane; runs are told
-// apart by their index among the warp's runs, so that equal i in two
-// separate runs never mix), and the run's last lane makes one atomic add.
+// warp scan (runs are told apart by their index among the warp's runs, so
+// that equal i in two separate runs never mix; the shuffle steps stop at the
+// warp's longest run, where every further step would add nothing), and the
+// run's last lane makes one atomic add.
 template <typename T>
 __device__ __forceinline__ void scatter_warp(int i, int j, size_t N, T ci[6], const T cj[6], T *__restrict__ force,
                                              T *__restrict__ torque)
@@ -469,9 +470,13 @@ __device__ __forceinline__ void scatter_warp(int i, int j, size_t N, T ci[6], co
     const int lane = threadIdx.x & 31;
     const int iprev = __shfl_up_sync(0xffffffffu, i, 1), inext = __shfl_down_sync(0xffffffffu, i, 1);
     const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || i != iprev);
-    const int run = __popc(heads & (0xffffffffu >> (31 - lane)));  // runs started at or before this lane
+    const unsigned upto = heads & (0xffffffffu >> (31 - lane));
+    const int run = __popc(upto);  // runs started at or before this lane
+    // the longest run of the warp, less one (the lane's offset in its run)
+    const int span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lane - (31 - __clz(upto))));
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
+        if (off > span) break;  // the same for every lane
         const int rup = __shfl_up_sync(0xffffffffu, run, off);
         const bool same = lane >= off && rup == run;
 #pragma unroll
