@@ -314,7 +314,8 @@ def run_multi(lub, torch, np, pl, P, stream, G, replays, step0):
 
 def kernels_in_step(form=None, precision="mixed"):
     # lub_pairs_build: zeroing of its counters, cells count, scan, cells fill,
-    # sweep, scan, compaction = 7.  lub_correct (the fused form), mixed:
+    # sweep, FP64 test of the candidates within the sweep's margin, scan,
+    # compaction = 8.  lub_correct (the fused form), mixed:
     # particle table (which also clears the sums and the work list), FP32
     # stage, work-list FP64 solves, resistance with scatter = 4; FP64: zeroing
     # and the one pass = 2.  The merged form (lub_closest_points, then
@@ -322,10 +323,10 @@ def kernels_in_step(form=None, precision="mixed"):
     # table); FP64: 1 + 2.
     form = form or STEP_FORM
     if form == "fused":
-        return 7 + (4 if precision == "mixed" else 2)
+        return 8 + (4 if precision == "mixed" else 2)
     if precision == "mixed":
-        return 7 + 3 + 3
-    return 7 + 1 + 2
+        return 8 + 3 + 3
+    return 8 + 1 + 2
 
 
 def rooflines(kernel_ms, call_ms, npairs, n, mean_it, pk, traffic):
@@ -335,7 +336,7 @@ def rooflines(kernel_ms, call_ms, npairs, n, mean_it, pk, traffic):
     b = n * PAIRS_BYTES_PER_PARTICLE + npairs * PAIRS_BYTES_PER_PAIR
     ach = b / (call_ms["pairs_build"] * 1e-3) / 1e9
     out["pairs_build"] = {
-        "kernel": "lub_pairs_build (7 kernels; k_pairs_sweep %.0f%% of the call)"
+        "kernel": "lub_pairs_build (8 kernels; k_pairs_sweep %.0f%% of the call)"
                   % (100 * kernel_ms["sweep"] / call_ms["pairs_build"]),
         "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
         "traffic": traffic.get("pairs_build"), "algorithmic_bytes": b, "ms": call_ms["pairs_build"],

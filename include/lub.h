@@ -201,9 +201,11 @@ const char *lub_last_error(const lub_ctx *ctx);
  * Order: particle pairs by (i, j) ascending, then wall pairs by (i, w).
  * Writes pair_i[k], pair_j[k] for k < min(count, capacity) and *d_count =
  * count (device int32).  The arrays also serve as the overflow store of the
- * build (pairs beyond 16 per particle, kept at their tail while it runs), so
- * the call needs capacity >= count + overflow entries, which is count for
- * any ordinary suspension; when that does not hold, *d_count receives the
+ * build (pairs beyond 16 per particle, and, for inputs with more candidates
+ * on the filters' edges than particles, the excess of those waiting for their
+ * FP64 test; kept at their tail while it runs), so the call needs capacity
+ * >= count + overflow entries, which is count for any ordinary suspension;
+ * when that does not hold, *d_count receives the
  * sum (> capacity), the listed content is unspecified and the call returns
  * LUB_ERR_CAPACITY when h_count_or_null is given (host int32, receives that
  * required capacity; the call then synchronises `stream`).  A bounded wait

@@ -17,9 +17,11 @@
 //      two indices in one of that particle's KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
 //      caller's pair arrays; each thread also tests its particle's plane walls;
-//   3. one scan over [particle-pair counts | wall-pair counts] gives every
+//   3. the FP64 test of the candidates the sweep's FP32 tests left inside
+//      their margin (k_pairs_undecided), stored as the sweep stores pairs;
+//   4. one scan over [particle-pair counts | wall-pair counts] gives every
 //      offset (wall pairs land after all particle pairs);
-//   4. compaction: each particle sorts its partners (canonical (i, j) order)
+//   5. compaction: each particle sorts its partners (canonical (i, j) order)
 //      and writes them, and its wall pairs, at its offsets.
 // The pair arrays must hold the pairs plus the overflow entries; the count
 // reports their sum when it does not fit (a capacity error, as for the pairs).
@@ -111,6 +113,8 @@ struct BuildView {
     float rmax_bound;
     int32_t cap;
     int64_t ncell_total;  // cells of all grids (the cell counts hold one more entry)
+    int2 *und;            // candidates left to the FP64 test (in the cell index storage, free after the fill)
+    int32_t und_cap;
 };
 
 // x < 0 in float-float
@@ -386,6 +390,26 @@ __device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__
     }
 }
 
+// A candidate inside the FP32 margin, left to the FP64 test of
+// k_pairs_undecided: (smaller index, larger index) in the buffer und, and
+// beyond its und_cap entries (at least one per particle: only inputs built to
+// sit on the filters' edges fill it) tagged (smaller index | INT32_MIN) at
+// the tail of the pair arrays, with the overflow list.
+__device__ __forceinline__ void defer_candidate(int i, int j, const BuildView &V)
+{
+    const int lo = min(i, j), hi = max(i, j);
+    const int u = atomicAdd(V.totals + 3, 1);
+    if (u < V.und_cap) {
+        V.und[u] = make_int2(lo, hi);
+    } else {
+        const int o = atomicAdd(V.totals + 2, 1);
+        if (o < V.cap) {
+            V.pair_i[V.cap - 1 - o] = (int32_t)((unsigned)lo | 0x80000000u);
+            V.pair_j[V.cap - 1 - o] = hi;
+        }
+    }
+}
+
 // One warp's shared memory in the sweep (the block holds blockDim.x / 32 of
 // them, dynamic): the groups' staging (rows padded by one entry, so that the
 // groups' broadcast reads fall in different banks), each lane's particle,
@@ -430,8 +454,10 @@ static_assert(sizeof(SweepWarp) % 16 == 0, "warp blocks stay 16-byte aligned");
 // E 2^-20 to the grid's, so that every decision inside it still goes to the
 // FP64 test.
 //
-// Candidates inside the FP32 margin (about one in 10^4) are decided on the
-// spot by the FP64 test, in the lane that holds them.
+// Candidates inside the FP32 margin (about one in 10^4) are left to the
+// FP64 test of the next kernel (defer_candidate): deciding them in the
+// drain would keep the FP64 test's registers in the sweep's loop, where
+// they cost spills (the sweep ran 10 % faster without it).
 
 template <bool ENS>
 __device__ __forceinline__ void sweep_groups(const BuildView &V)
@@ -477,10 +503,11 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const int bo = ENS ? sbat[s0w + o] : 0;
         const Grid &G = grid_ref<ENS>(G0, EG, bo);
         const int r = pair_decide(G.cutoff, wm.y, wm.x, W.own1[o], d.w, b1, d.x, d.y, d.z);
-        // inside the margin the FP64 test decides
-        if (r == kAccept ||
-            (r == kUndecided && pair_test_fp64(P, dom_ref<ENS>(D0, E, bo), ii, jj, cutoff_d)))
+        // inside the margin the FP64 test decides, in the next kernel
+        if (r == kAccept)
             store_candidate(ii, jj, N, cnt, slots, ovf_n, cap, pair_i, pair_j);
+        else if (r == kUndecided)
+            defer_candidate(ii, jj, V);
     };
     int b = 0, cc = 0, colkey = -1, pidx = -1;
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
@@ -716,6 +743,50 @@ __global__ void __launch_bounds__(256, 4) k_pairs_sweep(const __grid_constant__ 
     sweep_groups<ENS>(V);
 }
 
+// The FP64 test of the candidates the sweep left inside its FP32 margin: those
+// in und, then the tagged entries of the pair arrays' tail (entries untagged
+// there are pairs beyond their particle's slots).  An accepted candidate
+// takes the next slot of its smaller index as the sweep's pairs do; beyond
+// the slots it stays where it is, as a pair the compaction collects (an und
+// entry, or the tail entry untagged).  Every other entry becomes -1, which
+// the compaction never matches.  Nothing is appended here, so the tail's
+// length stays as the sweep left it.
+template <bool ENS>
+__global__ void __launch_bounds__(256) k_pairs_undecided(const __grid_constant__ BuildView V)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int N = V.P.n;
+    const int nu = min(V.totals[3], V.und_cap);
+    const int nt = V.totals[3] > V.und_cap ? min(V.totals[2], V.cap) : 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nu + nt; k += gridDim.x * blockDim.x) {
+        int lo, hi;
+        if (k < nu) {
+            const int2 e = V.und[k];
+            lo = e.x;
+            hi = e.y;
+        } else {
+            const int32_t t = V.pair_i[V.cap - 1 - (k - nu)];
+            if (t >= 0) continue;
+            lo = t & 0x7fffffff;
+            hi = V.pair_j[V.cap - 1 - (k - nu)];
+        }
+        const int b = ENS ? batch_of(V.E, lo) : 0;
+        bool keep = false;  // accepted beyond the slots
+        if (pair_test_fp64(V.P, dom_ref<ENS>(V.D, V.E, b), lo, hi, V.cutoff_d)) {
+            const int q = atomicAdd(V.cnt + lo, 1);
+            if (q < KSLOT)
+                V.slots[(size_t)q * N + lo] = hi;
+            else
+                keep = true;
+        }
+        if (k < nu)
+            V.und[k].x = keep ? lo : -1;
+        else
+            V.pair_i[V.cap - 1 - (k - nu)] = keep ? lo : -1;
+    }
+}
+
 // Canonical order: each particle's partners, sorted, then its wall pairs, at
 // the offsets of the scan (off = the scanned counts, off[2N] = the total).
 // The count is the total, or total + overflow entries when they do not fit.
@@ -785,7 +856,9 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
                 }
             }
         } else {
-            // the slots, then this particle's overflow entries, then sort in place
+            // the slots, then this particle's entries beyond them (at the
+            // tail, and among the candidates the FP64 test accepted), then
+            // sort in place
             for (int q = 0; q < KSLOT; ++q) {
                 pair_i[b + q] = i;
                 pair_j[b + q] = slots[(size_t)q * n + i];
@@ -794,6 +867,13 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
             for (int o = 0; o < novf && c < m; ++o)
                 if (pair_i[cap - 1 - o] == i) {
                     pair_j[b + c] = pair_j[cap - 1 - o];
+                    pair_i[b + c] = i;
+                    ++c;
+                }
+            const int nu = min(V.totals[3], V.und_cap);
+            for (int u = 0; u < nu && c < m; ++u)
+                if (V.und[u].x == i) {
+                    pair_j[b + c] = V.und[u].y;
                     pair_i[b + c] = i;
                     ++c;
                 }
@@ -908,7 +988,7 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     char *s = (char *)base;
     L.flags = (int32_t *)s;
     s += 256;
-    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] overflow entries
+    L.totals = (int32_t *)s;  // [0] all pairs, [1] cells, [2] tail entries, [3] candidates left to FP64
     s += 256;
     L.cell_cnt = (int32_t *)s;
     s += b_cell;
@@ -991,6 +1071,11 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.rmax_bound = rmax;
     V.cap = cap;
     V.ncell_total = G.ncell;
+    // the buffer of candidates left to the FP64 test: the cell index and
+    // slot arrays, contiguous and free once the cells are filled
+    V.und = reinterpret_cast<int2 *>(L.cell_of);
+    const int64_t und_cap = (int64_t)(L.slot - L.cell_of + (N + 1)) / 2;
+    V.und_cap = (int32_t)(und_cap < INT32_MAX ? und_cap : INT32_MAX);
     cudaError_t e;
     const int block = 256;
     const int gn = grid_for(N, block, num_sms, 32);  // one particle per thread up to 1.2M
@@ -1007,6 +1092,8 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     e = launch_pdl(k_pairs_sweep<ENS>, sw.grid, sw.block, (size_t)(sw.block / 32) * sizeof(SweepWarp), st, V);
     lub_trace_mark(ctx, LUB_TRACE_SWEEP, st);
     if ((rc = lub_check_cuda(ctx, e, "sweep launch"))) return rc;
+    e = launch_pdl(k_pairs_undecided<ENS>, num_sms, 256, 0, st, V);
+    if ((rc = lub_check_cuda(ctx, e, "undecided pairs launch"))) return rc;
     // one scan over [particle pairs | wall pairs] (+1 entry: the end of the last run)
     if ((rc = scan_exclusive(ctx, L.cnt, 2 * N + 1, L.totals + 0, L.tmp, L.tmp_bytes, st, L.flags, true))) return rc;
     e = launch_pdl(k_pairs_compact, grid_for(N, 256, num_sms, 32), 256, 0, st, V);

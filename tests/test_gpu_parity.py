@@ -284,15 +284,44 @@ def test_normal_only_model_parity(prec):
 def test_candidates_at_the_list_cutoff(P):
     """Sphere pairs at gaps within 1e-4 of Delta_L = 1.  For spheres the
     pre-filter values are h - Delta_L, so the FP32 tests leave every one of
-    these inside their margin and the sweep decides each in FP64, in the lane
-    that holds it: 500 and 3,000 pairs (1,000 and 6,000 borderline
-    candidates) give the oracle's set exactly."""
+    these inside their margin and the sweep leaves each to the FP64 test
+    after it: 500 and 3,000 pairs (1,000 and 6,000 particles) give the
+    oracle's set exactly."""
     parts, dom, _, _ = gen.pair_stream(P, seed=71, kind="spheres", gap_range=(1 - 1e-4, 1 + 1e-4))
     pi, pj = oracle.candidates(parts, dom, 1.0)
     assert P // 4 < len(pi) < 3 * P // 4             # both sides of the cut-off
     g = run_gpu(parts, dom, "fp64")
     np.testing.assert_array_equal(g["pi"], pi)
     np.testing.assert_array_equal(g["pj"], pj)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_candidates_on_the_filters_edge_beyond_the_buffer(prec):
+    """A periodic simple cubic lattice of 1,000 spheres (radius 2) whose
+    neighbours sit at gaps of Delta_L - 2e-5 along x and z and Delta_L + 2e-5
+    along y: each of the 3,000 neighbour pairs lies inside the FP32 margin,
+    more than the buffer of candidates left to the FP64 test holds (about one
+    per particle), so the rest wait, tagged, at the tail of the pair arrays
+    (the build asks for that room, then succeeds).  The list is the
+    oracle's: the x and z neighbours, 2,000 pairs."""
+    n, R = 10, 2.0
+    a = np.array([2 * R + 1.0 - 2e-5, 2 * R + 1.0 + 2e-5, 2 * R + 1.0 - 2e-5])
+    ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    pos = (np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1) + 0.5) * a
+    N = len(pos)
+    rng = np.random.default_rng(9)
+    q = gen.random_quaternions(N, rng)
+    r = np.full(N, R, np.float32)
+    parts = dict(x=pos[:, 0].copy(), y=pos[:, 1].copy(), z=pos[:, 2].copy(), qw=q[:, 0].copy(), qx=q[:, 1].copy(),
+                 qy=q[:, 2].copy(), qz=q[:, 3].copy(), r_par=r, r_perp=r.copy())
+    gen.velocities(parts, rng)
+    dom = dict(L=tuple(float(x) for x in n * a), periodic=(True, True, True), walls=[])
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert len(pi) == 2 * N
+    g = run_gpu(parts, dom, prec)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
 
 
 @pytest.mark.parametrize("case", ["periodic", "walls", "five_cells"])
