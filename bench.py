@@ -63,8 +63,8 @@ PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # (one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum per kernel
 # over `bench.py --only large --steps 3`, the last of its three steps)
 TRAFFIC = {
-    "large": {"sources": "e7b88ef85fd20fdc",
-              "bytes": {"pairs_build": 279898368, "k_closest_mixed": 385597440, "k_resistance_apply": 524585472}},
+    "large": {"sources": "22a46e3a59539880",
+              "bytes": {"pairs_build": 274670080, "k_closest_mixed": 362637056, "k_resistance_apply": 524588288}},
 }
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")

@@ -483,7 +483,7 @@ struct TuneDefault {
 // counts, refinement) on large inputs
 constexpr TuneDefault kTuneDefaults[LUB_TUNE_COUNT] = {
     {64, 256, 128},  // LUB_TUNE_CLOSEST_MIXED (the autotuner's choice at 1M and 32k particles)
-    {32, 64, 32},    // LUB_TUNE_CLOSEST_REFINE
+    {32, 8, 32},     // LUB_TUNE_CLOSEST_REFINE (the autotuner's choice at 1M particles and in the ensemble)
     {128, 64, 128},  // LUB_TUNE_CLOSEST_FP64
     {64, 256, 128},  // LUB_TUNE_RESISTANCE (the autotuner's choice at 1M particles)
     {256, 32, 256},  // LUB_TUNE_APPLY
