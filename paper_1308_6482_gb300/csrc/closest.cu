@@ -130,19 +130,6 @@ __device__ NewtonOut newton_sphere(const Shape<T> &si, const Shape<T> &sj, const
     return out;
 }
 
-// symmetry axis of q/|q| in float-float (quaternion components exact)
-__device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o[3])
-{
-    const ff q2 = ff_add(ff_add(two_prod(w, w), two_prod(x, x)), ff_add(two_prod(y, y), two_prod(z, z)));
-    // s = 2 / |q|^2: float reciprocal plus one correction with the exact residual
-    const float r0 = __fdiv_rn(2.0f, q2.hi);
-    const ff res = ff_sub(ff_make(2.0f), ff_mulf(q2, r0));
-    const ff s = fast_two_sum(r0, __fmul_rn(res.hi, __fmul_rn(r0, 0.5f)));
-    o[0] = ff_mul(s, ff_add(two_prod(x, z), two_prod(w, y)));
-    o[1] = ff_mul(s, ff_sub(two_prod(y, z), two_prod(w, x)));
-    o[2] = ff_sub(ff_make(1.0f), ff_mul(s, ff_add(two_prod(x, x), two_prod(y, y))));
-}
-
 // Minimum-image separation r_j - r_i in float-float from the particles'
 // records (rec_ld 0 and 1: the float-float centres); the image shift is
 // taken from the float part (listed pairs are far from the ambiguous half

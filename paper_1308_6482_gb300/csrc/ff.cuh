@@ -180,6 +180,20 @@ __device__ __forceinline__ ff ff_dot3_exact(const float a[3], const float b[3])
 }
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
+// symmetry axis (body z) of the rotation by q/|q| in float-float (quaternion
+// components exact): 2/|q|^2 (xz + wy, yz - wx, ...) and 1 - 2/|q|^2 (x^2 + y^2)
+__device__ __forceinline__ void ff_axis(float w, float x, float y, float z, ff o[3])
+{
+    const ff q2 = ff_add(ff_add(two_prod(w, w), two_prod(x, x)), ff_add(two_prod(y, y), two_prod(z, z)));
+    // s = 2 / |q|^2: float reciprocal plus one correction with the exact residual
+    const float r0 = __fdiv_rn(2.0f, q2.hi);
+    const ff res = ff_sub(ff_make(2.0f), ff_mulf(q2, r0));
+    const ff s = fast_two_sum(r0, __fmul_rn(res.hi, __fmul_rn(r0, 0.5f)));
+    o[0] = ff_mul(s, ff_add(two_prod(x, z), two_prod(w, y)));
+    o[1] = ff_mul(s, ff_sub(two_prod(y, z), two_prod(w, x)));
+    o[2] = ff_sub(ff_make(1.0f), ff_mul(s, ff_add(two_prod(x, x), two_prod(y, y))));
+}
+
 // Float-float split of a double with integer and FP32 operations only (no
 // FP64-pipe conversion): hi = d truncated to 24 significant bits, lo = the
 // next 23 bits, |hi + lo - d| < 2^-46 |d|.  Doubles with |d| < 2^-126

@@ -276,6 +276,67 @@ __device__ __forceinline__ bool pair_test_fp64(const PView &P, const DView &D, i
 // test decides)
 constexpr int kReject = 0, kAccept = 1, kUndecided = 2;
 
+// support function sqrt(a2 + E (o.e)^2) of a spheroid along the unit e, in
+// float-float (a2 = R_perp^2, E = R_par^2 - R_perp^2)
+__device__ __forceinline__ ff ff_support(const ff o[3], float rpar, float rperp, const ff e[3])
+{
+    const ff a2 = two_prod(rperp, rperp), E = ff_sub(two_prod(rpar, rpar), a2);
+    const ff c = ff_dot3(o, e);
+    const ff s2 = ff_add(a2, ff_mul(E, ff_mul(c, c)));
+    return ff_mul(s2, ff_rsqrt(s2));
+}
+
+// The three tests of pair_test_fp64 in float-float on the FP32 pipe, for the
+// candidates the sweep's FP32 tests leave inside their margin: the positions
+// split from their bits (within 2^-46 of each coordinate), the rest at about
+// 44 bits, so each test value is within about 1e-12 of the pair's reach plus
+// 1e-13 of the coordinates' magnitude of the exact one.  A test that clears
+// its bound by more than 1e-10 of the reach plus 3e-14 of the coordinates'
+// magnitude is decided here, as the FP64 test decides it; kUndecided
+// otherwise (then the FP64 test: a dependent chain of FP64 operations, at
+// 1/74 of the FP32 rate on this GPU, is the cost this saves).
+__device__ __forceinline__ int pair_decide_ff(const PView &P, const DView &D, int i, int j, double cutoff)
+{
+    const double *pos[3] = {P.x, P.y, P.z};
+    ff d[3];
+    float mag = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const ff pi = ff_split_bits_nan(pos[a][i]), pj = ff_split_bits_nan(pos[a][j]);
+        mag += fabsf(pi.hi) + fabsf(pj.hi);
+        d[a] = ff_sub(pj, pi);
+        if (D.periodic[a]) {
+            const float k = rintf(d[a].hi * D.invLf[a]);
+            if (k != 0.f) d[a] = ff_sub(d[a], ff_mulf(ff{D.Lff[a][0], D.Lff[a][1]}, k));
+        }
+    }
+    const float rpi = P.rpar[i], rqi = P.rperp[i], rpj = P.rpar[j], rqj = P.rperp[j];
+    const float rmi = fmaxf(rpi, rqi), rmj = fmaxf(rpj, rqj);
+    const ff cut = ff_split_bits(cutoff);
+    const ff r2 = ff_dot3(d, d);
+    if (!(r2.hi > 0.f) || !isfinite(r2.hi) || !isfinite(mag)) return kUndecided;
+    const ff ir = ff_rsqrt(r2);
+    const ff r = ff_mul(r2, ir);
+    const float margin = 1e-10f * (r.hi + rmi + rmj + cut.hi) + 3e-14f * mag;
+    bool sure = true;
+    // t > margin rejects; |t| <= margin leaves the pair undecided
+    auto clears = [&](const ff t) {
+        if (t.hi > margin) return false;
+        if (t.hi >= -margin) sure = false;
+        return true;
+    };
+    if (!clears(ff_sub(r, ff_add(ff_add(ff_make(rmi), ff_make(rmj)), cut)))) return kReject;
+    // the support functions are even: along d / r as along -d / r
+    ff e[3], oi[3], oj[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = ff_mul(d[a], ir);
+    ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], oi);
+    ff_axis(P.qw[j], P.qx[j], P.qy[j], P.qz[j], oj);
+    if (!clears(ff_sub(ff_sub(r, ff_support(oi, rpi, rqi, e)), ff_add(ff_make(rmj), cut)))) return kReject;
+    if (!clears(ff_sub(ff_sub(r, ff_support(oj, rpj, rqj, e)), ff_add(ff_make(rmi), cut)))) return kReject;
+    return sure ? kAccept : kUndecided;
+}
+
 // the decision of a candidate that passed the bounding-sphere prefilter: aw
 // and a1 the first particle's Rmax and record, bw and b1 the second's, d the
 // vector between their centres; margin the absolute FP32 error allowance
@@ -743,7 +804,8 @@ __global__ void __launch_bounds__(256, 4) k_pairs_sweep(const __grid_constant__ 
     sweep_groups<ENS>(V);
 }
 
-// The FP64 test of the candidates the sweep left inside its FP32 margin: those
+// The test of the candidates the sweep left inside its FP32 margin, in
+// float-float (pair_decide_ff) and in FP64 where that leaves it open: those
 // in und, then the tagged entries of the pair arrays' tail (entries untagged
 // there are pairs beyond their particle's slots).  An accepted candidate
 // takes the next slot of its smaller index as the sweep's pairs do; beyond
@@ -772,8 +834,10 @@ __global__ void __launch_bounds__(256) k_pairs_undecided(const __grid_constant__
             hi = V.pair_j[V.cap - 1 - (k - nu)];
         }
         const int b = ENS ? batch_of(V.E, lo) : 0;
+        const DView &D = dom_ref<ENS>(V.D, V.E, b);
+        const int dec = pair_decide_ff(V.P, D, lo, hi, V.cutoff_d);
         bool keep = false;  // accepted beyond the slots
-        if (pair_test_fp64(V.P, dom_ref<ENS>(V.D, V.E, b), lo, hi, V.cutoff_d)) {
+        if (dec == kAccept || (dec == kUndecided && pair_test_fp64(V.P, D, lo, hi, V.cutoff_d))) {
             const int q = atomicAdd(V.cnt + lo, 1);
             if (q < KSLOT)
                 V.slots[(size_t)q * N + lo] = hi;

@@ -324,6 +324,39 @@ def test_candidates_on_the_filters_edge_beyond_the_buffer(prec):
     compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_candidates_exactly_on_the_list_cutoff(prec):
+    """Sphere pairs (radius 2) whose centres lie exactly 2R + Delta_L = 5
+    apart, and 2^-30 nearer or farther (positions exactly representable):
+    the FP32 and float-float tests leave all of them inside their margins,
+    so the FP64 test decides each, as the oracle does: the pair at 5 and the
+    nearer ones are listed, the farther ones not."""
+    offs = [0.0, 2.0 ** -30, -(2.0 ** -30), 0.0, 2.0 ** -30, -(2.0 ** -30)]
+    xs, ys, zs = [], [], []
+    for k, o in enumerate(offs):
+        base = np.array([10.0 + 20.0 * (k % 3), 10.0 + 20.0 * (k // 3), 30.0])
+        ax = k // 3  # along x for the first three, along y for the rest
+        other = base.copy()
+        other[ax] += 5.0 + o
+        for pnt in (base, other):
+            xs.append(pnt[0])
+            ys.append(pnt[1])
+            zs.append(pnt[2])
+    n = len(xs)
+    rng = np.random.default_rng(12)
+    q = gen.random_quaternions(n, rng)
+    r = np.full(n, 2.0, np.float32)
+    parts = dict(x=np.array(xs), y=np.array(ys), z=np.array(zs), qw=q[:, 0].copy(), qx=q[:, 1].copy(),
+                 qy=q[:, 2].copy(), qz=q[:, 3].copy(), r_par=r, r_perp=r.copy())
+    gen.velocities(parts, rng)
+    dom = dict(L=(100.0, 100.0, 100.0), periodic=(True, True, True), walls=[])
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    np.testing.assert_array_equal(pi, [0, 4, 6, 10])
+    g = run_gpu(parts, dom, prec)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+
+
 @pytest.mark.parametrize("case", ["periodic", "walls", "five_cells"])
 def test_dense_packings(case):
     """Growth packings at Phi = 0.5 of spheroids with aspect ratios in
