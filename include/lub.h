@@ -196,7 +196,9 @@ const char *lub_last_error(const lub_ctx *ctx);
  * Particle w-wall pair (i, -1-w) is listed when the exact gap
  * wall_dir (z_i - wall_z) - sigma_i(e_z) < Delta_L.  The decisions are those
  * of double precision arithmetic: FP32 tests with a margin of 1e-5 (2 Rmax +
- * Delta_L + 1), and every candidate inside the margin decided again in FP64.
+ * Delta_L + 1); every candidate inside that margin is tested again in
+ * float-float (margin 1e-10 of the reach plus 3e-14 of the coordinates'
+ * magnitude), and inside that margin in FP64.
  *
  * Order: particle pairs by (i, j) ascending, then wall pairs by (i, w).
  * Writes pair_i[k], pair_j[k] for k < min(count, capacity) and *d_count =

@@ -17,8 +17,9 @@
 //      two indices in one of that particle's KSLOT slots (atomic slot index); the
 //      rare pairs beyond KSLOT go to an overflow list kept at the tail of the
 //      caller's pair arrays; each thread also tests its particle's plane walls;
-//   3. the FP64 test of the candidates the sweep's FP32 tests left inside
-//      their margin (k_pairs_undecided), stored as the sweep stores pairs;
+//   3. the test of the candidates the sweep's FP32 tests left inside their
+//      margin, in float-float, then in FP64 inside the float-float margin
+//      (k_pairs_undecided), stored as the sweep stores pairs;
 //   4. one scan over [particle-pair counts | wall-pair counts] gives every
 //      offset (wall pairs land after all particle pairs);
 //   5. compaction: each particle sorts its partners (canonical (i, j) order)
@@ -451,7 +452,7 @@ __device__ __forceinline__ void store_candidate(int i, int j, int N, int32_t *__
     }
 }
 
-// A candidate inside the FP32 margin, left to the FP64 test of
+// A candidate inside the FP32 margin, left to the tests of
 // k_pairs_undecided: (smaller index, larger index) in the buffer und, and
 // beyond its und_cap entries (at least one per particle: only inputs built to
 // sit on the filters' edges fill it) tagged (smaller index | INT32_MIN) at
@@ -516,9 +517,10 @@ static_assert(sizeof(SweepWarp) % 16 == 0, "warp blocks stay 16-byte aligned");
 // FP64 test.
 //
 // Candidates inside the FP32 margin (about one in 10^4) are left to the
-// FP64 test of the next kernel (defer_candidate): deciding them in the
-// drain would keep the FP64 test's registers in the sweep's loop, where
-// they cost spills (the sweep ran 10 % faster without it).
+// next kernel (defer_candidate), which tests them in float-float and, inside
+// that test's far smaller margin, in FP64: deciding them in the drain kept
+// the FP64 test's registers in the sweep's loop, where they cost spills
+// (the sweep ran 10 % faster without it).
 
 template <bool ENS>
 __device__ __forceinline__ void sweep_groups(const BuildView &V)
