@@ -511,38 +511,54 @@ __global__ void __launch_bounds__(256) k_particles_ff(PView P, float4 *__restric
 {
     pdl_wait();
     pdl_trigger();
+    // each warp's 32 records (2,560 contiguous bytes of out) pass through
+    // shared memory, so that their stores are whole 512-byte runs instead of
+    // 16-byte pieces at an 80-byte stride
+    __shared__ float4 stage[8][32 * kRec];
     if (zero16 && blockIdx.x == 0 && threadIdx.x < 4) zero16[threadIdx.x] = 0;
     const size_t n = (size_t)P.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        if (zf) {
-            zf[i] = 0.f;
-            zf[n + i] = 0.f;
-            zf[2 * n + i] = 0.f;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *const sw = stage[w];
+    // the loop bound is the same for every lane of a warp (the warp copies its records out together)
+    for (int base = blockIdx.x * blockDim.x; base < P.n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        if (i < P.n) {
+            if (zf) {
+                zf[i] = 0.f;
+                zf[n + i] = 0.f;
+                zf[2 * n + i] = 0.f;
+            }
+            if (zt) {
+                zt[i] = 0.f;
+                zt[n + i] = 0.f;
+                zt[2 * n + i] = 0.f;
+            }
+            // the centre split from its bits (46 bits: 1.5e-11 at |r| = 1024; no FP64 pipe)
+            const ff x = ff_split_bits_nan(P.x[i]), y = ff_split_bits_nan(P.y[i]), z = ff_split_bits_nan(P.z[i]);
+            ff o[3];
+            ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (P.vx) {
+                v[0] = P.vx[i];
+                v[1] = P.vy[i];
+                v[2] = P.vz[i];
+                v[3] = P.wx[i];
+                v[4] = P.wy[i];
+                v[5] = P.wz[i];
+            }
+            float4 *r = sw + lane * kRec;
+            r[0] = make_float4(x.hi, x.lo, y.hi, y.lo);
+            r[1] = make_float4(z.hi, z.lo, P.rpar[i], P.rperp[i]);
+            r[2] = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+            r[3] = make_float4(o[2].hi, o[2].lo, v[0], v[1]);
+            r[4] = make_float4(v[2], v[3], v[4], v[5]);
         }
-        if (zt) {
-            zt[i] = 0.f;
-            zt[n + i] = 0.f;
-            zt[2 * n + i] = 0.f;
-        }
-        // the centre split from its bits (46 bits: 1.5e-11 at |r| = 1024; no FP64 pipe)
-        const ff x = ff_split_bits_nan(P.x[i]), y = ff_split_bits_nan(P.y[i]), z = ff_split_bits_nan(P.z[i]);
-        ff o[3];
-        ff_axis(P.qw[i], P.qx[i], P.qy[i], P.qz[i], o);
-        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (P.vx) {
-            v[0] = P.vx[i];
-            v[1] = P.vy[i];
-            v[2] = P.vz[i];
-            v[3] = P.wx[i];
-            v[4] = P.wy[i];
-            v[5] = P.wz[i];
-        }
-        float4 *r = out + (size_t)i * kRec;
-        r[0] = make_float4(x.hi, x.lo, y.hi, y.lo);
-        r[1] = make_float4(z.hi, z.lo, P.rpar[i], P.rperp[i]);
-        r[2] = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
-        r[3] = make_float4(o[2].hi, o[2].lo, v[0], v[1]);
-        r[4] = make_float4(v[2], v[3], v[4], v[5]);
+        __syncwarp();
+        const int i0 = base + 32 * w;
+        const int cnt = P.n - i0 < 32 ? (P.n - i0 > 0 ? P.n - i0 : 0) : 32;
+        float4 *dst = out + (size_t)i0 * kRec;
+        for (int q = lane; q < cnt * kRec; q += 32) dst[q] = sw[q];
+        __syncwarp();
     }
 }
 
