@@ -880,8 +880,15 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
         }
     }
     if (need > cap) return;
+    // each warp's pairs are one run of the output (its particles are
+    // consecutive): staged in shared memory and stored as whole runs, unless
+    // a particle of the warp has more pairs than slots (then every lane
+    // stores its own)
+    __shared__ int2 stage[8][32 * KSLOT];
+    int2 *const sg = stage[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
     // warp-uniform loop bound: every lane of a warp takes part in the
-    // reduction of its largest partner count
+    // warp's reductions and its staged stores
     const int n_up = (n + 31) & ~31;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += gridDim.x * blockDim.x) {
         const bool live = i < n;
@@ -890,8 +897,7 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
         // count (mostly 4..8 of the 16), so the loads and stores beyond it
         // are skipped, not issued with every lane predicated off
         const int mw = __reduce_max_sync(0xffffffffu, m < KSLOT ? m : KSLOT);
-        if (!live) continue;
-        if (m <= KSLOT) {
+        if (!__any_sync(0xffffffffu, m > KSLOT)) {
             // sort in registers: compare-exchange passes (m is small, mostly 0..4)
             int v[KSLOT];
 #pragma unroll
@@ -913,23 +919,31 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
                     }
                 }
             }
+            // lane 0 is live whenever any lane is (i grows with the lane)
+            const int b0 = __shfl_sync(0xffffffffu, b, 0);
+            const int tw = (int)__reduce_max_sync(0xffffffffu, (unsigned)(live ? b + m - b0 : 0));
 #pragma unroll
             for (int q = 0; q < KSLOT; ++q) {
                 if (q >= mw) break;
-                if (q < m) {
-                    pair_i[b + q] = i;
-                    pair_j[b + q] = v[q];
-                }
+                if (q < m) sg[b - b0 + q] = make_int2(i, v[q]);
             }
-        } else {
-            // the slots, then this particle's entries beyond them (at the
-            // tail, and among the candidates the FP64 test accepted), then
+            __syncwarp();
+            for (int t = lane; t < tw; t += 32) {
+                const int2 e = sg[t];
+                pair_i[b0 + t] = e.x;
+                pair_j[b0 + t] = e.y;
+            }
+            __syncwarp();
+        } else if (live) {
+            // the slots, then (beyond them) this particle's entries at the
+            // tail and among the candidates the FP64 test accepted, then
             // sort in place
-            for (int q = 0; q < KSLOT; ++q) {
+            const int ms = m < KSLOT ? m : KSLOT;
+            for (int q = 0; q < ms; ++q) {
                 pair_i[b + q] = i;
                 pair_j[b + q] = slots[(size_t)q * n + i];
             }
-            int c = KSLOT;
+            int c = ms;
             for (int o = 0; o < novf && c < m; ++o)
                 if (pair_i[cap - 1 - o] == i) {
                     pair_j[b + c] = pair_j[cap - 1 - o];
@@ -953,6 +967,7 @@ __device__ __forceinline__ void pairs_compact(const BuildView &V)
                 pair_j[q + 1] = x;
             }
         }
+        if (!live) continue;
         const int wb = off[n + i];
         const int bits = wbits[i];
         int c = 0;
