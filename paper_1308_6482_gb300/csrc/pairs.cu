@@ -103,7 +103,8 @@ struct BuildView {
     Grid G;
     Ens E;
     const EnsGrid *EG;
-    int32_t *flags, *cell_cnt, *cell_of, *slot, *sorted, *cellc, *sbat, *cnt, *totals, *slots;
+    int32_t *flags, *cell_cnt, *cell_of, *slot, *sbat, *cnt, *totals, *slots;
+    int2 *sc;  // per slot: its particle and its cell (x | y << 10 | z << 20)
     uint8_t *wbits;
     float4 *rel;  // each particle's position relative to its cell's centre (cells count -> cells fill)
     float4 *rec0, *rec1;
@@ -217,10 +218,9 @@ __device__ __forceinline__ void cells_fill(const BuildView &V)
     const int32_t *__restrict__ cell_start = V.cell_cnt;
     const int32_t *__restrict__ cell_of = V.cell_of;
     const int32_t *__restrict__ slot = V.slot;
-    int32_t *__restrict__ sorted = V.sorted;
+    int2 *__restrict__ sc = V.sc;
     float4 *__restrict__ rec0 = V.rec0;
     float4 *__restrict__ rec1 = V.rec1;
-    int32_t *__restrict__ cellc = V.cellc;
     int32_t *__restrict__ sbat = V.sbat;
     int32_t *__restrict__ cnt = V.cnt;
     unsigned long long *__restrict__ zero = V.scan_state;
@@ -240,9 +240,8 @@ __device__ __forceinline__ void cells_fill(const BuildView &V)
         const float4 r = V.rel[i];
         const float rpar = P.rpar[i], rperp = P.rperp[i];
         const V3<float> o = quat_axis<float>(P.qw[i], P.qx[i], P.qy[i], P.qz[i]);
-        sorted[s] = i;
+        sc[s] = make_int2(i, cx | (cy << 10) | (cz << 20));  // nc <= 1024 per axis
         if (ENS) sbat[s] = b;
-        cellc[s] = cx | (cy << 10) | (cz << 20);  // nc <= 1024 per axis
         rec0[s] = make_float4(r.x, r.y, r.z, fmaxf(rpar, rperp));
         rec1[s] = make_float4(o.x, o.y, o.z, rpar * rpar - rperp * rperp);
     }
@@ -531,10 +530,9 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
     const Ens &E = V.E;
     const EnsGrid *__restrict__ EG = V.EG;
     const int32_t *__restrict__ cell_start = V.cell_cnt;
-    const int32_t *__restrict__ sorted = V.sorted;
+    const int2 *__restrict__ sc = V.sc;
     const float4 *__restrict__ rec0 = V.rec0;
     const float4 *__restrict__ rec1 = V.rec1;
-    const int32_t *__restrict__ cellc = V.cellc;
     const int32_t *__restrict__ sbat = V.sbat;
     int32_t *__restrict__ cnt = V.cnt;
     int32_t *__restrict__ slots = V.slots;
@@ -560,7 +558,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const int t = W.qt[e];
         const int o = W.qo[e];
         const float4 b1 = rec1[t];
-        const int jj = sorted[t];
+        const int jj = sc[t].x;
         const int ii = W.own_i[o];
         const float2 wm = W.ownw[o];
         const int bo = ENS ? sbat[s0w + o] : 0;
@@ -580,13 +578,14 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const DView &D = dom_ref<ENS>(D0, E, b);
         a0 = rec0[s];
         a1 = rec1[s];
-        cc = cellc[s];
+        const int2 own = sc[s];
+        cc = own.y;
         const int cy = (cc >> 10) & 1023, cz = cc >> 20;
         colkey = cell_base<ENS>(EG, b) + (cz * G.nc[1] + cy) * G.nc[0];  // first cell of the column
         // plane walls: the gap dir (z - z_w) - sigma(e_z) in FP32 from the
         // records (z - z_w in float-float), decided in FP64 only within the
         // margin (the exact test costs some 60 FP64 operations)
-        const int i = sorted[s];
+        const int i = own.x;
         pidx = i;
         const float rm2 = a0.w * a0.w;
         const float sz = sqrtf(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
@@ -715,7 +714,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
                                 t = k == 0 ? beg[0] + u : (k == 1 ? beg[1] + u - num[0] : beg[2] + u - num[0] - num[1]);
                             }
                             const float4 r0 = rec0[t];
-                            const int dc = (cellc[t] & 1023) + (k - 1) * nx - lcx;
+                            const int dc = (sc[t].y & 1023) + (k - 1) * nx - lcx;
                             v = make_float4(r0.x + (float)dc * cs0, r0.y + oy, r0.z + oz, r0.w);
                             // row 0: the image at +L_x comes after every slot
                             tk = (row == 0 && k == 2) ? (int)((unsigned)t | 0x80000000u) : t;
@@ -1077,7 +1076,7 @@ Layout layout(void *base, int64_t N, int64_t ncell, bool ens = false)
     s += b_n;
     L.slot = (int32_t *)s;
     s += b_n;
-    L.sorted = (int32_t *)s;
+    L.sorted = (int32_t *)s;  // with the cellc storage after it: the int2 per slot (particle, cell)
     s += b_n;
     L.cellc = (int32_t *)s;
     s += b_n;
@@ -1131,8 +1130,7 @@ int build_core(lub_ctx *ctx, int num_sms, void *scratch, const Grid &G, const PV
     V.cell_cnt = L.cell_cnt;
     V.cell_of = L.cell_of;
     V.slot = L.slot;
-    V.sorted = L.sorted;
-    V.cellc = L.cellc;
+    V.sc = reinterpret_cast<int2 *>(L.sorted);  // the sorted and cellc storage, contiguous
     V.sbat = L.sbat;
     V.cnt = L.cnt;
     V.totals = L.totals;
