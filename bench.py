@@ -63,8 +63,8 @@ PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # (one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum per kernel
 # over `bench.py --only large --steps 3`, the last of its three steps)
 TRAFFIC = {
-    "large": {"sources": "94564bc82336b1db",
-              "bytes": {"pairs_build": 274714368, "k_closest_mixed": 363924736, "k_resistance_apply": 514514432}},
+    "large": {"sources": "849edc8b3ad16d6a",
+              "bytes": {"pairs_build": 273368832, "k_closest_mixed": 372497664, "k_resistance_apply": 533056512}},
 }
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")
