@@ -165,17 +165,17 @@ def test_capacity_overflow_reports_required_count():
     np.testing.assert_array_equal(pl.results()["pi"], pi)
 
 
-def crowded_particle(n_around=30):
+def crowded_particle(n_around=30, gap=0.5):
     """Particle 0 (the lowest index, so every pair counts for it) with
-    n_around small spheres at gap 0.5 around it: more partners than the
-    builder's per-particle slots, so the overflow path runs."""
+    n_around small spheres at the given gap around it: more partners than
+    the builder's per-particle slots, so the overflow path runs."""
     rng = np.random.default_rng(5)
     k = np.arange(n_around) + 0.5
     th = np.arccos(1 - 2 * k / n_around)
     ph = np.pi * (1 + 5 ** 0.5) * k
     u = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
     c = np.array([50.0, 50.0, 50.0])
-    pos = np.vstack([c, c + (3.0 + 0.5 + 1.0) * u])
+    pos = np.vstack([c, c + (3.0 + gap + 1.0) * u])
     n = len(pos)
     r = np.r_[3.0, np.full(n_around, 1.0)].astype(np.float32)
     q = gen.random_quaternions(n, rng)
@@ -204,6 +204,22 @@ def test_more_partners_than_slots(prec):
     pl2 = lub.Pipeline(parts, dom, lub.default_params(), capacity=need)
     assert pl2.build_pairs() == len(pi)
     np.testing.assert_array_equal(pl2.results()["pj"], pj)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_more_partners_than_slots_on_the_filters_edge(prec):
+    """The crowded particle with its 30 partners at a gap of Delta_L - 2e-5:
+    every candidate lies inside the sweep's FP32 margin, so all are decided
+    after the sweep, and those accepted beyond the particle's 16 slots stay
+    in the buffer of decided candidates, where the compaction collects
+    them."""
+    parts, dom = crowded_particle(gap=1.0 - 2e-5)
+    pi, pj = oracle.candidates(parts, dom, 1.0)
+    assert np.sum(pi == 0) == 30
+    g = run_gpu(parts, dom, prec)
+    np.testing.assert_array_equal(g["pi"], pi)
+    np.testing.assert_array_equal(g["pj"], pj)
+    compare(parts, dom, g, oracle_ref(parts, dom, pi, pj), prec, pi, pj)
 
 
 def test_degenerate_pairs_are_flagged_not_faulted():
