@@ -196,8 +196,9 @@ constexpr int kNoEntry = 0x7fffffff;
 // well, so from the FP32 normal's ~1e-7 rad one step lands near 1e-13 rad.
 // The stepped normal m = n + s is normalised by 1 - (|m|^2 - 1)/2, |m|^2 - 1
 // of order 1e-7 (the next term is below 1e-14).  Out: nf the unit refined
-// normal, hf the gap (float-float).  Returns the step length (radians), or
-// infinity when the refined normal does not point from i towards j.
+// normal, hf the gap (float-float).  Returns the squared step length
+// (radians^2), or infinity when the refined normal does not point from i
+// towards j.
 __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], const ff oj[3], float api, float cpi,
                                                float apj, float cpj, const V3<float> n, ff nf[3], ff &hf)
 {
@@ -255,11 +256,11 @@ __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], co
     const float det = P11 * P22 - P12 * P12;
     float s1, s2;
     if (P11 > 0.f && det > 0.f) {
-        const float idet = 1.0f / det;
+        const float idet = rcp_fast(det);
         s1 = (P22 * G1 - P12 * G2) * idet;
         s2 = (P11 * G2 - P12 * G1) * idet;
     } else {
-        const float sc = 1.0f / (fabsf(P11) + fabsf(P22) + fabsf(P12) + Ai + Aj);
+        const float sc = rcp_fast(fabsf(P11) + fabsf(P22) + fabsf(P12) + Ai + Aj);
         s1 = G1 * sc;
         s2 = G2 * sc;
     }
@@ -278,9 +279,9 @@ __device__ __forceinline__ float polish_gap_ff(const ff d[3], const ff oi[3], co
     const float hem = -0.5f * (eps + (2.0f * ns + ss));
 #pragma unroll
     for (int a = 0; a < 3; ++a) nf[a] = fast_two_sum(m[a].hi, __fmaf_rn(hem, m[a].hi, m[a].lo));
-    const float step = sqrtf(s1 * s1 + s2 * s2);
+    const float step2 = s1 * s1 + s2 * s2;
     const float nd = m[0].hi * d[0].hi + m[1].hi * d[1].hi + m[2].hi * d[2].hi;
-    return (nd > 0.f && isfinite(step)) ? step : INFINITY;
+    return (nd > 0.f && isfinite(step2)) ? step2 : INFINITY;
 }
 
 // LUB_MIXED, FP32 stage of pair k = (i, j): FP32 Newton, then the
@@ -355,10 +356,10 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             const float scale = dl + fmaxf(rpi, rqi) + fmaxf(rpj, rqj);
             const NewtonOut o = newton_sphere<float>(si, sj, df, n, maxit, tol32, 4e-7f * scale);
             nit = o.iters;
-            const float step = polish_gap_ff(dff, oi, oj, rqi, rpi, rqj, rpj, n, nf, hf);
+            const float step2 = polish_gap_ff(dff, oi, oj, rqi, rpi, rqj, rpj, n, nf, hf);
             n64 = mk<double>(ff_to_double(nf[0]), ff_to_double(nf[1]), ff_to_double(nf[2]));
             h = ff_to_double(hf);
-            if (!o.converged || !(step < 1e-5f) || !isfinite(h)) {
+            if (!o.converged || !(step2 < 1e-10f) || !isfinite(h)) {
                 entry = -1 - k;
                 st |= LUB_ST_FP64;  // on the work list (solved again in FP64 next)
             }

@@ -265,7 +265,9 @@ __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt64(v); }
 __device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
 __device__ __forceinline__ double sqrt_t(double v) { return v > 0.0 ? v * rsqrt64(v) : 0.0; }
-__device__ __forceinline__ float rcp_t(float v) { return 1.0f / v; }
+// (the FP32 Newton step and the FP32 axis of the pair build's records take
+// the hardware reciprocal: about 1 ulp, far inside what either needs)
+__device__ __forceinline__ float rcp_t(float v) { return rcp_fast(v); }
 __device__ __forceinline__ double rcp_t(double v) { return rcp64(v); }
 __device__ __forceinline__ double sqrt_fast(double v) { return sqrt_t(v); }
 

@@ -415,8 +415,8 @@ __device__ __forceinline__ int2 row_window(const DView &D, const Grid &G, const 
     const float ez = dz == 0 ? 0.f : fmaxf(fabsf(oz - a0.z) - hz, 0.f);
     const float r2yz = ey * ey + ez * ez;
     if (r2yz > reach * reach) return make_int2(kNone, -kNone);
-    const float w = sqrtf(reach * reach - r2yz);
-    const float inv = 1.0f / G.cs[0];
+    const float w = sqrt_fast(reach * reach - r2yz);  // the margin covers its rounding
+    const float inv = G.inv_csf[0];
     const int nx = G.nc[0];
     int lo = row == 0 ? cx : cx + (int)floorf((a0.x - w) * inv + 0.5f);
     int hi = cx + (int)floorf((a0.x + w) * inv + 0.5f);
