@@ -345,8 +345,8 @@ __device__ __forceinline__ int closest_mixed_one(const PView &P, const DView &D0
             ff_axis_rec(rec_ld(pff, i, 2), rec_ld(pff, i, 3), oi);
             ff_axis_rec(rec_ld(pff, j, 2), rec_ld(pff, j, 3), oj);
             const Shape<float> si = shape_ff(oi, rpi, rqi), sj = shape_ff(oj, rpj, rqj);
-            const float dl = sqrtf(dd2);
-            V3<float> n = scl(1.0f / dl, df);
+            const float idl = rsqrtf(dd2), dl = dd2 * idl;  // Newton renormalises its start
+            V3<float> n = scl(idl, df);
             if (warm) {
                 const V3<float> w0 = mk<float>((float)nin[k], (float)nin[C + k], (float)nin[2 * C + k]);
                 const float wl2 = dot(w0, w0);

@@ -588,7 +588,7 @@ __device__ __forceinline__ void sweep_groups(const BuildView &V)
         const int i = own.x;
         pidx = i;
         const float rm2 = a0.w * a0.w;
-        const float sz = sqrtf(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
+        const float sz = sqrt_fast(fmaxf((a1.w > 0.f ? rm2 - a1.w : rm2) + a1.w * a1.z * a1.z, 0.f));
         int wf = 0, bits = 0;
         // z - z_w in float-float from the bits of both (no FP64 pipe)
         const ff zf = ff_split_bits_nan(P.z[i]);
