@@ -63,8 +63,8 @@ PAIRS_BYTES_PER_PAIR = 8.0       # (i, j) written
 # (one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum per kernel
 # over `bench.py --only large --steps 3`, the last of its three steps)
 TRAFFIC = {
-    "large": {"sources": "849edc8b3ad16d6a",
-              "bytes": {"pairs_build": 273368832, "k_closest_mixed": 372497664, "k_resistance_apply": 533056512}},
+    "large": {"sources": "f33b023ddd56a8f2",
+              "bytes": {"pairs_build": 274182656, "k_closest_mixed": 372022272, "k_resistance_apply": 496749056}},
 }
 TRAFFIC_SOURCES = ("closest.cu", "pair_force.cuh", "resistance.cu", "pairs.cu", "ff.cuh", "lub_internal.cuh",
                    "mlp_infer.cuh", "scan.cu", "scan_tile.cuh", "apply.cu")
