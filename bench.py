@@ -551,6 +551,30 @@ def e2e_large(args, lub, torch, np, parts, dom, dev, stream, rmax, net):
                    "step's result"}
 
 
+def cpu_model():
+    """The host CPU's model name and architecture, as the OS reports them."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return "%s (%s)" % (name or "unknown", platform.machine())
+
+
 def cpu_baseline(parts, dom, pairs0, budget_s=20.0):
     """The FP64 oracle, as it stands, on the host cores: closest points,
     forces and sums of the same workload's pairs (the list the GPU built from
@@ -582,7 +606,7 @@ def cpu_baseline(parts, dom, pairs0, budget_s=20.0):
     t1 = time.perf_counter()
     ci, _ = oracle.candidates(tile, tdom, 1.0)
     t_scan = time.perf_counter() - t1
-    return {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+    return {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": "all %d pairs of the first step, %d pass(es) of closest points + forces + sums (%d OpenMP "
                       "threads), %.1f s" % (len(pi), passes, cores, el),
             "candidate_scan": {"pairs_per_s": len(ci) / t_scan, "particles": n0, "pairs": int(len(ci)), "s": t_scan,
@@ -1048,7 +1072,7 @@ def run_reference(args):
            "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)", "pairs_per_step": m,
                       "sample": "the 16,384-particle slab of the packing (%d pairs), %d of them per step"
                                 % (len(pi), m)},
-           "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                             "sample": "%d pairs of the large run's growth-packed slab per step (closest points, "
                                       "forces, sums), %d OpenMP threads" % (m, cores)},
            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
